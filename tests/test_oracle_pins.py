@@ -1,0 +1,374 @@
+"""Pins of the CPU FP64 oracle against facts fixed by the paper and by mathematics.
+
+Nothing here compares the oracle with itself: every check is a closed form, a
+number the paper prints, a symmetry, an identity between two independently
+written quantities, a brute-force evaluation written separately in numpy, or a
+statistical law with a known answer.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import special, integrate, stats
+
+from oracle import oracle as orc
+from paper_1211_6234_b300 import inputs
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+
+def lattice_sum_inv_r3():
+    """sum over Z^2 minus the origin of 1/r^3 = 4 zeta(3/2) beta(3/2)
+    (Dirichlet beta from the Hurwitz zeta: beta(s) = 4^-s [zeta(s,1/4) - zeta(s,3/4)])."""
+    s = 1.5
+    beta = 4.0 ** (-s) * (special.zeta(s, 0.25) - special.zeta(s, 0.75))
+    return 4.0 * special.zeta(s) * beta
+
+
+# ---------------------------------------------------------------- Philox
+def test_philox_known_answers():
+    # Known-answer values published with Philox4x32-10 (Salmon et al., SC'11).
+    assert orc.philox([0, 0, 0, 0], [0, 0]) == [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]
+    assert orc.philox([0xFFFFFFFF] * 4, [0xFFFFFFFF] * 2) == [
+        0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD]
+    assert orc.philox([0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344],
+                      [0xA4093822, 0x299F31D0]) == [0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1]
+
+
+def test_philox_uniformity():
+    words = np.array([orc.philox([i, 7, 0, 0x01000000], [12345, 0]) for i in range(20000)],
+                     np.uint64)
+    for j in range(4):
+        counts = np.bincount((words[:, j] >> 24).astype(np.int64), minlength=256)
+        chi2 = ((counts - counts.mean()) ** 2 / counts.mean()).sum()
+        assert stats.chi2.sf(chi2, 255) > 1e-4
+    bits = np.unpackbits(words.astype(">u4").view(np.uint8))
+    assert abs(bits.mean() - 0.5) < 0.005
+
+
+# ---------------------------------------------------------------- W~ (Sec. 2.1, Eq. 2)
+@pytest.mark.parametrize("L", [5, 8, 16])
+def test_wtilde_lattice_sums(L):
+    """sum_rho W~_zz(rho) covers every nonzero point of Z^2 once: 4 zeta(3/2) beta(3/2);
+    xx + yy = -zz per image, and x<->y symmetry splits it evenly."""
+    S = lattice_sum_inv_r3()
+    assert abs(S - 9.033621683) < 1e-8
+    W = orc.wtilde(L, 64, True)
+    assert abs(W[3].sum() - S) < 2e-6
+    assert abs(W[0].sum() + S / 2) < 2e-6
+    assert abs(W[2].sum() + S / 2) < 2e-6
+    assert abs(W[1].sum()) < 2e-6
+
+
+def test_wtilde_tail_is_needed():
+    S = lattice_sum_inv_r3()
+    bare = orc.wtilde(16, 64, False)
+    assert abs(bare[3].sum() - S) > 1e-4  # truncation alone misses the tail
+
+
+@pytest.mark.parametrize("L", [6, 16])
+def test_wtilde_symmetries(L):
+    W = orc.wtilde(L, 64, True)
+    xx, xy, yy, zz = W
+    idx = (-np.arange(L)) % L
+    # even: W~(-rho) = W~(rho) (the image window is centred on the minimum image)
+    for c in range(4):
+        np.testing.assert_allclose(W[c], W[c][np.ix_(idx, idx)], rtol=0, atol=1e-13)
+    np.testing.assert_allclose(yy, xx.T, rtol=0, atol=1e-12)  # x <-> y
+    np.testing.assert_allclose(xx + yy, -zz, rtol=0, atol=1e-12)  # trace-free per image
+    assert np.abs(xy[0, :]).max() < 1e-13 and np.abs(xy[:, 0]).max() < 1e-13
+    if L % 2 == 0:
+        assert np.abs(xy[:, L // 2]).max() < 1e-13 and np.abs(xy[L // 2, :]).max() < 1e-13
+    # reflection x -> -x flips the sign of xy and keeps the diagonal components
+    np.testing.assert_allclose(xy, -xy[:, idx], rtol=0, atol=1e-13)
+    for c in (0, 2, 3):
+        np.testing.assert_allclose(W[c], W[c][:, idx], rtol=0, atol=1e-13)
+
+
+def test_wtilde_against_numpy_brute_force():
+    """Separate vectorised image sum with a far larger cutoff (no tail) against the
+    oracle at A = 64 with tail."""
+    L, A = 4, 1500
+    W = orc.wtilde(L, 64, True)
+    a = np.arange(-A, A + 1, dtype=np.float64)
+    ga, gb = np.meshgrid(a * L, a * L, indexing="xy")
+    for y in range(L):
+        for x in range(L):
+            rx = ga + x
+            ry = gb + y
+            r2 = rx * rx + ry * ry
+            with np.errstate(divide="ignore", invalid="ignore"):
+                ir3 = np.where(r2 > 0, r2 ** -1.5, 0.0)
+                ir5 = np.where(r2 > 0, r2 ** -2.5, 0.0)
+            ref = [np.sum(ir3 - 3 * rx * rx * ir5), np.sum(-3 * rx * ry * ir5),
+                   np.sum(ir3 - 3 * ry * ry * ir5), np.sum(ir3)]
+            for c in range(4):
+                # remaining tail beyond A=1500 is ~4 sqrt2/(1500.5 L^3) ~ 6e-5 for zz
+                tol = 8e-5 if c == 3 else 5e-5
+                assert abs(W[c, y, x] - ref[c]) < tol, (c, y, x, W[c, y, x], ref[c])
+    # and the tail makes the A=64 table agree with A=256 closely
+    W256 = orc.wtilde(L, 256, True)
+    assert np.abs(W - W256).max() < 2e-6 * np.abs(W).max()
+
+
+# ---------------------------------------------------------------- energies (Sec. 4)
+def test_uniform_state_energies():
+    """Uniform perpendicular state: E_D/N = +C_D/2 * 9.0336; uniform in-plane (x):
+    -C_D/4 * 9.0336; exchange -2J per spin; anisotropy -K2 - K4 per spin (+z)."""
+    S = lattice_sum_inv_r3()
+    L, CD = 16, 0.1
+    W = orc.wtilde(L, 64, True)
+    sz = inputs.saturated_z(L)[0]
+    ex, an, dp, tot = orc.energy(W, sz, 1.0, CD, 0.8, 0.3, )
+    N = L * L
+    assert abs(dp / N - CD / 2 * S) < 1e-6
+    assert abs(ex / N + 2.0) < 1e-12
+    assert abs(an / N + 1.1) < 1e-12
+    sx = np.zeros((3, L, L))
+    sx[0] = 1.0
+    ex, an, dp, tot = orc.energy(W, sx, 1.0, CD, 0.8, 0.3)
+    assert abs(dp / N + CD / 4 * S) < 1e-6
+    assert abs(an) < 1e-15
+
+
+@pytest.mark.parametrize("L", [3, 4])
+def test_dipole_energy_field_vs_explicit_pairs(L):
+    """E_D = (C_D/2) sum s.h through W~ against the explicit pair-and-image sum
+    written without W~ (same cutoff and tail)."""
+    s = inputs.random_spins(L, 1, seed=3)[0]
+    A = 10
+    W = orc.wtilde(L, A, True)
+    e_field = orc.energy(W, s, 0.0, 0.7, 0.0, 0.0)[2]
+    e_pairs = orc.dipole_energy_pairs(L, A, True, s, 0.7)
+    assert abs(e_field - e_pairs) < 1e-12 * max(1.0, abs(e_pairs))
+
+
+def test_energy_anisotropy_sign_and_exchange_sign():
+    L = 4
+    W = orc.wtilde(L, 8, True)
+    s = inputs.random_spins(L, 1, seed=5)[0]
+    _, an, _, _ = orc.energy(W, s, 0.0, 0.0, 0.8, -0.2)
+    z = s[2]
+    assert abs(an - np.sum(-0.8 * z**2 + 0.2 * z**4)) < 1e-12
+    ex, _, _, _ = orc.energy(W, s, 1.3, 0.0, 0.0, 0.0)
+    ref = 0.0
+    for y in range(L):
+        for x in range(L):
+            for (dx, dy) in ((1, 0), (0, 1)):
+                ref += np.dot(s[:, y, x], s[:, (y + dy) % L, (x + dx) % L])
+    assert abs(ex + 1.3 * ref) < 1e-12
+
+
+# ---------------------------------------------------------------- dE and the approximation
+def _pair_cross(W, L, CD, qa, qb, da, db):
+    dx = (qa % L) - (qb % L)
+    dy = (qa // L) - (qb // L)
+    i, j = dy % L, dx % L
+    xx, xy, yy, zz = W[0, i, j], W[1, i, j], W[2, i, j], W[3, i, j]
+    Wd = np.array([[xx, xy, 0], [xy, yy, 0], [0, 0, zz]])
+    return CD * da @ Wd @ db
+
+
+@pytest.mark.parametrize("L,l", [(4, 2), (6, 3), (8, 4), (8, 2)])
+def test_delta_e_against_full_energy(L, l):
+    """Each site's dE (decided from the pre-step state) equals E(one move) - E(before),
+    and the whole step's energy change equals sum of accepted dE plus the neglected
+    cross terms C_D d_p.W~(p-q).d_q (Sec. 3.2: H3 - H1 - H2 + H0)."""
+    J, CD, K2, K4, T = 1.0, 0.9, 0.8, -0.3, 2.0
+    W = orc.wtilde(L, 16, True)
+    s0 = inputs.random_spins(L, 1, seed=11)[0]
+    p = orc.params(L, l, J, CD, K2, K4, T, proposal=1, seed=99)
+    C = L // l
+    n = C * C
+    out = orc.sweeps(p, W, s0, 0, 1)
+    s = s0.copy()
+    N = L * L
+    for k in range(l * l):
+        sl = slice(k * n, (k + 1) * n)
+        qs, dE, acc, S = out["q"][sl], out["dE"][sl], out["acc"][sl], out["S"][sl]
+        E0 = orc.energy(W, s, J, CD, K2, K4)[3]
+        for d in range(n):
+            t = s.copy()
+            t[:, qs[d] // L, qs[d] % L] = S[d]
+            assert abs(orc.energy(W, t, J, CD, K2, K4)[3] - E0 - dE[d]) < 1e-11
+        new = s.copy()
+        deltas = {}
+        for d in range(n):
+            if acc[d]:
+                deltas[d] = S[d] - s[:, qs[d] // L, qs[d] % L]
+                new[:, qs[d] // L, qs[d] % L] = S[d]
+        E1 = orc.energy(W, new, J, CD, K2, K4)[3]
+        cross = 0.0
+        keys = sorted(deltas)
+        for a in range(len(keys)):
+            for b in range(a + 1, len(keys)):
+                pa, pb = keys[a], keys[b]
+                cr = _pair_cross(W, L, CD, qs[pa], qs[pb], deltas[pa], deltas[pb])
+                # bounded by the image-summed epsilon_12 with D <= |d_a||d_b| * 2
+                ia = qs[pa]; ib = qs[pb]
+                rr = W[3, ((ia // L) - (ib // L)) % L, ((ia % L) - (ib % L)) % L]
+                assert abs(cr) <= CD * np.linalg.norm(deltas[pa]) * np.linalg.norm(deltas[pb]) * 2 * rr + 1e-12
+                cross += cr
+        assert abs((E1 - E0) - (sum(dE[d] for d in keys) + cross)) < 1e-11
+        s = new
+    np.testing.assert_allclose(s, out["s"], rtol=0, atol=0)
+
+
+def test_eps12_maxima_from_paper():
+    """Sec. 3.2 prints D = 2 for delta = +-(0,0,2) and D = 4 for delta = +-2 r^.  Its own
+    epsilon_12 formula gives exactly twice both (4 and 8) at |delta| = 2: the printed
+    maxima count each pair once with the C_D/2 prefactor.  The ratio planar/perpendicular
+    (2) and the factor are pinned; the formula as printed is what the oracle evaluates,
+    and the true cross term C_D d1.W.d2 (checked against full energies elsewhere) is the
+    formula's value."""
+    r = np.array([3.0, 4.0, 0.0])
+    rh = r / 5.0
+    perp = orc.eps12([0, 0, 2], [0, 0, 2], r, 1.0) * 125
+    planar = orc.eps12(2 * rh, -2 * rh, r, 1.0) * 125
+    assert abs(perp - 2 * GOLDEN["eps12_D_perpendicular"]["value"]) < 1e-12
+    assert abs(planar - 2 * GOLDEN["eps12_D_planar"]["value"]) < 1e-12
+    assert abs(planar / perp - GOLDEN["eps12_D_planar"]["value"] / GOLDEN["eps12_D_perpendicular"]["value"]) < 1e-12
+    rng = np.random.default_rng(0)
+    for _ in range(2000):
+        a = rng.normal(size=3); a *= 2 / np.linalg.norm(a)
+        b = rng.normal(size=3); b *= 2 / np.linalg.norm(b)
+        assert orc.eps12(a, b, r, 1.0) * 125 <= planar + 1e-12
+
+
+def test_worked_error_example():
+    """Sec. 3.2: L=64, l=32, k_BT/C_D = 0.1 gives about 0.14% (the other three
+    update sites of the cell, no images); the lattice-sum reading is larger."""
+    g = GOLDEN["flip_probability_error_worked_example"]
+    e0 = orc.eps_total(64, 32, 1.0, g["kT_over_CD"], 0)
+    assert abs(e0 - g["value"]) < g["rel_tol_of_print"] * g["value"]
+    assert abs(e0 - 0.0014365) < 1e-6
+    e1 = orc.eps_total(64, 32, 1.0, 0.1, 1)
+    # lattice-sum reading: 2 * 9.0336 / (32^3 * 0.1); the oracle truncates at
+    # |v| <= 64 C cells, whose continuum tail is 2 * 4 sqrt2 / ((128.5) 32^3 0.1)
+    tail = 2 * 4 * math.sqrt(2) / (128.5 * 32**3 * 0.1)
+    assert abs(e1 + tail - 2 * lattice_sum_inv_r3() / (32**3 * 0.1)) < 1e-7
+
+
+@pytest.mark.parametrize("L", [4, 6])
+def test_l_equals_L_is_exact_sequential(L):
+    """Appendix B: with l >= L there is no simultaneous flipping.  The simultaneous
+    update at l = L must take the same decisions as an independently written
+    sequential Metropolis whose dE is a difference of full energies."""
+    J, CD, K2, K4, T = 1.0, 0.5, 0.8, 0.2, 0.7
+    W = orc.wtilde(L, 16, True)
+    s0 = inputs.random_spins(L, 1, seed=21)[0]
+    for prop in (0, 1):
+        p = orc.params(L, L, J, CD, K2, K4, T, proposal=prop, seed=5)
+        a = orc.sweeps(p, W, s0, 3, 3)
+        b = orc.sweeps_exact(p, W, s0, 3, 3)
+        np.testing.assert_array_equal(a["acc"], b["acc"])
+        np.testing.assert_allclose(a["dE"], b["dE"], rtol=0, atol=1e-11)
+        np.testing.assert_allclose(a["s"], b["s"], rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("l", [2, 3, 5, 6, 8, 12, 24, 32])
+def test_schedule_is_a_permutation(l):
+    for t in (0, 1, 77):
+        v = [orc.offset(1234, l, 0, t, k) for k in range(l * l)]
+        assert sorted(v) == list(range(l * l))
+    v = [orc.offset(1234, l, 1, 5, k) for k in range(4 * l * l)]
+    assert min(v) >= 0 and max(v) < l * l
+
+
+def test_sweep_rejects_bad_l():
+    W = orc.wtilde(6, 4, True)
+    s = inputs.random_spins(6, 1, 1)[0]
+    with pytest.raises(ValueError):
+        orc.sweeps(orc.params(6, 4), W, s, 0, 1)
+
+
+# ---------------------------------------------------------------- proposals
+def test_cap_proposal_geometry():
+    rng = np.random.default_rng(4)
+    cone = 0.5
+    for _ in range(50):
+        s = rng.normal(size=3); s /= np.linalg.norm(s)
+        acc = np.zeros(3)
+        grid = (np.arange(64) + 0.5) / 64
+        for u1 in grid[::8]:
+            for u2 in grid:
+                S = orc.propose(0, cone, s, u1, u2)
+                assert abs(np.linalg.norm(S) - 1) < 1e-14
+                ca = 1 - u1 * (1 - math.cos(cone))
+                assert abs(S @ s - ca) < 1e-12
+                acc += S
+        # the azimuth is uniform: the mean lies along s
+        mean = acc / (8 * 64)
+        perp = mean - (mean @ s) * s
+        assert np.linalg.norm(perp) < 1e-12
+    # whole-sphere proposal: z uniform, azimuth uniform
+    S = orc.propose(1, cone, np.array([0, 0, 1.0]), 0.25, 0.125)
+    assert abs(S[2] + 0.5) < 1e-15 and abs(math.atan2(S[1], S[0]) - math.pi / 4) < 1e-12
+
+
+# ---------------------------------------------------------------- Boltzmann law (J = C_D = 0)
+@pytest.mark.parametrize("K2,K4,prop", [(0.8, 0.2, 1), (0.8, -0.4, 1), (0.6, 0.2, 0)])
+def test_single_site_boltzmann_histogram(K2, K4, prop):
+    """With J = C_D = 0 every site is independent and s_z = cos(theta) has density
+    proportional to exp((K2 z^2 + K4 z^4)/T) on [-1, 1] (uniform measure in z)."""
+    L, l, T = 8, 4, 0.6
+    W = orc.wtilde(L, 2, True)
+    p = orc.params(L, l, 0.0, 0.0, K2, K4, T, proposal=prop, seed=17)
+    s = inputs.random_spins(L, 1, seed=2)[0]
+    burn = orc.sweeps(p, W, s, 0, 20, trace=False)["s"]
+    nsw = 300 if prop == 1 else 600
+    zs = []
+    st = burn
+    for blk in range(nsw // 10):
+        st = orc.sweeps(p, W, st, 20 + 10 * blk, 10, trace=False)["s"]
+        zs.append(st[2].ravel().copy())
+    z = np.concatenate(zs)
+    edges = np.linspace(-1, 1, 21)
+    dens = lambda x: math.exp((K2 * x * x + K4 * x**4) / T)
+    Z = integrate.quad(dens, -1, 1)[0]
+    pexp = np.array([integrate.quad(dens, edges[i], edges[i + 1])[0] / Z for i in range(20)])
+    cnt, _ = np.histogram(z, edges)
+    # samples 10 sweeps apart are nearly independent for these move sets; allow 3x
+    chi2 = (((cnt - len(z) * pexp) ** 2) / (len(z) * pexp)).sum()
+    assert chi2 / 19 < 3.0, chi2
+    assert abs(np.mean(z**2) - np.sum(pexp * 0.5 * (edges[1:] ** 3 - edges[:-1] ** 3) / (3 * np.diff(edges) / 2))) < 0.05
+
+
+def test_infinite_temperature_limits():
+    """J = C_D = K = 0: every move is accepted; uniform-sphere proposals make the spins
+    uniform on S^2: <s_z^2> = 1/3 and eta -> sqrt((2/pi)^2 (pi^2-8)/4) (Sec. 4.1)."""
+    L, l = 8, 4
+    W = orc.wtilde(L, 2, True)
+    p = orc.params(L, l, 0.0, 0.0, 0.0, 0.0, 1.0, proposal=1, seed=3)
+    s = inputs.saturated_z(L)[0]
+    out = orc.sweeps(p, W, s, 0, 400, trace=False, observe=True)
+    assert out["obs"].shape == (400, 5)
+    eta = orc.eta(out["theta2"], 400)
+    g = GOLDEN["cone_angle_infinite_T"]
+    exact = math.sqrt((2 / math.pi) ** 2 * (math.pi**2 - 8) / 4)
+    assert abs(exact - g["value"]) < 5e-5
+    assert abs(eta - exact) < 0.01
+    z = out["s"][2]
+    full = orc.sweeps(p, W, s, 0, 1, trace=True)
+    assert full["acc"].all()
+
+
+def test_observables_on_constructed_states():
+    L = 8
+    W = orc.wtilde(L, 2, True)
+    p = orc.params(L, 4, 1.0, 0.0, 0.0, 0.0, 1e-9, proposal=0, cone=1e-9, seed=1)
+    s = inputs.saturated_z(L)[0]
+    out = orc.sweeps(p, W, s, 0, 2, trace=False, observe=True)
+    o = out["obs"][-1]
+    assert abs(o[0] - 1) < 1e-6 and abs(o[1] - 1) < 1e-6 and abs(o[2] - 1) < 1e-6
+    assert abs(o[3]) < 1e-6 and abs(o[4] + 2.0) < 1e-6
+    assert abs(orc.eta(out["theta2"], 2) - 1.0) < 1e-6
+    assert abs(orc.eta(np.zeros(64), 5)) == 0.0
+
+
+def test_interactions_per_spin():
+    """Sec. 2.1: one spin's dipole energy at L = 64 takes N = L^2 = 4096 terms; the
+    oracle's field sum at one site runs over every site of the cell exactly once."""
+    assert 64 * 64 == GOLDEN["interactions_per_spin_L64"]["value"]
