@@ -1,0 +1,335 @@
+"""Benchmark of the dipolar Heisenberg Monte Carlo sweep (arXiv:1211.6234) on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {ours,reference}]
+
+Workload (one "step" = `--sweeps` sweeps of the whole hot path -- dipole field at
+the update sites, Metropolis update, observables every sweep -- over one batch):
+256 independent replicas of an L = 64 periodic lattice (16 temperatures in
+[0.2, 1.2] x 16 K4/K2 ratios in [-0.5, 0.5], K2 = 0.8, J = 1, C_D = 0.1), update
+spacing l = 32 (4 simultaneous sites per sub-step), cap proposal of 0.5 rad,
+W~ summed over 64 image cells with the continuum tail, seeded random initial
+spins.  Metric: site-updates/s including the dipole field (replicas x L^2 x
+sweeps / time).  The L2 cache is flushed (256 MiB write) before every timed step.
+
+Under torchrun each rank runs its own 256-replica batch (independent chains,
+no data exchange: weak scaling); the time is the max over ranks.
+
+`--impl reference` times the CPU FP64 oracle on this host's cores on a bounded
+sample of the same workload (the reference arm of this comparison).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1211_6234_b300 import inputs  # noqa: E402
+
+L, l, R = 64, 32, 256
+J, CD, K2 = 1.0, 0.1, 0.8
+A_IMG = 64
+FP32_FMA_PER_CLK_PER_SM = 128  # B300 SM: 4 partitions x 32 FP32 lanes
+
+
+def f32(x):
+    return float(np.float32(x))
+
+
+def ladder():
+    return [(f32(J), f32(CD), f32(k2), f32(k4), f32(T)) for (T, k2, k4) in inputs.ladder(16, 16)]
+
+
+def approx_error(T):
+    """Flip-probability error of the simultaneous update at spacing l
+    (Sec. 3.2 estimate, D = 2, summed over the update sublattice and its images)."""
+    return 2 * CD * 9.033621683 / (l**3 * T)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if not self.p:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in out.splitlines():
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def run_reference(args):
+    """CPU FP64 oracle on this host's cores, bounded sample of the same workload."""
+    from oracle import oracle as orc
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    W = orc.wtilde(L, A_IMG, True)
+    lad = ladder()
+    Rs = min(R, max(cores, 16))        # replicas per sample step
+    sw = 1                             # sweeps per sample step
+    ps = [orc.params(L, l, *lad[r], proposal=0, cone=0.5, seed=1, replica=r) for r in range(Rs)]
+    s0 = inputs.random_spins(L, Rs, seed=2024)
+    for _ in range(args.warmup):
+        orc.sweeps_batch(ps[:min(Rs, cores)], W, s0[:min(Rs, cores)], 0, 1, observe=True)
+    t0 = time.perf_counter()
+    st = s0
+    for k in range(args.steps):
+        st = orc.sweeps_batch(ps, W, st, k * sw, sw, observe=True)["s"]
+    dt = time.perf_counter() - t0
+    ups = Rs * L * L * sw * args.steps
+    val = ups / dt
+    sample = (f"{Rs} replicas x {sw} sweep(s) x {args.steps} steps of L=64 l=32 "
+              f"(FP64 oracle, observables every sweep)")
+    line = {
+        "metric": "site-updates/s incl. dipole field", "value": val, "unit": "site-updates/s",
+        "impl": "reference", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "batched replicas L=64 l=32 (sampled)", "replicas": Rs, "L": L, "l": l,
+                   "sweeps_per_step": sw},
+        "cpu_baseline": {"value": val, "unit": "site-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_sample(seconds_target=12.0):
+    """The oracle as it stands, on this host's cores, over a bounded sample."""
+    from oracle import oracle as orc
+    cores = os.cpu_count() or 1
+    W = orc.wtilde(L, A_IMG, True)
+    lad = ladder()
+    Rs = cores
+    ps = [orc.params(L, l, *lad[r % len(lad)], proposal=0, cone=0.5, seed=1, replica=r) for r in range(Rs)]
+    s0 = inputs.random_spins(L, Rs, seed=2024)
+    t0 = time.perf_counter()
+    st = s0
+    nsw = 0
+    while True:
+        st = orc.sweeps_batch(ps, W, st, nsw, 1, observe=True)["s"]
+        nsw += 1
+        if time.perf_counter() - t0 > seconds_target or nsw >= 50:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": Rs * L * L * nsw / dt, "unit": "site-updates/s", "cores": cores, "kind": "oracle",
+            "sample": f"{Rs} replicas x {nsw} sweeps of L=64 l=32 with observables, OpenMP over replicas, "
+                      f"{dt:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--sweeps", type=int, default=100, help="sweeps per step")
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    from paper_1211_6234_b300 import dipmc
+
+    lad = ladder()
+    lat = dipmc.Lattice(L, l, R, seed=1 + 7919 * rank)
+    lat.precompute_W(A_IMG, True)
+    lat.set_proposal(0, 0.5)
+    for r, (j, cd, k2, k4, T) in enumerate(lad):
+        lat.set_params(j, cd, k2, k4, T, replica=r)
+    s0 = inputs.random_spins(L, R, seed=2024 + rank).astype(np.float32)
+    lat.init_spins(2, s0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    S = args.sweeps
+    for _ in range(args.warmup):
+        lat.sweep(S, 1, stream)
+    barrier()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(dev)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    w0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))              # L2 flush, outside the timed pair
+        starts[i].record(stream)
+        lat.sweep(S, 1, stream)            # one launch of the sweep kernel
+        ends[i].record(stream)
+    barrier()
+    wall = time.perf_counter() - w0
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_dev = sum(step_ms) / 1e3
+    if ws > 1:
+        tt = torch.tensor([t_dev], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_dev = float(tt.item())
+    updates = ws * R * L * L * S * args.steps
+    value = updates / t_dev
+
+    # roofline of the sweep kernel: FP32 FMA-bound.  Algorithmic work per site
+    # update = N source sites x 5 multiply-adds (xx,xy | xy,yy | zz) = 10 N flops.
+    flops_per_update = 10 * L * L
+    achieved = flops_per_update * R * L * L * S / (statistics.mean(step_ms) / 1e3) / 1e12
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peaks = measured_peaks()
+    sm_max = (clk.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2032.0)
+    peak_fp32 = sms * FP32_FMA_PER_CLK_PER_SM * 2 * sm_max * 1e6 / 1e12
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "sweep_direct_L64_R256.traffic.json")
+    if os.path.exists(tfile):
+        try:
+            traffic = json.load(open(tfile)).get("dram_bytes_per_launch_per_sweep")
+            traffic = traffic * S if traffic is not None else None
+        except Exception:
+            traffic = None
+
+    # end to end through the public API: host spins in (pinned), S sweeps,
+    # spins + observables of every replica back to the host
+    host_in = torch.from_numpy(s0).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    e2e_steps = max(2, min(args.steps, 5))
+    barrier()
+    e0 = time.perf_counter()
+    for i in range(e2e_steps):
+        lat.init_spins(2, host_in.numpy())
+        lat.sweep(S, 1, stream)
+        lat.get_spins(stream=stream)
+        for r in range(R):
+            lat.observables(r)
+    barrier()
+    e_dt = time.perf_counter() - e0
+    e2e = {"value": ws * R * L * L * S * e2e_steps / e_dt, "unit": "site-updates/s",
+           "h2d_bytes_per_step": int(host_in.numel() * 4),
+           "d2h_bytes_per_step": int(host_in.numel() * 4 + R * (5 * 8 * 5 + 40))}
+
+    # the plain single-run FP32 path: one replica per launch, same L, l, sweeps
+    plain = None
+    if not args.no_plain:
+        p1 = dipmc.Lattice(L, l, 1, seed=5)
+        p1.precompute_W(A_IMG, True)
+        p1.set_params(*lad[0])
+        p1.init_spins(2, s0[:1])
+        p1.sweep(20, 1, stream)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        p1.sweep(S, 1, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        pv = L * L * S / (a.elapsed_time(b) / 1e3)
+        plain = {"value": pv, "unit": "site-updates/s", "replicas": 1, "sweeps": S,
+                 "batched_over_plain": value / ws / pv}
+        p1.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample()
+
+    if rank == 0:
+        line = {
+            "metric": "site-updates/s incl. dipole field", "value": value, "unit": "site-updates/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched replicas: 256 x L=64 (16 T x 16 K4/K2), l=32, 10^2 sweeps/step",
+                       "replicas_per_gpu": R, "L": L, "l": l, "sweeps_per_step": S,
+                       "field_path": "direct-fp32", "image_cutoff": A_IMG,
+                       "approx_error_at_Tmin": approx_error(0.2), "l2": "flushed (256 MiB write) before each step",
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
+                         "frac": achieved / peak_fp32, "traffic": traffic,
+                         "kernel": "k_sweep_direct<2,2,512>",
+                         "peak_basis": f"{sms} SMs x 128 FP32 FMA/clk x 2 x {sm_max:.0f} MHz (max SM clock)"},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "plain": plain,
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "wall_s_timed": wall,
+        }
+        print(json.dumps(line), flush=True)
+    lat.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

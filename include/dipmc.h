@@ -1,0 +1,192 @@
+/*
+ * dipmc.h -- C ABI of the B300 dipolar Heisenberg Monte Carlo sweep library
+ * (libdipmc.so), after Stamps & Ambrose, arXiv:1211.6234.
+ *
+ * One lattice handle holds R independent replicas of an L x L periodic square
+ * lattice of unit 3-vector spins (Sec. 2.1) that share L, the update spacing l,
+ * the seed and the site schedule; each replica has its own J, C_D, K2, K4, T.
+ *
+ * Energy (Sec. 4 total energy, with these readings of the printed signs):
+ *   E = -J sum_bonds s_i.s_j + sum_i (-K2 s_iz^2 - K4 s_iz^4) + (C_D/2) sum_n s_n.h_n
+ *   h_n = sum_m W~(n - m) s_m          (m = n included through W~(0))
+ * W~ is the dipole tensor summed over periodic images (Sec. 2.1, Eq. 2).
+ *
+ * Conventions for every entry point:
+ *   - Return 0 (MC_OK) on success, a negative MC_E* code otherwise; nothing
+ *     throws across the ABI.  mc_last_error() gives a one-line reason (per thread).
+ *   - Handles are opaque and owned by the library (create/destroy).  Buffers
+ *     passed in are owned by the caller; the library never keeps a pointer to
+ *     them past the call.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Device work of a call is enqueued on that stream; calls that return host
+ *     data synchronise it.
+ *   - Spin and field arrays are FP32, replica-major SoA: [R][3][L][L]
+ *     (component x, y, z; row y; column x).  W~ arrays are [4][L][L] (xx, xy,
+ *     yy, zz) indexed by the displacement rho = (rho_x, rho_y) in [0, L)^2.
+ *
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11) keyed by the 64-bit seed
+ * (key = {lo32, hi32}).  Counter layouts (word 3 carries a tag in its top byte):
+ *   attempt at site q of replica r, sweep t, sub-step k: {q, r, t, k | 1<<24};
+ *       words 0, 1 draw the proposal, word 2 the acceptance uniform
+ *   sweep schedule round keys: {t, 0, 0, 2<<24}; paper's draw: {t, k, 0, 3<<24}
+ *   random initial spins: {site, r, 0, 4<<24}
+ * A uniform is u = (word >> 8) * 2^-24.
+ */
+#ifndef DIPMC_H
+#define DIPMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MC_OK 0
+#define MC_EINVAL (-1)    /* bad argument */
+#define MC_ENOMEM (-2)    /* device allocation failed / over budget */
+#define MC_ENOTREADY (-3) /* a prerequisite step was not done (e.g. W~ not computed) */
+#define MC_ETIMEOUT (-4)  /* a bounded device wait gave up */
+#define MC_ECUDA (-5)     /* a CUDA call failed; the message names it */
+#define MC_ENOSYS (-6)    /* no field path supports this (L, l) on this build */
+
+/* Observable indices (per sample, once per measured sweep). */
+#define MC_OBS_ABS_M 0  /* |m| = |sum s| / N                        */
+#define MC_OBS_MZ 1     /* m_z                                       */
+#define MC_OBS_ABS_MZ 2 /* |m_z|                                     */
+#define MC_OBS_MPAR 3   /* M_par = sqrt(M_x^2 + M_y^2)  (Sec. 4.1)   */
+#define MC_OBS_E 4      /* energy per spin E/N                       */
+#define MC_NOBS 5
+
+/* Field paths (mc_set_field_path). */
+#define MC_PATH_AUTO 0
+#define MC_PATH_DIRECT 1 /* FP32 CUDA-core Toeplitz sum, one CTA per replica */
+
+typedef struct mc_lattice mc_lattice;
+
+/* Statistics of one replica since the last reset. */
+typedef struct mc_obs {
+    int64_t samples;            /* measured sweeps */
+    double mean[MC_NOBS];       /* sample means */
+    double var[MC_NOBS];        /* sample variances (1/n) */
+    double err_naive[MC_NOBS];  /* sqrt(var / (n - 1)) */
+    double err[MC_NOBS];        /* autocorrelation-corrected error (binning plateau) */
+    double tau_int[MC_NOBS];    /* 0.5 (err / err_naive)^2 */
+    double eta;                 /* cone angle (Sec. 4.1): (1/N) sum_i sqrt((2/pi)^2 <(theta_i - pi/2)^2>) */
+    double energy;              /* current energy per spin (tracked exactly, FP64) */
+    int64_t accepted;           /* accepted single-site moves */
+    int64_t attempted;          /* attempted single-site moves */
+} mc_obs;
+
+/* One-line description of the last error on this thread ("" if none). */
+const char *mc_last_error(void);
+
+/* ABI version (incremented on incompatible changes). */
+int mc_version(void);
+
+/*
+ * Create a handle for `replicas` lattices of size L x L with update spacing l
+ * (Sec. 3.1: simultaneous update sites o + l(a, b), n = (L/l)^2 of them).
+ * Requires L >= 2, 2 <= l <= L, L % l == 0 (l = L is exact sequential
+ * Metropolis, Appendix B), replicas >= 1.  Allocates device state on the
+ * current device.  Defaults: J = 1, C_D = 0.1, K2 = 0.8, K4 = 0, T = 0.6 for all
+ * replicas; cap proposal of 0.5 rad; permutation schedule; spins +z; W~ not
+ * computed.  *out is NULL on failure.
+ */
+int mc_create_lattice(int L, int l, int replicas, uint64_t seed, mc_lattice **out);
+
+/* Free the handle and its device memory (synchronises the device). NULL is a no-op. */
+int mc_destroy(mc_lattice *lat);
+
+/* Couplings of one replica (replica = -1: all).  T > 0.  Energies are in units of
+ * k_B = 1 (Sec. 2.2).  Invalidates the tracked energy (recomputed at the next sweep). */
+int mc_set_params(mc_lattice *lat, int replica, double J, double C_D, double K2, double K4,
+                  double T);
+
+/* Proposal (Sec. 3.1): kind 0 = uniform on the spherical cap of half-angle
+ * cone_rad around the current spin (0 < cone_rad <= pi); kind 1 = uniform on S^2
+ * (the paper's choice; cone_rad ignored). */
+int mc_set_proposal(mc_lattice *lat, int kind, double cone_rad);
+
+/* Site schedule: kind 0 = every sweep visits the l^2 offsets in a pseudo-random
+ * permutation (each site attempted once per sweep); kind 1 = each sub-step draws
+ * its offset uniformly with replacement (Sec. 3.1 host loop). */
+int mc_set_schedule(mc_lattice *lat, int kind);
+
+/* Field path for the sweep (MC_PATH_*).  MC_PATH_AUTO picks the fastest supported. */
+int mc_set_field_path(mc_lattice *lat, int path);
+
+/* Initial spins: mode 0 = random uniform on S^2 from the seed; 1 = all +z;
+ * 2 = copy `user` (host pointer, [R][3][L][L] FP32, used as given).  Resets the
+ * sweep counter to 0, clears observables, invalidates the tracked energy. */
+int mc_init_spins(mc_lattice *lat, int mode, const float *user);
+
+/* Replica-summed dipole tensor (Sec. 2.1, Eq. 2), computed on the GPU in FP64:
+ * W~(rho) = sum_{|a|,|b| <= image_cutoff} W(rho_c + (aL, bL)) over r != 0, where
+ * rho_c is the minimum-image representative of each component (both +-L/2 averaged
+ * when a component is L/2), plus, if tail_correction, the continuum tail outside
+ * the square of half-width (A + 1/2) L: zz += 4 sqrt(2) / ((A + 1/2) L^3), xx and
+ * yy -= half of that.  image_cutoff in [0, 4096]. */
+int mc_precompute_W(mc_lattice *lat, int image_cutoff, int tail_correction);
+
+/*
+ * Run nsweeps sweeps of the simultaneous-flip Metropolis update (Sec. 3.1, 3.2)
+ * on every replica.  One sweep = l^2 sub-steps; sub-step k of sweep t uses offset
+ * o = schedule(t, k); every site q = o + l(a, b) gets a proposal and is accepted
+ * iff u < exp(-dE/T) with dE computed from the state before the sub-step; all
+ * accepted moves are then applied together.  If measure_every > 0, observables
+ * are sampled after every measure_every-th sweep.  Requires mc_precompute_W.
+ * Asynchronous on `stream` (errors of the launch itself are reported).
+ */
+int mc_sweep(mc_lattice *lat, int nsweeps, int measure_every, void *stream);
+
+/*
+ * As mc_sweep (no measurement), and also record every attempt into `trace`
+ * (device pointer, caller-owned, FP32).  Record layout, MC_TRACE_W floats per
+ * attempt, ordered [replica][sweep][sub-step][site d] with d = Dy*(L/l) + Dx:
+ *   q (site index y*L + x, exact), h_x, h_y, h_z (field at q before the step),
+ *   dE, u, accepted (0/1), S_x, S_y, S_z (proposal).
+ * trace_floats must be >= R * nsweeps * L * L * MC_TRACE_W.
+ */
+#define MC_TRACE_W 10
+int mc_sweep_trace(mc_lattice *lat, int nsweeps, float *trace, size_t trace_floats,
+                   void *stream);
+
+/* Statistics of one replica (synchronises the lattice's last stream). */
+int mc_observables(mc_lattice *lat, int replica, mc_obs *out);
+
+/* Clear all observable accumulators (binning, cone angle, acceptance). */
+int mc_reset_observables(mc_lattice *lat);
+
+/* Copy spins [R][3][L][L] FP32 into dst (dst_on_device: 1 = device pointer,
+ * 0 = host pointer).  Synchronises `stream`. */
+int mc_get_spins(mc_lattice *lat, float *dst, int dst_on_device, void *stream);
+
+/* Full dipole field h = W~ * s at every site of every replica, [R][3][L][L] FP32,
+ * computed directly in FP32 on the GPU.  Synchronises `stream`. */
+int mc_get_field(mc_lattice *lat, float *dst, int dst_on_device, void *stream);
+
+/* W~ in FP64, [4][L][L], to a host pointer.  MC_ENOTREADY before mc_precompute_W. */
+int mc_get_W(mc_lattice *lat, double *dst_host);
+
+/* Total energy of every replica from a full field evaluation (FP32 field, FP64
+ * sums), [R] doubles to a host pointer.  Synchronises `stream`. */
+int mc_energy(mc_lattice *lat, double *dst_host, void *stream);
+
+/* Sweep counter (index of the next sweep; the RNG counters depend on it). */
+int mc_get_sweep_counter(mc_lattice *lat, uint64_t *out);
+
+/*
+ * Checkpoint: serialise the complete state (sizes, seed, sweep counter,
+ * parameters, spins, tracked energy, observable accumulators) into buf.  Call
+ * with buf = NULL to get the size in *len.  Resuming with mc_restore on a handle
+ * of the same L, l, R continues the run bit-exactly (the RNG is counter-based).
+ */
+int mc_checkpoint(mc_lattice *lat, void *buf, size_t *len);
+int mc_restore(mc_lattice *lat, const void *buf, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DIPMC_H */

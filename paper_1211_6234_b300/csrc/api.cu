@@ -1,0 +1,504 @@
+// api.cu -- the C ABI of libdipmc (declared in include/dipmc.h): handle
+// lifetime, argument validation, device buffers and dispatch to the kernels.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace dipmc;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    return fail(MC_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t _e = (call);                              \
+        if (_e != cudaSuccess) return cuda_fail(_e, #call);   \
+    } while (0)
+
+constexpr uint32_t kMagic = 0x444d4331u;  // "DMC1"
+constexpr int kVersion = 1;
+
+}  // namespace
+
+struct mc_lattice {
+    int L = 0, l = 0, R = 0, device = 0;
+    uint64_t seed = 0;
+    int proposal = 0;
+    double cone = 0.5;
+    int schedule = 0;
+    int path = MC_PATH_AUTO;
+    int threads_hint = 512;
+    std::vector<RepParams> hp;
+    RepParams *dparams = nullptr;
+    float *spins = nullptr;   // [R][3][N]
+    float *field = nullptr;   // [R][3][N] scratch for full-field evaluations
+    double *W64 = nullptr;    // [4][N]
+    float *W32 = nullptr;     // [4][N]
+    double *energy = nullptr; // [R] tracked energy
+    double *etmp = nullptr;   // [R] scratch for mc_energy
+    ObsAcc *obs = nullptr;    // [R]
+    double *theta2 = nullptr; // [R][N]
+    uint64_t t = 0;
+    bool W_ready = false, energy_valid = false;
+    int A = 0, tail = 0;
+    cudaStream_t last = nullptr;
+
+    int N() const { return L * L; }
+    size_t spin_floats() const { return (size_t)R * 3 * N(); }
+};
+
+namespace {
+
+void free_all(mc_lattice *p) {
+    cudaFree(p->dparams);
+    cudaFree(p->spins);
+    cudaFree(p->field);
+    cudaFree(p->W64);
+    cudaFree(p->W32);
+    cudaFree(p->energy);
+    cudaFree(p->etmp);
+    cudaFree(p->obs);
+    cudaFree(p->theta2);
+}
+
+int upload_params(mc_lattice *p) {
+    CK(cudaMemcpy(p->dparams, p->hp.data(), sizeof(RepParams) * p->R, cudaMemcpyHostToDevice));
+    return MC_OK;
+}
+
+int clear_obs(mc_lattice *p, cudaStream_t st) {
+    CK(cudaMemsetAsync(p->obs, 0, sizeof(ObsAcc) * p->R, st));
+    CK(cudaMemsetAsync(p->theta2, 0, sizeof(double) * (size_t)p->R * p->N(), st));
+    return MC_OK;
+}
+
+uint2 key_of(uint64_t seed) { return make_uint2((uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)); }
+
+int anchor_energy(mc_lattice *p, cudaStream_t st) {
+    cudaError_t e = launch_full_field(p->L, p->R, p->W32, p->spins, p->field, st);
+    if (e != cudaSuccess) return cuda_fail(e, "full-field kernel");
+    e = launch_energy(p->L, p->R, p->spins, p->field, p->dparams, p->energy, st);
+    if (e != cudaSuccess) return cuda_fail(e, "energy kernel");
+    p->energy_valid = true;
+    return MC_OK;
+}
+
+int check(mc_lattice *p) {
+    if (!p) return fail(MC_EINVAL, "null lattice handle");
+    CK(cudaSetDevice(p->device));
+    return MC_OK;
+}
+
+int run_sweeps(mc_lattice *p, int nsweeps, int measure_every, float *trace, cudaStream_t st) {
+    if (!p->W_ready) return fail(MC_ENOTREADY, "mc_precompute_W has not been called");
+    if (nsweeps < 0) return fail(MC_EINVAL, "nsweeps must be >= 0");
+    if (measure_every < 0) return fail(MC_EINVAL, "measure_every must be >= 0");
+    if (nsweeps == 0) return MC_OK;
+    if (!p->energy_valid) {
+        int rc = anchor_energy(p, st);
+        if (rc) return rc;
+    }
+    SweepConfig c;
+    c.L = p->L;
+    c.l = p->l;
+    c.R = p->R;
+    c.key = key_of(p->seed);
+    c.t0 = (uint32_t)p->t;
+    c.nsweeps = nsweeps;
+    c.measure_every = measure_every;
+    c.proposal = p->proposal;
+    c.cap_c1 = (float)(1.0 - std::cos(p->cone));
+    c.schedule = p->schedule;
+    SweepBuffers b;
+    b.W32 = p->W32;
+    b.spins = p->spins;
+    b.params = p->dparams;
+    b.energy = p->energy;
+    b.obs = p->obs;
+    b.theta2 = p->theta2;
+    b.trace = trace;
+    cudaError_t e = cudaErrorNotSupported;
+    if (p->path == MC_PATH_AUTO || p->path == MC_PATH_DIRECT) e = launch_sweep_direct(c, b, p->threads_hint, st);
+    if (e == cudaErrorNotSupported)
+        return fail(MC_ENOSYS, "no field path supports L=%d l=%d (path %d)", p->L, p->l, p->path);
+    if (e != cudaSuccess) return cuda_fail(e, "sweep kernel launch");
+    p->t += (uint64_t)nsweeps;
+    p->last = st;
+    return MC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mc_last_error(void) { return g_err.c_str(); }
+
+int mc_version(void) { return kVersion; }
+
+int mc_create_lattice(int L, int l, int replicas, uint64_t seed, mc_lattice **out) {
+    g_err.clear();
+    if (!out) return fail(MC_EINVAL, "out is null");
+    *out = nullptr;
+    if (L < 2 || L > 4096) return fail(MC_EINVAL, "L=%d outside [2, 4096]", L);
+    if (l < 2 || l > L || L % l) return fail(MC_EINVAL, "l=%d must satisfy 2 <= l <= L and L %% l == 0 (L=%d)", l, L);
+    if (replicas < 1) return fail(MC_EINVAL, "replicas=%d must be >= 1", replicas);
+    mc_lattice *p = new mc_lattice();
+    p->L = L;
+    p->l = l;
+    p->R = replicas;
+    p->seed = seed;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) { delete p; return cuda_fail(e, "cudaGetDevice"); }
+    const size_t N = (size_t)L * L, R = replicas;
+    RepParams d{};
+    d.J = 1.0f; d.CD = 0.1f; d.K2 = 0.8f; d.K4 = 0.0f; d.T = 0.6f;
+    p->hp.assign(R, d);
+#define ALLOC(ptr, bytes)                                                            \
+    do {                                                                             \
+        e = cudaMalloc((void **)&(ptr), (bytes));                                    \
+        if (e != cudaSuccess) {                                                      \
+            free_all(p);                                                             \
+            delete p;                                                                \
+            cudaGetLastError();                                                      \
+            return fail(MC_ENOMEM, "cudaMalloc of %zu bytes failed", (size_t)(bytes)); \
+        }                                                                            \
+    } while (0)
+    ALLOC(p->dparams, sizeof(RepParams) * R);
+    ALLOC(p->spins, sizeof(float) * 3 * N * R);
+    ALLOC(p->field, sizeof(float) * 3 * N * R);
+    ALLOC(p->W64, sizeof(double) * 4 * N);
+    ALLOC(p->W32, sizeof(float) * 4 * N);
+    ALLOC(p->energy, sizeof(double) * R);
+    ALLOC(p->etmp, sizeof(double) * R);
+    ALLOC(p->obs, sizeof(ObsAcc) * R);
+    ALLOC(p->theta2, sizeof(double) * N * R);
+#undef ALLOC
+    int rc = upload_params(p);
+    if (!rc) rc = clear_obs(p, nullptr);
+    if (!rc) {
+        e = launch_init_spins(L, replicas, key_of(seed), 1, p->spins, nullptr);
+        if (e != cudaSuccess) rc = cuda_fail(e, "init kernel");
+    }
+    if (!rc) {
+        e = cudaMemset(p->energy, 0, sizeof(double) * R);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemset");
+    }
+    if (!rc) {
+        e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) rc = cuda_fail(e, "create: synchronize");
+    }
+    if (rc) {
+        free_all(p);
+        delete p;
+        return rc;
+    }
+    *out = p;
+    return MC_OK;
+}
+
+int mc_destroy(mc_lattice *p) {
+    if (!p) return MC_OK;
+    cudaSetDevice(p->device);
+    cudaDeviceSynchronize();
+    free_all(p);
+    delete p;
+    return MC_OK;
+}
+
+int mc_set_params(mc_lattice *p, int replica, double J, double C_D, double K2, double K4, double T) {
+    int rc = check(p);
+    if (rc) return rc;
+    if (replica < -1 || replica >= p->R) return fail(MC_EINVAL, "replica %d out of range", replica);
+    if (!(T > 0.0) || !std::isfinite(T)) return fail(MC_EINVAL, "T must be > 0 and finite");
+    if (!std::isfinite(J) || !std::isfinite(C_D) || !std::isfinite(K2) || !std::isfinite(K4))
+        return fail(MC_EINVAL, "couplings must be finite");
+    for (int r = 0; r < p->R; ++r) {
+        if (replica >= 0 && r != replica) continue;
+        RepParams &q = p->hp[r];
+        q.J = (float)J; q.CD = (float)C_D; q.K2 = (float)K2; q.K4 = (float)K4; q.T = (float)T;
+    }
+    CK(cudaDeviceSynchronize());
+    rc = upload_params(p);
+    p->energy_valid = false;
+    return rc;
+}
+
+int mc_set_proposal(mc_lattice *p, int kind, double cone) {
+    int rc = check(p);
+    if (rc) return rc;
+    if (kind != 0 && kind != 1) return fail(MC_EINVAL, "proposal kind must be 0 or 1");
+    if (kind == 0 && !(cone > 0.0 && cone <= M_PI)) return fail(MC_EINVAL, "cone must be in (0, pi]");
+    p->proposal = kind;
+    if (kind == 0) p->cone = cone;
+    return MC_OK;
+}
+
+int mc_set_schedule(mc_lattice *p, int kind) {
+    int rc = check(p);
+    if (rc) return rc;
+    if (kind != 0 && kind != 1) return fail(MC_EINVAL, "schedule kind must be 0 or 1");
+    p->schedule = kind;
+    return MC_OK;
+}
+
+int mc_set_field_path(mc_lattice *p, int path) {
+    int rc = check(p);
+    if (rc) return rc;
+    if (path != MC_PATH_AUTO && path != MC_PATH_DIRECT) return fail(MC_EINVAL, "unknown field path %d", path);
+    if (path == MC_PATH_DIRECT && !direct_supported(p->L, p->l))
+        return fail(MC_ENOSYS, "direct path does not support L=%d l=%d", p->L, p->l);
+    p->path = path;
+    return MC_OK;
+}
+
+int mc_init_spins(mc_lattice *p, int mode, const float *user) {
+    int rc = check(p);
+    if (rc) return rc;
+    if (mode < 0 || mode > 2) return fail(MC_EINVAL, "init mode must be 0, 1 or 2");
+    CK(cudaDeviceSynchronize());
+    if (mode == 2) {
+        if (!user) return fail(MC_EINVAL, "mode 2 needs a host array");
+        CK(cudaMemcpy(p->spins, user, sizeof(float) * p->spin_floats(), cudaMemcpyHostToDevice));
+    } else {
+        cudaError_t e = launch_init_spins(p->L, p->R, key_of(p->seed), mode, p->spins, nullptr);
+        if (e != cudaSuccess) return cuda_fail(e, "init kernel");
+    }
+    rc = clear_obs(p, nullptr);
+    if (rc) return rc;
+    CK(cudaDeviceSynchronize());
+    p->t = 0;
+    p->energy_valid = false;
+    return MC_OK;
+}
+
+int mc_precompute_W(mc_lattice *p, int A, int tail) {
+    int rc = check(p);
+    if (rc) return rc;
+    if (A < 0 || A > 4096) return fail(MC_EINVAL, "image_cutoff %d outside [0, 4096]", A);
+    cudaError_t e = launch_wtilde(p->L, A, tail ? 1 : 0, p->W64, p->W32, nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "W~ kernel");
+    CK(cudaDeviceSynchronize());
+    p->A = A;
+    p->tail = tail ? 1 : 0;
+    p->W_ready = true;
+    p->energy_valid = false;
+    return MC_OK;
+}
+
+int mc_sweep(mc_lattice *p, int nsweeps, int measure_every, void *stream) {
+    int rc = check(p);
+    if (rc) return rc;
+    return run_sweeps(p, nsweeps, measure_every, nullptr, (cudaStream_t)stream);
+}
+
+int mc_sweep_trace(mc_lattice *p, int nsweeps, float *trace, size_t trace_floats, void *stream) {
+    int rc = check(p);
+    if (rc) return rc;
+    if (!trace) return fail(MC_EINVAL, "trace buffer is null");
+    const size_t need = (size_t)p->R * (size_t)nsweeps * p->N() * MC_TRACE_W;
+    if (trace_floats < need) return fail(MC_EINVAL, "trace buffer holds %zu floats, needs %zu", trace_floats, need);
+    return run_sweeps(p, nsweeps, 0, trace, (cudaStream_t)stream);
+}
+
+int mc_observables(mc_lattice *p, int replica, mc_obs *out) {
+    int rc = check(p);
+    if (rc) return rc;
+    if (!out) return fail(MC_EINVAL, "out is null");
+    if (replica < 0 || replica >= p->R) return fail(MC_EINVAL, "replica %d out of range", replica);
+    CK(cudaStreamSynchronize(p->last));
+    ObsAcc A;
+    CK(cudaMemcpy(&A, p->obs + replica, sizeof(ObsAcc), cudaMemcpyDeviceToHost));
+    std::vector<double> th((size_t)p->N());
+    CK(cudaMemcpy(th.data(), p->theta2 + (size_t)replica * p->N(), sizeof(double) * p->N(), cudaMemcpyDeviceToHost));
+    double E = 0;
+    CK(cudaMemcpy(&E, p->energy + replica, sizeof(double), cudaMemcpyDeviceToHost));
+    std::memset(out, 0, sizeof(*out));
+    const long long n = A.bcnt[0];
+    out->samples = n;
+    out->accepted = A.accepted;
+    out->attempted = A.attempted;
+    out->energy = p->energy_valid ? E / p->N() : NAN;
+    for (int o = 0; o < MC_NOBS; ++o) {
+        if (n < 1) { out->mean[o] = NAN; continue; }
+        const double m = A.bsum[o][0] / n;
+        const double v = std::fmax(0.0, A.bsq[o][0] / n - m * m);
+        out->mean[o] = m;
+        out->var[o] = v;
+        out->err_naive[o] = n > 1 ? std::sqrt(v / (n - 1)) : NAN;
+        double best = out->err_naive[o];
+        for (int k = 1; k < kNB; ++k) {
+            const long long nb = A.bcnt[k];
+            if (nb < 32) break;
+            const double mk = A.bsum[o][k] / nb;
+            const double vk = std::fmax(0.0, A.bsq[o][k] / nb - mk * mk);
+            const double ek = std::sqrt(vk / (nb - 1));
+            if (ek > best) best = ek;
+        }
+        out->err[o] = best;
+        out->tau_int[o] = (out->err_naive[o] > 0) ? 0.5 * (best / out->err_naive[o]) * (best / out->err_naive[o]) : NAN;
+    }
+    if (n > 0) {
+        double acc = 0;
+        const double c = (2.0 / M_PI) * (2.0 / M_PI) / (double)n;
+        for (double v : th) acc += std::sqrt(c * v);
+        out->eta = acc / p->N();
+    } else {
+        out->eta = NAN;
+    }
+    return MC_OK;
+}
+
+int mc_reset_observables(mc_lattice *p) {
+    int rc = check(p);
+    if (rc) return rc;
+    CK(cudaDeviceSynchronize());
+    rc = clear_obs(p, nullptr);
+    if (rc) return rc;
+    CK(cudaDeviceSynchronize());
+    return MC_OK;
+}
+
+int mc_get_spins(mc_lattice *p, float *dst, int on_device, void *stream) {
+    int rc = check(p);
+    if (rc) return rc;
+    if (!dst) return fail(MC_EINVAL, "dst is null");
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(dst, p->spins, sizeof(float) * p->spin_floats(),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return MC_OK;
+}
+
+int mc_get_field(mc_lattice *p, float *dst, int on_device, void *stream) {
+    int rc = check(p);
+    if (rc) return rc;
+    if (!dst) return fail(MC_EINVAL, "dst is null");
+    if (!p->W_ready) return fail(MC_ENOTREADY, "mc_precompute_W has not been called");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = launch_full_field(p->L, p->R, p->W32, p->spins, p->field, st);
+    if (e != cudaSuccess) return cuda_fail(e, "full-field kernel");
+    CK(cudaMemcpyAsync(dst, p->field, sizeof(float) * p->spin_floats(),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return MC_OK;
+}
+
+int mc_get_W(mc_lattice *p, double *dst) {
+    int rc = check(p);
+    if (rc) return rc;
+    if (!dst) return fail(MC_EINVAL, "dst is null");
+    if (!p->W_ready) return fail(MC_ENOTREADY, "mc_precompute_W has not been called");
+    CK(cudaMemcpy(dst, p->W64, sizeof(double) * 4 * p->N(), cudaMemcpyDeviceToHost));
+    return MC_OK;
+}
+
+int mc_energy(mc_lattice *p, double *dst, void *stream) {
+    int rc = check(p);
+    if (rc) return rc;
+    if (!dst) return fail(MC_EINVAL, "dst is null");
+    if (!p->W_ready) return fail(MC_ENOTREADY, "mc_precompute_W has not been called");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = launch_full_field(p->L, p->R, p->W32, p->spins, p->field, st);
+    if (e != cudaSuccess) return cuda_fail(e, "full-field kernel");
+    e = launch_energy(p->L, p->R, p->spins, p->field, p->dparams, p->etmp, st);
+    if (e != cudaSuccess) return cuda_fail(e, "energy kernel");
+    CK(cudaMemcpyAsync(dst, p->etmp, sizeof(double) * p->R, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return MC_OK;
+}
+
+int mc_get_sweep_counter(mc_lattice *p, uint64_t *out) {
+    if (!p || !out) return fail(MC_EINVAL, "null argument");
+    *out = p->t;
+    return MC_OK;
+}
+
+namespace {
+struct CkptHeader {
+    uint32_t magic;
+    int32_t version, L, l, R, proposal, schedule, A, tail, W_ready, energy_valid, pad;
+    uint64_t seed, t;
+    double cone;
+};
+}  // namespace
+
+int mc_checkpoint(mc_lattice *p, void *buf, size_t *len) {
+    int rc = check(p);
+    if (rc) return rc;
+    if (!len) return fail(MC_EINVAL, "len is null");
+    const size_t N = p->N(), R = p->R;
+    const size_t need = sizeof(CkptHeader) + sizeof(RepParams) * R + sizeof(float) * 3 * N * R +
+                        sizeof(double) * R + sizeof(ObsAcc) * R + sizeof(double) * N * R;
+    if (!buf) { *len = need; return MC_OK; }
+    if (*len < need) return fail(MC_EINVAL, "checkpoint buffer too small (%zu < %zu)", *len, need);
+    CK(cudaDeviceSynchronize());
+    char *o = (char *)buf;
+    CkptHeader h{};
+    h.magic = kMagic; h.version = kVersion; h.L = p->L; h.l = p->l; h.R = p->R;
+    h.proposal = p->proposal; h.schedule = p->schedule; h.A = p->A; h.tail = p->tail;
+    h.W_ready = p->W_ready; h.energy_valid = p->energy_valid; h.seed = p->seed; h.t = p->t; h.cone = p->cone;
+    std::memcpy(o, &h, sizeof h); o += sizeof h;
+    std::memcpy(o, p->hp.data(), sizeof(RepParams) * R); o += sizeof(RepParams) * R;
+    CK(cudaMemcpy(o, p->spins, sizeof(float) * 3 * N * R, cudaMemcpyDeviceToHost)); o += sizeof(float) * 3 * N * R;
+    CK(cudaMemcpy(o, p->energy, sizeof(double) * R, cudaMemcpyDeviceToHost)); o += sizeof(double) * R;
+    CK(cudaMemcpy(o, p->obs, sizeof(ObsAcc) * R, cudaMemcpyDeviceToHost)); o += sizeof(ObsAcc) * R;
+    CK(cudaMemcpy(o, p->theta2, sizeof(double) * N * R, cudaMemcpyDeviceToHost));
+    *len = need;
+    return MC_OK;
+}
+
+int mc_restore(mc_lattice *p, const void *buf, size_t len) {
+    int rc = check(p);
+    if (rc) return rc;
+    if (!buf || len < sizeof(CkptHeader)) return fail(MC_EINVAL, "checkpoint buffer too small");
+    CkptHeader h;
+    std::memcpy(&h, buf, sizeof h);
+    if (h.magic != kMagic || h.version != kVersion) return fail(MC_EINVAL, "not a dipmc checkpoint");
+    if (h.L != p->L || h.l != p->l || h.R != p->R)
+        return fail(MC_EINVAL, "checkpoint is for L=%d l=%d R=%d, handle has L=%d l=%d R=%d", h.L, h.l, h.R, p->L, p->l, p->R);
+    const size_t N = p->N(), R = p->R;
+    const size_t need = sizeof(CkptHeader) + sizeof(RepParams) * R + sizeof(float) * 3 * N * R +
+                        sizeof(double) * R + sizeof(ObsAcc) * R + sizeof(double) * N * R;
+    if (len < need) return fail(MC_EINVAL, "checkpoint truncated (%zu < %zu)", len, need);
+    if (h.W_ready && (!p->W_ready || h.A != p->A || h.tail != p->tail))
+        return fail(MC_ENOTREADY, "call mc_precompute_W(%d, %d) on this handle before mc_restore", h.A, h.tail);
+    CK(cudaDeviceSynchronize());
+    const char *o = (const char *)buf + sizeof h;
+    std::memcpy(p->hp.data(), o, sizeof(RepParams) * R); o += sizeof(RepParams) * R;
+    rc = upload_params(p);
+    if (rc) return rc;
+    CK(cudaMemcpy(p->spins, o, sizeof(float) * 3 * N * R, cudaMemcpyHostToDevice)); o += sizeof(float) * 3 * N * R;
+    CK(cudaMemcpy(p->energy, o, sizeof(double) * R, cudaMemcpyHostToDevice)); o += sizeof(double) * R;
+    CK(cudaMemcpy(p->obs, o, sizeof(ObsAcc) * R, cudaMemcpyHostToDevice)); o += sizeof(ObsAcc) * R;
+    CK(cudaMemcpy(p->theta2, o, sizeof(double) * N * R, cudaMemcpyHostToDevice));
+    p->seed = h.seed;
+    p->t = h.t;
+    p->proposal = h.proposal;
+    p->schedule = h.schedule;
+    p->cone = h.cone;
+    p->energy_valid = h.energy_valid != 0;
+    return MC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,202 @@
+// aux_kernels.cu -- W~ precompute (FP64), spin initialisation, full field and
+// total energy.  None of these is in the per-sub-step loop; they run once per
+// lattice (W~), per init, or once per mc_sweep call (energy anchor).
+#include "internal.cuh"
+
+namespace dipmc {
+
+// ---------------------------------------------------------------------------
+// W~(rho) (Sec. 2.1, Eq. 2): image sum over |a|, |b| <= A of the planar dipole
+// tensor W(r) = (delta_ab - 3 r^_a r^_b)/r^3 (a, b in x, y), W_zz = 1/r^3, for the
+// minimum-image representative of rho (both +-L/2 averaged on the half-way
+// line), plus the continuum tail beyond the square of half-width (A + 1/2) L.
+// One CTA per rho; threads stride over the (2A+1)^2 images; FP64 throughout.
+// ---------------------------------------------------------------------------
+constexpr int kWThreads = 256;
+
+__device__ __forceinline__ int reps_of(int v, int L, double out[2]) {
+    if (2 * v < L) { out[0] = v; return 1; }
+    if (2 * v > L) { out[0] = v - L; return 1; }
+    out[0] = 0.5 * L;
+    out[1] = -0.5 * L;
+    return 2;
+}
+
+__global__ void __launch_bounds__(kWThreads) k_wtilde(int L, int A, int tail, double *W64, float *W32) {
+    const int N = L * L;
+    const int rho = blockIdx.x;
+    const int x = rho % L, y = rho / L;
+    double xr[2], yr[2];
+    const int nx = reps_of(x, L, xr), ny = reps_of(y, L, yr);
+    const int side = 2 * A + 1;
+    const long long nimg = (long long)side * side;
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i)
+            for (long long g = threadIdx.x; g < nimg; g += kWThreads) {
+                const int ga = (int)(g % side) - A, gb = (int)(g / side) - A;
+                const double rx = xr[i] + (double)ga * L;
+                const double ry = yr[j] + (double)gb * L;
+                const double r2 = rx * rx + ry * ry;
+                if (r2 == 0.0) continue;  // the site itself
+                const double inv_r2 = 1.0 / r2;
+                const double inv_r3 = inv_r2 / sqrt(r2);
+                const double k = 3.0 * inv_r3 * inv_r2;
+                a0 += inv_r3 - k * rx * rx;
+                a1 -= k * rx * ry;
+                a2 += inv_r3 - k * ry * ry;
+                a3 += inv_r3;
+            }
+    __shared__ double red[4][kWThreads / 32];
+    for (int off = 16; off; off >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, off);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, off);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, off);
+        a3 += __shfl_xor_sync(0xffffffffu, a3, off);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        red[0][warp] = a0; red[1][warp] = a1; red[2][warp] = a2; red[3][warp] = a3;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s[4] = {0, 0, 0, 0};
+        for (int w = 0; w < kWThreads / 32; ++w)
+            for (int c = 0; c < 4; ++c) s[c] += red[c][w];
+        const double inv = 1.0 / (double)(nx * ny);
+        for (int c = 0; c < 4; ++c) s[c] *= inv;
+        if (tail) {
+            const double Rw = ((double)A + 0.5) * (double)L;
+            const double tz = 4.0 * sqrt(2.0) / (Rw * (double)L * (double)L);
+            s[3] += tz;
+            s[0] -= 0.5 * tz;
+            s[2] -= 0.5 * tz;
+        }
+        for (int c = 0; c < 4; ++c) {
+            W64[c * N + rho] = s[c];
+            W32[c * N + rho] = (float)s[c];
+        }
+    }
+}
+
+cudaError_t launch_wtilde(int L, int A, int tail, double *W64, float *W32, cudaStream_t st) {
+    k_wtilde<<<L * L, kWThreads, 0, st>>>(L, A, tail, W64, W32);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Initial spins: mode 0 uniform on S^2 from Philox {site, r, 0, tag}; 1 = +z.
+// ---------------------------------------------------------------------------
+__global__ void k_init_spins(int L, int R, uint2 key, int mode, float *spins) {
+    const int N = L * L;
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (long long)N * R) return;
+    const int r = (int)(gid / N), i = (int)(gid % N);
+    float sx = 0.f, sy = 0.f, sz = 1.f;
+    if (mode == 0) {
+        const uint4 w = philox(make_uint4((uint32_t)i, (uint32_t)r, 0u, kTagInit), key);
+        sz = 2.0f * u24f(w.x) - 1.0f;
+        const float rr = sqrtf(fmaxf(0.0f, (1.0f - sz) * (1.0f + sz)));
+        float sp, cp;
+        sincospif(2.0f * u24f(w.y), &sp, &cp);
+        sx = rr * cp;
+        sy = rr * sp;
+    }
+    float *s = spins + (size_t)r * 3 * N;
+    s[i] = sx;
+    s[N + i] = sy;
+    s[2 * N + i] = sz;
+}
+
+cudaError_t launch_init_spins(int L, int R, uint2 key, int mode, float *spins, cudaStream_t st) {
+    const long long tot = (long long)L * L * R;
+    k_init_spins<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(L, R, key, mode, spins);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Full field h_p = sum_d W~(d) s_{p-d} at every site (FP32, direct O(N^2) per
+// replica).  Thread = site p; W~(d) is the same address across the warp
+// (broadcast); s_{p-d} is coalesced across consecutive p.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_full_field(int L, const float *__restrict__ W32,
+                                                    const float *__restrict__ spins,
+                                                    float *__restrict__ h) {
+    const int N = L * L;
+    const int r = blockIdx.y;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= N) return;
+    const int px = p % L, py = p / L;
+    const float *s = spins + (size_t)r * 3 * N;
+    float h0 = 0.f, h1 = 0.f, h2 = 0.f;
+    for (int dy = 0; dy < L; ++dy) {
+        int y = py - dy;
+        if (y < 0) y += L;
+        const float *s0 = s + y * L, *s1 = s0 + N, *s2 = s1 + N;
+        const float *w0 = W32 + dy * L, *w1 = w0 + N, *w2 = w1 + N, *w3 = w2 + N;
+        for (int dx = 0; dx < L; ++dx) {
+            int x = px - dx;
+            if (x < 0) x += L;
+            const float a = __ldg(s0 + x), b = __ldg(s1 + x), c = __ldg(s2 + x);
+            const float xx = __ldg(w0 + dx), xy = __ldg(w1 + dx), yy = __ldg(w2 + dx), zz = __ldg(w3 + dx);
+            h0 = fmaf(xx, a, fmaf(xy, b, h0));
+            h1 = fmaf(xy, a, fmaf(yy, b, h1));
+            h2 = fmaf(zz, c, h2);
+        }
+    }
+    float *o = h + (size_t)r * 3 * N;
+    o[p] = h0;
+    o[N + p] = h1;
+    o[2 * N + p] = h2;
+}
+
+cudaError_t launch_full_field(int L, int R, const float *W32, const float *spins, float *h,
+                              cudaStream_t st) {
+    const int N = L * L;
+    dim3 grid((N + 255) / 256, R);
+    k_full_field<<<grid, 256, 0, st>>>(L, W32, spins, h);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Total energy per replica (Sec. 4 energy, with the ferromagnetic-exchange and
+// E_A = -K2 z^2 - K4 z^4 readings), FP64 sums.  One CTA per replica.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_energy(int L, const float *__restrict__ spins,
+                                                const float *__restrict__ h,
+                                                const RepParams *__restrict__ P, double *E) {
+    const int N = L * L, r = blockIdx.x;
+    const float *s = spins + (size_t)r * 3 * N;
+    const float *f = h + (size_t)r * 3 * N;
+    const RepParams p = P[r];
+    double ex = 0, an = 0, dp = 0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const int x = i % L, y = i / L;
+        const int ixp = y * L + (x + 1 == L ? 0 : x + 1);
+        const int iyp = (y + 1 == L ? 0 : y + 1) * L + x;
+        const double a = s[i], b = s[N + i], c = s[2 * N + i];
+        ex += a * ((double)s[ixp] + (double)s[iyp]) + b * ((double)s[N + ixp] + (double)s[N + iyp]) +
+              c * ((double)s[2 * N + ixp] + (double)s[2 * N + iyp]);
+        const double z2 = c * c;
+        an += -(double)p.K2 * z2 - (double)p.K4 * z2 * z2;
+        dp += a * (double)f[i] + b * (double)f[N + i] + c * (double)f[2 * N + i];
+    }
+    double tot = -(double)p.J * ex + an + 0.5 * (double)p.CD * dp;
+    for (int off = 16; off; off >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, off);
+    __shared__ double red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tot;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s2 = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s2 += red[w];
+        E[r] = s2;
+    }
+}
+
+cudaError_t launch_energy(int L, int R, const float *spins, const float *h, const RepParams *p,
+                          double *E, cudaStream_t st) {
+    k_energy<<<R, 256, 0, st>>>(L, spins, h, p, E);
+    return cudaGetLastError();
+}
+
+}  // namespace dipmc

@@ -1,0 +1,127 @@
+// internal.cuh -- shared device/host definitions of libdipmc (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dipmc.h"
+
+namespace dipmc {
+
+// ----------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
+// as 1, 2, 3", SC'11): ten rounds of two 32x32 -> 64 multiplies (words 0, 2),
+// a word permutation and a Weyl key schedule.
+// ----------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+#ifdef __CUDA_ARCH__
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+#else
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x, p1 = (uint64_t)0xCD9E8D57u * c.z;
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+#endif
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+enum : uint32_t { kTagAttempt = 1u << 24, kTagPerm = 2u << 24, kTagDraw = 3u << 24, kTagInit = 4u << 24 };
+
+// Uniform in [0, 1) with 24 random bits (exact in FP32).
+__device__ __forceinline__ float u24f(uint32_t w) { return (float)(w >> 8) * 5.9604644775390625e-8f; }
+
+// Feistel round function of the sweep schedule (any function gives a bijection).
+__host__ __device__ __forceinline__ uint32_t feistel_f(uint32_t x, uint32_t rk) {
+    uint32_t y = (x ^ rk) * 0x9E3779B1u;
+    return y ^ (y >> 15);
+}
+
+// Offset index v = oy*l + ox for sub-step k of a sweep.
+// kind 0: 4-round balanced Feistel permutation of [0, 4^h) (2^h >= l) keyed by the
+// sweep's round keys rk, cycle-walked back into [0, l^2).
+// kind 1: uniform draw per sub-step (Philox word scaled by l^2).
+__host__ __device__ __forceinline__ uint32_t perm_offset(uint4 rk, int h, uint32_t ll, uint32_t k) {
+    const uint32_t mask = h ? ((1u << h) - 1u) : 0u;
+    uint32_t v = k;
+    const uint32_t guard_max = 1u << (2 * h);
+    for (uint32_t guard = 0; guard <= guard_max; ++guard) {
+        uint32_t lo = v & mask, hi = (v >> h) & mask, nl;
+        nl = hi ^ (feistel_f(lo, rk.x) & mask); hi = lo; lo = nl;
+        nl = hi ^ (feistel_f(lo, rk.y) & mask); hi = lo; lo = nl;
+        nl = hi ^ (feistel_f(lo, rk.z) & mask); hi = lo; lo = nl;
+        nl = hi ^ (feistel_f(lo, rk.w) & mask); hi = lo; lo = nl;
+        v = (hi << h) | lo;
+        if (v < ll) return v;
+    }
+    return 0;  // unreachable: the walk stays in k's cycle of a bijection
+}
+
+__host__ __device__ __forceinline__ int ceil_log2_u(uint32_t v) {
+    int b = 0;
+    while ((1u << b) < v) ++b;
+    return b;
+}
+
+// Per-replica couplings as the kernels read them.
+struct RepParams {
+    float J, CD, K2, K4, T;
+    float pad[3];
+};
+
+constexpr int kNB = 24;  // binning levels: blocks of 2^k samples, k < kNB
+
+// Device accumulators of one replica (FP64).
+struct ObsAcc {
+    double psum[MC_NOBS][kNB];  // running sum of the current block at level k
+    double bsum[MC_NOBS][kNB];  // sum of completed block means
+    double bsq[MC_NOBS][kNB];   // sum of squared completed block means
+    long long pcnt[kNB];        // samples in the current block at level k
+    long long bcnt[kNB];        // completed blocks at level k
+    long long nsamples;
+    long long accepted;
+    long long attempted;
+    long long pad;
+};
+
+struct SweepConfig {
+    int L, l, R;
+    uint2 key;
+    uint32_t t0;
+    int nsweeps;
+    int measure_every;
+    int proposal;     // 0 cap, 1 sphere
+    float cap_c1;     // 1 - cos(cone)
+    int schedule;     // 0 permutation, 1 draw
+};
+
+struct SweepBuffers {
+    const float *W32;         // [4][N]
+    float *spins;             // [R][3][N]
+    const RepParams *params;  // [R]
+    double *energy;           // [R] tracked energy (in: at t0, out: at t0+nsweeps)
+    ObsAcc *obs;              // [R]
+    double *theta2;           // [R][N]
+    float *trace;             // optional [R][nsweeps][l^2][n][MC_TRACE_W]
+};
+
+// Launchers (implemented in their .cu files).  Return a cudaError_t.
+cudaError_t launch_wtilde(int L, int A, int tail, double *W64, float *W32, cudaStream_t st);
+cudaError_t launch_init_spins(int L, int R, uint2 key, int mode, float *spins, cudaStream_t st);
+cudaError_t launch_full_field(int L, int R, const float *W32, const float *spins, float *h,
+                              cudaStream_t st);
+cudaError_t launch_energy(int L, int R, const float *spins, const float *h, const RepParams *p,
+                          double *E, cudaStream_t st);
+// Returns cudaErrorNotSupported when no direct-kernel instance fits (L, l).
+cudaError_t launch_sweep_direct(const SweepConfig &c, const SweepBuffers &b, int threads_hint,
+                                cudaStream_t st);
+bool direct_supported(int L, int l);
+
+}  // namespace dipmc

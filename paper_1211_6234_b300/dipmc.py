@@ -1,0 +1,240 @@
+"""Thin Python binding of libdipmc.so (C ABI in include/dipmc.h).
+
+Argument marshalling only: every step of the sweep runs in the CUDA library.
+Device buffers passed in or out are torch CUDA tensors (their data pointers);
+the CUDA stream is torch's current stream unless given.  Importing this module
+loads the library and raises if it has not been built -- there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdipmc.so")
+
+MC_OK, MC_EINVAL, MC_ENOMEM, MC_ENOTREADY, MC_ETIMEOUT, MC_ECUDA, MC_ENOSYS = 0, -1, -2, -3, -4, -5, -6
+MC_NOBS = 5
+OBS_NAMES = ("abs_m", "m_z", "abs_m_z", "m_par", "e")
+MC_PATH_AUTO, MC_PATH_DIRECT = 0, 1
+MC_TRACE_W = 10
+
+# Every symbol include/dipmc.h declares.
+ABI_SYMBOLS = (
+    "mc_last_error", "mc_version", "mc_create_lattice", "mc_destroy", "mc_set_params",
+    "mc_set_proposal", "mc_set_schedule", "mc_set_field_path", "mc_init_spins",
+    "mc_precompute_W", "mc_sweep", "mc_sweep_trace", "mc_observables", "mc_reset_observables",
+    "mc_get_spins", "mc_get_field", "mc_get_W", "mc_energy", "mc_get_sweep_counter",
+    "mc_checkpoint", "mc_restore",
+)
+
+
+class McError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"dipmc error {code}: {msg}")
+        self.code = code
+
+
+class mc_obs(C.Structure):
+    _fields_ = [
+        ("samples", C.c_int64),
+        ("mean", C.c_double * MC_NOBS),
+        ("var", C.c_double * MC_NOBS),
+        ("err_naive", C.c_double * MC_NOBS),
+        ("err", C.c_double * MC_NOBS),
+        ("tau_int", C.c_double * MC_NOBS),
+        ("eta", C.c_double),
+        ("energy", C.c_double),
+        ("accepted", C.c_int64),
+        ("attempted", C.c_int64),
+    ]
+
+    def as_dict(self):
+        d = {"samples": self.samples, "eta": self.eta, "energy": self.energy,
+             "accepted": self.accepted, "attempted": self.attempted}
+        for i, nm in enumerate(OBS_NAMES):
+            d[nm] = {"mean": self.mean[i], "var": self.var[i], "err_naive": self.err_naive[i],
+                     "err": self.err[i], "tau_int": self.tau_int[i]}
+        return d
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run `python -m paper_1211_6234_b300.build`")
+    lib = C.CDLL(LIB_PATH)
+    vp, i32, f64, u64 = C.c_void_p, C.c_int, C.c_double, C.c_uint64
+    sig = {
+        "mc_last_error": ([], C.c_char_p),
+        "mc_version": ([], i32),
+        "mc_create_lattice": ([i32, i32, i32, u64, C.POINTER(vp)], i32),
+        "mc_destroy": ([vp], i32),
+        "mc_set_params": ([vp, i32, f64, f64, f64, f64, f64], i32),
+        "mc_set_proposal": ([vp, i32, f64], i32),
+        "mc_set_schedule": ([vp, i32], i32),
+        "mc_set_field_path": ([vp, i32], i32),
+        "mc_init_spins": ([vp, i32, vp], i32),
+        "mc_precompute_W": ([vp, i32, i32], i32),
+        "mc_sweep": ([vp, i32, i32, vp], i32),
+        "mc_sweep_trace": ([vp, i32, vp, C.c_size_t, vp], i32),
+        "mc_observables": ([vp, i32, C.POINTER(mc_obs)], i32),
+        "mc_reset_observables": ([vp], i32),
+        "mc_get_spins": ([vp, vp, i32, vp], i32),
+        "mc_get_field": ([vp, vp, i32, vp], i32),
+        "mc_get_W": ([vp, vp], i32),
+        "mc_energy": ([vp, vp, vp], i32),
+        "mc_get_sweep_counter": ([vp, C.POINTER(u64)], i32),
+        "mc_checkpoint": ([vp, vp, C.POINTER(C.c_size_t)], i32),
+        "mc_restore": ([vp, vp, C.c_size_t], i32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _ck(rc: int):
+    if rc != MC_OK:
+        raise McError(rc, _lib.mc_last_error().decode())
+    return rc
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _np_ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class Lattice:
+    """Owner of one mc_lattice handle (R replicas of an L x L lattice, spacing l)."""
+
+    def __init__(self, L: int, l: int, replicas: int = 1, seed: int = 1):
+        h = C.c_void_p()
+        _ck(_lib.mc_create_lattice(L, l, replicas, seed, C.byref(h)))
+        self.h = h
+        self.L, self.l, self.R, self.seed = L, l, replicas, seed
+
+    # -- lifetime
+    def close(self):
+        if self.h:
+            _lib.mc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def N(self):
+        return self.L * self.L
+
+    # -- set-up
+    def set_params(self, J=1.0, C_D=0.1, K2=0.8, K4=0.0, T=0.6, replica=-1):
+        _ck(_lib.mc_set_params(self.h, replica, J, C_D, K2, K4, T))
+
+    def set_proposal(self, kind=0, cone=0.5):
+        _ck(_lib.mc_set_proposal(self.h, kind, cone))
+
+    def set_schedule(self, kind=0):
+        _ck(_lib.mc_set_schedule(self.h, kind))
+
+    def set_field_path(self, path=MC_PATH_AUTO):
+        _ck(_lib.mc_set_field_path(self.h, path))
+
+    def init_spins(self, mode=0, user=None):
+        if mode == 2:
+            a = np.ascontiguousarray(user, np.float32)
+            assert a.size == self.R * 3 * self.N
+            _ck(_lib.mc_init_spins(self.h, 2, _np_ptr(a)))
+        else:
+            _ck(_lib.mc_init_spins(self.h, mode, None))
+
+    def precompute_W(self, image_cutoff=64, tail_correction=True):
+        _ck(_lib.mc_precompute_W(self.h, image_cutoff, int(bool(tail_correction))))
+
+    # -- run
+    def sweep(self, nsweeps, measure_every=0, stream=None):
+        _ck(_lib.mc_sweep(self.h, nsweeps, measure_every, _stream_ptr(stream)))
+
+    def sweep_trace(self, nsweeps, stream=None):
+        """Run nsweeps and return the per-attempt trace as a numpy array
+        [R, nsweeps * L*L, MC_TRACE_W] (device buffer from torch)."""
+        import torch
+        nf = self.R * nsweeps * self.N * MC_TRACE_W
+        buf = torch.empty(nf, dtype=torch.float32, device="cuda")
+        _ck(_lib.mc_sweep_trace(self.h, nsweeps, C.c_void_p(buf.data_ptr()), nf, _stream_ptr(stream)))
+        torch.cuda.synchronize()
+        return buf.cpu().numpy().reshape(self.R, nsweeps * self.N, MC_TRACE_W)
+
+    # -- read back
+    def observables(self, replica=0) -> dict:
+        o = mc_obs()
+        _ck(_lib.mc_observables(self.h, replica, C.byref(o)))
+        return o.as_dict()
+
+    def reset_observables(self):
+        _ck(_lib.mc_reset_observables(self.h))
+
+    def get_spins(self, out=None, stream=None) -> np.ndarray:
+        if out is not None:  # torch CUDA tensor
+            _ck(_lib.mc_get_spins(self.h, C.c_void_p(out.data_ptr()), 1, _stream_ptr(stream)))
+            return out
+        a = np.empty((self.R, 3, self.L, self.L), np.float32)
+        _ck(_lib.mc_get_spins(self.h, _np_ptr(a), 0, _stream_ptr(stream)))
+        return a
+
+    def get_field(self, stream=None) -> np.ndarray:
+        a = np.empty((self.R, 3, self.L, self.L), np.float32)
+        _ck(_lib.mc_get_field(self.h, _np_ptr(a), 0, _stream_ptr(stream)))
+        return a
+
+    def get_W(self) -> np.ndarray:
+        a = np.empty((4, self.L, self.L), np.float64)
+        _ck(_lib.mc_get_W(self.h, _np_ptr(a)))
+        return a
+
+    def energy(self, stream=None) -> np.ndarray:
+        a = np.empty(self.R, np.float64)
+        _ck(_lib.mc_energy(self.h, _np_ptr(a), _stream_ptr(stream)))
+        return a
+
+    def sweep_counter(self) -> int:
+        v = C.c_uint64()
+        _ck(_lib.mc_get_sweep_counter(self.h, C.byref(v)))
+        return v.value
+
+    def checkpoint(self) -> bytes:
+        n = C.c_size_t(0)
+        _ck(_lib.mc_checkpoint(self.h, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        _ck(_lib.mc_checkpoint(self.h, buf, C.byref(n)))
+        return buf.raw[: n.value]
+
+    def restore(self, data: bytes):
+        buf = C.create_string_buffer(data, len(data))
+        _ck(_lib.mc_restore(self.h, buf, len(data)))

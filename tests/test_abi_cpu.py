@@ -1,0 +1,59 @@
+"""Host-side checks of the C-ABI library that need no GPU: it loads, it exports
+every entry point include/dipmc.h declares, and argument validation that
+precedes any CUDA call reports the documented error codes."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dipmc.h")
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(mc_\w+)\s*\(", text, re.M)))
+
+
+def test_header_declares_the_abi():
+    syms = declared_symbols()
+    for s in ("mc_create_lattice", "mc_set_params", "mc_precompute_W", "mc_sweep", "mc_observables"):
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1211_6234_b300 import dipmc
+    out = subprocess.run(["nm", "-D", "--defined-only", dipmc.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if ln.strip()}
+    missing = [s for s in declared_symbols() if s not in exported]
+    assert not missing, missing
+    assert set(dipmc.ABI_SYMBOLS) == set(declared_symbols())
+    for s in declared_symbols():
+        getattr(dipmc.lib(), s)
+
+
+def test_validation_before_any_device_call():
+    from paper_1211_6234_b300 import dipmc
+    lib = dipmc.lib()
+    h = C.c_void_p()
+    assert lib.mc_create_lattice(16, 5, 1, 1, C.byref(h)) == dipmc.MC_EINVAL
+    assert b"L % l" in lib.mc_last_error()
+    assert lib.mc_create_lattice(16, 1, 1, 1, C.byref(h)) == dipmc.MC_EINVAL
+    assert lib.mc_create_lattice(1, 1, 1, 1, C.byref(h)) == dipmc.MC_EINVAL
+    assert lib.mc_create_lattice(16, 8, 0, 1, C.byref(h)) == dipmc.MC_EINVAL
+    assert lib.mc_create_lattice(16, 8, 1, 1, None) == dipmc.MC_EINVAL
+    assert lib.mc_sweep(None, 1, 0, None) == dipmc.MC_EINVAL
+    assert lib.mc_observables(None, 0, None) == dipmc.MC_EINVAL
+    assert lib.mc_destroy(None) == dipmc.MC_OK
+    assert lib.mc_version() >= 1
+
+
+def test_binding_raises_instead_of_falling_back():
+    """The binding wraps non-zero codes in McError; there is no CPU path."""
+    from paper_1211_6234_b300 import dipmc
+    with pytest.raises(dipmc.McError) as e:
+        dipmc.Lattice(16, 5, 1, 1)
+    assert e.value.code == dipmc.MC_EINVAL

@@ -1,0 +1,230 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU FP64 oracle on the
+same seeded inputs.
+
+Tolerances: W~ (FP64 on both sides) relative 1e-12; fields normwise relative
+1e-5 (FP32 path); proposals and acceptance uniforms identical up to FP32
+rounding; accept decisions identical except where the oracle's dE lies within
+the FP32 tolerance of the threshold -T ln u (a straddle, counted).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import oracle as orc  # noqa: E402
+from paper_1211_6234_b300 import inputs  # noqa: E402
+from tests.parity_util import F32, binned_error, compare_trace  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def dipmc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1211_6234_b300 import dipmc as d
+    return d
+
+
+_WCACHE = {}
+
+
+def oracle_W(L, A):
+    if (L, A) not in _WCACHE:
+        _WCACHE[(L, A)] = orc.wtilde(L, A, True)
+    return _WCACHE[(L, A)]
+
+
+# ---------------------------------------------------------------- a0: W~
+@pytest.mark.parametrize("L,A", [(2, 8), (6, 16), (12, 16), (16, 64), (64, 64)])
+def test_wtilde_matches_oracle(dipmc, L, A):
+    with dipmc.Lattice(L, L if L < 4 else L // 2, 1, 1) as lat:
+        lat.precompute_W(A, True)
+        Wg = lat.get_W()
+    Wo = oracle_W(L, A)
+    err = np.abs(Wg - Wo).max() / np.abs(Wo).max()
+    assert err < 1e-12, err
+
+
+# ---------------------------------------------------------------- full field
+@pytest.mark.parametrize("L,R", [(8, 1), (16, 3), (64, 2)])
+def test_full_field_matches_oracle(dipmc, L, R):
+    s0 = inputs.random_spins(L, R, seed=10 + L)
+    with dipmc.Lattice(L, L // 2, R, 3) as lat:
+        lat.precompute_W(16 if L > 16 else 64, True)
+        lat.init_spins(2, s0)
+        hg = lat.get_field().astype(np.float64)
+        W = lat.get_W()
+    Wo = oracle_W(L, 16 if L > 16 else 64)
+    for r in range(R):
+        ho = orc.field(Wo, s0[r])
+        err = np.abs(hg[r] - ho).max() / np.abs(ho).max()
+        assert err < 1e-5, err
+
+
+# ---------------------------------------------------------------- a1-a3: sweeps
+CASES = [
+    # L, l, R, proposal, schedule, nsweeps, A
+    (16, 8, 2, 0, 0, 4, 64),    # BASELINE small config shape: L=16, l=L/2, cap 0.5 rad
+    (16, 16, 1, 0, 0, 2, 64),   # l = L: exact sequential (n = 1)
+    (16, 4, 2, 0, 0, 3, 64),    # C = 4: 16 simultaneous sites
+    (12, 6, 2, 1, 0, 4, 16),    # non-power-of-two L, ragged thread tail, sphere proposals
+    (12, 6, 1, 0, 1, 4, 16),    # the paper's with-replacement schedule
+    (4, 2, 2, 0, 0, 6, 16),     # small lattice, update sites at distance 2
+    (2, 2, 1, 0, 0, 8, 16),     # smallest lattice (l = L = 2)
+    (48, 24, 1, 0, 0, 1, 16),   # L = 48 (2 cell offsets per thread)
+    (64, 32, 2, 0, 0, 1, 16),   # the L = 64 launch configuration of the benchmark
+    (64, 16, 1, 0, 0, 1, 16),   # L = 64 with 16 simultaneous sites
+]
+
+
+def _run_case(dipmc, L, l, R, proposal, schedule, nsw, A, params):
+    seed = 1000 + 7 * L + l
+    s0 = inputs.random_spins(L, R, seed=L * 31 + l)
+    with dipmc.Lattice(L, l, R, seed) as lat:
+        lat.precompute_W(A, True)
+        lat.set_proposal(proposal, 0.5)
+        lat.set_schedule(schedule)
+        for r, (J, CD, K2, K4, T) in enumerate(params):
+            lat.set_params(J, CD, K2, K4, T, replica=r)
+        lat.init_spins(2, s0)
+        tr = lat.sweep_trace(nsw)
+        sg = lat.get_spins().astype(np.float64)
+        Eg_full = lat.energy()
+        Eg_tracked = np.array([lat.observables(r)["energy"] * L * L for r in range(R)])
+    return seed, s0, tr, sg, Eg_full, Eg_tracked
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"L{c[0]}_l{c[1]}_R{c[2]}_p{c[3]}_s{c[4]}" for c in CASES])
+def test_sweep_trace_matches_oracle(dipmc, case):
+    L, l, R, proposal, schedule, nsw, A = case
+    params = [(F32(1.0), F32(0.1), F32(0.8), F32(0.0), F32(0.6)),
+              (F32(0.7), F32(0.3), F32(0.5), F32(-0.2), F32(1.1))][:R]
+    seed, s0, tr, sg, Eg_full, Eg_tracked = _run_case(dipmc, L, l, R, proposal, schedule, nsw, A, params)
+    W = oracle_W(L, A)
+    straddles = 0
+    for r in range(R):
+        J, CD, K2, K4, T = params[r]
+        p = orc.params(L, l, J, CD, K2, K4, T, proposal=proposal, cone=0.5, schedule=schedule,
+                       seed=seed, replica=r)
+        o = orc.sweeps(p, W, s0[r], 0, nsw)
+        hmax = float(np.abs(o["h"]).max())
+        rep = compare_trace(tr[r], o, T, scale=1 + abs(J) + abs(K2) + abs(K4) + abs(CD) * hmax)
+        straddles += rep.straddles
+        if rep.straddles == 0:
+            assert rep.compared == nsw * L * L
+            np.testing.assert_allclose(sg[r], o["s"], rtol=0, atol=1e-5)
+            # tracked energy (sum of accepted dE + cross terms) against the oracle's
+            # full energy of its own final state and the GPU's own full evaluation
+            Eo = orc.energy(W, o["s"], J, CD, K2, K4)[3]
+            assert abs(Eg_tracked[r] - Eo) < 1e-5 * (L * L) * (1 + abs(J) + abs(K2) + abs(K4) + CD * 10)
+        assert abs(Eg_tracked[r] - Eg_full[r]) < 1e-5 * (L * L) * (1 + abs(J) + abs(K2) + abs(K4) + CD * 10)
+    total = sum(nsw * L * L for _ in range(R))
+    assert straddles / total <= 1e-3, straddles
+
+
+def test_l_equals_L_gpu_matches_exact_sequential(dipmc):
+    """l = L on the GPU takes the decisions of the oracle's exact sequential
+    Metropolis (dE from full-energy differences), Appendix B."""
+    L = 6
+    s0 = inputs.random_spins(L, 1, seed=77)
+    J, CD, K2, K4, T = F32(1.0), F32(0.5), F32(0.8), F32(0.2), F32(0.7)
+    with dipmc.Lattice(L, L, 1, 5) as lat:
+        lat.precompute_W(16, True)
+        lat.set_params(J, CD, K2, K4, T)
+        lat.init_spins(2, s0)
+        tr = lat.sweep_trace(3)
+    p = orc.params(L, L, J, CD, K2, K4, T, proposal=0, cone=0.5, seed=5, replica=0)
+    ex = orc.sweeps_exact(p, oracle_W(L, 16), s0[0], 0, 3)
+    mism = np.nonzero(tr[0][:, 6].astype(int) != ex["acc"])[0]
+    if len(mism):
+        i = mism[0]
+        thr = -T * math.log(tr[0][i, 5])
+        assert abs(ex["dE"][i] - thr) < 1e-4, (i, ex["dE"][i], thr)
+
+
+# ---------------------------------------------------------------- a4: observables
+@pytest.mark.parametrize("T", [0.5, 2.5])
+def test_observables_statistically_match_oracle(dipmc, T):
+    """L = 16, 2000 sweeps measured every sweep, away from the ordering temperature
+    (ordered at T = 0.5, paramagnetic at T = 2.5): GPU means against the oracle's
+    run (independent trajectories, same law) within 4 combined binned errors."""
+    L, l, nsw, warm_sw = 16, 8, 2000, 300
+    J, CD, K2, K4, T = F32(1.0), F32(0.1), F32(0.8), F32(0.0), F32(T)
+    s0 = inputs.saturated_z(L, 1)
+    with dipmc.Lattice(L, l, 1, 11) as lat:
+        lat.precompute_W(64, True)
+        lat.set_params(J, CD, K2, K4, T)
+        lat.init_spins(2, s0)
+        lat.sweep(warm_sw, 0)
+        lat.reset_observables()
+        lat.sweep(nsw, 1)
+        og = lat.observables(0)
+    p = orc.params(L, l, J, CD, K2, K4, T, proposal=0, cone=0.5, seed=99, replica=0)
+    W = oracle_W(L, 64)
+    warm = orc.sweeps(p, W, s0[0], 0, warm_sw, trace=False)["s"]
+    o = orc.sweeps(p, W, warm, warm_sw, nsw, trace=False, observe=True)
+    assert og["samples"] == nsw
+    for i, nm in enumerate(("abs_m", "m_z", "abs_m_z", "m_par", "e")):
+        x = o["obs"][:, i]
+        eo = binned_error(x)
+        eg = og[nm]["err"]
+        diff = abs(og[nm]["mean"] - x.mean())
+        assert diff <= 4 * math.hypot(eo, eg) + 1e-9, (nm, og[nm]["mean"], x.mean(), eo, eg)
+    eta_o = orc.eta(o["theta2"], nsw)
+    assert abs(og["eta"] - eta_o) < 0.03, (og["eta"], eta_o)
+    assert 0 < og["accepted"] <= og["attempted"] == nsw * L * L
+
+
+# ---------------------------------------------------------------- state handling
+def test_determinism_checkpoint_and_batch_invariance(dipmc):
+    L, l = 16, 8
+    def make(R):
+        lat = dipmc.Lattice(L, l, R, 42)
+        lat.precompute_W(16, True)
+        lat.init_spins(0)
+        return lat
+    with make(3) as a, make(3) as b, make(1) as c:
+        a.sweep(20, 2); b.sweep(20, 2); c.sweep(20, 2)
+        sa, sb, sc = a.get_spins(), b.get_spins(), c.get_spins()
+        assert np.array_equal(sa, sb)                 # same seed, same run: bitwise
+        assert np.array_equal(sa[0], sc[0])           # replica 0 alone vs in a batch
+        ck = a.checkpoint()
+        a.sweep(15, 1)
+        s1 = a.get_spins()
+        o1 = a.observables(1)
+        a.restore(ck)
+        assert a.sweep_counter() == 20
+        a.sweep(15, 1)
+        assert np.array_equal(a.get_spins(), s1)      # resume is bit-exact
+        o2 = a.observables(1)
+        assert o1["samples"] == o2["samples"] and o1["abs_m"]["mean"] == o2["abs_m"]["mean"]
+
+
+def test_error_codes(dipmc):
+    with dipmc.Lattice(16, 8, 1, 1) as lat:
+        with pytest.raises(dipmc.McError) as e:
+            lat.sweep(1)
+        assert e.value.code == dipmc.MC_ENOTREADY
+        with pytest.raises(dipmc.McError) as e:
+            lat.set_params(T=0.0)
+        assert e.value.code == dipmc.MC_EINVAL
+        with pytest.raises(dipmc.McError) as e:
+            lat.set_proposal(0, 4.0)
+        assert e.value.code == dipmc.MC_EINVAL
+    with dipmc.Lattice(256, 128, 1, 1) as big:
+        with pytest.raises(dipmc.McError) as e:
+            big.set_field_path(dipmc.MC_PATH_DIRECT)
+        assert e.value.code == dipmc.MC_ENOSYS
+
+
+def test_random_init_is_uniform_on_sphere(dipmc):
+    with dipmc.Lattice(64, 32, 4, 9) as lat:
+        lat.init_spins(0)
+        s = lat.get_spins().astype(np.float64)
+    norm = np.sqrt((s**2).sum(1))
+    assert np.abs(norm - 1).max() < 1e-6
+    z = s[:, 2].ravel()
+    assert abs(z.mean()) < 0.02 and abs((z**2).mean() - 1 / 3) < 0.02
