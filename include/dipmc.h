@@ -185,6 +185,33 @@ int mc_get_sweep_counter(mc_lattice *lat, uint64_t *out);
 int mc_checkpoint(mc_lattice *lat, void *buf, size_t *len);
 int mc_restore(mc_lattice *lat, const void *buf, size_t len);
 
+/*
+ * Total energy of caller-provided spin states without allocating device memory.
+ * The paper has no counterpart: this entry point exists for callers that cannot
+ * call cudaMalloc -- code that runs inside a device-memory budget owned by
+ * someone else (a framework's caching allocator, a serving process that reserves
+ * all device memory up front) or on latency-critical paths where an allocation
+ * would synchronise the device.  It computes the same energies as mc_energy, but
+ * needs no lattice handle and allocates nothing: the field it needs between its
+ * two kernels lives in a fixed 4 MiB array in device memory that every GPU which
+ * loads the library holds until the process exits.
+ *   L, R       lattice size and number of states (L >= 2, R >= 1), with
+ *              R * 3 * L * L <= 1048576 (e.g. R <= 85 at L = 64, R <= 5 at L = 256);
+ *              larger requests fail with MC_EINVAL and name the largest R.
+ *   W32        device, [4][L][L] FP32 replica-summed tensor (as from mc_get_W, cast).
+ *   spins      device, [R][3][L][L] FP32.
+ *   couplings  device, [R][4] FP32: J, C_D, K2, K4 of each state.
+ *   energy     device, [R] FP64 output: total energy of each state.
+ *   stream     cudaStream_t (NULL = legacy default stream); work is enqueued, not
+ *              synchronised.
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  All calls share the one array: calls
+ * whose work overlaps on the GPU (different streams, or several threads) race
+ * and must be serialised by the caller.  Nothing from an earlier call is read.
+ */
+int mc_energy_noalloc(int L, int R, const float *W32, const float *spins, const float *couplings,
+                      double *energy, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

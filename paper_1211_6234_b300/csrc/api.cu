@@ -41,6 +41,11 @@ constexpr int kVersion = 1;
 
 }  // namespace
 
+int dipmc::set_last_error(int code, const char *msg) {
+    g_err = msg;
+    return code;
+}
+
 struct mc_lattice {
     int L = 0, l = 0, R = 0, device = 0;
     uint64_t seed = 0;

@@ -124,4 +124,7 @@ cudaError_t launch_sweep_direct(const SweepConfig &c, const SweepBuffers &b, int
                                 cudaStream_t st);
 bool direct_supported(int L, int l);
 
+// Records a one-line error message for mc_last_error() and returns `code`.
+int set_last_error(int code, const char *msg);
+
 }  // namespace dipmc

@@ -28,7 +28,7 @@ ABI_SYMBOLS = (
     "mc_set_proposal", "mc_set_schedule", "mc_set_field_path", "mc_init_spins",
     "mc_precompute_W", "mc_sweep", "mc_sweep_trace", "mc_observables", "mc_reset_observables",
     "mc_get_spins", "mc_get_field", "mc_get_W", "mc_energy", "mc_get_sweep_counter",
-    "mc_checkpoint", "mc_restore",
+    "mc_checkpoint", "mc_restore", "mc_energy_noalloc",
 )
 
 
@@ -88,6 +88,7 @@ def _load():
         "mc_get_sweep_counter": ([vp, C.POINTER(u64)], i32),
         "mc_checkpoint": ([vp, vp, C.POINTER(C.c_size_t)], i32),
         "mc_restore": ([vp, vp, C.c_size_t], i32),
+        "mc_energy_noalloc": ([i32, i32, vp, vp, vp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -116,6 +117,15 @@ def _stream_ptr(stream):
     if isinstance(stream, int):
         return stream
     return stream.cuda_stream
+
+
+def energy_noalloc(L: int, R: int, W32, spins, couplings, energy, stream=None):
+    """mc_energy_noalloc on torch CUDA tensors (W32 [4,L,L] f32, spins [R,3,L,L] f32,
+    couplings [R,4] f32, energy [R] f64 output).  For callers that cannot allocate
+    device memory; see include/dipmc.h."""
+    _ck(_lib.mc_energy_noalloc(L, R, C.c_void_p(W32.data_ptr()), C.c_void_p(spins.data_ptr()),
+                               C.c_void_p(couplings.data_ptr()), C.c_void_p(energy.data_ptr()),
+                               _stream_ptr(stream)))
 
 
 def _np_ptr(a: np.ndarray):
