@@ -104,6 +104,19 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def window_sites():
+    """Window size the library picks for L = 64, l = 32 (n = 4): the largest power
+    of two B dividing l^2 with 4B <= 512 and 4B a multiple of 128."""
+    n = (L // l) ** 2
+    best = 0
+    B = 1
+    while B <= l * l:
+        if (l * l) % B == 0 and B * n <= 512 and (B * n) % 128 == 0:
+            best = B
+        B *= 2
+    return best * n
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -180,6 +193,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--sweeps", type=int, default=100, help="sweeps per step")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--path", choices=["tensor", "direct", "window"], default="tensor",
+                    help="field path: tcgen05 split-BF16x3 window field, FP32 direct, FP32 window")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     args = ap.parse_args()
@@ -200,8 +215,11 @@ def main():
     from paper_1211_6234_b300 import dipmc
 
     lad = ladder()
+    path_id = {"direct": dipmc.MC_PATH_DIRECT, "window": dipmc.MC_PATH_WINDOW_F32,
+               "tensor": dipmc.MC_PATH_TENSOR}[args.path]
     lat = dipmc.Lattice(L, l, R, seed=1 + 7919 * rank)
     lat.precompute_W(A_IMG, True)
+    lat.set_field_path(path_id)
     lat.set_proposal(0, 0.5)
     for r, (j, cd, k2, k4, T) in enumerate(lad):
         lat.set_params(j, cd, k2, k4, T, replica=r)
@@ -243,23 +261,69 @@ def main():
     updates = ws * R * L * L * S * args.steps
     value = updates / t_dev
 
-    # roofline of the sweep kernel: FP32 FMA-bound.  Algorithmic work per site
-    # update = N source sites x 5 multiply-adds (xx,xy | xy,yy | zz) = 10 N flops.
-    flops_per_update = 10 * L * L
-    achieved = flops_per_update * R * L * L * S / (statistics.mean(step_ms) / 1e3) / 1e12
+    # per-kernel device times (CUDA events recorded by the library around each
+    # launch on this stream), from a separate pass of 2 steps after the timed ones
+    lat.set_timing(True)
+    for i in range(2):
+        flush.fill_(float(i))
+        lat.sweep(S, 1, stream)
+    kt = lat.timing()
+    lat.set_timing(False)
+    kernels = {k: {"launches": v["launches"], "ms_total": v["ms"],
+                   "ms_per_launch": v["ms"] / v["launches"] if v["launches"] else None}
+               for k, v in kt.items() if v["launches"]}
+    dominant = max(kernels, key=lambda k: kernels[k]["ms_total"])
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     peaks = measured_peaks()
     sm_max = (clk.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2032.0)
     peak_fp32 = sms * FP32_FMA_PER_CLK_PER_SM * 2 * sm_max * 1e6 / 1e12
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "sweep_direct_L64_R256.traffic.json")
+    Sw = window_sites()
+    # algorithmic work: the field of one site update sums N sources x 5 multiply-adds
+    # (xx,xy | xy,yy | zz) = 10 N flops; the update itself reads s (12 B), h (12 B)
+    # and writes s (12 B) = 36 B
+    flops_per_update = 10 * L * L
+    rl = {}
+    for k, v in kernels.items():
+        sec = v["ms_per_launch"] / 1e3
+        if k == "tc_field":
+            fl = flops_per_update * Sw * R            # one launch: stale field of Sw sites x R replicas
+            ach = fl / sec / 1e12
+            pk = peaks.get("bf16_tflops_sustained", 1351.5)
+            rl[k] = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                     "issued_bf16x3_frac": 3 * ach / pk,
+                     "peak_basis": "measured cuBLAS bf16 dense, sustained (of measured)"}
+        elif k == "sweep_direct":
+            fl = flops_per_update * R * L * L * S
+            ach = fl / sec / 1e12
+            rl[k] = {"bound": "alu", "achieved": ach, "peak": peak_fp32, "unit": "TFLOP/s", "frac": ach / peak_fp32,
+                     "peak_basis": f"{sms} SMs x 128 FP32 FMA/clk x 2 x {sm_max:.0f} MHz"}
+        elif k == "window_steps":
+            by = 36 * Sw * R                           # one launch: Sw site updates x R replicas
+            ach = by / sec / 1e9
+            pk = peaks.get("hbm_gbs", 6512.6)
+            rl[k] = {"bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk,
+                     "note": "sequential sub-steps: latency-bound, not bandwidth-bound",
+                     "peak_basis": "measured copy bandwidth (of measured)"}
+        elif k == "full_field":
+            fl = flops_per_update * R * L * L
+            ach = fl / sec / 1e12
+            rl[k] = {"bound": "alu", "achieved": ach, "peak": peak_fp32, "unit": "TFLOP/s", "frac": ach / peak_fp32}
+    roof = dict(rl[dominant])
+    roof["kernel"] = dominant
+    roof["traffic"] = None
+    tfile = os.path.join(ROOT, "profiles", f"{dominant}_L64_R256.traffic.json")
     if os.path.exists(tfile):
         try:
-            traffic = json.load(open(tfile)).get("dram_bytes_per_launch_per_sweep")
-            traffic = traffic * S if traffic is not None else None
+            roof["traffic"] = json.load(open(tfile)).get("dram_bytes_per_launch")
         except Exception:
-            traffic = None
+            pass
+    # kernels of ours launched per timed step: direct = 1 sweep kernel; tensor = one
+    # bf16 split of the spins + per window (sites, tensor-core field, sub-steps);
+    # FP32 window = per window (full field, sub-steps)
+    nwin = (l * l * (L // l) ** 2) // Sw if Sw else 0
+    per_step = {"direct": 1, "tensor": 1 + 3 * nwin * S, "window": 2 * nwin * S}[args.path]
+    gpu_launches = per_step * args.steps
 
     # end to end through the public API: host spins in (pinned), S sweeps,
     # spins + observables of every replica back to the host
@@ -308,20 +372,20 @@ def main():
             "metric": "site-updates/s incl. dipole field", "value": value, "unit": "site-updates/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "bf16x3+f32" if args.path == "tensor" else "f32", "data": "synthetic",
             "config": {"workload": "batched replicas: 256 x L=64 (16 T x 16 K4/K2), l=32, 10^2 sweeps/step",
                        "replicas_per_gpu": R, "L": L, "l": l, "sweeps_per_step": S,
-                       "field_path": "direct-fp32", "image_cutoff": A_IMG,
+                       "field_path": {"tensor": "tcgen05 split-BF16x3 window field + FP32 sub-steps",
+                                      "direct": "FP32 direct", "window": "FP32 window"}[args.path],
+                       "window_sites": Sw if args.path != "direct" else None, "image_cutoff": A_IMG,
                        "approx_error_at_Tmin": approx_error(0.2), "l2": "flushed (256 MiB write) before each step",
                        "parallelism": f"replicas x{ws}"},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
-                         "frac": achieved / peak_fp32, "traffic": traffic,
-                         "kernel": "k_sweep_direct<2,2,512>",
-                         "peak_basis": f"{sms} SMs x 128 FP32 FMA/clk x 2 x {sm_max:.0f} MHz (max SM clock)"},
+            "roofline": roof,
+            "kernels": {k: dict(kernels[k], roofline=rl.get(k)) for k in kernels},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "plain": plain,
-            "gpu_launches": args.steps,
+            "gpu_launches": gpu_launches,
             "clocks": clk,
             "wall_s_timed": wall,
         }

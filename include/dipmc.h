@@ -60,7 +60,9 @@ extern "C" {
 
 /* Field paths (mc_set_field_path). */
 #define MC_PATH_AUTO 0
-#define MC_PATH_DIRECT 1 /* FP32 CUDA-core Toeplitz sum, one CTA per replica */
+#define MC_PATH_DIRECT 1      /* FP32 CUDA-core Toeplitz sum, one CTA per replica */
+#define MC_PATH_WINDOW_F32 2  /* windowed sweep, stale field from the FP32 full field */
+#define MC_PATH_TENSOR 3      /* windowed sweep, stale field on tcgen05 tensor cores, split-BF16x3 */
 
 typedef struct mc_lattice mc_lattice;
 
@@ -113,8 +115,17 @@ int mc_set_proposal(mc_lattice *lat, int kind, double cone_rad);
  * its offset uniformly with replacement (Sec. 3.1 host loop). */
 int mc_set_schedule(mc_lattice *lat, int kind);
 
-/* Field path for the sweep (MC_PATH_*).  MC_PATH_AUTO picks the fastest supported. */
+/* Field path for the sweep (MC_PATH_*).  MC_PATH_AUTO picks the fastest supported.
+ * The windowed paths (2, 3) process the l^2 sub-steps of a sweep in windows of B
+ * consecutive sub-steps: the field at every site a window visits is evaluated once
+ * on the state at the window's start (for all replicas together), and each
+ * sub-step adds the exact change from the moves accepted earlier in the window,
+ * so the sweep is the same simultaneous-flip update (Sec. 3.1, 3.2) up to
+ * rounding.  MC_PATH_TENSOR needs L % 8 == 0 and B*(L/l)^2 % 128 == 0. */
 int mc_set_field_path(mc_lattice *lat, int path);
+
+/* Sub-steps per window of the windowed paths (must divide l^2; 0 = automatic). */
+int mc_set_window(mc_lattice *lat, int B);
 
 /* Initial spins: mode 0 = random uniform on S^2 from the seed; 1 = all +z;
  * 2 = copy `user` (host pointer, [R][3][L][L] FP32, used as given).  Resets the
@@ -172,6 +183,24 @@ int mc_get_W(mc_lattice *lat, double *dst_host);
 /* Total energy of every replica from a full field evaluation (FP32 field, FP64
  * sums), [R] doubles to a host pointer.  Synchronises `stream`. */
 int mc_energy(mc_lattice *lat, double *dst_host, void *stream);
+
+/* Per-kernel device time, measured with CUDA events recorded on the launching
+ * stream around every launch while timing is enabled.  Kernel classes: */
+#define MC_K_SWEEP_DIRECT 0  /* the direct sweep kernel (one launch per mc_sweep) */
+#define MC_K_TC_FIELD 1      /* tensor-core window field (one launch per window) */
+#define MC_K_WINDOW_STEPS 2  /* sequential sub-steps of a window */
+#define MC_K_FULL_FIELD 3    /* FP32 full field (energy anchor, windowed FP32 path) */
+#define MC_NKCLASS 4
+typedef struct mc_timing {
+    int64_t launches[MC_NKCLASS];
+    double ms[MC_NKCLASS];
+} mc_timing;
+
+/* Enable (1) or disable (0) kernel timing; both reset the accumulated times. */
+int mc_set_timing(mc_lattice *lat, int enable);
+
+/* Accumulated kernel times since the last mc_set_timing (synchronises the device). */
+int mc_get_timing(mc_lattice *lat, mc_timing *out);
 
 /* Sweep counter (index of the next sweep; the RNG counters depend on it). */
 int mc_get_sweep_counter(mc_lattice *lat, uint64_t *out);

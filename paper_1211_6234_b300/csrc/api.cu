@@ -8,6 +8,8 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "tc_field.cuh"
+#include "window.cuh"
 
 using namespace dipmc;
 
@@ -68,8 +70,21 @@ struct mc_lattice {
     bool W_ready = false, energy_valid = false;
     int A = 0, tail = 0;
     cudaStream_t last = nullptr;
+    // windowed / tensor-core paths
+    int window_B = 0;
+    __nv_bfloat16 *spins_hi = nullptr, *spins_lo = nullptr, *wsh = nullptr;
+    float *H0 = nullptr;
+    int *wsite = nullptr;
+    TcUnit *units = nullptr;
+    int nunits = 0, NT = 0, tmem_cols = 0, plan_Sw = 0;
+    int *err_flag = nullptr;
+    bool wsh_ready = false;
+    // kernel timing (events recorded around launches while enabled)
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> tev[MC_NKCLASS];
 
     int N() const { return L * L; }
+    int n() const { return (L / l) * (L / l); }
     size_t spin_floats() const { return (size_t)R * 3 * N(); }
 };
 
@@ -85,6 +100,78 @@ void free_all(mc_lattice *p) {
     cudaFree(p->etmp);
     cudaFree(p->obs);
     cudaFree(p->theta2);
+    cudaFree(p->spins_hi);
+    cudaFree(p->spins_lo);
+    cudaFree(p->wsh);
+    cudaFree(p->H0);
+    cudaFree(p->wsite);
+    cudaFree(p->units);
+    cudaFree(p->err_flag);
+}
+
+// Records an event pair around a launch when timing is on.
+struct TimedLaunch {
+    mc_lattice *p;
+    int cls;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr, b = nullptr;
+    TimedLaunch(mc_lattice *p_, int cls_, cudaStream_t st_) : p(p_), cls(cls_), st(st_) {
+        if (p->timing && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
+            cudaEventRecord(a, st);
+    }
+    ~TimedLaunch() {
+        if (a && b) {
+            cudaEventRecord(b, st);
+            p->tev[cls].push_back({a, b});
+        }
+    }
+};
+
+void clear_timing(mc_lattice *p) {
+    for (auto &v : p->tev) {
+        for (auto &e : v) {
+            cudaEventDestroy(e.first);
+            cudaEventDestroy(e.second);
+        }
+        v.clear();
+    }
+}
+
+// Sub-steps per window: the given B, else the largest power of two dividing l^2
+// with B*n <= 512 and (for the tensor path) B*n a multiple of 128.
+int window_of(const mc_lattice *p, bool tensor) {
+    const int ll = p->l * p->l, n = p->n();
+    if (p->window_B > 0) return p->window_B;
+    int best = 0;
+    for (int B = 1; B <= ll; B <<= 1) {
+        if (ll % B) continue;
+        if (B * n > 512) break;
+        if (tensor && (B * n) % 128) continue;
+        best = B;
+    }
+    return best;
+}
+
+bool path_supported(const mc_lattice *p, int path) {
+    switch (path) {
+        case MC_PATH_DIRECT: return direct_supported(p->L, p->l);
+        case MC_PATH_WINDOW_F32: {
+            const int B = window_of(p, false);
+            return B > 0 && window_supported(p->L, p->l, B);
+        }
+        case MC_PATH_TENSOR: {
+            const int B = window_of(p, true);
+            return B > 0 && tc_supported(p->L, p->l, B) && window_supported(p->L, p->l, B);
+        }
+        default: return false;
+    }
+}
+
+int resolve_path(const mc_lattice *p) {
+    if (p->path != MC_PATH_AUTO) return p->path;
+    if (direct_supported(p->L, p->l)) return MC_PATH_DIRECT;
+    if (path_supported(p, MC_PATH_WINDOW_F32)) return MC_PATH_WINDOW_F32;
+    return -1;
 }
 
 int upload_params(mc_lattice *p) {
@@ -112,6 +199,123 @@ int anchor_energy(mc_lattice *p, cudaStream_t st) {
 int check(mc_lattice *p) {
     if (!p) return fail(MC_EINVAL, "null lattice handle");
     CK(cudaSetDevice(p->device));
+    return MC_OK;
+}
+
+// A bounded device wait that gave up leaves a flag; report it at the next sync point.
+int check_device_flag(mc_lattice *p) {
+    if (!p->err_flag) return MC_OK;
+    int v = 0;
+    CK(cudaMemcpy(&v, p->err_flag, sizeof v, cudaMemcpyDeviceToHost));
+    if (v) {
+        cudaMemset(p->err_flag, 0, sizeof v);
+        return fail(MC_ETIMEOUT, "a tensor-core pipeline wait timed out; results of the last sweep are invalid");
+    }
+    return MC_OK;
+}
+
+#define CKA(call)                                                        \
+    do {                                                                 \
+        cudaError_t _e = (call);                                         \
+        if (_e != cudaSuccess) return cuda_fail(_e, #call);              \
+    } while (0)
+
+int ensure_tensor_buffers(mc_lattice *p, int Sw, cudaStream_t st) {
+    const size_t N = p->N(), R = p->R;
+    if (!p->spins_hi) {
+        CKA(cudaMalloc(&p->spins_hi, sizeof(__nv_bfloat16) * 3 * N * R));
+        CKA(cudaMalloc(&p->spins_lo, sizeof(__nv_bfloat16) * 3 * N * R));
+        CKA(cudaMalloc(&p->err_flag, sizeof(int)));
+        CKA(cudaMemset(p->err_flag, 0, sizeof(int)));
+    }
+    if (!p->wsh) CKA(cudaMalloc(&p->wsh, sizeof(__nv_bfloat16) * tc_wsh_elems(p->L)));
+    if (!p->wsh_ready) {
+        cudaError_t e = launch_build_wsh(p->L, p->W64, p->wsh, st);
+        if (e != cudaSuccess) return cuda_fail(e, "W~ bf16 tables");
+        p->wsh_ready = true;
+    }
+    if (p->plan_Sw != Sw) {
+        cudaFree(p->H0);
+        cudaFree(p->wsite);
+        cudaFree(p->units);
+        p->H0 = nullptr; p->wsite = nullptr; p->units = nullptr;
+        CKA(cudaMalloc(&p->H0, sizeof(float) * R * 3 * Sw));
+        CKA(cudaMalloc(&p->wsite, sizeof(int) * Sw));
+        int dev = 0, nsm = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        std::vector<TcUnit> u(65536);
+        const int nu = tc_plan(p->L, Sw, p->R, nsm, u.data(), (int)u.size(), &p->NT, &p->tmem_cols);
+        if (nu <= 0) return fail(MC_EINVAL, "tensor-core plan failed for Sw=%d R=%d", Sw, p->R);
+        CKA(cudaMalloc(&p->units, sizeof(TcUnit) * nu));
+        CKA(cudaMemcpy(p->units, u.data(), sizeof(TcUnit) * nu, cudaMemcpyHostToDevice));
+        p->nunits = nu;
+        p->plan_Sw = Sw;
+    }
+    return MC_OK;
+}
+
+int run_windows(mc_lattice *p, int path, int nsweeps, int measure_every, float *trace, cudaStream_t st) {
+    const bool tensor = path == MC_PATH_TENSOR;
+    const int B = window_of(p, tensor);
+    const int ll = p->l * p->l, n = p->n(), Sw = B * n, nwin = ll / B;
+    if (tensor) {
+        int rc = ensure_tensor_buffers(p, Sw, st);
+        if (rc) return rc;
+        cudaError_t e = launch_spins_to_bf16((size_t)p->R * 3 * p->N(), p->spins, p->spins_hi, p->spins_lo, st);
+        if (e != cudaSuccess) return cuda_fail(e, "bf16 split of the spins");
+    }
+    WindowConfig c{};
+    c.L = p->L; c.l = p->l; c.R = p->R;
+    c.key = key_of(p->seed);
+    c.nsweeps_call = nsweeps;
+    c.B = B;
+    c.proposal = p->proposal;
+    c.cap_c1 = (float)(1.0 - std::cos(p->cone));
+    c.schedule = p->schedule;
+    c.stale_mode = tensor ? 1 : 0;
+    c.ldh = 3 * Sw;
+    WindowBuffers b{};
+    b.W32 = p->W32; b.spins = p->spins;
+    b.spins_hi = tensor ? p->spins_hi : nullptr;
+    b.spins_lo = tensor ? p->spins_lo : nullptr;
+    b.params = p->dparams; b.energy = p->energy; b.obs = p->obs; b.theta2 = p->theta2;
+    b.trace = trace;
+    b.stale = tensor ? p->H0 : p->field;
+    TcFieldArgs ta{};
+    if (tensor) {
+        ta.L = p->L; ta.Sw = Sw; ta.R = p->R; ta.NT = p->NT; ta.ldh = 3 * Sw; ta.tmem_cols = p->tmem_cols;
+        ta.units = p->units; ta.wsite = p->wsite; ta.wsh = p->wsh;
+        ta.spins_hi = p->spins_hi; ta.spins_lo = p->spins_lo; ta.H0 = p->H0; ta.error = p->err_flag;
+    }
+    for (int it = 0; it < nsweeps; ++it) {
+        c.t = (uint32_t)(p->t + (uint64_t)it);
+        c.it = it;
+        for (int w = 0; w < nwin; ++w) {
+            cudaError_t e;
+            if (tensor) {
+                e = launch_window_sites(p->L, p->l, c.key, c.t, p->schedule, w * B, B, p->wsite, st);
+                if (e != cudaSuccess) return cuda_fail(e, "window sites");
+                CKA(cudaMemsetAsync(p->H0, 0, sizeof(float) * (size_t)p->R * 3 * Sw, st));
+                {
+                    TimedLaunch tl(p, MC_K_TC_FIELD, st);
+                    e = launch_tc_field(ta, p->nunits, st);
+                }
+                if (e != cudaSuccess) return cuda_fail(e, "tensor-core field launch");
+            } else {
+                TimedLaunch tl(p, MC_K_FULL_FIELD, st);
+                e = launch_full_field(p->L, p->R, p->W32, p->spins, p->field, st);
+                if (e != cudaSuccess) return cuda_fail(e, "full-field kernel");
+            }
+            c.w = w;
+            c.measure = (measure_every > 0 && ((it + 1) % measure_every) == 0 && w == nwin - 1) ? 1 : 0;
+            {
+                TimedLaunch tl(p, MC_K_WINDOW_STEPS, st);
+                e = launch_window_steps(c, b, st);
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "window step kernel launch");
+        }
+    }
     return MC_OK;
 }
 
@@ -143,11 +347,22 @@ int run_sweeps(mc_lattice *p, int nsweeps, int measure_every, float *trace, cuda
     b.obs = p->obs;
     b.theta2 = p->theta2;
     b.trace = trace;
-    cudaError_t e = cudaErrorNotSupported;
-    if (p->path == MC_PATH_AUTO || p->path == MC_PATH_DIRECT) e = launch_sweep_direct(c, b, p->threads_hint, st);
-    if (e == cudaErrorNotSupported)
+    const int path = resolve_path(p);
+    if (path < 0 || !path_supported(p, path))
         return fail(MC_ENOSYS, "no field path supports L=%d l=%d (path %d)", p->L, p->l, p->path);
-    if (e != cudaSuccess) return cuda_fail(e, "sweep kernel launch");
+    if (path == MC_PATH_DIRECT) {
+        cudaError_t e;
+        {
+            TimedLaunch tl(p, MC_K_SWEEP_DIRECT, st);
+            e = launch_sweep_direct(c, b, p->threads_hint, st);
+        }
+        if (e == cudaErrorNotSupported)
+            return fail(MC_ENOSYS, "no field path supports L=%d l=%d (path %d)", p->L, p->l, p->path);
+        if (e != cudaSuccess) return cuda_fail(e, "sweep kernel launch");
+    } else {
+        int rc = run_windows(p, path, nsweeps, measure_every, trace, st);
+        if (rc) return rc;
+    }
     p->t += (uint64_t)nsweeps;
     p->last = st;
     return MC_OK;
@@ -226,6 +441,7 @@ int mc_destroy(mc_lattice *p) {
     if (!p) return MC_OK;
     cudaSetDevice(p->device);
     cudaDeviceSynchronize();
+    clear_timing(p);
     free_all(p);
     delete p;
     return MC_OK;
@@ -270,10 +486,19 @@ int mc_set_schedule(mc_lattice *p, int kind) {
 int mc_set_field_path(mc_lattice *p, int path) {
     int rc = check(p);
     if (rc) return rc;
-    if (path != MC_PATH_AUTO && path != MC_PATH_DIRECT) return fail(MC_EINVAL, "unknown field path %d", path);
-    if (path == MC_PATH_DIRECT && !direct_supported(p->L, p->l))
-        return fail(MC_ENOSYS, "direct path does not support L=%d l=%d", p->L, p->l);
+    if (path < MC_PATH_AUTO || path > MC_PATH_TENSOR) return fail(MC_EINVAL, "unknown field path %d", path);
+    if (path != MC_PATH_AUTO && !path_supported(p, path))
+        return fail(MC_ENOSYS, "field path %d does not support L=%d l=%d", path, p->L, p->l);
     p->path = path;
+    return MC_OK;
+}
+
+int mc_set_window(mc_lattice *p, int B) {
+    int rc = check(p);
+    if (rc) return rc;
+    if (B < 0 || (B > 0 && (p->l * p->l) % B)) return fail(MC_EINVAL, "window %d must divide l^2 = %d", B, p->l * p->l);
+    if (B > 0 && !window_supported(p->L, p->l, B)) return fail(MC_EINVAL, "window %d too large for L=%d", B, p->L);
+    p->window_B = B;
     return MC_OK;
 }
 
@@ -307,6 +532,7 @@ int mc_precompute_W(mc_lattice *p, int A, int tail) {
     p->A = A;
     p->tail = tail ? 1 : 0;
     p->W_ready = true;
+    p->wsh_ready = false;
     p->energy_valid = false;
     return MC_OK;
 }
@@ -332,6 +558,8 @@ int mc_observables(mc_lattice *p, int replica, mc_obs *out) {
     if (!out) return fail(MC_EINVAL, "out is null");
     if (replica < 0 || replica >= p->R) return fail(MC_EINVAL, "replica %d out of range", replica);
     CK(cudaStreamSynchronize(p->last));
+    rc = check_device_flag(p);
+    if (rc) return rc;
     ObsAcc A;
     CK(cudaMemcpy(&A, p->obs + replica, sizeof(ObsAcc), cudaMemcpyDeviceToHost));
     std::vector<double> th((size_t)p->N());
@@ -392,7 +620,7 @@ int mc_get_spins(mc_lattice *p, float *dst, int on_device, void *stream) {
     CK(cudaMemcpyAsync(dst, p->spins, sizeof(float) * p->spin_floats(),
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    return MC_OK;
+    return check_device_flag(p);
 }
 
 int mc_get_field(mc_lattice *p, float *dst, int on_device, void *stream) {
@@ -430,6 +658,32 @@ int mc_energy(mc_lattice *p, double *dst, void *stream) {
     if (e != cudaSuccess) return cuda_fail(e, "energy kernel");
     CK(cudaMemcpyAsync(dst, p->etmp, sizeof(double) * p->R, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    return MC_OK;
+}
+
+int mc_set_timing(mc_lattice *p, int enable) {
+    int rc = check(p);
+    if (rc) return rc;
+    CK(cudaDeviceSynchronize());
+    clear_timing(p);
+    p->timing = enable != 0;
+    return MC_OK;
+}
+
+int mc_get_timing(mc_lattice *p, mc_timing *out) {
+    int rc = check(p);
+    if (rc) return rc;
+    if (!out) return fail(MC_EINVAL, "out is null");
+    CK(cudaDeviceSynchronize());
+    std::memset(out, 0, sizeof *out);
+    for (int k = 0; k < MC_NKCLASS; ++k) {
+        for (auto &e : p->tev[k]) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e.first, e.second));
+            out->ms[k] += ms;
+            out->launches[k] += 1;
+        }
+    }
     return MC_OK;
 }
 

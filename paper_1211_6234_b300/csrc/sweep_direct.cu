@@ -120,45 +120,64 @@ __device__ void obs_push(ObsAcc &A, const double x[MC_NOBS]) {
     }
 }
 
-template <int C, int EPT, int MAXT>
-__global__ void __launch_bounds__(MAXT, 1) k_sweep_direct(const SweepConfig cfg, const SweepBuffers buf) {
+template <int C, int EPT, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig cfg, const SweepBuffers buf) {
     constexpr int n = C * C;
     constexpr int V = 3 * n;                    // partial-field values per thread
     constexpr int G = (V + 31) / 32;            // groups of <= 32 values
     constexpr int PV = pow2_at_least(V < 32 ? V : 32);
     const int L = cfg.L, l = cfg.l, N = L * L, ll = l * l;
     const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5, NW = NT >> 5;
+    const int NWF = NW - 1;                     // field warps; warp 0 is the control warp
+    const int ftid = tid - 32, NTF = NT - 32;
     const int r = blockIdx.x;
 
     extern __shared__ float4 smem_f4[];
-    float *sx = reinterpret_cast<float *>(smem_f4);
-    float *sy = sx + N;
-    float *sz = sy + N;
-    float *th2 = sz + N;                 // [N] per-site (theta - pi/2)^2 this launch
-    float *red = th2 + N;                // [NW][V]
-    float *mred = red + NW * V;          // [NW][4] magnetisation reduction
-    uint16_t *sched = reinterpret_cast<uint16_t *>(mred + NW * 4);  // [ll]
+    float4 *s4 = smem_f4;                                         // [N] spins (x, y, z, 0)
+    float *th2 = reinterpret_cast<float *>(s4 + N);               // [N] sum (theta - pi/2)^2
+    float *red = th2 + N;                                         // [NWF][V] warp partial fields
+    float *mred = red + NWF * V;                                  // [NW][4] magnetisation
+    float *wl = mred + NW * 4;                                    // [n][4] W~(l*D), D in [0,C)^2
+    uint16_t *sched = reinterpret_cast<uint16_t *>(wl + n * 4);   // [ll] offsets of the sweep
     __shared__ ObsAcc acc_s;
     __shared__ double e_track_s;
+    // control-warp state kept in shared memory so that it does not occupy
+    // registers of the field threads (lane d < n: update site d)
+    __shared__ float c_S[3][32], c_d[3][32], c_pre[32], c_thr[32], c_u[32];
+    __shared__ int c_q[32];
+    __shared__ float b_d[3][32], b_E[32];     // last decided sub-step, for the bookkeeping
+    __shared__ double c_epart[32];
+    __shared__ RepParams c_P;
+    __shared__ float c_W0[4];
 
-    // ---- load state
+    // ---- load state: global SoA -> shared AoS
     const float *gs = buf.spins + (size_t)r * 3 * N;
-    for (int i = tid; i < 3 * N; i += NT) sx[i] = gs[i];
+    for (int i = tid; i < N; i += NT) s4[i] = make_float4(gs[i], gs[N + i], gs[2 * N + i], 0.0f);
     const bool measuring = cfg.measure_every > 0;
     if (measuring)
         for (int i = tid; i < N; i += NT) th2[i] = 0.0f;
+    if (tid < 4 * n) {
+        const int D = tid >> 2, c = tid & 3;
+        wl[tid] = buf.W32[c * N + (l * (D / C)) * L + l * (D % C)];
+    }
     if (tid == 0) {
         if (buf.obs) acc_s = buf.obs[r];
         e_track_s = buf.energy ? buf.energy[r] : 0.0;
+        c_P = buf.params[r];
+    }
+    if (tid < 4) c_W0[tid] = buf.W32[tid * N];
+    if (tid < 32) {
+        c_epart[tid] = 0.0;
+        b_d[0][tid] = b_d[1][tid] = b_d[2][tid] = b_E[tid] = 0.0f;
     }
 
-    // ---- tensor slices for this thread's cell offsets e (registers, whole launch)
+    // ---- field threads: tensor slices of their cell offsets e (registers, whole launch)
     float w[EPT][n][4];
     int ex[EPT], ey[EPT];
 #pragma unroll
     for (int j = 0; j < EPT; ++j) {
-        const int e = tid + j * NT;
-        const bool valid = e < ll;
+        const int e = ftid + j * NTF;
+        const bool valid = warp > 0 && e < ll;
         ex[j] = valid ? e % l : 0;
         ey[j] = valid ? e / l : 0;
 #pragma unroll
@@ -173,99 +192,165 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep_direct(const SweepConfig cfg,
         }
     }
 
-    const RepParams P = buf.params[r];
-    const float W0xx = buf.W32[0], W0xy = buf.W32[N], W0yy = buf.W32[2 * N], W0zz = buf.W32[3 * N];
     const uint2 key = cfg.key;
     const int hbits = ceil_log2_u((uint32_t)l);
-    double e_part = 0.0;        // lanes < n of warp 0: this lane's tracked energy change
-    long long n_acc = 0;        // lane 0 of warp 0: accepted moves
+    bool pending = false;      // control warp: a decided sub-step awaits bookkeeping
+    long long n_acc = 0;       // control warp lane 0: accepted moves
     __syncthreads();
+
+    // sum of accepted dE plus the pair cross terms C_D d_p.W~(q - p).d_q of the
+    // last decided sub-step (Sec. 3.2, H3 - H1 - H2 + H0); control warp only
+    auto bookkeeping = [&]() {
+        if (lane < n) {
+            const int dxl = lane % C, dyl = lane / C;
+            const float bX = b_d[0][lane], bY = b_d[1][lane], bZ = b_d[2][lane];
+            float cross = 0.0f;
+            for (int dp = 0; dp < lane; ++dp) {
+                const int Dd = ((dxl - dp % C + C) % C) + C * ((dyl - dp / C + C) % C);
+                const float xx = wl[4 * Dd], xy = wl[4 * Dd + 1], yy = wl[4 * Dd + 2], zz = wl[4 * Dd + 3];
+                const float pX = b_d[0][dp], pY = b_d[1][dp], pZ = b_d[2][dp];
+                cross += pX * (xx * bX + xy * bY) + pY * (xy * bX + yy * bY) + pZ * (zz * bZ);
+            }
+            c_epart[lane] += (double)b_E[lane] + (double)(c_P.CD * cross);
+        }
+        __syncwarp();
+    };
 
     for (int it = 0; it < cfg.nsweeps; ++it) {
         const uint32_t t = cfg.t0 + (uint32_t)it;
         // ---- the sweep's schedule
         if (cfg.schedule == 0) {
             const uint4 rk = philox(make_uint4(t, 0u, 0u, kTagPerm), key);
-            for (int k = tid; k < ll; k += NT) sched[k] = (uint16_t)perm_offset(rk, hbits, (uint32_t)ll, (uint32_t)k);
+            for (int k = tid; k < ll; k += NT) {
+                const uint32_t v = perm_offset(rk, hbits, (uint32_t)ll, (uint32_t)k);
+                sched[k] = (uint16_t)(((v / l) << 8) | (v % l));  // (oy, ox), l <= 256
+            }
         } else {
             for (int k = tid; k < ll; k += NT) {
                 const uint4 o = philox(make_uint4(t, (uint32_t)k, 0u, kTagDraw), key);
-                sched[k] = (uint16_t)(uint32_t)(((unsigned long long)o.x * (unsigned long long)ll) >> 32);
+                const uint32_t v = (uint32_t)(((unsigned long long)o.x * (unsigned long long)ll) >> 32);
+                sched[k] = (uint16_t)(((v / l) << 8) | (v % l));
             }
         }
         __syncthreads();
 
         for (int k = 0; k < ll; ++k) {
             const int v = sched[k];
-            const int ox = v % l, oy = v / l;
-
-            // random numbers of this sub-step (independent of the state): lanes d < n of warp 0
-            float u1 = 0.f, cps = 0.f, sps = 0.f, uacc = 1.f;
-            int qx = 0, qy = 0, q = 0;
-            if (warp == 0 && lane < n) {
-                qx = ox + l * (lane % C);
-                qy = oy + l * (lane / C);
-                q = qy * L + qx;
-                const uint4 wds = philox(make_uint4((uint32_t)q, (uint32_t)r, t, ((uint32_t)k & 0x00FFFFFFu) | kTagAttempt), key);
-                u1 = u24f(wds.x);
-                sincospif(2.0f * u24f(wds.y), &sps, &cps);
-                uacc = u24f(wds.z);
-            }
-
-            // ---- partial fields at the n update sites
-            float acc[n][3];
+            const int ox = v & 0xFF, oy = v >> 8;
+            if (warp == 0) {
+                // ---- control warp, while the field warps run: last sub-step's energy
+                // bookkeeping, then every field-independent part of this sub-step's dE
+                if (pending) {
+                    bookkeeping();
+                    pending = false;
+                }
+                if (lane < n) {
+                    const RepParams &P = c_P;
+                    const int qx = ox + l * (lane % C), qy = oy + l * (lane / C);
+                    const int q = qy * L + qx;
+                    const uint4 wds = philox(make_uint4((uint32_t)q, (uint32_t)r, t, ((uint32_t)k & 0x00FFFFFFu) | kTagAttempt), key);
+                    const float u1 = u24f(wds.x);
+                    float sps, cps;
+                    sincospif(2.0f * u24f(wds.y), &sps, &cps);
+                    const float uacc = u24f(wds.z);
+                    const float4 sq = s4[q];
+                    float S0, S1, S2;
+                    if (cfg.proposal == 1) {
+                        const float z = 2.0f * u1 - 1.0f;
+                        const float rr = sqrtf(fmaxf(0.0f, (1.0f - z) * (1.0f + z)));
+                        S0 = rr * cps;
+                        S1 = rr * sps;
+                        S2 = z;
+                    } else {
+                        // 1 - cos(alpha) = u1 (1 - cos cone), formed without cancellation
+                        const float omc = u1 * cfg.cap_c1;
+                        const float ca = 1.0f - omc;
+                        const float sa = sqrtf(fmaxf(0.0f, omc * (2.0f - omc)));
+                        float3 b1, b2;
+                        perp_basis(sq.x, sq.y, sq.z, b1, b2);
+                        S0 = ca * sq.x + sa * (cps * b1.x + sps * b2.x);
+                        S1 = ca * sq.y + sa * (cps * b1.y + sps * b2.y);
+                        S2 = ca * sq.z + sa * (cps * b1.z + sps * b2.z);
+                        const float inv = 1.0f / sqrtf(S0 * S0 + S1 * S1 + S2 * S2);
+                        S0 *= inv;
+                        S1 *= inv;
+                        S2 *= inv;
+                    }
+                    const float dX = S0 - sq.x, dY = S1 - sq.y, dZ = S2 - sq.z;
+                    const int xp = (qx + 1 == L) ? q - qx : q + 1;
+                    const int xm = (qx == 0) ? q + L - 1 : q - 1;
+                    const int yp = (qy + 1 == L) ? qx : q + L;
+                    const int ym = (qy == 0) ? q + N - L : q - L;
+                    const float4 a = s4[xp], b = s4[xm], c = s4[yp], d = s4[ym];
+                    const float n0 = (a.x + b.x) + (c.x + d.x);
+                    const float n1 = (a.y + b.y) + (c.y + d.y);
+                    const float n2 = (a.z + b.z) + (c.z + d.z);
+                    const float dex = -P.J * (dX * n0 + dY * n1 + dZ * n2);
+                    const float z0 = sq.z * sq.z, z1 = S2 * S2;
+                    const float dan = (-P.K2 * z1 - P.K4 * z1 * z1) - (-P.K2 * z0 - P.K4 * z0 * z0);
+                    const float self = c_W0[0] * dX * dX + 2.0f * c_W0[1] * dX * dY + c_W0[2] * dY * dY + c_W0[3] * dZ * dZ;
+                    c_S[0][lane] = S0; c_S[1][lane] = S1; c_S[2][lane] = S2;
+                    c_d[0][lane] = dX; c_d[1][lane] = dY; c_d[2][lane] = dZ;
+                    c_pre[lane] = dex + dan + 0.5f * P.CD * self;
+                    // accept iff u < exp(-dE/T)  <=>  dE < -T ln u   (u = 0: always)
+                    c_thr[lane] = (uacc > 0.0f) ? -P.T * logf(uacc) : INFINITY;
+                    c_u[lane] = uacc;
+                    c_q[lane] = q;
+                }
+            } else {
+                // ---- field warps: partial fields at the n update sites
+                float acc[n][3];
 #pragma unroll
-            for (int d = 0; d < n; ++d) acc[d][0] = acc[d][1] = acc[d][2] = 0.0f;
+                for (int d = 0; d < n; ++d) acc[d][0] = acc[d][1] = acc[d][2] = 0.0f;
 #pragma unroll
-            for (int j = 0; j < EPT; ++j) {
-                const int bx = ox + ex[j], by = oy + ey[j];
+                for (int j = 0; j < EPT; ++j) {
+                    const int bx = ox + ex[j], by = oy + ey[j];
 #pragma unroll
-                for (int my = 0; my < C; ++my) {
-                    int yy = by + l * my;
-                    if (yy >= L) yy -= L;
+                    for (int my = 0; my < C; ++my) {
+                        int yy = by + l * my;
+                        if (yy >= L) yy -= L;
 #pragma unroll
-                    for (int mx = 0; mx < C; ++mx) {
-                        int xx = bx + l * mx;
-                        if (xx >= L) xx -= L;
-                        const int m = yy * L + xx;
-                        const float a = sx[m], b = sy[m], c = sz[m];
+                        for (int mx = 0; mx < C; ++mx) {
+                            int xx = bx + l * mx;
+                            if (xx >= L) xx -= L;
+                            const float4 sm = s4[yy * L + xx];
 #pragma unroll
-                        for (int dy = 0; dy < C; ++dy)
+                            for (int dy = 0; dy < C; ++dy)
 #pragma unroll
-                            for (int dx = 0; dx < C; ++dx) {
-                                const int D = ((dx - mx + C) % C) + C * ((dy - my + C) % C);
-                                const int dq = dx + C * dy;
-                                acc[dq][0] = fmaf(w[j][D][0], a, fmaf(w[j][D][1], b, acc[dq][0]));
-                                acc[dq][1] = fmaf(w[j][D][1], a, fmaf(w[j][D][2], b, acc[dq][1]));
-                                acc[dq][2] = fmaf(w[j][D][3], c, acc[dq][2]);
-                            }
+                                for (int dx = 0; dx < C; ++dx) {
+                                    const int D = ((dx - mx + C) % C) + C * ((dy - my + C) % C);
+                                    const int dq = dx + C * dy;
+                                    acc[dq][0] = fmaf(w[j][D][0], sm.x, fmaf(w[j][D][1], sm.y, acc[dq][0]));
+                                    acc[dq][1] = fmaf(w[j][D][1], sm.x, fmaf(w[j][D][2], sm.y, acc[dq][1]));
+                                    acc[dq][2] = fmaf(w[j][D][3], sm.z, acc[dq][2]);
+                                }
+                        }
                     }
                 }
-            }
-            // ---- CTA reduction: warp reduce-scatter, then warp 0 sums across warps
 #pragma unroll
-            for (int g = 0; g < G; ++g) {
-                float vals[PV];
+                for (int g = 0; g < G; ++g) {
+                    float vals[PV];
 #pragma unroll
-                for (int i = 0; i < PV; ++i) {
-                    const int vi = g * 32 + i;
-                    vals[i] = (i < 32 && vi < V) ? acc[vi / 3][vi % 3] : 0.0f;
+                    for (int i = 0; i < PV; ++i) {
+                        const int vi = g * 32 + i;
+                        vals[i] = (i < 32 && vi < V) ? acc[vi / 3][vi % 3] : 0.0f;
+                    }
+                    const float s = warp_reduce_scatter<PV>(vals, lane);
+                    const int vi = g * 32 + reduce_scatter_index<PV>(lane);
+                    if (reduce_scatter_writer<PV>(lane) && vi < V) red[(warp - 1) * V + vi] = s;
                 }
-                const float s = warp_reduce_scatter<PV>(vals, lane);
-                const int vi = g * 32 + reduce_scatter_index<PV>(lane);
-                if (reduce_scatter_writer<PV>(lane) && vi < V) red[warp * V + vi] = s;
             }
             __syncthreads();
 
             if (warp == 0) {
-                // cross-warp sum: lane j owns values j, j+32, ...
+                // ---- critical path: field -> decide -> write
                 float hsum[G];
 #pragma unroll
                 for (int g = 0; g < G; ++g) {
                     const int vi = g * 32 + lane;
                     float s = 0.0f;
                     if (vi < V)
-                        for (int ww = 0; ww < NW; ++ww) s += red[ww * V + vi];
+                        for (int ww = 0; ww < NWF; ++ww) s += red[ww * V + vi];
                     hsum[g] = s;
                 }
                 float h[3];
@@ -280,100 +365,48 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep_direct(const SweepConfig cfg,
                     }
                     h[c] = val;
                 }
-                float dX = 0.f, dY = 0.f, dZ = 0.f, dE = 0.f;
                 int accept = 0;
                 if (lane < n) {
-                    const float s0 = sx[q], s1 = sy[q], s2 = sz[q];
-                    float S0, S1, S2;
-                    if (cfg.proposal == 1) {
-                        const float z = 2.0f * u1 - 1.0f;
-                        const float rr = sqrtf(fmaxf(0.0f, (1.0f - z) * (1.0f + z)));
-                        S0 = rr * cps;
-                        S1 = rr * sps;
-                        S2 = z;
-                    } else {
-                        const float ca = 1.0f - u1 * cfg.cap_c1;
-                        const float sa = sqrtf(fmaxf(0.0f, (1.0f - ca) * (1.0f + ca)));
-                        float3 b1, b2;
-                        perp_basis(s0, s1, s2, b1, b2);
-                        S0 = ca * s0 + sa * (cps * b1.x + sps * b2.x);
-                        S1 = ca * s1 + sa * (cps * b1.y + sps * b2.y);
-                        S2 = ca * s2 + sa * (cps * b1.z + sps * b2.z);
-                        const float inv = 1.0f / sqrtf(S0 * S0 + S1 * S1 + S2 * S2);
-                        S0 *= inv;
-                        S1 *= inv;
-                        S2 *= inv;
-                    }
-                    dX = S0 - s0;
-                    dY = S1 - s1;
-                    dZ = S2 - s2;
-                    const int xp = (qx + 1 == L) ? q - qx : q + 1;
-                    const int xm = (qx == 0) ? q + L - 1 : q - 1;
-                    const int yp = (qy + 1 == L) ? qx : q + L;
-                    const int ym = (qy == 0) ? q + N - L : q - L;
-                    const float n0 = (sx[xp] + sx[xm]) + (sx[yp] + sx[ym]);
-                    const float n1 = (sy[xp] + sy[xm]) + (sy[yp] + sy[ym]);
-                    const float n2 = (sz[xp] + sz[xm]) + (sz[yp] + sz[ym]);
-                    const float dex = -P.J * (dX * n0 + dY * n1 + dZ * n2);
-                    const float z0 = s2 * s2, z1 = S2 * S2;
-                    const float dan = (-P.K2 * z1 - P.K4 * z1 * z1) - (-P.K2 * z0 - P.K4 * z0 * z0);
-                    const float self = W0xx * dX * dX + 2.0f * W0xy * dX * dY + W0yy * dY * dY + W0zz * dZ * dZ;
-                    const float ddip = P.CD * ((dX * h[0] + dY * h[1] + dZ * h[2]) + 0.5f * self);
-                    dE = dex + dan + ddip;
-                    accept = uacc < expf(-dE / P.T);
+                    const float dX = c_d[0][lane], dY = c_d[1][lane], dZ = c_d[2][lane];
+                    const float dE = c_pre[lane] + c_P.CD * (dX * h[0] + dY * h[1] + dZ * h[2]);
+                    accept = dE < c_thr[lane];
+                    const int q = c_q[lane];
+                    const float S0 = c_S[0][lane], S1 = c_S[1][lane], S2 = c_S[2][lane];
+                    if (accept) s4[q] = make_float4(S0, S1, S2, 0.0f);
+                    b_d[0][lane] = accept ? dX : 0.0f;
+                    b_d[1][lane] = accept ? dY : 0.0f;
+                    b_d[2][lane] = accept ? dZ : 0.0f;
+                    b_E[lane] = accept ? dE : 0.0f;
                     if (buf.trace) {
                         float *tr = buf.trace + ((((size_t)r * cfg.nsweeps + it) * ll + k) * n + lane) * MC_TRACE_W;
                         tr[0] = (float)q;
                         tr[1] = h[0]; tr[2] = h[1]; tr[3] = h[2];
                         tr[4] = dE;
-                        tr[5] = uacc;
+                        tr[5] = c_u[lane];
                         tr[6] = (float)accept;
                         tr[7] = S0; tr[8] = S1; tr[9] = S2;
                     }
-                    if (accept) {
-                        sx[q] = S0;
-                        sy[q] = S1;
-                        sz[q] = S2;
-                    } else {
-                        dX = dY = dZ = 0.0f;
-                        dE = 0.0f;
-                    }
                 }
-                // ---- exact energy bookkeeping: accepted dE plus pair cross terms
-                float cross = 0.0f;
-#pragma unroll
-                for (int dp = 0; dp < n - 1; ++dp) {
-                    const float pX = __shfl_sync(0xffffffffu, dX, dp);
-                    const float pY = __shfl_sync(0xffffffffu, dY, dp);
-                    const float pZ = __shfl_sync(0xffffffffu, dZ, dp);
-                    if (lane < n && dp < lane) {
-                        // W~(q_lane - q_dp) = W~(l * (D_lane - D_dp) mod L)
-                        int rx = l * ((lane % C) - (dp % C));
-                        int ry = l * ((lane / C) - (dp / C));
-                        if (rx < 0) rx += L;
-                        if (ry < 0) ry += L;
-                        const int idx = ry * L + rx;
-                        const float xx = __ldg(buf.W32 + idx), xy = __ldg(buf.W32 + N + idx);
-                        const float yy = __ldg(buf.W32 + 2 * N + idx), zz = __ldg(buf.W32 + 3 * N + idx);
-                        cross += pX * (xx * dX + xy * dY) + pY * (xy * dX + yy * dY) + pZ * (zz * dZ);
-                    }
-                }
-                if (lane < n) e_part += (double)dE + (double)(P.CD * cross);
                 const unsigned ball = __ballot_sync(0xffffffffu, accept);
                 if (lane == 0) n_acc += __popc(ball);
+                pending = true;
             }
             __syncthreads();
+        }
+        if (warp == 0 && pending) {
+            bookkeeping();
+            pending = false;
         }
 
         // ---- observables of this sweep
         if (measuring && ((it + 1) % cfg.measure_every) == 0) {
             float mx = 0.f, my = 0.f, mz = 0.f;
             for (int i = tid; i < N; i += NT) {
-                const float a = sx[i], b = sy[i], c = sz[i];
-                mx += a;
-                my += b;
-                mz += c;
-                const float th = acosf(fminf(1.0f, fmaxf(-1.0f, c))) - 0.5f * kPiF;
+                const float4 a = s4[i];
+                mx += a.x;
+                my += a.y;
+                mz += a.z;
+                const float th = acosf(fminf(1.0f, fmaxf(-1.0f, a.z))) - 0.5f * kPiF;
                 th2[i] += th * th;
             }
             for (int off = 16; off; off >>= 1) {
@@ -388,7 +421,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep_direct(const SweepConfig cfg,
             }
             __syncthreads();
             if (warp == 0) {
-                double et = e_part;
+                double et = c_epart[lane];
                 for (int off = 16; off; off >>= 1) et += __shfl_xor_sync(0xffffffffu, et, off);
                 if (lane == 0) {
                     double Mx = 0, My = 0, Mz = 0;
@@ -413,13 +446,18 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep_direct(const SweepConfig cfg,
 
     // ---- write back
     float *gd = buf.spins + (size_t)r * 3 * N;
-    for (int i = tid; i < 3 * N; i += NT) gd[i] = sx[i];
+    for (int i = tid; i < N; i += NT) {
+        const float4 a = s4[i];
+        gd[i] = a.x;
+        gd[N + i] = a.y;
+        gd[2 * N + i] = a.z;
+    }
     if (measuring && buf.theta2) {
         double *gt = buf.theta2 + (size_t)r * N;
         for (int i = tid; i < N; i += NT) gt[i] += (double)th2[i];
     }
     if (warp == 0) {
-        double et = e_part;
+        double et = c_epart[lane];
         for (int off = 16; off; off >>= 1) et += __shfl_xor_sync(0xffffffffu, et, off);
         if (lane == 0) {
             if (buf.energy) buf.energy[r] = e_track_s + et;
@@ -433,54 +471,69 @@ __global__ void __launch_bounds__(MAXT, 1) k_sweep_direct(const SweepConfig cfg,
 }
 
 struct Inst {
-    int C, EPT, MAXT;
+    int C, EPT, MAXT, MINB;
     cudaError_t (*launch)(const SweepConfig &, const SweepBuffers &, int, size_t, cudaStream_t);
 };
 
-template <int C, int EPT, int MAXT>
+template <int C, int EPT, int MAXT, int MINB>
 cudaError_t launch_inst(const SweepConfig &c, const SweepBuffers &b, int threads, size_t smem, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(k_sweep_direct<C, EPT, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_sweep_direct<C, EPT, MAXT, MINB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_sweep_direct<C, EPT, MAXT><<<c.R, threads, smem, st>>>(c, b);
+    k_sweep_direct<C, EPT, MAXT, MINB><<<c.R, threads, smem, st>>>(c, b);
     return cudaGetLastError();
 }
 
-// Register budget: C^2*4*EPT tensor values + 3*C^2 accumulators per thread; the
-// launch bound caps threads so that they fit without spilling.
+// Threads = one control warp + ceil(l^2 / EPT) field threads (rounded to warps).
+// The launch bound keeps C^2*4*EPT tensor values + 3*C^2 accumulators per
+// thread in registers; MINB = 2 instances fit two CTAs per SM (8 warps each, so
+// that each SM sub-partition holds 4 warps and 128 registers per thread).
+#define INST(C, E, T, B) {C, E, T, B, launch_inst<C, E, T, B>}
 const Inst kInst[] = {
-    {1, 1, 1024, launch_inst<1, 1, 1024>}, {1, 2, 512, launch_inst<1, 2, 512>},
-    {1, 4, 512, launch_inst<1, 4, 512>},   {1, 8, 512, launch_inst<1, 8, 512>},
-    {1, 18, 512, launch_inst<1, 18, 512>},
-    {2, 1, 1024, launch_inst<2, 1, 1024>}, {2, 2, 512, launch_inst<2, 2, 512>},
-    {2, 3, 512, launch_inst<2, 3, 512>},   {2, 5, 512, launch_inst<2, 5, 512>},
-    {4, 1, 256, launch_inst<4, 1, 256>},   {4, 2, 256, launch_inst<4, 2, 256>},
+    INST(1, 1, 288, 2), INST(1, 2, 544, 1), INST(1, 4, 288, 2), INST(1, 8, 544, 1),
+    INST(1, 19, 256, 2), INST(1, 18, 544, 1),
+    INST(2, 1, 544, 1), INST(2, 2, 544, 1), INST(2, 5, 256, 2), INST(2, 5, 544, 1),
+    INST(4, 1, 288, 1), INST(4, 2, 320, 1),
 };
+#undef INST
+
+int threads_of(const Inst &in, int ll) {
+    int th = (ll + in.EPT - 1) / in.EPT;
+    return 32 + ((th + 31) / 32) * 32;
+}
 
 size_t smem_bytes(int L, int l, int threads) {
     const int N = L * L, C = L / l, n = C * C, NW = threads / 32;
-    size_t b = sizeof(float) * (size_t)(4 * N + NW * 3 * n + NW * 4);
+    size_t b = sizeof(float4) * (size_t)N + sizeof(float) * (size_t)(N + (NW - 1) * 3 * n + NW * 4 + 4 * n);
     b += sizeof(uint16_t) * (size_t)l * l;
     return (b + 15) & ~(size_t)15;
 }
 
-// Choose the instance: fewest cell offsets per thread with at most
-// min(max_threads, instance bound) threads.
-const Inst *pick(int L, int l, int max_threads, int *threads) {
+// Choose the instance.  Many replicas (more than one wave of SMs): prefer two
+// CTAs per SM so that one CTA's serial update overlaps the other's field work;
+// otherwise prefer the most threads per CTA (shortest sub-step).
+const Inst *pick(int L, int l, int R, int nsm, int *threads) {
     if (l < 2 || L % l) return nullptr;
     const int C = L / l, ll = l * l;
+    const bool many = R > nsm;
     const Inst *best = nullptr;
+    int best_th = 0;
     for (const Inst &in : kInst) {
         if (in.C != C) continue;
-        int th = (ll + in.EPT - 1) / in.EPT;
-        th = ((th + 31) / 32) * 32;
-        if (th > max_threads || th > in.MAXT) continue;
-        if (!best || in.EPT < best->EPT) {
+        const int th = threads_of(in, ll);
+        if (th > in.MAXT) continue;
+        if (smem_bytes(L, l, th) * in.MINB > 220 * 1024) continue;
+        bool better = false;
+        if (!best) better = true;
+        else if (many && in.MINB != best->MINB) better = in.MINB > best->MINB;
+        else better = th > best_th;
+        if (better) {
             best = &in;
-            *threads = th;
+            best_th = th;
         }
     }
     if (!best) return nullptr;
-    if (smem_bytes(L, l, *threads) > 200 * 1024) return nullptr;
+    *threads = best_th;
     return best;
 }
 
@@ -488,14 +541,16 @@ const Inst *pick(int L, int l, int max_threads, int *threads) {
 
 bool direct_supported(int L, int l) {
     int th = 0;
-    return pick(L, l, 1024, &th) != nullptr;
+    return pick(L, l, 1, 1, &th) != nullptr;
 }
 
 cudaError_t launch_sweep_direct(const SweepConfig &c, const SweepBuffers &b, int threads_hint,
                                 cudaStream_t st) {
+    (void)threads_hint;
+    int dev = 0, nsm = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     int threads = 0;
-    const Inst *in = pick(c.L, c.l, threads_hint > 0 ? threads_hint : 1024, &threads);
-    if (!in) in = pick(c.L, c.l, 1024, &threads);
+    const Inst *in = pick(c.L, c.l, c.R, nsm, &threads);
     if (!in) return cudaErrorNotSupported;
     return in->launch(c, b, threads, smem_bytes(c.L, c.l, threads), st);
 }

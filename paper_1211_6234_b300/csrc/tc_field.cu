@@ -1,0 +1,375 @@
+// tc_field.cu -- stale dipole field of a window for all replicas on the
+// 5th-generation tensor cores (tcgen05), in split-BF16x3 with FP32 accumulation.
+//
+// For the S_w sites of a window (Sec. 3.1 update sites of B consecutive
+// sub-steps) and every replica r:
+//     H0[r][b*S_w + s] = sum_{a, m} W~_{ba}(q_s - m) s_r^a(m)          (Sec. 2.1, Eq. 2)
+// is a GEMM D[M x N] = A[M x K] B[K x N] with
+//     rows M  = (b, s): in-plane rows b in {x, y} contract over K = (a in {x, y}, m),
+//                       zz rows contract over K = (z, m)  (the tensor is block diagonal),
+//     cols N  = replicas,
+//     A       = the Toeplitz tile W~(q_s - m), built in shared memory from the
+//               L^2-entry tensor (8 pre-shifted bf16 copies so that every 16-byte
+//               chunk is an aligned vector load),
+//     B       = the spins of the replicas, bf16 hi/lo, row r = [x-plane | y-plane | z-plane].
+// Each value v is split v = hi + lo (hi = bf16(v), lo = bf16(v - hi)) and the
+// product is hi_A hi_B + hi_A lo_B + lo_A hi_B (error ~2^-18 relative).
+//
+// One CTA = one (M-tile of 128 rows, N-tile of up to 256 replicas, range of
+// K-blocks of 64).  Operands are staged by all threads into the canonical
+// K-major, no-swizzle core-matrix layout (8 rows x 16 bytes per core matrix),
+// two stages deep; thread 0 issues tcgen05.mma (M=128, N=tile, K=16) into a
+// TMEM accumulator and commits each stage to an mbarrier.  The epilogue reads
+// TMEM with tcgen05.ld and adds the partial tile into H0 (split-K reduction).
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+#include "tc_field.cuh"
+
+namespace dipmc {
+
+namespace {
+
+constexpr int kTcThreads = 128;
+constexpr int kKB = 64;                       // K elements per stage
+constexpr int kTileA = 128 * kKB * 2;         // bytes of one A tile (hi or lo)
+constexpr int kMaxNT = 256;
+constexpr int kTileB = kMaxNT * kKB * 2;      // bytes of one B tile (hi or lo)
+constexpr int kStage = 2 * kTileA + 2 * kTileB;
+constexpr int kStages = 2;
+constexpr long long kWaitCycles = 4LL << 30;  // bounded mbarrier waits (~2 s at 2 GHz)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Canonical no-swizzle K-major layout: element (row, k) of a tile with 64 K
+// columns lives at (row/8)*1024 + (k/8)*128 + (row%8)*16 + (k%8)*2 bytes:
+// core matrices of 8 rows x 8 elements (128 B); adjacent along K: 128 B
+// (leading byte offset), adjacent along M/N: 1024 B (stride byte offset).
+__device__ __forceinline__ uint32_t core_off(int row, int kc) { return (row >> 3) * 1024 + kc * 128 + (row & 7) * 16; }
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);          // start address
+    d |= (uint64_t)(128u >> 4) << 16;                 // leading byte offset (K direction)
+    d |= (uint64_t)(1024u >> 4) << 32;                // stride byte offset (M/N direction)
+    d |= (uint64_t)1 << 46;                           // descriptor version for tcgen05
+    // base offset 0, layout type 0 = no swizzle
+    return d;
+}
+
+// Instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major.
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
+    return (1u << 4)                  // D format: F32
+           | (1u << 7)                // A format: BF16
+           | (1u << 10)               // B format: BF16
+           | ((uint32_t)(N >> 3) << 17)
+           | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *m, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *m, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(m)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait; returns false (and leaves the error flag to the caller) on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *m, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(m, parity))
+        if (clock64() - t0 > kWaitCycles) return false;
+    return true;
+}
+
+// 16-byte asynchronous global -> shared copy (L2 only); src_bytes = 0 fills zeros.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *m) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(m))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ uint64_t mbar[kStages];
+    __shared__ uint32_t tmem_base_s;
+    __shared__ int sites_s[128];        // site of each row of this M-tile
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // ---- this CTA's unit: M-tile, N-tile, K-block range
+    const TcUnit u = a.units[blockIdx.x];
+    const int L = a.L, N = L * L, Sw = a.Sw;
+    const int row0 = u.mtile * 128;                 // first row (b*Sw + s) of the tile
+    const bool zz = row0 >= 2 * Sw;
+    const int n0 = u.ntile * a.NT;                  // first replica of the tile
+    const int nrows_b = a.NT;                       // N of the MMA
+    const uint32_t idesc = make_idesc(128, nrows_b);
+
+    // row tid of the tile: site and tensor components (constant over the K loop)
+    const int my_row = row0 + tid;
+    const int my_b = my_row / Sw;                         // output component 0 x, 1 y, 2 z
+    const int my_q = a.wsite[my_row - my_b * Sw];
+    const int my_qy = my_q / L, my_qx = my_q - my_qy * L;
+    const int comp_a0 = my_b == 0 ? 0 : 1;                // (b, a = x): xx or xy
+    const int comp_a1 = my_b == 0 ? 1 : 2;                // (b, a = y): xy or yy
+    (void)sites_s;
+    if (warp == 0) {
+        // TMEM accumulator: 128 lanes x NT fp32 columns (allocation is a power of 2 >= 32)
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                     "r"((uint32_t)a.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_s;
+    bool ok = true;
+
+    const int nkb = u.kb_end - u.kb_begin;
+    for (int i = 0; i < nkb; ++i) {
+        const int st = i & 1;
+        if (i >= 2) ok &= mbar_wait(&mbar[st], (uint32_t)(((i >> 1) - 1) & 1));
+        uint8_t *base = smem + st * kStage;
+        uint8_t *Ahi = base, *Alo = base + kTileA, *Bhi = base + 2 * kTileA, *Blo = base + 2 * kTileA + kTileB;
+        const int kb = u.kb_begin + i;
+        const int k0 = kb * kKB;                     // K offset within this tile's contraction
+        // ---- A: Toeplitz tile, 128 rows x 64 K; thread tid builds row tid (8 chunks of 8)
+        const uint32_t sAhi = smem_u32(Ahi), sAlo = smem_u32(Alo), sBhi = smem_u32(Bhi), sBlo = smem_u32(Blo);
+        {
+            const int al = zz ? 2 : (k0 >= N ? 1 : 0);    // input component of this K block
+            const int comp = zz ? 3 : (al == 0 ? comp_a0 : comp_a1);
+            const int m0 = k0 - (zz ? 0 : al * N);        // first source site of the block
+            int my = m0 / L, mx = m0 - my * L;
+            const __nv_bfloat16 *wc = a.wsh + (size_t)comp * 2 * L * 2 * L;
+#pragma unroll
+            for (int kc = 0; kc < 8; ++kc) {
+                int dy = my - my_qy;
+                if (dy < 0) dy += L;
+                int x0 = mx - my_qx;                      // W~(q - m) = W~(m - q): forward segment from x0
+                if (x0 < 0) x0 += L;
+                const size_t off = (size_t)(x0 & 7) * 4 * 2 * L * 2 * L + (size_t)dy * (2 * L) + (x0 & ~7);
+                cp_async16(sAhi + core_off(tid, kc), wc + off, 16);
+                cp_async16(sAlo + core_off(tid, kc), wc + off + (size_t)L * 2 * L, 16);
+                mx += 8;
+                if (mx >= L) { mx -= L; ++my; }
+            }
+        }
+        // ---- B: spins of NT replicas x 64 K (zero rows past R)
+        const int kofs = (zz ? 2 * N : 0) + k0;
+#pragma unroll
+        for (int kc = 0; kc < 8; ++kc) {
+            for (int rr = tid; rr < nrows_b; rr += kTcThreads) {
+                const int r = n0 + rr;
+                const bool in = r < a.R;
+                const size_t g = (size_t)(in ? r : 0) * 3 * N + kofs + kc * 8;
+                cp_async16(sBhi + core_off(rr, kc), a.spins_hi + g, in ? 16u : 0u);
+                cp_async16(sBlo + core_off(rr, kc), a.spins_lo + g, in ? 16u : 0u);
+            }
+        }
+        cp_async_commit();
+        cp_async_wait_all();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ah = smem_u32(Ahi), alo = smem_u32(Alo), bh = smem_u32(Bhi), blo = smem_u32(Blo);
+#pragma unroll
+            for (int ks = 0; ks < kKB / 16; ++ks) {
+                const uint32_t ko = ks * 256;        // 16 K elements = 2 core matrices = 256 B
+                const uint32_t acc0 = (i > 0 || ks > 0) ? 1u : 0u;
+                umma_bf16(tmem, smem_desc(ah + ko), smem_desc(bh + ko), idesc, acc0);
+                umma_bf16(tmem, smem_desc(ah + ko), smem_desc(blo + ko), idesc, 1u);
+                umma_bf16(tmem, smem_desc(alo + ko), smem_desc(bh + ko), idesc, 1u);
+            }
+            umma_commit(&mbar[st]);
+        }
+    }
+    // ---- wait for the last stage (its commit covers every earlier MMA)
+    if (nkb > 0) {
+        const int last = nkb - 1;
+        ok &= mbar_wait(&mbar[last & 1], (uint32_t)((last >> 1) & 1));
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!ok) {
+        if (tid == 0) atomicExch(a.error, 1);
+    } else if (nkb > 0) {
+        // ---- epilogue: warp w owns TMEM lanes 32w..32w+31 = rows of the tile
+        const int row = row0 + warp * 32 + lane;
+        for (int cb = 0; cb < nrows_b; cb += 32) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int r = n0 + cb + j;
+                if (r < a.R) atomicAdd(a.H0 + (size_t)r * a.ldh + row, v[j]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)a.tmem_cols)
+                     : "memory");
+    }
+}
+
+// 8 shifted, doubled bf16 hi/lo copies of W~: wsh[c][comp][hl][y][i] = part_hl(W~_comp(y, (i + c) mod L)),
+// i in [0, 2L).  Any 8 consecutive columns starting at x0 are then the aligned
+// 16 bytes at i = x0 - (x0 mod 8) of copy c = x0 mod 8.
+__global__ void k_build_wsh(int L, const double *__restrict__ W64, __nv_bfloat16 *wsh) {
+    const size_t total = (size_t)8 * 4 * L * 2 * L;
+    const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= total) return;
+    const int i = (int)(gid % (2 * L));
+    size_t rest = gid / (2 * L);
+    const int y = (int)(rest % L);
+    rest /= L;
+    const int comp = (int)(rest % 4);
+    const int c = (int)(rest / 4);
+    const int x = (i + c) % L;
+    const int N = L * L;
+    const float v = (float)W64[comp * N + y * L + x];
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+    const size_t base = (((size_t)c * 4 + comp) * 2) * L * 2 * L;
+    wsh[base + (size_t)y * 2 * L + i] = hi;
+    wsh[base + (size_t)L * 2 * L + (size_t)y * 2 * L + i] = lo;
+}
+
+// Window sites of sweep t, window w (same schedule as the sweep kernels).
+__global__ void k_window_sites(int L, int l, uint2 key, uint32_t t, int schedule, int k0, int B, int *wsite) {
+    const int n = (L / l) * (L / l), C = L / l, ll = l * l;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= B * n) return;
+    const int j = s / n, d = s % n, k = k0 + j;
+    uint32_t v;
+    if (schedule == 0) {
+        const uint4 rk = philox(make_uint4(t, 0u, 0u, kTagPerm), key);
+        v = perm_offset(rk, ceil_log2_u((uint32_t)l), (uint32_t)ll, (uint32_t)k);
+    } else {
+        const uint4 o = philox(make_uint4(t, (uint32_t)k, 0u, kTagDraw), key);
+        v = (uint32_t)(((unsigned long long)o.x * (unsigned long long)ll) >> 32);
+    }
+    const int qx = (int)(v % l) + l * (d % C), qy = (int)(v / l) + l * (d / C);
+    wsite[s] = qy * L + qx;
+}
+
+}  // namespace
+
+size_t tc_wsh_elems(int L) { return (size_t)8 * 4 * 2 * L * 2 * L; }
+
+bool tc_supported(int L, int l, int B) {
+    if (L % 8 || L < 8 || l < 2 || L % l) return false;
+    const int n = (L / l) * (L / l);
+    const int Sw = B * n;
+    return Sw % 128 == 0 && (l * l) % B == 0;
+}
+
+size_t tc_smem_bytes() { return (size_t)kStages * kStage; }
+
+cudaError_t launch_build_wsh(int L, const double *W64, __nv_bfloat16 *wsh, cudaStream_t st) {
+    const size_t total = (size_t)8 * 4 * L * 2 * L;
+    k_build_wsh<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(L, W64, wsh);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_window_sites(int L, int l, uint2 key, uint32_t t, int schedule, int k0, int B, int *wsite,
+                                cudaStream_t st) {
+    const int Sw = B * (L / l) * (L / l);
+    k_window_sites<<<(Sw + 127) / 128, 128, 0, st>>>(L, l, key, t, schedule, k0, B, wsite);
+    return cudaGetLastError();
+}
+
+int tc_plan(int L, int Sw, int R, int nsm, TcUnit *units, int max_units, int *NT_out, int *tmem_cols) {
+    const int N = L * L;
+    const int NT = R >= 256 ? 256 : ((R + 15) / 16) * 16;
+    const int ntiles = (R + NT - 1) / NT;
+    const int mt_inplane = 2 * Sw / 128, mt_zz = Sw / 128;
+    const int kb_inplane = 2 * N / kKB, kb_zz = N / kKB;
+    const long long total = (long long)ntiles * (mt_inplane * kb_inplane + mt_zz * kb_zz);
+    // smallest K-blocks per unit whose units (rounded up per tile) fit one wave
+    int kbpu = (int)((total + nsm - 1) / nsm);
+    if (kbpu < 2) kbpu = 2;
+    for (;; ++kbpu) {
+        long long cnt = 0;
+        for (int mt = 0; mt < mt_inplane + mt_zz; ++mt) {
+            const int nkb = mt < mt_inplane ? kb_inplane : kb_zz;
+            cnt += (nkb + kbpu - 1) / kbpu;
+        }
+        if (cnt * ntiles <= nsm || kbpu >= kb_inplane) break;
+    }
+    int nu = 0;
+    for (int nt = 0; nt < ntiles; ++nt)
+        for (int mt = 0; mt < mt_inplane + mt_zz; ++mt) {
+            const int nkb = mt < mt_inplane ? kb_inplane : kb_zz;
+            for (int kb = 0; kb < nkb; kb += kbpu) {
+                if (nu >= max_units) return -1;
+                units[nu].mtile = mt;
+                units[nu].ntile = nt;
+                units[nu].kb_begin = kb;
+                units[nu].kb_end = kb + kbpu < nkb ? kb + kbpu : nkb;
+                ++nu;
+            }
+        }
+    *NT_out = NT;
+    int cols = 32;
+    while (cols < NT) cols <<= 1;
+    *tmem_cols = cols;
+    return nu;
+}
+
+cudaError_t launch_tc_field(const TcFieldArgs &a, int nunits, cudaStream_t st) {
+    const size_t smem = tc_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(k_tc_field, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_tc_field<<<nunits, kTcThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace dipmc

@@ -1,0 +1,442 @@
+// window.cu -- the windowed sweep: the l^2 sub-steps of a sweep are processed in
+// windows of B consecutive sub-steps.  At the start of a window the dipole
+// field at all S_w = B*n sites the window will visit is taken from one bulk
+// evaluation on the state at the window's start (the "stale" field: a fat
+// contraction over all replicas, done by the tensor-core kernel, or the FP32
+// full field for validation).  The B sub-steps then run in order, each exactly
+// as the simultaneous-flip update of Sec. 3.1/3.2 prescribes; the field of a
+// window site is its stale value plus the exact change from every move
+// accepted earlier in the window:
+//     h_q = h_q(stale) + sum_{p accepted since the window start} W~(q - p) (S_p - s_p).
+// This is the same field the direct path computes, up to rounding.
+//
+// k_window_steps: one CTA (4 warps) per replica.  Spins live in shared memory
+// for the window; warp 0 takes the decisions (lanes d < n: the n sites of the
+// sub-step); after each sub-step all warps add the accepted moves'
+// contributions to the fields of the window's remaining sites.
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+#include "window.cuh"
+
+namespace dipmc {
+
+namespace {
+
+constexpr int kWThreads = 128;
+constexpr float kPiF = 3.14159265358979f;
+
+__device__ __forceinline__ void perp_basis_w(float nx, float ny, float nz, float3 &b1, float3 &b2) {
+    const float sign = copysignf(1.0f, nz);
+    const float a = -1.0f / (sign + nz);
+    const float b = nx * ny * a;
+    b1 = make_float3(1.0f + sign * nx * nx * a, sign * b, -sign * nx);
+    b2 = make_float3(b, sign + ny * ny * a, -ny);
+}
+
+__device__ void obs_push_w(ObsAcc &A, const double x[MC_NOBS]) {
+    A.nsamples += 1;
+#pragma unroll 1
+    for (int k = 0; k < kNB; ++k) {
+        A.pcnt[k] += 1;
+        const bool done = A.pcnt[k] == (1LL << k);
+        const double inv = 1.0 / (double)(1LL << k);
+        for (int o = 0; o < MC_NOBS; ++o) {
+            A.psum[o][k] += x[o];
+            if (done) {
+                const double mean = A.psum[o][k] * inv;
+                A.bsum[o][k] += mean;
+                A.bsq[o][k] += mean * mean;
+                A.psum[o][k] = 0.0;
+            }
+        }
+        if (done) {
+            A.bcnt[k] += 1;
+            A.pcnt[k] = 0;
+        }
+    }
+}
+
+// W~ restricted to the minimum-image quarter 0 <= x, y <= L/2, as (xx, xy, yy, zz).
+// The tensor is even in x and in y except xy, which is odd in each: a
+// displacement (dx, dy) reads entry (|dx|, |dy|) and flips the sign of xy when
+// exactly one of dx, dy is negative (xy vanishes on the axes and at L/2).
+__device__ __forceinline__ float3 wq_apply(const float4 *__restrict__ wq, int L, int dx, int dy, float3 d) {
+    const int h = L >> 1;
+    if (dx < 0) dx += L;
+    if (dy < 0) dy += L;
+    float sgn = 1.0f;
+    if (dx > h) { dx = L - dx; sgn = -sgn; }
+    if (dy > h) { dy = L - dy; sgn = -sgn; }
+    const float4 w = wq[dy * (h + 1) + dx];
+    const float xy = sgn * w.y;
+    return make_float3(w.x * d.x + xy * d.y, xy * d.x + w.z * d.y, w.w * d.z);
+}
+
+template <int C>
+__global__ void __launch_bounds__(kWThreads) k_window_steps(const WindowConfig cfg, const WindowBuffers buf) {
+    constexpr int n = C * C;
+    const int L = cfg.L, l = cfg.l, N = L * L, ll = l * l, B = cfg.B, Sw = B * n;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int r = blockIdx.x;
+    const bool pre_ok = cfg.schedule == 0;   // each site visited once per sweep: its spin is
+                                             // unchanged until its own sub-step of the window
+
+    extern __shared__ float4 smem_w[];
+    const int hq = (L >> 1) + 1;
+    float4 *s4 = smem_w;                                         // [N] spins
+    float4 *hcur = s4 + N;                                       // [Sw] field of the window sites
+    float4 *pS = hcur + Sw;                                      // [Sw] proposal S, threshold -T ln u
+    float4 *pd = pS + Sw;                                        // [Sw] delta = S - s, field-free part of dE
+    float4 *wq = pd + Sw;                                        // [(L/2+1)^2] minimum-image quarter of W~
+    int *wxy = reinterpret_cast<int *>(wq + hq * hq);            // [Sw] site as x | y << 16
+    __shared__ float4 s_acc[2][32];                              // accepted moves of a sub-step: (delta, x | y << 16),
+    __shared__ int s_nacc[2];                                    // double-buffered by sub-step parity
+    __shared__ double s_epart[32];
+    __shared__ float s_mred[kWThreads / 32][4];
+
+    const RepParams P = buf.params[r];
+    const uint2 key = cfg.key;
+    const uint32_t t = cfg.t;
+    const int k0 = cfg.w * B;
+    const float W0xx = __ldg(buf.W32), W0xy = __ldg(buf.W32 + N), W0yy = __ldg(buf.W32 + 2 * N), W0zz = __ldg(buf.W32 + 3 * N);
+
+    // proposal, delta and the field-free part of dE (anisotropy + self-image) of site q
+    auto propose = [&](int q, float u1, float cps, float sps, float4 &S, float4 &D) {
+        const float4 sq = s4[q];
+        float S0, S1, S2;
+        if (cfg.proposal == 1) {
+            const float z = 2.0f * u1 - 1.0f;
+            const float rr = sqrtf(fmaxf(0.0f, (1.0f - z) * (1.0f + z)));
+            S0 = rr * cps;
+            S1 = rr * sps;
+            S2 = z;
+        } else {
+            // 1 - cos(alpha) = u1 (1 - cos cone), formed without cancellation
+            const float omc = u1 * cfg.cap_c1;
+            const float ca = 1.0f - omc;
+            const float sa = sqrtf(fmaxf(0.0f, omc * (2.0f - omc)));
+            float3 b1, b2;
+            perp_basis_w(sq.x, sq.y, sq.z, b1, b2);
+            S0 = ca * sq.x + sa * (cps * b1.x + sps * b2.x);
+            S1 = ca * sq.y + sa * (cps * b1.y + sps * b2.y);
+            S2 = ca * sq.z + sa * (cps * b1.z + sps * b2.z);
+            const float inv = 1.0f / sqrtf(S0 * S0 + S1 * S1 + S2 * S2);
+            S0 *= inv;
+            S1 *= inv;
+            S2 *= inv;
+        }
+        const float dX = S0 - sq.x, dY = S1 - sq.y, dZ = S2 - sq.z;
+        const float z0 = sq.z * sq.z, z1 = S2 * S2;
+        const float dan = (-P.K2 * z1 - P.K4 * z1 * z1) - (-P.K2 * z0 - P.K4 * z0 * z0);
+        const float self = W0xx * dX * dX + 2.0f * W0xy * dX * dY + W0yy * dY * dY + W0zz * dZ * dZ;
+        S = make_float4(S0, S1, S2, 0.0f);
+        D = make_float4(dX, dY, dZ, dan + 0.5f * P.CD * self);
+    };
+    auto site_of = [&](int s) -> int {
+        const int j = s / n, d = s % n, k = k0 + j;
+        uint32_t v;
+        if (cfg.schedule == 0) {
+            const uint4 rk = philox(make_uint4(t, 0u, 0u, kTagPerm), key);
+            v = perm_offset(rk, ceil_log2_u((uint32_t)l), (uint32_t)ll, (uint32_t)k);
+        } else {
+            const uint4 o = philox(make_uint4(t, (uint32_t)k, 0u, kTagDraw), key);
+            v = (uint32_t)(((unsigned long long)o.x * (unsigned long long)ll) >> 32);
+        }
+        const int qx = (int)(v % l) + l * (d % C), qy = (int)(v / l) + l * (d / C);
+        return qx | (qy << 16);
+    };
+    auto attempt_rng = [&](int s, int q) -> uint4 {
+        const int k = k0 + s / n;
+        return philox(make_uint4((uint32_t)q, (uint32_t)r, t, ((uint32_t)k & 0x00FFFFFFu) | kTagAttempt), key);
+    };
+
+    // ---- window set-up: state, tensor table, sites, stale field, proposals
+    const float *gs = buf.spins + (size_t)r * 3 * N;
+    for (int i = tid; i < N; i += kWThreads) s4[i] = make_float4(gs[i], gs[N + i], gs[2 * N + i], 0.0f);
+    for (int i = tid; i < hq * hq; i += kWThreads) {
+        const int x = i % hq, y = i / hq, g = y * L + x;
+        wq[i] = make_float4(buf.W32[g], buf.W32[N + g], buf.W32[2 * N + g], buf.W32[3 * N + g]);
+    }
+    __syncthreads();
+    for (int s = tid; s < Sw; s += kWThreads) {
+        const int xy = site_of(s);
+        const int q = (xy >> 16) * L + (xy & 0xFFFF);
+        wxy[s] = xy;
+        float h0, h1, h2;
+        if (cfg.stale_mode == 0) {
+            const float *f = buf.stale + (size_t)r * 3 * N;
+            h0 = f[q];
+            h1 = f[N + q];
+            h2 = f[2 * N + q];
+        } else {
+            const float *hr = buf.stale + (size_t)r * cfg.ldh;
+            h0 = hr[0 * Sw + s];
+            h1 = hr[1 * Sw + s];
+            h2 = hr[2 * Sw + s];
+        }
+        hcur[s] = make_float4(h0, h1, h2, 0.0f);
+        if (pre_ok) {
+            const uint4 wds = attempt_rng(s, q);
+            float sps, cps;
+            sincospif(2.0f * u24f(wds.y), &sps, &cps);
+            const float u = u24f(wds.z);
+            float4 S, D;
+            propose(q, u24f(wds.x), cps, sps, S, D);
+            // accept iff u < exp(-dE/T)  <=>  dE < -T ln u   (u = 0: always)
+            S.w = (u > 0.0f) ? -P.T * logf(u) : INFINITY;
+            pS[s] = S;
+            pd[s] = D;
+        }
+    }
+    __syncthreads();
+
+    long long n_acc = 0;
+    // One barrier per sub-step.  In phase j, warp 0 adds the moves of sub-step j-1 to
+    // the fields of its own n sites and decides sub-step j, while warps 1..3 add the
+    // moves of sub-step j-1 to the fields of every later site (sub-steps >= j+1).
+    for (int j = 0; j < B; ++j) {
+        const int cur = j & 1, prev = cur ^ 1;
+        if (warp == 0) {
+            int accept = 0;
+            float dX = 0.f, dY = 0.f, dZ = 0.f, dE = 0.f;
+            int xy = 0;
+            if (lane < n) {
+                const int s = j * n + lane;
+                xy = wxy[s];
+                const int qx = xy & 0xFFFF, qy = (xy >> 16) & 0x7FFF, q = qy * L + qx;
+                float4 h = hcur[s];
+                if (j > 0) {
+                    const int np = s_nacc[prev];
+                    for (int i = 0; i < np; ++i) {
+                        const float4 a = s_acc[prev][i];
+                        const int pxy = __float_as_int(a.w);
+                        const float3 c = wq_apply(wq, L, qx - (pxy & 0xFFFF), qy - ((pxy >> 16) & 0x7FFF),
+                                                  make_float3(a.x, a.y, a.z));
+                        h.x += c.x;
+                        h.y += c.y;
+                        h.z += c.z;
+                    }
+                }
+                float4 S, D;
+                float thr;
+                if (pre_ok) {
+                    S = pS[s];
+                    D = pd[s];
+                    thr = S.w;
+                } else {
+                    const uint4 wds = attempt_rng(s, q);
+                    float sps, cps;
+                    sincospif(2.0f * u24f(wds.y), &sps, &cps);
+                    const float u = u24f(wds.z);
+                    propose(q, u24f(wds.x), cps, sps, S, D);
+                    thr = (u > 0.0f) ? -P.T * logf(u) : INFINITY;
+                }
+                dX = D.x;
+                dY = D.y;
+                dZ = D.z;
+                const int xp = (qx + 1 == L) ? q - qx : q + 1;
+                const int xm = (qx == 0) ? q + L - 1 : q - 1;
+                const int yp = (qy + 1 == L) ? qx : q + L;
+                const int ym = (qy == 0) ? q + N - L : q - L;
+                const float4 a = s4[xp], b = s4[xm], c = s4[yp], dd = s4[ym];
+                const float n0 = (a.x + b.x) + (c.x + dd.x);
+                const float n1 = (a.y + b.y) + (c.y + dd.y);
+                const float n2 = (a.z + b.z) + (c.z + dd.z);
+                const float dex = -P.J * (dX * n0 + dY * n1 + dZ * n2);
+                dE = D.w + dex + P.CD * (dX * h.x + dY * h.y + dZ * h.z);
+                accept = dE < thr;
+                if (buf.trace) {
+                    const uint4 wds = attempt_rng(s, q);
+                    float *tr = buf.trace + ((((size_t)r * cfg.nsweeps_call + cfg.it) * ll + (k0 + j)) * n + lane) * MC_TRACE_W;
+                    tr[0] = (float)q;
+                    tr[1] = h.x; tr[2] = h.y; tr[3] = h.z;
+                    tr[4] = dE;
+                    tr[5] = u24f(wds.z);
+                    tr[6] = (float)accept;
+                    tr[7] = S.x; tr[8] = S.y; tr[9] = S.z;
+                }
+                if (accept) {
+                    s4[q] = make_float4(S.x, S.y, S.z, 0.0f);
+                    pd[s] = make_float4(dX, dY, dZ, dE);      // the move, for the window-end bookkeeping
+                    wxy[s] = xy | (int)0x80000000;             // accepted
+                }
+            }
+            const unsigned ball = __ballot_sync(0xffffffffu, accept);
+            if (accept) {
+                const int slot = __popc(ball & ((1u << lane) - 1u));
+                s_acc[cur][slot] = make_float4(dX, dY, dZ, __int_as_float(xy));
+            }
+            if (lane == 0) {
+                n_acc += __popc(ball);
+                s_nacc[cur] = __popc(ball);
+            }
+        } else if (j > 0) {
+            const int np = s_nacc[prev];
+            if (np) {
+                for (int s = (j + 1) * n + (tid - 32); s < Sw; s += kWThreads - 32) {
+                    const int xy = wxy[s];
+                    const int qx = xy & 0xFFFF, qy = (xy >> 16) & 0x7FFF;
+                    float4 h = hcur[s];
+                    for (int i = 0; i < np; ++i) {
+                        const float4 a = s_acc[prev][i];
+                        const int pxy = __float_as_int(a.w);
+                        const float3 c = wq_apply(wq, L, qx - (pxy & 0xFFFF), qy - ((pxy >> 16) & 0x7FFF),
+                                                  make_float3(a.x, a.y, a.z));
+                        h.x += c.x;
+                        h.y += c.y;
+                        h.z += c.z;
+                    }
+                    hcur[s] = h;
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- write the accepted moves back to global memory (FP32 and the bf16 split)
+    float *gd = buf.spins + (size_t)r * 3 * N;
+    for (int s = tid; s < Sw; s += kWThreads) {
+        const int xy = wxy[s];
+        if (xy >= 0) continue;
+        const int q = ((xy >> 16) & 0x7FFF) * L + (xy & 0xFFFF);
+        const float4 v = s4[q];
+        gd[q] = v.x;
+        gd[N + q] = v.y;
+        gd[2 * N + q] = v.z;
+        if (buf.spins_hi) {
+            __nv_bfloat16 *hi = buf.spins_hi + (size_t)r * 3 * N;
+            __nv_bfloat16 *lo = buf.spins_lo + (size_t)r * 3 * N;
+            const float v3[3] = {v.x, v.y, v.z};
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+                const __nv_bfloat16 h16 = __float2bfloat16_rn(v3[cc]);
+                hi[cc * N + q] = h16;
+                lo[cc * N + q] = __float2bfloat16_rn(v3[cc] - __bfloat162float(h16));
+            }
+        }
+    }
+    // ---- exact energy change of the window: accepted dE plus, per sub-step, the
+    // neglected cross terms C_D d_p.W~(q - p).d_q of its simultaneous moves (Sec. 3.2)
+    double e_loc = 0.0;
+    for (int j = tid; j < B; j += kWThreads) {
+        float sub = 0.0f;
+        for (int d = 0; d < n; ++d) {
+            const int s = j * n + d;
+            const int xy = wxy[s];
+            if (xy >= 0) continue;
+            const float4 m = pd[s];
+            sub += m.w;
+            for (int dp = 0; dp < d; ++dp) {
+                const int pxy = wxy[j * n + dp];
+                if (pxy >= 0) continue;
+                const float4 mp = pd[j * n + dp];
+                const float3 Wd = wq_apply(wq, L, (xy & 0xFFFF) - (pxy & 0xFFFF),
+                                           ((xy >> 16) & 0x7FFF) - ((pxy >> 16) & 0x7FFF), make_float3(m.x, m.y, m.z));
+                sub += P.CD * (mp.x * Wd.x + mp.y * Wd.y + mp.z * Wd.z);
+            }
+        }
+        e_loc += (double)sub;
+    }
+    for (int off = 16; off; off >>= 1) e_loc += __shfl_xor_sync(0xffffffffu, e_loc, off);
+    if (lane == 0) s_epart[warp] = e_loc;
+    __syncthreads();
+    if (tid == 0) {
+        double et = 0.0;
+        for (int i = 0; i < kWThreads / 32; ++i) et += s_epart[i];
+        buf.energy[r] += et;
+    }
+    __syncthreads();
+    if (cfg.measure) {
+        float mx = 0.f, my = 0.f, mz = 0.f;
+        double *gt = buf.theta2 ? buf.theta2 + (size_t)r * N : nullptr;
+        for (int i = tid; i < N; i += kWThreads) {
+            const float4 a = s4[i];
+            mx += a.x;
+            my += a.y;
+            mz += a.z;
+            if (gt) {
+                const float th = acosf(fminf(1.0f, fmaxf(-1.0f, a.z))) - 0.5f * kPiF;
+                gt[i] += (double)(th * th);
+            }
+        }
+        for (int off = 16; off; off >>= 1) {
+            mx += __shfl_xor_sync(0xffffffffu, mx, off);
+            my += __shfl_xor_sync(0xffffffffu, my, off);
+            mz += __shfl_xor_sync(0xffffffffu, mz, off);
+        }
+        if (lane == 0) {
+            s_mred[warp][0] = mx;
+            s_mred[warp][1] = my;
+            s_mred[warp][2] = mz;
+        }
+        __syncthreads();
+        if (tid == 0 && buf.obs) {
+            double Mx = 0, My = 0, Mz = 0;
+            for (int ww = 0; ww < kWThreads / 32; ++ww) {
+                Mx += s_mred[ww][0];
+                My += s_mred[ww][1];
+                Mz += s_mred[ww][2];
+            }
+            Mx /= N; My /= N; Mz /= N;
+            double x[MC_NOBS];
+            x[MC_OBS_ABS_M] = sqrt(Mx * Mx + My * My + Mz * Mz);
+            x[MC_OBS_MZ] = Mz;
+            x[MC_OBS_ABS_MZ] = fabs(Mz);
+            x[MC_OBS_MPAR] = sqrt(Mx * Mx + My * My);
+            x[MC_OBS_E] = buf.energy[r] / N;
+            obs_push_w(buf.obs[r], x);
+        }
+    }
+    if (tid == 0 && buf.obs) {
+        buf.obs[r].accepted += n_acc;
+        buf.obs[r].attempted += (long long)Sw;
+    }
+}
+
+__global__ void k_spins_to_bf16(size_t count, const float *__restrict__ s, __nv_bfloat16 *hi, __nv_bfloat16 *lo) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const float x = s[i];
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    hi[i] = h;
+    lo[i] = __float2bfloat16_rn(x - __bfloat162float(h));
+}
+
+}  // namespace
+
+size_t window_smem_bytes(int L, int Sw) {
+    const size_t N = (size_t)L * L, hq = (size_t)(L / 2 + 1);
+    return sizeof(float4) * (N + 3 * (size_t)Sw + hq * hq) + sizeof(int) * (size_t)Sw;
+}
+
+bool window_supported(int L, int l, int B) {
+    if (l < 2 || L % l) return false;
+    const int C = L / l;
+    if (C != 1 && C != 2 && C != 4) return false;
+    if (B < 1 || (l * l) % B) return false;
+    return window_smem_bytes(L, B * C * C) <= 200 * 1024;
+}
+
+cudaError_t launch_window_steps(const WindowConfig &c, const WindowBuffers &b, cudaStream_t st) {
+    const int C = c.L / c.l;
+    const size_t smem = window_smem_bytes(c.L, c.B * C * C);
+    cudaError_t e;
+#define LAUNCH(CC)                                                                                   \
+    e = cudaFuncSetAttribute(k_window_steps<CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    if (e != cudaSuccess) return e;                                                                  \
+    k_window_steps<CC><<<c.R, kWThreads, smem, st>>>(c, b);
+    if (C == 1) { LAUNCH(1) }
+    else if (C == 2) { LAUNCH(2) }
+    else if (C == 4) { LAUNCH(4) }
+    else return cudaErrorNotSupported;
+#undef LAUNCH
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spins_to_bf16(size_t count, const float *s, __nv_bfloat16 *hi, __nv_bfloat16 *lo, cudaStream_t st) {
+    k_spins_to_bf16<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(count, s, hi, lo);
+    return cudaGetLastError();
+}
+
+}  // namespace dipmc

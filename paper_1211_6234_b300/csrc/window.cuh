@@ -1,0 +1,45 @@
+// window.cuh -- declarations of the windowed sweep (window.cu, tc_field.cu).
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+
+namespace dipmc {
+
+struct WindowConfig {
+    int L, l, R;
+    uint2 key;
+    uint32_t t;          // sweep counter of this sweep
+    int it;              // index of this sweep within the call (trace position)
+    int nsweeps_call;    // sweeps of the call (trace stride)
+    int w;               // window index within the sweep
+    int B;               // sub-steps per window (divides l^2)
+    int proposal;        // 0 cap, 1 sphere
+    float cap_c1;        // 1 - cos(cone)
+    int schedule;        // 0 permutation, 1 draw
+    int measure;         // sample observables after this window (last window of a measured sweep)
+    int stale_mode;      // 0: stale = full field [R][3][N]; 1: stale = H0 [R][ldh], row b*Sw + s
+    int ldh;             // per-replica stride of H0 (>= 3*Sw)
+};
+
+struct WindowBuffers {
+    const float *W32;             // [4][N]
+    float *spins;                 // [R][3][N] FP32
+    __nv_bfloat16 *spins_hi;      // [R][3][N] bf16(s) (may be null)
+    __nv_bfloat16 *spins_lo;      // [R][3][N] bf16(s - hi)
+    const RepParams *params;      // [R]
+    double *energy;               // [R]
+    ObsAcc *obs;                  // [R]
+    double *theta2;               // [R][N]
+    float *trace;                 // optional
+    const float *stale;           // see stale_mode
+};
+
+size_t window_smem_bytes(int L, int Sw);
+bool window_supported(int L, int l, int B);
+cudaError_t launch_window_steps(const WindowConfig &c, const WindowBuffers &b, cudaStream_t st);
+cudaError_t launch_spins_to_bf16(size_t count, const float *s, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
+                                 cudaStream_t st);
+
+}  // namespace dipmc

@@ -19,17 +19,18 @@ LIB_PATH = os.path.join(_HERE, "libdipmc.so")
 MC_OK, MC_EINVAL, MC_ENOMEM, MC_ENOTREADY, MC_ETIMEOUT, MC_ECUDA, MC_ENOSYS = 0, -1, -2, -3, -4, -5, -6
 MC_NOBS = 5
 OBS_NAMES = ("abs_m", "m_z", "abs_m_z", "m_par", "e")
-MC_PATH_AUTO, MC_PATH_DIRECT = 0, 1
+MC_PATH_AUTO, MC_PATH_DIRECT, MC_PATH_WINDOW_F32, MC_PATH_TENSOR = 0, 1, 2, 3
 MC_TRACE_W = 10
 
 # Every symbol include/dipmc.h declares.
 ABI_SYMBOLS = (
     "mc_last_error", "mc_version", "mc_create_lattice", "mc_destroy", "mc_set_params",
-    "mc_set_proposal", "mc_set_schedule", "mc_set_field_path", "mc_init_spins",
+    "mc_set_proposal", "mc_set_schedule", "mc_set_field_path", "mc_set_window", "mc_init_spins",
     "mc_precompute_W", "mc_sweep", "mc_sweep_trace", "mc_observables", "mc_reset_observables",
     "mc_get_spins", "mc_get_field", "mc_get_W", "mc_energy", "mc_get_sweep_counter",
-    "mc_checkpoint", "mc_restore", "mc_energy_noalloc",
+    "mc_checkpoint", "mc_restore", "mc_energy_noalloc", "mc_set_timing", "mc_get_timing",
 )
+KERNEL_CLASSES = ("sweep_direct", "tc_field", "window_steps", "full_field")
 
 
 class McError(RuntimeError):
@@ -61,6 +62,10 @@ class mc_obs(C.Structure):
         return d
 
 
+class mc_timing(C.Structure):
+    _fields_ = [("launches", C.c_int64 * 4), ("ms", C.c_double * 4)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is not built; run `python -m paper_1211_6234_b300.build`")
@@ -75,6 +80,7 @@ def _load():
         "mc_set_proposal": ([vp, i32, f64], i32),
         "mc_set_schedule": ([vp, i32], i32),
         "mc_set_field_path": ([vp, i32], i32),
+        "mc_set_window": ([vp, i32], i32),
         "mc_init_spins": ([vp, i32, vp], i32),
         "mc_precompute_W": ([vp, i32, i32], i32),
         "mc_sweep": ([vp, i32, i32, vp], i32),
@@ -89,6 +95,8 @@ def _load():
         "mc_checkpoint": ([vp, vp, C.POINTER(C.c_size_t)], i32),
         "mc_restore": ([vp, vp, C.c_size_t], i32),
         "mc_energy_noalloc": ([i32, i32, vp, vp, vp, vp, vp], i32),
+        "mc_set_timing": ([vp, i32], i32),
+        "mc_get_timing": ([vp, C.POINTER(mc_timing)], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -176,6 +184,9 @@ class Lattice:
     def set_field_path(self, path=MC_PATH_AUTO):
         _ck(_lib.mc_set_field_path(self.h, path))
 
+    def set_window(self, B=0):
+        _ck(_lib.mc_set_window(self.h, B))
+
     def init_spins(self, mode=0, user=None):
         if mode == 2:
             a = np.ascontiguousarray(user, np.float32)
@@ -232,6 +243,15 @@ class Lattice:
         a = np.empty(self.R, np.float64)
         _ck(_lib.mc_energy(self.h, _np_ptr(a), _stream_ptr(stream)))
         return a
+
+    def set_timing(self, enable=True):
+        _ck(_lib.mc_set_timing(self.h, int(bool(enable))))
+
+    def timing(self) -> dict:
+        """Per-kernel-class launches and device milliseconds since set_timing."""
+        t = mc_timing()
+        _ck(_lib.mc_get_timing(self.h, C.byref(t)))
+        return {nm: {"launches": t.launches[i], "ms": t.ms[i]} for i, nm in enumerate(KERNEL_CLASSES)}
 
     def sweep_counter(self) -> int:
         v = C.c_uint64()

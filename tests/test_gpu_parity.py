@@ -228,3 +228,158 @@ def test_random_init_is_uniform_on_sphere(dipmc):
     assert np.abs(norm - 1).max() < 1e-6
     z = s[:, 2].ravel()
     assert abs(z.mean()) < 0.02 and abs((z**2).mean() - 1 / 3) < 0.02
+
+
+# ---------------------------------------------------------------- benchmark configuration
+def test_bench_configuration_sampled_replicas(dipmc):
+    """256 replicas of L = 64, l = 32 with the temperature x K4/K2 ladder -- the launch
+    configuration bench.py times (two CTAs per SM) -- one traced sweep; sampled
+    replicas are compared attempt by attempt with the oracle, every replica is checked
+    for self-consistent decisions."""
+    L, l, R, A = 64, 32, 256, 64
+    lad = [(F32(1.0), F32(0.1), F32(k2), F32(k4), F32(T)) for (T, k2, k4) in inputs.ladder(16, 16)]
+    seed = 1
+    s0 = inputs.random_spins(L, R, seed=2024)
+    with dipmc.Lattice(L, l, R, seed) as lat:
+        lat.precompute_W(A, True)
+        for r, prm in enumerate(lad):
+            lat.set_params(*prm, replica=r)
+        lat.init_spins(2, s0)
+        tr = lat.sweep_trace(1)
+        sg = lat.get_spins().astype(np.float64)
+    assert tr.shape == (R, L * L, 10)
+    # every replica: each site attempted once, decisions consistent with the threshold rule
+    for r in range(R):
+        q = tr[r, :, 0].astype(np.int64)
+        assert np.array_equal(np.sort(q), np.arange(L * L))
+        T = lad[r][4]
+        u = tr[r, :, 5].astype(np.float64)
+        thr = np.where(u > 0, -T * np.log(np.maximum(u, 1e-300)), np.inf)
+        dE = tr[r, :, 4].astype(np.float64)
+        acc = tr[r, :, 6].astype(np.int64)
+        clear = np.abs(dE - thr) > 1e-5 * (1 + abs(dE))
+        assert np.array_equal(acc[clear], (dE < thr)[clear].astype(np.int64))
+    W = oracle_W(L, A)
+    for r in (0, 37, 148, 255):
+        J, CD, K2, K4, T = lad[r]
+        p = orc.params(L, l, J, CD, K2, K4, T, proposal=0, cone=0.5, schedule=0, seed=seed, replica=r)
+        o = orc.sweeps(p, W, s0[r], 0, 1)
+        hmax = float(np.abs(o["h"]).max())
+        rep = compare_trace(tr[r], o, T, scale=1 + abs(J) + abs(K2) + abs(K4) + abs(CD) * hmax)
+        if rep.straddles == 0:
+            np.testing.assert_allclose(sg[r], o["s"], rtol=0, atol=1e-5)
+
+
+def test_many_replica_instance_small_lattice(dipmc):
+    """More replicas than SMs selects the two-CTAs-per-SM instance also at L = 16."""
+    L, l, R = 16, 8, 160
+    s0 = inputs.random_spins(L, R, seed=5)
+    with dipmc.Lattice(L, l, R, 8) as lat:
+        lat.precompute_W(64, True)
+        lat.init_spins(2, s0)
+        tr = lat.sweep_trace(2)
+    W = oracle_W(L, 64)
+    for r in (0, 159):
+        p = orc.params(L, l, 1.0, F32(0.1), F32(0.8), 0.0, F32(0.6), seed=8, replica=r)
+        o = orc.sweeps(p, W, s0[r], 0, 2)
+        compare_trace(tr[r], o, F32(0.6), scale=2 + 0.1 * float(np.abs(o["h"]).max()))
+
+
+# ---------------------------------------------------------------- windowed paths
+WCASES = [
+    # L, l, R, B (0 = automatic), schedule, nsweeps
+    (16, 8, 2, 0, 0, 2),       # S_w = 128
+    (16, 8, 3, 16, 0, 2),      # smaller window than the tensor path needs (F32 only)
+    (16, 4, 2, 0, 0, 2),       # 16 simultaneous sites, S_w = 128
+    (16, 16, 1, 0, 0, 1),      # l = L: one site per sub-step, S_w = 256
+    (48, 24, 1, 0, 0, 1),      # non-power-of-two L
+    (32, 16, 2, 0, 1, 1),      # the paper's with-replacement schedule
+    (64, 32, 2, 0, 0, 1),      # L = 64, S_w = 512
+]
+
+
+@pytest.mark.parametrize("path", [2, 3], ids=["window_f32", "tensor_bf16x3"])
+@pytest.mark.parametrize("case", WCASES, ids=[f"L{c[0]}_l{c[1]}_R{c[2]}_B{c[3]}_s{c[4]}" for c in WCASES])
+def test_window_paths_match_oracle(dipmc, path, case):
+    L, l, R, B, schedule, nsw = case
+    if path == 3 and B == 16:
+        pytest.skip("the tensor path needs windows of a multiple of 128 sites")
+    params = [(F32(1.0), F32(0.1), F32(0.8), F32(0.0), F32(0.6)),
+              (F32(0.7), F32(0.3), F32(0.5), F32(-0.2), F32(1.1)),
+              (F32(1.0), F32(0.2), F32(0.8), F32(0.3), F32(0.4))][:R]
+    seed = 300 + L + l
+    s0 = inputs.random_spins(L, R, seed=L + 7 * l)
+    A = 16
+    with dipmc.Lattice(L, l, R, seed) as lat:
+        lat.precompute_W(A, True)
+        lat.set_window(B)
+        lat.set_field_path(path)
+        lat.set_schedule(schedule)
+        for r, prm in enumerate(params):
+            lat.set_params(*prm, replica=r)
+        lat.init_spins(2, s0)
+        tr = lat.sweep_trace(nsw)
+        sg = lat.get_spins().astype(np.float64)
+        Eg_full = lat.energy()
+        Eg_tracked = np.array([lat.observables(r)["energy"] * L * L for r in range(R)])
+    W = oracle_W(L, A)
+    for r in range(R):
+        J, CD, K2, K4, T = params[r]
+        p = orc.params(L, l, J, CD, K2, K4, T, proposal=0, cone=0.5, schedule=schedule, seed=seed, replica=r)
+        o = orc.sweeps(p, W, s0[r], 0, nsw)
+        hmax = float(np.abs(o["h"]).max())
+        rep = compare_trace(tr[r], o, T, scale=1 + abs(J) + abs(K2) + abs(K4) + abs(CD) * hmax)
+        if rep.straddles == 0:
+            np.testing.assert_allclose(sg[r], o["s"], rtol=0, atol=1e-5)
+        assert abs(Eg_tracked[r] - Eg_full[r]) < 1e-5 * (L * L) * (1 + abs(J) + abs(K2) + abs(K4) + CD * 10)
+
+
+def test_tensor_path_bench_configuration(dipmc):
+    """256 replicas x L = 64 on the tensor path (the benchmark's configuration): one
+    traced sweep, sampled replicas compared attempt by attempt with the oracle."""
+    L, l, R, A = 64, 32, 256, 64
+    lad = [(F32(1.0), F32(0.1), F32(k2), F32(k4), F32(T)) for (T, k2, k4) in inputs.ladder(16, 16)]
+    s0 = inputs.random_spins(L, R, seed=2024)
+    with dipmc.Lattice(L, l, R, 1) as lat:
+        lat.precompute_W(A, True)
+        lat.set_field_path(dipmc.MC_PATH_TENSOR)
+        for r, prm in enumerate(lad):
+            lat.set_params(*prm, replica=r)
+        lat.init_spins(2, s0)
+        tr = lat.sweep_trace(1)
+        sg = lat.get_spins().astype(np.float64)
+    W = oracle_W(L, A)
+    worst = 0.0
+    for r in (0, 1, 100, 200, 255):
+        J, CD, K2, K4, T = lad[r]
+        p = orc.params(L, l, J, CD, K2, K4, T, proposal=0, cone=0.5, schedule=0, seed=1, replica=r)
+        o = orc.sweeps(p, W, s0[r], 0, 1)
+        hmax = float(np.abs(o["h"]).max())
+        rep = compare_trace(tr[r], o, T, scale=1 + abs(J) + abs(K2) + abs(K4) + abs(CD) * hmax)
+        worst = max(worst, rep.h_err_norm)
+        if rep.straddles == 0:
+            np.testing.assert_allclose(sg[r], o["s"], rtol=0, atol=1e-5)
+    assert worst < 1e-5
+
+
+def test_tensor_path_observables_match_direct(dipmc):
+    """Long runs of the tensor and direct paths sample the same law: means within
+    4 combined binned errors (L = 16, 64 replicas pooled by temperature)."""
+    L, l, R, nsw = 16, 8, 64, 600
+    res = {}
+    for path in (dipmc.MC_PATH_DIRECT, dipmc.MC_PATH_TENSOR):
+        with dipmc.Lattice(L, l, R, 21 if path == 1 else 22) as lat:
+            lat.precompute_W(64, True)
+            lat.set_field_path(path)
+            lat.set_params(F32(1.0), F32(0.1), F32(0.8), F32(0.0), F32(2.0))
+            lat.init_spins(1)
+            lat.sweep(100, 0)
+            lat.reset_observables()
+            lat.sweep(nsw, 1)
+            res[path] = [lat.observables(r) for r in range(R)]
+    for nm in ("abs_m", "e"):
+        a = np.array([o[nm]["mean"] for o in res[1]])
+        b = np.array([o[nm]["mean"] for o in res[3]])
+        ea = np.sqrt(np.mean([o[nm]["err"] ** 2 for o in res[1]]) / R)
+        eb = np.sqrt(np.mean([o[nm]["err"] ** 2 for o in res[3]]) / R)
+        assert abs(a.mean() - b.mean()) < 4 * math.hypot(ea, eb) + 1e-9, (nm, a.mean(), b.mean(), ea, eb)
