@@ -104,10 +104,13 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def window_sites():
-    """Window size the library picks for L = 64, l = 32 (n = 4): the largest power
-    of two B dividing l^2 with 4B <= 512 and 4B a multiple of 128."""
+def window_sites(B_set=0):
+    """Sites per window: B_set sub-steps if given, else the library's default for
+    L = 64, l = 32 (n = 4): the largest power of two B dividing l^2 with 4B <= 512
+    and 4B a multiple of 128."""
     n = (L // l) ** 2
+    if B_set:
+        return B_set * n
     best = 0
     B = 1
     while B <= l * l:
@@ -195,6 +198,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--path", choices=["tensor", "direct", "window"], default="tensor",
                     help="field path: tcgen05 split-BF16x3 window field, FP32 direct, FP32 window")
+    ap.add_argument("--window", type=int, default=0, help="sub-steps per window (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     args = ap.parse_args()
@@ -219,6 +223,7 @@ def main():
                "tensor": dipmc.MC_PATH_TENSOR}[args.path]
     lat = dipmc.Lattice(L, l, R, seed=1 + 7919 * rank)
     lat.precompute_W(A_IMG, True)
+    lat.set_window(args.window)
     lat.set_field_path(path_id)
     lat.set_proposal(0, 0.5)
     for r, (j, cd, k2, k4, T) in enumerate(lad):
@@ -278,7 +283,7 @@ def main():
     peaks = measured_peaks()
     sm_max = (clk.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2032.0)
     peak_fp32 = sms * FP32_FMA_PER_CLK_PER_SM * 2 * sm_max * 1e6 / 1e12
-    Sw = window_sites()
+    Sw = window_sites(args.window)
     # algorithmic work: the field of one site update sums N sources x 5 multiply-adds
     # (xx,xy | xy,yy | zz) = 10 N flops; the update itself reads s (12 B), h (12 B)
     # and writes s (12 B) = 36 B

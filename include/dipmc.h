@@ -63,6 +63,7 @@ extern "C" {
 #define MC_PATH_DIRECT 1      /* FP32 CUDA-core Toeplitz sum, one CTA per replica */
 #define MC_PATH_WINDOW_F32 2  /* windowed sweep, stale field from the FP32 full field */
 #define MC_PATH_TENSOR 3      /* windowed sweep, stale field on tcgen05 tensor cores, split-BF16x3 */
+#define MC_PATH_FFT 4         /* full field per sub-step by 2D FFT convolution (L a power of two) */
 
 typedef struct mc_lattice mc_lattice;
 
@@ -121,7 +122,10 @@ int mc_set_schedule(mc_lattice *lat, int kind);
  * on the state at the window's start (for all replicas together), and each
  * sub-step adds the exact change from the moves accepted earlier in the window,
  * so the sweep is the same simultaneous-flip update (Sec. 3.1, 3.2) up to
- * rounding.  MC_PATH_TENSOR needs L % 8 == 0 and B*(L/l)^2 % 128 == 0. */
+ * rounding.  MC_PATH_TENSOR needs L % 8 == 0 and B*(L/l)^2 % 128 == 0.
+ * MC_PATH_FFT evaluates the full field of every replica by FFT convolution before
+ * each sub-step (L a power of two, 8 <= L <= 1024, spins in global memory); it is
+ * the path for large lattices, where mc_get_field and mc_energy also use the FFT. */
 int mc_set_field_path(mc_lattice *lat, int path);
 
 /* Sub-steps per window of the windowed paths (must divide l^2; 0 = automatic). */

@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "fft_field.cuh"
 #include "internal.cuh"
 #include "tc_field.cuh"
 #include "window.cuh"
@@ -79,6 +80,10 @@ struct mc_lattice {
     int nunits = 0, NT = 0, tmem_cols = 0, plan_Sw = 0;
     int *err_flag = nullptr;
     bool wsh_ready = false;
+    float4 *wq = nullptr;     // quarter table of W~ for the windowed paths
+    float *What = nullptr;    // [4][N] transform of W~ (FFT path), transposed layout
+    float2 *fft_scratch = nullptr;
+    bool what_ready = false;
     // kernel timing (events recorded around launches while enabled)
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> tev[MC_NKCLASS];
@@ -107,6 +112,9 @@ void free_all(mc_lattice *p) {
     cudaFree(p->wsite);
     cudaFree(p->units);
     cudaFree(p->err_flag);
+    cudaFree(p->wq);
+    cudaFree(p->What);
+    cudaFree(p->fft_scratch);
 }
 
 // Records an event pair around a launch when timing is on.
@@ -163,6 +171,7 @@ bool path_supported(const mc_lattice *p, int path) {
             const int B = window_of(p, true);
             return B > 0 && tc_supported(p->L, p->l, B) && window_supported(p->L, p->l, B);
         }
+        case MC_PATH_FFT: return fft_supported(p->L);
         default: return false;
     }
 }
@@ -170,6 +179,7 @@ bool path_supported(const mc_lattice *p, int path) {
 int resolve_path(const mc_lattice *p) {
     if (p->path != MC_PATH_AUTO) return p->path;
     if (direct_supported(p->L, p->l)) return MC_PATH_DIRECT;
+    if (fft_supported(p->L)) return MC_PATH_FFT;
     if (path_supported(p, MC_PATH_WINDOW_F32)) return MC_PATH_WINDOW_F32;
     return -1;
 }
@@ -187,10 +197,12 @@ int clear_obs(mc_lattice *p, cudaStream_t st) {
 
 uint2 key_of(uint64_t seed) { return make_uint2((uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)); }
 
+int full_field(mc_lattice *p, cudaStream_t st);
+
 int anchor_energy(mc_lattice *p, cudaStream_t st) {
-    cudaError_t e = launch_full_field(p->L, p->R, p->W32, p->spins, p->field, st);
-    if (e != cudaSuccess) return cuda_fail(e, "full-field kernel");
-    e = launch_energy(p->L, p->R, p->spins, p->field, p->dparams, p->energy, st);
+    int rc = full_field(p, st);
+    if (rc) return rc;
+    cudaError_t e = launch_energy(p->L, p->R, p->spins, p->field, p->dparams, p->energy, st);
     if (e != cudaSuccess) return cuda_fail(e, "energy kernel");
     p->energy_valid = true;
     return MC_OK;
@@ -282,6 +294,7 @@ int run_windows(mc_lattice *p, int path, int nsweeps, int measure_every, float *
     b.params = p->dparams; b.energy = p->energy; b.obs = p->obs; b.theta2 = p->theta2;
     b.trace = trace;
     b.stale = tensor ? p->H0 : p->field;
+    b.wq = p->wq;
     TcFieldArgs ta{};
     if (tensor) {
         ta.L = p->L; ta.Sw = Sw; ta.R = p->R; ta.NT = p->NT; ta.ldh = 3 * Sw; ta.tmem_cols = p->tmem_cols;
@@ -319,12 +332,91 @@ int run_windows(mc_lattice *p, int path, int nsweeps, int measure_every, float *
     return MC_OK;
 }
 
+int ensure_fft(mc_lattice *p, cudaStream_t st) {
+    if (!p->What) CKA(cudaMalloc(&p->What, sizeof(float) * 4 * (size_t)p->N()));
+    if (!p->fft_scratch) CKA(cudaMalloc(&p->fft_scratch, fft_scratch_bytes(p->L, p->R)));
+    if (!p->what_ready) {
+        cudaError_t e = launch_build_what(p->L, p->W64, p->What, st);
+        if (e != cudaSuccess) return cuda_fail(e, "transform of W~");
+        p->what_ready = true;
+    }
+    return MC_OK;
+}
+
+bool use_fft_full_field(const mc_lattice *p) {
+    return fft_supported(p->L) && (p->path == MC_PATH_FFT || p->L >= 128);
+}
+
+// Full field of every replica into p->field: FFT for large lattices, else direct.
+int full_field(mc_lattice *p, cudaStream_t st) {
+    cudaError_t e;
+    if (use_fft_full_field(p)) {
+        int rc = ensure_fft(p, st);
+        if (rc) return rc;
+        TimedLaunch tl(p, MC_K_FULL_FIELD, st);
+        e = launch_fft_field(p->L, p->R, p->spins, p->What, p->fft_scratch, p->field, st);
+    } else {
+        TimedLaunch tl(p, MC_K_FULL_FIELD, st);
+        e = launch_full_field(p->L, p->R, p->W32, p->spins, p->field, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "full-field evaluation");
+    return MC_OK;
+}
+
+int run_fft(mc_lattice *p, int nsweeps, int measure_every, float *trace, cudaStream_t st) {
+    int rc = ensure_fft(p, st);
+    if (rc) return rc;
+    const int ll = p->l * p->l;
+    FftStepConfig c{};
+    c.L = p->L; c.l = p->l; c.R = p->R;
+    c.key = key_of(p->seed);
+    c.nsweeps_call = nsweeps;
+    c.proposal = p->proposal;
+    c.cap_c1 = (float)(1.0 - std::cos(p->cone));
+    c.schedule = p->schedule;
+    FftStepBuffers b{};
+    b.W32 = p->W32; b.spins = p->spins; b.field = p->field; b.params = p->dparams; b.obs = p->obs;
+    b.trace = trace;
+    bool measured_last = false;
+    for (int it = 0; it < nsweeps; ++it) {
+        c.t = (uint32_t)(p->t + (uint64_t)it);
+        c.it = it;
+        for (int k = 0; k < ll; ++k) {
+            cudaError_t e;
+            {
+                TimedLaunch tl(p, MC_K_FULL_FIELD, st);
+                e = launch_fft_field(p->L, p->R, p->spins, p->What, p->fft_scratch, p->field, st);
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "FFT field");
+            c.k = k;
+            {
+                TimedLaunch tl(p, MC_K_WINDOW_STEPS, st);
+                e = launch_fft_update(c, b, st);
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "FFT update kernel");
+        }
+        measured_last = measure_every > 0 && ((it + 1) % measure_every) == 0;
+        if (measured_last) {
+            cudaError_t e = launch_fft_field(p->L, p->R, p->spins, p->What, p->fft_scratch, p->field, st);
+            if (e != cudaSuccess) return cuda_fail(e, "FFT field");
+            e = launch_fft_observe(p->L, p->R, p->spins, p->field, p->dparams, p->energy, p->obs, p->theta2, st);
+            if (e != cudaSuccess) return cuda_fail(e, "observables");
+        }
+    }
+    cudaError_t e = launch_add_attempted(p->obs, p->R, (long long)nsweeps * p->N(), st);
+    if (e != cudaSuccess) return cuda_fail(e, "acceptance counters");
+    // the FFT path does not track the energy between measurements
+    p->energy_valid = measured_last;
+    return MC_OK;
+}
+
 int run_sweeps(mc_lattice *p, int nsweeps, int measure_every, float *trace, cudaStream_t st) {
     if (!p->W_ready) return fail(MC_ENOTREADY, "mc_precompute_W has not been called");
     if (nsweeps < 0) return fail(MC_EINVAL, "nsweeps must be >= 0");
     if (measure_every < 0) return fail(MC_EINVAL, "measure_every must be >= 0");
     if (nsweeps == 0) return MC_OK;
-    if (!p->energy_valid) {
+    const int path0 = resolve_path(p);
+    if (!p->energy_valid && path0 != MC_PATH_FFT) {
         int rc = anchor_energy(p, st);
         if (rc) return rc;
     }
@@ -359,6 +451,9 @@ int run_sweeps(mc_lattice *p, int nsweeps, int measure_every, float *trace, cuda
         if (e == cudaErrorNotSupported)
             return fail(MC_ENOSYS, "no field path supports L=%d l=%d (path %d)", p->L, p->l, p->path);
         if (e != cudaSuccess) return cuda_fail(e, "sweep kernel launch");
+    } else if (path == MC_PATH_FFT) {
+        int rc = run_fft(p, nsweeps, measure_every, trace, st);
+        if (rc) return rc;
     } else {
         int rc = run_windows(p, path, nsweeps, measure_every, trace, st);
         if (rc) return rc;
@@ -486,7 +581,7 @@ int mc_set_schedule(mc_lattice *p, int kind) {
 int mc_set_field_path(mc_lattice *p, int path) {
     int rc = check(p);
     if (rc) return rc;
-    if (path < MC_PATH_AUTO || path > MC_PATH_TENSOR) return fail(MC_EINVAL, "unknown field path %d", path);
+    if (path < MC_PATH_AUTO || path > MC_PATH_FFT) return fail(MC_EINVAL, "unknown field path %d", path);
     if (path != MC_PATH_AUTO && !path_supported(p, path))
         return fail(MC_ENOSYS, "field path %d does not support L=%d l=%d", path, p->L, p->l);
     p->path = path;
@@ -528,11 +623,15 @@ int mc_precompute_W(mc_lattice *p, int A, int tail) {
     if (A < 0 || A > 4096) return fail(MC_EINVAL, "image_cutoff %d outside [0, 4096]", A);
     cudaError_t e = launch_wtilde(p->L, A, tail ? 1 : 0, p->W64, p->W32, nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "W~ kernel");
+    if (!p->wq) CK(cudaMalloc(&p->wq, sizeof(float4) * (size_t)(p->L / 2 + 1) * (p->L / 2 + 1)));
+    e = launch_build_wq(p->L, p->W32, p->wq, nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "W~ quarter table");
     CK(cudaDeviceSynchronize());
     p->A = A;
     p->tail = tail ? 1 : 0;
     p->W_ready = true;
     p->wsh_ready = false;
+    p->what_ready = false;
     p->energy_valid = false;
     return MC_OK;
 }
@@ -629,8 +728,8 @@ int mc_get_field(mc_lattice *p, float *dst, int on_device, void *stream) {
     if (!dst) return fail(MC_EINVAL, "dst is null");
     if (!p->W_ready) return fail(MC_ENOTREADY, "mc_precompute_W has not been called");
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = launch_full_field(p->L, p->R, p->W32, p->spins, p->field, st);
-    if (e != cudaSuccess) return cuda_fail(e, "full-field kernel");
+    rc = full_field(p, st);
+    if (rc) return rc;
     CK(cudaMemcpyAsync(dst, p->field, sizeof(float) * p->spin_floats(),
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -652,9 +751,9 @@ int mc_energy(mc_lattice *p, double *dst, void *stream) {
     if (!dst) return fail(MC_EINVAL, "dst is null");
     if (!p->W_ready) return fail(MC_ENOTREADY, "mc_precompute_W has not been called");
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = launch_full_field(p->L, p->R, p->W32, p->spins, p->field, st);
-    if (e != cudaSuccess) return cuda_fail(e, "full-field kernel");
-    e = launch_energy(p->L, p->R, p->spins, p->field, p->dparams, p->etmp, st);
+    rc = full_field(p, st);
+    if (rc) return rc;
+    cudaError_t e = launch_energy(p->L, p->R, p->spins, p->field, p->dparams, p->etmp, st);
     if (e != cudaSuccess) return cuda_fail(e, "energy kernel");
     CK(cudaMemcpyAsync(dst, p->etmp, sizeof(double) * p->R, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));

@@ -4,7 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/dipmc.h"
+#include "dipmc.h"
 
 namespace dipmc {
 

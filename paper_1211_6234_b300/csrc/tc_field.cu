@@ -133,7 +133,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a)
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ uint64_t mbar[kStages];
     __shared__ uint32_t tmem_base_s;
-    __shared__ int sites_s[128];        // site of each row of this M-tile
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     // ---- this CTA's unit: M-tile, N-tile, K-block range
@@ -152,7 +151,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a)
     const int my_qy = my_q / L, my_qx = my_q - my_qy * L;
     const int comp_a0 = my_b == 0 ? 0 : 1;                // (b, a = x): xx or xy
     const int comp_a1 = my_b == 0 ? 1 : 2;                // (b, a = y): xy or yy
-    (void)sites_s;
     if (warp == 0) {
         // TMEM accumulator: 128 lanes x NT fp32 columns (allocation is a power of 2 >= 32)
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),

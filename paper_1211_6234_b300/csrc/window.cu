@@ -10,9 +10,9 @@
 //     h_q = h_q(stale) + sum_{p accepted since the window start} W~(q - p) (S_p - s_p).
 // This is the same field the direct path computes, up to rounding.
 //
-// k_window_steps: one CTA (4 warps) per replica.  Spins live in shared memory
+// k_window_steps: one CTA (8 warps) per replica.  Spins live in shared memory
 // for the window; warp 0 takes the decisions (lanes d < n: the n sites of the
-// sub-step); after each sub-step all warps add the accepted moves'
+// sub-step); warps 1..7 add the accepted moves
 // contributions to the fields of the window's remaining sites.
 #include <cuda_bf16.h>
 
@@ -23,7 +23,7 @@ namespace dipmc {
 
 namespace {
 
-constexpr int kWThreads = 128;
+constexpr int kWThreads = 256;
 constexpr float kPiF = 3.14159265358979f;
 
 __device__ __forceinline__ void perp_basis_w(float nx, float ny, float nz, float3 &b1, float3 &b2) {
@@ -34,27 +34,39 @@ __device__ __forceinline__ void perp_basis_w(float nx, float ny, float nz, float
     b2 = make_float3(b, sign + ny * ny * a, -ny);
 }
 
-__device__ void obs_push_w(ObsAcc &A, const double x[MC_NOBS]) {
-    A.nsamples += 1;
-#pragma unroll 1
-    for (int k = 0; k < kNB; ++k) {
-        A.pcnt[k] += 1;
-        const bool done = A.pcnt[k] == (1LL << k);
-        const double inv = 1.0 / (double)(1LL << k);
-        for (int o = 0; o < MC_NOBS; ++o) {
-            A.psum[o][k] += x[o];
-            if (done) {
-                const double mean = A.psum[o][k] * inv;
-                A.bsum[o][k] += mean;
-                A.bsq[o][k] += mean * mean;
-                A.psum[o][k] = 0.0;
-            }
-        }
+// One measurement sample into the log-binning accumulators (FP64, global memory):
+// thread k < kNB updates binning level k (blocks of 2^k samples); the levels are
+// independent, so their memory round trips overlap.
+__device__ void obs_push_level(ObsAcc &A, const double x[MC_NOBS], int k) {
+    const long long pc = A.pcnt[k] + 1;
+    const bool done = pc == (1LL << k);
+    const double inv = 1.0 / (double)(1LL << k);
+    double ps[MC_NOBS], bs[MC_NOBS], bq[MC_NOBS];
+#pragma unroll
+    for (int o = 0; o < MC_NOBS; ++o) {
+        ps[o] = A.psum[o][k];
+        bs[o] = A.bsum[o][k];
+        bq[o] = A.bsq[o][k];
+    }
+#pragma unroll
+    for (int o = 0; o < MC_NOBS; ++o) {
+        const double p = ps[o] + x[o];
         if (done) {
-            A.bcnt[k] += 1;
-            A.pcnt[k] = 0;
+            const double mean = p * inv;
+            A.bsum[o][k] = bs[o] + mean;
+            A.bsq[o][k] = bq[o] + mean * mean;
+            A.psum[o][k] = 0.0;
+        } else {
+            A.psum[o][k] = p;
         }
     }
+    if (done) {
+        A.bcnt[k] += 1;
+        A.pcnt[k] = 0;
+    } else {
+        A.pcnt[k] = pc;
+    }
+    if (k == 0) A.nsamples += 1;
 }
 
 // W~ restricted to the minimum-image quarter 0 <= x, y <= L/2, as (xx, xy, yy, zz).
@@ -74,7 +86,7 @@ __device__ __forceinline__ float3 wq_apply(const float4 *__restrict__ wq, int L,
 }
 
 template <int C>
-__global__ void __launch_bounds__(kWThreads) k_window_steps(const WindowConfig cfg, const WindowBuffers buf) {
+__global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfig cfg, const WindowBuffers buf) {
     constexpr int n = C * C;
     const int L = cfg.L, l = cfg.l, N = L * L, ll = l * l, B = cfg.B, Sw = B * n;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -133,12 +145,13 @@ __global__ void __launch_bounds__(kWThreads) k_window_steps(const WindowConfig c
         S = make_float4(S0, S1, S2, 0.0f);
         D = make_float4(dX, dY, dZ, dan + 0.5f * P.CD * self);
     };
+    const uint4 rk = cfg.schedule == 0 ? philox(make_uint4(t, 0u, 0u, kTagPerm), key) : make_uint4(0, 0, 0, 0);
+    const int hbits = ceil_log2_u((uint32_t)l);
     auto site_of = [&](int s) -> int {
         const int j = s / n, d = s % n, k = k0 + j;
         uint32_t v;
         if (cfg.schedule == 0) {
-            const uint4 rk = philox(make_uint4(t, 0u, 0u, kTagPerm), key);
-            v = perm_offset(rk, ceil_log2_u((uint32_t)l), (uint32_t)ll, (uint32_t)k);
+            v = perm_offset(rk, hbits, (uint32_t)ll, (uint32_t)k);
         } else {
             const uint4 o = philox(make_uint4(t, (uint32_t)k, 0u, kTagDraw), key);
             v = (uint32_t)(((unsigned long long)o.x * (unsigned long long)ll) >> 32);
@@ -153,11 +166,19 @@ __global__ void __launch_bounds__(kWThreads) k_window_steps(const WindowConfig c
 
     // ---- window set-up: state, tensor table, sites, stale field, proposals
     const float *gs = buf.spins + (size_t)r * 3 * N;
-    for (int i = tid; i < N; i += kWThreads) s4[i] = make_float4(gs[i], gs[N + i], gs[2 * N + i], 0.0f);
-    for (int i = tid; i < hq * hq; i += kWThreads) {
-        const int x = i % hq, y = i / hq, g = y * L + x;
-        wq[i] = make_float4(buf.W32[g], buf.W32[N + g], buf.W32[2 * N + g], buf.W32[3 * N + g]);
+    {
+        const float4 *gx = reinterpret_cast<const float4 *>(gs);            // N % 4 == 0 (L even)
+        const float4 *gy = reinterpret_cast<const float4 *>(gs + N);
+        const float4 *gz = reinterpret_cast<const float4 *>(gs + 2 * N);
+        for (int i = tid; i < N / 4; i += kWThreads) {
+            const float4 a = gx[i], b = gy[i], c = gz[i];
+            s4[4 * i + 0] = make_float4(a.x, b.x, c.x, 0.0f);
+            s4[4 * i + 1] = make_float4(a.y, b.y, c.y, 0.0f);
+            s4[4 * i + 2] = make_float4(a.z, b.z, c.z, 0.0f);
+            s4[4 * i + 3] = make_float4(a.w, b.w, c.w, 0.0f);
+        }
     }
+    for (int i = tid; i < hq * hq; i += kWThreads) wq[i] = buf.wq[i];
     __syncthreads();
     for (int s = tid; s < Sw; s += kWThreads) {
         const int xy = site_of(s);
@@ -189,40 +210,88 @@ __global__ void __launch_bounds__(kWThreads) k_window_steps(const WindowConfig c
             pd[s] = D;
         }
     }
+    if (tid < 64) s_acc[tid >> 5][tid & 31] = make_float4(0.f, 0.f, 0.f, __int_as_float(0));
     __syncthreads();
 
     long long n_acc = 0;
     // One barrier per sub-step.  In phase j, warp 0 adds the moves of sub-step j-1 to
-    // the fields of its own n sites and decides sub-step j, while warps 1..3 add the
+    // the fields of its own n sites and decides sub-step j, while warps 1.. add the
     // moves of sub-step j-1 to the fields of every later site (sub-steps >= j+1).
+    // Warp 0 keeps the static data of its next sites (coordinates, proposal,
+    // field-free part of dE) in registers, loaded one sub-step ahead.
+    int nx_xy = 0;
+    float4 nx_S = make_float4(0.f, 0.f, 0.f, 0.f), nx_D = nx_S;
+    if (warp == 0 && lane < n) {
+        nx_xy = wxy[lane];
+        if (pre_ok) {
+            nx_S = pS[lane];
+            nx_D = pd[lane];
+        }
+    }
     for (int j = 0; j < B; ++j) {
         const int cur = j & 1, prev = cur ^ 1;
         if (warp == 0) {
             int accept = 0;
             float dX = 0.f, dY = 0.f, dZ = 0.f, dE = 0.f;
-            int xy = 0;
+            const int s = j * n + lane;
+            const int xy = nx_xy;
+            const int qx = xy & 0xFFFF, qy = (xy >> 16) & 0x7FFF, q = qy * L + qx;
+            float4 h = make_float4(0.f, 0.f, 0.f, 0.f), a = h, b = h, c = h, dd = h;
+            int xp = 0, xm = 0, yp = 0, ym = 0;
             if (lane < n) {
-                const int s = j * n + lane;
-                xy = wxy[s];
-                const int qx = xy & 0xFFFF, qy = (xy >> 16) & 0x7FFF, q = qy * L + qx;
-                float4 h = hcur[s];
-                if (j > 0) {
-                    const int np = s_nacc[prev];
-                    for (int i = 0; i < np; ++i) {
-                        const float4 a = s_acc[prev][i];
-                        const int pxy = __float_as_int(a.w);
-                        const float3 c = wq_apply(wq, L, qx - (pxy & 0xFFFF), qy - ((pxy >> 16) & 0x7FFF),
-                                                  make_float3(a.x, a.y, a.z));
-                        h.x += c.x;
-                        h.y += c.y;
-                        h.z += c.z;
+                h = hcur[s];
+                xp = (qx + 1 == L) ? q - qx : q + 1;
+                xm = (qx == 0) ? q + L - 1 : q - 1;
+                yp = (qy + 1 == L) ? qx : q + L;
+                ym = (qy == 0) ? q + N - L : q - L;
+                a = s4[xp]; b = s4[xm]; c = s4[yp]; dd = s4[ym];
+            }
+            // field change from the last sub-step's moves: one (site, move) pair per lane
+            if (j > 0) {
+                float3 cr = make_float3(0.f, 0.f, 0.f);
+                if constexpr (n * n <= 32) {
+                    const int d = lane / n, m = lane % n;
+                    const int sxy = __shfl_sync(0xffffffffu, xy, d < n ? d : 0);
+                    if (lane < n * n) {
+                        const float4 mv = s_acc[prev][m];
+                        const int pxy = __float_as_int(mv.w);
+                        cr = wq_apply(wq, L, (sxy & 0xFFFF) - (pxy & 0xFFFF),
+                                      ((sxy >> 16) & 0x7FFF) - ((pxy >> 16) & 0x7FFF), make_float3(mv.x, mv.y, mv.z));
+                    }
+#pragma unroll
+                    for (int off = 1; off < n; off <<= 1) {
+                        cr.x += __shfl_xor_sync(0xffffffffu, cr.x, off);
+                        cr.y += __shfl_xor_sync(0xffffffffu, cr.y, off);
+                        cr.z += __shfl_xor_sync(0xffffffffu, cr.z, off);
+                    }
+                    const int src = (lane < n ? lane : 0) * n;
+                    cr.x = __shfl_sync(0xffffffffu, cr.x, src);
+                    cr.y = __shfl_sync(0xffffffffu, cr.y, src);
+                    cr.z = __shfl_sync(0xffffffffu, cr.z, src);
+                } else {
+                    if (lane < n) {
+#pragma unroll
+                        for (int i = 0; i < n; ++i) {
+                            const float4 mv = s_acc[prev][i];
+                            const int pxy = __float_as_int(mv.w);
+                            const float3 cc = wq_apply(wq, L, qx - (pxy & 0xFFFF), qy - ((pxy >> 16) & 0x7FFF),
+                                                       make_float3(mv.x, mv.y, mv.z));
+                            cr.x += cc.x;
+                            cr.y += cc.y;
+                            cr.z += cc.z;
+                        }
                     }
                 }
+                h.x += cr.x;
+                h.y += cr.y;
+                h.z += cr.z;
+            }
+            if (lane < n) {
                 float4 S, D;
                 float thr;
                 if (pre_ok) {
-                    S = pS[s];
-                    D = pd[s];
+                    S = nx_S;
+                    D = nx_D;
                     thr = S.w;
                 } else {
                     const uint4 wds = attempt_rng(s, q);
@@ -235,11 +304,6 @@ __global__ void __launch_bounds__(kWThreads) k_window_steps(const WindowConfig c
                 dX = D.x;
                 dY = D.y;
                 dZ = D.z;
-                const int xp = (qx + 1 == L) ? q - qx : q + 1;
-                const int xm = (qx == 0) ? q + L - 1 : q - 1;
-                const int yp = (qy + 1 == L) ? qx : q + L;
-                const int ym = (qy == 0) ? q + N - L : q - L;
-                const float4 a = s4[xp], b = s4[xm], c = s4[yp], dd = s4[ym];
                 const float n0 = (a.x + b.x) + (c.x + dd.x);
                 const float n1 = (a.y + b.y) + (c.y + dd.y);
                 const float n2 = (a.z + b.z) + (c.z + dd.z);
@@ -261,11 +325,26 @@ __global__ void __launch_bounds__(kWThreads) k_window_steps(const WindowConfig c
                     pd[s] = make_float4(dX, dY, dZ, dE);      // the move, for the window-end bookkeeping
                     wxy[s] = xy | (int)0x80000000;             // accepted
                 }
+                if (j + 1 < B) {                               // next sub-step's static data
+                    nx_xy = wxy[s + n];
+                    if (pre_ok) {
+                        nx_S = pS[s + n];
+                        nx_D = pd[s + n];
+                    }
+                }
             }
+            // slots [0, n) of the move list are all written every sub-step: accepted
+            // moves first, then one zero move per rejected site (readers use all n)
             const unsigned ball = __ballot_sync(0xffffffffu, accept);
-            if (accept) {
-                const int slot = __popc(ball & ((1u << lane) - 1u));
-                s_acc[cur][slot] = make_float4(dX, dY, dZ, __int_as_float(xy));
+            const unsigned below = (1u << lane) - 1u;
+            const unsigned nmask = (n >= 32) ? 0xffffffffu : ((1u << n) - 1u);
+            if (lane < n) {
+                if (accept) {
+                    s_acc[cur][__popc(ball & below)] = make_float4(dX, dY, dZ, __int_as_float(xy));
+                } else {
+                    const int slot = __popc(ball) + __popc(~ball & below & nmask);
+                    s_acc[cur][slot] = make_float4(0.f, 0.f, 0.f, __int_as_float(0));
+                }
             }
             if (lane == 0) {
                 n_acc += __popc(ball);
@@ -274,20 +353,38 @@ __global__ void __launch_bounds__(kWThreads) k_window_steps(const WindowConfig c
         } else if (j > 0) {
             const int np = s_nacc[prev];
             if (np) {
-                for (int s = (j + 1) * n + (tid - 32); s < Sw; s += kWThreads - 32) {
-                    const int xy = wxy[s];
+                // the sub-step's moves, in registers (n slots, unused ones are zero moves)
+                float4 mv[n];
+                int mx[n], my[n];
+#pragma unroll
+                for (int i = 0; i < n; ++i) {
+                    mv[i] = s_acc[prev][i];
+                    const int pxy = __float_as_int(mv[i].w);
+                    mx[i] = pxy & 0xFFFF;
+                    my[i] = (pxy >> 16) & 0x7FFF;
+                }
+                constexpr int kC = kWThreads - 32;
+                // two later sites per pass for independent chains
+                for (int s = (j + 1) * n + (tid - 32); s < Sw; s += 2 * kC) {
+                    const int s2 = s + kC;
+                    const bool two = s2 < Sw;
+                    const int xy = wxy[s], xy2 = two ? wxy[s2] : xy;
                     const int qx = xy & 0xFFFF, qy = (xy >> 16) & 0x7FFF;
+                    const int qx2 = xy2 & 0xFFFF, qy2 = (xy2 >> 16) & 0x7FFF;
                     float4 h = hcur[s];
-                    for (int i = 0; i < np; ++i) {
-                        const float4 a = s_acc[prev][i];
-                        const int pxy = __float_as_int(a.w);
-                        const float3 c = wq_apply(wq, L, qx - (pxy & 0xFFFF), qy - ((pxy >> 16) & 0x7FFF),
-                                                  make_float3(a.x, a.y, a.z));
-                        h.x += c.x;
-                        h.y += c.y;
-                        h.z += c.z;
+                    float4 h2 = two ? hcur[s2] : h;
+#pragma unroll
+                    for (int i = 0; i < n; ++i) {
+                        if (i < np) {
+                            const float3 d3 = make_float3(mv[i].x, mv[i].y, mv[i].z);
+                            const float3 c = wq_apply(wq, L, qx - mx[i], qy - my[i], d3);
+                            const float3 c2 = wq_apply(wq, L, qx2 - mx[i], qy2 - my[i], d3);
+                            h.x += c.x; h.y += c.y; h.z += c.z;
+                            h2.x += c2.x; h2.y += c2.y; h2.z += c2.z;
+                        }
                     }
                     hcur[s] = h;
+                    if (two) hcur[s2] = h2;
                 }
             }
         }
@@ -371,7 +468,7 @@ __global__ void __launch_bounds__(kWThreads) k_window_steps(const WindowConfig c
             s_mred[warp][2] = mz;
         }
         __syncthreads();
-        if (tid == 0 && buf.obs) {
+        if (tid < kNB && buf.obs) {
             double Mx = 0, My = 0, Mz = 0;
             for (int ww = 0; ww < kWThreads / 32; ++ww) {
                 Mx += s_mred[ww][0];
@@ -385,13 +482,21 @@ __global__ void __launch_bounds__(kWThreads) k_window_steps(const WindowConfig c
             x[MC_OBS_ABS_MZ] = fabs(Mz);
             x[MC_OBS_MPAR] = sqrt(Mx * Mx + My * My);
             x[MC_OBS_E] = buf.energy[r] / N;
-            obs_push_w(buf.obs[r], x);
+            obs_push_level(buf.obs[r], x, tid);
         }
     }
     if (tid == 0 && buf.obs) {
         buf.obs[r].accepted += n_acc;
         buf.obs[r].attempted += (long long)Sw;
     }
+}
+
+__global__ void k_build_wq(int L, const float *__restrict__ W32, float4 *wq) {
+    const int hq = L / 2 + 1, N = L * L;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= hq * hq) return;
+    const int g = (i / hq) * L + (i % hq);
+    wq[i] = make_float4(W32[g], W32[N + g], W32[2 * N + g], W32[3 * N + g]);
 }
 
 __global__ void k_spins_to_bf16(size_t count, const float *__restrict__ s, __nv_bfloat16 *hi, __nv_bfloat16 *lo) {
@@ -411,7 +516,7 @@ size_t window_smem_bytes(int L, int Sw) {
 }
 
 bool window_supported(int L, int l, int B) {
-    if (l < 2 || L % l) return false;
+    if (l < 2 || L % l || L % 2) return false;   // even L: 16-byte aligned spin rows
     const int C = L / l;
     if (C != 1 && C != 2 && C != 4) return false;
     if (B < 1 || (l * l) % B) return false;
@@ -431,6 +536,12 @@ cudaError_t launch_window_steps(const WindowConfig &c, const WindowBuffers &b, c
     else if (C == 4) { LAUNCH(4) }
     else return cudaErrorNotSupported;
 #undef LAUNCH
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_wq(int L, const float *W32, float4 *wq, cudaStream_t st) {
+    const int hq = L / 2 + 1;
+    k_build_wq<<<(hq * hq + 127) / 128, 128, 0, st>>>(L, W32, wq);
     return cudaGetLastError();
 }
 

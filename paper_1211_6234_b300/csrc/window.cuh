@@ -34,9 +34,11 @@ struct WindowBuffers {
     double *theta2;               // [R][N]
     float *trace;                 // optional
     const float *stale;           // see stale_mode
+    const float4 *wq;             // [(L/2+1)^2] W~ on the minimum-image quarter, (xx, xy, yy, zz)
 };
 
 size_t window_smem_bytes(int L, int Sw);
+cudaError_t launch_build_wq(int L, const float *W32, float4 *wq, cudaStream_t st);
 bool window_supported(int L, int l, int B);
 cudaError_t launch_window_steps(const WindowConfig &c, const WindowBuffers &b, cudaStream_t st);
 cudaError_t launch_spins_to_bf16(size_t count, const float *s, __nv_bfloat16 *hi, __nv_bfloat16 *lo,

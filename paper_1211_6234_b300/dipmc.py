@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libdipmc.so")
 MC_OK, MC_EINVAL, MC_ENOMEM, MC_ENOTREADY, MC_ETIMEOUT, MC_ECUDA, MC_ENOSYS = 0, -1, -2, -3, -4, -5, -6
 MC_NOBS = 5
 OBS_NAMES = ("abs_m", "m_z", "abs_m_z", "m_par", "e")
-MC_PATH_AUTO, MC_PATH_DIRECT, MC_PATH_WINDOW_F32, MC_PATH_TENSOR = 0, 1, 2, 3
+MC_PATH_AUTO, MC_PATH_DIRECT, MC_PATH_WINDOW_F32, MC_PATH_TENSOR, MC_PATH_FFT = 0, 1, 2, 3, 4
 MC_TRACE_W = 10
 
 # Every symbol include/dipmc.h declares.

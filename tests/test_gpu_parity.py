@@ -383,3 +383,112 @@ def test_tensor_path_observables_match_direct(dipmc):
         ea = np.sqrt(np.mean([o[nm]["err"] ** 2 for o in res[1]]) / R)
         eb = np.sqrt(np.mean([o[nm]["err"] ** 2 for o in res[3]]) / R)
         assert abs(a.mean() - b.mean()) < 4 * math.hypot(ea, eb) + 1e-9, (nm, a.mean(), b.mean(), ea, eb)
+
+
+# ---------------------------------------------------------------- FFT path
+@pytest.mark.parametrize("L,R", [(8, 1), (16, 3), (64, 2), (128, 1)])
+def test_fft_full_field_matches_oracle(dipmc, L, R):
+    s0 = inputs.random_spins(L, R, seed=40 + L)
+    A = 16
+    with dipmc.Lattice(L, L // 2, R, 3) as lat:
+        lat.precompute_W(A, True)
+        lat.set_field_path(dipmc.MC_PATH_FFT)
+        lat.init_spins(2, s0)
+        hg = lat.get_field().astype(np.float64)
+    Wo = oracle_W(L, A)
+    for r in range(R):
+        ho = orc.field(Wo, s0[r])
+        err = np.abs(hg[r] - ho).max() / np.abs(ho).max()
+        assert err < 1e-5, err
+
+
+def test_fft_full_field_L256_sampled_sites(dipmc):
+    """L = 256 (N = 65536): the FFT field of two replicas at sampled sites against
+    the oracle's direct sum at those sites (energy of the same state as a check of
+    all sites)."""
+    L, R, A = 256, 2, 8
+    s0 = inputs.random_spins(L, R, seed=256)
+    with dipmc.Lattice(L, 32, R, 3) as lat:
+        lat.precompute_W(A, True)
+        lat.init_spins(2, s0)
+        hg = lat.get_field().astype(np.float64)
+        Wg = lat.get_W()
+    Wo = orc.wtilde(L, A, True)
+    assert np.abs(Wg - Wo).max() / np.abs(Wo).max() < 1e-12
+    rng = np.random.default_rng(0)
+    sites = rng.integers(0, L * L, size=24)
+    hmax = 0.0
+    errs = []
+    for r in range(R):
+        for q in sites:
+            qy, qx = divmod(int(q), L)
+            # h_q = sum_m W~(q - m) s_m, by numpy over the whole lattice
+            dy = (qy - np.arange(L)[:, None]) % L
+            dx = (qx - np.arange(L)[None, :]) % L
+            xx, xy, yy, zz = Wo[0][dy, dx], Wo[1][dy, dx], Wo[2][dy, dx], Wo[3][dy, dx]
+            sx, sy, sz = s0[r]
+            ho = np.array([(xx * sx + xy * sy).sum(), (xy * sx + yy * sy).sum(), (zz * sz).sum()])
+            hmax = max(hmax, np.abs(ho).max())
+            errs.append(np.abs(hg[r, :, qy, qx] - ho).max())
+    assert max(errs) / hmax < 1e-5, (max(errs), hmax)
+
+
+FCASES = [
+    # L, l, R, schedule, nsweeps
+    (16, 8, 2, 0, 2),
+    (32, 8, 2, 0, 1),      # 16 simultaneous sites
+    (64, 16, 1, 1, 1),     # the paper's with-replacement schedule
+    (128, 64, 1, 0, 1),    # large lattice, 4 sites per sub-step
+]
+
+
+@pytest.mark.parametrize("case", FCASES, ids=[f"L{c[0]}_l{c[1]}_R{c[2]}_s{c[3]}" for c in FCASES])
+def test_fft_path_trace_matches_oracle(dipmc, case):
+    L, l, R, schedule, nsw = case
+    params = [(F32(1.0), F32(0.1), F32(0.8), F32(0.0), F32(0.6)),
+              (F32(0.7), F32(0.3), F32(0.5), F32(-0.2), F32(1.1))][:R]
+    seed = 500 + L + l
+    s0 = inputs.random_spins(L, R, seed=3 * L + l)
+    A = 16
+    with dipmc.Lattice(L, l, R, seed) as lat:
+        lat.precompute_W(A, True)
+        lat.set_field_path(dipmc.MC_PATH_FFT)
+        lat.set_schedule(schedule)
+        for r, prm in enumerate(params):
+            lat.set_params(*prm, replica=r)
+        lat.init_spins(2, s0)
+        tr = lat.sweep_trace(nsw)
+        sg = lat.get_spins().astype(np.float64)
+    W = oracle_W(L, A)
+    for r in range(R):
+        J, CD, K2, K4, T = params[r]
+        p = orc.params(L, l, J, CD, K2, K4, T, proposal=0, cone=0.5, schedule=schedule, seed=seed, replica=r)
+        o = orc.sweeps(p, W, s0[r], 0, nsw)
+        hmax = float(np.abs(o["h"]).max())
+        rep = compare_trace(tr[r], o, T, scale=1 + abs(J) + abs(K2) + abs(K4) + abs(CD) * hmax)
+        if rep.straddles == 0:
+            np.testing.assert_allclose(sg[r], o["s"], rtol=0, atol=1e-5)
+
+
+def test_fft_path_observables_match_direct(dipmc):
+    """The FFT and direct paths sample the same law (L = 16, pooled replicas)."""
+    L, l, R, nsw = 16, 8, 32, 400
+    res = {}
+    for path in (dipmc.MC_PATH_DIRECT, dipmc.MC_PATH_FFT):
+        with dipmc.Lattice(L, l, R, 31 if path == 1 else 32) as lat:
+            lat.precompute_W(64, True)
+            lat.set_field_path(path)
+            lat.set_params(F32(1.0), F32(0.1), F32(0.8), F32(0.0), F32(2.0))
+            lat.init_spins(1)
+            lat.sweep(100, 0)
+            lat.reset_observables()
+            lat.sweep(nsw, 1)
+            res[path] = [lat.observables(r) for r in range(R)]
+    for o in res[4]:
+        assert o["samples"] == nsw and o["attempted"] == nsw * L * L
+    for nm in ("abs_m", "e"):
+        a = np.array([o[nm]["mean"] for o in res[1]])
+        b = np.array([o[nm]["mean"] for o in res[4]])
+        ea = np.sqrt(np.mean([o[nm]["err"] ** 2 for o in res[1]]) / R)
+        eb = np.sqrt(np.mean([o[nm]["err"] ** 2 for o in res[4]]) / R)
+        assert abs(a.mean() - b.mean()) < 4 * math.hypot(ea, eb) + 1e-9, (nm, a.mean(), b.mean(), ea, eb)
