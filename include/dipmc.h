@@ -206,6 +206,24 @@ int mc_set_timing(mc_lattice *lat, int enable);
 /* Accumulated kernel times since the last mc_set_timing (synchronises the device). */
 int mc_get_timing(mc_lattice *lat, mc_timing *out);
 
+/*
+ * Update spacing for a stated error (Sec. 3.2).  The flip probability of the
+ * simultaneous update errs by about eps/T with eps = 2 C_D sum_{v != 0} |l v|^-3
+ * = 2 C_D 9.033621683 / l^3 (D = 2, summed over the update sublattice l Z^2 and
+ * its images).  Returns in *l_out the smallest l >= 2 dividing L with
+ * eps/T_min <= max_error (most simultaneous sites), or L if none is smaller.
+ */
+int mc_choose_spacing(int L, double C_D, double T_min, double max_error, int *l_out);
+
+/*
+ * Autotuner: times every supported field path (and, for the tensor path, window
+ * sizes of 32, 64 and 128 sub-steps) for nsweeps_trial sweeps on this handle,
+ * restoring the state after each trial (checkpoint/restore), and keeps the
+ * fastest.  The chosen path and window are returned (either pointer may be NULL).
+ * Synchronises the device.
+ */
+int mc_autotune(mc_lattice *lat, int nsweeps_trial, void *stream, int *path_out, int *window_out);
+
 /* Sweep counter (index of the next sweep; the RNG counters depend on it). */
 int mc_get_sweep_counter(mc_lattice *lat, uint64_t *out);
 

@@ -4,7 +4,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "fft_field.cuh"
@@ -84,6 +86,12 @@ struct mc_lattice {
     float *What = nullptr;    // [4][N] transform of W~ (FFT path), transposed layout
     float2 *fft_scratch = nullptr;
     bool what_ready = false;
+    // CUDA graphs of the multi-launch paths, keyed by (path, nsweeps, measure_every)
+    uint32_t *t_dev = nullptr;            // sweep counter at the start of the current call
+    cudaStream_t own = nullptr;           // capture/replay stream (joined to the caller's by events)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;
+    std::map<std::tuple<int, int, int>, int> seen;
     // kernel timing (events recorded around launches while enabled)
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> tev[MC_NKCLASS];
@@ -115,6 +123,18 @@ void free_all(mc_lattice *p) {
     cudaFree(p->wq);
     cudaFree(p->What);
     cudaFree(p->fft_scratch);
+    cudaFree(p->t_dev);
+    for (auto &g : p->graphs) cudaGraphExecDestroy(g.second);
+    p->graphs.clear();
+    if (p->own) cudaStreamDestroy(p->own);
+    if (p->ev_in) cudaEventDestroy(p->ev_in);
+    if (p->ev_out) cudaEventDestroy(p->ev_out);
+}
+
+void drop_graphs(mc_lattice *p) {
+    for (auto &g : p->graphs) cudaGraphExecDestroy(g.second);
+    p->graphs.clear();
+    p->seen.clear();
 }
 
 // Records an event pair around a launch when timing is on.
@@ -278,6 +298,7 @@ int run_windows(mc_lattice *p, int path, int nsweeps, int measure_every, float *
         if (e != cudaSuccess) return cuda_fail(e, "bf16 split of the spins");
     }
     WindowConfig c{};
+    c.t_dev = p->t_dev;
     c.L = p->L; c.l = p->l; c.R = p->R;
     c.key = key_of(p->seed);
     c.nsweeps_call = nsweeps;
@@ -307,7 +328,7 @@ int run_windows(mc_lattice *p, int path, int nsweeps, int measure_every, float *
         for (int w = 0; w < nwin; ++w) {
             cudaError_t e;
             if (tensor) {
-                e = launch_window_sites(p->L, p->l, c.key, c.t, p->schedule, w * B, B, p->wsite, st);
+                e = launch_window_sites(p->L, p->l, c.key, c.t, p->t_dev, it, p->schedule, w * B, B, p->wsite, st);
                 if (e != cudaSuccess) return cuda_fail(e, "window sites");
                 CKA(cudaMemsetAsync(p->H0, 0, sizeof(float) * (size_t)p->R * 3 * Sw, st));
                 {
@@ -368,6 +389,7 @@ int run_fft(mc_lattice *p, int nsweeps, int measure_every, float *trace, cudaStr
     if (rc) return rc;
     const int ll = p->l * p->l;
     FftStepConfig c{};
+    c.t_dev = p->t_dev;
     c.L = p->L; c.l = p->l; c.R = p->R;
     c.key = key_of(p->seed);
     c.nsweeps_call = nsweeps;
@@ -407,6 +429,54 @@ int run_fft(mc_lattice *p, int nsweeps, int measure_every, float *trace, cudaStr
     if (e != cudaSuccess) return cuda_fail(e, "acceptance counters");
     // the FFT path does not track the energy between measurements
     p->energy_valid = measured_last;
+    return MC_OK;
+}
+
+int run_path(mc_lattice *p, int path, int nsweeps, int measure_every, float *trace, cudaStream_t st) {
+    return path == MC_PATH_FFT ? run_fft(p, nsweeps, measure_every, trace, st)
+                               : run_windows(p, path, nsweeps, measure_every, trace, st);
+}
+
+// The windowed and FFT paths launch several kernels per window or sub-step.  The
+// first call of a given (path, nsweeps, measure_every) runs them directly; later
+// calls replay a CUDA graph of the whole call, captured on a library stream that
+// is joined to the caller's stream by events.  Kernels read the sweep counter
+// from t_dev, set before each call, so one graph serves every call of its shape.
+int run_multi(mc_lattice *p, int path, int nsweeps, int measure_every, float *trace, cudaStream_t st) {
+    if (!p->t_dev) CKA(cudaMalloc(&p->t_dev, sizeof(uint32_t)));
+    cudaError_t e = launch_set_u32(p->t_dev, (uint32_t)p->t, st);
+    if (e != cudaSuccess) return cuda_fail(e, "sweep counter");
+    const bool graphable = !trace && !p->timing;
+    const auto key = std::make_tuple(path, nsweeps, measure_every);
+    if (!graphable || p->seen[key]++ == 0) return run_path(p, path, nsweeps, measure_every, trace, st);
+    if (!p->own) {
+        CKA(cudaStreamCreateWithFlags(&p->own, cudaStreamNonBlocking));
+        CKA(cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming));
+        CKA(cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming));
+    }
+    auto it = p->graphs.find(key);
+    if (it == p->graphs.end()) {
+        cudaGraph_t g = nullptr;
+        CKA(cudaStreamBeginCapture(p->own, cudaStreamCaptureModeThreadLocal));
+        int rc = run_path(p, path, nsweeps, measure_every, nullptr, p->own);
+        cudaError_t ec = cudaStreamEndCapture(p->own, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (ec != cudaSuccess) return cuda_fail(ec, "graph capture");
+        cudaGraphExec_t ex = nullptr;
+        ec = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (ec != cudaSuccess) return cuda_fail(ec, "graph instantiate");
+        it = p->graphs.emplace(key, ex).first;
+    }
+    CKA(cudaEventRecord(p->ev_in, st));
+    CKA(cudaStreamWaitEvent(p->own, p->ev_in, 0));
+    CKA(cudaGraphLaunch(it->second, p->own));
+    CKA(cudaEventRecord(p->ev_out, p->own));
+    CKA(cudaStreamWaitEvent(st, p->ev_out, 0));
+    if (path == MC_PATH_FFT) p->energy_valid = measure_every > 0 && nsweeps % measure_every == 0;
     return MC_OK;
 }
 
@@ -451,11 +521,8 @@ int run_sweeps(mc_lattice *p, int nsweeps, int measure_every, float *trace, cuda
         if (e == cudaErrorNotSupported)
             return fail(MC_ENOSYS, "no field path supports L=%d l=%d (path %d)", p->L, p->l, p->path);
         if (e != cudaSuccess) return cuda_fail(e, "sweep kernel launch");
-    } else if (path == MC_PATH_FFT) {
-        int rc = run_fft(p, nsweeps, measure_every, trace, st);
-        if (rc) return rc;
     } else {
-        int rc = run_windows(p, path, nsweeps, measure_every, trace, st);
+        int rc = run_multi(p, path, nsweeps, measure_every, trace, st);
         if (rc) return rc;
     }
     p->t += (uint64_t)nsweeps;
@@ -561,6 +628,7 @@ int mc_set_params(mc_lattice *p, int replica, double J, double C_D, double K2, d
 }
 
 int mc_set_proposal(mc_lattice *p, int kind, double cone) {
+    if (p) drop_graphs(p);
     int rc = check(p);
     if (rc) return rc;
     if (kind != 0 && kind != 1) return fail(MC_EINVAL, "proposal kind must be 0 or 1");
@@ -571,6 +639,7 @@ int mc_set_proposal(mc_lattice *p, int kind, double cone) {
 }
 
 int mc_set_schedule(mc_lattice *p, int kind) {
+    if (p) drop_graphs(p);
     int rc = check(p);
     if (rc) return rc;
     if (kind != 0 && kind != 1) return fail(MC_EINVAL, "schedule kind must be 0 or 1");
@@ -579,6 +648,7 @@ int mc_set_schedule(mc_lattice *p, int kind) {
 }
 
 int mc_set_field_path(mc_lattice *p, int path) {
+    if (p) drop_graphs(p);
     int rc = check(p);
     if (rc) return rc;
     if (path < MC_PATH_AUTO || path > MC_PATH_FFT) return fail(MC_EINVAL, "unknown field path %d", path);
@@ -589,6 +659,7 @@ int mc_set_field_path(mc_lattice *p, int path) {
 }
 
 int mc_set_window(mc_lattice *p, int B) {
+    if (p) drop_graphs(p);
     int rc = check(p);
     if (rc) return rc;
     if (B < 0 || (B > 0 && (p->l * p->l) % B)) return fail(MC_EINVAL, "window %d must divide l^2 = %d", B, p->l * p->l);
@@ -618,6 +689,7 @@ int mc_init_spins(mc_lattice *p, int mode, const float *user) {
 }
 
 int mc_precompute_W(mc_lattice *p, int A, int tail) {
+    if (p) drop_graphs(p);
     int rc = check(p);
     if (rc) return rc;
     if (A < 0 || A > 4096) return fail(MC_EINVAL, "image_cutoff %d outside [0, 4096]", A);
@@ -783,6 +855,80 @@ int mc_get_timing(mc_lattice *p, mc_timing *out) {
             out->launches[k] += 1;
         }
     }
+    return MC_OK;
+}
+
+int mc_choose_spacing(int L, double C_D, double T_min, double max_error, int *l_out) {
+    if (!l_out || L < 2 || !(T_min > 0.0) || !(max_error > 0.0)) return fail(MC_EINVAL, "bad arguments");
+    constexpr double kLatticeSum = 9.033621683;   // sum over Z^2 \ 0 of |v|^-3 = 4 zeta(3/2) beta(3/2)
+    for (int l = 2; l <= L; ++l) {
+        if (L % l) continue;
+        const double eps = 2.0 * std::fabs(C_D) * kLatticeSum / ((double)l * l * l);
+        if (eps / T_min <= max_error) {
+            *l_out = l;
+            return MC_OK;
+        }
+    }
+    *l_out = L;
+    return MC_OK;
+}
+
+int mc_autotune(mc_lattice *p, int nsweeps_trial, void *stream, int *path_out, int *window_out) {
+    int rc = check(p);
+    if (rc) return rc;
+    if (nsweeps_trial < 1) return fail(MC_EINVAL, "nsweeps_trial must be >= 1");
+    if (!p->W_ready) return fail(MC_ENOTREADY, "mc_precompute_W has not been called");
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t len = 0;
+    rc = mc_checkpoint(p, nullptr, &len);
+    if (rc) return rc;
+    std::vector<char> saved(len);
+    rc = mc_checkpoint(p, saved.data(), &len);
+    if (rc) return rc;
+    const int old_path = p->path, old_B = p->window_B;
+    struct Cand { int path, B; };
+    std::vector<Cand> cands;
+    if (path_supported(p, MC_PATH_DIRECT)) cands.push_back({MC_PATH_DIRECT, 0});
+    for (int B : {32, 64, 128}) {
+        p->window_B = B;
+        if ((p->l * p->l) % B == 0 && path_supported(p, MC_PATH_TENSOR)) cands.push_back({MC_PATH_TENSOR, B});
+    }
+    p->window_B = old_B;
+    if (path_supported(p, MC_PATH_FFT)) cands.push_back({MC_PATH_FFT, 0});
+    if (cands.empty()) return fail(MC_ENOSYS, "no field path supports L=%d l=%d", p->L, p->l);
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    float best = 1e30f;
+    Cand win = cands[0];
+    for (const Cand &c : cands) {
+        drop_graphs(p);
+        p->path = c.path;
+        p->window_B = c.B;
+        rc = run_sweeps(p, 1, 0, nullptr, st);                 // warm-up (allocations, attributes)
+        if (!rc) {
+            CK(cudaEventRecord(a, st));
+            rc = run_sweeps(p, nsweeps_trial, 0, nullptr, st);
+            CK(cudaEventRecord(b, st));
+        }
+        CK(cudaStreamSynchronize(st));
+        float ms = 0.f;
+        if (!rc) CK(cudaEventElapsedTime(&ms, a, b));
+        if (!rc && ms < best) {
+            best = ms;
+            win = c;
+        }
+        int r2 = mc_restore(p, saved.data(), len);
+        if (r2) return r2;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    drop_graphs(p);
+    (void)old_path;
+    p->path = win.path;
+    p->window_B = win.B;
+    if (path_out) *path_out = win.path;
+    if (window_out) *window_out = win.B;
     return MC_OK;
 }
 

@@ -200,7 +200,7 @@ __global__ void k_fft_update(const FftStepConfig cfg, const FftStepBuffers buf) 
     __syncthreads();
     int accept = 0;
     if (d < n) {
-        const uint32_t t = cfg.t, k = (uint32_t)cfg.k;
+        const uint32_t t = cfg.t_dev ? *cfg.t_dev + (uint32_t)cfg.it : cfg.t, k = (uint32_t)cfg.k;
         uint32_t v;
         if (cfg.schedule == 0) {
             const uint4 rk = philox(make_uint4(t, 0u, 0u, kTagPerm), cfg.key);

@@ -8,7 +8,8 @@ namespace dipmc {
 struct FftStepConfig {
     int L, l, R;
     uint2 key;
-    uint32_t t;          // sweep counter
+    uint32_t t;          // sweep counter (when t_dev is null)
+    const uint32_t *t_dev;  // device sweep counter at the start of the call (graph replays)
     int k;               // sub-step within the sweep
     int it;              // sweep index within the call (trace position)
     int nsweeps_call;    // sweeps of the call (trace stride)

@@ -281,7 +281,9 @@ __global__ void k_build_wsh(int L, const double *__restrict__ W64, __nv_bfloat16
 }
 
 // Window sites of sweep t, window w (same schedule as the sweep kernels).
-__global__ void k_window_sites(int L, int l, uint2 key, uint32_t t, int schedule, int k0, int B, int *wsite) {
+__global__ void k_window_sites(int L, int l, uint2 key, uint32_t t_host, const uint32_t *t_dev, int it, int schedule,
+                               int k0, int B, int *wsite) {
+    const uint32_t t = t_dev ? *t_dev + (uint32_t)it : t_host;
     const int n = (L / l) * (L / l), C = L / l, ll = l * l;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= B * n) return;
@@ -317,10 +319,10 @@ cudaError_t launch_build_wsh(int L, const double *W64, __nv_bfloat16 *wsh, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t launch_window_sites(int L, int l, uint2 key, uint32_t t, int schedule, int k0, int B, int *wsite,
-                                cudaStream_t st) {
+cudaError_t launch_window_sites(int L, int l, uint2 key, uint32_t t, const uint32_t *t_dev, int it, int schedule,
+                                int k0, int B, int *wsite, cudaStream_t st) {
     const int Sw = B * (L / l) * (L / l);
-    k_window_sites<<<(Sw + 127) / 128, 128, 0, st>>>(L, l, key, t, schedule, k0, B, wsite);
+    k_window_sites<<<(Sw + 127) / 128, 128, 0, st>>>(L, l, key, t, t_dev, it, schedule, k0, B, wsite);
     return cudaGetLastError();
 }
 

@@ -28,8 +28,8 @@ size_t tc_wsh_elems(int L);
 bool tc_supported(int L, int l, int B);
 size_t tc_smem_bytes();
 cudaError_t launch_build_wsh(int L, const double *W64, __nv_bfloat16 *wsh, cudaStream_t st);
-cudaError_t launch_window_sites(int L, int l, uint2 key, uint32_t t, int schedule, int k0, int B, int *wsite,
-                                cudaStream_t st);
+cudaError_t launch_window_sites(int L, int l, uint2 key, uint32_t t, const uint32_t *t_dev, int it, int schedule,
+                                int k0, int B, int *wsite, cudaStream_t st);
 // Fills units[] for a window of Sw sites and R replicas; returns the number of
 // units (CTAs) or -1 if max_units is too small.
 int tc_plan(int L, int Sw, int R, int nsm, TcUnit *units, int max_units, int *NT, int *tmem_cols);

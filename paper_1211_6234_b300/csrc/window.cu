@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
 
     const RepParams P = buf.params[r];
     const uint2 key = cfg.key;
-    const uint32_t t = cfg.t;
+    const uint32_t t = cfg.t_dev ? *cfg.t_dev + (uint32_t)cfg.it : cfg.t;
     const int k0 = cfg.w * B;
     const float W0xx = __ldg(buf.W32), W0xy = __ldg(buf.W32 + N), W0yy = __ldg(buf.W32 + 2 * N), W0zz = __ldg(buf.W32 + 3 * N);
 
@@ -536,6 +536,13 @@ cudaError_t launch_window_steps(const WindowConfig &c, const WindowBuffers &b, c
     else if (C == 4) { LAUNCH(4) }
     else return cudaErrorNotSupported;
 #undef LAUNCH
+    return cudaGetLastError();
+}
+
+__global__ void k_set_u32(uint32_t *dst, uint32_t v) { *dst = v; }
+
+cudaError_t launch_set_u32(uint32_t *dst, uint32_t v, cudaStream_t st) {
+    k_set_u32<<<1, 1, 0, st>>>(dst, v);
     return cudaGetLastError();
 }
 

@@ -10,7 +10,8 @@ namespace dipmc {
 struct WindowConfig {
     int L, l, R;
     uint2 key;
-    uint32_t t;          // sweep counter of this sweep
+    uint32_t t;          // sweep counter of this sweep (when t_dev is null)
+    const uint32_t *t_dev;  // device sweep counter at the start of the call (graph replays)
     int it;              // index of this sweep within the call (trace position)
     int nsweeps_call;    // sweeps of the call (trace stride)
     int w;               // window index within the sweep
@@ -39,6 +40,7 @@ struct WindowBuffers {
 
 size_t window_smem_bytes(int L, int Sw);
 cudaError_t launch_build_wq(int L, const float *W32, float4 *wq, cudaStream_t st);
+cudaError_t launch_set_u32(uint32_t *dst, uint32_t v, cudaStream_t st);
 bool window_supported(int L, int l, int B);
 cudaError_t launch_window_steps(const WindowConfig &c, const WindowBuffers &b, cudaStream_t st);
 cudaError_t launch_spins_to_bf16(size_t count, const float *s, __nv_bfloat16 *hi, __nv_bfloat16 *lo,

@@ -29,6 +29,7 @@ ABI_SYMBOLS = (
     "mc_precompute_W", "mc_sweep", "mc_sweep_trace", "mc_observables", "mc_reset_observables",
     "mc_get_spins", "mc_get_field", "mc_get_W", "mc_energy", "mc_get_sweep_counter",
     "mc_checkpoint", "mc_restore", "mc_energy_noalloc", "mc_set_timing", "mc_get_timing",
+    "mc_choose_spacing", "mc_autotune",
 )
 KERNEL_CLASSES = ("sweep_direct", "tc_field", "window_steps", "full_field")
 
@@ -96,6 +97,8 @@ def _load():
         "mc_restore": ([vp, vp, C.c_size_t], i32),
         "mc_energy_noalloc": ([i32, i32, vp, vp, vp, vp, vp], i32),
         "mc_set_timing": ([vp, i32], i32),
+        "mc_choose_spacing": ([i32, f64, f64, f64, C.POINTER(i32)], i32),
+        "mc_autotune": ([vp, i32, vp, C.POINTER(i32), C.POINTER(i32)], i32),
         "mc_get_timing": ([vp, C.POINTER(mc_timing)], i32),
     }
     for name, (args, res) in sig.items():
@@ -134,6 +137,13 @@ def energy_noalloc(L: int, R: int, W32, spins, couplings, energy, stream=None):
     _ck(_lib.mc_energy_noalloc(L, R, C.c_void_p(W32.data_ptr()), C.c_void_p(spins.data_ptr()),
                                C.c_void_p(couplings.data_ptr()), C.c_void_p(energy.data_ptr()),
                                _stream_ptr(stream)))
+
+
+def choose_spacing(L: int, C_D: float, T_min: float, max_error: float) -> int:
+    """Smallest update spacing l | L meeting the Sec. 3.2 error estimate (mc_choose_spacing)."""
+    v = C.c_int(0)
+    _ck(_lib.mc_choose_spacing(L, C_D, T_min, max_error, C.byref(v)))
+    return v.value
 
 
 def _np_ptr(a: np.ndarray):
@@ -252,6 +262,13 @@ class Lattice:
         t = mc_timing()
         _ck(_lib.mc_get_timing(self.h, C.byref(t)))
         return {nm: {"launches": t.launches[i], "ms": t.ms[i]} for i, nm in enumerate(KERNEL_CLASSES)}
+
+    def autotune(self, nsweeps_trial=2, stream=None):
+        """Time the supported paths on a copy of the state; keep the fastest.
+        Returns (path, window)."""
+        pth, win = C.c_int(0), C.c_int(0)
+        _ck(_lib.mc_autotune(self.h, nsweeps_trial, _stream_ptr(stream), C.byref(pth), C.byref(win)))
+        return pth.value, win.value
 
     def sweep_counter(self) -> int:
         v = C.c_uint64()

@@ -2,6 +2,7 @@
 every entry point include/dipmc.h declares, and argument validation that
 precedes any CUDA call reports the documented error codes."""
 import ctypes as C
+import math
 import os
 import re
 import subprocess
@@ -57,3 +58,21 @@ def test_binding_raises_instead_of_falling_back():
     with pytest.raises(dipmc.McError) as e:
         dipmc.Lattice(16, 5, 1, 1)
     assert e.value.code == dipmc.MC_EINVAL
+
+
+@pytest.mark.parametrize("L,CD,T,err", [(64, 0.1, 0.2, 1e-3), (64, 0.1, 0.6, 1e-3), (256, 0.1, 0.3, 1e-3),
+                                        (256, 0.2, 0.3, 1e-4), (48, 0.1, 0.5, 1e-3), (16, 0.1, 0.6, 1e-2)])
+def test_choose_spacing_against_oracle_error_estimate(L, CD, T, err):
+    """The spacing chooser (host logic of the library) against the oracle's own
+    evaluation of the Sec. 3.2 error estimate summed over the update sublattice:
+    the chosen l meets the bound and every smaller divisor of L violates it."""
+    from oracle import oracle as orc
+    from paper_1211_6234_b300 import dipmc
+    l = dipmc.choose_spacing(L, CD, T, err)
+    assert L % l == 0 and l >= 2
+    tail = lambda ll: 2 * CD * 4 * math.sqrt(2) / ((64 * (L // ll) + 0.5) * ll**3 * T)  # noqa: E731
+    if l < L:
+        assert orc.eps_total(L, l, CD, T, 1, 64) + tail(l) <= err * (1 + 1e-9)
+    for m in range(2, l):
+        if L % m == 0:
+            assert orc.eps_total(L, m, CD, T, 1, 64) + tail(m) > err

@@ -492,3 +492,41 @@ def test_fft_path_observables_match_direct(dipmc):
         ea = np.sqrt(np.mean([o[nm]["err"] ** 2 for o in res[1]]) / R)
         eb = np.sqrt(np.mean([o[nm]["err"] ** 2 for o in res[4]]) / R)
         assert abs(a.mean() - b.mean()) < 4 * math.hypot(ea, eb) + 1e-9, (nm, a.mean(), b.mean(), ea, eb)
+
+
+# ---------------------------------------------------------------- graphs and autotuning
+@pytest.mark.parametrize("path", [3, 4], ids=["tensor", "fft"])
+def test_graph_replay_is_bit_identical(dipmc, path):
+    """Repeated calls of the windowed / FFT paths replay a captured CUDA graph; three
+    calls of 2 sweeps must equal one direct call of 6 sweeps bit for bit."""
+    L, l, R = 32, 16, 8
+    s0 = inputs.random_spins(L, R, seed=9)
+    out = []
+    for calls in ((2, 2, 2), (6,)):
+        with dipmc.Lattice(L, l, R, 77) as lat:
+            lat.precompute_W(16, True)
+            lat.set_field_path(path)
+            lat.init_spins(2, s0)
+            for c in calls:
+                lat.sweep(c, 1)
+            out.append((lat.get_spins(), lat.observables(3), lat.sweep_counter()))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][2] == out[1][2] == 6
+    assert out[0][1]["samples"] == out[1][1]["samples"] == 6
+    assert out[0][1]["abs_m"]["mean"] == out[1][1]["abs_m"]["mean"]
+
+
+def test_autotune_keeps_state_and_picks_a_path(dipmc):
+    L, l, R = 64, 32, 64
+    s0 = inputs.random_spins(L, R, seed=4)
+    with dipmc.Lattice(L, l, R, 5) as lat:
+        lat.precompute_W(16, True)
+        lat.init_spins(2, s0)
+        lat.sweep(1, 0)
+        before = lat.get_spins()
+        t0 = lat.sweep_counter()
+        path, win = lat.autotune(1)
+        assert path in (dipmc.MC_PATH_DIRECT, dipmc.MC_PATH_TENSOR, dipmc.MC_PATH_FFT)
+        assert np.array_equal(lat.get_spins(), before) and lat.sweep_counter() == t0
+        lat.sweep(2, 1)
+        assert lat.observables(0)["samples"] == 2
