@@ -189,6 +189,60 @@ def cpu_baseline_sample(seconds_target=12.0):
                       f"{dt:.1f} s"}
 
 
+def serving_leg(dipmc, n_req, scale, quantum, budget_gb, rate_hz, timeout_s=240.0):
+    """Continuous batching of a Poisson stream of simulation requests (L uniform
+    over {32, 48, 64, 96, 128, 256}, T ~ U[0.2, 1.2], K2 ~ U[0.5, 1], K4 ~
+    U[-0.3, 0.3], C_D = 0.1, log-uniform sweeps scaled by `scale`, l chosen at
+    flip-probability error 1e-3).  Requests are submitted at their arrival times;
+    latency = completion (results on the host) - arrival."""
+    reqs = inputs.request_stream(n_req, seed=7, rate_hz=rate_hz, sweeps_scale=scale)
+    srv = dipmc.Server(hbm_budget_bytes=int(budget_gb * (1 << 30)), quantum_sweeps=quantum, max_error=1e-3)
+    # untimed warm-up: W~ of every L and one handle per L, one sweep each
+    warm = [srv.submit(L=Lw, T=0.6, sweeps=1, seed=99 + Lw, l=0) for Lw in (32, 48, 64, 96, 128, 256)]
+    srv.run_until_done(warm, timeout_s=120)
+    for rid in warm:
+        srv.release(rid)
+    lat, upd, failed = [], 0, 0
+    reasons = {}
+    pending = {}
+    i = 0
+    t0 = time.perf_counter()
+    while i < len(reqs) or pending:
+        now = time.perf_counter() - t0
+        if now > timeout_s:
+            break
+        while i < len(reqs) and reqs[i]["arrival"] <= now:
+            r = reqs[i]
+            rid = srv.submit(L=r["L"], T=r["T"], sweeps=r["sweeps"], seed=r["seed"], J=r["J"], C_D=r["CD"],
+                             K2=r["K2"], K4=r["K4"], l=0, measure_every=1)
+            pending[rid] = r
+            i += 1
+        srv.step()
+        for rid in list(pending):
+            st, _ = srv.poll(rid)
+            if st == dipmc.MC_REQ_DONE or st == dipmc.MC_REQ_FAILED:
+                r = pending.pop(rid)
+                if st == dipmc.MC_REQ_DONE:
+                    lat.append(time.perf_counter() - t0 - r["arrival"])
+                    upd += r["L"] * r["L"] * r["sweeps"]
+                else:
+                    failed += 1
+                    inf = srv.info(rid)
+                    why = f"L={r['L']} l={inf['l']}: {inf['error'][:80]}"
+                    reasons[why] = reasons.get(why, 0) + 1
+                srv.release(rid)
+    span = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat.sort()
+    q = (lambda f: lat[min(len(lat) - 1, int(f * len(lat)))] if lat else None)  # noqa: E731
+    return {"requests": len(reqs), "completed": len(lat), "failed": failed, "unfinished": len(pending) + len(reqs) - i,
+            "site_updates_per_s": upd / span, "makespan_s": span, "p50_latency_s": q(0.50), "p99_latency_s": q(0.99),
+            "arrival_rate_hz": rate_hz, "sweeps": f"log-uniform [1e3, 1e5] x {scale}", "quantum_sweeps": quantum,
+            "hbm_budget_gb": budget_gb, "packs": st["packs"], "lone_handles": st["lone"],
+            "site_updates": upd, "failure_reasons": reasons}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -201,6 +255,12 @@ def main():
     ap.add_argument("--window", type=int, default=0, help="sub-steps per window (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--serve-only", action="store_true", help="run only the serving leg")
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-scale", type=float, default=0.002, help="factor on the requests' sweep counts")
+    ap.add_argument("--serve-quantum", type=int, default=8)
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate, requests/s")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -217,6 +277,11 @@ def main():
         torch.cuda.set_device(0)
     dev = torch.cuda.current_device()
     from paper_1211_6234_b300 import dipmc
+    if args.serve_only:
+        if rank == 0:
+            print(json.dumps({"serving": serving_leg(dipmc, args.serve_requests, args.serve_scale,
+                                                     args.serve_quantum, 64.0, args.serve_rate)}), flush=True)
+        return
 
     lad = ladder()
     path_id = {"direct": dipmc.MC_PATH_DIRECT, "window": dipmc.MC_PATH_WINDOW_F32,
@@ -368,6 +433,11 @@ def main():
                  "batched_over_plain": value / ws / pv}
         p1.close()
 
+    serving = None
+    if rank == 0 and not args.no_serve:
+        serving = serving_leg(dipmc, args.serve_requests, args.serve_scale, args.serve_quantum, 64.0,
+                              args.serve_rate)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample()
@@ -390,6 +460,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
             "plain": plain,
+            "serving": serving,
             "gpu_launches": gpu_launches,
             "clocks": clk,
             "wall_s_timed": wall,

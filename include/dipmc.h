@@ -263,6 +263,89 @@ int mc_restore(mc_lattice *lat, const void *buf, size_t len);
 int mc_energy_noalloc(int L, int R, const float *W32, const float *spins, const float *couplings,
                       double *energy, void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous batching of simulation requests.  The paper runs one    */
+/* lattice at a time and has no counterpart; a request is one run of Sec. 4's  */
+/* model (L, couplings, temperature, sweeps) with its own seed.                */
+/* ------------------------------------------------------------------------ */
+#define MC_REQ_QUEUED 0
+#define MC_REQ_RUNNING 1
+#define MC_REQ_DONE 2
+#define MC_REQ_FAILED 3
+#define MC_REQ_RELEASED 4
+
+typedef struct mc_request {
+    int L, l;                /* l = 0: chosen by mc_choose_spacing at the server's error bound */
+    int replicas;            /* < 1 means 1; replica r draws the counters of replica r of a lone handle */
+    double J, C_D, K2, K4, T;
+    int64_t sweeps;
+    int measure_every;       /* observables every this many sweeps (0 = none); results match a lone
+                                run whose mc_sweep calls are multiples of it */
+    uint64_t seed;
+    int init_mode;           /* 0 random on S^2 from the seed, 1 all +z (as mc_init_spins) */
+    int image_cutoff;        /* A of mc_precompute_W; 0 = 64 (tail correction on) */
+    int proposal;            /* 0 cap of half-angle cone (0 = 0.5 rad), 1 uniform on S^2 */
+    double cone;
+} mc_request;
+
+typedef struct mc_request_info {
+    int state, l, path;
+    int packed;                         /* 1 = shares packed launches with other requests */
+    int64_t sweeps_done;
+    double t_submit, t_admit, t_done;   /* seconds on the host's monotonic clock */
+    size_t bytes;                       /* device bytes attributed to it while admitted */
+    char error[160];
+} mc_request_info;
+
+typedef struct mc_server_stats {
+    int queued, running, done, failed;
+    int packs, lone;                    /* device handles held: packs and lone handles */
+    int64_t completed;
+    size_t bytes_in_use, budget;
+} mc_server_stats;
+
+typedef struct mc_server mc_server;
+
+/* Device bytes of a handle of `replicas` lattices L x L at spacing l on the path
+ * that (L, l) resolves to automatically (the server's admission estimate). */
+int mc_footprint(int L, int l, int replicas, size_t *bytes);
+
+/*
+ * Requests whose (L, l) the direct path serves share packed launches: one handle
+ * whose replica slots belong to different requests, each slot with its own seed,
+ * sweep counter and sweep budget, so that a request's result is bit-identical to
+ * the same request run alone on a lone handle (mc_create_lattice with its seed,
+ * mc_set_params, mc_precompute_W(A, 1), mc_init_spins, mc_sweep).  Other requests
+ * get a lone handle of their own.  Handles run on separate streams and overlap.
+ *
+ * Requests are admitted in arrival order while the device bytes of the handles
+ * they need fit hbm_budget_bytes and fewer than max_active are running; a packed
+ * request waits only for free slots.  Sweeps are issued in quanta of at most
+ * quantum_sweeps; a request joins or leaves a pack between quanta.  max_error is
+ * the flip-probability error bound (Sec. 3.2) used when a request leaves l = 0.
+ * The server is single-threaded: call every function from one host thread.
+ */
+int mc_server_create(size_t hbm_budget_bytes, int max_active, int quantum_sweeps, double max_error,
+                     mc_server **out);
+/* Queue a request (copied).  MC_EINVAL for bad fields, MC_ENOMEM if it can never fit. */
+int mc_server_submit(mc_server *srv, const mc_request *req, uint64_t *id);
+/* One scheduling pass: retire finished launches (finished requests are read back
+ * to host memory and free their device memory), admit waiting requests, launch
+ * the next quantum everywhere idle.  Does not wait for the GPU except to read the
+ * results of a request that just finished; call it repeatedly. */
+int mc_server_step(mc_server *srv);
+int mc_server_poll(mc_server *srv, uint64_t id, int *state, int64_t *sweeps_done);
+int mc_server_request_info(mc_server *srv, uint64_t id, mc_request_info *out);
+/* Observables of one replica of a DONE request (as mc_observables).  MC_ENOTREADY otherwise. */
+int mc_server_collect(mc_server *srv, uint64_t id, int replica, mc_obs *out);
+/* Final spins of a DONE request, [replicas][3][L][L] FP32, to a host pointer. */
+int mc_server_get_spins(mc_server *srv, uint64_t id, float *dst_host);
+/* Drop a request in any state: a queued or running one stops (its slots are
+ * refilled only behind the launch that still carries it); stored results are freed. */
+int mc_server_release(mc_server *srv, uint64_t id);
+int mc_server_get_stats(mc_server *srv, mc_server_stats *out);
+int mc_server_destroy(mc_server *srv);
+
 #ifdef __cplusplus
 }
 #endif

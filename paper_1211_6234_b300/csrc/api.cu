@@ -1,5 +1,6 @@
 // api.cu -- the C ABI of libdipmc (declared in include/dipmc.h): handle
 // lifetime, argument validation, device buffers and dispatch to the kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -95,6 +96,12 @@ struct mc_lattice {
     // kernel timing (events recorded around launches while enabled)
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> tev[MC_NKCLASS];
+    // packed launches (serving): per-slot stream state, host shadow and pinned staging
+    bool packed = false;
+    SlotState *slots_dev = nullptr, *slots_pin = nullptr;
+    RepParams *params_pin = nullptr;
+    std::vector<SlotState> slots_host;
+    cudaEvent_t slots_copied = nullptr;
 
     int N() const { return L * L; }
     int n() const { return (L / l) * (L / l); }
@@ -129,6 +136,10 @@ void free_all(mc_lattice *p) {
     if (p->own) cudaStreamDestroy(p->own);
     if (p->ev_in) cudaEventDestroy(p->ev_in);
     if (p->ev_out) cudaEventDestroy(p->ev_out);
+    cudaFree(p->slots_dev);
+    if (p->slots_pin) cudaFreeHost(p->slots_pin);
+    if (p->params_pin) cudaFreeHost(p->params_pin);
+    if (p->slots_copied) cudaEventDestroy(p->slots_copied);
 }
 
 void drop_graphs(mc_lattice *p) {
@@ -399,6 +410,7 @@ int run_fft(mc_lattice *p, int nsweeps, int measure_every, float *trace, cudaStr
     FftStepBuffers b{};
     b.W32 = p->W32; b.spins = p->spins; b.field = p->field; b.params = p->dparams; b.obs = p->obs;
     b.trace = trace;
+    b.slots = p->packed ? p->slots_dev : nullptr;
     bool measured_last = false;
     for (int it = 0; it < nsweeps; ++it) {
         c.t = (uint32_t)(p->t + (uint64_t)it);
@@ -417,18 +429,20 @@ int run_fft(mc_lattice *p, int nsweeps, int measure_every, float *trace, cudaStr
             }
             if (e != cudaSuccess) return cuda_fail(e, "FFT update kernel");
         }
-        measured_last = measure_every > 0 && ((it + 1) % measure_every) == 0;
+        // a pack measures every sweep; each slot decides from its own sweep count
+        measured_last = measure_every > 0 && (b.slots || ((it + 1) % measure_every) == 0);
         if (measured_last) {
             cudaError_t e = launch_fft_field(p->L, p->R, p->spins, p->What, p->fft_scratch, p->field, st);
             if (e != cudaSuccess) return cuda_fail(e, "FFT field");
-            e = launch_fft_observe(p->L, p->R, p->spins, p->field, p->dparams, p->energy, p->obs, p->theta2, st);
+            e = launch_fft_observe(p->L, p->R, p->spins, p->field, p->dparams, p->energy, p->obs, p->theta2,
+                                   b.slots, it, measure_every, st);
             if (e != cudaSuccess) return cuda_fail(e, "observables");
         }
     }
-    cudaError_t e = launch_add_attempted(p->obs, p->R, (long long)nsweeps * p->N(), st);
+    cudaError_t e = launch_add_attempted(p->obs, p->R, (long long)nsweeps * p->N(), b.slots, nsweeps, p->N(), st);
     if (e != cudaSuccess) return cuda_fail(e, "acceptance counters");
     // the FFT path does not track the energy between measurements
-    p->energy_valid = measured_last;
+    p->energy_valid = p->packed || measured_last;
     return MC_OK;
 }
 
@@ -448,7 +462,9 @@ int run_multi(mc_lattice *p, int path, int nsweeps, int measure_every, float *tr
     if (e != cudaSuccess) return cuda_fail(e, "sweep counter");
     const bool graphable = !trace && !p->timing;
     const auto key = std::make_tuple(path, nsweeps, measure_every);
-    if (!graphable || p->seen[key]++ == 0) return run_path(p, path, nsweeps, measure_every, trace, st);
+    // a pack repeats its quantum: capture at once; a lone handle captures a
+    // shape on its second call
+    if (!graphable || (p->seen[key]++ == 0 && !p->packed)) return run_path(p, path, nsweeps, measure_every, trace, st);
     if (!p->own) {
         CKA(cudaStreamCreateWithFlags(&p->own, cudaStreamNonBlocking));
         CKA(cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming));
@@ -456,12 +472,17 @@ int run_multi(mc_lattice *p, int path, int nsweeps, int measure_every, float *tr
     }
     auto it = p->graphs.find(key);
     if (it == p->graphs.end()) {
+        if (path == MC_PATH_FFT) {  // buffers and tables are made outside the capture
+            int rc = ensure_fft(p, st);
+            if (rc) return rc;
+        }
         cudaGraph_t g = nullptr;
         CKA(cudaStreamBeginCapture(p->own, cudaStreamCaptureModeThreadLocal));
         int rc = run_path(p, path, nsweeps, measure_every, nullptr, p->own);
         cudaError_t ec = cudaStreamEndCapture(p->own, &g);
         if (rc) {
             if (g) cudaGraphDestroy(g);
+            cudaGetLastError();  // the failed capture's error must not reach later launches
             return rc;
         }
         if (ec != cudaSuccess) return cuda_fail(ec, "graph capture");
@@ -476,7 +497,7 @@ int run_multi(mc_lattice *p, int path, int nsweeps, int measure_every, float *tr
     CKA(cudaGraphLaunch(it->second, p->own));
     CKA(cudaEventRecord(p->ev_out, p->own));
     CKA(cudaStreamWaitEvent(st, p->ev_out, 0));
-    if (path == MC_PATH_FFT) p->energy_valid = measure_every > 0 && nsweeps % measure_every == 0;
+    if (path == MC_PATH_FFT) p->energy_valid = p->packed || (measure_every > 0 && nsweeps % measure_every == 0);
     return MC_OK;
 }
 
@@ -1006,3 +1027,200 @@ int mc_restore(mc_lattice *p, const void *buf, size_t len) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Internal entry points of the serving layer (server.cu).  None is exported.
+// ---------------------------------------------------------------------------
+namespace dipmc {
+
+// W~ (FP64, device) computed once for (L, cutoff) and copied into the handle with
+// its derived tables; equivalent to mc_precompute_W(p, A, tail).
+int lattice_copy_W(mc_lattice *p, const double *W64_dev, int A, int tail) {
+    int rc = check(p);
+    if (rc) return rc;
+    drop_graphs(p);
+    CK(cudaMemcpy(p->W64, W64_dev, sizeof(double) * 4 * (size_t)p->N(), cudaMemcpyDeviceToDevice));
+    cudaError_t e = launch_cast_W(p->L, p->W64, p->W32, nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "W~ cast");
+    if (!p->wq) CK(cudaMalloc(&p->wq, sizeof(float4) * (size_t)(p->L / 2 + 1) * (p->L / 2 + 1)));
+    e = launch_build_wq(p->L, p->W32, p->wq, nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "W~ quarter table");
+    CK(cudaDeviceSynchronize());
+    p->A = A;
+    p->tail = tail ? 1 : 0;
+    p->W_ready = true;
+    p->wsh_ready = false;
+    p->what_ready = false;
+    p->energy_valid = false;
+    return MC_OK;
+}
+
+// Device bytes of a handle on the path its (L, l) resolves to automatically.
+size_t lattice_footprint(int L, int l, int R) {
+    const size_t N = (size_t)L * L, hq = (size_t)(L / 2 + 1);
+    size_t b = sizeof(RepParams) * R + sizeof(float) * 3 * N * R * 2 + sizeof(double) * 4 * N +
+               sizeof(float) * 4 * N + sizeof(double) * 2 * R + sizeof(ObsAcc) * R + sizeof(double) * N * R +
+               sizeof(float4) * hq * hq + sizeof(SlotState) * R;
+    if (fft_supported(L) && (!direct_supported(L, l) || L >= 128))
+        b += sizeof(float) * 4 * N + fft_scratch_bytes(L, R) + sizeof(double2) * 4 * N;
+    return b + 4096;
+}
+
+int lattice_resolved_path(mc_lattice *p) { return resolve_path(p); }
+
+// Turn a fresh handle (direct path) into a pack of independent replica slots.
+int pack_enable(mc_lattice *p, int path) {
+    int rc = check(p);
+    if (rc) return rc;
+    if (path == MC_PATH_DIRECT ? !direct_supported(p->L, p->l) : path != MC_PATH_FFT || !fft_supported(p->L))
+        return fail(MC_ENOSYS, "packed launches need the direct or the FFT path");
+    CK(cudaMalloc(&p->slots_dev, sizeof(SlotState) * p->R));
+    CK(cudaMallocHost(&p->slots_pin, sizeof(SlotState) * p->R));
+    CK(cudaMallocHost(&p->params_pin, sizeof(RepParams) * p->R));
+    CK(cudaEventCreateWithFlags(&p->slots_copied, cudaEventDisableTiming));
+    p->slots_host.assign(p->R, SlotState{});
+    p->packed = true;
+    p->path = path;
+    p->energy_valid = true;  // direct: anchored when a slot is filled; FFT: set at measurements
+    return MC_OK;
+}
+
+// Fill slots [slot, slot + count) with one request: its couplings, its seed and
+// spins initialised exactly as mc_init_spins does for a lone lattice of `count`
+// replicas, cleared accumulators and an anchored energy.  Stream-ordered on st.
+int pack_fill(mc_lattice *p, int slot, int count, uint64_t seed, const RepParams &rp, int init_mode,
+              cudaStream_t st) {
+    if (!p->packed || slot < 0 || count < 1 || slot + count > p->R) return fail(MC_EINVAL, "bad slot range");
+    const uint2 key = key_of(seed);
+    for (int i = 0; i < count; ++i) {
+        p->params_pin[slot + i] = rp;
+        p->hp[slot + i] = rp;
+        SlotState s{};
+        s.key_lo = key.x;
+        s.key_hi = key.y;
+        s.rid = (uint32_t)i;
+        p->slots_host[slot + i] = s;
+    }
+    const size_t N = p->N(), off = (size_t)slot * 3 * N;
+    CK(cudaMemcpyAsync(p->dparams + slot, p->params_pin + slot, sizeof(RepParams) * count, cudaMemcpyHostToDevice, st));
+    cudaError_t e = launch_init_spins(p->L, count, key, init_mode, p->spins + off, st);
+    if (e != cudaSuccess) return cuda_fail(e, "init kernel");
+    CK(cudaMemsetAsync(p->obs + slot, 0, sizeof(ObsAcc) * count, st));
+    CK(cudaMemsetAsync(p->theta2 + (size_t)slot * N, 0, sizeof(double) * N * count, st));
+    p->last = st;
+    if (p->path == MC_PATH_FFT) {
+        // the FFT path measures the energy afresh; NaN (all bits set) until then,
+        // as a lone handle reports before its first measurement
+        CK(cudaMemsetAsync(p->energy + slot, 0xFF, sizeof(double) * count, st));
+        return MC_OK;
+    }
+    e = launch_full_field(p->L, count, p->W32, p->spins + off, p->field + off, st);
+    if (e != cudaSuccess) return cuda_fail(e, "full-field kernel");
+    e = launch_energy(p->L, count, p->spins + off, p->field + off, p->dparams + slot, p->energy + slot, st);
+    if (e != cudaSuccess) return cuda_fail(e, "energy kernel");
+    p->last = st;
+    return MC_OK;
+}
+
+void pack_set_sweeps(mc_lattice *p, int slot, int count, int nsweeps) {
+    for (int i = 0; i < count; ++i) p->slots_host[slot + i].nsweeps = nsweeps;
+}
+
+int pack_launch_direct(mc_lattice *p, int mx, int measure_every, cudaStream_t st);
+
+// One packed launch: every slot with nsweeps > 0 advances that many sweeps of its
+// own chain; idle slots are untouched.  *launched = the longest slot's sweeps.
+int pack_launch(mc_lattice *p, int measure_every, cudaStream_t st, int *launched) {
+    *launched = 0;
+    int mx = 0;
+    for (const SlotState &s : p->slots_host) mx = std::max(mx, (int)s.nsweeps);
+    if (mx == 0) return MC_OK;
+    CK(cudaEventSynchronize(p->slots_copied));  // the previous launch's staging copy is done
+    std::memcpy(p->slots_pin, p->slots_host.data(), sizeof(SlotState) * p->R);
+    CK(cudaMemcpyAsync(p->slots_dev, p->slots_pin, sizeof(SlotState) * p->R, cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(p->slots_copied, st));
+    if (p->path == MC_PATH_FFT) {
+        // the FFT pack replays a captured graph per sweep count; round the count
+        // up to a power of two (slots past their own count idle) so that a pack
+        // needs only a few graphs
+        int g = 1;
+        while (g < mx) g <<= 1;
+        int rc = run_multi(p, MC_PATH_FFT, g, measure_every, nullptr, st);
+        if (rc) return rc;
+    } else {
+        int rc = pack_launch_direct(p, mx, measure_every, st);
+        if (rc) return rc;
+    }
+    for (SlotState &s : p->slots_host) {
+        s.t0 += (uint32_t)std::min(mx, (int)s.nsweeps);
+        s.nsweeps = 0;
+    }
+    p->last = st;
+    *launched = mx;
+    return MC_OK;
+}
+
+int pack_launch_direct(mc_lattice *p, int mx, int measure_every, cudaStream_t st) {
+    SweepConfig c{};
+    c.L = p->L;
+    c.l = p->l;
+    c.R = p->R;
+    c.key = key_of(p->seed);
+    c.nsweeps = mx;
+    c.measure_every = measure_every;
+    c.proposal = p->proposal;
+    c.cap_c1 = (float)(1.0 - std::cos(p->cone));
+    c.schedule = p->schedule;
+    SweepBuffers b;
+    b.W32 = p->W32;
+    b.spins = p->spins;
+    b.params = p->dparams;
+    b.energy = p->energy;
+    b.obs = p->obs;
+    b.theta2 = p->theta2;
+    b.slots = p->slots_dev;
+    cudaError_t e;
+    {
+        TimedLaunch tl(p, MC_K_SWEEP_DIRECT, st);
+        e = launch_sweep_direct(c, b, p->threads_hint, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "packed sweep launch");
+    return MC_OK;
+}
+
+// Results of replicas [first, first + count): observables and spins [count][3][N]
+// to host memory (spins may be null).  Synchronises st.
+int read_replicas(mc_lattice *p, int first, int count, cudaStream_t st, mc_obs *obs, float *spins) {
+    CK(cudaStreamSynchronize(st));
+    p->last = st;
+    for (int i = 0; i < count; ++i) {
+        int rc = mc_observables(p, first + i, obs + i);
+        if (rc) return rc;
+    }
+    if (spins)
+        CK(cudaMemcpy(spins, p->spins + (size_t)first * 3 * p->N(), sizeof(float) * 3 * p->N() * count,
+                      cudaMemcpyDeviceToHost));
+    return MC_OK;
+}
+
+// Reuse a lone handle for a new request: new seed, couplings of every replica and
+// initial spins, stream-ordered on st (no device-wide synchronisation).
+int lattice_refill(mc_lattice *p, uint64_t seed, const RepParams &rp, int init_mode, cudaStream_t st) {
+    int rc = check(p);
+    if (rc) return rc;
+    drop_graphs(p);
+    if (!p->params_pin) CK(cudaMallocHost(&p->params_pin, sizeof(RepParams) * p->R));
+    for (int i = 0; i < p->R; ++i) p->params_pin[i] = p->hp[i] = rp;
+    p->seed = seed;
+    CK(cudaMemcpyAsync(p->dparams, p->params_pin, sizeof(RepParams) * p->R, cudaMemcpyHostToDevice, st));
+    cudaError_t e = launch_init_spins(p->L, p->R, key_of(seed), init_mode, p->spins, st);
+    if (e != cudaSuccess) return cuda_fail(e, "init kernel");
+    rc = clear_obs(p, st);
+    if (rc) return rc;
+    p->t = 0;
+    p->energy_valid = false;  // anchored by the first sweep call, on the same stream
+    p->last = st;
+    return MC_OK;
+}
+
+}  // namespace dipmc

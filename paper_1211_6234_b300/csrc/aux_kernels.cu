@@ -79,6 +79,17 @@ __global__ void __launch_bounds__(kWThreads) k_wtilde(int L, int A, int tail, do
     }
 }
 
+__global__ void k_cast_W(size_t n, const double *__restrict__ W64, float *W32) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) W32[i] = (float)W64[i];
+}
+
+cudaError_t launch_cast_W(int L, const double *W64, float *W32, cudaStream_t st) {
+    const size_t n = (size_t)4 * L * L;
+    k_cast_W<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, W64, W32);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_wtilde(int L, int A, int tail, double *W64, float *W32, cudaStream_t st) {
     k_wtilde<<<L * L, kWThreads, 0, st>>>(L, A, tail, W64, W32);
     return cudaGetLastError();

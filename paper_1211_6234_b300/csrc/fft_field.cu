@@ -195,18 +195,27 @@ __global__ void k_fft_update(const FftStepConfig cfg, const FftStepBuffers buf) 
     const int L = cfg.L, l = cfg.l, N = L * L, C = L / l, n = C * C, ll = l * l;
     const int r = blockIdx.y;
     const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    uint2 key = cfg.key;
+    uint32_t t = cfg.t_dev ? *cfg.t_dev + (uint32_t)cfg.it : cfg.t, rid = (uint32_t)r;
+    if (buf.slots) {
+        const SlotState sl = buf.slots[r];
+        if (cfg.it >= sl.nsweeps) return;   // idle or finished slot: whole block, before any barrier
+        key = make_uint2(sl.key_lo, sl.key_hi);
+        t = sl.t0 + (uint32_t)cfg.it;
+        rid = sl.rid;
+    }
     __shared__ int s_acc;
     if (threadIdx.x == 0) s_acc = 0;
     __syncthreads();
     int accept = 0;
     if (d < n) {
-        const uint32_t t = cfg.t_dev ? *cfg.t_dev + (uint32_t)cfg.it : cfg.t, k = (uint32_t)cfg.k;
+        const uint32_t k = (uint32_t)cfg.k;
         uint32_t v;
         if (cfg.schedule == 0) {
-            const uint4 rk = philox(make_uint4(t, 0u, 0u, kTagPerm), cfg.key);
+            const uint4 rk = philox(make_uint4(t, 0u, 0u, kTagPerm), key);
             v = perm_offset(rk, ceil_log2_u((uint32_t)l), (uint32_t)ll, k);
         } else {
-            const uint4 o = philox(make_uint4(t, k, 0u, kTagDraw), cfg.key);
+            const uint4 o = philox(make_uint4(t, k, 0u, kTagDraw), key);
             v = (uint32_t)(((unsigned long long)o.x * (unsigned long long)ll) >> 32);
         }
         const int qx = (int)(v % l) + l * (d % C), qy = (int)(v / l) + l * (d / C);
@@ -214,7 +223,7 @@ __global__ void k_fft_update(const FftStepConfig cfg, const FftStepBuffers buf) 
         const RepParams P = buf.params[r];
         float *s = buf.spins + (size_t)r * 3 * N;
         const float *h = buf.field + (size_t)r * 3 * N;
-        const uint4 wds = philox(make_uint4((uint32_t)q, (uint32_t)r, t, (k & 0x00FFFFFFu) | kTagAttempt), cfg.key);
+        const uint4 wds = philox(make_uint4((uint32_t)q, rid, t, (k & 0x00FFFFFFu) | kTagAttempt), key);
         const float u1 = u24f(wds.x), uacc = u24f(wds.z);
         float sps, cps;
         sincospif(2.0f * u24f(wds.y), &sps, &cps);
@@ -283,8 +292,13 @@ __global__ void k_fft_update(const FftStepConfig cfg, const FftStepBuffers buf) 
 // the log-binning push (thread k < kNB updates level k).
 __global__ void __launch_bounds__(256) k_fft_observe(int L, const float *__restrict__ spins,
                                                      const float *__restrict__ field, const RepParams *__restrict__ P,
-                                                     double *energy, ObsAcc *obs, double *theta2) {
+                                                     double *energy, ObsAcc *obs, double *theta2,
+                                                     const SlotState *slots, int it, int measure_every) {
     const int N = L * L, r = blockIdx.x, tid = threadIdx.x;
+    if (slots) {
+        const SlotState sl = slots[r];
+        if (it >= sl.nsweeps || measure_every <= 0 || (sl.t0 + (uint32_t)it + 1u) % (uint32_t)measure_every) return;
+    }
     const float *s = spins + (size_t)r * 3 * N;
     const float *f = field + (size_t)r * 3 * N;
     const RepParams p = P[r];
@@ -356,9 +370,12 @@ __global__ void __launch_bounds__(256) k_fft_observe(int L, const float *__restr
     }
 }
 
-__global__ void k_add_attempted(ObsAcc *obs, int R, long long add) {
+__global__ void k_add_attempted(ObsAcc *obs, int R, long long add, const SlotState *slots, int nsweeps_call,
+                                long long N) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < R) obs[r].attempted += add;
+    if (r >= R) return;
+    if (slots) add = (long long)min(nsweeps_call, (int)slots[r].nsweeps) * N;
+    obs[r].attempted += add;
 }
 
 int ilog2(int v) {
@@ -446,13 +463,15 @@ cudaError_t launch_fft_update(const FftStepConfig &c, const FftStepBuffers &b, c
 }
 
 cudaError_t launch_fft_observe(int L, int R, const float *spins, const float *field, const RepParams *P,
-                               double *energy, ObsAcc *obs, double *theta2, cudaStream_t st) {
-    k_fft_observe<<<R, 256, 0, st>>>(L, spins, field, P, energy, obs, theta2);
+                               double *energy, ObsAcc *obs, double *theta2, const SlotState *slots, int it,
+                               int measure_every, cudaStream_t st) {
+    k_fft_observe<<<R, 256, 0, st>>>(L, spins, field, P, energy, obs, theta2, slots, it, measure_every);
     return cudaGetLastError();
 }
 
-cudaError_t launch_add_attempted(ObsAcc *obs, int R, long long add, cudaStream_t st) {
-    k_add_attempted<<<(R + 127) / 128, 128, 0, st>>>(obs, R, add);
+cudaError_t launch_add_attempted(ObsAcc *obs, int R, long long add, const SlotState *slots, int nsweeps_call,
+                                 long long N, cudaStream_t st) {
+    k_add_attempted<<<(R + 127) / 128, 128, 0, st>>>(obs, R, add, slots, nsweeps_call, N);
     return cudaGetLastError();
 }
 

@@ -25,6 +25,7 @@ struct FftStepBuffers {
     const RepParams *params;   // [R]
     ObsAcc *obs;               // [R] (accepted count)
     float *trace;              // optional
+    const SlotState *slots;    // optional [R]: packed launch (per-replica key, counter, sweeps)
 };
 
 bool fft_supported(int L);
@@ -34,8 +35,13 @@ cudaError_t launch_build_what(int L, const double *W64, float *What, cudaStream_
 cudaError_t launch_fft_field(int L, int R, const float *spins, const float *What, float2 *scratch, float *field,
                              cudaStream_t st);
 cudaError_t launch_fft_update(const FftStepConfig &c, const FftStepBuffers &b, cudaStream_t st);
+// Observables of every replica; with slots, only replicas whose own sweep count
+// (t0 + it + 1) is a multiple of measure_every and that are active at sweep `it`.
 cudaError_t launch_fft_observe(int L, int R, const float *spins, const float *field, const RepParams *P,
-                               double *energy, ObsAcc *obs, double *theta2, cudaStream_t st);
-cudaError_t launch_add_attempted(ObsAcc *obs, int R, long long add, cudaStream_t st);
+                               double *energy, ObsAcc *obs, double *theta2, const SlotState *slots, int it,
+                               int measure_every, cudaStream_t st);
+// attempted += add for every replica; with slots, += min(nsweeps_call, slot sweeps) * N.
+cudaError_t launch_add_attempted(ObsAcc *obs, int R, long long add, const SlotState *slots, int nsweeps_call,
+                                 long long N, cudaStream_t st);
 
 }  // namespace dipmc

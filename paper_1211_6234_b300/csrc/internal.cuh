@@ -102,18 +102,32 @@ struct SweepConfig {
     int schedule;     // 0 permutation, 1 draw
 };
 
+// Per-replica stream state of a packed launch: independent requests share one
+// launch, each replica slot with its own Philox key, its own sweep counter t0,
+// the replica index its counters use, and how many of the launch's sweeps it
+// takes (0 = idle slot, left untouched).
+struct SlotState {
+    uint32_t key_lo, key_hi;
+    uint32_t t0;
+    int32_t nsweeps;
+    uint32_t rid;
+    uint32_t pad[3];
+};
+
 struct SweepBuffers {
-    const float *W32;         // [4][N]
-    float *spins;             // [R][3][N]
-    const RepParams *params;  // [R]
-    double *energy;           // [R] tracked energy (in: at t0, out: at t0+nsweeps)
-    ObsAcc *obs;              // [R]
-    double *theta2;           // [R][N]
-    float *trace;             // optional [R][nsweeps][l^2][n][MC_TRACE_W]
+    const float *W32 = nullptr;         // [4][N]
+    float *spins = nullptr;             // [R][3][N]
+    const RepParams *params = nullptr;  // [R]
+    double *energy = nullptr;           // [R] tracked energy (in: at t0, out: at t0+nsweeps)
+    ObsAcc *obs = nullptr;              // [R]
+    double *theta2 = nullptr;           // [R][N]
+    float *trace = nullptr;             // optional [R][nsweeps][l^2][n][MC_TRACE_W]
+    const SlotState *slots = nullptr;   // optional [R]: packed launch
 };
 
 // Launchers (implemented in their .cu files).  Return a cudaError_t.
 cudaError_t launch_wtilde(int L, int A, int tail, double *W64, float *W32, cudaStream_t st);
+cudaError_t launch_cast_W(int L, const double *W64, float *W32, cudaStream_t st);
 cudaError_t launch_init_spins(int L, int R, uint2 key, int mode, float *spins, cudaStream_t st);
 cudaError_t launch_full_field(int L, int R, const float *W32, const float *spins, float *h,
                               cudaStream_t st);
@@ -123,6 +137,8 @@ cudaError_t launch_energy(int L, int R, const float *spins, const float *h, cons
 cudaError_t launch_sweep_direct(const SweepConfig &c, const SweepBuffers &b, int threads_hint,
                                 cudaStream_t st);
 bool direct_supported(int L, int l);
+// CTAs of the direct kernel resident on the whole GPU for a packed launch of (L, l).
+int direct_resident_ctas(int L, int l);
 
 // Records a one-line error message for mc_last_error() and returns `code`.
 int set_last_error(int code, const char *msg);

@@ -131,11 +131,23 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
     const int NWF = NW - 1;                     // field warps; warp 0 is the control warp
     const int ftid = tid - 32, NTF = NT - 32;
     const int r = blockIdx.x;
+    // stream state of this replica: the lattice's own, or its slot's in a packed launch
+    uint2 key = cfg.key;
+    uint32_t t0 = cfg.t0, rid = (uint32_t)r, mphase = 0;
+    int nsw = cfg.nsweeps;
+    if (buf.slots) {
+        const SlotState sl = buf.slots[r];
+        key = make_uint2(sl.key_lo, sl.key_hi);
+        t0 = sl.t0;
+        mphase = sl.t0;             // measure on the slot's own sweep count
+        rid = sl.rid;
+        nsw = min(nsw, (int)sl.nsweeps);
+        if (nsw <= 0) return;       // idle slot: whole CTA leaves before any barrier
+    }
 
     extern __shared__ float4 smem_f4[];
     float4 *s4 = smem_f4;                                         // [N] spins (x, y, z, 0)
-    float *th2 = reinterpret_cast<float *>(s4 + N);               // [N] sum (theta - pi/2)^2
-    float *red = th2 + N;                                         // [NWF][V] warp partial fields
+    float *red = reinterpret_cast<float *>(s4 + N);               // [NWF][V] warp partial fields
     float *mred = red + NWF * V;                                  // [NW][4] magnetisation
     float *wl = mred + NW * 4;                                    // [n][4] W~(l*D), D in [0,C)^2
     uint16_t *sched = reinterpret_cast<uint16_t *>(wl + n * 4);   // [ll] offsets of the sweep
@@ -154,8 +166,9 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
     const float *gs = buf.spins + (size_t)r * 3 * N;
     for (int i = tid; i < N; i += NT) s4[i] = make_float4(gs[i], gs[N + i], gs[2 * N + i], 0.0f);
     const bool measuring = cfg.measure_every > 0;
-    if (measuring)
-        for (int i = tid; i < N; i += NT) th2[i] = 0.0f;
+    // per-site sum of (theta - pi/2)^2, added in FP64 at every measured sweep so
+    // that the result does not depend on how the sweeps are split into launches
+    double *gt = buf.theta2 ? buf.theta2 + (size_t)r * N : nullptr;
     if (tid < 4 * n) {
         const int D = tid >> 2, c = tid & 3;
         wl[tid] = buf.W32[c * N + (l * (D / C)) * L + l * (D % C)];
@@ -192,7 +205,6 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
         }
     }
 
-    const uint2 key = cfg.key;
     const int hbits = ceil_log2_u((uint32_t)l);
     bool pending = false;      // control warp: a decided sub-step awaits bookkeeping
     long long n_acc = 0;       // control warp lane 0: accepted moves
@@ -216,8 +228,8 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
         __syncwarp();
     };
 
-    for (int it = 0; it < cfg.nsweeps; ++it) {
-        const uint32_t t = cfg.t0 + (uint32_t)it;
+    for (int it = 0; it < nsw; ++it) {
+        const uint32_t t = t0 + (uint32_t)it;
         // ---- the sweep's schedule
         if (cfg.schedule == 0) {
             const uint4 rk = philox(make_uint4(t, 0u, 0u, kTagPerm), key);
@@ -248,7 +260,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
                     const RepParams &P = c_P;
                     const int qx = ox + l * (lane % C), qy = oy + l * (lane / C);
                     const int q = qy * L + qx;
-                    const uint4 wds = philox(make_uint4((uint32_t)q, (uint32_t)r, t, ((uint32_t)k & 0x00FFFFFFu) | kTagAttempt), key);
+                    const uint4 wds = philox(make_uint4((uint32_t)q, rid, t, ((uint32_t)k & 0x00FFFFFFu) | kTagAttempt), key);
                     const float u1 = u24f(wds.x);
                     float sps, cps;
                     sincospif(2.0f * u24f(wds.y), &sps, &cps);
@@ -393,21 +405,31 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
             }
             __syncthreads();
         }
-        if (warp == 0 && pending) {
-            bookkeeping();
-            pending = false;
+        if (warp == 0) {
+            if (pending) {
+                bookkeeping();
+                pending = false;
+            }
+            // fold the sweep's energy change into the tracked energy, so that the
+            // sum does not depend on how the sweeps are split into launches
+            double et = c_epart[lane];
+            c_epart[lane] = 0.0;
+            for (int off = 16; off; off >>= 1) et += __shfl_xor_sync(0xffffffffu, et, off);
+            if (lane == 0) e_track_s += et;
         }
 
         // ---- observables of this sweep
-        if (measuring && ((it + 1) % cfg.measure_every) == 0) {
+        if (measuring && ((mphase + (uint32_t)it + 1u) % (uint32_t)cfg.measure_every) == 0) {
             float mx = 0.f, my = 0.f, mz = 0.f;
             for (int i = tid; i < N; i += NT) {
                 const float4 a = s4[i];
                 mx += a.x;
                 my += a.y;
                 mz += a.z;
-                const float th = acosf(fminf(1.0f, fmaxf(-1.0f, a.z))) - 0.5f * kPiF;
-                th2[i] += th * th;
+                if (gt) {
+                    const float th = acosf(fminf(1.0f, fmaxf(-1.0f, a.z))) - 0.5f * kPiF;
+                    gt[i] += (double)(th * th);
+                }
             }
             for (int off = 16; off; off >>= 1) {
                 mx += __shfl_xor_sync(0xffffffffu, mx, off);
@@ -421,8 +443,6 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
             }
             __syncthreads();
             if (warp == 0) {
-                double et = c_epart[lane];
-                for (int off = 16; off; off >>= 1) et += __shfl_xor_sync(0xffffffffu, et, off);
                 if (lane == 0) {
                     double Mx = 0, My = 0, Mz = 0;
                     for (int ww = 0; ww < NW; ++ww) {
@@ -436,7 +456,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
                     x[MC_OBS_MZ] = Mz;
                     x[MC_OBS_ABS_MZ] = fabs(Mz);
                     x[MC_OBS_MPAR] = sqrt(Mx * Mx + My * My);
-                    x[MC_OBS_E] = (e_track_s + et) / N;
+                    x[MC_OBS_E] = e_track_s / N;
                     if (buf.obs) obs_push(acc_s, x);
                 }
             }
@@ -452,18 +472,12 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
         gd[N + i] = a.y;
         gd[2 * N + i] = a.z;
     }
-    if (measuring && buf.theta2) {
-        double *gt = buf.theta2 + (size_t)r * N;
-        for (int i = tid; i < N; i += NT) gt[i] += (double)th2[i];
-    }
     if (warp == 0) {
-        double et = c_epart[lane];
-        for (int off = 16; off; off >>= 1) et += __shfl_xor_sync(0xffffffffu, et, off);
         if (lane == 0) {
-            if (buf.energy) buf.energy[r] = e_track_s + et;
+            if (buf.energy) buf.energy[r] = e_track_s;
             if (buf.obs) {
                 acc_s.accepted += n_acc;
-                acc_s.attempted += (long long)cfg.nsweeps * N;
+                acc_s.attempted += (long long)nsw * N;
                 buf.obs[r] = acc_s;
             }
         }
@@ -473,7 +487,16 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
 struct Inst {
     int C, EPT, MAXT, MINB;
     cudaError_t (*launch)(const SweepConfig &, const SweepBuffers &, int, size_t, cudaStream_t);
+    cudaError_t (*occupancy)(int, size_t, int *);
 };
+
+template <int C, int EPT, int MAXT, int MINB>
+cudaError_t occupancy_inst(int threads, size_t smem, int *per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(k_sweep_direct<C, EPT, MAXT, MINB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_sweep_direct<C, EPT, MAXT, MINB>, threads, smem);
+}
 
 template <int C, int EPT, int MAXT, int MINB>
 cudaError_t launch_inst(const SweepConfig &c, const SweepBuffers &b, int threads, size_t smem, cudaStream_t st) {
@@ -488,7 +511,7 @@ cudaError_t launch_inst(const SweepConfig &c, const SweepBuffers &b, int threads
 // The launch bound keeps C^2*4*EPT tensor values + 3*C^2 accumulators per
 // thread in registers; MINB = 2 instances fit two CTAs per SM (8 warps each, so
 // that each SM sub-partition holds 4 warps and 128 registers per thread).
-#define INST(C, E, T, B) {C, E, T, B, launch_inst<C, E, T, B>}
+#define INST(C, E, T, B) {C, E, T, B, launch_inst<C, E, T, B>, occupancy_inst<C, E, T, B>}
 const Inst kInst[] = {
     INST(1, 1, 288, 2), INST(1, 2, 544, 1), INST(1, 4, 288, 2), INST(1, 8, 544, 1),
     INST(1, 19, 256, 2), INST(1, 18, 544, 1),
@@ -504,7 +527,7 @@ int threads_of(const Inst &in, int ll) {
 
 size_t smem_bytes(int L, int l, int threads) {
     const int N = L * L, C = L / l, n = C * C, NW = threads / 32;
-    size_t b = sizeof(float4) * (size_t)N + sizeof(float) * (size_t)(N + (NW - 1) * 3 * n + NW * 4 + 4 * n);
+    size_t b = sizeof(float4) * (size_t)N + sizeof(float) * (size_t)((NW - 1) * 3 * n + NW * 4 + 4 * n);
     b += sizeof(uint16_t) * (size_t)l * l;
     return (b + 15) & ~(size_t)15;
 }
@@ -544,13 +567,25 @@ bool direct_supported(int L, int l) {
     return pick(L, l, 1, 1, &th) != nullptr;
 }
 
+int direct_resident_ctas(int L, int l) {
+    int dev = 0, nsm = 148, th = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const Inst *in = pick(L, l, 1, nsm, &th);
+    if (!in) return 0;
+    int per_sm = 0;
+    if (in->occupancy(th, smem_bytes(L, l, th), &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
+    return per_sm * nsm;
+}
+
 cudaError_t launch_sweep_direct(const SweepConfig &c, const SweepBuffers &b, int threads_hint,
                                 cudaStream_t st) {
     (void)threads_hint;
     int dev = 0, nsm = 148;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     int threads = 0;
-    const Inst *in = pick(c.L, c.l, c.R, nsm, &threads);
+    // a packed launch uses the instance a lone replica would, so that every
+    // slot's arithmetic (and trajectory) is the one it has alone
+    const Inst *in = pick(c.L, c.l, b.slots ? 1 : c.R, nsm, &threads);
     if (!in) return cudaErrorNotSupported;
     return in->launch(c, b, threads, smem_bytes(c.L, c.l, threads), st);
 }

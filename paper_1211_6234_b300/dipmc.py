@@ -30,7 +30,10 @@ ABI_SYMBOLS = (
     "mc_get_spins", "mc_get_field", "mc_get_W", "mc_energy", "mc_get_sweep_counter",
     "mc_checkpoint", "mc_restore", "mc_energy_noalloc", "mc_set_timing", "mc_get_timing",
     "mc_choose_spacing", "mc_autotune",
+    "mc_footprint", "mc_server_create", "mc_server_submit", "mc_server_step", "mc_server_poll", "mc_server_request_info",
+    "mc_server_collect", "mc_server_get_spins", "mc_server_release", "mc_server_get_stats", "mc_server_destroy",
 )
+MC_REQ_QUEUED, MC_REQ_RUNNING, MC_REQ_DONE, MC_REQ_FAILED, MC_REQ_RELEASED = range(5)
 KERNEL_CLASSES = ("sweep_direct", "tc_field", "window_steps", "full_field")
 
 
@@ -61,6 +64,25 @@ class mc_obs(C.Structure):
             d[nm] = {"mean": self.mean[i], "var": self.var[i], "err_naive": self.err_naive[i],
                      "err": self.err[i], "tau_int": self.tau_int[i]}
         return d
+
+
+class mc_request(C.Structure):
+    _fields_ = [("L", C.c_int), ("l", C.c_int), ("replicas", C.c_int),
+                ("J", C.c_double), ("C_D", C.c_double), ("K2", C.c_double), ("K4", C.c_double), ("T", C.c_double),
+                ("sweeps", C.c_int64), ("measure_every", C.c_int), ("seed", C.c_uint64), ("init_mode", C.c_int),
+                ("image_cutoff", C.c_int), ("proposal", C.c_int), ("cone", C.c_double)]
+
+
+class mc_request_info(C.Structure):
+    _fields_ = [("state", C.c_int), ("l", C.c_int), ("path", C.c_int), ("packed", C.c_int), ("sweeps_done", C.c_int64),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("bytes", C.c_size_t), ("error", C.c_char * 160)]
+
+
+class mc_server_stats(C.Structure):
+    _fields_ = [("queued", C.c_int), ("running", C.c_int), ("done", C.c_int), ("failed", C.c_int),
+                ("packs", C.c_int), ("lone", C.c_int), ("completed", C.c_int64),
+                ("bytes_in_use", C.c_size_t), ("budget", C.c_size_t)]
 
 
 class mc_timing(C.Structure):
@@ -99,6 +121,17 @@ def _load():
         "mc_set_timing": ([vp, i32], i32),
         "mc_choose_spacing": ([i32, f64, f64, f64, C.POINTER(i32)], i32),
         "mc_autotune": ([vp, i32, vp, C.POINTER(i32), C.POINTER(i32)], i32),
+        "mc_footprint": ([i32, i32, i32, C.POINTER(C.c_size_t)], i32),
+        "mc_server_create": ([C.c_size_t, i32, i32, f64, C.POINTER(vp)], i32),
+        "mc_server_submit": ([vp, C.POINTER(mc_request), C.POINTER(u64)], i32),
+        "mc_server_step": ([vp], i32),
+        "mc_server_poll": ([vp, u64, C.POINTER(i32), C.POINTER(C.c_int64)], i32),
+        "mc_server_request_info": ([vp, u64, C.POINTER(mc_request_info)], i32),
+        "mc_server_collect": ([vp, u64, i32, C.POINTER(mc_obs)], i32),
+        "mc_server_get_spins": ([vp, u64, C.POINTER(C.c_float)], i32),
+        "mc_server_release": ([vp, u64], i32),
+        "mc_server_get_stats": ([vp, C.POINTER(mc_server_stats)], i32),
+        "mc_server_destroy": ([vp], i32),
         "mc_get_timing": ([vp, C.POINTER(mc_timing)], i32),
     }
     for name, (args, res) in sig.items():
@@ -285,3 +318,97 @@ class Lattice:
     def restore(self, data: bytes):
         buf = C.create_string_buffer(data, len(data))
         _ck(_lib.mc_restore(self.h, buf, len(data)))
+
+
+def footprint(L: int, l: int, replicas: int = 1) -> int:
+    """Device bytes of a handle (the server's admission estimate)."""
+    b = C.c_size_t()
+    _ck(_lib.mc_footprint(L, l, replicas, C.byref(b)))
+    return b.value
+
+
+class Server:
+    """Continuous-batching service (mc_server_*).  Requests of the same (L, l)
+    share packed launches; each request's result equals its lone run."""
+
+    def __init__(self, hbm_budget_bytes=8 << 30, max_active=4096, quantum_sweeps=50, max_error=1e-3):
+        h = C.c_void_p()
+        _ck(_lib.mc_server_create(int(hbm_budget_bytes), max_active, quantum_sweeps, max_error, C.byref(h)))
+        self.h = h
+        self._shape = {}
+
+    def close(self):
+        if self.h:
+            _lib.mc_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, L, T, sweeps, seed, l=0, replicas=1, J=1.0, C_D=0.1, K2=0.8, K4=0.0,
+               measure_every=1, init_mode=0, image_cutoff=64, proposal=0, cone=0.5) -> int:
+        r = mc_request(L, l, replicas, J, C_D, K2, K4, T, int(sweeps), measure_every, int(seed), init_mode,
+                       image_cutoff, proposal, cone)
+        rid = C.c_uint64()
+        _ck(_lib.mc_server_submit(self.h, C.byref(r), C.byref(rid)))
+        self._shape[rid.value] = (max(1, replicas), L)
+        return rid.value
+
+    def step(self):
+        _ck(_lib.mc_server_step(self.h))
+
+    def poll(self, rid):
+        st, done = C.c_int(), C.c_int64()
+        _ck(_lib.mc_server_poll(self.h, rid, C.byref(st), C.byref(done)))
+        return st.value, done.value
+
+    def info(self, rid) -> dict:
+        i = mc_request_info()
+        _ck(_lib.mc_server_request_info(self.h, rid, C.byref(i)))
+        return {"state": i.state, "l": i.l, "path": i.path, "packed": bool(i.packed), "sweeps_done": i.sweeps_done,
+                "t_submit": i.t_submit, "t_admit": i.t_admit, "t_done": i.t_done, "bytes": i.bytes,
+                "error": i.error.decode()}
+
+    def collect(self, rid, replica=0) -> dict:
+        o = mc_obs()
+        _ck(_lib.mc_server_collect(self.h, rid, replica, C.byref(o)))
+        return o.as_dict()
+
+    def spins(self, rid) -> np.ndarray:
+        R, L = self._shape[rid]
+        a = np.empty((R, 3, L, L), np.float32)
+        _ck(_lib.mc_server_get_spins(self.h, rid, a.ctypes.data_as(C.POINTER(C.c_float))))
+        return a
+
+    def release(self, rid):
+        _ck(_lib.mc_server_release(self.h, rid))
+
+    def stats(self) -> dict:
+        s = mc_server_stats()
+        _ck(_lib.mc_server_get_stats(self.h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in mc_server_stats._fields_}
+
+    def run_until_done(self, ids, timeout_s=600.0, on_done=None):
+        """Step until every id in `ids` is DONE or FAILED; on_done(id) when each ends."""
+        import time
+        left = set(ids)
+        t_end = time.monotonic() + timeout_s
+        while left:
+            self.step()
+            for rid in list(left):
+                st, _ = self.poll(rid)
+                if st in (MC_REQ_DONE, MC_REQ_FAILED):
+                    left.discard(rid)
+                    if on_done:
+                        on_done(rid)
+            if time.monotonic() > t_end:
+                raise TimeoutError(f"{len(left)} requests unfinished")
