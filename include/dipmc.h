@@ -64,6 +64,7 @@ extern "C" {
 #define MC_PATH_WINDOW_F32 2  /* windowed sweep, stale field from the FP32 full field */
 #define MC_PATH_TENSOR 3      /* windowed sweep, stale field on tcgen05 tensor cores, split-BF16x3 */
 #define MC_PATH_FFT 4         /* full field per sub-step by 2D FFT convolution (L a power of two) */
+#define MC_PATH_SPECTRAL 5    /* field at the sub-step's sites from sub-lattice spectra (L/l <= 32) */
 
 typedef struct mc_lattice mc_lattice;
 
@@ -125,7 +126,14 @@ int mc_set_schedule(mc_lattice *lat, int kind);
  * rounding.  MC_PATH_TENSOR needs L % 8 == 0 and B*(L/l)^2 % 128 == 0.
  * MC_PATH_FFT evaluates the full field of every replica by FFT convolution before
  * each sub-step (L a power of two, 8 <= L <= 1024, spins in global memory); it is
- * the path for large lattices, where mc_get_field and mc_energy also use the FFT. */
+ * the path for large lattices, where mc_get_field and mc_energy also use the FFT.
+ * MC_PATH_SPECTRAL splits the field at a sub-step's sites into l^2 circular
+ * convolutions on the (L/l) x (L/l) grid of each cell offset and keeps the DFT of
+ * every offset's spin sub-lattice on the device: a sub-step is an O(L^2)
+ * contraction of those spectra with the transforms of W~, an inverse DFT, the
+ * update and the DFT of the updated sub-lattice (2 <= L/l <= 32, any L).  The FFT
+ * and spectral paths measure the energy afresh from the full field at each
+ * measured sweep.  MC_PATH_AUTO order: direct, spectral, FFT, windowed. */
 int mc_set_field_path(mc_lattice *lat, int path);
 
 /* Sub-steps per window of the windowed paths (must divide l^2; 0 = automatic). */
@@ -194,7 +202,9 @@ int mc_energy(mc_lattice *lat, double *dst_host, void *stream);
 #define MC_K_TC_FIELD 1      /* tensor-core window field (one launch per window) */
 #define MC_K_WINDOW_STEPS 2  /* sequential sub-steps of a window */
 #define MC_K_FULL_FIELD 3    /* FP32 full field (energy anchor, windowed FP32 path) */
-#define MC_NKCLASS 4
+#define MC_K_SPEC_FIELD 4    /* spectral path: field spectra at the sub-step's sites */
+#define MC_K_SPEC_UPDATE 5   /* spectral path: inverse DFT, update, DFT of the updated sub-lattice */
+#define MC_NKCLASS 6
 typedef struct mc_timing {
     int64_t launches[MC_NKCLASS];
     double ms[MC_NKCLASS];

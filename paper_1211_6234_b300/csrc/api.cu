@@ -12,6 +12,7 @@
 
 #include "fft_field.cuh"
 #include "internal.cuh"
+#include "spectral.cuh"
 #include "tc_field.cuh"
 #include "window.cuh"
 
@@ -87,6 +88,10 @@ struct mc_lattice {
     float *What = nullptr;    // [4][N] transform of W~ (FFT path), transposed layout
     float2 *fft_scratch = nullptr;
     bool what_ready = false;
+    // sub-lattice spectral path
+    float2 *specT = nullptr, *specS = nullptr, *specH = nullptr;
+    bool spec_ready = false;
+    int spec_esplit = 0;
     // CUDA graphs of the multi-launch paths, keyed by (path, nsweeps, measure_every)
     uint32_t *t_dev = nullptr;            // sweep counter at the start of the current call
     cudaStream_t own = nullptr;           // capture/replay stream (joined to the caller's by events)
@@ -136,6 +141,9 @@ void free_all(mc_lattice *p) {
     if (p->own) cudaStreamDestroy(p->own);
     if (p->ev_in) cudaEventDestroy(p->ev_in);
     if (p->ev_out) cudaEventDestroy(p->ev_out);
+    cudaFree(p->specT);
+    cudaFree(p->specS);
+    cudaFree(p->specH);
     cudaFree(p->slots_dev);
     if (p->slots_pin) cudaFreeHost(p->slots_pin);
     if (p->params_pin) cudaFreeHost(p->params_pin);
@@ -203,6 +211,7 @@ bool path_supported(const mc_lattice *p, int path) {
             return B > 0 && tc_supported(p->L, p->l, B) && window_supported(p->L, p->l, B);
         }
         case MC_PATH_FFT: return fft_supported(p->L);
+        case MC_PATH_SPECTRAL: return spectral_supported(p->L, p->l);
         default: return false;
     }
 }
@@ -210,6 +219,7 @@ bool path_supported(const mc_lattice *p, int path) {
 int resolve_path(const mc_lattice *p) {
     if (p->path != MC_PATH_AUTO) return p->path;
     if (direct_supported(p->L, p->l)) return MC_PATH_DIRECT;
+    if (spectral_supported(p->L, p->l)) return MC_PATH_SPECTRAL;
     if (fft_supported(p->L)) return MC_PATH_FFT;
     if (path_supported(p, MC_PATH_WINDOW_F32)) return MC_PATH_WINDOW_F32;
     return -1;
@@ -446,9 +456,85 @@ int run_fft(mc_lattice *p, int nsweeps, int measure_every, float *trace, cudaStr
     return MC_OK;
 }
 
+int ensure_spectral(mc_lattice *p, cudaStream_t st) {
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int es = spectral_esplit(p->L, p->l, p->R, nsm);
+    if (!p->specT) CKA(cudaMalloc(&p->specT, sizeof(float2) * 4 * (size_t)p->N()));
+    if (!p->specS) CKA(cudaMalloc(&p->specS, sizeof(float2) * spectral_S_elems(p->L, p->R)));
+    if (p->spec_esplit != es) {
+        cudaFree(p->specH);
+        p->specH = nullptr;
+        CKA(cudaMalloc(&p->specH, sizeof(float2) * spectral_part_elems(p->L, p->l, p->R, es)));
+        p->spec_esplit = es;
+    }
+    if (!p->spec_ready) {
+        cudaError_t e = launch_spec_table(p->L, p->l, p->W64, p->specT, st);
+        if (e != cudaSuccess) return cuda_fail(e, "spectral W~ table");
+        p->spec_ready = true;
+    }
+    return MC_OK;
+}
+
+// Sub-lattice spectral path: spectra of every offset from the spins, then per
+// sub-step the field spectra at the sub-step's sites and the update; the energy
+// and observables from a full field at measured sweeps (as the FFT path).
+int run_spectral(mc_lattice *p, int nsweeps, int measure_every, float *trace, cudaStream_t st) {
+    int rc = ensure_spectral(p, st);
+    if (rc) return rc;
+    const int ll = p->l * p->l;
+    SpecConfig c{};
+    c.t_dev = p->t_dev;
+    c.L = p->L; c.l = p->l; c.R = p->R;
+    c.key = key_of(p->seed);
+    c.nsweeps_call = nsweeps;
+    c.proposal = p->proposal;
+    c.cap_c1 = (float)(1.0 - std::cos(p->cone));
+    c.schedule = p->schedule;
+    c.esplit = p->spec_esplit;
+    SpecBuffers b;
+    b.W32 = p->W32; b.spins = p->spins; b.params = p->dparams; b.obs = p->obs; b.trace = trace;
+    b.slots = p->packed ? p->slots_dev : nullptr;
+    b.T = p->specT; b.S = p->specS; b.Hpart = p->specH;
+    cudaError_t e = launch_spec_init(p->L, p->l, p->R, p->spins, p->specS, st);
+    if (e != cudaSuccess) return cuda_fail(e, "spectra of the spin sub-lattices");
+    bool measured_last = false;
+    for (int it = 0; it < nsweeps; ++it) {
+        c.t = (uint32_t)(p->t + (uint64_t)it);
+        c.it = it;
+        for (int k = 0; k < ll; ++k) {
+            c.k = k;
+            {
+                TimedLaunch tl(p, MC_K_SPEC_FIELD, st);
+                e = launch_spec_field(c, b, st);
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "spectral field");
+            {
+                TimedLaunch tl(p, MC_K_SPEC_UPDATE, st);
+                e = launch_spec_update(c, b, st);
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "spectral update");
+        }
+        measured_last = measure_every > 0 && (b.slots || ((it + 1) % measure_every) == 0);
+        if (measured_last) {
+            rc = full_field(p, st);
+            if (rc) return rc;
+            e = launch_fft_observe(p->L, p->R, p->spins, p->field, p->dparams, p->energy, p->obs, p->theta2,
+                                   b.slots, it, measure_every, st);
+            if (e != cudaSuccess) return cuda_fail(e, "observables");
+        }
+    }
+    e = launch_add_attempted(p->obs, p->R, (long long)nsweeps * p->N(), b.slots, nsweeps, p->N(), st);
+    if (e != cudaSuccess) return cuda_fail(e, "acceptance counters");
+    p->energy_valid = p->packed || measured_last;
+    return MC_OK;
+}
+
 int run_path(mc_lattice *p, int path, int nsweeps, int measure_every, float *trace, cudaStream_t st) {
-    return path == MC_PATH_FFT ? run_fft(p, nsweeps, measure_every, trace, st)
-                               : run_windows(p, path, nsweeps, measure_every, trace, st);
+    if (path == MC_PATH_FFT) return run_fft(p, nsweeps, measure_every, trace, st);
+    if (path == MC_PATH_SPECTRAL) return run_spectral(p, nsweeps, measure_every, trace, st);
+    return run_windows(p, path, nsweeps, measure_every, trace, st);
 }
 
 // The windowed and FFT paths launch several kernels per window or sub-step.  The
@@ -472,8 +558,13 @@ int run_multi(mc_lattice *p, int path, int nsweeps, int measure_every, float *tr
     }
     auto it = p->graphs.find(key);
     if (it == p->graphs.end()) {
-        if (path == MC_PATH_FFT) {  // buffers and tables are made outside the capture
+        // buffers and tables are made outside the capture
+        if (path == MC_PATH_FFT || (path == MC_PATH_SPECTRAL && use_fft_full_field(p))) {
             int rc = ensure_fft(p, st);
+            if (rc) return rc;
+        }
+        if (path == MC_PATH_SPECTRAL) {
+            int rc = ensure_spectral(p, st);
             if (rc) return rc;
         }
         cudaGraph_t g = nullptr;
@@ -497,7 +588,8 @@ int run_multi(mc_lattice *p, int path, int nsweeps, int measure_every, float *tr
     CKA(cudaGraphLaunch(it->second, p->own));
     CKA(cudaEventRecord(p->ev_out, p->own));
     CKA(cudaStreamWaitEvent(st, p->ev_out, 0));
-    if (path == MC_PATH_FFT) p->energy_valid = p->packed || (measure_every > 0 && nsweeps % measure_every == 0);
+    if (path == MC_PATH_FFT || path == MC_PATH_SPECTRAL)
+        p->energy_valid = p->packed || (measure_every > 0 && nsweeps % measure_every == 0);
     return MC_OK;
 }
 
@@ -507,7 +599,7 @@ int run_sweeps(mc_lattice *p, int nsweeps, int measure_every, float *trace, cuda
     if (measure_every < 0) return fail(MC_EINVAL, "measure_every must be >= 0");
     if (nsweeps == 0) return MC_OK;
     const int path0 = resolve_path(p);
-    if (!p->energy_valid && path0 != MC_PATH_FFT) {
+    if (!p->energy_valid && path0 != MC_PATH_FFT && path0 != MC_PATH_SPECTRAL) {
         int rc = anchor_energy(p, st);
         if (rc) return rc;
     }
@@ -672,7 +764,7 @@ int mc_set_field_path(mc_lattice *p, int path) {
     if (p) drop_graphs(p);
     int rc = check(p);
     if (rc) return rc;
-    if (path < MC_PATH_AUTO || path > MC_PATH_FFT) return fail(MC_EINVAL, "unknown field path %d", path);
+    if (path < MC_PATH_AUTO || path > MC_PATH_SPECTRAL) return fail(MC_EINVAL, "unknown field path %d", path);
     if (path != MC_PATH_AUTO && !path_supported(p, path))
         return fail(MC_ENOSYS, "field path %d does not support L=%d l=%d", path, p->L, p->l);
     p->path = path;
@@ -725,6 +817,7 @@ int mc_precompute_W(mc_lattice *p, int A, int tail) {
     p->W_ready = true;
     p->wsh_ready = false;
     p->what_ready = false;
+    p->spec_ready = false;
     p->energy_valid = false;
     return MC_OK;
 }
@@ -916,6 +1009,7 @@ int mc_autotune(mc_lattice *p, int nsweeps_trial, void *stream, int *path_out, i
     }
     p->window_B = old_B;
     if (path_supported(p, MC_PATH_FFT)) cands.push_back({MC_PATH_FFT, 0});
+    if (path_supported(p, MC_PATH_SPECTRAL)) cands.push_back({MC_PATH_SPECTRAL, 0});
     if (cands.empty()) return fail(MC_ENOSYS, "no field path supports L=%d l=%d", p->L, p->l);
     cudaEvent_t a, b;
     CK(cudaEventCreate(&a));
@@ -1051,6 +1145,7 @@ int lattice_copy_W(mc_lattice *p, const double *W64_dev, int A, int tail) {
     p->W_ready = true;
     p->wsh_ready = false;
     p->what_ready = false;
+    p->spec_ready = false;
     p->energy_valid = false;
     return MC_OK;
 }
@@ -1063,6 +1158,10 @@ size_t lattice_footprint(int L, int l, int R) {
                sizeof(float4) * hq * hq + sizeof(SlotState) * R;
     if (fft_supported(L) && (!direct_supported(L, l) || L >= 128))
         b += sizeof(float) * 4 * N + fft_scratch_bytes(L, R) + sizeof(double2) * 4 * N;
+    if ((!direct_supported(L, l) || L >= 128) && spectral_supported(L, l)) {
+        const int es = spectral_esplit(L, l, R, 148);
+        b += sizeof(float2) * (4 * N + spectral_S_elems(L, R) + spectral_part_elems(L, l, R, std::max(es, 16)));
+    }
     return b + 4096;
 }
 
@@ -1072,8 +1171,11 @@ int lattice_resolved_path(mc_lattice *p) { return resolve_path(p); }
 int pack_enable(mc_lattice *p, int path) {
     int rc = check(p);
     if (rc) return rc;
-    if (path == MC_PATH_DIRECT ? !direct_supported(p->L, p->l) : path != MC_PATH_FFT || !fft_supported(p->L))
-        return fail(MC_ENOSYS, "packed launches need the direct or the FFT path");
+    const bool ok = path == MC_PATH_DIRECT     ? direct_supported(p->L, p->l)
+                    : path == MC_PATH_FFT      ? fft_supported(p->L)
+                    : path == MC_PATH_SPECTRAL ? spectral_supported(p->L, p->l)
+                                               : false;
+    if (!ok) return fail(MC_ENOSYS, "packed launches need the direct, FFT or spectral path");
     CK(cudaMalloc(&p->slots_dev, sizeof(SlotState) * p->R));
     CK(cudaMallocHost(&p->slots_pin, sizeof(SlotState) * p->R));
     CK(cudaMallocHost(&p->params_pin, sizeof(RepParams) * p->R));
@@ -1108,8 +1210,8 @@ int pack_fill(mc_lattice *p, int slot, int count, uint64_t seed, const RepParams
     CK(cudaMemsetAsync(p->obs + slot, 0, sizeof(ObsAcc) * count, st));
     CK(cudaMemsetAsync(p->theta2 + (size_t)slot * N, 0, sizeof(double) * N * count, st));
     p->last = st;
-    if (p->path == MC_PATH_FFT) {
-        // the FFT path measures the energy afresh; NaN (all bits set) until then,
+    if (p->path == MC_PATH_FFT || p->path == MC_PATH_SPECTRAL) {
+        // these paths measure the energy afresh; NaN (all bits set) until then,
         // as a lone handle reports before its first measurement
         CK(cudaMemsetAsync(p->energy + slot, 0xFF, sizeof(double) * count, st));
         return MC_OK;
@@ -1139,13 +1241,13 @@ int pack_launch(mc_lattice *p, int measure_every, cudaStream_t st, int *launched
     std::memcpy(p->slots_pin, p->slots_host.data(), sizeof(SlotState) * p->R);
     CK(cudaMemcpyAsync(p->slots_dev, p->slots_pin, sizeof(SlotState) * p->R, cudaMemcpyHostToDevice, st));
     CK(cudaEventRecord(p->slots_copied, st));
-    if (p->path == MC_PATH_FFT) {
-        // the FFT pack replays a captured graph per sweep count; round the count
-        // up to a power of two (slots past their own count idle) so that a pack
+    if (p->path == MC_PATH_FFT || p->path == MC_PATH_SPECTRAL) {
+        // these packs replay a captured graph per sweep count; round the count up
+        // to a power of two (slots past their own count idle) so that a pack
         // needs only a few graphs
         int g = 1;
         while (g < mx) g <<= 1;
-        int rc = run_multi(p, MC_PATH_FFT, g, measure_every, nullptr, st);
+        int rc = run_multi(p, p->path, g, measure_every, nullptr, st);
         if (rc) return rc;
     } else {
         int rc = pack_launch_direct(p, mx, measure_every, st);

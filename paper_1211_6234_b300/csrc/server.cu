@@ -5,10 +5,11 @@
 // requests, each slot carrying its own Philox key, sweep counter and sweep
 // budget, so one launch advances many independent chains and each chain is
 // bit-identical to the same request run alone.  Packs use the direct path
-// (one CTA per slot, as many slots as CTAs fit on the GPU at once) or, for
-// large power-of-two L, the FFT path (R slots share every FFT launch).  Other
-// requests (windowed path) get a lone handle of their own from a pool.  Packs
-// and lone handles run on separate streams, so their work overlaps on the GPU.
+// (one CTA per slot, as many slots as CTAs fit on the GPU at once) for small
+// lattices and the sub-lattice spectral path (or the FFT path) for large ones,
+// where all slots share every launch.  Requests too large for a pack get a lone
+// handle of their own from a pool.  Packs and lone handles run on separate
+// streams, so their work overlaps on the GPU.
 //
 // mc_server_step() is the whole scheduler and never waits for the GPU:
 //   1. retire: a pack or lone handle whose last launch finished credits the
@@ -36,6 +37,7 @@
 
 #include "fft_field.cuh"
 #include "internal.cuh"
+#include "spectral.cuh"
 
 namespace dipmc {
 int lattice_copy_W(mc_lattice *p, const double *W64_dev, int A, int tail);
@@ -63,19 +65,25 @@ double now_s() {
 // measurement interval.
 using PackKey = std::tuple<int, int, int, int, double, int>;
 
-// Sites of all slots of an FFT pack: enough replicas per launch to fill the GPU
-// with the FFT's row and transpose blocks.
-constexpr long long kFftPackSites = 1LL << 20;
+// Sites of all slots of a spectral or FFT pack: enough replicas per launch to
+// fill the GPU with the contraction's (or the FFT's) blocks.
+constexpr long long kPackSites = 1LL << 21;
 
 // Path and slot count of a pack for (L, l), or path -1 if requests of this
-// shape run on lone handles.
+// shape run on lone handles.  Small lattices: the direct kernel, one CTA per
+// slot; else the sub-lattice spectral path; else the full-lattice FFT.
 int pack_shape(int L, int l, int *cap) {
+    const long long N = (long long)L * L;
     if (direct_supported(L, l) && L < 128) {
         *cap = std::max(1, direct_resident_ctas(L, l));
         return MC_PATH_DIRECT;
     }
+    if (spectral_supported(L, l)) {
+        *cap = (int)std::max(1LL, std::min(256LL, kPackSites / N));
+        return MC_PATH_SPECTRAL;
+    }
     if (fft_supported(L)) {
-        *cap = (int)std::max(1LL, std::min(64LL, kFftPackSites / ((long long)L * L)));
+        *cap = (int)std::max(1LL, std::min(64LL, kPackSites / N));
         return MC_PATH_FFT;
     }
     *cap = 0;

@@ -1,0 +1,437 @@
+// spectral.cu -- the dipole field at a sub-step's update sites by sub-lattice
+// spectra, and the sweep path built on it (Sec. 3.1, 3.2 update; Eq. 2 field).
+//
+// With C = L/l, every site is m = e + l*D (cell offset e in [0, l)^2, coarse
+// position D in [0, C)^2), and the update sites of offset o are q = o + l*Dq.
+// Their field splits into l^2 circular convolutions on the C x C coarse grid:
+//     h(o + l*Dq) = sum_e sum_Dm W~(o - e + l*(Dq - Dm)) s(e + l*Dm).
+// With the C x C DFT (omega = exp(-2 pi i / C)), S_e(K) = DFT_D s(e + l*D) and
+// T_d(K) = DFT_D W~(d + l*D) for d in [0, l)^2, the convolution theorem gives
+//     H_o(K) = sum_e omega^(K . sigma) T_{(o - e) mod l}(K) S_e(K),
+// sigma_x = 1 where o_x < e_x (and likewise y): the wrap of o - e into [0, l)
+// shifts the coarse sequence by one cell.  h at the n sites is the inverse DFT
+// of H_o.  Only S_o changes in a sub-step (the update sites are exactly the
+// sub-lattice of offset o), so after the update S_o is recomputed from the new
+// spins.  A sub-step therefore costs O(N) -- the contraction over e -- instead
+// of the O(N n) of a direct sum or the O(N log N) of a full-lattice FFT.
+//
+// Kernels per sub-step: k_spec_field (contraction; grid over (replica, K)
+// pairs and chunks of e, partial spectra reduced in a fixed order) and
+// k_spec_update (one CTA per replica: inverse DFT, Metropolis decisions,
+// forward DFT of the updated sub-lattice).  DFTs are separable direct sums in
+// shared memory (C <= 32).  T is built once in FP64.
+#include <algorithm>
+
+#include "spectral.cuh"
+
+namespace dipmc {
+
+namespace {
+
+constexpr int kSpecThreads = 256;
+constexpr int kSpecMaxC = 32;
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {  // a*b + c
+    return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
+}
+// omega^m = exp(-2 pi i m / C), m in [0, C)
+__device__ __forceinline__ float2 omega(int m, int C) {
+    float s, c;
+    sincospif(2.0f * (float)m / (float)C, &s, &c);
+    return make_float2(c, -s);
+}
+
+// Stream state of replica r: its key, its sweep counter at sweep `it` of the
+// call and the replica index its counters use; false for an idle slot.
+__device__ __forceinline__ bool stream_state(const SpecConfig &cfg, const SpecBuffers &b, int r, uint2 &key,
+                                             uint32_t &t, uint32_t &rid) {
+    key = cfg.key;
+    t = cfg.t_dev ? *cfg.t_dev + (uint32_t)cfg.it : cfg.t;
+    rid = (uint32_t)r;
+    if (b.slots) {
+        const SlotState sl = b.slots[r];
+        if (cfg.it >= sl.nsweeps) return false;
+        key = make_uint2(sl.key_lo, sl.key_hi);
+        t = sl.t0 + (uint32_t)cfg.it;
+        rid = sl.rid;
+    }
+    return true;
+}
+
+// Offset (ox, oy) of sub-step k of sweep t (the schedule of the other paths).
+__device__ __forceinline__ void sub_offset(const SpecConfig &cfg, uint2 key, uint32_t t, int &ox, int &oy) {
+    const int l = cfg.l, ll = l * l;
+    const uint32_t k = (uint32_t)cfg.k;
+    uint32_t v;
+    if (cfg.schedule == 0) {
+        const uint4 rk = philox(make_uint4(t, 0u, 0u, kTagPerm), key);
+        v = perm_offset(rk, ceil_log2_u((uint32_t)l), (uint32_t)ll, k);
+    } else {
+        const uint4 o = philox(make_uint4(t, k, 0u, kTagDraw), key);
+        v = (uint32_t)(((unsigned long long)o.x * (unsigned long long)ll) >> 32);
+    }
+    ox = (int)(v % l);
+    oy = (int)(v / l);
+}
+
+__device__ __forceinline__ void perp_basis_s(float nx, float ny, float nz, float3 &b1, float3 &b2) {
+    const float sign = copysignf(1.0f, nz);
+    const float a = -1.0f / (sign + nz);
+    const float bb = nx * ny * a;
+    b1 = make_float3(1.0f + sign * nx * nx * a, sign * bb, -sign * nx);
+    b2 = make_float3(bb, sign + ny * ny * a, -ny);
+}
+
+// ---------------------------------------------------------------------------
+// T_d^c(K) = sum_D W~_c(d + l*D) omega^(K.D): one CTA per (d, c), FP64.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSpecThreads) k_spec_table(int L, int l, const double *__restrict__ W64,
+                                                             float2 *__restrict__ T) {
+    const int C = L / l, n = C * C, N = L * L;
+    const int d = blockIdx.x >> 2, c = blockIdx.x & 3;
+    const int dx = d % l, dy = d / l;
+    extern __shared__ double2 sm_d[];
+    double2 *U = sm_d;           // [Dy][Kx]
+    double2 *tw = sm_d + n;      // [C]
+    for (int m = threadIdx.x; m < C; m += blockDim.x) {
+        double s, co;
+        sincospi(2.0 * (double)m / (double)C, &s, &co);
+        tw[m] = make_double2(co, -s);
+    }
+    __syncthreads();
+    const double *w = W64 + (size_t)c * N;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int Dy = i / C, Kx = i % C;
+        const double *row = w + (size_t)(dy + l * Dy) * L + dx;
+        double re = 0, im = 0;
+        for (int Dx = 0; Dx < C; ++Dx) {
+            const double v = row[l * Dx];
+            const double2 o = tw[(Kx * Dx) % C];
+            re += v * o.x;
+            im += v * o.y;
+        }
+        U[i] = make_double2(re, im);
+    }
+    __syncthreads();
+    float2 *out = T + ((size_t)d * 4 + c) * n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int Ky = i / C, Kx = i % C;
+        double re = 0, im = 0;
+        for (int Dy = 0; Dy < C; ++Dy) {
+            const double2 u = U[Dy * C + Kx], o = tw[(Ky * Dy) % C];
+            re += u.x * o.x - u.y * o.y;
+            im += u.x * o.y + u.y * o.x;
+        }
+        out[i] = make_float2((float)re, (float)im);
+    }
+}
+
+// Forward DFT of three real C x C planes in shared memory (x[3][n]) into
+// out[3][n] (global), through U[3][n]; tw = omega^m.
+__device__ __forceinline__ void dft3_forward(const float *x, float2 *U, const float2 *tw, int C, float2 *out,
+                                             size_t out_stride) {
+    const int n = C * C;
+    for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
+        const int b = i / n, j = i % n, Dy = j / C, Kx = j % C;
+        const float *row = x + b * n + Dy * C;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int Dx = 0; Dx < C; ++Dx) {
+            const float2 o = tw[(Kx * Dx) % C];
+            acc.x = fmaf(row[Dx], o.x, acc.x);
+            acc.y = fmaf(row[Dx], o.y, acc.y);
+        }
+        U[i] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
+        const int b = i / n, j = i % n, Ky = j / C, Kx = j % C;
+        const float2 *col = U + b * n + Kx;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int Dy = 0; Dy < C; ++Dy) acc = cfma(col[Dy * C], tw[(Ky * Dy) % C], acc);
+        out[(size_t)b * out_stride + j] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// S_e for every (replica, cell offset): one CTA per (e, r).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSpecThreads) k_spec_init(int L, int l, const float *__restrict__ spins,
+                                                            float2 *__restrict__ S) {
+    const int C = L / l, n = C * C, N = L * L, ll = l * l;
+    const int e = blockIdx.x, r = blockIdx.y;
+    const int ex = e % l, ey = e / l;
+    extern __shared__ float2 sm_f2[];
+    float2 *tw = sm_f2;                                         // [C]
+    float2 *U = tw + kSpecMaxC;                                 // [3][n]
+    float *x = reinterpret_cast<float *>(U + 3 * n);            // [3][n]
+    for (int m = threadIdx.x; m < C; m += blockDim.x) tw[m] = omega(m, C);
+    const float *s = spins + (size_t)r * 3 * N;
+    for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
+        const int b = i / n, D = i % n;
+        x[i] = s[(size_t)b * N + (size_t)(ey + l * (D / C)) * L + ex + l * (D % C)];
+    }
+    __syncthreads();
+    dft3_forward(x, U, tw, C, S + ((size_t)r * ll + e) * 3 * n, (size_t)n);
+}
+
+// ---------------------------------------------------------------------------
+// Partial field spectra: thread = (replica r, wave vector K) x a slice of the
+// cell offsets e; the 8 warps of a CTA take interleaved e of the CTA's chunk and
+// are summed in a fixed order.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSpecThreads) k_spec_field(const SpecConfig cfg, const SpecBuffers b) {
+    const int L = cfg.L, l = cfg.l, C = L / l, n = C * C, ll = l * l, R = cfg.R;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int j = blockIdx.x * 32 + lane;
+    const int r = j < R * n ? j / n : 0, K = j < R * n ? j % n : 0;
+    uint2 key;
+    uint32_t t, rid;
+    const bool active = j < R * n && stream_state(cfg, b, r, key, t, rid);
+    float2 hx = make_float2(0.f, 0.f), hy = hx, hz = hx;
+    if (active) {
+        int ox, oy;
+        sub_offset(cfg, key, t, ox, oy);
+        const int Kx = K % C, Ky = K / C;
+        float2 ph[4];
+        ph[0] = make_float2(1.f, 0.f);
+        ph[1] = omega(Kx, C);
+        ph[2] = omega(Ky, C);
+        ph[3] = omega((Kx + Ky) % C, C);
+        const int ec = (ll + gridDim.y - 1) / gridDim.y;
+        const int e0 = blockIdx.y * ec, e1 = min(ll, e0 + ec);
+        const float2 *Sr = b.S + (size_t)r * ll * 3 * n + K;
+        for (int e = e0 + w; e < e1; e += kSpecThreads / 32) {
+            const int ex = e % l, ey = e / l;
+            int dx = ox - ex, dy = oy - ey;
+            const int sx = dx < 0, sy = dy < 0;
+            dx += sx ? l : 0;
+            dy += sy ? l : 0;
+            const float2 *Tp = b.T + (size_t)(dy * l + dx) * 4 * n + K;
+            const float2 p = ph[sx + 2 * sy];
+            const float2 txx = cmul(__ldg(Tp), p), txy = cmul(__ldg(Tp + n), p);
+            const float2 tyy = cmul(__ldg(Tp + 2 * n), p), tzz = cmul(__ldg(Tp + 3 * n), p);
+            const float2 *Sp = Sr + (size_t)e * 3 * n;
+            const float2 s0 = Sp[0], s1 = Sp[n], s2 = Sp[2 * n];
+            hx = cfma(txx, s0, cfma(txy, s1, hx));
+            hy = cfma(txy, s0, cfma(tyy, s1, hy));
+            hz = cfma(tzz, s2, hz);
+        }
+    }
+    __shared__ float2 red[kSpecThreads / 32][3][32];
+    red[w][0][lane] = hx;
+    red[w][1][lane] = hy;
+    red[w][2][lane] = hz;
+    __syncthreads();
+    if (active && w < 3) {
+        float2 acc = red[0][w][lane];
+        for (int v = 1; v < kSpecThreads / 32; ++v) {
+            acc.x += red[v][w][lane].x;
+            acc.y += red[v][w][lane].y;
+        }
+        b.Hpart[(((size_t)blockIdx.y * R + r) * 3 + w) * n + K] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Per replica: field at the n sites (inverse DFT of the summed partial spectra),
+// Metropolis decisions, new S of the updated offset.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSpecThreads) k_spec_update(const SpecConfig cfg, const SpecBuffers b) {
+    const int L = cfg.L, l = cfg.l, C = L / l, n = C * C, ll = l * l, N = L * L, R = cfg.R;
+    const int r = blockIdx.x;
+    uint2 key;
+    uint32_t t, rid;
+    if (!stream_state(cfg, b, r, key, t, rid)) return;  // whole block, before any barrier
+    int ox, oy;
+    sub_offset(cfg, key, t, ox, oy);
+    extern __shared__ float2 sm_f2[];
+    float2 *tw = sm_f2;                                          // [C]
+    float2 *H = tw + kSpecMaxC;                                  // [3][n]
+    float2 *U = H + 3 * n;                                       // [3][n]
+    float *hs = reinterpret_cast<float *>(U + 3 * n);            // [3][n] field at the sites
+    float *sn = hs + 3 * n;                                      // [3][n] spins after the update
+    __shared__ int s_acc;
+    if (threadIdx.x == 0) s_acc = 0;
+    for (int m = threadIdx.x; m < C; m += blockDim.x) tw[m] = omega(m, C);
+    for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
+        float2 acc = b.Hpart[((size_t)r * 3) * n + i];
+        for (int z = 1; z < cfg.esplit; ++z) {
+            const float2 v = b.Hpart[(((size_t)z * R + r) * 3) * n + i];
+            acc.x += v.x;
+            acc.y += v.y;
+        }
+        H[i] = acc;
+    }
+    __syncthreads();
+    // inverse DFT: over Kx, then over Ky (conjugate twiddles), real part / n
+    for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
+        const int a = i / n, jj = i % n, Ky = jj / C, Dx = jj % C;
+        const float2 *row = H + a * n + Ky * C;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int Kx = 0; Kx < C; ++Kx) {
+            const float2 o = tw[(Kx * Dx) % C];
+            acc = cfma(row[Kx], make_float2(o.x, -o.y), acc);
+        }
+        U[i] = acc;
+    }
+    __syncthreads();
+    const float inv_n = 1.0f / (float)n;
+    for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
+        const int a = i / n, jj = i % n, Dy = jj / C, Dx = jj % C;
+        const float2 *col = U + a * n + Dx;
+        float re = 0.f;
+        for (int Ky = 0; Ky < C; ++Ky) {
+            const float2 u = col[Ky * C], o = tw[(Ky * Dy) % C];
+            re = fmaf(u.x, o.x, fmaf(u.y, o.y, re));   // Re(u * conj(o))
+        }
+        hs[i] = re * inv_n;
+    }
+    __syncthreads();
+    // the sub-step's n sites (numbered as in the other paths: d -> (d % C, d / C))
+    float *s = b.spins + (size_t)r * 3 * N;
+    const RepParams P = b.params[r];
+    const float W0xx = __ldg(b.W32), W0xy = __ldg(b.W32 + N), W0yy = __ldg(b.W32 + 2 * N), W0zz = __ldg(b.W32 + 3 * N);
+    int nacc = 0;
+    for (int d = threadIdx.x; d < n; d += blockDim.x) {
+        const int qx = ox + l * (d % C), qy = oy + l * (d / C);
+        const int q = qy * L + qx;
+        const uint4 wds = philox(make_uint4((uint32_t)q, rid, t, ((uint32_t)cfg.k & 0x00FFFFFFu) | kTagAttempt), key);
+        const float u1 = u24f(wds.x), uacc = u24f(wds.z);
+        float sps, cps;
+        sincospif(2.0f * u24f(wds.y), &sps, &cps);
+        const float s0 = s[q], s1 = s[N + q], s2 = s[2 * N + q];
+        float S0, S1, S2;
+        if (cfg.proposal == 1) {
+            const float z = 2.0f * u1 - 1.0f;
+            const float rr = sqrtf(fmaxf(0.0f, (1.0f - z) * (1.0f + z)));
+            S0 = rr * cps;
+            S1 = rr * sps;
+            S2 = z;
+        } else {
+            const float omc = u1 * cfg.cap_c1;             // 1 - cos(alpha), no cancellation
+            const float ca = 1.0f - omc;
+            const float sa = sqrtf(fmaxf(0.0f, omc * (2.0f - omc)));
+            float3 b1, b2;
+            perp_basis_s(s0, s1, s2, b1, b2);
+            S0 = ca * s0 + sa * (cps * b1.x + sps * b2.x);
+            S1 = ca * s1 + sa * (cps * b1.y + sps * b2.y);
+            S2 = ca * s2 + sa * (cps * b1.z + sps * b2.z);
+            const float inv = 1.0f / sqrtf(S0 * S0 + S1 * S1 + S2 * S2);
+            S0 *= inv;
+            S1 *= inv;
+            S2 *= inv;
+        }
+        const float dX = S0 - s0, dY = S1 - s1, dZ = S2 - s2;
+        const int xp = (qx + 1 == L) ? q - qx : q + 1;
+        const int xm = (qx == 0) ? q + L - 1 : q - 1;
+        const int yp = (qy + 1 == L) ? qx : q + L;
+        const int ym = (qy == 0) ? q + N - L : q - L;
+        const float n0 = (s[xp] + s[xm]) + (s[yp] + s[ym]);
+        const float n1 = (s[N + xp] + s[N + xm]) + (s[N + yp] + s[N + ym]);
+        const float n2 = (s[2 * N + xp] + s[2 * N + xm]) + (s[2 * N + yp] + s[2 * N + ym]);
+        const float dex = -P.J * (dX * n0 + dY * n1 + dZ * n2);
+        const float z0 = s2 * s2, z1 = S2 * S2;
+        const float dan = (-P.K2 * z1 - P.K4 * z1 * z1) - (-P.K2 * z0 - P.K4 * z0 * z0);
+        const float self = W0xx * dX * dX + 2.0f * W0xy * dX * dY + W0yy * dY * dY + W0zz * dZ * dZ;
+        const float h0 = hs[d], h1 = hs[n + d], h2 = hs[2 * n + d];
+        const float dE = dex + dan + P.CD * ((dX * h0 + dY * h1 + dZ * h2) + 0.5f * self);
+        const float thr = (uacc > 0.0f) ? -P.T * logf(uacc) : INFINITY;
+        const int accept = dE < thr;
+        if (b.trace) {
+            float *tr = b.trace + ((((size_t)r * cfg.nsweeps_call + cfg.it) * ll + cfg.k) * n + d) * MC_TRACE_W;
+            tr[0] = (float)q;
+            tr[1] = h0; tr[2] = h1; tr[3] = h2;
+            tr[4] = dE;
+            tr[5] = uacc;
+            tr[6] = (float)accept;
+            tr[7] = S0; tr[8] = S1; tr[9] = S2;
+        }
+        sn[d] = accept ? S0 : s0;
+        sn[n + d] = accept ? S1 : s1;
+        sn[2 * n + d] = accept ? S2 : s2;
+        nacc += accept;
+    }
+    // every read of the pre-step spins is done before any write (neighbours of
+    // update sites are never update sites, but keep the phases separate)
+    __syncthreads();
+    for (int d = threadIdx.x; d < n; d += blockDim.x) {
+        const int q = (oy + l * (d / C)) * L + ox + l * (d % C);
+        s[q] = sn[d];
+        s[N + q] = sn[n + d];
+        s[2 * N + q] = sn[2 * n + d];
+    }
+    if (nacc) atomicAdd(&s_acc, nacc);
+    dft3_forward(sn, U, tw, C, b.S + ((size_t)r * ll + (oy * l + ox)) * 3 * n, (size_t)n);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_acc && b.obs)
+        atomicAdd((unsigned long long *)&b.obs[r].accepted, (unsigned long long)s_acc);
+}
+
+size_t update_smem(int C) {
+    const size_t n = (size_t)C * C;
+    return sizeof(float2) * (kSpecMaxC + 6 * n) + sizeof(float) * 6 * n;
+}
+
+size_t init_smem(int C) {
+    const size_t n = (size_t)C * C;
+    return sizeof(float2) * (kSpecMaxC + 3 * n) + sizeof(float) * 3 * n;
+}
+
+}  // namespace
+
+bool spectral_supported(int L, int l) {
+    if (l < 2 || L % l) return false;
+    const int C = L / l;
+    return C >= 2 && C <= kSpecMaxC && L <= 4096;
+}
+
+int spectral_esplit(int L, int l, int R, int nsm) {
+    const long long n = (long long)(L / l) * (L / l), ll = (long long)l * l;
+    const long long tiles = (R * n + 31) / 32;
+    long long z = (4LL * nsm + tiles - 1) / tiles;
+    z = std::min(z, std::max(1LL, ll / 16));  // every warp keeps at least two cell offsets
+    return (int)std::max(1LL, z);
+}
+
+size_t spectral_S_elems(int L, int R) { return (size_t)3 * L * L * R; }
+
+size_t spectral_part_elems(int L, int l, int R, int esplit) {
+    return (size_t)esplit * R * 3 * (L / l) * (L / l);
+}
+
+cudaError_t launch_spec_table(int L, int l, const double *W64, float2 *T, cudaStream_t st) {
+    const int C = L / l;
+    const size_t smem = sizeof(double2) * ((size_t)C * C + C);
+    cudaError_t e = cudaFuncSetAttribute(k_spec_table, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_spec_table<<<l * l * 4, kSpecThreads, smem, st>>>(L, l, W64, T);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spec_init(int L, int l, int R, const float *spins, float2 *S, cudaStream_t st) {
+    const size_t smem = init_smem(L / l);
+    cudaError_t e = cudaFuncSetAttribute(k_spec_init, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_spec_init<<<dim3(l * l, R), kSpecThreads, smem, st>>>(L, l, spins, S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spec_field(const SpecConfig &c, const SpecBuffers &b, cudaStream_t st) {
+    const int C = c.L / c.l, n = C * C;
+    const unsigned tiles = (unsigned)((c.R * n + 31) / 32);
+    k_spec_field<<<dim3(tiles, c.esplit), kSpecThreads, 0, st>>>(c, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spec_update(const SpecConfig &c, const SpecBuffers &b, cudaStream_t st) {
+    const size_t smem = update_smem(c.L / c.l);
+    cudaError_t e = cudaFuncSetAttribute(k_spec_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_spec_update<<<c.R, kSpecThreads, smem, st>>>(c, b);
+    return cudaGetLastError();
+}
+
+}  // namespace dipmc

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libdipmc.so")
 MC_OK, MC_EINVAL, MC_ENOMEM, MC_ENOTREADY, MC_ETIMEOUT, MC_ECUDA, MC_ENOSYS = 0, -1, -2, -3, -4, -5, -6
 MC_NOBS = 5
 OBS_NAMES = ("abs_m", "m_z", "abs_m_z", "m_par", "e")
-MC_PATH_AUTO, MC_PATH_DIRECT, MC_PATH_WINDOW_F32, MC_PATH_TENSOR, MC_PATH_FFT = 0, 1, 2, 3, 4
+MC_PATH_AUTO, MC_PATH_DIRECT, MC_PATH_WINDOW_F32, MC_PATH_TENSOR, MC_PATH_FFT, MC_PATH_SPECTRAL = 0, 1, 2, 3, 4, 5
 MC_TRACE_W = 10
 
 # Every symbol include/dipmc.h declares.
@@ -34,7 +34,7 @@ ABI_SYMBOLS = (
     "mc_server_collect", "mc_server_get_spins", "mc_server_release", "mc_server_get_stats", "mc_server_destroy",
 )
 MC_REQ_QUEUED, MC_REQ_RUNNING, MC_REQ_DONE, MC_REQ_FAILED, MC_REQ_RELEASED = range(5)
-KERNEL_CLASSES = ("sweep_direct", "tc_field", "window_steps", "full_field")
+KERNEL_CLASSES = ("sweep_direct", "tc_field", "window_steps", "full_field", "spec_field", "spec_update")
 
 
 class McError(RuntimeError):
@@ -86,7 +86,7 @@ class mc_server_stats(C.Structure):
 
 
 class mc_timing(C.Structure):
-    _fields_ = [("launches", C.c_int64 * 4), ("ms", C.c_double * 4)]
+    _fields_ = [("launches", C.c_int64 * 6), ("ms", C.c_double * 6)]
 
 
 def _load():

@@ -434,17 +434,26 @@ def test_fft_full_field_L256_sampled_sites(dipmc):
 
 
 FCASES = [
-    # L, l, R, schedule, nsweeps
-    (16, 8, 2, 0, 2),
-    (32, 8, 2, 0, 1),      # 16 simultaneous sites
-    (64, 16, 1, 1, 1),     # the paper's with-replacement schedule
-    (128, 64, 1, 0, 1),    # large lattice, 4 sites per sub-step
+    # path, L, l, R, schedule, nsweeps
+    (4, 16, 8, 2, 0, 2),
+    (4, 32, 8, 2, 0, 1),      # 16 simultaneous sites
+    (4, 64, 16, 1, 1, 1),     # the paper's with-replacement schedule
+    (4, 128, 64, 1, 0, 1),    # large lattice, 4 sites per sub-step
+    (5, 16, 8, 2, 0, 2),      # spectral path: 2 x 2 coarse grid
+    (5, 32, 8, 2, 1, 1),      # 4 x 4, with-replacement schedule
+    (5, 48, 16, 2, 0, 1),     # L not a power of two, odd coarse grid (3 x 3)
+    (5, 96, 12, 1, 0, 1),     # 8 x 8 coarse grid, L not a power of two
+    (5, 128, 8, 1, 0, 1),     # 16 x 16 coarse grid, 256 simultaneous sites
 ]
 
 
-@pytest.mark.parametrize("case", FCASES, ids=[f"L{c[0]}_l{c[1]}_R{c[2]}_s{c[3]}" for c in FCASES])
+@pytest.mark.parametrize("case", FCASES, ids=[f"{'fft' if c[0] == 4 else 'spec'}_L{c[1]}_l{c[2]}_R{c[3]}_s{c[4]}"
+                                              for c in FCASES])
 def test_fft_path_trace_matches_oracle(dipmc, case):
-    L, l, R, schedule, nsw = case
+    """FFT (full-lattice transform per sub-step) and spectral (sub-lattice
+    spectra) paths against the oracle's sweep: field at every update site,
+    dE, decisions and final spins."""
+    path, L, l, R, schedule, nsw = case
     params = [(F32(1.0), F32(0.1), F32(0.8), F32(0.0), F32(0.6)),
               (F32(0.7), F32(0.3), F32(0.5), F32(-0.2), F32(1.1))][:R]
     seed = 500 + L + l
@@ -452,7 +461,7 @@ def test_fft_path_trace_matches_oracle(dipmc, case):
     A = 16
     with dipmc.Lattice(L, l, R, seed) as lat:
         lat.precompute_W(A, True)
-        lat.set_field_path(dipmc.MC_PATH_FFT)
+        lat.set_field_path(path)
         lat.set_schedule(schedule)
         for r, prm in enumerate(params):
             lat.set_params(*prm, replica=r)
@@ -470,11 +479,13 @@ def test_fft_path_trace_matches_oracle(dipmc, case):
             np.testing.assert_allclose(sg[r], o["s"], rtol=0, atol=1e-5)
 
 
-def test_fft_path_observables_match_direct(dipmc):
-    """The FFT and direct paths sample the same law (L = 16, pooled replicas)."""
+@pytest.mark.parametrize("other", [4, 5], ids=["fft", "spectral"])
+def test_fft_path_observables_match_direct(dipmc, other):
+    """The FFT and spectral paths sample the same law as the direct path (L = 16,
+    pooled replicas)."""
     L, l, R, nsw = 16, 8, 32, 400
     res = {}
-    for path in (dipmc.MC_PATH_DIRECT, dipmc.MC_PATH_FFT):
+    for path in (dipmc.MC_PATH_DIRECT, other):
         with dipmc.Lattice(L, l, R, 31 if path == 1 else 32) as lat:
             lat.precompute_W(64, True)
             lat.set_field_path(path)
@@ -484,18 +495,18 @@ def test_fft_path_observables_match_direct(dipmc):
             lat.reset_observables()
             lat.sweep(nsw, 1)
             res[path] = [lat.observables(r) for r in range(R)]
-    for o in res[4]:
+    for o in res[other]:
         assert o["samples"] == nsw and o["attempted"] == nsw * L * L
     for nm in ("abs_m", "e"):
         a = np.array([o[nm]["mean"] for o in res[1]])
-        b = np.array([o[nm]["mean"] for o in res[4]])
+        b = np.array([o[nm]["mean"] for o in res[other]])
         ea = np.sqrt(np.mean([o[nm]["err"] ** 2 for o in res[1]]) / R)
-        eb = np.sqrt(np.mean([o[nm]["err"] ** 2 for o in res[4]]) / R)
+        eb = np.sqrt(np.mean([o[nm]["err"] ** 2 for o in res[other]]) / R)
         assert abs(a.mean() - b.mean()) < 4 * math.hypot(ea, eb) + 1e-9, (nm, a.mean(), b.mean(), ea, eb)
 
 
 # ---------------------------------------------------------------- graphs and autotuning
-@pytest.mark.parametrize("path", [3, 4], ids=["tensor", "fft"])
+@pytest.mark.parametrize("path", [3, 4, 5], ids=["tensor", "fft", "spectral"])
 def test_graph_replay_is_bit_identical(dipmc, path):
     """Repeated calls of the windowed / FFT paths replay a captured CUDA graph; three
     calls of 2 sweeps must equal one direct call of 6 sweeps bit for bit."""
@@ -526,7 +537,7 @@ def test_autotune_keeps_state_and_picks_a_path(dipmc):
         before = lat.get_spins()
         t0 = lat.sweep_counter()
         path, win = lat.autotune(1)
-        assert path in (dipmc.MC_PATH_DIRECT, dipmc.MC_PATH_TENSOR, dipmc.MC_PATH_FFT)
+        assert path in (dipmc.MC_PATH_DIRECT, dipmc.MC_PATH_TENSOR, dipmc.MC_PATH_FFT, dipmc.MC_PATH_SPECTRAL)
         assert np.array_equal(lat.get_spins(), before) and lat.sweep_counter() == t0
         lat.sweep(2, 1)
         assert lat.observables(0)["samples"] == 2

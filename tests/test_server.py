@@ -77,7 +77,7 @@ def dipmc():
 @gpu
 def test_packed_requests_equal_their_lone_runs(dipmc):
     """Requests of several (L, l) groups and lengths share packed launches (direct
-    packs at L = 32, 64; an FFT pack at L = 128), advanced in quanta that do not
+    packs at L = 32, 64; a spectral pack at L = 128), advanced in quanta that do not
     divide their sweep counts; every one matches its lone run bit for bit,
     multi-replica requests included."""
     specs = [
@@ -97,7 +97,7 @@ def test_packed_requests_equal_their_lone_runs(dipmc):
             info = srv.info(rid)
             assert info["state"] == dipmc.MC_REQ_DONE, info
             assert info["packed"] and info["sweeps_done"] == s["sweeps"]
-            assert info["path"] == (dipmc.MC_PATH_FFT if s["L"] == 128 else dipmc.MC_PATH_DIRECT)
+            assert info["path"] == (dipmc.MC_PATH_SPECTRAL if s["L"] == 128 else dipmc.MC_PATH_DIRECT)
             spins_lone, obs_lone = lone_run(dipmc, **s)
             np.testing.assert_array_equal(srv.spins(rid), spins_lone)
             for r in range(s.get("replicas", 1)):
@@ -110,18 +110,18 @@ def test_packed_requests_equal_their_lone_runs(dipmc):
 @gpu
 def test_lone_handle_requests_equal_their_lone_runs(dipmc):
     """Requests with more replicas than a pack holds run on pooled lone handles
-    (direct path at L = 64, FFT path at L = 256) beside a pack and match their
+    (direct path at L = 64, spectral path at L = 256) beside a pack and match their
     lone runs; a later request of the same shape reuses a pooled handle.  A
-    shape no path serves (L/l = 3) fails alone, with its reason, and stops
-    nothing."""
+    shape no path serves (L = 96, l = 2: L/l = 48) fails alone, with its reason,
+    and stops nothing."""
     specs = [
         dict(L=64, l=32, T=0.8, sweeps=4, seed=22, replicas=300),
-        dict(L=256, l=16, T=0.7, sweeps=2, seed=25, replicas=17),
+        dict(L=256, l=16, T=0.7, sweeps=2, seed=25, replicas=40),
         dict(L=32, l=8, T=0.7, sweeps=12, seed=23),
         dict(L=64, l=32, T=0.5, sweeps=3, seed=26, K4=-0.1, replicas=300),
     ]
     with dipmc.Server(hbm_budget_bytes=8 << 30, quantum_sweeps=2) as srv:
-        bad = srv.submit(L=48, l=16, T=0.8, sweeps=2, seed=1)
+        bad = srv.submit(L=96, l=2, T=0.8, sweeps=2, seed=1)
         ids = [srv.submit(**s) for s in specs]
         srv.run_until_done(ids + [bad], timeout_s=300)
         info = srv.info(bad)
@@ -135,7 +135,7 @@ def test_lone_handle_requests_equal_their_lone_runs(dipmc):
             for r in (0, s.get("replicas", 1) - 1):
                 same_obs(srv.collect(rid, r), obs_lone[r])
         st = srv.stats()
-        assert st["lone"] == 4 and st["failed"] == 1     # L=48 (failed), 2 x L=64, L=256
+        assert st["lone"] == 4 and st["failed"] == 1     # L=96 (failed), 2 x L=64, L=256
         again = dict(L=64, l=32, T=0.6, sweeps=2, seed=27, replicas=300)
         rid = srv.submit(**again)
         srv.run_until_done([rid], timeout_s=120)
@@ -145,7 +145,7 @@ def test_lone_handle_requests_equal_their_lone_runs(dipmc):
 
 @gpu
 def test_admission_waits_for_budget_in_arrival_order(dipmc):
-    """With room for one L=128 slot only, the FFT pack shrinks to one slot and
+    """With room for one L=128 slot only, the spectral pack shrinks to one slot and
     three such requests run one after the other in arrival order; the bytes in
     use never exceed the budget; a request that can never fit is refused."""
     f1, f2 = dipmc.footprint(128, 16, 1), dipmc.footprint(128, 16, 2)
@@ -210,9 +210,10 @@ def test_spacing_chosen_at_the_error_bound(dipmc):
         rid = srv.submit(L=64, l=0, T=0.9, sweeps=3, seed=5)
         srv.run_until_done([rid], timeout_s=120)
         assert srv.info(rid)["l"] == dipmc.choose_spacing(64, 0.1, 0.9, 1e-3)
-        # L = 96 at T = 0.9: the bound allows l = 16 (L/l = 6, no pack path); the
-        # server moves up to l = 24, the next divisor the direct pack serves
+        # L = 96 at T = 0.9: the bound allows l = 16 (L/l = 6: no direct kernel
+        # instance); the request goes to a spectral pack at that spacing
         assert dipmc.choose_spacing(96, 0.1, 0.9, 1e-3) == 16
         rid = srv.submit(L=96, l=0, T=0.9, sweeps=2, seed=6)
         srv.run_until_done([rid], timeout_s=120)
-        assert srv.info(rid)["l"] == 24 and srv.info(rid)["packed"]
+        info = srv.info(rid)
+        assert info["l"] == 16 and info["packed"] and info["path"] == dipmc.MC_PATH_SPECTRAL
