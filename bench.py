@@ -243,6 +243,48 @@ def serving_leg(dipmc, n_req, scale, quantum, budget_gb, rate_hz, timeout_s=240.
             "site_updates": upd, "failure_reasons": reasons}
 
 
+def large_lattice_leg(dipmc, stream, sweeps=8):
+    """L = 256, 16 replicas at T in [0.3, 0.9], C_D in {0.05, 0.1, 0.2}: the
+    spacing l that the Sec. 3.2 error bound 1e-3 allows at T = 0.3, then each
+    field path that serves (L, l) timed on `sweeps` sweeps (observables every
+    sweep), and the path the autotuner picks."""
+    import torch
+    Lb, Rb = 256, 16
+    Ts = np.linspace(0.3, 0.9, Rb)
+    names = {dipmc.MC_PATH_FFT: "fft", dipmc.MC_PATH_SPECTRAL: "spectral", dipmc.MC_PATH_DIRECT: "direct"}
+    out = []
+    for cd in (0.05, 0.1, 0.2):
+        lb = dipmc.choose_spacing(Lb, cd, 0.3, 1e-3)
+        lat = dipmc.Lattice(Lb, lb, Rb, seed=11)
+        lat.precompute_W(A_IMG, True)
+        for r in range(Rb):
+            lat.set_params(J, cd, K2, 0.0, f32(Ts[r]), replica=r)
+        lat.init_spins(0)
+        res = {"C_D": cd, "l": lb, "sweeps": sweeps, "paths": {}}
+        for path, nm in names.items():
+            try:
+                lat.set_field_path(path)
+                lat.sweep(1, 1, stream)
+                lat.sweep(1, 1, stream)
+                torch.cuda.synchronize()
+            except dipmc.McError:
+                continue
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            lat.sweep(sweeps, 1, stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            res["paths"][nm] = Rb * Lb * Lb * sweeps / (a.elapsed_time(b) / 1e3)
+        lat.set_field_path(dipmc.MC_PATH_AUTO)
+        pth, _ = lat.autotune(2, stream)
+        res["autotuned"] = names.get(pth, str(pth))
+        res["site_updates_per_s"] = max(res["paths"].values()) if res["paths"] else None
+        out.append(res)
+        lat.close()
+    return {"workload": "L=256, 16 replicas, T in [0.3, 0.9], l at flip-probability error 1e-3",
+            "runs": out}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -256,6 +298,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--no-large", action="store_true", help="skip the L=256 leg")
+    ap.add_argument("--large-only", action="store_true", help="run only the L=256 leg")
     ap.add_argument("--serve-only", action="store_true", help="run only the serving leg")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-scale", type=float, default=0.002, help="factor on the requests' sweep counts")
@@ -277,6 +321,11 @@ def main():
         torch.cuda.set_device(0)
     dev = torch.cuda.current_device()
     from paper_1211_6234_b300 import dipmc
+    if args.large_only:
+        if rank == 0:
+            print(json.dumps({"large_lattice": large_lattice_leg(dipmc, torch.cuda.current_stream(),
+                                                                 sweeps=args.sweeps)}), flush=True)
+        return
     if args.serve_only:
         if rank == 0:
             print(json.dumps({"serving": serving_leg(dipmc, args.serve_requests, args.serve_scale,
@@ -433,6 +482,10 @@ def main():
                  "batched_over_plain": value / ws / pv}
         p1.close()
 
+    large = None
+    if rank == 0 and not args.no_large:
+        large = large_lattice_leg(dipmc, stream)
+
     serving = None
     if rank == 0 and not args.no_serve:
         serving = serving_leg(dipmc, args.serve_requests, args.serve_scale, args.serve_quantum, 64.0,
@@ -460,6 +513,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
             "plain": plain,
+            "large_lattice": large,
             "serving": serving,
             "gpu_launches": gpu_launches,
             "clocks": clk,

@@ -90,6 +90,7 @@ struct mc_lattice {
     bool what_ready = false;
     // sub-lattice spectral path
     float2 *specT = nullptr, *specS = nullptr, *specH = nullptr;
+    int *specOff = nullptr;
     bool spec_ready = false;
     int spec_esplit = 0;
     // CUDA graphs of the multi-launch paths, keyed by (path, nsweeps, measure_every)
@@ -144,6 +145,7 @@ void free_all(mc_lattice *p) {
     cudaFree(p->specT);
     cudaFree(p->specS);
     cudaFree(p->specH);
+    cudaFree(p->specOff);
     cudaFree(p->slots_dev);
     if (p->slots_pin) cudaFreeHost(p->slots_pin);
     if (p->params_pin) cudaFreeHost(p->params_pin);
@@ -463,6 +465,7 @@ int ensure_spectral(mc_lattice *p, cudaStream_t st) {
     const int es = spectral_esplit(p->L, p->l, p->R, nsm);
     if (!p->specT) CKA(cudaMalloc(&p->specT, sizeof(float2) * 4 * (size_t)p->N()));
     if (!p->specS) CKA(cudaMalloc(&p->specS, sizeof(float2) * spectral_S_elems(p->L, p->R)));
+    if (!p->specOff) CKA(cudaMalloc(&p->specOff, sizeof(int) * (size_t)p->R * p->l * p->l));
     if (p->spec_esplit != es) {
         cudaFree(p->specH);
         p->specH = nullptr;
@@ -496,13 +499,15 @@ int run_spectral(mc_lattice *p, int nsweeps, int measure_every, float *trace, cu
     SpecBuffers b;
     b.W32 = p->W32; b.spins = p->spins; b.params = p->dparams; b.obs = p->obs; b.trace = trace;
     b.slots = p->packed ? p->slots_dev : nullptr;
-    b.T = p->specT; b.S = p->specS; b.Hpart = p->specH;
+    b.T = p->specT; b.S = p->specS; b.Hpart = p->specH; b.off = p->specOff;
     cudaError_t e = launch_spec_init(p->L, p->l, p->R, p->spins, p->specS, st);
     if (e != cudaSuccess) return cuda_fail(e, "spectra of the spin sub-lattices");
     bool measured_last = false;
     for (int it = 0; it < nsweeps; ++it) {
         c.t = (uint32_t)(p->t + (uint64_t)it);
         c.it = it;
+        e = launch_spec_offsets(c, b, st);
+        if (e != cudaSuccess) return cuda_fail(e, "sub-step offsets");
         for (int k = 0; k < ll; ++k) {
             c.k = k;
             {

@@ -29,6 +29,7 @@ namespace dipmc {
 namespace {
 
 constexpr int kSpecThreads = 256;
+constexpr int kUpdMaxThreads = 1024;
 constexpr int kSpecMaxC = 32;
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -83,6 +84,28 @@ __device__ __forceinline__ void perp_basis_s(float nx, float ny, float nz, float
     const float bb = nx * ny * a;
     b1 = make_float3(1.0f + sign * nx * nx * a, sign * bb, -sign * nx);
     b2 = make_float3(bb, sign + ny * ny * a, -ny);
+}
+
+// ---------------------------------------------------------------------------
+// Offsets of every sub-step of sweep `it` for every replica: off[r][k] =
+// (oy << 16) | ox, or -1 for a slot idle in this sweep.
+// ---------------------------------------------------------------------------
+__global__ void k_spec_offsets(const SpecConfig cfg, const SpecBuffers b) {
+    const int ll = cfg.l * cfg.l;
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (long long)cfg.R * ll) return;
+    const int r = (int)(g / ll), k = (int)(g % ll);
+    uint2 key;
+    uint32_t t, rid;
+    int v = -1;
+    if (stream_state(cfg, b, r, key, t, rid)) {
+        SpecConfig c = cfg;
+        c.k = k;
+        int ox, oy;
+        sub_offset(c, key, t, ox, oy);
+        v = (oy << 16) | ox;
+    }
+    b.off[g] = v;
 }
 
 // ---------------------------------------------------------------------------
@@ -182,42 +205,58 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec_init(int L, int l, const 
 // cell offsets e; the 8 warps of a CTA take interleaved e of the CTA's chunk and
 // are summed in a fixed order.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSpecThreads) k_spec_field(const SpecConfig cfg, const SpecBuffers b) {
+__global__ void __launch_bounds__(kSpecThreads, 3) k_spec_field(const SpecConfig cfg, const SpecBuffers b) {
     const int L = cfg.L, l = cfg.l, C = L / l, n = C * C, ll = l * l, R = cfg.R;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int j = blockIdx.x * 32 + lane;
     const int r = j < R * n ? j / n : 0, K = j < R * n ? j % n : 0;
-    uint2 key;
-    uint32_t t, rid;
-    const bool active = j < R * n && stream_state(cfg, b, r, key, t, rid);
+    const int ov = j < R * n ? b.off[(size_t)r * ll + cfg.k] : -1;
+    const bool active = ov >= 0;
     float2 hx = make_float2(0.f, 0.f), hy = hx, hz = hx;
     if (active) {
-        int ox, oy;
-        sub_offset(cfg, key, t, ox, oy);
+        const int ox = ov & 0xFFFF, oy = ov >> 16;
         const int Kx = K % C, Ky = K / C;
-        float2 ph[4];
-        ph[0] = make_float2(1.f, 0.f);
-        ph[1] = omega(Kx, C);
-        ph[2] = omega(Ky, C);
-        ph[3] = omega((Kx + Ky) % C, C);
+        const float2 ph1 = omega(Kx, C), ph2 = omega(Ky, C), ph3 = omega((Kx + Ky) % C, C);
         const int ec = (ll + gridDim.y - 1) / gridDim.y;
         const int e0 = blockIdx.y * ec, e1 = min(ll, e0 + ec);
         const float2 *Sr = b.S + (size_t)r * ll * 3 * n + K;
-        for (int e = e0 + w; e < e1; e += kSpecThreads / 32) {
-            const int ex = e % l, ey = e / l;
-            int dx = ox - ex, dy = oy - ey;
-            const int sx = dx < 0, sy = dy < 0;
-            dx += sx ? l : 0;
-            dy += sy ? l : 0;
-            const float2 *Tp = b.T + (size_t)(dy * l + dx) * 4 * n + K;
-            const float2 p = ph[sx + 2 * sy];
-            const float2 txx = cmul(__ldg(Tp), p), txy = cmul(__ldg(Tp + n), p);
-            const float2 tyy = cmul(__ldg(Tp + 2 * n), p), tzz = cmul(__ldg(Tp + 3 * n), p);
-            const float2 *Sp = Sr + (size_t)e * 3 * n;
-            const float2 s0 = Sp[0], s1 = Sp[n], s2 = Sp[2 * n];
-            hx = cfma(txx, s0, cfma(txy, s1, hx));
-            hy = cfma(txy, s0, cfma(tyy, s1, hy));
-            hz = cfma(tzz, s2, hz);
+        constexpr int kW = kSpecThreads / 32, kU = 2;  // warps; cell offsets in flight per warp
+        for (int eb = e0 + w; eb < e1; eb += kW * kU) {
+            float2 tv[kU][4], sv[kU][3];
+            int sg[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int e = eb + u * kW;
+                sg[u] = 0;
+                if (e < e1) {
+                    const int ex = e % l, ey = e / l;
+                    int dx = ox - ex, dy = oy - ey;
+                    const int sx = dx < 0, sy = dy < 0;
+                    dx += sx ? l : 0;
+                    dy += sy ? l : 0;
+                    sg[u] = sx + 2 * sy;
+                    const float2 *Tp = b.T + (size_t)(dy * l + dx) * 4 * n + K;
+                    const float2 *Sp = Sr + (size_t)e * 3 * n;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) tv[u][c] = __ldg(Tp + c * n);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) sv[u][c] = Sp[c * n];
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) tv[u][c] = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) sv[u][c] = make_float2(0.f, 0.f);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const float2 p = sg[u] == 0 ? make_float2(1.f, 0.f) : sg[u] == 1 ? ph1 : sg[u] == 2 ? ph2 : ph3;
+                const float2 txx = cmul(tv[u][0], p), txy = cmul(tv[u][1], p);
+                const float2 tyy = cmul(tv[u][2], p), tzz = cmul(tv[u][3], p);
+                hx = cfma(txx, sv[u][0], cfma(txy, sv[u][1], hx));
+                hy = cfma(txy, sv[u][0], cfma(tyy, sv[u][1], hy));
+                hz = cfma(tzz, sv[u][2], hz);
+            }
         }
     }
     __shared__ float2 red[kSpecThreads / 32][3][32];
@@ -239,14 +278,14 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec_field(const SpecConfig cf
 // Per replica: field at the n sites (inverse DFT of the summed partial spectra),
 // Metropolis decisions, new S of the updated offset.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSpecThreads) k_spec_update(const SpecConfig cfg, const SpecBuffers b) {
+__global__ void __launch_bounds__(kUpdMaxThreads) k_spec_update(const SpecConfig cfg, const SpecBuffers b) {
     const int L = cfg.L, l = cfg.l, C = L / l, n = C * C, ll = l * l, N = L * L, R = cfg.R;
     const int r = blockIdx.x;
     uint2 key;
     uint32_t t, rid;
     if (!stream_state(cfg, b, r, key, t, rid)) return;  // whole block, before any barrier
-    int ox, oy;
-    sub_offset(cfg, key, t, ox, oy);
+    const int ov = b.off[(size_t)r * ll + cfg.k];
+    const int ox = ov & 0xFFFF, oy = ov >> 16;
     extern __shared__ float2 sm_f2[];
     float2 *tw = sm_f2;                                          // [C]
     float2 *H = tw + kSpecMaxC;                                  // [3][n]
@@ -419,6 +458,12 @@ cudaError_t launch_spec_init(int L, int l, int R, const float *spins, float2 *S,
     return cudaGetLastError();
 }
 
+cudaError_t launch_spec_offsets(const SpecConfig &c, const SpecBuffers &b, cudaStream_t st) {
+    const long long tot = (long long)c.R * c.l * c.l;
+    k_spec_offsets<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(c, b);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_spec_field(const SpecConfig &c, const SpecBuffers &b, cudaStream_t st) {
     const int C = c.L / c.l, n = C * C;
     const unsigned tiles = (unsigned)((c.R * n + 31) / 32);
@@ -430,7 +475,10 @@ cudaError_t launch_spec_update(const SpecConfig &c, const SpecBuffers &b, cudaSt
     const size_t smem = update_smem(c.L / c.l);
     cudaError_t e = cudaFuncSetAttribute(k_spec_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_spec_update<<<c.R, kSpecThreads, smem, st>>>(c, b);
+    // one thread per output of a DFT stage (3 n), so that no warp idles at the
+    // stage barriers
+    const int C = c.L / c.l, th = std::min(kUpdMaxThreads, ((3 * C * C + 31) / 32) * 32);
+    k_spec_update<<<c.R, std::max(64, th), smem, st>>>(c, b);
     return cudaGetLastError();
 }
 

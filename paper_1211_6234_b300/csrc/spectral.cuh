@@ -29,6 +29,7 @@ struct SpecBuffers {
     const float2 *T = nullptr;           // [l^2][4][n]: transforms of the W~ sub-lattice sequences
     float2 *S = nullptr;                 // [R][l^2][3][n]: transforms of the spin sub-lattices
     float2 *Hpart = nullptr;             // [esplit][R][3][n]: partial field spectra
+    int *off = nullptr;                  // [R][l^2]: offsets of the sweep's sub-steps (-1: idle slot)
 };
 
 bool spectral_supported(int L, int l);
@@ -39,6 +40,8 @@ size_t spectral_part_elems(int L, int l, int R, int esplit);
 cudaError_t launch_spec_table(int L, int l, const double *W64, float2 *T, cudaStream_t st);
 // S of every cell offset from the spins.
 cudaError_t launch_spec_init(int L, int l, int R, const float *spins, float2 *S, cudaStream_t st);
+// Offsets of all sub-steps of sweep cfg.it for every replica (once per sweep).
+cudaError_t launch_spec_offsets(const SpecConfig &c, const SpecBuffers &b, cudaStream_t st);
 // One sub-step is launch_spec_field (partial field spectra at the sub-step's
 // sites: contraction over cell offsets) then launch_spec_update (per replica the
 // inverse transform, the update and the new S of the updated offset).
