@@ -44,6 +44,7 @@
 #include <string.h>
 
 #define ORC_PI 3.14159265358979323846
+#define ORC_NOBS 6   /* |m|, m_z, |m_z|, M_par, E/N, m_st */
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10, written from its published definition (Salmon et al.,     */
@@ -275,7 +276,8 @@ double orc_dipole_energy_pairs(int L, int A, int tail, const double *s, double C
 typedef struct {
     int L, l;
     double J, CD, K2, K4, T;
-    int proposal;   /* 0: uniform on the cap of half-angle `cone` around s; 1: uniform on S^2 */
+    int proposal;   /* 0: uniform on the cap of half-angle `cone` around s; 1: uniform on S^2;
+                       2: reversal S = -s (Appendix B: Ising spins s = (0, 0, +-1)) */
     double cone;    /* radians */
     int schedule;   /* 0: permutation of the l^2 offsets per sweep; 1: draw with replacement */
     uint64_t seed;  /* Philox key */
@@ -356,9 +358,14 @@ static void perp_basis(const double n[3], double b1[3], double b2[3])
 }
 
 /* Proposal S for current spin s from uniforms u1, u2 (Sec. 3.1 proposal; cap
- * of half-angle `cone` when kind 0, whole sphere when kind 1). */
+ * of half-angle `cone` when kind 0, whole sphere when kind 1, the complete
+ * reversal of Appendix B when kind 2). */
 static void propose(int kind, double cone, const double s[3], double u1, double u2, double S[3])
 {
+    if (kind == 2) {
+        for (int c = 0; c < 3; ++c) S[c] = -s[c];
+        return;
+    }
     double psi = 2.0 * ORC_PI * u2;
     if (kind == 1) {
         double z = 2.0 * u1 - 1.0;
@@ -403,16 +410,26 @@ static double delta_e(const orc_params *p, const double *W, const double *s, int
     return dex + dan + ddip;
 }
 
-/* Observables of one state: out = {|m|, m_z, |m_z|, M_par, E/N}. */
+/* Observables of one state: out = {|m|, m_z, |m_z|, M_par, E/N, m_st}.
+ * m_st (Appendix B): with the four sub-lattices of the 2 x 2 cell, 1 = (x even,
+ * y even), 2 = (x odd, y even), 3 = (x odd, y odd), 4 = (x even, y odd), and
+ * m_lambda = (1/N) sum_{i in lambda} s_i^z, m_h = m1 + m2 - m3 - m4 (horizontal
+ * stripes), m_v = m1 + m4 - m3 - m2 (vertical stripes), m_st = sqrt(m_h^2 + m_v^2). */
 static void observe(const orc_params *p, const double *W, const double *s, double *out)
 {
     const int L = p->L, N = L * L;
     double mx = 0, my = 0, mz = 0;
+    double m[4] = {0, 0, 0, 0};
     for (int i = 0; i < N; ++i) {
         mx += s[i];
         my += s[N + i];
         mz += s[2 * N + i];
+        const int x = i % L, y = i / L;
+        const int lam = (y & 1) ? ((x & 1) ? 2 : 3) : ((x & 1) ? 1 : 0);   /* 0-based: 1, 2, 3, 4 */
+        m[lam] += s[2 * N + i];
     }
+    for (int k = 0; k < 4; ++k) m[k] /= N;
+    const double mh = m[0] + m[1] - m[2] - m[3], mv = m[0] + m[3] - m[2] - m[1];
     mx /= N;
     my /= N;
     mz /= N;
@@ -423,6 +440,7 @@ static void observe(const orc_params *p, const double *W, const double *s, doubl
     out[2] = fabs(mz);
     out[3] = sqrt(mx * mx + my * my);
     out[4] = e[3] / N;
+    out[5] = sqrt(mh * mh + mv * mv);
 }
 
 /*
@@ -430,7 +448,7 @@ static void observe(const orc_params *p, const double *W, const double *s, doubl
  * s is [3][L][L], updated in place.  Sweeps t0 .. t0+nsweeps-1; each has l^2
  * sub-steps.  Trace arrays (may be NULL) hold one record per attempt, in order
  * (sweep, sub-step, site d = Dy*C + Dx with C = L/l):  q (site index), h[3],
- * dE, u, accept, S[3].  obs (may be NULL) gets 5 values per sweep;
+ * dE, u, accept, S[3].  obs (may be NULL) gets ORC_NOBS values per sweep;
  * theta2 (may be NULL) accumulates (acos s_z - pi/2)^2 per site per sweep.
  */
 int orc_sweeps(const orc_params *p, const double *W, double *s, uint32_t t0, int nsweeps,
@@ -485,7 +503,7 @@ int orc_sweeps(const orc_params *p, const double *W, double *s, uint32_t t0, int
                 if (acc[d])
                     for (int c3 = 0; c3 < 3; ++c3) s[c3 * N + qs[d]] = Sq[3 * d + c3];
         }
-        if (obs) observe(p, W, s, obs + 5 * it);
+        if (obs) observe(p, W, s, obs + ORC_NOBS * it);
         if (theta2)
             for (int i = 0; i < N; ++i) {
                 double zc = fmax(-1.0, fmin(1.0, s[2 * N + i]));
@@ -510,7 +528,7 @@ int orc_sweeps_batch(int R, const orc_params *ps, const double *W, double *s, ui
     for (int r = 0; r < R; ++r) {
         const int N = ps[r].L * ps[r].L;
         bad |= orc_sweeps(&ps[r], W, s + (size_t)r * 3 * N, t0, nsweeps, NULL, NULL, NULL, NULL,
-                          NULL, NULL, obs ? obs + (size_t)r * nsweeps * 5 : NULL,
+                          NULL, NULL, obs ? obs + (size_t)r * nsweeps * ORC_NOBS : NULL,
                           theta2 ? theta2 + (size_t)r * N : NULL) != 0;
     }
     return bad ? -1 : 0;
@@ -556,6 +574,22 @@ int orc_sweeps_exact(const orc_params *p, const double *W, double *s, uint32_t t
     }
     free(trial);
     return 0;
+}
+
+/* Random Ising initial spins (Appendix B): s = (0, 0, +1) if u0 < 1/2 else
+ * (0, 0, -1), u0 from the counter (site, replica, 0, TAG_INIT). */
+void orc_init_ising(int L, uint64_t seed, uint32_t replica, double *s)
+{
+    const int N = L * L;
+    uint32_t key[2];
+    keyof(seed, key);
+    for (int i = 0; i < N; ++i) {
+        uint32_t c[4] = {(uint32_t)i, replica, 0u, TAG_INIT << 24}, w[4];
+        orc_philox4x32_10(c, key, w);
+        s[i] = 0.0;
+        s[N + i] = 0.0;
+        s[2 * N + i] = u24(w[0]) < 0.5 ? 1.0 : -1.0;
+    }
 }
 
 /* Random-uniform initial spins on S^2 from the seed (counter = site, replica,

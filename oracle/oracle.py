@@ -20,6 +20,10 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 
+# per-sweep observables: |m|, m_z, |m_z|, M_par, E/N, m_st (Appendix B staggered magnetisation)
+NOBS = 6
+
+
 def build(force: bool = False) -> str:
     """Compile oracle.c into liboracle.so with gcc (IEEE FP64, no fast-math)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
@@ -77,6 +81,7 @@ def lib():
         _lib.orc_sweeps_exact.argtypes = [C.POINTER(Params), d, d, C.c_uint32, C.c_int, d, i32]
         _lib.orc_sweeps_exact.restype = C.c_int
         _lib.orc_init_random.argtypes = [C.c_int, C.c_uint64, C.c_uint32, d]
+        _lib.orc_init_ising.argtypes = [C.c_int, C.c_uint64, C.c_uint32, d]
         _lib.orc_eta.argtypes = [C.c_int, d, C.c_double]
         _lib.orc_eta.restype = C.c_double
         _lib.orc_eps12.argtypes = [d, d, d, C.c_double]
@@ -160,7 +165,7 @@ def sweeps(p: Params, W, s, t0: int, nsweeps: int, trace: bool = True, observe: 
         out["acc"] = np.zeros(ntr, np.int32)
         out["S"] = np.zeros((ntr, 3), np.float64)
     if observe:
-        out["obs"] = np.zeros((nsweeps, 5), np.float64)
+        out["obs"] = np.zeros((nsweeps, NOBS), np.float64)
         out["theta2"] = np.zeros(L * L, np.float64)
     rc = lib().orc_sweeps(
         C.byref(p), _dp(W), _dp(s), t0, nsweeps,
@@ -181,7 +186,7 @@ def sweeps_batch(ps, W, s, t0, nsweeps, observe=True):
     W = np.ascontiguousarray(W, np.float64)
     s = np.array(s, np.float64, copy=True, order="C")
     L = ps[0].L
-    obs = np.zeros((R, nsweeps, 5), np.float64) if observe else None
+    obs = np.zeros((R, nsweeps, NOBS), np.float64) if observe else None
     th = np.zeros((R, L * L), np.float64) if observe else None
     rc = lib().orc_sweeps_batch(R, arr, _dp(W), _dp(s), t0, nsweeps,
                                 _dp(obs) if observe else None, _dp(th) if observe else None)
@@ -204,6 +209,13 @@ def sweeps_exact(p: Params, W, s, t0, nsweeps):
 def init_random(L, seed, replica=0):
     s = np.zeros((3, L, L), np.float64)
     lib().orc_init_random(L, seed, replica, _dp(s))
+    return s
+
+
+def init_ising(L, seed, replica=0):
+    """Random Ising state s = (0, 0, +-1) from the seed (Appendix B)."""
+    s = np.zeros((3, L, L), np.float64)
+    lib().orc_init_ising(L, seed, replica, _dp(s))
     return s
 
 

@@ -161,10 +161,12 @@ __device__ __forceinline__ void dft3_forward(const float *x, float2 *U, const fl
         const int b = i / n, j = i % n, Dy = j / C, Kx = j % C;
         const float *row = x + b * n + Dy * C;
         float2 acc = make_float2(0.f, 0.f);
-        for (int Dx = 0; Dx < C; ++Dx) {
-            const float2 o = tw[(Kx * Dx) % C];
+        for (int Dx = 0, m = 0; Dx < C; ++Dx) {       // m = Kx * Dx mod C
+            const float2 o = tw[m];
             acc.x = fmaf(row[Dx], o.x, acc.x);
             acc.y = fmaf(row[Dx], o.y, acc.y);
+            m += Kx;
+            if (m >= C) m -= C;
         }
         U[i] = acc;
     }
@@ -173,7 +175,11 @@ __device__ __forceinline__ void dft3_forward(const float *x, float2 *U, const fl
         const int b = i / n, j = i % n, Ky = j / C, Kx = j % C;
         const float2 *col = U + b * n + Kx;
         float2 acc = make_float2(0.f, 0.f);
-        for (int Dy = 0; Dy < C; ++Dy) acc = cfma(col[Dy * C], tw[(Ky * Dy) % C], acc);
+        for (int Dy = 0, m = 0; Dy < C; ++Dy) {       // m = Ky * Dy mod C
+            acc = cfma(col[Dy * C], tw[m], acc);
+            m += Ky;
+            if (m >= C) m -= C;
+        }
         out[(size_t)b * out_stride + j] = acc;
     }
 }
@@ -221,15 +227,21 @@ __global__ void __launch_bounds__(kSpecThreads, 3) k_spec_field(const SpecConfig
         const int e0 = blockIdx.y * ec, e1 = min(ll, e0 + ec);
         const float2 *Sr = b.S + (size_t)r * ll * 3 * n + K;
         constexpr int kW = kSpecThreads / 32, kU = 2;  // warps; cell offsets in flight per warp
+        // cell offset (ex, ey) of e = eb + u * kW, stepped without divisions
+        int bx = (e0 + w) % l, by = (e0 + w) / l;
         for (int eb = e0 + w; eb < e1; eb += kW * kU) {
             float2 tv[kU][4], sv[kU][3];
             int sg[kU];
+            int ex = bx, ey = by;
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
                 const int e = eb + u * kW;
                 sg[u] = 0;
+                if (u > 0) {
+                    ex += kW;
+                    while (ex >= l) { ex -= l; ++ey; }
+                }
                 if (e < e1) {
-                    const int ex = e % l, ey = e / l;
                     int dx = ox - ex, dy = oy - ey;
                     const int sx = dx < 0, sy = dy < 0;
                     dx += sx ? l : 0;
@@ -248,6 +260,9 @@ __global__ void __launch_bounds__(kSpecThreads, 3) k_spec_field(const SpecConfig
                     for (int c = 0; c < 3; ++c) sv[u][c] = make_float2(0.f, 0.f);
                 }
             }
+            bx = ex + kW;
+            by = ey;
+            while (bx >= l) { bx -= l; ++by; }
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
                 const float2 p = sg[u] == 0 ? make_float2(1.f, 0.f) : sg[u] == 1 ? ph1 : sg[u] == 2 ? ph2 : ph3;
@@ -310,9 +325,11 @@ __global__ void __launch_bounds__(kUpdMaxThreads) k_spec_update(const SpecConfig
         const int a = i / n, jj = i % n, Ky = jj / C, Dx = jj % C;
         const float2 *row = H + a * n + Ky * C;
         float2 acc = make_float2(0.f, 0.f);
-        for (int Kx = 0; Kx < C; ++Kx) {
-            const float2 o = tw[(Kx * Dx) % C];
+        for (int Kx = 0, m = 0; Kx < C; ++Kx) {       // m = Kx * Dx mod C
+            const float2 o = tw[m];
             acc = cfma(row[Kx], make_float2(o.x, -o.y), acc);
+            m += Dx;
+            if (m >= C) m -= C;
         }
         U[i] = acc;
     }
@@ -322,9 +339,11 @@ __global__ void __launch_bounds__(kUpdMaxThreads) k_spec_update(const SpecConfig
         const int a = i / n, jj = i % n, Dy = jj / C, Dx = jj % C;
         const float2 *col = U + a * n + Dx;
         float re = 0.f;
-        for (int Ky = 0; Ky < C; ++Ky) {
-            const float2 u = col[Ky * C], o = tw[(Ky * Dy) % C];
+        for (int Ky = 0, m = 0; Ky < C; ++Ky) {       // m = Ky * Dy mod C
+            const float2 u = col[Ky * C], o = tw[m];
             re = fmaf(u.x, o.x, fmaf(u.y, o.y, re));   // Re(u * conj(o))
+            m += Dy;
+            if (m >= C) m -= C;
         }
         hs[i] = re * inv_n;
     }

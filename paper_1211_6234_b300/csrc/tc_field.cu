@@ -16,11 +16,13 @@
 // product is hi_A hi_B + hi_A lo_B + lo_A hi_B (error ~2^-18 relative).
 //
 // One CTA = one (M-tile of 128 rows, N-tile of up to 256 replicas, range of
-// K-blocks of 64).  Operands are staged by all threads into the canonical
-// K-major, no-swizzle core-matrix layout (8 rows x 16 bytes per core matrix),
-// two stages deep; thread 0 issues tcgen05.mma (M=128, N=tile, K=16) into a
-// TMEM accumulator and commits each stage to an mbarrier.  The epilogue reads
-// TMEM with tcgen05.ld and adds the partial tile into H0 (split-K reduction).
+// K-blocks of 32).  Operands are staged by all threads with cp.async into the
+// canonical K-major, no-swizzle core-matrix layout (8 rows x 16 bytes per core
+// matrix) in a ring of 4 stages, loads running 2 stages ahead of the MMAs; a
+// stage is refilled once the MMAs that read it have committed.  Thread 0 issues
+// tcgen05.mma (M=128, N=tile, K=16) into a TMEM accumulator and commits each
+// stage to its mbarrier.  The epilogue reads TMEM with tcgen05.ld and adds the
+// partial tile into H0 (split-K reduction).
 #include <cuda_bf16.h>
 
 #include "internal.cuh"
@@ -31,27 +33,30 @@ namespace dipmc {
 namespace {
 
 constexpr int kTcThreads = 128;
-constexpr int kKB = 64;                       // K elements per stage
+constexpr int kKB = 32;                       // K elements per stage
+constexpr int kKC = kKB / 8;                  // core matrices along K per row
+constexpr int kSBO = kKC * 128;               // bytes between 8-row groups
 constexpr int kTileA = 128 * kKB * 2;         // bytes of one A tile (hi or lo)
 constexpr int kMaxNT = 256;
 constexpr int kTileB = kMaxNT * kKB * 2;      // bytes of one B tile (hi or lo)
 constexpr int kStage = 2 * kTileA + 2 * kTileB;
-constexpr int kStages = 2;
+constexpr int kStages = 4;
+constexpr int kAhead = 2;                     // stages loaded ahead of the MMAs
 constexpr long long kWaitCycles = 4LL << 30;  // bounded mbarrier waits (~2 s at 2 GHz)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// Canonical no-swizzle K-major layout: element (row, k) of a tile with 64 K
-// columns lives at (row/8)*1024 + (k/8)*128 + (row%8)*16 + (k%8)*2 bytes:
+// Canonical no-swizzle K-major layout: element (row, k) of a tile with kKB K
+// columns lives at (row/8)*kSBO + (k/8)*128 + (row%8)*16 + (k%8)*2 bytes:
 // core matrices of 8 rows x 8 elements (128 B); adjacent along K: 128 B
-// (leading byte offset), adjacent along M/N: 1024 B (stride byte offset).
-__device__ __forceinline__ uint32_t core_off(int row, int kc) { return (row >> 3) * 1024 + kc * 128 + (row & 7) * 16; }
+// (leading byte offset), adjacent along M/N: kSBO bytes (stride byte offset).
+__device__ __forceinline__ uint32_t core_off(int row, int kc) { return (row >> 3) * kSBO + kc * 128 + (row & 7) * 16; }
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
     uint64_t d = 0;
     d |= (uint64_t)((addr >> 4) & 0x3FFFu);          // start address
     d |= (uint64_t)(128u >> 4) << 16;                 // leading byte offset (K direction)
-    d |= (uint64_t)(1024u >> 4) << 32;                // stride byte offset (M/N direction)
+    d |= (uint64_t)((uint32_t)kSBO >> 4) << 32;       // stride byte offset (M/N direction)
     d |= (uint64_t)1 << 46;                           // descriptor version for tcgen05
     // base offset 0, layout type 0 = no swizzle
     return d;
@@ -98,6 +103,9 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait_pending() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
     asm volatile(
@@ -159,8 +167,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
+        for (int s = 0; s < kStages; ++s) mbar_init(&mbar[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -170,15 +177,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a)
     bool ok = true;
 
     const int nkb = u.kb_end - u.kb_begin;
-    for (int i = 0; i < nkb; ++i) {
-        const int st = i & 1;
-        if (i >= 2) ok &= mbar_wait(&mbar[st], (uint32_t)(((i >> 1) - 1) & 1));
-        uint8_t *base = smem + st * kStage;
-        uint8_t *Ahi = base, *Alo = base + kTileA, *Bhi = base + 2 * kTileA, *Blo = base + 2 * kTileA + kTileB;
-        const int kb = u.kb_begin + i;
-        const int k0 = kb * kKB;                     // K offset within this tile's contraction
-        // ---- A: Toeplitz tile, 128 rows x 64 K; thread tid builds row tid (8 chunks of 8)
-        const uint32_t sAhi = smem_u32(Ahi), sAlo = smem_u32(Alo), sBhi = smem_u32(Bhi), sBlo = smem_u32(Blo);
+    // stage the operands of K-block i into ring slot i % kStages
+    auto load_stage = [&](int i) {
+        uint8_t *base = smem + (i % kStages) * kStage;
+        const uint32_t sAhi = smem_u32(base), sAlo = sAhi + kTileA;
+        const uint32_t sBhi = sAhi + 2 * kTileA, sBlo = sBhi + kTileB;
+        const int k0 = (u.kb_begin + i) * kKB;       // K offset within this tile's contraction
+        // A: Toeplitz tile, 128 rows x kKB; thread tid builds row tid (kKC chunks of 8)
         {
             const int al = zz ? 2 : (k0 >= N ? 1 : 0);    // input component of this K block
             const int comp = zz ? 3 : (al == 0 ? comp_a0 : comp_a1);
@@ -186,7 +191,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a)
             int my = m0 / L, mx = m0 - my * L;
             const __nv_bfloat16 *wc = a.wsh + (size_t)comp * 2 * L * 2 * L;
 #pragma unroll
-            for (int kc = 0; kc < 8; ++kc) {
+            for (int kc = 0; kc < kKC; ++kc) {
                 int dy = my - my_qy;
                 if (dy < 0) dy += L;
                 int x0 = mx - my_qx;                      // W~(q - m) = W~(m - q): forward segment from x0
@@ -198,25 +203,40 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a)
                 if (mx >= L) { mx -= L; ++my; }
             }
         }
-        // ---- B: spins of NT replicas x 64 K (zero rows past R)
+        // B: spins of NT replicas x kKB (zero rows past R); kKC consecutive threads
+        // read the kKC chunks of one replica row (contiguous in global memory)
         const int kofs = (zz ? 2 * N : 0) + k0;
-#pragma unroll
-        for (int kc = 0; kc < 8; ++kc) {
-            for (int rr = tid; rr < nrows_b; rr += kTcThreads) {
-                const int r = n0 + rr;
-                const bool in = r < a.R;
-                const size_t g = (size_t)(in ? r : 0) * 3 * N + kofs + kc * 8;
-                cp_async16(sBhi + core_off(rr, kc), a.spins_hi + g, in ? 16u : 0u);
-                cp_async16(sBlo + core_off(rr, kc), a.spins_lo + g, in ? 16u : 0u);
-            }
+        for (int idx = tid; idx < nrows_b * kKC; idx += kTcThreads) {
+            const int rr = idx / kKC, kc = idx % kKC;
+            const int r = n0 + rr;
+            const bool in = r < a.R;
+            const size_t g = (size_t)(in ? r : 0) * 3 * N + kofs + kc * 8;
+            cp_async16(sBhi + core_off(rr, kc), a.spins_hi + g, in ? 16u : 0u);
+            cp_async16(sBlo + core_off(rr, kc), a.spins_lo + g, in ? 16u : 0u);
+        }
+    };
+    // prologue: the first kAhead stages
+    for (int i = 0; i < kAhead; ++i) {
+        if (i < nkb) load_stage(i);
+        cp_async_commit();
+    }
+    for (int i = 0; i < nkb; ++i) {
+        // refill: K-block i + kAhead goes to the slot that K-block i + kAhead - kStages
+        // used; its MMAs were committed two iterations ago
+        const int j = i + kAhead;
+        if (j < nkb) {
+            const int prev = j - kStages;
+            if (prev >= 0) ok &= mbar_wait(&mbar[prev % kStages], (uint32_t)((prev / kStages) & 1));
+            load_stage(j);
         }
         cp_async_commit();
-        cp_async_wait_all();
+        cp_async_wait_pending<kAhead>();             // K-block i has landed (this thread's copies)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
+        __syncthreads();                              // ... and every thread's
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t ah = smem_u32(Ahi), alo = smem_u32(Alo), bh = smem_u32(Bhi), blo = smem_u32(Blo);
+            const uint32_t ah = smem_u32(smem + (i % kStages) * kStage);
+            const uint32_t alo = ah + kTileA, bh = ah + 2 * kTileA, blo = bh + kTileB;
 #pragma unroll
             for (int ks = 0; ks < kKB / 16; ++ks) {
                 const uint32_t ko = ks * 256;        // 16 K elements = 2 core matrices = 256 B
@@ -225,13 +245,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a)
                 umma_bf16(tmem, smem_desc(ah + ko), smem_desc(blo + ko), idesc, 1u);
                 umma_bf16(tmem, smem_desc(alo + ko), smem_desc(bh + ko), idesc, 1u);
             }
-            umma_commit(&mbar[st]);
+            umma_commit(&mbar[i % kStages]);
         }
     }
     // ---- wait for the last stage (its commit covers every earlier MMA)
     if (nkb > 0) {
         const int last = nkb - 1;
-        ok &= mbar_wait(&mbar[last & 1], (uint32_t)((last >> 1) & 1));
+        ok &= mbar_wait(&mbar[last % kStages], (uint32_t)((last / kStages) & 1));
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!ok) {

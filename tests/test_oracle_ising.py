@@ -1,0 +1,106 @@
+"""Pins of the oracle's dipolar Ising variant (Appendix B): spins (0, 0, +-1),
+complete reversal as the move, staggered magnetisation m_st of the four 2 x 2
+sub-lattices.  Pinned against closed forms (perfect stripes, checkerboard and
+ferromagnet), Onsager's exact solution of the square-lattice Ising model
+(C_D = 0), and exact enumeration of all 2^16 states of a 4 x 4 lattice with
+the dipole term."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+from scipy.special import ellipk
+
+from oracle import oracle as orc
+from tests.parity_util import binned_error
+
+
+def ising_state(L, pattern):
+    y, x = np.mgrid[0:L, 0:L]
+    z = {"hstripes": np.where(y % 2 == 0, 1.0, -1.0), "vstripes": np.where(x % 2 == 0, 1.0, -1.0),
+         "checker": np.where((x + y) % 2 == 0, 1.0, -1.0), "ferro": np.ones((L, L))}[pattern]
+    s = np.zeros((3, L, L))
+    s[2] = z
+    return s
+
+
+@pytest.mark.parametrize("pattern,mst", [("hstripes", 1.0), ("vstripes", 1.0), ("checker", 0.0), ("ferro", 0.0)])
+def test_staggered_magnetisation_closed_forms(pattern, mst):
+    """With J = C_D = K = 0 every reversal is accepted (dE = 0), so one sweep
+    reverses every spin: m_st is unchanged and m_z changes sign."""
+    L = 8
+    s = ising_state(L, pattern)
+    W = orc.wtilde(L, 4, True)
+    p = orc.params(L, 2, 0.0, 0.0, 0.0, 0.0, 1.0, proposal=2, seed=1)
+    o = orc.sweeps(p, W, s.copy(), 0, 2, observe=True)
+    assert np.allclose(o["obs"][:, 5], mst, atol=1e-15)
+    mz0 = s[2].mean()
+    assert o["obs"][0, 1] == pytest.approx(-mz0) and o["obs"][1, 1] == pytest.approx(mz0)
+    assert np.all(o["acc"] == 1)
+
+
+def test_ising_energy_is_the_restricted_heisenberg_energy():
+    """Appendix B energy: -J sum_bonds s_i s_j + (C_D/2) sum_ij W~_zz(i - j) s_i s_j
+    (self-image included), written out with an explicit double loop."""
+    L, J, CD = 6, 1.0, 1 / 1.7
+    s = orc.init_ising(L, 9)
+    W = orc.wtilde(L, 8, True)
+    z = s[2]
+    ex = -J * sum(z[y, x] * (z[y, (x + 1) % L] + z[(y + 1) % L, x]) for y in range(L) for x in range(L))
+    dip = 0.0
+    for yi, xi, yj, xj in itertools.product(range(L), repeat=4):
+        dip += z[yi, xi] * z[yj, xj] * W[3][(yi - yj) % L, (xi - xj) % L]
+    e = orc.energy(W, s, J, CD, 0.0, 0.0)
+    assert e[3] == pytest.approx(ex + 0.5 * CD * dip, rel=1e-12)
+
+
+def test_onsager_energy_and_magnetisation():
+    """C_D = 0: exact sequential Metropolis with reversals on a 16 x 16 lattice
+    at T = 1.5 (below T_c = 2.269) reproduces Onsager's energy per spin
+    u = -coth(2K)[1 + (2/pi)(2 tanh^2(2K) - 1) K1(k)], k = 2 sinh(2K)/cosh^2(2K),
+    and Yang's spontaneous magnetisation (1 - sinh^-4(2K))^(1/8), K = J/T."""
+    L, T = 16, 1.5
+    K = 1.0 / T
+    k = 2 * math.sinh(2 * K) / math.cosh(2 * K) ** 2
+    u_exact = -1 / math.tanh(2 * K) * (1 + 2 / math.pi * (2 * math.tanh(2 * K) ** 2 - 1) * ellipk(k * k))
+    m_exact = (1 - math.sinh(2 * K) ** -4) ** 0.125
+    W = orc.wtilde(L, 4, True)
+    s = ising_state(L, "ferro")
+    p = orc.params(L, L, 1.0, 0.0, 0.0, 0.0, T, proposal=2, seed=11)
+    s = orc.sweeps(p, W, s, 0, 500, trace=False)["s"]            # equilibrate
+    o = orc.sweeps(p, W, s, 500, 12000, trace=False, observe=True)
+    e, m = o["obs"][:, 4], o["obs"][:, 2]
+    assert abs(e.mean() - u_exact) < 4 * binned_error(e) + 2e-4, (e.mean(), u_exact, binned_error(e))
+    assert abs(m.mean() - m_exact) < 4 * binned_error(m) + 2e-4, (m.mean(), m_exact, binned_error(m))
+
+
+def test_exact_enumeration_4x4_with_dipoles():
+    """All 2^16 states of a 4 x 4 lattice at J/C_D = 1.7 (Appendix B), T = 0.6:
+    Boltzmann averages of E/N and m_st against the exact sequential Metropolis
+    chain of the oracle (l = L)."""
+    L, J, T = 4, 1.0, 0.6
+    CD = J / 1.7
+    W = orc.wtilde(L, 16, True)
+    N = L * L
+    idx = np.arange(N)
+    yy, xx = idx // L, idx % L
+    M = W[3][(yy[:, None] - yy[None, :]) % L, (xx[:, None] - xx[None, :]) % L]
+    right = yy * L + (xx + 1) % L
+    up = ((yy + 1) % L) * L + xx
+    states = 1 - 2 * ((np.arange(2 ** N)[:, None] >> idx[None, :]) & 1).astype(np.float64)
+    E = -J * (states * (states[:, right] + states[:, up])).sum(1) + 0.5 * CD * np.einsum("si,ij,sj->s", states, M, states)
+    lam = np.where(yy % 2 == 0, np.where(xx % 2 == 0, 0, 1), np.where(xx % 2 == 1, 2, 3))
+    msub = np.stack([states[:, lam == k].sum(1) / N for k in range(4)], 1)
+    mh = msub[:, 0] + msub[:, 1] - msub[:, 2] - msub[:, 3]
+    mv = msub[:, 0] + msub[:, 3] - msub[:, 2] - msub[:, 1]
+    mst = np.sqrt(mh ** 2 + mv ** 2)
+    w = np.exp(-(E - E.min()) / T)
+    w /= w.sum()
+    e_exact, m_exact = float((w * E).sum() / N), float((w * mst).sum())
+    s = orc.init_ising(L, 4)
+    p = orc.params(L, L, J, CD, 0.0, 0.0, T, proposal=2, seed=21)
+    s = orc.sweeps(p, W, s, 0, 2000, trace=False)["s"]
+    o = orc.sweeps(p, W, s, 2000, 150000, trace=False, observe=True)
+    e, m = o["obs"][:, 4], o["obs"][:, 5]
+    assert abs(e.mean() - e_exact) < 4 * binned_error(e) + 1e-4, (e.mean(), e_exact, binned_error(e))
+    assert abs(m.mean() - m_exact) < 4 * binned_error(m) + 1e-4, (m.mean(), m_exact, binned_error(m))

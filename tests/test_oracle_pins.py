@@ -344,7 +344,7 @@ def test_infinite_temperature_limits():
     p = orc.params(L, l, 0.0, 0.0, 0.0, 0.0, 1.0, proposal=1, seed=3)
     s = inputs.saturated_z(L)[0]
     out = orc.sweeps(p, W, s, 0, 400, trace=False, observe=True)
-    assert out["obs"].shape == (400, 5)
+    assert out["obs"].shape == (400, orc.NOBS)
     eta = orc.eta(out["theta2"], 400)
     g = GOLDEN["cone_angle_infinite_T"]
     exact = math.sqrt((2 / math.pi) ** 2 * (math.pi**2 - 8) / 4)
