@@ -285,6 +285,45 @@ def large_lattice_leg(dipmc, stream, sweeps=8):
             "runs": out}
 
 
+def ising_leg(dipmc, stream, sweeps=50, neq=100, nms=200):
+    """Dipolar Ising variant (Appendix B): 256 replicas of L = 64 at a coupling of
+    0.85 C_D per bond (the paper's J/C_D = 1.7 with J/2 per bond), T/C_D =
+    linspace(0.7, 1.0, 16), reversal moves from stripes of width 1.  Throughput
+    of the simultaneous update (l = 32) and of the exact sequential one (l = L),
+    and their m_st per temperature after a short run."""
+    import torch
+    Lb, Rb = 64, 256
+    cd = 1.0 / 0.85
+    tt = np.repeat(np.linspace(0.7, 1.0, 16), Rb // 16)
+    y = np.arange(Lb)[:, None] * np.ones((1, Lb))
+    s0 = np.zeros((Rb, 3, Lb, Lb), np.float32)
+    s0[:, 2] = np.where(y % 2 == 0, 1.0, -1.0)
+    out = {"workload": "256 x L=64 Ising, J_bond/C_D = 0.85, T/C_D in [0.7, 1.0], reversal moves",
+           "sweeps_timed": sweeps}
+    for lb in (32, 64):
+        lat = dipmc.Lattice(Lb, lb, Rb, seed=17)
+        lat.precompute_W(A_IMG, True)
+        lat.set_field_path(dipmc.MC_PATH_DIRECT)
+        lat.set_proposal(dipmc.PROPOSAL_FLIP, 0.5)
+        for r in range(Rb):
+            lat.set_params(1.0, cd, 0.0, 0.0, f32(tt[r] * cd), replica=r)
+        lat.init_spins(dipmc.INIT_USER, s0)
+        lat.sweep(neq, 0, stream)
+        lat.reset_observables()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        lat.sweep(nms, 1, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        key = "simultaneous_l32" if lb == 32 else "exact_l64"
+        mst = [lat.observables(r)["m_st"]["mean"] for r in range(Rb)]
+        out[key] = {"site_updates_per_s": Rb * Lb * Lb * nms / (a.elapsed_time(b) / 1e3),
+                    "m_st_by_T": [round(float(np.mean(mst[i * 16:(i + 1) * 16])), 4) for i in range(16)]}
+        lat.close()
+    out["T_over_CD"] = [round(float(v), 4) for v in np.linspace(0.7, 1.0, 16)]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -300,6 +339,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-large", action="store_true", help="skip the L=256 leg")
     ap.add_argument("--large-only", action="store_true", help="run only the L=256 leg")
+    ap.add_argument("--no-ising", action="store_true", help="skip the dipolar Ising leg")
     ap.add_argument("--serve-only", action="store_true", help="run only the serving leg")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-scale", type=float, default=0.002, help="factor on the requests' sweep counts")
@@ -486,6 +526,10 @@ def main():
     if rank == 0 and not args.no_large:
         large = large_lattice_leg(dipmc, stream)
 
+    ising = None
+    if rank == 0 and not args.no_ising:
+        ising = ising_leg(dipmc, stream)
+
     serving = None
     if rank == 0 and not args.no_serve:
         serving = serving_leg(dipmc, args.serve_requests, args.serve_scale, args.serve_quantum, 64.0,
@@ -514,6 +558,7 @@ def main():
             "e2e": e2e,
             "plain": plain,
             "large_lattice": large,
+            "ising": ising,
             "serving": serving,
             "gpu_launches": gpu_launches,
             "clocks": clk,

@@ -56,7 +56,11 @@ extern "C" {
 #define MC_OBS_ABS_MZ 2 /* |m_z|                                     */
 #define MC_OBS_MPAR 3   /* M_par = sqrt(M_x^2 + M_y^2)  (Sec. 4.1)   */
 #define MC_OBS_E 4      /* energy per spin E/N                       */
-#define MC_NOBS 5
+#define MC_OBS_MST 5    /* staggered magnetisation m_st (Appendix B): sqrt(m_h^2 + m_v^2) from the z
+                           components of the four 2 x 2 sub-lattices, m_h = m1 + m2 - m3 - m4,
+                           m_v = m1 + m4 - m3 - m2, m_lambda = (1/N) sum over sub-lattice lambda;
+                           1 = (x, y even), 2 = (x odd, y even), 3 = (x, y odd), 4 = (x even, y odd) */
+#define MC_NOBS 6
 
 /* Field paths (mc_set_field_path). */
 #define MC_PATH_AUTO 0
@@ -109,7 +113,8 @@ int mc_set_params(mc_lattice *lat, int replica, double J, double C_D, double K2,
 
 /* Proposal (Sec. 3.1): kind 0 = uniform on the spherical cap of half-angle
  * cone_rad around the current spin (0 < cone_rad <= pi); kind 1 = uniform on S^2
- * (the paper's choice; cone_rad ignored). */
+ * (the paper's choice; cone_rad ignored); kind 2 = complete reversal S = -s, the
+ * dipolar Ising variant of Appendix B when the spins are (0, 0, +-1) (init mode 3). */
 int mc_set_proposal(mc_lattice *lat, int kind, double cone_rad);
 
 /* Site schedule: kind 0 = every sweep visits the l^2 offsets in a pseudo-random
@@ -140,8 +145,10 @@ int mc_set_field_path(mc_lattice *lat, int path);
 int mc_set_window(mc_lattice *lat, int B);
 
 /* Initial spins: mode 0 = random uniform on S^2 from the seed; 1 = all +z;
- * 2 = copy `user` (host pointer, [R][3][L][L] FP32, used as given).  Resets the
- * sweep counter to 0, clears observables, invalidates the tracked energy. */
+ * 2 = copy `user` (host pointer, [R][3][L][L] FP32, used as given); 3 = random
+ * Ising spins (0, 0, +-1) from the seed (+1 where the site's first uniform is
+ * below 1/2).  Resets the sweep counter to 0, clears observables and the energy
+ * histogram, invalidates the tracked energy. */
 int mc_init_spins(mc_lattice *lat, int mode, const float *user);
 
 /* Replica-summed dipole tensor (Sec. 2.1, Eq. 2), computed on the GPU in FP64:
@@ -177,6 +184,14 @@ int mc_sweep_trace(mc_lattice *lat, int nsweeps, float *trace, size_t trace_floa
 
 /* Statistics of one replica (synchronises the lattice's last stream). */
 int mc_observables(mc_lattice *lat, int replica, mc_obs *out);
+
+/* Histogram of the energy per spin E/N over the measured sweeps (Appendix B,
+ * energy distributions near the transition): nbins equal bins on [lo, hi) per
+ * replica; samples outside are not counted.  Setting it clears the counts;
+ * nbins = 0 turns it off.  mc_get_histogram copies nbins counts of one replica
+ * to a host array (synchronises the lattice's last stream). */
+int mc_set_histogram(mc_lattice *lat, double lo, double hi, int nbins);
+int mc_get_histogram(mc_lattice *lat, int replica, int64_t *counts);
 
 /* Clear all observable accumulators (binning, cone angle, acceptance). */
 int mc_reset_observables(mc_lattice *lat);
@@ -292,9 +307,9 @@ typedef struct mc_request {
     int measure_every;       /* observables every this many sweeps (0 = none); results match a lone
                                 run whose mc_sweep calls are multiples of it */
     uint64_t seed;
-    int init_mode;           /* 0 random on S^2 from the seed, 1 all +z (as mc_init_spins) */
+    int init_mode;           /* 0 random on S^2 from the seed, 1 all +z, 3 random Ising (as mc_init_spins) */
     int image_cutoff;        /* A of mc_precompute_W; 0 = 64 (tail correction on) */
-    int proposal;            /* 0 cap of half-angle cone (0 = 0.5 rad), 1 uniform on S^2 */
+    int proposal;            /* 0 cap of half-angle cone (0 = 0.5 rad), 1 uniform on S^2, 2 reversal */
     double cone;
 } mc_request;
 

@@ -44,7 +44,7 @@ int cuda_fail(cudaError_t e, const char *what) {
     } while (0)
 
 constexpr uint32_t kMagic = 0x444d4331u;  // "DMC1"
-constexpr int kVersion = 1;
+constexpr int kVersion = 2;
 
 }  // namespace
 
@@ -102,6 +102,10 @@ struct mc_lattice {
     // kernel timing (events recorded around launches while enabled)
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> tev[MC_NKCLASS];
+    // energy histogram of the measured sweeps, [R][hist_bins]
+    unsigned long long *hist = nullptr;
+    double hist_lo = 0.0, hist_scale = 0.0;
+    int hist_bins = 0;
     // packed launches (serving): per-slot stream state, host shadow and pinned staging
     bool packed = false;
     SlotState *slots_dev = nullptr, *slots_pin = nullptr;
@@ -142,6 +146,7 @@ void free_all(mc_lattice *p) {
     if (p->own) cudaStreamDestroy(p->own);
     if (p->ev_in) cudaEventDestroy(p->ev_in);
     if (p->ev_out) cudaEventDestroy(p->ev_out);
+    cudaFree(p->hist);
     cudaFree(p->specT);
     cudaFree(p->specS);
     cudaFree(p->specH);
@@ -218,6 +223,17 @@ bool path_supported(const mc_lattice *p, int path) {
     }
 }
 
+EnergyHist hist_of(const mc_lattice *p) {
+    EnergyHist h;
+    if (p->hist && p->hist_bins > 0) {
+        h.counts = p->hist;
+        h.lo = p->hist_lo;
+        h.scale = p->hist_scale;
+        h.nbins = p->hist_bins;
+    }
+    return h;
+}
+
 int resolve_path(const mc_lattice *p) {
     if (p->path != MC_PATH_AUTO) return p->path;
     if (direct_supported(p->L, p->l)) return MC_PATH_DIRECT;
@@ -235,6 +251,7 @@ int upload_params(mc_lattice *p) {
 int clear_obs(mc_lattice *p, cudaStream_t st) {
     CK(cudaMemsetAsync(p->obs, 0, sizeof(ObsAcc) * p->R, st));
     CK(cudaMemsetAsync(p->theta2, 0, sizeof(double) * (size_t)p->R * p->N(), st));
+    if (p->hist) CK(cudaMemsetAsync(p->hist, 0, sizeof(unsigned long long) * p->R * p->hist_bins, st));
     return MC_OK;
 }
 
@@ -339,6 +356,7 @@ int run_windows(mc_lattice *p, int path, int nsweeps, int measure_every, float *
     b.trace = trace;
     b.stale = tensor ? p->H0 : p->field;
     b.wq = p->wq;
+    b.hist = hist_of(p);
     TcFieldArgs ta{};
     if (tensor) {
         ta.L = p->L; ta.Sw = Sw; ta.R = p->R; ta.NT = p->NT; ta.ldh = 3 * Sw; ta.tmem_cols = p->tmem_cols;
@@ -447,7 +465,7 @@ int run_fft(mc_lattice *p, int nsweeps, int measure_every, float *trace, cudaStr
             cudaError_t e = launch_fft_field(p->L, p->R, p->spins, p->What, p->fft_scratch, p->field, st);
             if (e != cudaSuccess) return cuda_fail(e, "FFT field");
             e = launch_fft_observe(p->L, p->R, p->spins, p->field, p->dparams, p->energy, p->obs, p->theta2,
-                                   b.slots, it, measure_every, st);
+                                   b.slots, it, measure_every, hist_of(p), st);
             if (e != cudaSuccess) return cuda_fail(e, "observables");
         }
     }
@@ -526,7 +544,7 @@ int run_spectral(mc_lattice *p, int nsweeps, int measure_every, float *trace, cu
             rc = full_field(p, st);
             if (rc) return rc;
             e = launch_fft_observe(p->L, p->R, p->spins, p->field, p->dparams, p->energy, p->obs, p->theta2,
-                                   b.slots, it, measure_every, st);
+                                   b.slots, it, measure_every, hist_of(p), st);
             if (e != cudaSuccess) return cuda_fail(e, "observables");
         }
     }
@@ -627,6 +645,7 @@ int run_sweeps(mc_lattice *p, int nsweeps, int measure_every, float *trace, cuda
     b.obs = p->obs;
     b.theta2 = p->theta2;
     b.trace = trace;
+    b.hist = hist_of(p);
     const int path = resolve_path(p);
     if (path < 0 || !path_supported(p, path))
         return fail(MC_ENOSYS, "no field path supports L=%d l=%d (path %d)", p->L, p->l, p->path);
@@ -749,7 +768,7 @@ int mc_set_proposal(mc_lattice *p, int kind, double cone) {
     if (p) drop_graphs(p);
     int rc = check(p);
     if (rc) return rc;
-    if (kind != 0 && kind != 1) return fail(MC_EINVAL, "proposal kind must be 0 or 1");
+    if (kind < 0 || kind > 2) return fail(MC_EINVAL, "proposal kind must be 0, 1 or 2");
     if (kind == 0 && !(cone > 0.0 && cone <= M_PI)) return fail(MC_EINVAL, "cone must be in (0, pi]");
     p->proposal = kind;
     if (kind == 0) p->cone = cone;
@@ -789,7 +808,7 @@ int mc_set_window(mc_lattice *p, int B) {
 int mc_init_spins(mc_lattice *p, int mode, const float *user) {
     int rc = check(p);
     if (rc) return rc;
-    if (mode < 0 || mode > 2) return fail(MC_EINVAL, "init mode must be 0, 1 or 2");
+    if (mode < 0 || mode > 3) return fail(MC_EINVAL, "init mode must be 0, 1, 2 or 3");
     CK(cudaDeviceSynchronize());
     if (mode == 2) {
         if (!user) return fail(MC_EINVAL, "mode 2 needs a host array");
@@ -889,6 +908,37 @@ int mc_observables(mc_lattice *p, int replica, mc_obs *out) {
     } else {
         out->eta = NAN;
     }
+    return MC_OK;
+}
+
+int mc_set_histogram(mc_lattice *p, double lo, double hi, int nbins) {
+    if (p) drop_graphs(p);
+    int rc = check(p);
+    if (rc) return rc;
+    if (nbins < 0 || nbins > (1 << 20)) return fail(MC_EINVAL, "nbins %d outside [0, 2^20]", nbins);
+    if (nbins > 0 && !(hi > lo)) return fail(MC_EINVAL, "histogram range needs hi > lo");
+    CK(cudaDeviceSynchronize());
+    cudaFree(p->hist);
+    p->hist = nullptr;
+    p->hist_bins = 0;
+    if (nbins == 0) return MC_OK;
+    CK(cudaMalloc(&p->hist, sizeof(unsigned long long) * p->R * nbins));
+    CK(cudaMemset(p->hist, 0, sizeof(unsigned long long) * p->R * nbins));
+    p->hist_bins = nbins;
+    p->hist_lo = lo;
+    p->hist_scale = (double)nbins / (hi - lo);
+    return MC_OK;
+}
+
+int mc_get_histogram(mc_lattice *p, int replica, int64_t *counts) {
+    int rc = check(p);
+    if (rc) return rc;
+    if (!counts) return fail(MC_EINVAL, "counts is null");
+    if (!p->hist) return fail(MC_ENOTREADY, "no histogram set (mc_set_histogram)");
+    if (replica < 0 || replica >= p->R) return fail(MC_EINVAL, "replica %d out of range", replica);
+    CK(cudaStreamSynchronize(p->last));
+    CK(cudaMemcpy(counts, p->hist + (size_t)replica * p->hist_bins, sizeof(int64_t) * p->hist_bins,
+                  cudaMemcpyDeviceToHost));
     return MC_OK;
 }
 
@@ -1214,6 +1264,9 @@ int pack_fill(mc_lattice *p, int slot, int count, uint64_t seed, const RepParams
     if (e != cudaSuccess) return cuda_fail(e, "init kernel");
     CK(cudaMemsetAsync(p->obs + slot, 0, sizeof(ObsAcc) * count, st));
     CK(cudaMemsetAsync(p->theta2 + (size_t)slot * N, 0, sizeof(double) * N * count, st));
+    if (p->hist)
+        CK(cudaMemsetAsync(p->hist + (size_t)slot * p->hist_bins, 0,
+                           sizeof(unsigned long long) * p->hist_bins * count, st));
     p->last = st;
     if (p->path == MC_PATH_FFT || p->path == MC_PATH_SPECTRAL) {
         // these paths measure the energy afresh; NaN (all bits set) until then,
@@ -1286,6 +1339,7 @@ int pack_launch_direct(mc_lattice *p, int mx, int measure_every, cudaStream_t st
     b.obs = p->obs;
     b.theta2 = p->theta2;
     b.slots = p->slots_dev;
+    b.hist = hist_of(p);
     cudaError_t e;
     {
         TimedLaunch tl(p, MC_K_SWEEP_DIRECT, st);

@@ -96,7 +96,8 @@ cudaError_t launch_wtilde(int L, int A, int tail, double *W64, float *W32, cudaS
 }
 
 // ---------------------------------------------------------------------------
-// Initial spins: mode 0 uniform on S^2 from Philox {site, r, 0, tag}; 1 = +z.
+// Initial spins: mode 0 uniform on S^2 from Philox {site, r, 0, tag}; 1 = +z;
+// 3 = Ising +-z from the same counter.
 // ---------------------------------------------------------------------------
 __global__ void k_init_spins(int L, int R, uint2 key, int mode, float *spins) {
     const int N = L * L;
@@ -104,7 +105,11 @@ __global__ void k_init_spins(int L, int R, uint2 key, int mode, float *spins) {
     if (gid >= (long long)N * R) return;
     const int r = (int)(gid / N), i = (int)(gid % N);
     float sx = 0.f, sy = 0.f, sz = 1.f;
-    if (mode == 0) {
+    if (mode == 3) {
+        // Ising spin (Appendix B): +z where the first uniform is below 1/2
+        const uint4 w = philox(make_uint4((uint32_t)i, (uint32_t)r, 0u, kTagInit), key);
+        sz = u24f(w.x) < 0.5f ? 1.0f : -1.0f;
+    } else if (mode == 0) {
         const uint4 w = philox(make_uint4((uint32_t)i, (uint32_t)r, 0u, kTagInit), key);
         sz = 2.0f * u24f(w.x) - 1.0f;
         const float rr = sqrtf(fmaxf(0.0f, (1.0f - sz) * (1.0f + sz)));

@@ -229,7 +229,11 @@ __global__ void k_fft_update(const FftStepConfig cfg, const FftStepBuffers buf) 
         sincospif(2.0f * u24f(wds.y), &sps, &cps);
         const float s0 = s[q], s1 = s[N + q], s2 = s[2 * N + q];
         float S0, S1, S2;
-        if (cfg.proposal == 1) {
+        if (cfg.proposal == kPropFlip) {            // Appendix B reversal
+            S0 = -s0;
+            S1 = -s1;
+            S2 = -s2;
+        } else if (cfg.proposal == kPropSphere) {
             const float z = 2.0f * u1 - 1.0f;
             const float rr = sqrtf(fmaxf(0.0f, (1.0f - z) * (1.0f + z)));
             S0 = rr * cps;
@@ -293,7 +297,8 @@ __global__ void k_fft_update(const FftStepConfig cfg, const FftStepBuffers buf) 
 __global__ void __launch_bounds__(256) k_fft_observe(int L, const float *__restrict__ spins,
                                                      const float *__restrict__ field, const RepParams *__restrict__ P,
                                                      double *energy, ObsAcc *obs, double *theta2,
-                                                     const SlotState *slots, int it, int measure_every) {
+                                                     const SlotState *slots, int it, int measure_every,
+                                                     const EnergyHist hist) {
     const int N = L * L, r = blockIdx.x, tid = threadIdx.x;
     if (slots) {
         const SlotState sl = slots[r];
@@ -302,7 +307,7 @@ __global__ void __launch_bounds__(256) k_fft_observe(int L, const float *__restr
     const float *s = spins + (size_t)r * 3 * N;
     const float *f = field + (size_t)r * 3 * N;
     const RepParams p = P[r];
-    double mx = 0, my = 0, mz = 0, ex = 0, an = 0, dp = 0;
+    double mx = 0, my = 0, mz = 0, ex = 0, an = 0, dp = 0, mh = 0, mv = 0;
     for (int i = tid; i < N; i += blockDim.x) {
         const int x = i % L, y = i / L;
         const int ixp = y * L + (x + 1 == L ? 0 : x + 1);
@@ -311,6 +316,8 @@ __global__ void __launch_bounds__(256) k_fft_observe(int L, const float *__restr
         mx += a;
         my += b;
         mz += c;
+        mh += (y & 1) ? -c : c;     // m1 + m2 - m3 - m4 (rows)
+        mv += (x & 1) ? -c : c;     // m1 + m4 - m3 - m2 (columns)
         ex += a * ((double)s[ixp] + (double)s[iyp]) + b * ((double)s[N + ixp] + (double)s[N + iyp]) +
               c * ((double)s[2 * N + ixp] + (double)s[2 * N + iyp]);
         const double z2 = c * c;
@@ -321,18 +328,18 @@ __global__ void __launch_bounds__(256) k_fft_observe(int L, const float *__restr
             theta2[(size_t)r * N + i] += (double)(th * th);
         }
     }
-    __shared__ double red[6][8];
-    double v[6] = {mx, my, mz, ex, an, dp};
-    for (int k = 0; k < 6; ++k)
+    __shared__ double red[8][8];
+    double v[8] = {mx, my, mz, ex, an, dp, mh, mv};
+    for (int k = 0; k < 8; ++k)
         for (int off = 16; off; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
     if ((tid & 31) == 0)
-        for (int k = 0; k < 6; ++k) red[k][tid >> 5] = v[k];
+        for (int k = 0; k < 8; ++k) red[k][tid >> 5] = v[k];
     __syncthreads();
     __shared__ double x_s[MC_NOBS];
     if (tid == 0) {
-        double t[6] = {0, 0, 0, 0, 0, 0};
+        double t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-            for (int k = 0; k < 6; ++k) t[k] += red[k][w];
+            for (int k = 0; k < 8; ++k) t[k] += red[k][w];
         const double Mx = t[0] / N, My = t[1] / N, Mz = t[2] / N;
         const double E = -(double)p.J * t[3] + t[4] + 0.5 * (double)p.CD * t[5];
         energy[r] = E;
@@ -341,6 +348,8 @@ __global__ void __launch_bounds__(256) k_fft_observe(int L, const float *__restr
         x_s[MC_OBS_ABS_MZ] = fabs(Mz);
         x_s[MC_OBS_MPAR] = sqrt(Mx * Mx + My * My);
         x_s[MC_OBS_E] = E / N;
+        x_s[MC_OBS_MST] = sqrt(t[6] * t[6] + t[7] * t[7]) / N;
+        hist_push(hist, r, E / N);
     }
     __syncthreads();
     if (obs && tid < kNB) {
@@ -464,8 +473,8 @@ cudaError_t launch_fft_update(const FftStepConfig &c, const FftStepBuffers &b, c
 
 cudaError_t launch_fft_observe(int L, int R, const float *spins, const float *field, const RepParams *P,
                                double *energy, ObsAcc *obs, double *theta2, const SlotState *slots, int it,
-                               int measure_every, cudaStream_t st) {
-    k_fft_observe<<<R, 256, 0, st>>>(L, spins, field, P, energy, obs, theta2, slots, it, measure_every);
+                               int measure_every, const EnergyHist &hist, cudaStream_t st) {
+    k_fft_observe<<<R, 256, 0, st>>>(L, spins, field, P, energy, obs, theta2, slots, it, measure_every, hist);
     return cudaGetLastError();
 }
 

@@ -39,7 +39,7 @@ cudaError_t launch_fft_update(const FftStepConfig &c, const FftStepBuffers &b, c
 // (t0 + it + 1) is a multiple of measure_every and that are active at sweep `it`.
 cudaError_t launch_fft_observe(int L, int R, const float *spins, const float *field, const RepParams *P,
                                double *energy, ObsAcc *obs, double *theta2, const SlotState *slots, int it,
-                               int measure_every, cudaStream_t st);
+                               int measure_every, const EnergyHist &hist, cudaStream_t st);
 // attempted += add for every replica; with slots, += min(nsweeps_call, slot sweeps) * N.
 cudaError_t launch_add_attempted(ObsAcc *obs, int R, long long add, const SlotState *slots, int nsweeps_call,
                                  long long N, cudaStream_t st);

@@ -35,6 +35,8 @@ __host__ __device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
 
 enum : uint32_t { kTagAttempt = 1u << 24, kTagPerm = 2u << 24, kTagDraw = 3u << 24, kTagInit = 4u << 24 };
 
+enum : int { kPropCap = 0, kPropSphere = 1, kPropFlip = 2 };
+
 // Uniform in [0, 1) with 24 random bits (exact in FP32).
 __device__ __forceinline__ float u24f(uint32_t w) { return (float)(w >> 8) * 5.9604644775390625e-8f; }
 
@@ -102,6 +104,19 @@ struct SweepConfig {
     int schedule;     // 0 permutation, 1 draw
 };
 
+// Histogram of E/N per replica: counts[R][nbins] over [lo, lo + nbins / scale).
+struct EnergyHist {
+    unsigned long long *counts = nullptr;
+    double lo = 0.0, scale = 0.0;
+    int nbins = 0;
+};
+
+__device__ __forceinline__ void hist_push(const EnergyHist &h, int r, double e) {
+    if (!h.counts) return;
+    const double b = (e - h.lo) * h.scale;
+    if (b >= 0.0 && b < (double)h.nbins) atomicAdd(h.counts + (size_t)r * h.nbins + (int)b, 1ULL);
+}
+
 // Per-replica stream state of a packed launch: independent requests share one
 // launch, each replica slot with its own Philox key, its own sweep counter t0,
 // the replica index its counters use, and how many of the launch's sweeps it
@@ -123,6 +138,7 @@ struct SweepBuffers {
     double *theta2 = nullptr;           // [R][N]
     float *trace = nullptr;             // optional [R][nsweeps][l^2][n][MC_TRACE_W]
     const SlotState *slots = nullptr;   // optional [R]: packed launch
+    EnergyHist hist;                    // optional energy histogram
 };
 
 // Launchers (implemented in their .cu files).  Return a cudaError_t.

@@ -285,7 +285,7 @@ int try_admit(mc_server *s, Req &q) {
             slot = 0;
             s->packs.push_back(std::move(np));
         }
-        int rc = pack_fill(pk->lat, slot, r.replicas, r.seed, params_of(r), r.init_mode == 1 ? 1 : 0, pk->st);
+        int rc = pack_fill(pk->lat, slot, r.replicas, r.seed, params_of(r), r.init_mode, pk->st);
         if (rc) return fail_req(s, q, mc_last_error());
         for (int i = 0; i < r.replicas; ++i) pk->owner[slot + i] = q.id;
         q.pack = pk;
@@ -322,7 +322,7 @@ int try_admit(mc_server *s, Req &q) {
             so = nu.get();
             s->solos.push_back(std::move(nu));
         }
-        int rc = lattice_refill(so->lat, r.seed, params_of(r), r.init_mode == 1 ? 1 : 0, so->st);
+        int rc = lattice_refill(so->lat, r.seed, params_of(r), r.init_mode, so->st);
         if (rc) return fail_req(s, q, mc_last_error());
         so->owner = q.id;
         q.solo = so;
@@ -481,9 +481,9 @@ int mc_server_submit(mc_server *s, const mc_request *r, uint64_t *id) {
     mc_request q = *r;
     if (q.replicas < 1) q.replicas = 1;
     if (q.L < 2 || q.L > 4096 || q.sweeps < 0 || !(q.T > 0) || q.measure_every < 0 || q.init_mode < 0 ||
-        q.init_mode > 1 || q.proposal < 0 || q.proposal > 1)
+        q.init_mode > 3 || q.init_mode == 2 || q.proposal < 0 || q.proposal > 2)
         return set_last_error(MC_EINVAL, "request needs 2 <= L <= 4096, T > 0, sweeps >= 0, measure_every >= 0, "
-                                         "init_mode and proposal in {0, 1}");
+                                         "init_mode in {0, 1, 3} and proposal in {0, 1, 2}");
     if (q.l == 0) {
         // the smallest spacing within the error bound; a larger divisor of L only
         // lowers the error, so move up to the first one a pack path serves

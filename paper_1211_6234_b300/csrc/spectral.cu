@@ -362,7 +362,11 @@ __global__ void __launch_bounds__(kUpdMaxThreads) k_spec_update(const SpecConfig
         sincospif(2.0f * u24f(wds.y), &sps, &cps);
         const float s0 = s[q], s1 = s[N + q], s2 = s[2 * N + q];
         float S0, S1, S2;
-        if (cfg.proposal == 1) {
+        if (cfg.proposal == kPropFlip) {            // Appendix B reversal
+            S0 = -s0;
+            S1 = -s1;
+            S2 = -s2;
+        } else if (cfg.proposal == kPropSphere) {
             const float z = 2.0f * u1 - 1.0f;
             const float rr = sqrtf(fmaxf(0.0f, (1.0f - z) * (1.0f + z)));
             S0 = rr * cps;

@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
     __shared__ float4 s_acc[2][32];                              // accepted moves of a sub-step: (delta, x | y << 16),
     __shared__ int s_nacc[2];                                    // double-buffered by sub-step parity
     __shared__ double s_epart[32];
-    __shared__ float s_mred[kWThreads / 32][4];
+    __shared__ float s_mred[kWThreads / 32][6];
 
     const RepParams P = buf.params[r];
     const uint2 key = cfg.key;
@@ -117,7 +117,11 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
     auto propose = [&](int q, float u1, float cps, float sps, float4 &S, float4 &D) {
         const float4 sq = s4[q];
         float S0, S1, S2;
-        if (cfg.proposal == 1) {
+        if (cfg.proposal == kPropFlip) {            // Appendix B reversal
+            S0 = -sq.x;
+            S1 = -sq.y;
+            S2 = -sq.z;
+        } else if (cfg.proposal == kPropSphere) {
             const float z = 2.0f * u1 - 1.0f;
             const float rr = sqrtf(fmaxf(0.0f, (1.0f - z) * (1.0f + z)));
             S0 = rr * cps;
@@ -445,13 +449,16 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
     }
     __syncthreads();
     if (cfg.measure) {
-        float mx = 0.f, my = 0.f, mz = 0.f;
+        float mx = 0.f, my = 0.f, mz = 0.f, mh = 0.f, mv = 0.f;
         double *gt = buf.theta2 ? buf.theta2 + (size_t)r * N : nullptr;
         for (int i = tid; i < N; i += kWThreads) {
             const float4 a = s4[i];
             mx += a.x;
             my += a.y;
             mz += a.z;
+            const int iy = i / L, ix = i - iy * L;
+            mh += (iy & 1) ? -a.z : a.z;     // m1 + m2 - m3 - m4 (rows)
+            mv += (ix & 1) ? -a.z : a.z;     // m1 + m4 - m3 - m2 (columns)
             if (gt) {
                 const float th = acosf(fminf(1.0f, fmaxf(-1.0f, a.z))) - 0.5f * kPiF;
                 gt[i] += (double)(th * th);
@@ -461,28 +468,36 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
             mx += __shfl_xor_sync(0xffffffffu, mx, off);
             my += __shfl_xor_sync(0xffffffffu, my, off);
             mz += __shfl_xor_sync(0xffffffffu, mz, off);
+            mh += __shfl_xor_sync(0xffffffffu, mh, off);
+            mv += __shfl_xor_sync(0xffffffffu, mv, off);
         }
         if (lane == 0) {
             s_mred[warp][0] = mx;
             s_mred[warp][1] = my;
             s_mred[warp][2] = mz;
+            s_mred[warp][3] = mh;
+            s_mred[warp][4] = mv;
         }
         __syncthreads();
         if (tid < kNB && buf.obs) {
-            double Mx = 0, My = 0, Mz = 0;
+            double Mx = 0, My = 0, Mz = 0, Mh = 0, Mv = 0;
             for (int ww = 0; ww < kWThreads / 32; ++ww) {
                 Mx += s_mred[ww][0];
                 My += s_mred[ww][1];
                 Mz += s_mred[ww][2];
+                Mh += s_mred[ww][3];
+                Mv += s_mred[ww][4];
             }
-            Mx /= N; My /= N; Mz /= N;
+            Mx /= N; My /= N; Mz /= N; Mh /= N; Mv /= N;
             double x[MC_NOBS];
             x[MC_OBS_ABS_M] = sqrt(Mx * Mx + My * My + Mz * Mz);
             x[MC_OBS_MZ] = Mz;
             x[MC_OBS_ABS_MZ] = fabs(Mz);
             x[MC_OBS_MPAR] = sqrt(Mx * Mx + My * My);
             x[MC_OBS_E] = buf.energy[r] / N;
+            x[MC_OBS_MST] = sqrt(Mh * Mh + Mv * Mv);
             obs_push_level(buf.obs[r], x, tid);
+            if (tid == 0) hist_push(buf.hist, r, x[MC_OBS_E]);
         }
     }
     if (tid == 0 && buf.obs) {

@@ -36,6 +36,7 @@ struct WindowBuffers {
     float *trace;                 // optional
     const float *stale;           // see stale_mode
     const float4 *wq;             // [(L/2+1)^2] W~ on the minimum-image quarter, (xx, xy, yy, zz)
+    EnergyHist hist;              // optional energy histogram
 };
 
 size_t window_smem_bytes(int L, int Sw);

@@ -17,10 +17,12 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdipmc.so")
 
 MC_OK, MC_EINVAL, MC_ENOMEM, MC_ENOTREADY, MC_ETIMEOUT, MC_ECUDA, MC_ENOSYS = 0, -1, -2, -3, -4, -5, -6
-MC_NOBS = 5
-OBS_NAMES = ("abs_m", "m_z", "abs_m_z", "m_par", "e")
+MC_NOBS = 6
+OBS_NAMES = ("abs_m", "m_z", "abs_m_z", "m_par", "e", "m_st")
 MC_PATH_AUTO, MC_PATH_DIRECT, MC_PATH_WINDOW_F32, MC_PATH_TENSOR, MC_PATH_FFT, MC_PATH_SPECTRAL = 0, 1, 2, 3, 4, 5
 MC_TRACE_W = 10
+PROPOSAL_CAP, PROPOSAL_SPHERE, PROPOSAL_FLIP = 0, 1, 2
+INIT_RANDOM, INIT_UP, INIT_USER, INIT_ISING = 0, 1, 2, 3
 
 # Every symbol include/dipmc.h declares.
 ABI_SYMBOLS = (
@@ -29,7 +31,7 @@ ABI_SYMBOLS = (
     "mc_precompute_W", "mc_sweep", "mc_sweep_trace", "mc_observables", "mc_reset_observables",
     "mc_get_spins", "mc_get_field", "mc_get_W", "mc_energy", "mc_get_sweep_counter",
     "mc_checkpoint", "mc_restore", "mc_energy_noalloc", "mc_set_timing", "mc_get_timing",
-    "mc_choose_spacing", "mc_autotune",
+    "mc_choose_spacing", "mc_autotune", "mc_set_histogram", "mc_get_histogram",
     "mc_footprint", "mc_server_create", "mc_server_submit", "mc_server_step", "mc_server_poll", "mc_server_request_info",
     "mc_server_collect", "mc_server_get_spins", "mc_server_release", "mc_server_get_stats", "mc_server_destroy",
 )
@@ -109,6 +111,8 @@ def _load():
         "mc_sweep": ([vp, i32, i32, vp], i32),
         "mc_sweep_trace": ([vp, i32, vp, C.c_size_t, vp], i32),
         "mc_observables": ([vp, i32, C.POINTER(mc_obs)], i32),
+        "mc_set_histogram": ([vp, f64, f64, i32], i32),
+        "mc_get_histogram": ([vp, i32, C.POINTER(C.c_int64)], i32),
         "mc_reset_observables": ([vp], i32),
         "mc_get_spins": ([vp, vp, i32, vp], i32),
         "mc_get_field": ([vp, vp, i32, vp], i32),
@@ -263,6 +267,16 @@ class Lattice:
 
     def reset_observables(self):
         _ck(_lib.mc_reset_observables(self.h))
+
+    def set_histogram(self, lo, hi, nbins):
+        """Histogram of E/N over the measured sweeps: nbins bins on [lo, hi)."""
+        _ck(_lib.mc_set_histogram(self.h, lo, hi, nbins))
+        self._hist_bins = nbins
+
+    def histogram(self, replica=0) -> np.ndarray:
+        a = np.zeros(self._hist_bins, np.int64)
+        _ck(_lib.mc_get_histogram(self.h, replica, a.ctypes.data_as(C.POINTER(C.c_int64))))
+        return a
 
     def get_spins(self, out=None, stream=None) -> np.ndarray:
         if out is not None:  # torch CUDA tensor

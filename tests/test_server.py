@@ -15,9 +15,10 @@ torch = pytest.importorskip("torch")
 
 
 def lone_run(dipmc, L, l, T, sweeps, seed, replicas=1, K2=0.8, K4=0.0, C_D=0.1, J=1.0, measure_every=1,
-             init_mode=0, path=None):
+             init_mode=0, path=None, proposal=0):
     with dipmc.Lattice(L, l, replicas, seed) as lat:
         lat.set_params(J=J, C_D=C_D, K2=K2, K4=K4, T=T)
+        lat.set_proposal(proposal, 0.5)
         lat.precompute_W(64, True)
         if path is not None:
             lat.set_field_path(path)
@@ -89,6 +90,7 @@ def test_packed_requests_equal_their_lone_runs(dipmc):
         dict(L=32, l=16, T=0.6, sweeps=33, seed=16),
         dict(L=128, l=16, T=0.6, sweeps=5, seed=21),
         dict(L=128, l=16, T=0.4, sweeps=3, seed=24, K4=0.2, replicas=2),
+        dict(L=32, l=8, T=0.5, sweeps=19, seed=17, C_D=0.588, K2=0.0, proposal=2, init_mode=3),
     ]
     with dipmc.Server(hbm_budget_bytes=4 << 30, quantum_sweeps=2) as srv:
         ids = [srv.submit(**s) for s in specs]
@@ -104,7 +106,7 @@ def test_packed_requests_equal_their_lone_runs(dipmc):
                 same_obs(srv.collect(rid, r), obs_lone[r])
         st = srv.stats()
         assert st["done"] == len(specs) and st["running"] == 0 and st["queued"] == 0
-        assert st["packs"] == 4 and st["lone"] == 0
+        assert st["packs"] == 5 and st["lone"] == 0
 
 
 @gpu
