@@ -150,6 +150,81 @@ int orc_wtilde(int L, int A, int tail, double *W)
     return 0;
 }
 
+/*
+ * W~ by the Ewald/Harris split of Sec. 2.1 (real-space erfc part plus a Fourier
+ * part over the reciprocal lattice of the L x L cell), for two layers a height
+ * z apart (z = 0: the lattice itself).  With F(R) = sum_G 1/|R + G| over the
+ * in-plane lattice vectors G and the tensor W_ab = -d_a d_b (1/r) =
+ * (delta_ab - 3 r^_a r^_b)/r^3 of Sec. 2.1, 1/r = erfc(r/a)/r + erf(r/a)/r,
+ * a = 2 eta:
+ *   short range: -d_a d_b of g(R) = erfc(R/a)/R summed over G, using
+ *     d_a d_b g(|d|) = g'' d_a d_b / R^2 + g' (delta_ab - d_a d_b / R^2) / R;
+ *   long range: the in-plane Fourier series (1/A) sum_k g^(k, z) e^{i k.rho}
+ *     (A = L^2, k = 2 pi (m, n) / L) of the erf part, with
+ *     g^(k, z) = (pi/k) [e^{kz} erfc(k eta + z/a) + e^{-kz} erfc(k eta - z/a)],
+ *     d_z g^ = pi [e^{kz} erfc(k eta + z/a) - e^{-kz} erfc(k eta - z/a)],
+ *     d_z^2 g^ = k^2 g^ - (2 sqrt(pi)/eta) exp(-k^2 eta^2 - z^2/a^2);
+ *     the k = 0 term only reaches zz: -(1/A)(-(2 sqrt(pi)/eta) exp(-z^2/a^2));
+ *   self term (z = 0, rho = 0): the site itself is excluded, G = 0 is dropped
+ *     from the real-space sum and d_a d_b [erf(R/a)/R] at R = 0,
+ *     -4 delta_ab / (3 a^3 sqrt(pi)), is added back.
+ * Output W6[c][L][L], c = xx, xy, yy, zz, xz, yz.  The sums run until the
+ * neglected terms are below 1e-16 relative (erfc(6) ~ 2e-17; exp(-42) ~ 6e-19).
+ */
+int orc_wtilde_ewald(int L, double z, double eta, double *W6)
+{
+    if (L < 1 || !(eta > 0.0) || !W6) return -1;
+    const int N = L * L;
+    const double a = 2.0 * eta, area = (double)L * L, spi = sqrt(ORC_PI);
+    const int nreal = (int)ceil(6.0 * a / L) + 1;
+    const int nrec = (int)ceil(6.5 / eta * L / (2.0 * ORC_PI)) + 1;
+    for (int y = 0; y < L; ++y)
+        for (int x = 0; x < L; ++x) {
+            double w[6] = {0, 0, 0, 0, 0, 0};
+            /* short range */
+            for (int j = -nreal; j <= nreal; ++j)
+                for (int i = -nreal; i <= nreal; ++i) {
+                    const double d[3] = {x + (double)i * L, y + (double)j * L, z};
+                    const double R2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    if (R2 == 0.0) continue;
+                    const double R = sqrt(R2), ga = exp(-R2 / (a * a)), ec = erfc(R / a);
+                    const double g1 = -(2.0 / (a * spi)) * ga / R - ec / R2;
+                    const double g2 = (4.0 / (a * a * a * spi)) * ga + (4.0 / (a * spi)) * ga / R2 + 2.0 * ec / (R2 * R);
+                    const int ia[6] = {0, 0, 1, 2, 0, 1}, ib[6] = {0, 1, 1, 2, 2, 2};
+                    for (int c = 0; c < 6; ++c) {
+                        const double dd = d[ia[c]] * d[ib[c]] / R2;
+                        w[c] -= g2 * dd + g1 * ((ia[c] == ib[c] ? 1.0 : 0.0) - dd) / R;
+                    }
+                }
+            /* long range */
+            for (int n = -nrec; n <= nrec; ++n)
+                for (int m = -nrec; m <= nrec; ++m) {
+                    if (m == 0 && n == 0) continue;
+                    const double kx = 2.0 * ORC_PI * m / L, ky = 2.0 * ORC_PI * n / L;
+                    const double k = sqrt(kx * kx + ky * ky);
+                    const double ep = exp(k * z) * erfc(k * eta + z / a), em = exp(-k * z) * erfc(k * eta - z / a);
+                    const double gh = ORC_PI / k * (ep + em), dgh = ORC_PI * (ep - em);
+                    const double d2gh = k * k * gh - (2.0 * spi / eta) * exp(-k * k * eta * eta - z * z / (a * a));
+                    const double ph = kx * x + ky * y, cs = cos(ph), sn = sin(ph);
+                    w[0] += kx * kx * gh * cs / area;
+                    w[1] += kx * ky * gh * cs / area;
+                    w[2] += ky * ky * gh * cs / area;
+                    w[3] -= d2gh * cs / area;
+                    w[4] += kx * dgh * sn / area;
+                    w[5] += ky * dgh * sn / area;
+                }
+            w[3] += (2.0 * spi / eta) * exp(-z * z / (a * a)) / area;
+            if (z == 0.0 && x == 0 && y == 0) {
+                const double self = -4.0 / (3.0 * a * a * a * spi);
+                w[0] += self;
+                w[2] += self;
+                w[3] += self;
+            }
+            for (int c = 0; c < 6; ++c) W6[c * N + y * L + x] = w[c];
+        }
+    return 0;
+}
+
 static inline int wrap(int v, int L) { v %= L; return v < 0 ? v + L : v; }
 
 /* W~(p - m) applied to a vector s: out = W~(d) s, d = (dx, dy) taken mod L. */

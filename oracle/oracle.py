@@ -65,6 +65,8 @@ def lib():
         _lib.orc_philox4x32_10.argtypes = [u32, u32, u32]
         _lib.orc_wtilde.argtypes = [C.c_int, C.c_int, C.c_int, d]
         _lib.orc_wtilde.restype = C.c_int
+        _lib.orc_wtilde_ewald.argtypes = [C.c_int, C.c_double, C.c_double, d]
+        _lib.orc_wtilde_ewald.restype = C.c_int
         _lib.orc_field.argtypes = [C.c_int, d, d, d]
         _lib.orc_energy.argtypes = [C.c_int, d, d, C.c_double, C.c_double, C.c_double,
                                     C.c_double, d]
@@ -115,6 +117,15 @@ def wtilde(L: int, A: int = 64, tail: bool = True) -> np.ndarray:
     """Replica-summed dipole tensor, shape [4, L, L] (xx, xy, yy, zz; [rho_y, rho_x])."""
     W = np.zeros((4, L, L), np.float64)
     if lib().orc_wtilde(L, A, int(bool(tail)), _dp(W)) != 0:
+        raise ValueError("bad arguments")
+    return W
+
+
+def wtilde_ewald(L: int, z: float = 0.0, eta: float = 0.0) -> np.ndarray:
+    """W~ by the Ewald/Harris split (Sec. 2.1), [6][L][L]: xx, xy, yy, zz, xz, yz
+    for two layers a height z apart; eta = 0 takes L / 4."""
+    W = np.zeros((6, L, L), np.float64)
+    if lib().orc_wtilde_ewald(L, float(z), float(eta) if eta > 0 else L / 4.0, _dp(W)) != 0:
         raise ValueError("bad arguments")
     return W
 
