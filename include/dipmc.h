@@ -204,6 +204,18 @@ int mc_get_spins(mc_lattice *lat, float *dst, int dst_on_device, void *stream);
  * computed directly in FP32 on the GPU.  Synchronises `stream`. */
 int mc_get_field(mc_lattice *lat, float *dst, int dst_on_device, void *stream);
 
+/* W~ by the Ewald/Harris split of Sec. 2.1 (real-space erfc sum plus the
+ * reciprocal-lattice sum of the erf part; FP64 on the GPU): the exact infinite
+ * image sum, which the image window plus continuum tail of mc_precompute_W
+ * approximates.  eta is the splitting width (<= 0: L/4); the result does not
+ * depend on it.  mc_precompute_W_ewald installs it in a handle (as
+ * mc_precompute_W does, recorded with image_cutoff -1).  mc_wtilde_ewald gives
+ * the tensor between two layers a height z apart (the quasi-3D case of the
+ * Sec. 2.1 footnote; z = 0 is the lattice itself), [6][L][L] FP64 to a host
+ * pointer: xx, xy, yy, zz, xz, yz, rho = (x, y) at [y][x].  |z| <= L. */
+int mc_precompute_W_ewald(mc_lattice *lat, double eta);
+int mc_wtilde_ewald(int L, double z, double eta, double *dst_host);
+
 /* W~ in FP64, [4][L][L], to a host pointer.  MC_ENOTREADY before mc_precompute_W. */
 int mc_get_W(mc_lattice *lat, double *dst_host);
 

@@ -846,6 +846,48 @@ int mc_precompute_W(mc_lattice *p, int A, int tail) {
     return MC_OK;
 }
 
+int mc_precompute_W_ewald(mc_lattice *p, double eta) {
+    if (p) drop_graphs(p);
+    int rc = check(p);
+    if (rc) return rc;
+    if (!(eta > 0.0)) eta = p->L / 4.0;
+    double *W6 = nullptr;
+    CK(cudaMalloc(&W6, sizeof(double) * 6 * (size_t)p->N()));
+    cudaError_t e = launch_wtilde_ewald(p->L, 0.0, eta, W6, nullptr);
+    if (e == cudaSuccess) e = launch_take_plane(p->L, W6, p->W64, p->W32, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(W6);
+    if (e != cudaSuccess) return cuda_fail(e, "Ewald W~ kernel");
+    if (!p->wq) CK(cudaMalloc(&p->wq, sizeof(float4) * (size_t)(p->L / 2 + 1) * (p->L / 2 + 1)));
+    e = launch_build_wq(p->L, p->W32, p->wq, nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "W~ quarter table");
+    CK(cudaDeviceSynchronize());
+    p->A = -1;
+    p->tail = 0;
+    p->W_ready = true;
+    p->wsh_ready = false;
+    p->what_ready = false;
+    p->spec_ready = false;
+    p->energy_valid = false;
+    return MC_OK;
+}
+
+int mc_wtilde_ewald(int L, double z, double eta, double *dst) {
+    g_err.clear();
+    if (!dst) return fail(MC_EINVAL, "dst is null");
+    if (L < 2 || L > 4096) return fail(MC_EINVAL, "L=%d outside [2, 4096]", L);
+    if (!(std::fabs(z) <= (double)L)) return fail(MC_EINVAL, "|z| must be <= L");
+    if (!(eta > 0.0)) eta = L / 4.0;
+    const size_t n = (size_t)6 * L * L;
+    double *W6 = nullptr;
+    CK(cudaMalloc(&W6, sizeof(double) * n));
+    cudaError_t e = launch_wtilde_ewald(L, z, eta, W6, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(dst, W6, sizeof(double) * n, cudaMemcpyDeviceToHost);
+    cudaFree(W6);
+    if (e != cudaSuccess) return cuda_fail(e, "Ewald W~ kernel");
+    return MC_OK;
+}
+
 int mc_sweep(mc_lattice *p, int nsweeps, int measure_every, void *stream) {
     int rc = check(p);
     if (rc) return rc;

@@ -79,6 +79,106 @@ __global__ void __launch_bounds__(kWThreads) k_wtilde(int L, int A, int tail, do
     }
 }
 
+// ---------------------------------------------------------------------------
+// W~ by the Ewald/Harris split (Sec. 2.1) for two layers a height z apart
+// (z = 0: the lattice itself), all six components xx, xy, yy, zz, xz, yz.
+// With W_ab = -d_a d_b (1/r) and 1/r = erfc(r/a)/r + erf(r/a)/r, a = 2 eta:
+// the erfc part is summed in real space over the images, the erf part as the
+// in-plane Fourier series over the reciprocal lattice k = 2 pi (m, n) / L of
+//   g^(k, z) = (pi/k)[e^{kz} erfc(k eta + z/a) + e^{-kz} erfc(k eta - z/a)]
+// (d_z g^ = pi[e^{kz} erfc(..) - e^{-kz} erfc(..)], d_z^2 g^ = k^2 g^ -
+// (2 sqrt(pi)/eta) exp(-k^2 eta^2 - z^2/a^2); k = 0 reaches zz only).  At z = 0
+// the site itself is left out and the R -> 0 limit of the erf part,
+// -4/(3 a^3 sqrt(pi)) on the diagonal, is taken back out.  One CTA per rho,
+// threads over the real and reciprocal terms, FP64.
+// ---------------------------------------------------------------------------
+constexpr double kPiD = 3.141592653589793238462643383279502884;
+
+__global__ void __launch_bounds__(kWThreads) k_wtilde_ewald(int L, double z, double eta, int nreal, int nrec,
+                                                            double *W6) {
+    const int N = L * L, rho = blockIdx.x, x = rho % L, y = rho / L;
+    const double a = 2.0 * eta, area = (double)L * L, spi = sqrt(kPiD);
+    const int sr = 2 * nreal + 1, sk = 2 * nrec + 1;
+    const long long nr = (long long)sr * sr, nt = nr + (long long)sk * sk;
+    double w[6] = {0, 0, 0, 0, 0, 0};
+    for (long long g = threadIdx.x; g < nt; g += kWThreads) {
+        if (g < nr) {
+            const int i = (int)(g % sr) - nreal, j = (int)(g / sr) - nreal;
+            const double d0 = x + (double)i * L, d1 = y + (double)j * L, d2 = z;
+            const double R2 = d0 * d0 + d1 * d1 + d2 * d2;
+            if (R2 == 0.0) continue;
+            const double R = sqrt(R2), ga = exp(-R2 / (a * a)), ec = erfc(R / a);
+            const double g1 = -(2.0 / (a * spi)) * ga / R - ec / R2;
+            const double g2 = (4.0 / (a * a * a * spi)) * ga + (4.0 / (a * spi)) * ga / R2 + 2.0 * ec / (R2 * R);
+            const double d[3] = {d0, d1, d2};
+            const int ia[6] = {0, 0, 1, 2, 0, 1}, ib[6] = {0, 1, 1, 2, 2, 2};
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                const double dd = d[ia[c]] * d[ib[c]] / R2;
+                w[c] -= g2 * dd + g1 * ((ia[c] == ib[c] ? 1.0 : 0.0) - dd) / R;
+            }
+        } else {
+            const long long h = g - nr;
+            const int m = (int)(h % sk) - nrec, n = (int)(h / sk) - nrec;
+            if (m == 0 && n == 0) continue;
+            const double kx = 2.0 * kPiD * m / L, ky = 2.0 * kPiD * n / L;
+            const double k = sqrt(kx * kx + ky * ky);
+            const double ep = exp(k * z) * erfc(k * eta + z / a), em = exp(-k * z) * erfc(k * eta - z / a);
+            const double gh = kPiD / k * (ep + em), dgh = kPiD * (ep - em);
+            const double d2gh = k * k * gh - (2.0 * spi / eta) * exp(-k * k * eta * eta - z * z / (a * a));
+            double sn, cs;
+            sincos(kx * x + ky * y, &sn, &cs);
+            w[0] += kx * kx * gh * cs / area;
+            w[1] += kx * ky * gh * cs / area;
+            w[2] += ky * ky * gh * cs / area;
+            w[3] -= d2gh * cs / area;
+            w[4] += kx * dgh * sn / area;
+            w[5] += ky * dgh * sn / area;
+        }
+    }
+    __shared__ double red[6][kWThreads / 32];
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+        for (int off = 16; off; off >>= 1) w[c] += __shfl_xor_sync(0xffffffffu, w[c], off);
+    if ((threadIdx.x & 31) == 0)
+        for (int c = 0; c < 6; ++c) red[c][threadIdx.x >> 5] = w[c];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s[6] = {0, 0, 0, 0, 0, 0};
+        for (int v = 0; v < kWThreads / 32; ++v)
+            for (int c = 0; c < 6; ++c) s[c] += red[c][v];
+        s[3] += (2.0 * spi / eta) * exp(-z * z / (a * a)) / area;
+        if (z == 0.0 && rho == 0) {
+            const double self = -4.0 / (3.0 * a * a * a * spi);
+            s[0] += self;
+            s[2] += self;
+            s[3] += self;
+        }
+        for (int c = 0; c < 6; ++c) W6[(size_t)c * N + rho] = s[c];
+    }
+}
+
+cudaError_t launch_wtilde_ewald(int L, double z, double eta, double *W6, cudaStream_t st) {
+    const int nreal = (int)ceil(6.0 * 2.0 * eta / L) + 1;
+    const int nrec = (int)ceil(6.5 / eta * L / (2.0 * kPiD)) + 1;
+    k_wtilde_ewald<<<L * L, kWThreads, 0, st>>>(L, z, eta, nreal, nrec, W6);
+    return cudaGetLastError();
+}
+
+// The in-plane components of a six-component tensor as W~ (FP64 and FP32).
+__global__ void k_take_plane(size_t N, const double *__restrict__ W6, double *W64, float *W32) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 4 * N) return;
+    W64[i] = W6[i];
+    W32[i] = (float)W6[i];
+}
+
+cudaError_t launch_take_plane(int L, const double *W6, double *W64, float *W32, cudaStream_t st) {
+    const size_t N = (size_t)L * L;
+    k_take_plane<<<(unsigned)((4 * N + 255) / 256), 256, 0, st>>>(N, W6, W64, W32);
+    return cudaGetLastError();
+}
+
 __global__ void k_cast_W(size_t n, const double *__restrict__ W64, float *W32) {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) W32[i] = (float)W64[i];

@@ -144,6 +144,9 @@ struct SweepBuffers {
 // Launchers (implemented in their .cu files).  Return a cudaError_t.
 cudaError_t launch_wtilde(int L, int A, int tail, double *W64, float *W32, cudaStream_t st);
 cudaError_t launch_cast_W(int L, const double *W64, float *W32, cudaStream_t st);
+// W~ by the Ewald/Harris split, [6][L][L] (xx, xy, yy, zz, xz, yz), layers z apart.
+cudaError_t launch_wtilde_ewald(int L, double z, double eta, double *W6, cudaStream_t st);
+cudaError_t launch_take_plane(int L, const double *W6, double *W64, float *W32, cudaStream_t st);
 cudaError_t launch_init_spins(int L, int R, uint2 key, int mode, float *spins, cudaStream_t st);
 cudaError_t launch_full_field(int L, int R, const float *W32, const float *spins, float *h,
                               cudaStream_t st);

@@ -32,6 +32,7 @@ ABI_SYMBOLS = (
     "mc_get_spins", "mc_get_field", "mc_get_W", "mc_energy", "mc_get_sweep_counter",
     "mc_checkpoint", "mc_restore", "mc_energy_noalloc", "mc_set_timing", "mc_get_timing",
     "mc_choose_spacing", "mc_autotune", "mc_set_histogram", "mc_get_histogram",
+    "mc_precompute_W_ewald", "mc_wtilde_ewald",
     "mc_footprint", "mc_server_create", "mc_server_submit", "mc_server_step", "mc_server_poll", "mc_server_request_info",
     "mc_server_collect", "mc_server_get_spins", "mc_server_release", "mc_server_get_stats", "mc_server_destroy",
 )
@@ -112,6 +113,8 @@ def _load():
         "mc_sweep_trace": ([vp, i32, vp, C.c_size_t, vp], i32),
         "mc_observables": ([vp, i32, C.POINTER(mc_obs)], i32),
         "mc_set_histogram": ([vp, f64, f64, i32], i32),
+        "mc_precompute_W_ewald": ([vp, f64], i32),
+        "mc_wtilde_ewald": ([i32, f64, f64, C.POINTER(C.c_double)], i32),
         "mc_get_histogram": ([vp, i32, C.POINTER(C.c_int64)], i32),
         "mc_reset_observables": ([vp], i32),
         "mc_get_spins": ([vp, vp, i32, vp], i32),
@@ -242,6 +245,9 @@ class Lattice:
         else:
             _ck(_lib.mc_init_spins(self.h, mode, None))
 
+    def precompute_W_ewald(self, eta=0.0):
+        _ck(_lib.mc_precompute_W_ewald(self.h, eta))
+
     def precompute_W(self, image_cutoff=64, tail_correction=True):
         _ck(_lib.mc_precompute_W(self.h, image_cutoff, int(bool(tail_correction))))
 
@@ -332,6 +338,13 @@ class Lattice:
     def restore(self, data: bytes):
         buf = C.create_string_buffer(data, len(data))
         _ck(_lib.mc_restore(self.h, buf, len(data)))
+
+
+def wtilde_ewald(L: int, z: float = 0.0, eta: float = 0.0) -> np.ndarray:
+    """W~ by the Ewald/Harris split on the GPU, [6][L][L] FP64 (xx, xy, yy, zz, xz, yz)."""
+    a = np.zeros((6, L, L), np.float64)
+    _ck(_lib.mc_wtilde_ewald(L, z, eta, a.ctypes.data_as(C.POINTER(C.c_double))))
+    return a
 
 
 def footprint(L: int, l: int, replicas: int = 1) -> int:
