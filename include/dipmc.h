@@ -69,6 +69,7 @@ extern "C" {
 #define MC_PATH_TENSOR 3      /* windowed sweep, stale field on tcgen05 tensor cores, split-BF16x3 */
 #define MC_PATH_FFT 4         /* full field per sub-step by 2D FFT convolution (L a power of two) */
 #define MC_PATH_SPECTRAL 5    /* field at the sub-step's sites from sub-lattice spectra (L/l <= 32) */
+#define MC_PATH_INCREMENTAL 6 /* field kept at every site, rank-n update per sub-step (L <= 64, (L/l)^2 <= 64) */
 
 typedef struct mc_lattice mc_lattice;
 
@@ -138,7 +139,12 @@ int mc_set_schedule(mc_lattice *lat, int kind);
  * contraction of those spectra with the transforms of W~, an inverse DFT, the
  * update and the DFT of the updated sub-lattice (2 <= L/l <= 32, any L).  The FFT
  * and spectral paths measure the energy afresh from the full field at each
- * measured sweep.  MC_PATH_AUTO order: direct, spectral, FFT, windowed. */
+ * measured sweep.  MC_PATH_INCREMENTAL keeps the field at every site in shared
+ * memory and adds W~ * delta of the accepted moves after each sub-step, so the
+ * energy of a measured sweep is an O(L^2) sum over the kept field; the field is
+ * re-evaluated from scratch every 8 sweeps.  MC_PATH_AUTO order: direct,
+ * spectral, FFT, windowed (the incremental path is chosen explicitly or by
+ * mc_autotune). */
 int mc_set_field_path(mc_lattice *lat, int path);
 
 /* Sub-steps per window of the windowed paths (must divide l^2; 0 = automatic). */

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "fft_field.cuh"
+#include "incremental.cuh"
 #include "internal.cuh"
 #include "spectral.cuh"
 #include "tc_field.cuh"
@@ -219,6 +220,7 @@ bool path_supported(const mc_lattice *p, int path) {
         }
         case MC_PATH_FFT: return fft_supported(p->L);
         case MC_PATH_SPECTRAL: return spectral_supported(p->L, p->l);
+        case MC_PATH_INCREMENTAL: return incremental_supported(p->L, p->l);
         default: return false;
     }
 }
@@ -554,6 +556,45 @@ int run_spectral(mc_lattice *p, int nsweeps, int measure_every, float *trace, cu
     return MC_OK;
 }
 
+// Incremental path: launches of at most kIncrChunk sweeps, each starting from a
+// freshly evaluated full field (so FP32 rank-n updates do not accumulate).
+constexpr int kIncrChunk = 8;
+
+int run_incremental(mc_lattice *p, int nsweeps, int measure_every, float *trace, cudaStream_t st) {
+    IncrConfig c{};
+    c.L = p->L; c.l = p->l; c.R = p->R;
+    c.key = key_of(p->seed);
+    c.nsweeps_call = nsweeps;
+    c.measure_every = measure_every;
+    c.proposal = p->proposal;
+    c.cap_c1 = (float)(1.0 - std::cos(p->cone));
+    c.schedule = p->schedule;
+    IncrBuffers b;
+    b.W32 = p->W32; b.spins = p->spins; b.field = p->field; b.params = p->dparams; b.energy = p->energy;
+    b.obs = p->obs; b.theta2 = p->theta2; b.trace = trace; b.hist = hist_of(p);
+    bool measured_last = false;
+    for (int done = 0; done < nsweeps; done += kIncrChunk) {
+        const int chunk = std::min(kIncrChunk, nsweeps - done);
+        cudaError_t e;
+        {
+            TimedLaunch tl(p, MC_K_FULL_FIELD, st);
+            e = launch_full_field(p->L, p->R, p->W32, p->spins, p->field, st);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "full-field kernel");
+        c.t0 = (uint32_t)(p->t + (uint64_t)done);
+        c.nsweeps = chunk;
+        c.it0 = done;
+        {
+            TimedLaunch tl(p, MC_K_SWEEP_DIRECT, st);
+            e = launch_sweep_incremental(c, b, st);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "incremental sweep kernel");
+    }
+    measured_last = measure_every > 0 && nsweeps % measure_every == 0;
+    p->energy_valid = measured_last;
+    return MC_OK;
+}
+
 int run_path(mc_lattice *p, int path, int nsweeps, int measure_every, float *trace, cudaStream_t st) {
     if (path == MC_PATH_FFT) return run_fft(p, nsweeps, measure_every, trace, st);
     if (path == MC_PATH_SPECTRAL) return run_spectral(p, nsweeps, measure_every, trace, st);
@@ -622,7 +663,7 @@ int run_sweeps(mc_lattice *p, int nsweeps, int measure_every, float *trace, cuda
     if (measure_every < 0) return fail(MC_EINVAL, "measure_every must be >= 0");
     if (nsweeps == 0) return MC_OK;
     const int path0 = resolve_path(p);
-    if (!p->energy_valid && path0 != MC_PATH_FFT && path0 != MC_PATH_SPECTRAL) {
+    if (!p->energy_valid && path0 != MC_PATH_FFT && path0 != MC_PATH_SPECTRAL && path0 != MC_PATH_INCREMENTAL) {
         int rc = anchor_energy(p, st);
         if (rc) return rc;
     }
@@ -649,7 +690,10 @@ int run_sweeps(mc_lattice *p, int nsweeps, int measure_every, float *trace, cuda
     const int path = resolve_path(p);
     if (path < 0 || !path_supported(p, path))
         return fail(MC_ENOSYS, "no field path supports L=%d l=%d (path %d)", p->L, p->l, p->path);
-    if (path == MC_PATH_DIRECT) {
+    if (path == MC_PATH_INCREMENTAL) {
+        int rc = run_incremental(p, nsweeps, measure_every, trace, st);
+        if (rc) return rc;
+    } else if (path == MC_PATH_DIRECT) {
         cudaError_t e;
         {
             TimedLaunch tl(p, MC_K_SWEEP_DIRECT, st);
@@ -788,7 +832,7 @@ int mc_set_field_path(mc_lattice *p, int path) {
     if (p) drop_graphs(p);
     int rc = check(p);
     if (rc) return rc;
-    if (path < MC_PATH_AUTO || path > MC_PATH_SPECTRAL) return fail(MC_EINVAL, "unknown field path %d", path);
+    if (path < MC_PATH_AUTO || path > MC_PATH_INCREMENTAL) return fail(MC_EINVAL, "unknown field path %d", path);
     if (path != MC_PATH_AUTO && !path_supported(p, path))
         return fail(MC_ENOSYS, "field path %d does not support L=%d l=%d", path, p->L, p->l);
     p->path = path;
@@ -1107,6 +1151,7 @@ int mc_autotune(mc_lattice *p, int nsweeps_trial, void *stream, int *path_out, i
     p->window_B = old_B;
     if (path_supported(p, MC_PATH_FFT)) cands.push_back({MC_PATH_FFT, 0});
     if (path_supported(p, MC_PATH_SPECTRAL)) cands.push_back({MC_PATH_SPECTRAL, 0});
+    if (path_supported(p, MC_PATH_INCREMENTAL)) cands.push_back({MC_PATH_INCREMENTAL, 0});
     if (cands.empty()) return fail(MC_ENOSYS, "no field path supports L=%d l=%d", p->L, p->l);
     cudaEvent_t a, b;
     CK(cudaEventCreate(&a));

@@ -444,10 +444,14 @@ FCASES = [
     (5, 48, 16, 2, 0, 1),     # L not a power of two, odd coarse grid (3 x 3)
     (5, 96, 12, 1, 0, 1),     # 8 x 8 coarse grid, L not a power of two
     (5, 128, 8, 1, 0, 1),     # 16 x 16 coarse grid, 256 simultaneous sites
+    (6, 16, 8, 2, 0, 2),      # incremental field: 4 sites per sub-step
+    (6, 32, 4, 2, 1, 1),      # 64 sites per sub-step, with-replacement schedule
+    (6, 48, 24, 1, 0, 1),     # L not a power of two
+    (6, 64, 32, 1, 0, 1),     # the paper's L and l
 ]
 
 
-@pytest.mark.parametrize("case", FCASES, ids=[f"{'fft' if c[0] == 4 else 'spec'}_L{c[1]}_l{c[2]}_R{c[3]}_s{c[4]}"
+@pytest.mark.parametrize("case", FCASES, ids=[f"{ {4: 'fft', 5: 'spec', 6: 'incr'}[c[0]]}_L{c[1]}_l{c[2]}_R{c[3]}_s{c[4]}"
                                               for c in FCASES])
 def test_fft_path_trace_matches_oracle(dipmc, case):
     """FFT (full-lattice transform per sub-step) and spectral (sub-lattice
@@ -479,7 +483,7 @@ def test_fft_path_trace_matches_oracle(dipmc, case):
             np.testing.assert_allclose(sg[r], o["s"], rtol=0, atol=1e-5)
 
 
-@pytest.mark.parametrize("other", [4, 5], ids=["fft", "spectral"])
+@pytest.mark.parametrize("other", [4, 5, 6], ids=["fft", "spectral", "incremental"])
 def test_fft_path_observables_match_direct(dipmc, other):
     """The FFT and spectral paths sample the same law as the direct path (L = 16,
     pooled replicas)."""
@@ -537,7 +541,25 @@ def test_autotune_keeps_state_and_picks_a_path(dipmc):
         before = lat.get_spins()
         t0 = lat.sweep_counter()
         path, win = lat.autotune(1)
-        assert path in (dipmc.MC_PATH_DIRECT, dipmc.MC_PATH_TENSOR, dipmc.MC_PATH_FFT, dipmc.MC_PATH_SPECTRAL)
+        assert path in (dipmc.MC_PATH_DIRECT, dipmc.MC_PATH_TENSOR, dipmc.MC_PATH_FFT, dipmc.MC_PATH_SPECTRAL,
+                        dipmc.MC_PATH_INCREMENTAL)
         assert np.array_equal(lat.get_spins(), before) and lat.sweep_counter() == t0
         lat.sweep(2, 1)
         assert lat.observables(0)["samples"] == 2
+
+
+def test_incremental_path_energy_from_the_kept_field(dipmc):
+    """The incremental path measures E from its kept field; after 13 sweeps (two
+    launches, the field re-evaluated between them) it equals a full-field
+    evaluation of the final state."""
+    L, l, R = 32, 16, 4
+    s0 = inputs.random_spins(L, R, seed=13)
+    with dipmc.Lattice(L, l, R, 3) as lat:
+        lat.precompute_W(16, True)
+        lat.set_field_path(dipmc.MC_PATH_INCREMENTAL)
+        lat.set_params(F32(1.0), F32(0.2), F32(0.8), F32(0.1), F32(0.7))
+        lat.init_spins(2, s0)
+        lat.sweep(13, 1)
+        e_kept = np.array([lat.observables(r)["energy"] for r in range(R)]) * L * L
+        e_full = lat.energy()
+    np.testing.assert_allclose(e_kept, e_full, rtol=0, atol=2e-4 * L * L * 1e-2 + 1e-3)
