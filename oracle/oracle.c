@@ -44,7 +44,7 @@
 #include <string.h>
 
 #define ORC_PI 3.14159265358979323846
-#define ORC_NOBS 6   /* |m|, m_z, |m_z|, M_par, E/N, m_st */
+#define ORC_NOBS 11  /* |m|, m_z, |m_z|, M_par, E/N, m_st, wall density, O_x, O_y, O_z, cone */
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10, written from its published definition (Salmon et al.,     */
@@ -516,6 +516,26 @@ static void observe(const orc_params *p, const double *W, const double *s, doubl
     out[3] = sqrt(mx * mx + my * my);
     out[4] = e[3] / N;
     out[5] = sqrt(mh * mh + mv * mv);
+    /* Sec. 4.1 domain walls: n_v^a = sum_i 1 - sgn(s_i^a s_{i+y}^a), n_h^a with i+x;
+     * wall density (n_v^z + n_h^z)/(4N); orientational order of one state
+     * |n_h^a - n_v^a| / (n_h^a + n_v^a) (0 when there is no wall); and the cone
+     * angle of one state (2/pi)(1/N) sum_i |theta_i - pi/2|, theta_i = acos s_i^z. */
+    double nh[3] = {0, 0, 0}, nv[3] = {0, 0, 0}, cone = 0.0;
+    for (int i = 0; i < N; ++i) {
+        const int x = i % L, y = i / L;
+        const int ix = y * L + (x + 1) % L, iy = ((y + 1) % L) * L + x;
+        for (int c = 0; c < 3; ++c) {
+            const double a = s[c * N + i];
+            const double ph = a * s[c * N + ix], pv = a * s[c * N + iy];
+            nh[c] += 1.0 - (ph > 0 ? 1.0 : (ph < 0 ? -1.0 : 0.0));
+            nv[c] += 1.0 - (pv > 0 ? 1.0 : (pv < 0 ? -1.0 : 0.0));
+        }
+        const double zc = fmax(-1.0, fmin(1.0, s[2 * N + i]));
+        cone += fabs(acos(zc) - 0.5 * ORC_PI);
+    }
+    out[6] = (nv[2] + nh[2]) / (4.0 * N);
+    for (int c = 0; c < 3; ++c) out[7 + c] = (nh[c] + nv[c] > 0) ? fabs(nh[c] - nv[c]) / (nh[c] + nv[c]) : 0.0;
+    out[10] = (2.0 / ORC_PI) * cone / N;
 }
 
 /*

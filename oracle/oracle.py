@@ -20,8 +20,9 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 
-# per-sweep observables: |m|, m_z, |m_z|, M_par, E/N, m_st (Appendix B staggered magnetisation)
-NOBS = 6
+# per-sweep observables: |m|, m_z, |m_z|, M_par, E/N, m_st (Appendix B staggered magnetisation),
+# wall density, orientational order O_x, O_y, O_z and the cone angle of one state (Sec. 4.1)
+NOBS = 11
 
 
 def build(force: bool = False) -> str:

@@ -129,3 +129,38 @@ def test_exact_enumeration_4x4_with_dipoles():
     e, m = o["obs"][:, 4], o["obs"][:, 5]
     assert abs(e.mean() - e_exact) < 4 * binned_error(e) + 1e-4, (e.mean(), e_exact, binned_error(e))
     assert abs(m.mean() - m_exact) < 4 * binned_error(m) + 1e-4, (m.mean(), m_exact, binned_error(m))
+
+
+@pytest.mark.parametrize("pattern,wall,oz", [("ferro", 0.0, 0.0), ("checker", 1.0, 0.0), ("hstripes", 0.5, 1.0),
+                                             ("vstripes", 0.5, 1.0), ("h2", 0.25, 1.0)])
+def test_wall_density_and_orientational_order_closed_forms(pattern, wall, oz):
+    """Sec. 4.1 walls and orientational order of perpendicular states: n_v^z counts
+    sign changes to the site above, n_h^z to the right (2 per wall); the x and y
+    components are zero, so every pair counts 1 and O_x = O_y = 0; the cone angle
+    of one state is 1 for spins along +-z."""
+    L = 8
+    if pattern == "h2":
+        y = np.arange(L)[:, None] * np.ones((1, L))
+        s = np.zeros((3, L, L))
+        s[2] = np.where((y // 2) % 2 == 0, 1.0, -1.0)
+    else:
+        s = ising_state(L, pattern)
+    W = orc.wtilde(L, 4, True)
+    p = orc.params(L, 2, 0.0, 0.0, 0.0, 0.0, 1.0, proposal=2, seed=1)
+    o = orc.sweeps(p, W, s, 0, 1, observe=True)["obs"][0]   # one sweep reverses every spin
+    assert o[6] == pytest.approx(wall, abs=1e-15)
+    assert o[7] == 0.0 and o[8] == 0.0
+    assert o[9] == pytest.approx(oz, abs=1e-15)
+    assert o[10] == pytest.approx(1.0, abs=1e-15)
+
+
+def test_walls_and_cone_of_random_states():
+    """J = C_D = K = 0 with uniform proposals: every move is accepted and the
+    spins are uniform on S^2, so the wall density tends to 1/2 (Sec. 4.1, T -> oo)
+    and the cone angle of a state to (2/pi) E|asin z| = 1 - 2/pi."""
+    L = 32
+    W = orc.wtilde(L, 4, True)
+    p = orc.params(L, 2, 0.0, 0.0, 0.0, 0.0, 1.0, proposal=1, seed=3)
+    o = orc.sweeps(p, W, orc.init_random(L, 7), 0, 200, trace=False, observe=True)["obs"]
+    assert o[:, 6].mean() == pytest.approx(0.5, abs=4 * binned_error(o[:, 6]) + 1e-4)
+    assert o[:, 10].mean() == pytest.approx(1 - 2 / math.pi, abs=4 * binned_error(o[:, 10]) + 1e-4)
