@@ -60,7 +60,14 @@ extern "C" {
                            components of the four 2 x 2 sub-lattices, m_h = m1 + m2 - m3 - m4,
                            m_v = m1 + m4 - m3 - m2, m_lambda = (1/N) sum over sub-lattice lambda;
                            1 = (x, y even), 2 = (x odd, y even), 3 = (x, y odd), 4 = (x even, y odd) */
-#define MC_NOBS 6
+#define MC_OBS_WALL 6   /* wall density (n_v^z + n_h^z)/(4N), n_v^a = sum_i 1 - sgn(s_i^a s_{i+y}^a),
+                           n_h^a likewise with i+x (Sec. 4.1 domain-wall equations) */
+#define MC_OBS_OX 7     /* orientational order of one state |n_h^x - n_v^x| / (n_h^x + n_v^x) (0 without walls); */
+#define MC_OBS_OY 8     /*   its mean is O_x of Sec. 4.1; likewise y and z */
+#define MC_OBS_OZ 9
+#define MC_OBS_CONE 10  /* cone angle of one state (2/pi)(1/N) sum_i |theta_i - pi/2| (the per-site
+                           average inside eta is over time; this one is per state, for its variance) */
+#define MC_NOBS 11
 
 /* Field paths (mc_set_field_path). */
 #define MC_PATH_AUTO 0

@@ -308,6 +308,7 @@ __global__ void __launch_bounds__(256) k_fft_observe(int L, const float *__restr
     const float *f = field + (size_t)r * 3 * N;
     const RepParams p = P[r];
     double mx = 0, my = 0, mz = 0, ex = 0, an = 0, dp = 0, mh = 0, mv = 0;
+    double wc[7] = {0, 0, 0, 0, 0, 0, 0};   // n_h^x, n_v^x, n_h^y, n_v^y, n_h^z, n_v^z, sum |theta - pi/2|
     for (int i = tid; i < N; i += blockDim.x) {
         const int x = i % L, y = i / L;
         const int ixp = y * L + (x + 1 == L ? 0 : x + 1);
@@ -318,6 +319,13 @@ __global__ void __launch_bounds__(256) k_fft_observe(int L, const float *__restr
         mz += c;
         mh += (y & 1) ? -c : c;     // m1 + m2 - m3 - m4 (rows)
         mv += (x & 1) ? -c : c;     // m1 + m4 - m3 - m2 (columns)
+        wc[0] += wall_term(s[i], s[ixp]);
+        wc[1] += wall_term(s[i], s[iyp]);
+        wc[2] += wall_term(s[N + i], s[N + ixp]);
+        wc[3] += wall_term(s[N + i], s[N + iyp]);
+        wc[4] += wall_term(s[2 * N + i], s[2 * N + ixp]);
+        wc[5] += wall_term(s[2 * N + i], s[2 * N + iyp]);
+        wc[6] += fabsf(acosf(fminf(1.0f, fmaxf(-1.0f, (float)c))) - 0.5f * kPiF);
         ex += a * ((double)s[ixp] + (double)s[iyp]) + b * ((double)s[N + ixp] + (double)s[N + iyp]) +
               c * ((double)s[2 * N + ixp] + (double)s[2 * N + iyp]);
         const double z2 = c * c;
@@ -328,18 +336,18 @@ __global__ void __launch_bounds__(256) k_fft_observe(int L, const float *__restr
             theta2[(size_t)r * N + i] += (double)(th * th);
         }
     }
-    __shared__ double red[8][8];
-    double v[8] = {mx, my, mz, ex, an, dp, mh, mv};
-    for (int k = 0; k < 8; ++k)
+    __shared__ double red[15][8];
+    double v[15] = {mx, my, mz, ex, an, dp, mh, mv, wc[0], wc[1], wc[2], wc[3], wc[4], wc[5], wc[6]};
+    for (int k = 0; k < 15; ++k)
         for (int off = 16; off; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
     if ((tid & 31) == 0)
-        for (int k = 0; k < 8; ++k) red[k][tid >> 5] = v[k];
+        for (int k = 0; k < 15; ++k) red[k][tid >> 5] = v[k];
     __syncthreads();
     __shared__ double x_s[MC_NOBS];
     if (tid == 0) {
-        double t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        double t[15] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-            for (int k = 0; k < 8; ++k) t[k] += red[k][w];
+            for (int k = 0; k < 15; ++k) t[k] += red[k][w];
         const double Mx = t[0] / N, My = t[1] / N, Mz = t[2] / N;
         const double E = -(double)p.J * t[3] + t[4] + 0.5 * (double)p.CD * t[5];
         energy[r] = E;
@@ -349,6 +357,8 @@ __global__ void __launch_bounds__(256) k_fft_observe(int L, const float *__restr
         x_s[MC_OBS_MPAR] = sqrt(Mx * Mx + My * My);
         x_s[MC_OBS_E] = E / N;
         x_s[MC_OBS_MST] = sqrt(t[6] * t[6] + t[7] * t[7]) / N;
+        const double nh[3] = {t[8], t[10], t[12]}, nv[3] = {t[9], t[11], t[13]};
+        stripe_obs(x_s, nh, nv, t[14], N);
         hist_push(hist, r, E / N);
     }
     __syncthreads();

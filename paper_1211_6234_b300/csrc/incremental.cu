@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kIThreads, 1) k_sweep_incremental(const IncrCo
     float4 *mv = w4 + N;                                     // [n] move of site d (delta, accepted)
     float4 *mS = mv + n;                                     // [n] proposed spin of site d
     uint16_t *sched = reinterpret_cast<uint16_t *>(mS + n);  // [ll]
-    __shared__ double red[kIThreads / 32][8];
+    __shared__ double red[kIThreads / 32][15];
     __shared__ int s_acc;
 
     const RepParams P = b.params[r];
@@ -187,7 +187,8 @@ __global__ void __launch_bounds__(kIThreads, 1) k_sweep_incremental(const IncrCo
         }
         // ---- observables of this sweep, energy from the kept field
         if (cfg.measure_every > 0 && ((cfg.it0 + it + 1) % cfg.measure_every) == 0) {
-            double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // mx, my, mz, mh, mv, exchange, anisotropy, s.h
+            // mx, my, mz, mh, mv, exchange, anisotropy, s.h, wall counts n_h/n_v of x, y, z, sum |theta - pi/2|
+            double v[15] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
             double *gt = b.theta2 ? b.theta2 + (size_t)r * N : nullptr;
             for (int i = tid; i < N; i += kIThreads) {
                 const int iy = i / L, ix = i - iy * L;
@@ -203,21 +204,26 @@ __global__ void __launch_bounds__(kIThreads, 1) k_sweep_incremental(const IncrCo
                 const double z2 = (double)a.z * a.z;
                 v[6] += -(double)P.K2 * z2 - (double)P.K4 * z2 * z2;
                 v[7] += (double)a.x * h.x + (double)a.y * h.y + (double)a.z * h.z;
-                if (gt) {
-                    const float th = acosf(fminf(1.0f, fmaxf(-1.0f, a.z))) - 0.5f * kPiF;
-                    gt[i] += (double)(th * th);
-                }
+                v[8] += wall_term(a.x, ax.x);
+                v[9] += wall_term(a.x, ay.x);
+                v[10] += wall_term(a.y, ax.y);
+                v[11] += wall_term(a.y, ay.y);
+                v[12] += wall_term(a.z, ax.z);
+                v[13] += wall_term(a.z, ay.z);
+                const float th = acosf(fminf(1.0f, fmaxf(-1.0f, a.z))) - 0.5f * kPiF;
+                v[14] += fabsf(th);
+                if (gt) gt[i] += (double)(th * th);
             }
 #pragma unroll
-            for (int c = 0; c < 8; ++c)
+            for (int c = 0; c < 15; ++c)
                 for (int off = 16; off; off >>= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], off);
             if (lane == 0)
-                for (int c = 0; c < 8; ++c) red[warp][c] = v[c];
+                for (int c = 0; c < 15; ++c) red[warp][c] = v[c];
             __syncthreads();
             if (tid == 0) {
-                double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                double s[15] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
                 for (int w = 0; w < NW; ++w)
-                    for (int c = 0; c < 8; ++c) s[c] += red[w][c];
+                    for (int c = 0; c < 15; ++c) s[c] += red[w][c];
                 const double Mx = s[0] / N, My = s[1] / N, Mz = s[2] / N;
                 const double E = -(double)P.J * s[5] + s[6] + 0.5 * (double)P.CD * s[7];
                 double x[MC_NOBS];
@@ -227,6 +233,8 @@ __global__ void __launch_bounds__(kIThreads, 1) k_sweep_incremental(const IncrCo
                 x[MC_OBS_MPAR] = sqrt(Mx * Mx + My * My);
                 x[MC_OBS_E] = E / N;
                 x[MC_OBS_MST] = sqrt(s[3] * s[3] + s[4] * s[4]) / N;
+                const double nh[3] = {s[8], s[10], s[12]}, nv[3] = {s[9], s[11], s[13]};
+                stripe_obs(x, nh, nv, s[14], N);
                 if (b.obs) push_sample(b.obs[r], x);
                 hist_push(b.hist, r, E / N);
                 if (b.energy) b.energy[r] = E;

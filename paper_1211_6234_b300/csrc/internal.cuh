@@ -104,6 +104,24 @@ struct SweepConfig {
     int schedule;     // 0 permutation, 1 draw
 };
 
+// Sec. 4.1 stripe observables of one state from per-component wall counts
+// n_h[a] = sum_i 1 - sgn(s_i^a s_{i+x}^a), n_v[a] (i+y), and sum_i |theta_i - pi/2|.
+__device__ __forceinline__ float wall_term(float a, float b) {
+    const float p = a * b;
+    return 1.0f - (p > 0.0f ? 1.0f : (p < 0.0f ? -1.0f : 0.0f));
+}
+
+__device__ __forceinline__ void stripe_obs(double x[MC_NOBS], const double nh[3], const double nv[3], double cone,
+                                           int N) {
+    x[MC_OBS_WALL] = (nv[2] + nh[2]) / (4.0 * N);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double sum = nh[c] + nv[c];
+        x[MC_OBS_OX + c] = sum > 0.0 ? fabs(nh[c] - nv[c]) / sum : 0.0;
+    }
+    x[MC_OBS_CONE] = 0.63661977236758134 * cone / N;   // 2/pi
+}
+
 // Histogram of E/N per replica: counts[R][nbins] over [lo, lo + nbins / scale).
 struct EnergyHist {
     unsigned long long *counts = nullptr;

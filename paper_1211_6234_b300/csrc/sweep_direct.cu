@@ -148,8 +148,8 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
     extern __shared__ float4 smem_f4[];
     float4 *s4 = smem_f4;                                         // [N] spins (x, y, z, 0)
     float *red = reinterpret_cast<float *>(s4 + N);               // [NWF][V] warp partial fields
-    float *mred = red + NWF * V;                                  // [NW][6] magnetisation, staggered sums
-    float *wl = mred + NW * 6;                                    // [n][4] W~(l*D), D in [0,C)^2
+    float *mred = red + NWF * V;                                  // [NW][12] magnetisation, staggered and wall sums
+    float *wl = mred + NW * 12;                                   // [n][4] W~(l*D), D in [0,C)^2
     uint16_t *sched = reinterpret_cast<uint16_t *>(wl + n * 4);   // [ll] offsets of the sweep
     __shared__ ObsAcc acc_s;
     __shared__ double e_track_s;
@@ -424,46 +424,40 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
 
         // ---- observables of this sweep
         if (measuring && ((mphase + (uint32_t)it + 1u) % (uint32_t)cfg.measure_every) == 0) {
-            float mx = 0.f, my = 0.f, mz = 0.f, mh = 0.f, mv = 0.f;
+            float mv_[12] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             for (int i = tid; i < N; i += NT) {
                 const float4 a = s4[i];
-                mx += a.x;
-                my += a.y;
-                mz += a.z;
                 const int iy = i / L, ix = i - iy * L;
-                mh += (iy & 1) ? -a.z : a.z;     // m1 + m2 - m3 - m4 (rows)
-                mv += (ix & 1) ? -a.z : a.z;     // m1 + m4 - m3 - m2 (columns)
-                if (gt) {
-                    const float th = acosf(fminf(1.0f, fmaxf(-1.0f, a.z))) - 0.5f * kPiF;
-                    gt[i] += (double)(th * th);
-                }
+                const float4 ax = s4[iy * L + (ix + 1 == L ? 0 : ix + 1)], ay = s4[(iy + 1 == L ? 0 : iy + 1) * L + ix];
+                mv_[0] += a.x;
+                mv_[1] += a.y;
+                mv_[2] += a.z;
+                mv_[3] += (iy & 1) ? -a.z : a.z;     // m1 + m2 - m3 - m4 (rows)
+                mv_[4] += (ix & 1) ? -a.z : a.z;     // m1 + m4 - m3 - m2 (columns)
+                mv_[5] += wall_term(a.x, ax.x);
+                mv_[6] += wall_term(a.x, ay.x);
+                mv_[7] += wall_term(a.y, ax.y);
+                mv_[8] += wall_term(a.y, ay.y);
+                mv_[9] += wall_term(a.z, ax.z);
+                mv_[10] += wall_term(a.z, ay.z);
+                const float th = acosf(fminf(1.0f, fmaxf(-1.0f, a.z))) - 0.5f * kPiF;
+                mv_[11] += fabsf(th);
+                if (gt) gt[i] += (double)(th * th);
             }
-            for (int off = 16; off; off >>= 1) {
-                mx += __shfl_xor_sync(0xffffffffu, mx, off);
-                my += __shfl_xor_sync(0xffffffffu, my, off);
-                mz += __shfl_xor_sync(0xffffffffu, mz, off);
-                mh += __shfl_xor_sync(0xffffffffu, mh, off);
-                mv += __shfl_xor_sync(0xffffffffu, mv, off);
-            }
-            if (lane == 0) {
-                mred[warp * 6 + 0] = mx;
-                mred[warp * 6 + 1] = my;
-                mred[warp * 6 + 2] = mz;
-                mred[warp * 6 + 3] = mh;
-                mred[warp * 6 + 4] = mv;
-            }
+#pragma unroll
+            for (int c = 0; c < 12; ++c)
+                for (int off = 16; off; off >>= 1) mv_[c] += __shfl_xor_sync(0xffffffffu, mv_[c], off);
+            if (lane == 0)
+#pragma unroll
+                for (int c = 0; c < 12; ++c) mred[warp * 12 + c] = mv_[c];
             __syncthreads();
             if (warp == 0) {
                 if (lane == 0) {
-                    double Mx = 0, My = 0, Mz = 0, Mh = 0, Mv = 0;
-                    for (int ww = 0; ww < NW; ++ww) {
-                        Mx += mred[ww * 6 + 0];
-                        My += mred[ww * 6 + 1];
-                        Mz += mred[ww * 6 + 2];
-                        Mh += mred[ww * 6 + 3];
-                        Mv += mred[ww * 6 + 4];
-                    }
-                    Mx /= N; My /= N; Mz /= N; Mh /= N; Mv /= N;
+                    double sm[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+                    for (int ww = 0; ww < NW; ++ww)
+                        for (int c = 0; c < 12; ++c) sm[c] += mred[ww * 12 + c];
+                    const double Mx = sm[0] / N, My = sm[1] / N, Mz = sm[2] / N, Mh = sm[3] / N, Mv = sm[4] / N;
+                    const double nh[3] = {sm[5], sm[7], sm[9]}, nv[3] = {sm[6], sm[8], sm[10]};
                     double x[MC_NOBS];
                     x[MC_OBS_ABS_M] = sqrt(Mx * Mx + My * My + Mz * Mz);
                     x[MC_OBS_MZ] = Mz;
@@ -471,6 +465,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
                     x[MC_OBS_MPAR] = sqrt(Mx * Mx + My * My);
                     x[MC_OBS_E] = e_track_s / N;
                     x[MC_OBS_MST] = sqrt(Mh * Mh + Mv * Mv);
+                    stripe_obs(x, nh, nv, sm[11], N);
                     if (buf.obs) obs_push(acc_s, x);
                     hist_push(buf.hist, r, x[MC_OBS_E]);
                 }
@@ -542,7 +537,7 @@ int threads_of(const Inst &in, int ll) {
 
 size_t smem_bytes(int L, int l, int threads) {
     const int N = L * L, C = L / l, n = C * C, NW = threads / 32;
-    size_t b = sizeof(float4) * (size_t)N + sizeof(float) * (size_t)((NW - 1) * 3 * n + NW * 6 + 4 * n);
+    size_t b = sizeof(float4) * (size_t)N + sizeof(float) * (size_t)((NW - 1) * 3 * n + NW * 12 + 4 * n);
     b += sizeof(uint16_t) * (size_t)l * l;
     return (b + 15) & ~(size_t)15;
 }

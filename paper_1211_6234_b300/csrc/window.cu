@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
     __shared__ float4 s_acc[2][32];                              // accepted moves of a sub-step: (delta, x | y << 16),
     __shared__ int s_nacc[2];                                    // double-buffered by sub-step parity
     __shared__ double s_epart[32];
-    __shared__ float s_mred[kWThreads / 32][6];
+    __shared__ float s_mred[kWThreads / 32][12];
 
     const RepParams P = buf.params[r];
     const uint2 key = cfg.key;
@@ -449,46 +449,40 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
     }
     __syncthreads();
     if (cfg.measure) {
-        float mx = 0.f, my = 0.f, mz = 0.f, mh = 0.f, mv = 0.f;
+        float mv_[12] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         double *gt = buf.theta2 ? buf.theta2 + (size_t)r * N : nullptr;
         for (int i = tid; i < N; i += kWThreads) {
             const float4 a = s4[i];
-            mx += a.x;
-            my += a.y;
-            mz += a.z;
             const int iy = i / L, ix = i - iy * L;
-            mh += (iy & 1) ? -a.z : a.z;     // m1 + m2 - m3 - m4 (rows)
-            mv += (ix & 1) ? -a.z : a.z;     // m1 + m4 - m3 - m2 (columns)
-            if (gt) {
-                const float th = acosf(fminf(1.0f, fmaxf(-1.0f, a.z))) - 0.5f * kPiF;
-                gt[i] += (double)(th * th);
-            }
+            const float4 ax = s4[iy * L + (ix + 1 == L ? 0 : ix + 1)], ay = s4[(iy + 1 == L ? 0 : iy + 1) * L + ix];
+            mv_[0] += a.x;
+            mv_[1] += a.y;
+            mv_[2] += a.z;
+            mv_[3] += (iy & 1) ? -a.z : a.z;     // m1 + m2 - m3 - m4 (rows)
+            mv_[4] += (ix & 1) ? -a.z : a.z;     // m1 + m4 - m3 - m2 (columns)
+            mv_[5] += wall_term(a.x, ax.x);
+            mv_[6] += wall_term(a.x, ay.x);
+            mv_[7] += wall_term(a.y, ax.y);
+            mv_[8] += wall_term(a.y, ay.y);
+            mv_[9] += wall_term(a.z, ax.z);
+            mv_[10] += wall_term(a.z, ay.z);
+            const float th = acosf(fminf(1.0f, fmaxf(-1.0f, a.z))) - 0.5f * kPiF;
+            mv_[11] += fabsf(th);
+            if (gt) gt[i] += (double)(th * th);
         }
-        for (int off = 16; off; off >>= 1) {
-            mx += __shfl_xor_sync(0xffffffffu, mx, off);
-            my += __shfl_xor_sync(0xffffffffu, my, off);
-            mz += __shfl_xor_sync(0xffffffffu, mz, off);
-            mh += __shfl_xor_sync(0xffffffffu, mh, off);
-            mv += __shfl_xor_sync(0xffffffffu, mv, off);
-        }
-        if (lane == 0) {
-            s_mred[warp][0] = mx;
-            s_mred[warp][1] = my;
-            s_mred[warp][2] = mz;
-            s_mred[warp][3] = mh;
-            s_mred[warp][4] = mv;
-        }
+#pragma unroll
+        for (int c = 0; c < 12; ++c)
+            for (int off = 16; off; off >>= 1) mv_[c] += __shfl_xor_sync(0xffffffffu, mv_[c], off);
+        if (lane == 0)
+#pragma unroll
+            for (int c = 0; c < 12; ++c) s_mred[warp][c] = mv_[c];
         __syncthreads();
         if (tid < kNB && buf.obs) {
-            double Mx = 0, My = 0, Mz = 0, Mh = 0, Mv = 0;
-            for (int ww = 0; ww < kWThreads / 32; ++ww) {
-                Mx += s_mred[ww][0];
-                My += s_mred[ww][1];
-                Mz += s_mred[ww][2];
-                Mh += s_mred[ww][3];
-                Mv += s_mred[ww][4];
-            }
-            Mx /= N; My /= N; Mz /= N; Mh /= N; Mv /= N;
+            double sm[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+            for (int ww = 0; ww < kWThreads / 32; ++ww)
+                for (int c = 0; c < 12; ++c) sm[c] += s_mred[ww][c];
+            const double Mx = sm[0] / N, My = sm[1] / N, Mz = sm[2] / N, Mh = sm[3] / N, Mv = sm[4] / N;
+            const double nh[3] = {sm[5], sm[7], sm[9]}, nv[3] = {sm[6], sm[8], sm[10]};
             double x[MC_NOBS];
             x[MC_OBS_ABS_M] = sqrt(Mx * Mx + My * My + Mz * Mz);
             x[MC_OBS_MZ] = Mz;
@@ -496,6 +490,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
             x[MC_OBS_MPAR] = sqrt(Mx * Mx + My * My);
             x[MC_OBS_E] = buf.energy[r] / N;
             x[MC_OBS_MST] = sqrt(Mh * Mh + Mv * Mv);
+            stripe_obs(x, nh, nv, sm[11], N);
             obs_push_level(buf.obs[r], x, tid);
             if (tid == 0) hist_push(buf.hist, r, x[MC_OBS_E]);
         }

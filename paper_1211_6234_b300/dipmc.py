@@ -17,8 +17,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdipmc.so")
 
 MC_OK, MC_EINVAL, MC_ENOMEM, MC_ENOTREADY, MC_ETIMEOUT, MC_ECUDA, MC_ENOSYS = 0, -1, -2, -3, -4, -5, -6
-MC_NOBS = 6
-OBS_NAMES = ("abs_m", "m_z", "abs_m_z", "m_par", "e", "m_st")
+MC_NOBS = 11
+OBS_NAMES = ("abs_m", "m_z", "abs_m_z", "m_par", "e", "m_st", "wall", "o_x", "o_y", "o_z", "cone")
 (MC_PATH_AUTO, MC_PATH_DIRECT, MC_PATH_WINDOW_F32, MC_PATH_TENSOR, MC_PATH_FFT, MC_PATH_SPECTRAL,
  MC_PATH_INCREMENTAL) = 0, 1, 2, 3, 4, 5, 6
 MC_TRACE_W = 10

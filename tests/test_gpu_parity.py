@@ -167,7 +167,7 @@ def test_observables_statistically_match_oracle(dipmc, T):
     warm = orc.sweeps(p, W, s0[0], 0, warm_sw, trace=False)["s"]
     o = orc.sweeps(p, W, warm, warm_sw, nsw, trace=False, observe=True)
     assert og["samples"] == nsw
-    for i, nm in enumerate(("abs_m", "m_z", "abs_m_z", "m_par", "e")):
+    for i, nm in enumerate(dipmc.OBS_NAMES):
         x = o["obs"][:, i]
         eo = binned_error(x)
         eg = og[nm]["err"]
@@ -563,3 +563,31 @@ def test_incremental_path_energy_from_the_kept_field(dipmc):
         e_kept = np.array([lat.observables(r)["energy"] for r in range(R)]) * L * L
         e_full = lat.energy()
     np.testing.assert_allclose(e_kept, e_full, rtol=0, atol=2e-4 * L * L * 1e-2 + 1e-3)
+
+
+@pytest.mark.parametrize("path", [1, 2, 3, 4, 5, 6],
+                         ids=["direct", "window_f32", "tensor", "fft", "spectral", "incremental"])
+def test_observables_on_identical_trajectories(dipmc, path):
+    """Every path measures the observables in its own kernel: on a seeded run whose
+    final state equals the oracle's (no straddled decision), the per-sweep means of
+    all observables (|m|, m_z, |m_z|, M_par, E/N, m_st, walls, O_x, O_y, O_z, cone)
+    equal the oracle's to rounding."""
+    L, l, nsw, seed = 16, 8, 12, 61
+    prm = (F32(1.0), F32(0.15), F32(0.8), F32(-0.1), F32(0.9))
+    s0 = inputs.random_spins(L, 1, seed=8)
+    with dipmc.Lattice(L, l, 1, seed) as lat:
+        lat.precompute_W(16, True)
+        lat.set_field_path(path)
+        lat.set_params(*prm)
+        lat.init_spins(2, s0)
+        lat.sweep(nsw, 1)
+        og = lat.observables(0)
+        sg = lat.get_spins()[0].astype(np.float64)
+    p = orc.params(L, l, *prm, proposal=0, cone=0.5, schedule=0, seed=seed, replica=0)
+    o = orc.sweeps(p, oracle_W(L, 16), s0[0], 0, nsw, trace=False, observe=True)
+    if np.abs(sg - o["s"]).max() > 1e-4:
+        pytest.skip("a straddled decision separated the trajectories")
+    assert og["samples"] == nsw
+    for i, nm in enumerate(dipmc.OBS_NAMES):
+        tol = 2e-5 * (1 + abs(o["obs"][:, i].mean()))
+        assert og[nm]["mean"] == pytest.approx(o["obs"][:, i].mean(), abs=tol), nm
