@@ -288,17 +288,17 @@ def large_lattice_leg(dipmc, stream, sweeps=8):
 def ising_leg(dipmc, stream, sweeps=50, neq=100, nms=200):
     """Dipolar Ising variant (Appendix B): 256 replicas of L = 64 at a coupling of
     0.85 C_D per bond (the paper's J/C_D = 1.7 with J/2 per bond), T/C_D =
-    linspace(0.7, 1.0, 16), reversal moves from stripes of width 1.  Throughput
+    linspace(0.3, 1.0, 16), reversal moves from stripes of width 1.  Throughput
     of the simultaneous update (l = 32) and of the exact sequential one (l = L),
     and their m_st per temperature after a short run."""
     import torch
     Lb, Rb = 64, 256
     cd = 1.0 / 0.85
-    tt = np.repeat(np.linspace(0.7, 1.0, 16), Rb // 16)
+    tt = np.repeat(np.linspace(0.3, 1.0, 16), Rb // 16)
     y = np.arange(Lb)[:, None] * np.ones((1, Lb))
     s0 = np.zeros((Rb, 3, Lb, Lb), np.float32)
     s0[:, 2] = np.where(y % 2 == 0, 1.0, -1.0)
-    out = {"workload": "256 x L=64 Ising, J_bond/C_D = 0.85, T/C_D in [0.7, 1.0], reversal moves",
+    out = {"workload": "256 x L=64 Ising, J_bond/C_D = 0.85, T/C_D in [0.3, 1.0], reversal moves",
            "sweeps_timed": sweeps}
     for lb in (32, 64):
         lat = dipmc.Lattice(Lb, lb, Rb, seed=17)
@@ -320,7 +320,46 @@ def ising_leg(dipmc, stream, sweeps=50, neq=100, nms=200):
         out[key] = {"site_updates_per_s": Rb * Lb * Lb * nms / (a.elapsed_time(b) / 1e3),
                     "m_st_by_T": [round(float(np.mean(mst[i * 16:(i + 1) * 16])), 4) for i in range(16)]}
         lat.close()
-    out["T_over_CD"] = [round(float(v), 4) for v in np.linspace(0.7, 1.0, 16)]
+    out["T_over_CD"] = [round(float(v), 4) for v in np.linspace(0.3, 1.0, 16)]
+    return out
+
+
+def srt_scan_leg(dipmc, stream, neq=500, nms=500):
+    """Sec. 4 scans at reduced length: L = 64, l = 32, J/C_D = 8.9, K/C_D = 15,
+    a in {-1, 0, 2} (K2 = K (1 - a), K4 = K a), T/C_D on 16 log-spaced points in
+    [0.5, 10], from perpendicular stripes of width 8; neq + nms sweeps per
+    replica (the paper uses 1e5 + 5e4).  Reports per a and T: eta, O_z, wall
+    density, M_par and |m|, with their binned errors -- qualitative only."""
+    import torch
+    Lb, lb = 64, 32
+    Ts = np.geomspace(0.5, 10.0, 16)
+    avals = (-1.0, 0.0, 2.0)
+    R = len(avals) * len(Ts)
+    y = np.arange(Lb)[:, None] * np.ones((1, Lb))
+    s0 = np.zeros((R, 3, Lb, Lb), np.float32)
+    s0[:, 2] = np.where((y // 8) % 2 == 0, 1.0, -1.0)
+    lat = dipmc.Lattice(Lb, lb, R, seed=29)
+    lat.precompute_W(A_IMG, True)
+    lat.set_field_path(dipmc.MC_PATH_DIRECT)
+    for i, a in enumerate(avals):
+        for j, T in enumerate(Ts):
+            lat.set_params(8.9, 1.0, 15.0 * (1.0 - a), 15.0 * a, f32(T), replica=i * len(Ts) + j)
+    lat.init_spins(dipmc.INIT_USER, s0)
+    lat.sweep(neq, 0, stream)
+    lat.reset_observables()
+    t0 = time.perf_counter()
+    lat.sweep(nms, 1, stream)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    out = {"workload": "L=64, l=32, J/C_D=8.9, K/C_D=15, a in {-1, 0, 2}, 16 T/C_D in [0.5, 10]",
+           "sweeps": {"equilibration": neq, "measured": nms}, "T_over_CD": [round(float(v), 4) for v in Ts],
+           "site_updates_per_s": R * Lb * Lb * nms / dt, "by_a": {}}
+    for i, a in enumerate(avals):
+        rows = [lat.observables(i * len(Ts) + j) for j in range(len(Ts))]
+        out["by_a"][str(a)] = {nm: [round(float(o[nm]["mean"]), 4) for o in rows]
+                               for nm in ("o_z", "wall", "m_par", "abs_m", "cone")}
+        out["by_a"][str(a)]["eta"] = [round(float(o["eta"]), 4) for o in rows]
+    lat.close()
     return out
 
 
@@ -340,6 +379,7 @@ def main():
     ap.add_argument("--no-large", action="store_true", help="skip the L=256 leg")
     ap.add_argument("--large-only", action="store_true", help="run only the L=256 leg")
     ap.add_argument("--no-ising", action="store_true", help="skip the dipolar Ising leg")
+    ap.add_argument("--no-scan", action="store_true", help="skip the Sec. 4 scan leg")
     ap.add_argument("--serve-only", action="store_true", help="run only the serving leg")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-scale", type=float, default=0.002, help="factor on the requests' sweep counts")
@@ -530,6 +570,10 @@ def main():
     if rank == 0 and not args.no_ising:
         ising = ising_leg(dipmc, stream)
 
+    scan = None
+    if rank == 0 and not args.no_scan:
+        scan = srt_scan_leg(dipmc, stream)
+
     serving = None
     if rank == 0 and not args.no_serve:
         serving = serving_leg(dipmc, args.serve_requests, args.serve_scale, args.serve_quantum, 64.0,
@@ -559,6 +603,7 @@ def main():
             "plain": plain,
             "large_lattice": large,
             "ising": ising,
+            "srt_scan": scan,
             "serving": serving,
             "gpu_launches": gpu_launches,
             "clocks": clk,
