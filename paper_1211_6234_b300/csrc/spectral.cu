@@ -20,6 +20,12 @@
 // k_spec_update (one CTA per replica: inverse DFT, Metropolis decisions,
 // forward DFT of the updated sub-lattice).  DFTs are separable direct sums in
 // shared memory (C <= 32).  T is built once in FP64.
+//
+// Pipelining: the contraction of sub-step k+1 needs every S_e, but only S_o of
+// the offset o updated in sub-step k changes; so it leaves that e out and runs
+// concurrently with the update of sub-step k, which, once it has the new S_o,
+// adds that single term T_{(o' - o) mod l} S_o of the next offset o' as one
+// more partial chunk.  Partial spectra are double-buffered by sub-step parity.
 #include <algorithm>
 
 #include "spectral.cuh"
@@ -218,6 +224,11 @@ __global__ void __launch_bounds__(kSpecThreads, 3) k_spec_field(const SpecConfig
     const int r = j < R * n ? j / n : 0, K = j < R * n ? j % n : 0;
     const int ov = j < R * n ? b.off[(size_t)r * ll + cfg.k] : -1;
     const bool active = ov >= 0;
+    int eskip = -1;                                  // the previous sub-step's offset (added by its update)
+    if (active && cfg.skip_prev) {
+        const int pv = b.off[(size_t)r * ll + cfg.k - 1];
+        eskip = (pv >> 16) * l + (pv & 0xFFFF);
+    }
     float2 hx = make_float2(0.f, 0.f), hy = hx, hz = hx;
     if (active) {
         const int ox = ov & 0xFFFF, oy = ov >> 16;
@@ -241,7 +252,7 @@ __global__ void __launch_bounds__(kSpecThreads, 3) k_spec_field(const SpecConfig
                     ex += kW;
                     while (ex >= l) { ex -= l; ++ey; }
                 }
-                if (e < e1) {
+                if (e < e1 && e != eskip) {
                     int dx = ox - ex, dy = oy - ey;
                     const int sx = dx < 0, sy = dy < 0;
                     dx += sx ? l : 0;
@@ -295,7 +306,7 @@ __global__ void __launch_bounds__(kSpecThreads, 3) k_spec_field(const SpecConfig
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kUpdMaxThreads) k_spec_update(const SpecConfig cfg, const SpecBuffers b) {
     const int L = cfg.L, l = cfg.l, C = L / l, n = C * C, ll = l * l, N = L * L, R = cfg.R;
-    const int r = blockIdx.x;
+    const int r = blockIdx.x, tid = threadIdx.x;
     uint2 key;
     uint32_t t, rid;
     if (!stream_state(cfg, b, r, key, t, rid)) return;  // whole block, before any barrier
@@ -303,65 +314,41 @@ __global__ void __launch_bounds__(kUpdMaxThreads) k_spec_update(const SpecConfig
     const int ox = ov & 0xFFFF, oy = ov >> 16;
     extern __shared__ float2 sm_f2[];
     float2 *tw = sm_f2;                                          // [C]
-    float2 *H = tw + kSpecMaxC;                                  // [3][n]
+    float2 *H = tw + kSpecMaxC;                                  // [3][n] field spectra, later S_o
     float2 *U = H + 3 * n;                                       // [3][n]
     float *hs = reinterpret_cast<float *>(U + 3 * n);            // [3][n] field at the sites
     float *sn = hs + 3 * n;                                      // [3][n] spins after the update
     __shared__ int s_acc;
-    if (threadIdx.x == 0) s_acc = 0;
-    for (int m = threadIdx.x; m < C; m += blockDim.x) tw[m] = omega(m, C);
-    for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
-        float2 acc = b.Hpart[((size_t)r * 3) * n + i];
-        for (int z = 1; z < cfg.esplit; ++z) {
-            const float2 v = b.Hpart[(((size_t)z * R + r) * 3) * n + i];
-            acc.x += v.x;
-            acc.y += v.y;
-        }
-        H[i] = acc;
-    }
-    __syncthreads();
-    // inverse DFT: over Kx, then over Ky (conjugate twiddles), real part / n
-    for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
-        const int a = i / n, jj = i % n, Ky = jj / C, Dx = jj % C;
-        const float2 *row = H + a * n + Ky * C;
-        float2 acc = make_float2(0.f, 0.f);
-        for (int Kx = 0, m = 0; Kx < C; ++Kx) {       // m = Kx * Dx mod C
-            const float2 o = tw[m];
-            acc = cfma(row[Kx], make_float2(o.x, -o.y), acc);
-            m += Dx;
-            if (m >= C) m -= C;
-        }
-        U[i] = acc;
-    }
-    __syncthreads();
-    const float inv_n = 1.0f / (float)n;
-    for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
-        const int a = i / n, jj = i % n, Dy = jj / C, Dx = jj % C;
-        const float2 *col = U + a * n + Dx;
-        float re = 0.f;
-        for (int Ky = 0, m = 0; Ky < C; ++Ky) {       // m = Ky * Dy mod C
-            const float2 u = col[Ky * C], o = tw[m];
-            re = fmaf(u.x, o.x, fmaf(u.y, o.y, re));   // Re(u * conj(o))
-            m += Dy;
-            if (m >= C) m -= C;
-        }
-        hs[i] = re * inv_n;
-    }
-    __syncthreads();
-    // the sub-step's n sites (numbered as in the other paths: d -> (d % C, d / C))
+    if (tid == 0) s_acc = 0;
+    for (int m = tid; m < C; m += blockDim.x) tw[m] = omega(m, C);
+
+    // ---- everything that does not need the field, issued before the field arrives:
+    // thread d < n (blockDim >= n) owns site d: its spins, neighbours, proposal and
+    // the field-free part of dE
     float *s = b.spins + (size_t)r * 3 * N;
     const RepParams P = b.params[r];
-    const float W0xx = __ldg(b.W32), W0xy = __ldg(b.W32 + N), W0yy = __ldg(b.W32 + 2 * N), W0zz = __ldg(b.W32 + 3 * N);
-    int nacc = 0;
-    for (int d = threadIdx.x; d < n; d += blockDim.x) {
+    const int d = tid;
+    const bool site = d < n;
+    int q = 0;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, S0 = 0.f, S1 = 0.f, S2 = 0.f, pre = 0.f, thr = 0.f, uacc = 0.f;
+    if (site) {
         const int qx = ox + l * (d % C), qy = oy + l * (d / C);
-        const int q = qy * L + qx;
+        q = qy * L + qx;
         const uint4 wds = philox(make_uint4((uint32_t)q, rid, t, ((uint32_t)cfg.k & 0x00FFFFFFu) | kTagAttempt), key);
-        const float u1 = u24f(wds.x), uacc = u24f(wds.z);
+        const float u1 = u24f(wds.x);
+        uacc = u24f(wds.z);
         float sps, cps;
         sincospif(2.0f * u24f(wds.y), &sps, &cps);
-        const float s0 = s[q], s1 = s[N + q], s2 = s[2 * N + q];
-        float S0, S1, S2;
+        s0 = s[q];
+        s1 = s[N + q];
+        s2 = s[2 * N + q];
+        const int xp = (qx + 1 == L) ? q - qx : q + 1;
+        const int xm = (qx == 0) ? q + L - 1 : q - 1;
+        const int yp = (qy + 1 == L) ? qx : q + L;
+        const int ym = (qy == 0) ? q + N - L : q - L;
+        const float n0 = (s[xp] + s[xm]) + (s[yp] + s[ym]);
+        const float n1 = (s[N + xp] + s[N + xm]) + (s[N + yp] + s[N + ym]);
+        const float n2 = (s[2 * N + xp] + s[2 * N + xm]) + (s[2 * N + yp] + s[2 * N + ym]);
         if (cfg.proposal == kPropFlip) {            // Appendix B reversal
             S0 = -s0;
             S1 = -s1;
@@ -387,21 +374,62 @@ __global__ void __launch_bounds__(kUpdMaxThreads) k_spec_update(const SpecConfig
             S2 *= inv;
         }
         const float dX = S0 - s0, dY = S1 - s1, dZ = S2 - s2;
-        const int xp = (qx + 1 == L) ? q - qx : q + 1;
-        const int xm = (qx == 0) ? q + L - 1 : q - 1;
-        const int yp = (qy + 1 == L) ? qx : q + L;
-        const int ym = (qy == 0) ? q + N - L : q - L;
-        const float n0 = (s[xp] + s[xm]) + (s[yp] + s[ym]);
-        const float n1 = (s[N + xp] + s[N + xm]) + (s[N + yp] + s[N + ym]);
-        const float n2 = (s[2 * N + xp] + s[2 * N + xm]) + (s[2 * N + yp] + s[2 * N + ym]);
         const float dex = -P.J * (dX * n0 + dY * n1 + dZ * n2);
         const float z0 = s2 * s2, z1 = S2 * S2;
         const float dan = (-P.K2 * z1 - P.K4 * z1 * z1) - (-P.K2 * z0 - P.K4 * z0 * z0);
+        const float W0xx = __ldg(b.W32), W0xy = __ldg(b.W32 + N), W0yy = __ldg(b.W32 + 2 * N), W0zz = __ldg(b.W32 + 3 * N);
         const float self = W0xx * dX * dX + 2.0f * W0xy * dX * dY + W0yy * dY * dY + W0zz * dZ * dZ;
+        pre = dex + dan + P.CD * 0.5f * self;
+        thr = (uacc > 0.0f) ? -P.T * logf(uacc) : INFINITY;
+    }
+
+    // ---- field spectra at the sites: sum of the partial chunks
+    const int nchunks = cfg.esplit + (cfg.extra_in ? 1 : 0);
+    for (int i = tid; i < 3 * n; i += blockDim.x) {
+        float2 acc = b.Hpart[((size_t)r * 3) * n + i];
+        for (int z = 1; z < nchunks; ++z) {
+            const float2 v = b.Hpart[(((size_t)z * R + r) * 3) * n + i];
+            acc.x += v.x;
+            acc.y += v.y;
+        }
+        H[i] = acc;
+    }
+    __syncthreads();
+    // inverse DFT: over Kx, then over Ky (conjugate twiddles), real part / n
+    for (int i = tid; i < 3 * n; i += blockDim.x) {
+        const int a = i / n, jj = i % n, Ky = jj / C, Dx = jj % C;
+        const float2 *row = H + a * n + Ky * C;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int Kx = 0, m = 0; Kx < C; ++Kx) {       // m = Kx * Dx mod C
+            const float2 o = tw[m];
+            acc = cfma(row[Kx], make_float2(o.x, -o.y), acc);
+            m += Dx;
+            if (m >= C) m -= C;
+        }
+        U[i] = acc;
+    }
+    __syncthreads();
+    const float inv_n = 1.0f / (float)n;
+    for (int i = tid; i < 3 * n; i += blockDim.x) {
+        const int a = i / n, jj = i % n, Dy = jj / C, Dx = jj % C;
+        const float2 *col = U + a * n + Dx;
+        float re = 0.f;
+        for (int Ky = 0, m = 0; Ky < C; ++Ky) {       // m = Ky * Dy mod C
+            const float2 u = col[Ky * C], o = tw[m];
+            re = fmaf(u.x, o.x, fmaf(u.y, o.y, re));   // Re(u * conj(o))
+            m += Dy;
+            if (m >= C) m -= C;
+        }
+        hs[i] = re * inv_n;
+    }
+    __syncthreads();
+    // ---- decisions (sites are numbered as in the other paths: d -> (d % C, d / C))
+    int accept = 0;
+    if (site) {
+        const float dX = S0 - s0, dY = S1 - s1, dZ = S2 - s2;
         const float h0 = hs[d], h1 = hs[n + d], h2 = hs[2 * n + d];
-        const float dE = dex + dan + P.CD * ((dX * h0 + dY * h1 + dZ * h2) + 0.5f * self);
-        const float thr = (uacc > 0.0f) ? -P.T * logf(uacc) : INFINITY;
-        const int accept = dE < thr;
+        const float dE = pre + P.CD * (dX * h0 + dY * h1 + dZ * h2);
+        accept = dE < thr;
         if (b.trace) {
             float *tr = b.trace + ((((size_t)r * cfg.nsweeps_call + cfg.it) * ll + cfg.k) * n + d) * MC_TRACE_W;
             tr[0] = (float)q;
@@ -414,21 +442,70 @@ __global__ void __launch_bounds__(kUpdMaxThreads) k_spec_update(const SpecConfig
         sn[d] = accept ? S0 : s0;
         sn[n + d] = accept ? S1 : s1;
         sn[2 * n + d] = accept ? S2 : s2;
-        nacc += accept;
+        if (accept) {
+            s[q] = S0;
+            s[N + q] = S1;
+            s[2 * N + q] = S2;
+        }
     }
-    // every read of the pre-step spins is done before any write (neighbours of
-    // update sites are never update sites, but keep the phases separate)
+    const unsigned ball = __ballot_sync(0xffffffffu, accept);
+    if ((tid & 31) == 0 && ball) atomicAdd(&s_acc, __popc(ball));
     __syncthreads();
-    for (int d = threadIdx.x; d < n; d += blockDim.x) {
-        const int q = (oy + l * (d / C)) * L + ox + l * (d % C);
-        s[q] = sn[d];
-        s[N + q] = sn[n + d];
-        s[2 * N + q] = sn[2 * n + d];
+    // ---- new S of the updated offset (global, and in H for the next sub-step's term)
+    float2 *So = b.S + ((size_t)r * ll + (oy * l + ox)) * 3 * n;
+    for (int i = tid; i < 3 * n; i += blockDim.x) {
+        const int bb = i / n, j = i % n, Dy = j / C, Kx = j % C;
+        const float *row = sn + bb * n + Dy * C;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int Dx = 0, m = 0; Dx < C; ++Dx) {       // m = Kx * Dx mod C
+            const float2 o = tw[m];
+            acc.x = fmaf(row[Dx], o.x, acc.x);
+            acc.y = fmaf(row[Dx], o.y, acc.y);
+            m += Kx;
+            if (m >= C) m -= C;
+        }
+        U[i] = acc;
     }
-    if (nacc) atomicAdd(&s_acc, nacc);
-    dft3_forward(sn, U, tw, C, b.S + ((size_t)r * ll + (oy * l + ox)) * 3 * n, (size_t)n);
     __syncthreads();
-    if (threadIdx.x == 0 && s_acc && b.obs)
+    for (int i = tid; i < 3 * n; i += blockDim.x) {
+        const int bb = i / n, j = i % n, Ky = j / C, Kx = j % C;
+        const float2 *col = U + bb * n + Kx;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int Dy = 0, m = 0; Dy < C; ++Dy) {       // m = Ky * Dy mod C
+            acc = cfma(col[Dy * C], tw[m], acc);
+            m += Ky;
+            if (m >= C) m -= C;
+        }
+        So[i] = acc;
+        H[i] = acc;
+    }
+    if (cfg.extra_out) {
+        __syncthreads();
+        // the next sub-step's term of this offset: omega^(K.sigma) T_{(o' - o) mod l}(K) S_o(K)
+        const int nv = b.off[(size_t)r * ll + cfg.k + 1];
+        const int nx = nv & 0xFFFF, ny = nv >> 16;
+        int dx = nx - ox, dy = ny - oy;
+        const int sx = dx < 0, sy = dy < 0;
+        dx += sx ? l : 0;
+        dy += sy ? l : 0;
+        const float2 *Tp = b.T + (size_t)(dy * l + dx) * 4 * n;
+        for (int i = tid; i < 3 * n; i += blockDim.x) {
+            const int a = i / n, K = i % n, Kx = K % C, Ky = K / C;
+            int m = (sx ? Kx : 0) + (sy ? Ky : 0);
+            if (m >= C) m -= C;
+            const float2 p = omega(m, C);
+            float2 h;
+            if (a == 2) {
+                h = cmul(cmul(__ldg(Tp + 3 * n + K), p), H[2 * n + K]);
+            } else {
+                const float2 t0 = cmul(__ldg(Tp + (a == 0 ? 0 : 1) * n + K), p);
+                const float2 t1 = cmul(__ldg(Tp + (a == 0 ? 1 : 2) * n + K), p);
+                h = cfma(t0, H[K], cmul(t1, H[n + K]));
+            }
+            b.Hnext[(((size_t)cfg.esplit * R + r) * 3 + a) * n + K] = h;
+        }
+    }
+    if (tid == 0 && s_acc && b.obs)
         atomicAdd((unsigned long long *)&b.obs[r].accepted, (unsigned long long)s_acc);
 }
 
@@ -461,7 +538,7 @@ int spectral_esplit(int L, int l, int R, int nsm) {
 size_t spectral_S_elems(int L, int R) { return (size_t)3 * L * L * R; }
 
 size_t spectral_part_elems(int L, int l, int R, int esplit) {
-    return (size_t)esplit * R * 3 * (L / l) * (L / l);
+    return (size_t)2 * (esplit + 1) * R * 3 * (L / l) * (L / l);
 }
 
 cudaError_t launch_spec_table(int L, int l, const double *W64, float2 *T, cudaStream_t st) {

@@ -17,6 +17,9 @@ struct SpecConfig {
     float cap_c1;
     int schedule;
     int esplit;             // chunks of the cell-offset sum (partial spectra)
+    int skip_prev;          // field: leave out the previous sub-step's offset (its term comes from the update)
+    int extra_in;           // update: the partial spectra have one more chunk (that term)
+    int extra_out;          // update: write the next sub-step's term of the updated offset
 };
 
 struct SpecBuffers {
@@ -28,13 +31,15 @@ struct SpecBuffers {
     const SlotState *slots = nullptr;    // optional [R]: packed launch
     const float2 *T = nullptr;           // [l^2][4][n]: transforms of the W~ sub-lattice sequences
     float2 *S = nullptr;                 // [R][l^2][3][n]: transforms of the spin sub-lattices
-    float2 *Hpart = nullptr;             // [esplit][R][3][n]: partial field spectra
+    float2 *Hpart = nullptr;             // [esplit + 1][R][3][n]: partial field spectra of this sub-step
+    float2 *Hnext = nullptr;             // the same for the next sub-step (double buffer)
     int *off = nullptr;                  // [R][l^2]: offsets of the sweep's sub-steps (-1: idle slot)
 };
 
 bool spectral_supported(int L, int l);
 int spectral_esplit(int L, int l, int R, int nsm);
 size_t spectral_S_elems(int L, int R);
+// both partial-spectrum buffers: 2 x (esplit + 1) x R x 3 x n
 size_t spectral_part_elems(int L, int l, int R, int esplit);
 // T from W~ (FP64 separable DFTs, rounded to FP32 complex).
 cudaError_t launch_spec_table(int L, int l, const double *W64, float2 *T, cudaStream_t st);
