@@ -485,6 +485,9 @@ int run_fft(mc_lattice *p, int nsweeps, int measure_every, float *trace, cudaStr
 }
 
 int ensure_spectral(mc_lattice *p, cudaStream_t st) {
+    // the kernels divide (replica, K) indices below R n by n with a multiply-high
+    if ((unsigned long long)p->R * p->n() * p->n() >= (1ull << 32))
+        return fail(MC_ENOSYS, "spectral path needs replicas * (L/l)^4 < 2^32");
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -527,6 +530,8 @@ int run_spectral(mc_lattice *p, int nsweeps, int measure_every, float *trace, cu
     c.cap_c1 = (float)(1.0 - std::cos(p->cone));
     c.schedule = p->schedule;
     c.esplit = p->spec_esplit;
+    c.mC = fastdiv_magic((uint32_t)(p->L / p->l));
+    c.mn = fastdiv_magic((uint32_t)p->n());
     SpecBuffers b;
     b.W32 = p->W32; b.spins = p->spins; b.params = p->dparams; b.obs = p->obs; b.trace = trace;
     b.slots = p->packed ? p->slots_dev : nullptr;

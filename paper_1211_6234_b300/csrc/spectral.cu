@@ -38,6 +38,10 @@ constexpr int kSpecThreads = 256;
 constexpr int kUpdMaxThreads = 1024;
 constexpr int kSpecMaxC = 32;
 
+// x / d by a multiply-high with m = ceil(2^32 / d): exact while x * d < 2^32
+// (here x < 3 n <= 3072, d <= 1024)
+__device__ __forceinline__ int qdiv(int x, uint32_t m) { return (int)__umulhi((uint32_t)x, m); }
+
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -221,7 +225,8 @@ __global__ void __launch_bounds__(kSpecThreads, 3) k_spec_field(const SpecConfig
     const int L = cfg.L, l = cfg.l, C = L / l, n = C * C, ll = l * l, R = cfg.R;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int j = blockIdx.x * 32 + lane;
-    const int r = j < R * n ? j / n : 0, K = j < R * n ? j % n : 0;
+    const int rq = qdiv(j, cfg.mn);
+    const int r = j < R * n ? rq : 0, K = j < R * n ? j - rq * n : 0;
     const int ov = j < R * n ? b.off[(size_t)r * ll + cfg.k] : -1;
     const bool active = ov >= 0;
     int eskip = -1;                                  // the previous sub-step's offset (added by its update)
@@ -232,8 +237,8 @@ __global__ void __launch_bounds__(kSpecThreads, 3) k_spec_field(const SpecConfig
     float2 hx = make_float2(0.f, 0.f), hy = hx, hz = hx;
     if (active) {
         const int ox = ov & 0xFFFF, oy = ov >> 16;
-        const int Kx = K % C, Ky = K / C;
-        const float2 ph1 = omega(Kx, C), ph2 = omega(Ky, C), ph3 = omega((Kx + Ky) % C, C);
+        const int Ky = qdiv(K, cfg.mC), Kx = K - Ky * C;
+        const float2 ph1 = omega(Kx, C), ph2 = omega(Ky, C), ph3 = omega(Kx + Ky < C ? Kx + Ky : Kx + Ky - C, C);
         const int ec = (ll + gridDim.y - 1) / gridDim.y;
         const int e0 = blockIdx.y * ec, e1 = min(ll, e0 + ec);
         const float2 *Sr = b.S + (size_t)r * ll * 3 * n + K;
@@ -332,7 +337,8 @@ __global__ void __launch_bounds__(kUpdMaxThreads) k_spec_update(const SpecConfig
     int q = 0;
     float s0 = 0.f, s1 = 0.f, s2 = 0.f, S0 = 0.f, S1 = 0.f, S2 = 0.f, pre = 0.f, thr = 0.f, uacc = 0.f;
     if (site) {
-        const int qx = ox + l * (d % C), qy = oy + l * (d / C);
+        const int dy_ = qdiv(d, cfg.mC);
+        const int qx = ox + l * (d - dy_ * C), qy = oy + l * dy_;
         q = qy * L + qx;
         const uint4 wds = philox(make_uint4((uint32_t)q, rid, t, ((uint32_t)cfg.k & 0x00FFFFFFu) | kTagAttempt), key);
         const float u1 = u24f(wds.x);
@@ -397,7 +403,7 @@ __global__ void __launch_bounds__(kUpdMaxThreads) k_spec_update(const SpecConfig
     __syncthreads();
     // inverse DFT: over Kx, then over Ky (conjugate twiddles), real part / n
     for (int i = tid; i < 3 * n; i += blockDim.x) {
-        const int a = i / n, jj = i % n, Ky = jj / C, Dx = jj % C;
+        const int a = qdiv(i, cfg.mn), jj = i - a * n, Ky = qdiv(jj, cfg.mC), Dx = jj - Ky * C;
         const float2 *row = H + a * n + Ky * C;
         float2 acc = make_float2(0.f, 0.f);
         for (int Kx = 0, m = 0; Kx < C; ++Kx) {       // m = Kx * Dx mod C
@@ -411,7 +417,7 @@ __global__ void __launch_bounds__(kUpdMaxThreads) k_spec_update(const SpecConfig
     __syncthreads();
     const float inv_n = 1.0f / (float)n;
     for (int i = tid; i < 3 * n; i += blockDim.x) {
-        const int a = i / n, jj = i % n, Dy = jj / C, Dx = jj % C;
+        const int a = qdiv(i, cfg.mn), jj = i - a * n, Dy = qdiv(jj, cfg.mC), Dx = jj - Dy * C;
         const float2 *col = U + a * n + Dx;
         float re = 0.f;
         for (int Ky = 0, m = 0; Ky < C; ++Ky) {       // m = Ky * Dy mod C
@@ -454,7 +460,7 @@ __global__ void __launch_bounds__(kUpdMaxThreads) k_spec_update(const SpecConfig
     // ---- new S of the updated offset (global, and in H for the next sub-step's term)
     float2 *So = b.S + ((size_t)r * ll + (oy * l + ox)) * 3 * n;
     for (int i = tid; i < 3 * n; i += blockDim.x) {
-        const int bb = i / n, j = i % n, Dy = j / C, Kx = j % C;
+        const int bb = qdiv(i, cfg.mn), j = i - bb * n, Dy = qdiv(j, cfg.mC), Kx = j - Dy * C;
         const float *row = sn + bb * n + Dy * C;
         float2 acc = make_float2(0.f, 0.f);
         for (int Dx = 0, m = 0; Dx < C; ++Dx) {       // m = Kx * Dx mod C
@@ -468,7 +474,7 @@ __global__ void __launch_bounds__(kUpdMaxThreads) k_spec_update(const SpecConfig
     }
     __syncthreads();
     for (int i = tid; i < 3 * n; i += blockDim.x) {
-        const int bb = i / n, j = i % n, Ky = j / C, Kx = j % C;
+        const int bb = qdiv(i, cfg.mn), j = i - bb * n, Ky = qdiv(j, cfg.mC), Kx = j - Ky * C;
         const float2 *col = U + bb * n + Kx;
         float2 acc = make_float2(0.f, 0.f);
         for (int Dy = 0, m = 0; Dy < C; ++Dy) {       // m = Ky * Dy mod C
@@ -490,7 +496,7 @@ __global__ void __launch_bounds__(kUpdMaxThreads) k_spec_update(const SpecConfig
         dy += sy ? l : 0;
         const float2 *Tp = b.T + (size_t)(dy * l + dx) * 4 * n;
         for (int i = tid; i < 3 * n; i += blockDim.x) {
-            const int a = i / n, K = i % n, Kx = K % C, Ky = K / C;
+            const int a = qdiv(i, cfg.mn), K = i - a * n, Ky = qdiv(K, cfg.mC), Kx = K - Ky * C;
             int m = (sx ? Kx : 0) + (sy ? Ky : 0);
             if (m >= C) m -= C;
             const float2 p = omega(m, C);

@@ -20,7 +20,10 @@ struct SpecConfig {
     int skip_prev;          // field: leave out the previous sub-step's offset (its term comes from the update)
     int extra_in;           // update: the partial spectra have one more chunk (that term)
     int extra_out;          // update: write the next sub-step's term of the updated offset
+    uint32_t mC, mn;        // ceil(2^32 / C), ceil(2^32 / n): exact x / C and x / n for x * C, x * n < 2^32
 };
+
+inline uint32_t fastdiv_magic(uint32_t d) { return (uint32_t)(((1ull << 32) + d - 1) / d); }
 
 struct SpecBuffers {
     const float *W32 = nullptr;          // [4][N]: W~(0) for the self term

@@ -11,9 +11,9 @@
 // This is the same field the direct path computes, up to rounding.
 //
 // k_window_steps: one CTA (8 warps) per replica.  Spins live in shared memory
-// for the window; warp 0 takes the decisions (lanes d < n: the n sites of the
-// sub-step); warps 1..7 add the accepted moves
-// contributions to the fields of the window's remaining sites.
+// for the window; warp 0 takes the decisions of blocks of 8 sub-steps on its
+// own (pulling the corrections of the last two blocks' moves); warps 1..7 push
+// older moves into the fields of the window's later sites.
 #include <cuda_bf16.h>
 
 #include "internal.cuh"
@@ -24,6 +24,7 @@ namespace dipmc {
 namespace {
 
 constexpr int kWThreads = 256;
+constexpr int kBlockSites = 16; // sites per decider block (G = 16 / n sub-steps; at least one sub-step)
 constexpr float kPiF = 3.14159265358979f;
 
 __device__ __forceinline__ void perp_basis_w(float nx, float ny, float nz, float3 &b1, float3 &b2) {
@@ -73,6 +74,18 @@ __device__ void obs_push_level(ObsAcc &A, const double x[MC_NOBS], int k) {
 // The tensor is even in x and in y except xy, which is odd in each: a
 // displacement (dx, dy) reads entry (|dx|, |dy|) and flips the sign of xy when
 // exactly one of dx, dy is negative (xy vanishes on the axes and at L/2).
+// W~(dx, dy) itself, (xx, xy, yy, zz), from the quarter table.
+__device__ __forceinline__ float4 wq_get(const float4 *__restrict__ wq, int L, int dx, int dy) {
+    const int h = L >> 1;
+    if (dx < 0) dx += L;
+    if (dy < 0) dy += L;
+    float sgn = 1.0f;
+    if (dx > h) { dx = L - dx; sgn = -sgn; }
+    if (dy > h) { dy = L - dy; sgn = -sgn; }
+    const float4 w = wq[dy * (h + 1) + dx];
+    return make_float4(w.x, sgn * w.y, w.z, w.w);
+}
+
 __device__ __forceinline__ float3 wq_apply(const float4 *__restrict__ wq, int L, int dx, int dy, float3 d) {
     const int h = L >> 1;
     if (dx < 0) dx += L;
@@ -101,9 +114,12 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
     float4 *pS = hcur + Sw;                                      // [Sw] proposal S, threshold -T ln u
     float4 *pd = pS + Sw;                                        // [Sw] delta = S - s, field-free part of dE
     float4 *wq = pd + Sw;                                        // [(L/2+1)^2] minimum-image quarter of W~
-    int *wxy = reinterpret_cast<int *>(wq + hq * hq);            // [Sw] site as x | y << 16
-    __shared__ float4 s_acc[2][32];                              // accepted moves of a sub-step: (delta, x | y << 16),
-    __shared__ int s_nacc[2];                                    // double-buffered by sub-step parity
+    constexpr int GN = n >= kBlockSites ? n : kBlockSites;       // sites per decider block
+    float4 *s_mvb = wq + hq * hq;                                // [2][GN] accepted moves of a block:
+                                                                 // (delta, x | y << 16), double-buffered by parity
+    float4 *wpair = s_mvb + 2 * GN;                              // [GN][GN] W~ between the sites of a block
+    int *wxy = reinterpret_cast<int *>(wpair + GN * GN);         // [Sw] site as x | y << 16
+    __shared__ int s_nmv[2];
     __shared__ double s_epart[32];
     __shared__ float s_mred[kWThreads / 32][12];
 
@@ -214,182 +230,179 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
             pd[s] = D;
         }
     }
-    if (tid < 64) s_acc[tid >> 5][tid & 31] = make_float4(0.f, 0.f, 0.f, __int_as_float(0));
     __syncthreads();
 
     long long n_acc = 0;
-    // One barrier per sub-step.  In phase j, warp 0 adds the moves of sub-step j-1 to
-    // the fields of its own n sites and decides sub-step j, while warps 1.. add the
-    // moves of sub-step j-1 to the fields of every later site (sub-steps >= j+1).
-    // Warp 0 keeps the static data of its next sites (coordinates, proposal,
-    // field-free part of dE) in registers, loaded one sub-step ahead.
-    int nx_xy = 0;
-    float4 nx_S = make_float4(0.f, 0.f, 0.f, 0.f), nx_D = nx_S;
-    if (warp == 0 && lane < n) {
-        nx_xy = wxy[lane];
-        if (pre_ok) {
-            nx_S = pS[lane];
-            nx_D = pd[lane];
-        }
+    // Blocks of G sub-steps (16 sites), two CTA barriers per block.  At the start
+    // of block b all warps add the moves of block b-1 to the fields of block b's
+    // sites, which then hold the stale field plus every move before the block (the
+    // moves of blocks <= b-2 were pushed there earlier by the helpers), and tabulate
+    // W~ between each site of the block and the sites of its earlier sub-steps.
+    // Then warp 0 (the decider) runs the block's sub-steps alone, pulling the moves
+    // of the block's earlier sub-steps through that table (lanes split them, a
+    // shuffle reduction sums them per site), while warps 1.. (the helpers) push the
+    // moves of block b-1 into every site of blocks >= b+1.  Block move lists are
+    // compact (accepted moves only) and double-buffered by parity.
+    const int G = B % (GN / n) == 0 ? GN / n : 1;   // sub-steps per block
+    const int nblk = B / G;
+    constexpr int LPS = 32 / n;                       // decider lanes per site
+    const int dsite = lane / LPS, dsub = lane % LPS;  // decider lane -> (site, move subset)
+    if (tid == 0) {
+        s_nmv[0] = 0;
+        s_nmv[1] = 0;
     }
-    for (int j = 0; j < B; ++j) {
-        const int cur = j & 1, prev = cur ^ 1;
-        if (warp == 0) {
-            int accept = 0;
-            float dX = 0.f, dY = 0.f, dZ = 0.f, dE = 0.f;
-            const int s = j * n + lane;
-            const int xy = nx_xy;
-            const int qx = xy & 0xFFFF, qy = (xy >> 16) & 0x7FFF, q = qy * L + qx;
-            float4 h = make_float4(0.f, 0.f, 0.f, 0.f), a = h, b = h, c = h, dd = h;
-            int xp = 0, xm = 0, yp = 0, ym = 0;
-            if (lane < n) {
-                h = hcur[s];
-                xp = (qx + 1 == L) ? q - qx : q + 1;
-                xm = (qx == 0) ? q + L - 1 : q - 1;
-                yp = (qy + 1 == L) ? qx : q + L;
-                ym = (qy == 0) ? q + N - L : q - L;
-                a = s4[xp]; b = s4[xm]; c = s4[yp]; dd = s4[ym];
-            }
-            // field change from the last sub-step's moves: one (site, move) pair per lane
-            if (j > 0) {
-                float3 cr = make_float3(0.f, 0.f, 0.f);
-                if constexpr (n * n <= 32) {
-                    const int d = lane / n, m = lane % n;
-                    const int sxy = __shfl_sync(0xffffffffu, xy, d < n ? d : 0);
-                    if (lane < n * n) {
-                        const float4 mv = s_acc[prev][m];
-                        const int pxy = __float_as_int(mv.w);
-                        cr = wq_apply(wq, L, (sxy & 0xFFFF) - (pxy & 0xFFFF),
-                                      ((sxy >> 16) & 0x7FFF) - ((pxy >> 16) & 0x7FFF), make_float3(mv.x, mv.y, mv.z));
-                    }
-#pragma unroll
-                    for (int off = 1; off < n; off <<= 1) {
-                        cr.x += __shfl_xor_sync(0xffffffffu, cr.x, off);
-                        cr.y += __shfl_xor_sync(0xffffffffu, cr.y, off);
-                        cr.z += __shfl_xor_sync(0xffffffffu, cr.z, off);
-                    }
-                    const int src = (lane < n ? lane : 0) * n;
-                    cr.x = __shfl_sync(0xffffffffu, cr.x, src);
-                    cr.y = __shfl_sync(0xffffffffu, cr.y, src);
-                    cr.z = __shfl_sync(0xffffffffu, cr.z, src);
-                } else {
-                    if (lane < n) {
-#pragma unroll
-                        for (int i = 0; i < n; ++i) {
-                            const float4 mv = s_acc[prev][i];
-                            const int pxy = __float_as_int(mv.w);
-                            const float3 cc = wq_apply(wq, L, qx - (pxy & 0xFFFF), qy - ((pxy >> 16) & 0x7FFF),
-                                                       make_float3(mv.x, mv.y, mv.z));
-                            cr.x += cc.x;
-                            cr.y += cc.y;
-                            cr.z += cc.z;
-                        }
-                    }
+    __syncthreads();
+    const int tps = kWThreads / (G * n);               // threads per block site in the catch-up
+    for (int bk = 0; bk < nblk; ++bk) {
+        const int cur = bk & 1, prv = cur ^ 1;
+        const int nprev = bk > 0 ? s_nmv[prv] : 0;
+        if (G > 1) {
+            // W~ between each site of the block and the sites of its earlier sub-steps
+            const int base = bk * G * n;
+            for (int idx = tid; idx < G * n * G * n; idx += kWThreads) {
+                const int i = idx / (G * n), i2 = idx - i * (G * n);
+                if (i2 / n < i / n) {
+                    const int a = wxy[base + i], c = wxy[base + i2];
+                    wpair[idx] = wq_get(wq, L, (a & 0xFFFF) - (c & 0xFFFF), ((a >> 16) & 0x7FFF) - ((c >> 16) & 0x7FFF));
                 }
+            }
+        }
+        if (nprev > 0) {
+            // catch-up: the moves of block b-1 into the sites of block b
+            const int site = tid / tps, g = tid - site * tps, s = bk * G * n + site;
+            const int xy = wxy[s];
+            const int qx = xy & 0xFFFF, qy = (xy >> 16) & 0x7FFF;
+            float3 cr = make_float3(0.f, 0.f, 0.f);
+            for (int m = g; m < nprev; m += tps) {
+                const float4 mv = s_mvb[prv * GN + m];
+                const int pxy = __float_as_int(mv.w);
+                const float3 c = wq_apply(wq, L, qx - (pxy & 0xFFFF), qy - ((pxy >> 16) & 0x7FFF),
+                                          make_float3(mv.x, mv.y, mv.z));
+                cr.x += c.x;
+                cr.y += c.y;
+                cr.z += c.z;
+            }
+            for (int off = 1; off < tps; off <<= 1) {
+                cr.x += __shfl_xor_sync(0xffffffffu, cr.x, off);
+                cr.y += __shfl_xor_sync(0xffffffffu, cr.y, off);
+                cr.z += __shfl_xor_sync(0xffffffffu, cr.z, off);
+            }
+            if (g == 0) {
+                float4 h = hcur[s];
                 h.x += cr.x;
                 h.y += cr.y;
                 h.z += cr.z;
+                hcur[s] = h;
             }
-            if (lane < n) {
-                float4 S, D;
-                float thr;
-                if (pre_ok) {
-                    S = nx_S;
-                    D = nx_D;
-                    thr = S.w;
-                } else {
-                    const uint4 wds = attempt_rng(s, q);
-                    float sps, cps;
-                    sincospif(2.0f * u24f(wds.y), &sps, &cps);
-                    const float u = u24f(wds.z);
-                    propose(q, u24f(wds.x), cps, sps, S, D);
-                    thr = (u > 0.0f) ? -P.T * logf(u) : INFINITY;
+        }
+        if (G > 1 || nprev > 0) __syncthreads();
+        if (warp == 0) {
+            int ncur = 0;                                    // moves of this block so far (warp-uniform)
+            for (int u = 0; u < G; ++u) {
+                const int j = bk * G + u;
+                const int s = j * n + dsite;
+                const int xy = wxy[s];
+                const int qx = xy & 0xFFFF, qy = (xy >> 16) & 0x7FFF, q = qy * L + qx;
+                // pull: moves of this block's earlier sub-steps (pd holds the move of an
+                // accepted site and zero for a rejected one), split over the site's lanes
+                float3 cr = make_float3(0.f, 0.f, 0.f);
+                const float4 *wrow = wpair + (u * n + dsite) * (G * n);
+                const int base = bk * G * n;
+                for (int i2 = dsub; i2 < u * n; i2 += LPS) {
+                    const float4 w = wrow[i2], mv = pd[base + i2];
+                    cr.x += w.x * mv.x + w.y * mv.y;
+                    cr.y += w.y * mv.x + w.z * mv.y;
+                    cr.z += w.w * mv.z;
                 }
-                dX = D.x;
-                dY = D.y;
-                dZ = D.z;
-                const float n0 = (a.x + b.x) + (c.x + dd.x);
-                const float n1 = (a.y + b.y) + (c.y + dd.y);
-                const float n2 = (a.z + b.z) + (c.z + dd.z);
-                const float dex = -P.J * (dX * n0 + dY * n1 + dZ * n2);
-                dE = D.w + dex + P.CD * (dX * h.x + dY * h.y + dZ * h.z);
-                accept = dE < thr;
-                if (buf.trace) {
-                    const uint4 wds = attempt_rng(s, q);
-                    float *tr = buf.trace + ((((size_t)r * cfg.nsweeps_call + cfg.it) * ll + (k0 + j)) * n + lane) * MC_TRACE_W;
-                    tr[0] = (float)q;
-                    tr[1] = h.x; tr[2] = h.y; tr[3] = h.z;
-                    tr[4] = dE;
-                    tr[5] = u24f(wds.z);
-                    tr[6] = (float)accept;
-                    tr[7] = S.x; tr[8] = S.y; tr[9] = S.z;
+#pragma unroll
+                for (int off = 1; off < LPS; off <<= 1) {
+                    cr.x += __shfl_xor_sync(0xffffffffu, cr.x, off);
+                    cr.y += __shfl_xor_sync(0xffffffffu, cr.y, off);
+                    cr.z += __shfl_xor_sync(0xffffffffu, cr.z, off);
                 }
-                if (accept) {
-                    s4[q] = make_float4(S.x, S.y, S.z, 0.0f);
-                    pd[s] = make_float4(dX, dY, dZ, dE);      // the move, for the window-end bookkeeping
-                    wxy[s] = xy | (int)0x80000000;             // accepted
-                }
-                if (j + 1 < B) {                               // next sub-step's static data
-                    nx_xy = wxy[s + n];
+                int accept = 0;
+                float dX = 0.f, dY = 0.f, dZ = 0.f;
+                if (dsub == 0) {
+                    float4 h = hcur[s];
+                    h.x += cr.x;
+                    h.y += cr.y;
+                    h.z += cr.z;
+                    const int xp = (qx + 1 == L) ? q - qx : q + 1;
+                    const int xm = (qx == 0) ? q + L - 1 : q - 1;
+                    const int yp = (qy + 1 == L) ? qx : q + L;
+                    const int ym = (qy == 0) ? q + N - L : q - L;
+                    const float4 a = s4[xp], bb = s4[xm], c = s4[yp], dd = s4[ym];
+                    float4 S, D;
+                    float thr;
                     if (pre_ok) {
-                        nx_S = pS[s + n];
-                        nx_D = pd[s + n];
+                        S = pS[s];
+                        D = pd[s];
+                        thr = S.w;
+                    } else {
+                        const uint4 wds = attempt_rng(s, q);
+                        float sps, cps;
+                        sincospif(2.0f * u24f(wds.y), &sps, &cps);
+                        const float uu = u24f(wds.z);
+                        propose(q, u24f(wds.x), cps, sps, S, D);
+                        thr = (uu > 0.0f) ? -P.T * logf(uu) : INFINITY;
                     }
+                    dX = D.x;
+                    dY = D.y;
+                    dZ = D.z;
+                    const float n0 = (a.x + bb.x) + (c.x + dd.x);
+                    const float n1 = (a.y + bb.y) + (c.y + dd.y);
+                    const float n2 = (a.z + bb.z) + (c.z + dd.z);
+                    const float dex = -P.J * (dX * n0 + dY * n1 + dZ * n2);
+                    const float dE = D.w + dex + P.CD * (dX * h.x + dY * h.y + dZ * h.z);
+                    accept = dE < thr;
+                    if (buf.trace) {
+                        const uint4 wds = attempt_rng(s, q);
+                        float *tr = buf.trace + ((((size_t)r * cfg.nsweeps_call + cfg.it) * ll + (k0 + j)) * n + dsite) *
+                                                    MC_TRACE_W;
+                        tr[0] = (float)q;
+                        tr[1] = h.x; tr[2] = h.y; tr[3] = h.z;
+                        tr[4] = dE;
+                        tr[5] = u24f(wds.z);
+                        tr[6] = (float)accept;
+                        tr[7] = S.x; tr[8] = S.y; tr[9] = S.z;
+                    }
+                    if (accept) {
+                        s4[q] = make_float4(S.x, S.y, S.z, 0.0f);
+                        wxy[s] = xy | (int)0x80000000;             // accepted
+                    }
+                    // the move (for the block's later sub-steps and the window-end bookkeeping)
+                    pd[s] = accept ? make_float4(dX, dY, dZ, dE) : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
-            }
-            // slots [0, n) of the move list are all written every sub-step: accepted
-            // moves first, then one zero move per rejected site (readers use all n)
-            const unsigned ball = __ballot_sync(0xffffffffu, accept);
-            const unsigned below = (1u << lane) - 1u;
-            const unsigned nmask = (n >= 32) ? 0xffffffffu : ((1u << n) - 1u);
-            if (lane < n) {
+                // append the accepted moves of this sub-step to the block's list, in site order
+                const unsigned ball = __ballot_sync(0xffffffffu, accept);
                 if (accept) {
-                    s_acc[cur][__popc(ball & below)] = make_float4(dX, dY, dZ, __int_as_float(xy));
-                } else {
-                    const int slot = __popc(ball) + __popc(~ball & below & nmask);
-                    s_acc[cur][slot] = make_float4(0.f, 0.f, 0.f, __int_as_float(0));
+                    const unsigned below = ball & ((1u << lane) - 1u);
+                    s_mvb[cur * GN + ncur + __popc(below)] = make_float4(dX, dY, dZ, __int_as_float(xy));
                 }
+                ncur += __popc(ball);
+                __syncwarp();
             }
             if (lane == 0) {
-                n_acc += __popc(ball);
-                s_nacc[cur] = __popc(ball);
+                s_nmv[cur] = ncur;
+                n_acc += ncur;
             }
-        } else if (j > 0) {
-            const int np = s_nacc[prev];
-            if (np) {
-                // the sub-step's moves, in registers (n slots, unused ones are zero moves)
-                float4 mv[n];
-                int mx[n], my[n];
-#pragma unroll
-                for (int i = 0; i < n; ++i) {
-                    mv[i] = s_acc[prev][i];
-                    const int pxy = __float_as_int(mv[i].w);
-                    mx[i] = pxy & 0xFFFF;
-                    my[i] = (pxy >> 16) & 0x7FFF;
+        } else if (nprev > 0) {
+            // helpers: push the moves of block b-1 into the sites of blocks >= b+1
+            constexpr int kH = kWThreads - 32;
+            for (int s = (bk + 1) * G * n + (tid - 32); s < Sw; s += kH) {
+                const int xy = wxy[s];
+                const int qx = xy & 0xFFFF, qy = (xy >> 16) & 0x7FFF;
+                float4 h = hcur[s];
+                for (int m = 0; m < nprev; ++m) {
+                    const float4 mv = s_mvb[prv * GN + m];
+                    const int pxy = __float_as_int(mv.w);
+                    const float3 c = wq_apply(wq, L, qx - (pxy & 0xFFFF), qy - ((pxy >> 16) & 0x7FFF),
+                                              make_float3(mv.x, mv.y, mv.z));
+                    h.x += c.x;
+                    h.y += c.y;
+                    h.z += c.z;
                 }
-                constexpr int kC = kWThreads - 32;
-                // two later sites per pass for independent chains
-                for (int s = (j + 1) * n + (tid - 32); s < Sw; s += 2 * kC) {
-                    const int s2 = s + kC;
-                    const bool two = s2 < Sw;
-                    const int xy = wxy[s], xy2 = two ? wxy[s2] : xy;
-                    const int qx = xy & 0xFFFF, qy = (xy >> 16) & 0x7FFF;
-                    const int qx2 = xy2 & 0xFFFF, qy2 = (xy2 >> 16) & 0x7FFF;
-                    float4 h = hcur[s];
-                    float4 h2 = two ? hcur[s2] : h;
-#pragma unroll
-                    for (int i = 0; i < n; ++i) {
-                        if (i < np) {
-                            const float3 d3 = make_float3(mv[i].x, mv[i].y, mv[i].z);
-                            const float3 c = wq_apply(wq, L, qx - mx[i], qy - my[i], d3);
-                            const float3 c2 = wq_apply(wq, L, qx2 - mx[i], qy2 - my[i], d3);
-                            h.x += c.x; h.y += c.y; h.z += c.z;
-                            h2.x += c2.x; h2.y += c2.y; h2.z += c2.z;
-                        }
-                    }
-                    hcur[s] = h;
-                    if (two) hcur[s2] = h2;
-                }
+                hcur[s] = h;
             }
         }
         __syncthreads();
@@ -520,9 +533,10 @@ __global__ void k_spins_to_bf16(size_t count, const float *__restrict__ s, __nv_
 
 }  // namespace
 
-size_t window_smem_bytes(int L, int Sw) {
+size_t window_smem_bytes(int L, int Sw, int n) {
     const size_t N = (size_t)L * L, hq = (size_t)(L / 2 + 1);
-    return sizeof(float4) * (N + 3 * (size_t)Sw + hq * hq) + sizeof(int) * (size_t)Sw;
+    const size_t GN = n >= kBlockSites ? n : kBlockSites;
+    return sizeof(float4) * (N + 3 * (size_t)Sw + hq * hq + 2 * GN + GN * GN) + sizeof(int) * (size_t)Sw;
 }
 
 bool window_supported(int L, int l, int B) {
@@ -530,12 +544,16 @@ bool window_supported(int L, int l, int B) {
     const int C = L / l;
     if (C != 1 && C != 2 && C != 4) return false;
     if (B < 1 || (l * l) % B) return false;
-    return window_smem_bytes(L, B * C * C) <= 200 * 1024;
+    // decider blocks of at least 8 sites (the catch-up reduces within a warp)
+    const int n = C * C, GN = n >= kBlockSites ? n : kBlockSites;
+    const int G = B % (GN / n) == 0 ? GN / n : 1;
+    if (G * n < 8) return false;
+    return window_smem_bytes(L, B * C * C, C * C) <= 200 * 1024;
 }
 
 cudaError_t launch_window_steps(const WindowConfig &c, const WindowBuffers &b, cudaStream_t st) {
     const int C = c.L / c.l;
-    const size_t smem = window_smem_bytes(c.L, c.B * C * C);
+    const size_t smem = window_smem_bytes(c.L, c.B * C * C, C * C);
     cudaError_t e;
 #define LAUNCH(CC)                                                                                   \
     e = cudaFuncSetAttribute(k_window_steps<CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \

@@ -39,7 +39,7 @@ struct WindowBuffers {
     EnergyHist hist;              // optional energy histogram
 };
 
-size_t window_smem_bytes(int L, int Sw);
+size_t window_smem_bytes(int L, int Sw, int n);
 cudaError_t launch_build_wq(int L, const float *W32, float4 *wq, cudaStream_t st);
 cudaError_t launch_set_u32(uint32_t *dst, uint32_t v, cudaStream_t st);
 bool window_supported(int L, int l, int B);
