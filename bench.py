@@ -517,11 +517,12 @@ def main():
             roof["traffic"] = json.load(open(tfile)).get("dram_bytes_per_launch")
         except Exception:
             pass
-    # kernels of ours launched per timed step: direct = 1 sweep kernel; tensor = one
-    # bf16 split of the spins + per window (sites, tensor-core field, sub-steps);
-    # FP32 window = per window (full field, sub-steps)
+    # kernels of ours launched per timed step: direct = 1 sweep kernel; tensor = the
+    # sweep counter, one bf16 split of the spins + per window (sites, tensor-core
+    # field, split-K reduction, sub-steps); FP32 window = counter + per window
+    # (full field, sub-steps)
     nwin = (l * l * (L // l) ** 2) // Sw if Sw else 0
-    per_step = {"direct": 1, "tensor": 1 + 3 * nwin * S, "window": 2 * nwin * S}[args.path]
+    per_step = {"direct": 1, "tensor": 2 + 4 * nwin * S, "window": 1 + 2 * nwin * S}[args.path]
     gpu_launches = per_step * args.steps
 
     # end to end through the public API: host spins in (pinned), S sweeps,

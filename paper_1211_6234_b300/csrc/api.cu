@@ -83,6 +83,11 @@ struct mc_lattice {
     int *wsite = nullptr;
     TcUnit *units = nullptr;
     int nunits = 0, NT = 0, tmem_cols = 0, plan_Sw = 0;
+    float *tcpart = nullptr;      // [nunits][NT][128] partial tiles of the split-K contraction
+    alignas(64) unsigned char tm_hi[128], tm_lo[128];   // TMA maps of spins_hi / spins_lo
+    int tm_NT = 0;
+    int *tile_first = nullptr;    // [ntiles * mtiles + 1]
+    int mtiles = 0, ntiles = 0;
     int *err_flag = nullptr;
     bool wsh_ready = false;
     float4 *wq = nullptr;     // quarter table of W~ for the windowed paths
@@ -139,6 +144,8 @@ void free_all(mc_lattice *p) {
     cudaFree(p->H0);
     cudaFree(p->wsite);
     cudaFree(p->units);
+    cudaFree(p->tcpart);
+    cudaFree(p->tile_first);
     cudaFree(p->err_flag);
     cudaFree(p->wq);
     cudaFree(p->What);
@@ -318,19 +325,31 @@ int ensure_tensor_buffers(mc_lattice *p, int Sw, cudaStream_t st) {
         cudaFree(p->H0);
         cudaFree(p->wsite);
         cudaFree(p->units);
-        p->H0 = nullptr; p->wsite = nullptr; p->units = nullptr;
+        cudaFree(p->tcpart);
+        cudaFree(p->tile_first);
+        p->H0 = nullptr; p->wsite = nullptr; p->units = nullptr; p->tcpart = nullptr; p->tile_first = nullptr;
         CKA(cudaMalloc(&p->H0, sizeof(float) * R * 3 * Sw));
         CKA(cudaMalloc(&p->wsite, sizeof(int) * Sw));
         int dev = 0, nsm = 148;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         std::vector<TcUnit> u(65536);
-        const int nu = tc_plan(p->L, Sw, p->R, nsm, u.data(), (int)u.size(), &p->NT, &p->tmem_cols);
+        std::vector<int> tf(1 << 16);
+        const int nu = tc_plan(p->L, Sw, p->R, nsm, u.data(), (int)u.size(), &p->NT, &p->tmem_cols, tf.data(),
+                               &p->mtiles, &p->ntiles);
         if (nu <= 0) return fail(MC_EINVAL, "tensor-core plan failed for Sw=%d R=%d", Sw, p->R);
         CKA(cudaMalloc(&p->units, sizeof(TcUnit) * nu));
         CKA(cudaMemcpy(p->units, u.data(), sizeof(TcUnit) * nu, cudaMemcpyHostToDevice));
+        const int ntf = p->ntiles * p->mtiles + 1;
+        CKA(cudaMalloc(&p->tile_first, sizeof(int) * ntf));
+        CKA(cudaMemcpy(p->tile_first, tf.data(), sizeof(int) * ntf, cudaMemcpyHostToDevice));
+        CKA(cudaMalloc(&p->tcpart, sizeof(float) * (size_t)nu * p->NT * 128));
         p->nunits = nu;
         p->plan_Sw = Sw;
+        if (tc_map_bytes() > sizeof(p->tm_hi) || tc_encode_map(p->tm_hi, p->spins_hi, p->L, p->R, p->NT) ||
+            tc_encode_map(p->tm_lo, p->spins_lo, p->L, p->R, p->NT))
+            return fail(MC_ECUDA, "TMA map of the bf16 spins could not be encoded");
+        p->tm_NT = p->NT;
     }
     return MC_OK;
 }
@@ -370,6 +389,7 @@ int run_windows(mc_lattice *p, int path, int nsweeps, int measure_every, float *
         ta.L = p->L; ta.Sw = Sw; ta.R = p->R; ta.NT = p->NT; ta.ldh = 3 * Sw; ta.tmem_cols = p->tmem_cols;
         ta.units = p->units; ta.wsite = p->wsite; ta.wsh = p->wsh;
         ta.spins_hi = p->spins_hi; ta.spins_lo = p->spins_lo; ta.H0 = p->H0; ta.error = p->err_flag;
+        ta.part = p->tcpart; ta.tile_first = p->tile_first; ta.mtiles = p->mtiles; ta.ntiles = p->ntiles;
     }
     for (int it = 0; it < nsweeps; ++it) {
         c.t = (uint32_t)(p->t + (uint64_t)it);
@@ -379,12 +399,16 @@ int run_windows(mc_lattice *p, int path, int nsweeps, int measure_every, float *
             if (tensor) {
                 e = launch_window_sites(p->L, p->l, c.key, c.t, p->t_dev, it, p->schedule, w * B, B, p->wsite, st);
                 if (e != cudaSuccess) return cuda_fail(e, "window sites");
-                CKA(cudaMemsetAsync(p->H0, 0, sizeof(float) * (size_t)p->R * 3 * Sw, st));
                 {
                     TimedLaunch tl(p, MC_K_TC_FIELD, st);
-                    e = launch_tc_field(ta, p->nunits, st);
+                    e = launch_tc_field(ta, p->nunits, p->tm_hi, p->tm_lo, st);
                 }
                 if (e != cudaSuccess) return cuda_fail(e, "tensor-core field launch");
+                {
+                    TimedLaunch tl(p, MC_K_TC_REDUCE, st);
+                    e = launch_tc_reduce(ta, st);
+                }
+                if (e != cudaSuccess) return cuda_fail(e, "split-K reduction launch");
             } else {
                 TimedLaunch tl(p, MC_K_FULL_FIELD, st);
                 e = launch_full_field(p->L, p->R, p->W32, p->spins, p->field, st);

@@ -16,13 +16,18 @@
 // product is hi_A hi_B + hi_A lo_B + lo_A hi_B (error ~2^-18 relative).
 //
 // One CTA = one (M-tile of 128 rows, N-tile of up to 256 replicas, range of
-// K-blocks of 32).  Operands are staged by all threads with cp.async into the
-// canonical K-major, no-swizzle core-matrix layout (8 rows x 16 bytes per core
-// matrix) in a ring of 4 stages, loads running 2 stages ahead of the MMAs; a
-// stage is refilled once the MMAs that read it have committed.  Thread 0 issues
+// K-blocks of 32).  Operands sit in the canonical K-major, no-swizzle
+// core-matrix layout (8 rows x 16 bytes per core matrix) in a ring of 4 stages,
+// loads running 2 stages ahead of the MMAs; a stage is refilled once the MMAs
+// that read it have committed.  The Toeplitz A tile is gathered by all threads
+// with cp.async; the spin tile B comes by TMA, one 2D box of 8 K-elements x NT
+// replicas per core-matrix column (rows past R arrive as zeros), completing on
+// the stage's full barrier.  Thread 0 issues
 // tcgen05.mma (M=128, N=tile, K=16) into a TMEM accumulator and commits each
-// stage to its mbarrier.  The epilogue reads TMEM with tcgen05.ld and adds the
-// partial tile into H0 (split-K reduction).
+// stage to its mbarrier.  The epilogue reads TMEM with tcgen05.ld and stores the
+// unit's partial tile (split-K); k_tc_reduce sums the partial tiles of each
+// output tile in a fixed order into H0 (deterministic, no atomics).
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "internal.cuh"
@@ -52,14 +57,30 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)_
 // (leading byte offset), adjacent along M/N: kSBO bytes (stride byte offset).
 __device__ __forceinline__ uint32_t core_off(int row, int kc) { return (row >> 3) * kSBO + kc * 128 + (row & 7) * 16; }
 
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo = 128u, uint32_t sbo = (uint32_t)kSBO) {
     uint64_t d = 0;
     d |= (uint64_t)((addr >> 4) & 0x3FFFu);          // start address
-    d |= (uint64_t)(128u >> 4) << 16;                 // leading byte offset (K direction)
-    d |= (uint64_t)((uint32_t)kSBO >> 4) << 32;       // stride byte offset (M/N direction)
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;      // leading byte offset (K direction)
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;      // stride byte offset (M/N direction)
     d |= (uint64_t)1 << 46;                           // descriptor version for tcgen05
     // base offset 0, layout type 0 = no swizzle
     return d;
+}
+
+// B tile as the TMA boxes leave it: core-matrix column kc (8 K-elements of all
+// NT rows) at kc * NT * 16 bytes, 8-row groups 128 bytes apart.
+__device__ __forceinline__ uint32_t bcol_off(int NT, int kc) { return (uint32_t)(kc * NT * 16); }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *m, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
+}
+
+// 2D TMA load of a box at (x, y) of the tensor map into shared memory.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint64_t *m) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(m))
+        : "memory");
 }
 
 // Instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major.
@@ -102,8 +123,6 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
 template <int N>
 __device__ __forceinline__ void cp_async_wait_pending() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
@@ -137,9 +156,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a) {
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a, const __grid_constant__ CUtensorMap tm_hi,
+                                                           const __grid_constant__ CUtensorMap tm_lo) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ uint64_t mbar[kStages];
+    __shared__ uint64_t mbar[kStages];       // MMAs of a stage done (stage free)
+    __shared__ uint64_t fbar[kStages];       // TMA bytes of a stage arrived (stage full)
     __shared__ uint32_t tmem_base_s;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -167,7 +188,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) mbar_init(&mbar[s], 1);
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&mbar[s], 1);
+            mbar_init(&fbar[s], 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -203,16 +227,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a)
                 if (mx >= L) { mx -= L; ++my; }
             }
         }
-        // B: spins of NT replicas x kKB (zero rows past R); kKC consecutive threads
-        // read the kKC chunks of one replica row (contiguous in global memory)
-        const int kofs = (zz ? 2 * N : 0) + k0;
-        for (int idx = tid; idx < nrows_b * kKC; idx += kTcThreads) {
-            const int rr = idx / kKC, kc = idx % kKC;
-            const int r = n0 + rr;
-            const bool in = r < a.R;
-            const size_t g = (size_t)(in ? r : 0) * 3 * N + kofs + kc * 8;
-            cp_async16(sBhi + core_off(rr, kc), a.spins_hi + g, in ? 16u : 0u);
-            cp_async16(sBlo + core_off(rr, kc), a.spins_lo + g, in ? 16u : 0u);
+        // B: spins of NT replicas x kKB by TMA (x = K offset, a multiple of 8
+        // elements = 16 bytes; rows past R read as zeros)
+        if (tid == 0) {
+            const int kofs = (zz ? 2 * N : 0) + k0;
+            uint64_t *fb = &fbar[i % kStages];
+            mbar_expect_tx(fb, (uint32_t)(2 * kKC * nrows_b * 16));
+#pragma unroll
+            for (int kc = 0; kc < kKC; ++kc) {
+                tma_load_2d(sBhi + bcol_off(nrows_b, kc), &tm_hi, kofs + kc * 8, n0, fb);
+                tma_load_2d(sBlo + bcol_off(nrows_b, kc), &tm_lo, kofs + kc * 8, n0, fb);
+            }
         }
     };
     // prologue: the first kAhead stages
@@ -234,16 +259,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();                              // ... and every thread's
         if (tid == 0) {
+            ok &= mbar_wait(&fbar[i % kStages], (uint32_t)((i / kStages) & 1));   // the stage's B tile
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t ah = smem_u32(smem + (i % kStages) * kStage);
             const uint32_t alo = ah + kTileA, bh = ah + 2 * kTileA, blo = bh + kTileB;
+            const uint32_t blbo = (uint32_t)(nrows_b * 16);   // K-adjacent core matrices of B
 #pragma unroll
             for (int ks = 0; ks < kKB / 16; ++ks) {
-                const uint32_t ko = ks * 256;        // 16 K elements = 2 core matrices = 256 B
+                const uint32_t ko = ks * 256;        // A: 16 K elements = 2 core matrices = 256 B
+                const uint32_t kb = ks * 2 * blbo;   // B: 2 core-matrix columns
                 const uint32_t acc0 = (i > 0 || ks > 0) ? 1u : 0u;
-                umma_bf16(tmem, smem_desc(ah + ko), smem_desc(bh + ko), idesc, acc0);
-                umma_bf16(tmem, smem_desc(ah + ko), smem_desc(blo + ko), idesc, 1u);
-                umma_bf16(tmem, smem_desc(alo + ko), smem_desc(bh + ko), idesc, 1u);
+                umma_bf16(tmem, smem_desc(ah + ko), smem_desc(bh + kb, blbo, 128u), idesc, acc0);
+                umma_bf16(tmem, smem_desc(ah + ko), smem_desc(blo + kb, blbo, 128u), idesc, 1u);
+                umma_bf16(tmem, smem_desc(alo + ko), smem_desc(bh + kb, blbo, 128u), idesc, 1u);
             }
             umma_commit(&mbar[i % kStages]);
         }
@@ -257,16 +285,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a)
     if (!ok) {
         if (tid == 0) atomicExch(a.error, 1);
     } else if (nkb > 0) {
-        // ---- epilogue: warp w owns TMEM lanes 32w..32w+31 = rows of the tile
-        const int row = row0 + warp * 32 + lane;
+        // ---- epilogue: warp w owns TMEM lanes 32w..32w+31 = rows of the tile; the
+        // partial tile goes to the unit's slot, row fastest (a warp stores 128 B per column)
+        float *pt = a.part + (size_t)blockIdx.x * nrows_b * 128 + warp * 32 + lane;
         for (int cb = 0; cb < nrows_b; cb += 32) {
             float v[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int r = n0 + cb + j;
-                if (r < a.R) atomicAdd(a.H0 + (size_t)r * a.ldh + row, v[j]);
-            }
+            for (int j = 0; j < 32; ++j)
+                if (cb + j < nrows_b) pt[(size_t)(cb + j) * 128] = v[j];   // NT may end mid-chunk (NT % 32 == 16)
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -275,6 +302,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)a.tmem_cols)
                      : "memory");
     }
+}
+
+// H0 of output tile (mt, nt): the sum of its units' partial tiles, in unit order.
+// Thread = (column, row) with row fastest: partial reads and H0 writes coalesce.
+__global__ void __launch_bounds__(256) k_tc_reduce(const TcFieldArgs a) {
+    const int mt = blockIdx.x, nt = blockIdx.y;
+    const int idx = blockIdx.z * 256 + threadIdx.x;
+    const int col = idx >> 7, row = idx & 127;
+    if (col >= a.NT) return;
+    const int r = nt * a.NT + col;
+    if (r >= a.R) return;
+    const int u0 = a.tile_first[nt * a.mtiles + mt], u1 = a.tile_first[nt * a.mtiles + mt + 1];
+    float s = 0.f;
+    for (int u = u0; u < u1; ++u) s += a.part[((size_t)u * a.NT + col) * 128 + row];
+    a.H0[(size_t)r * a.ldh + mt * 128 + row] = s;
 }
 
 // 8 shifted, doubled bf16 hi/lo copies of W~: wsh[c][comp][hl][y][i] = part_hl(W~_comp(y, (i + c) mod L)),
@@ -346,7 +388,8 @@ cudaError_t launch_window_sites(int L, int l, uint2 key, uint32_t t, const uint3
     return cudaGetLastError();
 }
 
-int tc_plan(int L, int Sw, int R, int nsm, TcUnit *units, int max_units, int *NT_out, int *tmem_cols) {
+int tc_plan(int L, int Sw, int R, int nsm, TcUnit *units, int max_units, int *NT_out, int *tmem_cols,
+            int *tile_first, int *mtiles_out, int *ntiles_out) {
     const int N = L * L;
     const int NT = R >= 256 ? 256 : ((R + 15) / 16) * 16;
     const int ntiles = (R + NT - 1) / NT;
@@ -365,8 +408,10 @@ int tc_plan(int L, int Sw, int R, int nsm, TcUnit *units, int max_units, int *NT
         if (cnt * ntiles <= nsm || kbpu >= kb_inplane) break;
     }
     int nu = 0;
+    const int mtiles = mt_inplane + mt_zz;
     for (int nt = 0; nt < ntiles; ++nt)
-        for (int mt = 0; mt < mt_inplane + mt_zz; ++mt) {
+        for (int mt = 0; mt < mtiles; ++mt) {
+            tile_first[nt * mtiles + mt] = nu;
             const int nkb = mt < mt_inplane ? kb_inplane : kb_zz;
             for (int kb = 0; kb < nkb; kb += kbpu) {
                 if (nu >= max_units) return -1;
@@ -377,6 +422,9 @@ int tc_plan(int L, int Sw, int R, int nsm, TcUnit *units, int max_units, int *NT
                 ++nu;
             }
         }
+    tile_first[ntiles * mtiles] = nu;
+    *mtiles_out = mtiles;
+    *ntiles_out = ntiles;
     *NT_out = NT;
     int cols = 32;
     while (cols < NT) cols <<= 1;
@@ -384,11 +432,32 @@ int tc_plan(int L, int Sw, int R, int nsm, TcUnit *units, int max_units, int *NT
     return nu;
 }
 
-cudaError_t launch_tc_field(const TcFieldArgs &a, int nunits, cudaStream_t st) {
+cudaError_t launch_tc_reduce(const TcFieldArgs &a, cudaStream_t st) {
+    k_tc_reduce<<<dim3(a.mtiles, a.ntiles, (a.NT * 128 + 255) / 256), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// 2D tensor map of a [R][3N] bf16 spin array: boxes of 8 elements x NT rows.
+int tc_encode_map(void *map, const __nv_bfloat16 *spins, int L, int R, int NT) {
+    const cuuint64_t dims[2] = {(cuuint64_t)3 * L * L, (cuuint64_t)R};
+    const cuuint64_t strides[1] = {(cuuint64_t)3 * L * L * sizeof(__nv_bfloat16)};
+    const cuuint32_t box[2] = {8u, (cuuint32_t)NT};
+    const cuuint32_t estr[2] = {1u, 1u};
+    const CUresult r = cuTensorMapEncodeTiled(static_cast<CUtensorMap *>(map), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                                              const_cast<__nv_bfloat16 *>(spins), dims, strides, box, estr,
+                                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : -1;
+}
+
+size_t tc_map_bytes() { return sizeof(CUtensorMap); }
+
+cudaError_t launch_tc_field(const TcFieldArgs &a, int nunits, const void *map_hi, const void *map_lo, cudaStream_t st) {
     const size_t smem = tc_smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(k_tc_field, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_tc_field<<<nunits, kTcThreads, smem, st>>>(a);
+    k_tc_field<<<nunits, kTcThreads, smem, st>>>(a, *static_cast<const CUtensorMap *>(map_hi),
+                                                  *static_cast<const CUtensorMap *>(map_lo));
     return cudaGetLastError();
 }
 

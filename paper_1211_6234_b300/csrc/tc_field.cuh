@@ -20,8 +20,11 @@ struct TcFieldArgs {
     const __nv_bfloat16 *wsh;            // tc_wsh_elems(L): shifted hi/lo copies of W~
     const __nv_bfloat16 *spins_hi;       // [R][3][N]
     const __nv_bfloat16 *spins_lo;       // [R][3][N]
-    float *H0;                           // [R][ldh] (+=)
+    float *H0;                           // [R][ldh], written by the reduction
     int *error;                          // set to 1 if a bounded wait gave up
+    float *part;                         // [nunits][NT][128]: each unit's partial tile, row fastest
+    const int *tile_first;               // [ntiles * mtiles + 1]: first unit of tile (nt, mt)
+    int mtiles, ntiles;
 };
 
 size_t tc_wsh_elems(int L);
@@ -32,7 +35,15 @@ cudaError_t launch_window_sites(int L, int l, uint2 key, uint32_t t, const uint3
                                 int k0, int B, int *wsite, cudaStream_t st);
 // Fills units[] for a window of Sw sites and R replicas; returns the number of
 // units (CTAs) or -1 if max_units is too small.
-int tc_plan(int L, int Sw, int R, int nsm, TcUnit *units, int max_units, int *NT, int *tmem_cols);
-cudaError_t launch_tc_field(const TcFieldArgs &a, int nunits, cudaStream_t st);
+// Work plan: units ordered by (N-tile, M-tile, K range); tile_first (host,
+// ntiles * mtiles + 1 entries) gets the first unit of each tile.
+int tc_plan(int L, int Sw, int R, int nsm, TcUnit *units, int max_units, int *NT, int *tmem_cols,
+            int *tile_first, int *mtiles, int *ntiles);
+// TMA maps of the bf16 spin arrays (opaque 64-byte-aligned buffers of tc_map_bytes()).
+size_t tc_map_bytes();
+int tc_encode_map(void *map, const __nv_bfloat16 *spins, int L, int R, int NT);
+cudaError_t launch_tc_field(const TcFieldArgs &a, int nunits, const void *map_hi, const void *map_lo, cudaStream_t st);
+// H0 = sum over each tile's units of their partial tiles, in unit order.
+cudaError_t launch_tc_reduce(const TcFieldArgs &a, cudaStream_t st);
 
 }  // namespace dipmc

@@ -38,7 +38,7 @@ ABI_SYMBOLS = (
     "mc_server_collect", "mc_server_get_spins", "mc_server_release", "mc_server_get_stats", "mc_server_destroy",
 )
 MC_REQ_QUEUED, MC_REQ_RUNNING, MC_REQ_DONE, MC_REQ_FAILED, MC_REQ_RELEASED = range(5)
-KERNEL_CLASSES = ("sweep_direct", "tc_field", "window_steps", "full_field", "spec_field", "spec_update")
+KERNEL_CLASSES = ("sweep_direct", "tc_field", "window_steps", "full_field", "spec_field", "spec_update", "tc_reduce")
 
 
 class McError(RuntimeError):
@@ -90,7 +90,7 @@ class mc_server_stats(C.Structure):
 
 
 class mc_timing(C.Structure):
-    _fields_ = [("launches", C.c_int64 * 6), ("ms", C.c_double * 6)]
+    _fields_ = [("launches", C.c_int64 * 7), ("ms", C.c_double * 7)]
 
 
 def _load():
