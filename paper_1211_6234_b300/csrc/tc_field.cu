@@ -37,7 +37,7 @@ namespace dipmc {
 
 namespace {
 
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 256;              // two threads per row of the 128-row tile
 constexpr int kKB = 32;                       // K elements per stage
 constexpr int kKC = kKB / 8;                  // core matrices along K per row
 constexpr int kSBO = kKC * 128;               // bytes between 8-row groups
@@ -173,8 +173,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a,
     const int nrows_b = a.NT;                       // N of the MMA
     const uint32_t idesc = make_idesc(128, nrows_b);
 
-    // row tid of the tile: site and tensor components (constant over the K loop)
-    const int my_row = row0 + tid;
+    // row (tid % 128) of the tile: site and tensor components (constant over the K
+    // loop); threads tid and tid + 128 gather the two halves of the row's K block
+    const int arow = tid & 127, ahalf = tid >> 7;
+    const int my_row = row0 + arow;
     const int my_b = my_row / Sw;                         // output component 0 x, 1 y, 2 z
     const int my_q = a.wsite[my_row - my_b * Sw];
     const int my_qy = my_q / L, my_qx = my_q - my_qy * L;
@@ -207,22 +209,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a,
         const uint32_t sAhi = smem_u32(base), sAlo = sAhi + kTileA;
         const uint32_t sBhi = sAhi + 2 * kTileA, sBlo = sBhi + kTileB;
         const int k0 = (u.kb_begin + i) * kKB;       // K offset within this tile's contraction
-        // A: Toeplitz tile, 128 rows x kKB; thread tid builds row tid (kKC chunks of 8)
+        // A: Toeplitz tile, 128 rows x kKB; thread (arow, ahalf) builds chunks
+        // [ahalf * kKC/2, (ahalf + 1) * kKC/2) of row arow
         {
+            constexpr int kHalf = kKC / 2;
             const int al = zz ? 2 : (k0 >= N ? 1 : 0);    // input component of this K block
             const int comp = zz ? 3 : (al == 0 ? comp_a0 : comp_a1);
-            const int m0 = k0 - (zz ? 0 : al * N);        // first source site of the block
+            const int m0 = k0 - (zz ? 0 : al * N) + ahalf * kHalf * 8;   // first source site of the half
             int my = m0 / L, mx = m0 - my * L;
             const __nv_bfloat16 *wc = a.wsh + (size_t)comp * 2 * L * 2 * L;
 #pragma unroll
-            for (int kc = 0; kc < kKC; ++kc) {
+            for (int c = 0; c < kHalf; ++c) {
+                const int kc = ahalf * kHalf + c;
                 int dy = my - my_qy;
                 if (dy < 0) dy += L;
                 int x0 = mx - my_qx;                      // W~(q - m) = W~(m - q): forward segment from x0
                 if (x0 < 0) x0 += L;
                 const size_t off = (size_t)(x0 & 7) * 4 * 2 * L * 2 * L + (size_t)dy * (2 * L) + (x0 & ~7);
-                cp_async16(sAhi + core_off(tid, kc), wc + off, 16);
-                cp_async16(sAlo + core_off(tid, kc), wc + off + (size_t)L * 2 * L, 16);
+                cp_async16(sAhi + core_off(arow, kc), wc + off, 16);
+                cp_async16(sAlo + core_off(arow, kc), wc + off + (size_t)L * 2 * L, 16);
                 mx += 8;
                 if (mx >= L) { mx -= L; ++my; }
             }
@@ -285,12 +290,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a,
     if (!ok) {
         if (tid == 0) atomicExch(a.error, 1);
     } else if (nkb > 0) {
-        // ---- epilogue: warp w owns TMEM lanes 32w..32w+31 = rows of the tile; the
-        // partial tile goes to the unit's slot, row fastest (a warp stores 128 B per column)
-        float *pt = a.part + (size_t)blockIdx.x * nrows_b * 128 + warp * 32 + lane;
-        for (int cb = 0; cb < nrows_b; cb += 32) {
+        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 = rows of the tile,
+        // warps w and w + 4 alternate 32-column chunks; the partial tile goes to the
+        // unit's slot, row fastest (a warp stores 128 B per column)
+        const int wl = warp & 3;
+        float *pt = a.part + (size_t)blockIdx.x * nrows_b * 128 + wl * 32 + lane;
+        for (int cb = (warp >> 2) * 32; cb < nrows_b; cb += 64) {
             float v[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
+            tmem_ld32(tmem + ((uint32_t)(wl * 32) << 16) + (uint32_t)cb, v);
 #pragma unroll
             for (int j = 0; j < 32; ++j)
                 if (cb + j < nrows_b) pt[(size_t)(cb + j) * 128] = v[j];   // NT may end mid-chunk (NT % 32 == 16)
