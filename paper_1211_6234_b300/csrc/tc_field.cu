@@ -28,6 +28,7 @@
 // unit's partial tile (split-K); k_tc_reduce sums the partial tiles of each
 // output tile in a fixed order into H0 (deterministic, no atomics).
 #include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include "internal.cuh"
@@ -444,13 +445,24 @@ cudaError_t launch_tc_reduce(const TcFieldArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// 2D tensor map of a [R][3N] bf16 spin array: boxes of 8 elements x NT rows.
+// 2D tensor map of a [R][3N] bf16 spin array: boxes of 8 elements x NT rows.  The
+// driver's encoder is reached through the runtime's entry-point query, so the
+// library does not link libcuda and loads on hosts without a driver.
 int tc_encode_map(void *map, const __nv_bfloat16 *spins, int L, int R, int NT) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return -1;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
     const cuuint64_t dims[2] = {(cuuint64_t)3 * L * L, (cuuint64_t)R};
     const cuuint64_t strides[1] = {(cuuint64_t)3 * L * L * sizeof(__nv_bfloat16)};
     const cuuint32_t box[2] = {8u, (cuuint32_t)NT};
     const cuuint32_t estr[2] = {1u, 1u};
-    const CUresult r = cuTensorMapEncodeTiled(static_cast<CUtensorMap *>(map), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+    const CUresult r = encode(static_cast<CUtensorMap *>(map), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
                                               const_cast<__nv_bfloat16 *>(spins), dims, strides, box, estr,
                                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
