@@ -11,9 +11,10 @@
 // This is the same field the direct path computes, up to rounding.
 //
 // k_window_steps: one CTA (8 warps) per replica.  Spins live in shared memory
-// for the window; warp 0 takes the decisions of blocks of 8 sub-steps on its
-// own (pulling the corrections of the last two blocks' moves); warps 1..7 push
-// older moves into the fields of the window's later sites.
+// for the window; warp 0 takes the decisions of blocks of 16 sites on its own;
+// warps 1..7 push older moves into the window's later sites.  Under the
+// permutation schedule a site's proposal is fixed at the window's start, so what
+// the decider adds per sub-step is a sum of precomputed scalar pair energies.
 #include <cuda_bf16.h>
 
 #include "internal.cuh"
@@ -98,27 +99,55 @@ __device__ __forceinline__ float3 wq_apply(const float4 *__restrict__ wq, int L,
     return make_float3(w.x * d.x + xy * d.y, xy * d.x + w.z * d.y, w.w * d.z);
 }
 
-template <int C>
+// Scalar pair energy of two window sites i and p (x | y << 16 coordinates, flag bit
+// ignored): the dipolar change C_D d_i.W~(q_i - q_p).d_p of site i's move once p has
+// moved, plus, when `exch`, the exchange change -J m d_i.d_p, m = the number of lattice
+// directions in which q_p neighbours q_i (Eq. 1 with both moves in place).
+__device__ __forceinline__ float pair_energy(const float4 *__restrict__ wq, int L, int ai, int ap, float4 di,
+                                             float4 dp, float CD, float J, bool exch) {
+    const int dx = (ai & 0xFFFF) - (ap & 0xFFFF), dy = ((ai >> 16) & 0x7FFF) - ((ap >> 16) & 0x7FFF);
+    const float3 w = wq_apply(wq, L, dx, dy, make_float3(dp.x, dp.y, dp.z));
+    float e = CD * (di.x * w.x + di.y * w.y + di.z * w.z);
+    if (exch) {
+        const int ax = dx < 0 ? dx + L : dx, ay = dy < 0 ? dy + L : dy;
+        int m = 0;
+        if (ay == 0) m += (ax == 1) + (ax == L - 1);
+        if (ax == 0) m += (ay == 1) + (ay == L - 1);
+        if (m) e -= J * (float)m * (di.x * dp.x + di.y * dp.y + di.z * dp.z);
+    }
+    return e;
+}
+
+// PRE: the permutation schedule, where every site is visited once per sweep, so the
+// proposal, its threshold and the field-free part of dE of every window site are fixed
+// at the window's start.  The window's sub-steps then only add, to each site's dE, the
+// pair energies of the moves accepted before it, and the decisions of a block of 16
+// sites run as a chain of ballots over precomputed pair energies.  Otherwise (the
+// with-replacement schedule, where a site may recur within a window) each decision
+// proposes from the current spin and pulls the field vector of the block's moves.
+template <int C, bool PRE>
 __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfig cfg, const WindowBuffers buf) {
     constexpr int n = C * C;
+    constexpr int NB = kBlockSites;   // sites per decider block
+    constexpr int G = NB / n;         // sub-steps per block
     const int L = cfg.L, l = cfg.l, N = L * L, ll = l * l, B = cfg.B, Sw = B * n;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int r = blockIdx.x;
-    const bool pre_ok = cfg.schedule == 0;   // each site visited once per sweep: its spin is
-                                             // unchanged until its own sub-step of the window
 
     extern __shared__ float4 smem_w[];
     const int hq = (L >> 1) + 1;
-    float4 *s4 = smem_w;                                         // [N] spins
-    float4 *hcur = s4 + N;                                       // [Sw] field of the window sites
-    float4 *pS = hcur + Sw;                                      // [Sw] proposal S, threshold -T ln u
-    float4 *pd = pS + Sw;                                        // [Sw] delta = S - s, field-free part of dE
-    float4 *wq = pd + Sw;                                        // [(L/2+1)^2] minimum-image quarter of W~
-    constexpr int GN = n >= kBlockSites ? n : kBlockSites;       // sites per decider block
-    float4 *s_mvb = wq + hq * hq;                                // [2][GN] accepted moves of a block:
-                                                                 // (delta, x | y << 16), double-buffered by parity
-    float4 *wpair = s_mvb + 2 * GN;                              // [GN][GN] W~ between the sites of a block
-    int *wxy = reinterpret_cast<int *>(wpair + GN * GN);         // [Sw] site as x | y << 16
+    float4 *s4 = smem_w;                                 // [N] spins
+    float4 *hcur = s4 + N;                               // [Sw] !PRE: field of the window sites (stale + pushed moves)
+    float *dacc = reinterpret_cast<float *>(hcur);       // PRE: [Sw] dE so far, without exchange and block pairs
+    float4 *pS = hcur + Sw;                              // [Sw] proposal S, threshold -T ln u; after the decision w = dE
+    float4 *pd = pS + Sw;                                // [Sw] delta = S - s, field-free part of dE
+    float4 *wq = pd + Sw;                                // [(L/2+1)^2] minimum-image quarter of W~
+    float4 *s_mvb = wq + hq * hq;                        // [2][NB] accepted moves of a block:
+                                                         // (delta, x | y << 16), double-buffered by parity
+    float4 *wpair = s_mvb + 2 * NB;                      // !PRE: [NB][NB] W~ between the sites of a block
+    float4 *etab = wpair;                                // PRE: [2][2 NB / 4][NB] pair energies by block parity,
+                                                         // four columns of a row per float4
+    int *wxy = reinterpret_cast<int *>(wpair + NB * NB); // [Sw] site as x | y << 16 (bit 31: accepted)
     __shared__ int s_nmv[2];
     __shared__ double s_epart[32];
     __shared__ float s_mred[kWThreads / 32][12];
@@ -165,12 +194,12 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
         S = make_float4(S0, S1, S2, 0.0f);
         D = make_float4(dX, dY, dZ, dan + 0.5f * P.CD * self);
     };
-    const uint4 rk = cfg.schedule == 0 ? philox(make_uint4(t, 0u, 0u, kTagPerm), key) : make_uint4(0, 0, 0, 0);
+    const uint4 rk = PRE ? philox(make_uint4(t, 0u, 0u, kTagPerm), key) : make_uint4(0, 0, 0, 0);
     const int hbits = ceil_log2_u((uint32_t)l);
     auto site_of = [&](int s) -> int {
         const int j = s / n, d = s % n, k = k0 + j;
         uint32_t v;
-        if (cfg.schedule == 0) {
+        if (PRE) {
             v = perm_offset(rk, hbits, (uint32_t)ll, (uint32_t)k);
         } else {
             const uint4 o = philox(make_uint4(t, (uint32_t)k, 0u, kTagDraw), key);
@@ -183,41 +212,44 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
         const int k = k0 + s / n;
         return philox(make_uint4((uint32_t)q, (uint32_t)r, t, ((uint32_t)k & 0x00FFFFFFu) | kTagAttempt), key);
     };
+    auto trace_row = [&](int s) -> float * {
+        return buf.trace + ((((size_t)r * cfg.nsweeps_call + cfg.it) * ll + (k0 + s / n)) * n + s % n) * MC_TRACE_W;
+    };
+    // neighbour sum of site (qx, qy) from the spins in shared memory
+    auto nbr_sum = [&](int qx, int qy) -> float3 {
+        const int q = qy * L + qx;
+        const int xp = (qx + 1 == L) ? q - qx : q + 1;
+        const int xm = (qx == 0) ? q + L - 1 : q - 1;
+        const int yp = (qy + 1 == L) ? qx : q + L;
+        const int ym = (qy == 0) ? q + N - L : q - L;
+        const float4 a = s4[xp], bb = s4[xm], c = s4[yp], dd = s4[ym];
+        return make_float3((a.x + bb.x) + (c.x + dd.x), (a.y + bb.y) + (c.y + dd.y), (a.z + bb.z) + (c.z + dd.z));
+    };
+
+    // the stale field at window site s (lattice site q)
+    auto stale_at = [&](int s, int q) -> float3 {
+        if (cfg.stale_mode == 0) {
+            const float *f = buf.stale + (size_t)r * 3 * N;
+            return make_float3(f[q], f[N + q], f[2 * N + q]);
+        }
+        const float *hr = buf.stale + (size_t)r * cfg.ldh;
+        return make_float3(hr[0 * Sw + s], hr[1 * Sw + s], hr[2 * Sw + s]);
+    };
 
     // ---- window set-up: state, tensor table, sites, stale field, proposals
     const float *gs = buf.spins + (size_t)r * 3 * N;
-    {
-        const float4 *gx = reinterpret_cast<const float4 *>(gs);            // N % 4 == 0 (L even)
-        const float4 *gy = reinterpret_cast<const float4 *>(gs + N);
-        const float4 *gz = reinterpret_cast<const float4 *>(gs + 2 * N);
-        for (int i = tid; i < N / 4; i += kWThreads) {
-            const float4 a = gx[i], b = gy[i], c = gz[i];
-            s4[4 * i + 0] = make_float4(a.x, b.x, c.x, 0.0f);
-            s4[4 * i + 1] = make_float4(a.y, b.y, c.y, 0.0f);
-            s4[4 * i + 2] = make_float4(a.z, b.z, c.z, 0.0f);
-            s4[4 * i + 3] = make_float4(a.w, b.w, c.w, 0.0f);
-        }
-    }
+#pragma unroll 4
+    for (int q = tid; q < N; q += kWThreads) s4[q] = make_float4(gs[q], gs[N + q], gs[2 * N + q], 0.0f);
+#pragma unroll 4
     for (int i = tid; i < hq * hq; i += kWThreads) wq[i] = buf.wq[i];
     __syncthreads();
     for (int s = tid; s < Sw; s += kWThreads) {
         const int xy = site_of(s);
         const int q = (xy >> 16) * L + (xy & 0xFFFF);
         wxy[s] = xy;
-        float h0, h1, h2;
-        if (cfg.stale_mode == 0) {
-            const float *f = buf.stale + (size_t)r * 3 * N;
-            h0 = f[q];
-            h1 = f[N + q];
-            h2 = f[2 * N + q];
-        } else {
-            const float *hr = buf.stale + (size_t)r * cfg.ldh;
-            h0 = hr[0 * Sw + s];
-            h1 = hr[1 * Sw + s];
-            h2 = hr[2 * Sw + s];
-        }
-        hcur[s] = make_float4(h0, h1, h2, 0.0f);
-        if (pre_ok) {
+        const float3 hs = stale_at(s, q);
+        const float h0 = hs.x, h1 = hs.y, h2 = hs.z;
+        if (PRE) {
             const uint4 wds = attempt_rng(s, q);
             float sps, cps;
             sincospif(2.0f * u24f(wds.y), &sps, &cps);
@@ -228,184 +260,305 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
             S.w = (u > 0.0f) ? -P.T * logf(u) : INFINITY;
             pS[s] = S;
             pd[s] = D;
+            dacc[s] = D.w + P.CD * (D.x * h0 + D.y * h1 + D.z * h2);
+        } else {
+            hcur[s] = make_float4(h0, h1, h2, 0.0f);
         }
     }
-    __syncthreads();
-
-    long long n_acc = 0;
-    // Blocks of G sub-steps (16 sites), two CTA barriers per block.  At the start
-    // of block b all warps add the moves of block b-1 to the fields of block b's
-    // sites, which then hold the stale field plus every move before the block (the
-    // moves of blocks <= b-2 were pushed there earlier by the helpers), and tabulate
-    // W~ between each site of the block and the sites of its earlier sub-steps.
-    // Then warp 0 (the decider) runs the block's sub-steps alone, pulling the moves
-    // of the block's earlier sub-steps through that table (lanes split them, a
-    // shuffle reduction sums them per site), while warps 1.. (the helpers) push the
-    // moves of block b-1 into every site of blocks >= b+1.  Block move lists are
-    // compact (accepted moves only) and double-buffered by parity.
-    const int G = B % (GN / n) == 0 ? GN / n : 1;   // sub-steps per block
-    const int nblk = B / G;
-    constexpr int LPS = 32 / n;                       // decider lanes per site
-    const int dsite = lane / LPS, dsub = lane % LPS;  // decider lane -> (site, move subset)
     if (tid == 0) {
         s_nmv[0] = 0;
         s_nmv[1] = 0;
     }
     __syncthreads();
-    const int tps = kWThreads / (G * n);               // threads per block site in the catch-up
-    for (int bk = 0; bk < nblk; ++bk) {
-        const int cur = bk & 1, prv = cur ^ 1;
-        const int nprev = bk > 0 ? s_nmv[prv] : 0;
-        if (G > 1) {
-            // W~ between each site of the block and the sites of its earlier sub-steps
-            const int base = bk * G * n;
-            for (int idx = tid; idx < G * n * G * n; idx += kWThreads) {
-                const int i = idx / (G * n), i2 = idx - i * (G * n);
-                if (i2 / n < i / n) {
-                    const int a = wxy[base + i], c = wxy[base + i2];
-                    wpair[idx] = wq_get(wq, L, (a & 0xFFFF) - (c & 0xFFFF), ((a >> 16) & 0x7FFF) - ((c >> 16) & 0x7FFF));
+
+    long long n_acc = 0;
+    const int nblk = B / G;
+    if constexpr (PRE) {
+        // pair energies of block nb into etab[nb & 1]: row i is site nb*NB + i; columns
+        // 0..NB-1 the sites of block nb-1 (dipolar part: their exchange acts through the
+        // spins, which hold those moves by the time block nb decides), columns NB.. the
+        // sites of the block's own earlier sub-steps (dipolar and exchange).  Entry e is
+        // column e / NB of row e % NB, so a warp's lanes take one column pair.
+        auto etab_fill = [&](int nb, int t0, int stride) {
+            float *et = reinterpret_cast<float *>(etab + (nb & 1) * (2 * NB / 4) * NB);
+            for (int e = t0; e < NB * 2 * NB; e += stride) {
+                const int c = e / NB, i = e % NB;
+                const int si = nb * NB + i;
+                float v = 0.0f;
+                if (c < NB) {
+                    if (nb > 0) {
+                        const int sp = (nb - 1) * NB + c;
+                        v = pair_energy(wq, L, wxy[si], wxy[sp], pd[si], pd[sp], P.CD, P.J, false);
+                    }
+                } else if ((c - NB) / n < i / n) {
+                    const int sp = nb * NB + (c - NB);
+                    v = pair_energy(wq, L, wxy[si], wxy[sp], pd[si], pd[sp], P.CD, P.J, true);
                 }
+                et[((c >> 2) * NB + i) * 4 + (c & 3)] = v;
             }
-        }
-        if (nprev > 0) {
-            // catch-up: the moves of block b-1 into the sites of block b
-            const int site = tid / tps, g = tid - site * tps, s = bk * G * n + site;
-            const int xy = wxy[s];
-            const int qx = xy & 0xFFFF, qy = (xy >> 16) & 0x7FFF;
-            float3 cr = make_float3(0.f, 0.f, 0.f);
-            for (int m = g; m < nprev; m += tps) {
-                const float4 mv = s_mvb[prv * GN + m];
-                const int pxy = __float_as_int(mv.w);
-                const float3 c = wq_apply(wq, L, qx - (pxy & 0xFFFF), qy - ((pxy >> 16) & 0x7FFF),
-                                          make_float3(mv.x, mv.y, mv.z));
-                cr.x += c.x;
-                cr.y += c.y;
-                cr.z += c.z;
-            }
-            for (int off = 1; off < tps; off <<= 1) {
-                cr.x += __shfl_xor_sync(0xffffffffu, cr.x, off);
-                cr.y += __shfl_xor_sync(0xffffffffu, cr.y, off);
-                cr.z += __shfl_xor_sync(0xffffffffu, cr.z, off);
-            }
-            if (g == 0) {
-                float4 h = hcur[s];
-                h.x += cr.x;
-                h.y += cr.y;
-                h.z += cr.z;
-                hcur[s] = h;
-            }
-        }
-        if (G > 1 || nprev > 0) __syncthreads();
-        if (warp == 0) {
-            int ncur = 0;                                    // moves of this block so far (warp-uniform)
-            for (int u = 0; u < G; ++u) {
-                const int j = bk * G + u;
-                const int s = j * n + dsite;
+        };
+        etab_fill(0, tid, kWThreads);
+        __syncthreads();
+        // Blocks of G sub-steps (16 sites), one CTA barrier per block.  Warp 0 (the
+        // decider) takes block b's decisions: a site's dE is its window-start value, plus
+        // the pushed pair energies of the moves of blocks <= b-2, plus those of block b-1
+        // and of the block's earlier sub-steps from the pair table, with the exchange of
+        // all earlier moves through the current neighbour spins.  Warps 1.. (the helpers)
+        // meanwhile push the moves of block b-1 into the sites of blocks >= b+1 and
+        // tabulate block b+1's pair energies.
+        unsigned pm = 0;   // accepted sites of the previous block (decider)
+        for (int bk = 0; bk < nblk; ++bk) {
+            const int cur = bk & 1, prv = cur ^ 1, base = bk * NB;
+            if (warp == 0) {
+                const int i = lane & (NB - 1);
+                const int s = base + i;
+                const float4 *er = etab + cur * (2 * NB / 4) * NB + i;
+                float E[2 * NB];
+#pragma unroll
+                for (int c = 0; c < 2 * NB; c += 4) {
+                    const float4 v = er[(c >> 2) * NB];
+                    E[c] = v.x;
+                    E[c + 1] = v.y;
+                    E[c + 2] = v.z;
+                    E[c + 3] = v.w;
+                }
                 const int xy = wxy[s];
                 const int qx = xy & 0xFFFF, qy = (xy >> 16) & 0x7FFF, q = qy * L + qx;
-                // pull: moves of this block's earlier sub-steps (pd holds the move of an
-                // accepted site and zero for a rejected one), split over the site's lanes
-                float3 cr = make_float3(0.f, 0.f, 0.f);
-                const float4 *wrow = wpair + (u * n + dsite) * (G * n);
-                const int base = bk * G * n;
-                for (int i2 = dsub; i2 < u * n; i2 += LPS) {
-                    const float4 w = wrow[i2], mv = pd[base + i2];
-                    cr.x += w.x * mv.x + w.y * mv.y;
-                    cr.y += w.y * mv.x + w.z * mv.y;
-                    cr.z += w.w * mv.z;
-                }
+                const float4 D = pd[s], S = pS[s];
+                const float3 nb3 = nbr_sum(qx, qy);
+                float dE = dacc[s] - P.J * (D.x * nb3.x + D.y * nb3.y + D.z * nb3.z);
 #pragma unroll
-                for (int off = 1; off < LPS; off <<= 1) {
+                for (int p = 0; p < NB; ++p)
+                    if ((pm >> p) & 1u) dE += E[p];
+                unsigned am = 0;
+#pragma unroll
+                for (int u = 0; u < G; ++u) {
+                    const unsigned ball = __ballot_sync(0xffffffffu, lane < NB && i / n == u && dE < S.w);
+                    am |= ball;
+                    if (u + 1 < G) {
+#pragma unroll
+                        for (int d = 0; d < n; ++d)
+                            if ((ball >> (u * n + d)) & 1u) dE += E[NB + u * n + d];
+                    }
+                }
+                const bool act = lane < NB;
+                const bool acc = act && ((am >> i) & 1u);
+                if (act && buf.trace) {
+                    // the field the decision saw: stale field plus every earlier accepted move
+                    const float3 h0 = stale_at(s, q);
+                    float hx = h0.x, hy = h0.y, hz = h0.z;
+                    for (int p = 0; p < base + i; ++p) {
+                        const int pxy = wxy[p];
+                        const bool moved = p < base ? pxy < 0 : ((p - base) / n < i / n && ((am >> (p - base)) & 1u));
+                        if (!moved) continue;
+                        const float4 dp = pd[p];
+                        const float3 w = wq_apply(wq, L, qx - (pxy & 0xFFFF), qy - ((pxy >> 16) & 0x7FFF),
+                                                  make_float3(dp.x, dp.y, dp.z));
+                        hx += w.x;
+                        hy += w.y;
+                        hz += w.z;
+                    }
+                    const uint4 wds = attempt_rng(s, q);
+                    float *tr = trace_row(s);
+                    tr[0] = (float)q;
+                    tr[1] = hx; tr[2] = hy; tr[3] = hz;
+                    tr[4] = dE;
+                    tr[5] = u24f(wds.z);
+                    tr[6] = (float)acc;
+                    tr[7] = S.x; tr[8] = S.y; tr[9] = S.z;
+                }
+                __syncwarp();
+                if (act) {
+                    reinterpret_cast<float *>(pS + s)[3] = dE;
+                    if (acc) {
+                        s4[q] = make_float4(S.x, S.y, S.z, 0.0f);
+                        wxy[s] = xy | (int)0x80000000;
+                        s_mvb[cur * NB + __popc(am & ((1u << lane) - 1u))] = make_float4(D.x, D.y, D.z, __int_as_float(xy));
+                    }
+                }
+                pm = am;
+                if (lane == 0) {
+                    s_nmv[cur] = __popc(am);
+                    n_acc += __popc(am);
+                }
+            } else {
+                constexpr int kH = kWThreads - 32;
+                const int ht = tid - 32;
+                const int nprev = bk > 0 ? s_nmv[prv] : 0;
+                // push the moves of block b-1 into the dE of the sites of blocks >= b+1
+                if (nprev > 0) {
+                    for (int s = base + NB + ht; s < Sw; s += kH) {
+                        const int xy = wxy[s];
+                        const int qx = xy & 0xFFFF, qy = (xy >> 16) & 0x7FFF;
+                        const float4 D = pd[s];
+                        float e = 0.0f;
+                        for (int m = 0; m < nprev; ++m) {
+                            const float4 mv = s_mvb[prv * NB + m];
+                            const int pxy = __float_as_int(mv.w);
+                            const float3 w = wq_apply(wq, L, qx - (pxy & 0xFFFF), qy - ((pxy >> 16) & 0x7FFF),
+                                                      make_float3(mv.x, mv.y, mv.z));
+                            e += D.x * w.x + D.y * w.y + D.z * w.z;
+                        }
+                        dacc[s] += P.CD * e;
+                    }
+                }
+                if (bk + 1 < nblk) etab_fill(bk + 1, ht, kH);
+            }
+            __syncthreads();
+        }
+    } else {
+        // Blocks of G sub-steps (16 sites), two CTA barriers per block.  At the start
+        // of block b all warps add the moves of block b-1 to the fields of block b's
+        // sites, which then hold the stale field plus every move before the block (the
+        // moves of blocks <= b-2 were pushed there earlier by the helpers), and tabulate
+        // W~ between each site of the block and the sites of its earlier sub-steps.
+        // Then warp 0 (the decider) runs the block's sub-steps alone, pulling the moves
+        // of the block's earlier sub-steps through that table (lanes split them, a
+        // shuffle reduction sums them per site), while warps 1.. (the helpers) push the
+        // moves of block b-1 into every site of blocks >= b+1.  Block move lists are
+        // compact (accepted moves only) and double-buffered by parity.
+        constexpr int LPS = 32 / n;                       // decider lanes per site
+        const int dsite = lane / LPS, dsub = lane % LPS;  // decider lane -> (site, move subset)
+        constexpr int tps = kWThreads / NB;               // threads per block site in the catch-up
+        for (int bk = 0; bk < nblk; ++bk) {
+            const int cur = bk & 1, prv = cur ^ 1;
+            const int nprev = bk > 0 ? s_nmv[prv] : 0;
+            if (G > 1) {
+                // W~ between each site of the block and the sites of its earlier sub-steps
+                const int base = bk * NB;
+                for (int idx = tid; idx < NB * NB; idx += kWThreads) {
+                    const int i = idx / NB, i2 = idx - i * NB;
+                    if (i2 / n < i / n) {
+                        const int a = wxy[base + i], c = wxy[base + i2];
+                        wpair[idx] = wq_get(wq, L, (a & 0xFFFF) - (c & 0xFFFF), ((a >> 16) & 0x7FFF) - ((c >> 16) & 0x7FFF));
+                    }
+                }
+            }
+            if (nprev > 0) {
+                // catch-up: the moves of block b-1 into the sites of block b
+                const int site = tid / tps, g = tid - site * tps, s = bk * NB + site;
+                const int xy = wxy[s];
+                const int qx = xy & 0xFFFF, qy = (xy >> 16) & 0x7FFF;
+                float3 cr = make_float3(0.f, 0.f, 0.f);
+                for (int m = g; m < nprev; m += tps) {
+                    const float4 mv = s_mvb[prv * NB + m];
+                    const int pxy = __float_as_int(mv.w);
+                    const float3 c = wq_apply(wq, L, qx - (pxy & 0xFFFF), qy - ((pxy >> 16) & 0x7FFF),
+                                              make_float3(mv.x, mv.y, mv.z));
+                    cr.x += c.x;
+                    cr.y += c.y;
+                    cr.z += c.z;
+                }
+                for (int off = 1; off < tps; off <<= 1) {
                     cr.x += __shfl_xor_sync(0xffffffffu, cr.x, off);
                     cr.y += __shfl_xor_sync(0xffffffffu, cr.y, off);
                     cr.z += __shfl_xor_sync(0xffffffffu, cr.z, off);
                 }
-                int accept = 0;
-                float dX = 0.f, dY = 0.f, dZ = 0.f;
-                if (dsub == 0) {
+                if (g == 0) {
                     float4 h = hcur[s];
                     h.x += cr.x;
                     h.y += cr.y;
                     h.z += cr.z;
-                    const int xp = (qx + 1 == L) ? q - qx : q + 1;
-                    const int xm = (qx == 0) ? q + L - 1 : q - 1;
-                    const int yp = (qy + 1 == L) ? qx : q + L;
-                    const int ym = (qy == 0) ? q + N - L : q - L;
-                    const float4 a = s4[xp], bb = s4[xm], c = s4[yp], dd = s4[ym];
-                    float4 S, D;
-                    float thr;
-                    if (pre_ok) {
-                        S = pS[s];
-                        D = pd[s];
-                        thr = S.w;
-                    } else {
+                    hcur[s] = h;
+                }
+            }
+            if (G > 1 || nprev > 0) __syncthreads();
+            if (warp == 0) {
+                int ncur = 0;                                    // moves of this block so far (warp-uniform)
+                for (int u = 0; u < G; ++u) {
+                    const int j = bk * G + u;
+                    const int s = j * n + dsite;
+                    const int xy = wxy[s];
+                    const int qx = xy & 0xFFFF, qy = (xy >> 16) & 0x7FFF, q = qy * L + qx;
+                    // pull: moves of this block's earlier sub-steps (pd holds the move of an
+                    // accepted site and zero for a rejected one), split over the site's lanes
+                    float3 cr = make_float3(0.f, 0.f, 0.f);
+                    const float4 *wrow = wpair + (u * n + dsite) * NB;
+                    const int base = bk * NB;
+                    for (int i2 = dsub; i2 < u * n; i2 += LPS) {
+                        const float4 w = wrow[i2], mv = pd[base + i2];
+                        cr.x += w.x * mv.x + w.y * mv.y;
+                        cr.y += w.y * mv.x + w.z * mv.y;
+                        cr.z += w.w * mv.z;
+                    }
+#pragma unroll
+                    for (int off = 1; off < LPS; off <<= 1) {
+                        cr.x += __shfl_xor_sync(0xffffffffu, cr.x, off);
+                        cr.y += __shfl_xor_sync(0xffffffffu, cr.y, off);
+                        cr.z += __shfl_xor_sync(0xffffffffu, cr.z, off);
+                    }
+                    int accept = 0;
+                    float dX = 0.f, dY = 0.f, dZ = 0.f;
+                    if (dsub == 0) {
+                        float4 h = hcur[s];
+                        h.x += cr.x;
+                        h.y += cr.y;
+                        h.z += cr.z;
+                        const float3 nb3 = nbr_sum(qx, qy);
                         const uint4 wds = attempt_rng(s, q);
                         float sps, cps;
                         sincospif(2.0f * u24f(wds.y), &sps, &cps);
                         const float uu = u24f(wds.z);
+                        float4 S, D;
                         propose(q, u24f(wds.x), cps, sps, S, D);
-                        thr = (uu > 0.0f) ? -P.T * logf(uu) : INFINITY;
+                        const float thr = (uu > 0.0f) ? -P.T * logf(uu) : INFINITY;
+                        dX = D.x;
+                        dY = D.y;
+                        dZ = D.z;
+                        const float dex = -P.J * (dX * nb3.x + dY * nb3.y + dZ * nb3.z);
+                        const float dE = D.w + dex + P.CD * (dX * h.x + dY * h.y + dZ * h.z);
+                        accept = dE < thr;
+                        if (buf.trace) {
+                            float *tr = trace_row(s);
+                            tr[0] = (float)q;
+                            tr[1] = h.x; tr[2] = h.y; tr[3] = h.z;
+                            tr[4] = dE;
+                            tr[5] = uu;
+                            tr[6] = (float)accept;
+                            tr[7] = S.x; tr[8] = S.y; tr[9] = S.z;
+                        }
+                        if (accept) {
+                            s4[q] = make_float4(S.x, S.y, S.z, 0.0f);
+                            wxy[s] = xy | (int)0x80000000;             // accepted
+                        }
+                        // the move (for the block's later sub-steps and the window-end bookkeeping)
+                        pd[s] = accept ? make_float4(dX, dY, dZ, dE) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        pS[s] = make_float4(S.x, S.y, S.z, dE);
                     }
-                    dX = D.x;
-                    dY = D.y;
-                    dZ = D.z;
-                    const float n0 = (a.x + bb.x) + (c.x + dd.x);
-                    const float n1 = (a.y + bb.y) + (c.y + dd.y);
-                    const float n2 = (a.z + bb.z) + (c.z + dd.z);
-                    const float dex = -P.J * (dX * n0 + dY * n1 + dZ * n2);
-                    const float dE = D.w + dex + P.CD * (dX * h.x + dY * h.y + dZ * h.z);
-                    accept = dE < thr;
-                    if (buf.trace) {
-                        const uint4 wds = attempt_rng(s, q);
-                        float *tr = buf.trace + ((((size_t)r * cfg.nsweeps_call + cfg.it) * ll + (k0 + j)) * n + dsite) *
-                                                    MC_TRACE_W;
-                        tr[0] = (float)q;
-                        tr[1] = h.x; tr[2] = h.y; tr[3] = h.z;
-                        tr[4] = dE;
-                        tr[5] = u24f(wds.z);
-                        tr[6] = (float)accept;
-                        tr[7] = S.x; tr[8] = S.y; tr[9] = S.z;
-                    }
+                    // append the accepted moves of this sub-step to the block's list, in site order
+                    const unsigned ball = __ballot_sync(0xffffffffu, accept);
                     if (accept) {
-                        s4[q] = make_float4(S.x, S.y, S.z, 0.0f);
-                        wxy[s] = xy | (int)0x80000000;             // accepted
+                        const unsigned below = ball & ((1u << lane) - 1u);
+                        s_mvb[cur * NB + ncur + __popc(below)] = make_float4(dX, dY, dZ, __int_as_float(xy));
                     }
-                    // the move (for the block's later sub-steps and the window-end bookkeeping)
-                    pd[s] = accept ? make_float4(dX, dY, dZ, dE) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    ncur += __popc(ball);
+                    __syncwarp();
                 }
-                // append the accepted moves of this sub-step to the block's list, in site order
-                const unsigned ball = __ballot_sync(0xffffffffu, accept);
-                if (accept) {
-                    const unsigned below = ball & ((1u << lane) - 1u);
-                    s_mvb[cur * GN + ncur + __popc(below)] = make_float4(dX, dY, dZ, __int_as_float(xy));
+                if (lane == 0) {
+                    s_nmv[cur] = ncur;
+                    n_acc += ncur;
                 }
-                ncur += __popc(ball);
-                __syncwarp();
-            }
-            if (lane == 0) {
-                s_nmv[cur] = ncur;
-                n_acc += ncur;
-            }
-        } else if (nprev > 0) {
-            // helpers: push the moves of block b-1 into the sites of blocks >= b+1
-            constexpr int kH = kWThreads - 32;
-            for (int s = (bk + 1) * G * n + (tid - 32); s < Sw; s += kH) {
-                const int xy = wxy[s];
-                const int qx = xy & 0xFFFF, qy = (xy >> 16) & 0x7FFF;
-                float4 h = hcur[s];
-                for (int m = 0; m < nprev; ++m) {
-                    const float4 mv = s_mvb[prv * GN + m];
-                    const int pxy = __float_as_int(mv.w);
-                    const float3 c = wq_apply(wq, L, qx - (pxy & 0xFFFF), qy - ((pxy >> 16) & 0x7FFF),
-                                              make_float3(mv.x, mv.y, mv.z));
-                    h.x += c.x;
-                    h.y += c.y;
-                    h.z += c.z;
+            } else if (nprev > 0) {
+                // helpers: push the moves of block b-1 into the sites of blocks >= b+1
+                constexpr int kH = kWThreads - 32;
+                for (int s = (bk + 1) * NB + (tid - 32); s < Sw; s += kH) {
+                    const int xy = wxy[s];
+                    const int qx = xy & 0xFFFF, qy = (xy >> 16) & 0x7FFF;
+                    float4 h = hcur[s];
+                    for (int m = 0; m < nprev; ++m) {
+                        const float4 mv = s_mvb[prv * NB + m];
+                        const int pxy = __float_as_int(mv.w);
+                        const float3 c = wq_apply(wq, L, qx - (pxy & 0xFFFF), qy - ((pxy >> 16) & 0x7FFF),
+                                                  make_float3(mv.x, mv.y, mv.z));
+                        h.x += c.x;
+                        h.y += c.y;
+                        h.z += c.z;
+                    }
+                    hcur[s] = h;
                 }
-                hcur[s] = h;
             }
+            __syncthreads();
         }
-        __syncthreads();
     }
 
     // ---- write the accepted moves back to global memory (FP32 and the bf16 split)
@@ -440,7 +593,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
             const int xy = wxy[s];
             if (xy >= 0) continue;
             const float4 m = pd[s];
-            sub += m.w;
+            sub += pS[s].w;
             for (int dp = 0; dp < d; ++dp) {
                 const int pxy = wxy[j * n + dp];
                 if (pxy >= 0) continue;
@@ -535,8 +688,9 @@ __global__ void k_spins_to_bf16(size_t count, const float *__restrict__ s, __nv_
 
 size_t window_smem_bytes(int L, int Sw, int n) {
     const size_t N = (size_t)L * L, hq = (size_t)(L / 2 + 1);
-    const size_t GN = n >= kBlockSites ? n : kBlockSites;
-    return sizeof(float4) * (N + 3 * (size_t)Sw + hq * hq + 2 * GN + GN * GN) + sizeof(int) * (size_t)Sw;
+    (void)n;   // blocks of kBlockSites sites (n <= kBlockSites)
+    return sizeof(float4) * (N + 3 * (size_t)Sw + hq * hq + 2 * kBlockSites + kBlockSites * kBlockSites) +
+           sizeof(int) * (size_t)Sw;
 }
 
 bool window_supported(int L, int l, int B) {
@@ -544,10 +698,9 @@ bool window_supported(int L, int l, int B) {
     const int C = L / l;
     if (C != 1 && C != 2 && C != 4) return false;
     if (B < 1 || (l * l) % B) return false;
-    // decider blocks of at least 8 sites (the catch-up reduces within a warp)
-    const int n = C * C, GN = n >= kBlockSites ? n : kBlockSites;
-    const int G = B % (GN / n) == 0 ? GN / n : 1;
-    if (G * n < 8) return false;
+    // decider blocks of 16 sites: whole sub-steps
+    const int n = C * C;
+    if (B % (kBlockSites / n)) return false;
     return window_smem_bytes(L, B * C * C, C * C) <= 200 * 1024;
 }
 
@@ -555,15 +708,18 @@ cudaError_t launch_window_steps(const WindowConfig &c, const WindowBuffers &b, c
     const int C = c.L / c.l;
     const size_t smem = window_smem_bytes(c.L, c.B * C * C, C * C);
     cudaError_t e;
-#define LAUNCH(CC)                                                                                   \
-    e = cudaFuncSetAttribute(k_window_steps<CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+#define LAUNCH1(CC, PRE)                                                                             \
+    e = cudaFuncSetAttribute(k_window_steps<CC, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
     if (e != cudaSuccess) return e;                                                                  \
-    k_window_steps<CC><<<c.R, kWThreads, smem, st>>>(c, b);
+    k_window_steps<CC, PRE><<<c.R, kWThreads, smem, st>>>(c, b);
+#define LAUNCH(CC)                                                                                   \
+    if (c.schedule == 0) { LAUNCH1(CC, true) } else { LAUNCH1(CC, false) }
     if (C == 1) { LAUNCH(1) }
     else if (C == 2) { LAUNCH(2) }
     else if (C == 4) { LAUNCH(4) }
     else return cudaErrorNotSupported;
 #undef LAUNCH
+#undef LAUNCH1
     return cudaGetLastError();
 }
 
