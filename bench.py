@@ -106,15 +106,15 @@ class ClockSampler:
 
 def window_sites(B_set=0):
     """Sites per window: B_set sub-steps if given, else the library's default for
-    L = 64, l = 32 (n = 4): the largest power of two B dividing l^2 with 4B <= 512
-    and 4B a multiple of 128."""
+    the tensor path at L = 64, l = 32 (n = 4): the largest power of two B dividing
+    l^2 with 4B <= 256 and 4B a multiple of 128."""
     n = (L // l) ** 2
     if B_set:
         return B_set * n
     best = 0
     B = 1
     while B <= l * l:
-        if (l * l) % B == 0 and B * n <= 512 and (B * n) % 128 == 0:
+        if (l * l) % B == 0 and B * n <= 256 and (B * n) % 128 == 0:
             best = B
         B *= 2
     return best * n
@@ -519,10 +519,10 @@ def main():
             pass
     # kernels of ours launched per timed step: direct = 1 sweep kernel; tensor = the
     # sweep counter, one bf16 split of the spins + per window (sites, tensor-core
-    # field, split-K reduction, sub-steps); FP32 window = counter + per window
+    # field, sub-steps with the split-K sum); FP32 window = counter + per window
     # (full field, sub-steps)
     nwin = (l * l * (L // l) ** 2) // Sw if Sw else 0
-    per_step = {"direct": 1, "tensor": 2 + 4 * nwin * S, "window": 1 + 2 * nwin * S}[args.path]
+    per_step = {"direct": 1, "tensor": 2 + 3 * nwin * S, "window": 1 + 2 * nwin * S}[args.path]
     gpu_launches = per_step * args.steps
 
     # end to end through the public API: host spins in (pinned), S sweeps,

@@ -244,7 +244,7 @@ int mc_energy(mc_lattice *lat, double *dst_host, void *stream);
 #define MC_K_FULL_FIELD 3    /* FP32 full field (energy anchor, windowed FP32 path) */
 #define MC_K_SPEC_FIELD 4    /* spectral path: field spectra at the sub-step's sites */
 #define MC_K_SPEC_UPDATE 5   /* spectral path: inverse DFT, update, DFT of the updated sub-lattice */
-#define MC_K_TC_REDUCE 6     /* tensor path: fixed-order sum of the split-K partial tiles */
+#define MC_K_TC_REDUCE 6     /* retired: the split-K sum now runs inside the sub-step kernel (no launches) */
 #define MC_NKCLASS 7
 typedef struct mc_timing {
     int64_t launches[MC_NKCLASS];

@@ -79,7 +79,6 @@ struct mc_lattice {
     // windowed / tensor-core paths
     int window_B = 0;
     __nv_bfloat16 *spins_hi = nullptr, *spins_lo = nullptr, *wsh = nullptr;
-    float *H0 = nullptr;
     int *wsite = nullptr;
     TcUnit *units = nullptr;
     int nunits = 0, NT = 0, tmem_cols = 0, plan_Sw = 0;
@@ -141,7 +140,6 @@ void free_all(mc_lattice *p) {
     cudaFree(p->spins_hi);
     cudaFree(p->spins_lo);
     cudaFree(p->wsh);
-    cudaFree(p->H0);
     cudaFree(p->wsite);
     cudaFree(p->units);
     cudaFree(p->tcpart);
@@ -206,14 +204,16 @@ void clear_timing(mc_lattice *p) {
 }
 
 // Sub-steps per window: the given B, else the largest power of two dividing l^2
-// with B*n <= 512 and (for the tensor path) B*n a multiple of 128.
+// with B*n <= 512 (tensor path: <= 256, and a multiple of 128).  The in-window
+// pushes grow with B*n per site while the per-window costs shrink; at L = 64,
+// l = 32 the tensor path is fastest with 256-site windows.
 int window_of(const mc_lattice *p, bool tensor) {
     const int ll = p->l * p->l, n = p->n();
     if (p->window_B > 0) return p->window_B;
     int best = 0;
     for (int B = 1; B <= ll; B <<= 1) {
         if (ll % B) continue;
-        if (B * n > 512) break;
+        if (B * n > (tensor ? 256 : 512)) break;
         if (tensor && (B * n) % 128) continue;
         best = B;
     }
@@ -322,13 +322,11 @@ int ensure_tensor_buffers(mc_lattice *p, int Sw, cudaStream_t st) {
         p->wsh_ready = true;
     }
     if (p->plan_Sw != Sw) {
-        cudaFree(p->H0);
         cudaFree(p->wsite);
         cudaFree(p->units);
         cudaFree(p->tcpart);
         cudaFree(p->tile_first);
-        p->H0 = nullptr; p->wsite = nullptr; p->units = nullptr; p->tcpart = nullptr; p->tile_first = nullptr;
-        CKA(cudaMalloc(&p->H0, sizeof(float) * R * 3 * Sw));
+        p->wsite = nullptr; p->units = nullptr; p->tcpart = nullptr; p->tile_first = nullptr;
         CKA(cudaMalloc(&p->wsite, sizeof(int) * Sw));
         int dev = 0, nsm = 148;
         cudaGetDevice(&dev);
@@ -373,22 +371,25 @@ int run_windows(mc_lattice *p, int path, int nsweeps, int measure_every, float *
     c.proposal = p->proposal;
     c.cap_c1 = (float)(1.0 - std::cos(p->cone));
     c.schedule = p->schedule;
-    c.stale_mode = tensor ? 1 : 0;
-    c.ldh = 3 * Sw;
+    c.stale_mode = tensor ? 2 : 0;   // tensor path: the sub-step kernel sums the split-K partial tiles
+    c.NT = p->NT;
+    c.mtiles = p->mtiles;
     WindowBuffers b{};
     b.W32 = p->W32; b.spins = p->spins;
     b.spins_hi = tensor ? p->spins_hi : nullptr;
     b.spins_lo = tensor ? p->spins_lo : nullptr;
     b.params = p->dparams; b.energy = p->energy; b.obs = p->obs; b.theta2 = p->theta2;
     b.trace = trace;
-    b.stale = tensor ? p->H0 : p->field;
+    b.stale = tensor ? nullptr : p->field;
+    b.part = tensor ? p->tcpart : nullptr;
+    b.tile_first = tensor ? p->tile_first : nullptr;
     b.wq = p->wq;
     b.hist = hist_of(p);
     TcFieldArgs ta{};
     if (tensor) {
-        ta.L = p->L; ta.Sw = Sw; ta.R = p->R; ta.NT = p->NT; ta.ldh = 3 * Sw; ta.tmem_cols = p->tmem_cols;
+        ta.L = p->L; ta.Sw = Sw; ta.R = p->R; ta.NT = p->NT; ta.tmem_cols = p->tmem_cols;
         ta.units = p->units; ta.wsite = p->wsite; ta.wsh = p->wsh;
-        ta.spins_hi = p->spins_hi; ta.spins_lo = p->spins_lo; ta.H0 = p->H0; ta.error = p->err_flag;
+        ta.spins_hi = p->spins_hi; ta.spins_lo = p->spins_lo; ta.error = p->err_flag;
         ta.part = p->tcpart; ta.tile_first = p->tile_first; ta.mtiles = p->mtiles; ta.ntiles = p->ntiles;
     }
     for (int it = 0; it < nsweeps; ++it) {
@@ -404,11 +405,6 @@ int run_windows(mc_lattice *p, int path, int nsweeps, int measure_every, float *
                     e = launch_tc_field(ta, p->nunits, p->tm_hi, p->tm_lo, st);
                 }
                 if (e != cudaSuccess) return cuda_fail(e, "tensor-core field launch");
-                {
-                    TimedLaunch tl(p, MC_K_TC_REDUCE, st);
-                    e = launch_tc_reduce(ta, st);
-                }
-                if (e != cudaSuccess) return cuda_fail(e, "split-K reduction launch");
             } else {
                 TimedLaunch tl(p, MC_K_FULL_FIELD, st);
                 e = launch_full_field(p->L, p->R, p->W32, p->spins, p->field, st);

@@ -25,8 +25,9 @@
 // the stage's full barrier.  Thread 0 issues
 // tcgen05.mma (M=128, N=tile, K=16) into a TMEM accumulator and commits each
 // stage to its mbarrier.  The epilogue reads TMEM with tcgen05.ld and stores the
-// unit's partial tile (split-K); k_tc_reduce sums the partial tiles of each
-// output tile in a fixed order into H0 (deterministic, no atomics).
+// unit's partial tile (split-K); the sub-step kernel sums the partial tiles of
+// each output tile in a fixed order as it loads the window (deterministic, no
+// atomics).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -312,21 +313,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a,
     }
 }
 
-// H0 of output tile (mt, nt): the sum of its units' partial tiles, in unit order.
-// Thread = (column, row) with row fastest: partial reads and H0 writes coalesce.
-__global__ void __launch_bounds__(256) k_tc_reduce(const TcFieldArgs a) {
-    const int mt = blockIdx.x, nt = blockIdx.y;
-    const int idx = blockIdx.z * 256 + threadIdx.x;
-    const int col = idx >> 7, row = idx & 127;
-    if (col >= a.NT) return;
-    const int r = nt * a.NT + col;
-    if (r >= a.R) return;
-    const int u0 = a.tile_first[nt * a.mtiles + mt], u1 = a.tile_first[nt * a.mtiles + mt + 1];
-    float s = 0.f;
-    for (int u = u0; u < u1; ++u) s += a.part[((size_t)u * a.NT + col) * 128 + row];
-    a.H0[(size_t)r * a.ldh + mt * 128 + row] = s;
-}
-
 // 8 shifted, doubled bf16 hi/lo copies of W~: wsh[c][comp][hl][y][i] = part_hl(W~_comp(y, (i + c) mod L)),
 // i in [0, 2L).  Any 8 consecutive columns starting at x0 are then the aligned
 // 16 bytes at i = x0 - (x0 mod 8) of copy c = x0 mod 8.
@@ -438,11 +424,6 @@ int tc_plan(int L, int Sw, int R, int nsm, TcUnit *units, int max_units, int *NT
     while (cols < NT) cols <<= 1;
     *tmem_cols = cols;
     return nu;
-}
-
-cudaError_t launch_tc_reduce(const TcFieldArgs &a, cudaStream_t st) {
-    k_tc_reduce<<<dim3(a.mtiles, a.ntiles, (a.NT * 128 + 255) / 256), 256, 0, st>>>(a);
-    return cudaGetLastError();
 }
 
 // 2D tensor map of a [R][3N] bf16 spin array: boxes of 8 elements x NT rows.  The

@@ -14,13 +14,12 @@ struct TcUnit {
 };
 
 struct TcFieldArgs {
-    int L, Sw, R, NT, ldh, tmem_cols;
+    int L, Sw, R, NT, tmem_cols;
     const TcUnit *units;                 // [nunits]
     const int *wsite;                    // [Sw] window sites
     const __nv_bfloat16 *wsh;            // tc_wsh_elems(L): shifted hi/lo copies of W~
     const __nv_bfloat16 *spins_hi;       // [R][3][N]
     const __nv_bfloat16 *spins_lo;       // [R][3][N]
-    float *H0;                           // [R][ldh], written by the reduction
     int *error;                          // set to 1 if a bounded wait gave up
     float *part;                         // [nunits][NT][128]: each unit's partial tile, row fastest
     const int *tile_first;               // [ntiles * mtiles + 1]: first unit of tile (nt, mt)
@@ -43,7 +42,5 @@ int tc_plan(int L, int Sw, int R, int nsm, TcUnit *units, int max_units, int *NT
 size_t tc_map_bytes();
 int tc_encode_map(void *map, const __nv_bfloat16 *spins, int L, int R, int NT);
 cudaError_t launch_tc_field(const TcFieldArgs &a, int nunits, const void *map_hi, const void *map_lo, cudaStream_t st);
-// H0 = sum over each tile's units of their partial tiles, in unit order.
-cudaError_t launch_tc_reduce(const TcFieldArgs &a, cudaStream_t st);
 
 }  // namespace dipmc

@@ -232,8 +232,35 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
             const float *f = buf.stale + (size_t)r * 3 * N;
             return make_float3(f[q], f[N + q], f[2 * N + q]);
         }
-        const float *hr = buf.stale + (size_t)r * cfg.ldh;
-        return make_float3(hr[0 * Sw + s], hr[1 * Sw + s], hr[2 * Sw + s]);
+        // stale_mode 2: row b*Sw + s of this replica's column is the sum of the split-K
+        // partial tiles of its output tile, in unit order (the tensor-core field's reduction)
+        const int nt = r / cfg.NT, col = r - nt * cfg.NT;
+        const float *pc[3];
+        int cnt[3];
+        float h[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb) {
+            const int row = bb * Sw + s, mt = row >> 7, rr = row & 127;
+            const int u0 = buf.tile_first[nt * cfg.mtiles + mt], u1 = buf.tile_first[nt * cfg.mtiles + mt + 1];
+            pc[bb] = buf.part + ((size_t)u0 * cfg.NT + col) * 128 + rr;
+            cnt[bb] = u1 - u0;
+        }
+        const size_t ustride = (size_t)cfg.NT * 128;
+        const int cmax = max(cnt[0], max(cnt[1], cnt[2]));
+        // four partial tiles of each row in flight; summed in unit order
+        for (int j0 = 0; j0 < cmax; j0 += 4) {
+            float v[3][4];
+#pragma unroll
+            for (int bb = 0; bb < 3; ++bb)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) v[bb][j] = (j0 + j < cnt[bb]) ? __ldcg(pc[bb] + (size_t)(j0 + j) * ustride) : 0.f;
+#pragma unroll
+            for (int bb = 0; bb < 3; ++bb)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (j0 + j < cnt[bb]) h[bb] += v[bb][j];
+        }
+        return make_float3(h[0], h[1], h[2]);
     };
 
     // ---- window set-up: state, tensor table, sites, stale field, proposals

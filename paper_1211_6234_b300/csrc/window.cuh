@@ -20,8 +20,9 @@ struct WindowConfig {
     float cap_c1;        // 1 - cos(cone)
     int schedule;        // 0 permutation, 1 draw
     int measure;         // sample observables after this window (last window of a measured sweep)
-    int stale_mode;      // 0: stale = full field [R][3][N]; 1: stale = H0 [R][ldh], row b*Sw + s
-    int ldh;             // per-replica stride of H0 (>= 3*Sw)
+    int stale_mode;      // 0: stale = full field [R][3][N]; 2: the split-K partial tiles of the
+                         // tensor-core field (part, tile_first), rows b*Sw + s
+    int NT, mtiles;      // stale_mode 2: replicas per N-tile, M-tiles of 128 rows
 };
 
 struct WindowBuffers {
@@ -35,6 +36,8 @@ struct WindowBuffers {
     double *theta2;               // [R][N]
     float *trace;                 // optional
     const float *stale;           // see stale_mode
+    const float *part;            // stale_mode 2: [units][NT][128] partial tiles, row fastest
+    const int *tile_first;        // stale_mode 2: [ntiles * mtiles + 1] first unit of tile (nt, mt)
     const float4 *wq;             // [(L/2+1)^2] W~ on the minimum-image quarter, (xx, xy, yy, zz)
     EnergyHist hist;              // optional energy histogram
 };

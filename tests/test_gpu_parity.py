@@ -294,7 +294,8 @@ WCASES = [
     (16, 16, 1, 0, 0, 1),      # l = L: one site per sub-step, S_w = 256
     (48, 24, 1, 0, 0, 1),      # non-power-of-two L
     (32, 16, 2, 0, 1, 1),      # the paper's with-replacement schedule
-    (64, 32, 2, 0, 0, 1),      # L = 64, S_w = 512
+    (64, 32, 2, 0, 0, 1),      # L = 64, S_w = 512 (F32) / 256 (tensor)
+    (64, 32, 2, 128, 0, 1),    # L = 64, S_w = 512 on both paths
 ]
 
 
