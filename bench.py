@@ -518,11 +518,11 @@ def main():
         except Exception:
             pass
     # kernels of ours launched per timed step: direct = 1 sweep kernel; tensor = the
-    # sweep counter, one bf16 split of the spins + per window (sites, tensor-core
-    # field, sub-steps with the split-K sum); FP32 window = counter + per window
-    # (full field, sub-steps)
+    # sweep counter, one bf16 split of the spins + per window (tensor-core field with
+    # the window's sites, sub-steps with the split-K sum); FP32 window = counter +
+    # per window (full field, sub-steps)
     nwin = (l * l * (L // l) ** 2) // Sw if Sw else 0
-    per_step = {"direct": 1, "tensor": 2 + 3 * nwin * S, "window": 1 + 2 * nwin * S}[args.path]
+    per_step = {"direct": 1, "tensor": 2 + 2 * nwin * S, "window": 1 + 2 * nwin * S}[args.path]
     gpu_launches = per_step * args.steps
 
     # end to end through the public API: host spins in (pinned), S sweeps,

@@ -79,7 +79,6 @@ struct mc_lattice {
     // windowed / tensor-core paths
     int window_B = 0;
     __nv_bfloat16 *spins_hi = nullptr, *spins_lo = nullptr, *wsh = nullptr;
-    int *wsite = nullptr;
     TcUnit *units = nullptr;
     int nunits = 0, NT = 0, tmem_cols = 0, plan_Sw = 0;
     float *tcpart = nullptr;      // [nunits][NT][128] partial tiles of the split-K contraction
@@ -140,7 +139,6 @@ void free_all(mc_lattice *p) {
     cudaFree(p->spins_hi);
     cudaFree(p->spins_lo);
     cudaFree(p->wsh);
-    cudaFree(p->wsite);
     cudaFree(p->units);
     cudaFree(p->tcpart);
     cudaFree(p->tile_first);
@@ -322,12 +320,10 @@ int ensure_tensor_buffers(mc_lattice *p, int Sw, cudaStream_t st) {
         p->wsh_ready = true;
     }
     if (p->plan_Sw != Sw) {
-        cudaFree(p->wsite);
         cudaFree(p->units);
         cudaFree(p->tcpart);
         cudaFree(p->tile_first);
-        p->wsite = nullptr; p->units = nullptr; p->tcpart = nullptr; p->tile_first = nullptr;
-        CKA(cudaMalloc(&p->wsite, sizeof(int) * Sw));
+        p->units = nullptr; p->tcpart = nullptr; p->tile_first = nullptr;
         int dev = 0, nsm = 148;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -388,7 +384,8 @@ int run_windows(mc_lattice *p, int path, int nsweeps, int measure_every, float *
     TcFieldArgs ta{};
     if (tensor) {
         ta.L = p->L; ta.Sw = Sw; ta.R = p->R; ta.NT = p->NT; ta.tmem_cols = p->tmem_cols;
-        ta.units = p->units; ta.wsite = p->wsite; ta.wsh = p->wsh;
+        ta.units = p->units; ta.wsh = p->wsh;
+        ta.l = p->l; ta.schedule = p->schedule; ta.key = c.key; ta.t_dev = p->t_dev;
         ta.spins_hi = p->spins_hi; ta.spins_lo = p->spins_lo; ta.error = p->err_flag;
         ta.part = p->tcpart; ta.tile_first = p->tile_first; ta.mtiles = p->mtiles; ta.ntiles = p->ntiles;
     }
@@ -398,8 +395,9 @@ int run_windows(mc_lattice *p, int path, int nsweeps, int measure_every, float *
         for (int w = 0; w < nwin; ++w) {
             cudaError_t e;
             if (tensor) {
-                e = launch_window_sites(p->L, p->l, c.key, c.t, p->t_dev, it, p->schedule, w * B, B, p->wsite, st);
-                if (e != cudaSuccess) return cuda_fail(e, "window sites");
+                ta.t_host = c.t;
+                ta.it = it;
+                ta.k0 = w * B;
                 {
                     TimedLaunch tl(p, MC_K_TC_FIELD, st);
                     e = launch_tc_field(ta, p->nunits, p->tm_hi, p->tm_lo, st);

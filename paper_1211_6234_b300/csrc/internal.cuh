@@ -72,6 +72,33 @@ __host__ __device__ __forceinline__ int ceil_log2_u(uint32_t v) {
     return b;
 }
 
+// Lattice site visited by slot s of a window that starts at sub-step k0 of sweep t:
+// sub-step k0 + s / n, cell s % n of the C x C grid of its offset (Sec. 3.1 update
+// sites), as x | y << 16.  rk = philox({t, 0, 0, kTagPerm}, key) under the
+// permutation schedule (schedule 0); the draw schedule draws the offset per sub-step.
+__device__ __forceinline__ int window_site_xy(int l, int C, uint2 key, uint32_t t, int schedule, uint4 rk, int k0,
+                                              int s) {
+    const int n = C * C, j = s / n, d = s - j * n, k = k0 + j;
+    const uint32_t ll = (uint32_t)(l * l);
+    uint32_t v;
+    if (schedule == 0) {
+        v = perm_offset(rk, ceil_log2_u((uint32_t)l), ll, (uint32_t)k);
+    } else {
+        const uint4 o = philox(make_uint4(t, (uint32_t)k, 0u, kTagDraw), key);
+        v = (uint32_t)(((unsigned long long)o.x * (unsigned long long)ll) >> 32);
+    }
+    const int qx = (int)(v % (uint32_t)l) + l * (d % C), qy = (int)(v / (uint32_t)l) + l * (d / C);
+    return qx | (qy << 16);
+}
+
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while the previous kernel of its stream drains; it
+// must wait for that kernel (and, transitively, everything before it) before
+// touching memory the stream's earlier kernels write.  Without the launch
+// attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Per-replica couplings as the kernels read them.
 struct RepParams {
     float J, CD, K2, K4, T;

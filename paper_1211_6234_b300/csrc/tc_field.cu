@@ -167,6 +167,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a,
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     // ---- this CTA's unit: M-tile, N-tile, K-block range
+    pdl_trigger();
     const TcUnit u = a.units[blockIdx.x];
     const int L = a.L, N = L * L, Sw = a.Sw;
     const int row0 = u.mtile * 128;                 // first row (b*Sw + s) of the tile
@@ -180,8 +181,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a,
     const int arow = tid & 127, ahalf = tid >> 7;
     const int my_row = row0 + arow;
     const int my_b = my_row / Sw;                         // output component 0 x, 1 y, 2 z
-    const int my_q = a.wsite[my_row - my_b * Sw];
-    const int my_qy = my_q / L, my_qx = my_q - my_qy * L;
+    int my_qx, my_qy;
+    {
+        // the row's window site (depends on the sweep counter only)
+        const uint32_t t = a.t_dev ? *a.t_dev + (uint32_t)a.it : a.t_host;
+        const uint4 rk = a.schedule == 0 ? philox(make_uint4(t, 0u, 0u, kTagPerm), a.key) : make_uint4(0, 0, 0, 0);
+        const int xy = window_site_xy(a.l, L / a.l, a.key, t, a.schedule, rk, a.k0, my_row - my_b * Sw);
+        my_qx = xy & 0xFFFF;
+        my_qy = xy >> 16;
+    }
     const int comp_a0 = my_b == 0 ? 0 : 1;                // (b, a = x): xx or xy
     const int comp_a1 = my_b == 0 ? 1 : 2;                // (b, a = y): xy or yy
     if (warp == 0) {
@@ -203,6 +211,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a,
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base_s;
     bool ok = true;
+    // everything above overlaps the previous kernel's tail; the spins (B) and the
+    // partial tiles (read by the previous window's sub-step kernel) wait for it
+    pdl_wait();
 
     const int nkb = u.kb_end - u.kb_begin;
     // stage the operands of K-block i into ring slot i % kStages
@@ -337,25 +348,6 @@ __global__ void k_build_wsh(int L, const double *__restrict__ W64, __nv_bfloat16
 }
 
 // Window sites of sweep t, window w (same schedule as the sweep kernels).
-__global__ void k_window_sites(int L, int l, uint2 key, uint32_t t_host, const uint32_t *t_dev, int it, int schedule,
-                               int k0, int B, int *wsite) {
-    const uint32_t t = t_dev ? *t_dev + (uint32_t)it : t_host;
-    const int n = (L / l) * (L / l), C = L / l, ll = l * l;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= B * n) return;
-    const int j = s / n, d = s % n, k = k0 + j;
-    uint32_t v;
-    if (schedule == 0) {
-        const uint4 rk = philox(make_uint4(t, 0u, 0u, kTagPerm), key);
-        v = perm_offset(rk, ceil_log2_u((uint32_t)l), (uint32_t)ll, (uint32_t)k);
-    } else {
-        const uint4 o = philox(make_uint4(t, (uint32_t)k, 0u, kTagDraw), key);
-        v = (uint32_t)(((unsigned long long)o.x * (unsigned long long)ll) >> 32);
-    }
-    const int qx = (int)(v % l) + l * (d % C), qy = (int)(v / l) + l * (d / C);
-    wsite[s] = qy * L + qx;
-}
-
 }  // namespace
 
 size_t tc_wsh_elems(int L) { return (size_t)8 * 4 * 2 * L * 2 * L; }
@@ -372,13 +364,6 @@ size_t tc_smem_bytes() { return (size_t)kStages * kStage; }
 cudaError_t launch_build_wsh(int L, const double *W64, __nv_bfloat16 *wsh, cudaStream_t st) {
     const size_t total = (size_t)8 * 4 * L * 2 * L;
     k_build_wsh<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(L, W64, wsh);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_window_sites(int L, int l, uint2 key, uint32_t t, const uint32_t *t_dev, int it, int schedule,
-                                int k0, int B, int *wsite, cudaStream_t st) {
-    const int Sw = B * (L / l) * (L / l);
-    k_window_sites<<<(Sw + 127) / 128, 128, 0, st>>>(L, l, key, t, t_dev, it, schedule, k0, B, wsite);
     return cudaGetLastError();
 }
 
@@ -456,9 +441,18 @@ cudaError_t launch_tc_field(const TcFieldArgs &a, int nunits, const void *map_hi
     const size_t smem = tc_smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(k_tc_field, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_tc_field<<<nunits, kTcThreads, smem, st>>>(a, *static_cast<const CUtensorMap *>(map_hi),
-                                                  *static_cast<const CUtensorMap *>(map_lo));
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(nunits);
+    cfg.blockDim = dim3(kTcThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_tc_field, a, *static_cast<const CUtensorMap *>(map_hi),
+                              *static_cast<const CUtensorMap *>(map_lo));
 }
 
 }  // namespace dipmc

@@ -16,7 +16,12 @@ struct TcUnit {
 struct TcFieldArgs {
     int L, Sw, R, NT, tmem_cols;
     const TcUnit *units;                 // [nunits]
-    const int *wsite;                    // [Sw] window sites
+    // the window's sites (computed in the kernel): sub-steps k0 .. k0 + Sw/n - 1 of sweep
+    // t (t_dev[0] + it when t_dev is set, else t_host) under the given schedule
+    int l, schedule, it, k0;
+    uint2 key;
+    uint32_t t_host;
+    const uint32_t *t_dev;
     const __nv_bfloat16 *wsh;            // tc_wsh_elems(L): shifted hi/lo copies of W~
     const __nv_bfloat16 *spins_hi;       // [R][3][N]
     const __nv_bfloat16 *spins_lo;       // [R][3][N]
@@ -30,8 +35,6 @@ size_t tc_wsh_elems(int L);
 bool tc_supported(int L, int l, int B);
 size_t tc_smem_bytes();
 cudaError_t launch_build_wsh(int L, const double *W64, __nv_bfloat16 *wsh, cudaStream_t st);
-cudaError_t launch_window_sites(int L, int l, uint2 key, uint32_t t, const uint32_t *t_dev, int it, int schedule,
-                                int k0, int B, int *wsite, cudaStream_t st);
 // Fills units[] for a window of Sw sites and R replicas; returns the number of
 // units (CTAs) or -1 if max_units is too small.
 // Work plan: units ordered by (N-tile, M-tile, K range); tile_first (host,

@@ -195,19 +195,6 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
         D = make_float4(dX, dY, dZ, dan + 0.5f * P.CD * self);
     };
     const uint4 rk = PRE ? philox(make_uint4(t, 0u, 0u, kTagPerm), key) : make_uint4(0, 0, 0, 0);
-    const int hbits = ceil_log2_u((uint32_t)l);
-    auto site_of = [&](int s) -> int {
-        const int j = s / n, d = s % n, k = k0 + j;
-        uint32_t v;
-        if (PRE) {
-            v = perm_offset(rk, hbits, (uint32_t)ll, (uint32_t)k);
-        } else {
-            const uint4 o = philox(make_uint4(t, (uint32_t)k, 0u, kTagDraw), key);
-            v = (uint32_t)(((unsigned long long)o.x * (unsigned long long)ll) >> 32);
-        }
-        const int qx = (int)(v % l) + l * (d % C), qy = (int)(v / l) + l * (d / C);
-        return qx | (qy << 16);
-    };
     auto attempt_rng = [&](int s, int q) -> uint4 {
         const int k = k0 + s / n;
         return philox(make_uint4((uint32_t)q, (uint32_t)r, t, ((uint32_t)k & 0x00FFFFFFu) | kTagAttempt), key);
@@ -263,17 +250,21 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
         return make_float3(h[0], h[1], h[2]);
     };
 
-    // ---- window set-up: state, tensor table, sites, stale field, proposals
+    // ---- window set-up.  Before the previous kernel of the stream has finished:
+    // the tensor table and the window's sites (they depend on the sweep counter
+    // only); then the state, stale field and proposals.
+    pdl_trigger();
+#pragma unroll 4
+    for (int i = tid; i < hq * hq; i += kWThreads) wq[i] = buf.wq[i];
+    for (int s = tid; s < Sw; s += kWThreads) wxy[s] = window_site_xy(l, C, key, t, cfg.schedule, rk, k0, s);
+    pdl_wait();
     const float *gs = buf.spins + (size_t)r * 3 * N;
 #pragma unroll 4
     for (int q = tid; q < N; q += kWThreads) s4[q] = make_float4(gs[q], gs[N + q], gs[2 * N + q], 0.0f);
-#pragma unroll 4
-    for (int i = tid; i < hq * hq; i += kWThreads) wq[i] = buf.wq[i];
     __syncthreads();
     for (int s = tid; s < Sw; s += kWThreads) {
-        const int xy = site_of(s);
+        const int xy = wxy[s];
         const int q = (xy >> 16) * L + (xy & 0xFFFF);
-        wxy[s] = xy;
         const float3 hs = stale_at(s, q);
         const float h0 = hs.x, h1 = hs.y, h2 = hs.z;
         if (PRE) {
@@ -738,7 +729,20 @@ cudaError_t launch_window_steps(const WindowConfig &c, const WindowBuffers &b, c
 #define LAUNCH1(CC, PRE)                                                                             \
     e = cudaFuncSetAttribute(k_window_steps<CC, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
     if (e != cudaSuccess) return e;                                                                  \
-    k_window_steps<CC, PRE><<<c.R, kWThreads, smem, st>>>(c, b);
+    {                                                                                                \
+        cudaLaunchConfig_t lc{};                                                                     \
+        lc.gridDim = dim3(c.R);                                                                      \
+        lc.blockDim = dim3(kWThreads);                                                               \
+        lc.dynamicSmemBytes = smem;                                                                  \
+        lc.stream = st;                                                                              \
+        cudaLaunchAttribute at[1];                                                                   \
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;                               \
+        at[0].val.programmaticStreamSerializationAllowed = 1;                                        \
+        lc.attrs = at;                                                                               \
+        lc.numAttrs = 1;                                                                             \
+        e = cudaLaunchKernelEx(&lc, k_window_steps<CC, PRE>, c, b);                                  \
+        if (e != cudaSuccess) return e;                                                              \
+    }
 #define LAUNCH(CC)                                                                                   \
     if (c.schedule == 0) { LAUNCH1(CC, true) } else { LAUNCH1(CC, false) }
     if (C == 1) { LAUNCH(1) }
