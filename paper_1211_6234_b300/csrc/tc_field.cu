@@ -17,14 +17,14 @@
 //
 // One CTA = one (M-tile of 128 rows, N-tile of up to 256 replicas, range of
 // K-blocks of 32).  Operands sit in the canonical K-major, no-swizzle
-// core-matrix layout (8 rows x 16 bytes per core matrix) in a ring of 4 stages,
-// loads running 2 stages ahead of the MMAs; a stage is refilled once the MMAs
-// that read it have committed.  The Toeplitz A tile is gathered by all threads
-// with cp.async; the spin tile B comes by TMA, one 2D box of 8 K-elements x NT
-// replicas per core-matrix column (rows past R arrive as zeros), completing on
-// the stage's full barrier.  Thread 0 issues
-// tcgen05.mma (M=128, N=tile, K=16) into a TMEM accumulator and commits each
-// stage to its mbarrier.  The epilogue reads TMEM with tcgen05.ld and stores the
+// core-matrix layout (8 rows x 16 bytes per core matrix) in a ring of 4 stages
+// handed between warp roles through mbarriers (no CTA-wide barrier in the K
+// loop): four producer warps gather the Toeplitz A tile with cp.async, one
+// thread per row; one thread loads the spin tile B by TMA, one 2D box of 8
+// K-elements x NT replicas per core-matrix column (rows past R arrive as
+// zeros); one thread issues tcgen05.mma (M=128, N=tile, K=16) into a TMEM
+// accumulator as soon as a stage's operands have landed and commits the stage
+// back to the producers.  The epilogue reads TMEM with tcgen05.ld and stores the
 // unit's partial tile (split-K); the sub-step kernel sums the partial tiles of
 // each output tile in a fixed order as it loads the window (deterministic, no
 // atomics).
@@ -48,7 +48,6 @@ constexpr int kMaxNT = 256;
 constexpr int kTileB = kMaxNT * kKB * 2;      // bytes of one B tile (hi or lo)
 constexpr int kStage = 2 * kTileA + 2 * kTileB;
 constexpr int kStages = 4;
-constexpr int kAhead = 2;                     // stages loaded ahead of the MMAs
 constexpr long long kWaitCycles = 4LL << 30;  // bounded mbarrier waits (~2 s at 2 GHz)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -123,10 +122,6 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
 
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-
-template <int N>
-__device__ __forceinline__ void cp_async_wait_pending() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
     asm volatile(
@@ -158,16 +153,54 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Arrive on m once every cp.async this thread has issued so far has landed (the
+// barrier's count includes these arrivals).
+__device__ __forceinline__ void cp_async_arrive(uint64_t *m) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(m)) : "memory");
+}
+
+// Bounded wait that gives up early once another role has given up; the first
+// role to time out raises the CTA's abort flag.
+__device__ __forceinline__ bool mbar_wait_abort(uint64_t *m, uint32_t parity, volatile int *abort) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(m, parity)) {
+        if (*abort) return false;
+        if (clock64() - t0 > kWaitCycles) {
+            *abort = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+// Warp roles of a CTA (one unit):
+//   warp 0, lane 0  issues the MMAs of each stage once its A rows and B tile have
+//                   landed, and commits the stage's slot back to the producers;
+//   warp 1, lane 0  loads the spin tile B of each stage by TMA;
+//   warps 4..7      gather the Toeplitz tile A, one thread per tile row; each
+//                   thread's arrival on the stage's barrier fires when its copies
+//                   have landed;
+//   all warps       read the accumulator out of TMEM at the end.
+// No CTA-wide barrier in the K loop: the ring of kStages slots is handed between
+// the roles through mbarriers.
+constexpr int kProdWarp0 = 4;
+constexpr int kProducers = kTcThreads - kProdWarp0 * 32;   // 128: one per tile row
+static_assert(kProducers == 128, "one producer per tile row");
+
 __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a, const __grid_constant__ CUtensorMap tm_hi,
                                                            const __grid_constant__ CUtensorMap tm_lo) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ uint64_t mbar[kStages];       // MMAs of a stage done (stage free)
-    __shared__ uint64_t fbar[kStages];       // TMA bytes of a stage arrived (stage full)
+    __shared__ uint64_t afull[kStages];      // the A rows of a stage landed (one arrival per producer)
+    __shared__ uint64_t bfull[kStages];      // the TMA bytes of a stage's B tile arrived
+    __shared__ uint64_t empty[kStages];      // the MMAs that read a stage completed (slot free)
+    __shared__ uint64_t done;                // every MMA of the unit completed
     __shared__ uint32_t tmem_base_s;
+    __shared__ int abort_s;
+    volatile int *abort = &abort_s;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    pdl_trigger();
 
     // ---- this CTA's unit: M-tile, N-tile, K-block range
-    pdl_trigger();
     const TcUnit u = a.units[blockIdx.x];
     const int L = a.L, N = L * L, Sw = a.Sw;
     const int row0 = u.mtile * 128;                 // first row (b*Sw + s) of the tile
@@ -175,23 +208,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a,
     const int n0 = u.ntile * a.NT;                  // first replica of the tile
     const int nrows_b = a.NT;                       // N of the MMA
     const uint32_t idesc = make_idesc(128, nrows_b);
+    const int nkb = u.kb_end - u.kb_begin;
 
-    // row (tid % 128) of the tile: site and tensor components (constant over the K
-    // loop); threads tid and tid + 128 gather the two halves of the row's K block
-    const int arow = tid & 127, ahalf = tid >> 7;
-    const int my_row = row0 + arow;
-    const int my_b = my_row / Sw;                         // output component 0 x, 1 y, 2 z
-    int my_qx, my_qy;
-    {
-        // the row's window site (depends on the sweep counter only)
+    // producer thread: its tile row's window site and tensor components
+    const bool producer = warp >= kProdWarp0;
+    const int arow = tid - kProdWarp0 * 32;
+    int my_b = 0, my_qx = 0, my_qy = 0;
+    if (producer) {
+        const int my_row = row0 + arow;
+        my_b = my_row / Sw;                          // output component 0 x, 1 y, 2 z
         const uint32_t t = a.t_dev ? *a.t_dev + (uint32_t)a.it : a.t_host;
         const uint4 rk = a.schedule == 0 ? philox(make_uint4(t, 0u, 0u, kTagPerm), a.key) : make_uint4(0, 0, 0, 0);
         const int xy = window_site_xy(a.l, L / a.l, a.key, t, a.schedule, rk, a.k0, my_row - my_b * Sw);
         my_qx = xy & 0xFFFF;
         my_qy = xy >> 16;
     }
-    const int comp_a0 = my_b == 0 ? 0 : 1;                // (b, a = x): xx or xy
-    const int comp_a1 = my_b == 0 ? 1 : 2;                // (b, a = y): xy or yy
     if (warp == 0) {
         // TMEM accumulator: 128 lanes x NT fp32 columns (allocation is a power of 2 >= 32)
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
@@ -201,39 +232,39 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a,
     }
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(&mbar[s], 1);
-            mbar_init(&fbar[s], 1);
+            mbar_init(&afull[s], kProducers);
+            mbar_init(&bfull[s], 1);
+            mbar_init(&empty[s], 1);
         }
+        mbar_init(&done, 1);
+        abort_s = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base_s;
-    bool ok = true;
-    // everything above overlaps the previous kernel's tail; the spins (B) and the
-    // partial tiles (read by the previous window's sub-step kernel) wait for it
-    pdl_wait();
+    // Under programmatic dependent launch everything up to here, and the gather of
+    // the Toeplitz operand (it reads only W~), overlaps the previous kernel's tail;
+    // the spin tiles (B) and the partial-tile stores (the previous window's sub-step
+    // kernel reads that buffer) wait for it.
 
-    const int nkb = u.kb_end - u.kb_begin;
-    // stage the operands of K-block i into ring slot i % kStages
-    auto load_stage = [&](int i) {
-        uint8_t *base = smem + (i % kStages) * kStage;
-        const uint32_t sAhi = smem_u32(base), sAlo = sAhi + kTileA;
-        const uint32_t sBhi = sAhi + 2 * kTileA, sBlo = sBhi + kTileB;
-        const int k0 = (u.kb_begin + i) * kKB;       // K offset within this tile's contraction
-        // A: Toeplitz tile, 128 rows x kKB; thread (arow, ahalf) builds chunks
-        // [ahalf * kKC/2, (ahalf + 1) * kKC/2) of row arow
-        {
-            constexpr int kHalf = kKC / 2;
-            const int al = zz ? 2 : (k0 >= N ? 1 : 0);    // input component of this K block
+    if (producer) {
+        // ---- A: Toeplitz rows W~(q - m) of K-block i into slot i % kStages
+        const int comp_a0 = my_b == 0 ? 0 : 1;             // (b, a = x): xx or xy
+        const int comp_a1 = my_b == 0 ? 1 : 2;             // (b, a = y): xy or yy
+        for (int i = 0; i < nkb; ++i) {
+            const int s = i % kStages;
+            if (i >= kStages && !mbar_wait_abort(&empty[s], (uint32_t)(((i / kStages) - 1) & 1), abort)) break;
+            const uint32_t sAhi = smem_u32(smem + s * kStage), sAlo = sAhi + kTileA;
+            const int k0 = (u.kb_begin + i) * kKB;             // K offset within this tile's contraction
+            const int al = zz ? 2 : (k0 >= N ? 1 : 0);         // input component of this K block
             const int comp = zz ? 3 : (al == 0 ? comp_a0 : comp_a1);
-            const int m0 = k0 - (zz ? 0 : al * N) + ahalf * kHalf * 8;   // first source site of the half
+            const int m0 = k0 - (zz ? 0 : al * N);             // first source site
             int my = m0 / L, mx = m0 - my * L;
             const __nv_bfloat16 *wc = a.wsh + (size_t)comp * 2 * L * 2 * L;
 #pragma unroll
-            for (int c = 0; c < kHalf; ++c) {
-                const int kc = ahalf * kHalf + c;
+            for (int kc = 0; kc < kKC; ++kc) {
                 int dy = my - my_qy;
                 if (dy < 0) dy += L;
                 int x0 = mx - my_qx;                      // W~(q - m) = W~(m - q): forward segment from x0
@@ -244,62 +275,67 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a,
                 mx += 8;
                 if (mx >= L) { mx -= L; ++my; }
             }
+            cp_async_arrive(&afull[s]);
         }
-        // B: spins of NT replicas x kKB by TMA (x = K offset, a multiple of 8
-        // elements = 16 bytes; rows past R read as zeros)
-        if (tid == 0) {
-            const int kofs = (zz ? 2 * N : 0) + k0;
-            uint64_t *fb = &fbar[i % kStages];
-            mbar_expect_tx(fb, (uint32_t)(2 * kKC * nrows_b * 16));
+        asm volatile("cp.async.wait_all;" ::: "memory");   // no copy outlives the CTA
+    } else if (warp == 1) {
+        if (lane == 0) {
+            pdl_wait();
+            // ---- B: spins of NT replicas x kKB by TMA (x = K offset, a multiple of 8
+            // elements = 16 bytes; rows past R read as zeros)
+            int issued = 0;
+            for (int i = 0; i < nkb; ++i) {
+                const int s = i % kStages;
+                if (i >= kStages && !mbar_wait_abort(&empty[s], (uint32_t)(((i / kStages) - 1) & 1), abort)) break;
+                const int kofs = (zz ? 2 * N : 0) + (u.kb_begin + i) * kKB;
+                const uint32_t sBhi = smem_u32(smem + s * kStage) + 2 * kTileA, sBlo = sBhi + kTileB;
+                mbar_expect_tx(&bfull[s], (uint32_t)(2 * kKC * nrows_b * 16));
 #pragma unroll
-            for (int kc = 0; kc < kKC; ++kc) {
-                tma_load_2d(sBhi + bcol_off(nrows_b, kc), &tm_hi, kofs + kc * 8, n0, fb);
-                tma_load_2d(sBlo + bcol_off(nrows_b, kc), &tm_lo, kofs + kc * 8, n0, fb);
+                for (int kc = 0; kc < kKC; ++kc) {
+                    tma_load_2d(sBhi + bcol_off(nrows_b, kc), &tm_hi, kofs + kc * 8, n0, &bfull[s]);
+                    tma_load_2d(sBlo + bcol_off(nrows_b, kc), &tm_lo, kofs + kc * 8, n0, &bfull[s]);
+                }
+                issued = i + 1;
             }
+            // every issued copy lands before the CTA may leave (each slot's latest use)
+            for (int i = issued > kStages ? issued - kStages : 0; i < issued; ++i)
+                mbar_wait(&bfull[i % kStages], (uint32_t)((i / kStages) & 1));
         }
-    };
-    // prologue: the first kAhead stages
-    for (int i = 0; i < kAhead; ++i) {
-        if (i < nkb) load_stage(i);
-        cp_async_commit();
-    }
-    for (int i = 0; i < nkb; ++i) {
-        // refill: K-block i + kAhead goes to the slot that K-block i + kAhead - kStages
-        // used; its MMAs were committed two iterations ago
-        const int j = i + kAhead;
-        if (j < nkb) {
-            const int prev = j - kStages;
-            if (prev >= 0) ok &= mbar_wait(&mbar[prev % kStages], (uint32_t)((prev / kStages) & 1));
-            load_stage(j);
-        }
-        cp_async_commit();
-        cp_async_wait_pending<kAhead>();             // K-block i has landed (this thread's copies)
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();                              // ... and every thread's
-        if (tid == 0) {
-            ok &= mbar_wait(&fbar[i % kStages], (uint32_t)((i / kStages) & 1));   // the stage's B tile
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t ah = smem_u32(smem + (i % kStages) * kStage);
-            const uint32_t alo = ah + kTileA, bh = ah + 2 * kTileA, blo = bh + kTileB;
+        __syncwarp();
+    } else if (warp == 0) {
+        if (lane == 0) {
+            // ---- MMAs: stage i once both operands landed; the commit frees the slot
             const uint32_t blbo = (uint32_t)(nrows_b * 16);   // K-adjacent core matrices of B
+            for (int i = 0; i < nkb; ++i) {
+                const int s = i % kStages;
+                const uint32_t par = (uint32_t)((i / kStages) & 1);
+                if (!mbar_wait_abort(&afull[s], par, abort) || !mbar_wait_abort(&bfull[s], par, abort)) break;
+                // the A rows were written by the producers' cp.async (generic proxy); the
+                // MMAs read them through the async proxy
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t ah = smem_u32(smem + s * kStage);
+                const uint32_t alo = ah + kTileA, bh = ah + 2 * kTileA, blo = bh + kTileB;
 #pragma unroll
-            for (int ks = 0; ks < kKB / 16; ++ks) {
-                const uint32_t ko = ks * 256;        // A: 16 K elements = 2 core matrices = 256 B
-                const uint32_t kb = ks * 2 * blbo;   // B: 2 core-matrix columns
-                const uint32_t acc0 = (i > 0 || ks > 0) ? 1u : 0u;
-                umma_bf16(tmem, smem_desc(ah + ko), smem_desc(bh + kb, blbo, 128u), idesc, acc0);
-                umma_bf16(tmem, smem_desc(ah + ko), smem_desc(blo + kb, blbo, 128u), idesc, 1u);
-                umma_bf16(tmem, smem_desc(alo + ko), smem_desc(bh + kb, blbo, 128u), idesc, 1u);
+                for (int ks = 0; ks < kKB / 16; ++ks) {
+                    const uint32_t ko = ks * 256;        // A: 16 K elements = 2 core matrices = 256 B
+                    const uint32_t kb = ks * 2 * blbo;   // B: 2 core-matrix columns
+                    const uint32_t acc0 = (i > 0 || ks > 0) ? 1u : 0u;
+                    umma_bf16(tmem, smem_desc(ah + ko), smem_desc(bh + kb, blbo, 128u), idesc, acc0);
+                    umma_bf16(tmem, smem_desc(ah + ko), smem_desc(blo + kb, blbo, 128u), idesc, 1u);
+                    umma_bf16(tmem, smem_desc(alo + ko), smem_desc(bh + kb, blbo, 128u), idesc, 1u);
+                }
+                umma_commit(&empty[s]);
             }
-            umma_commit(&mbar[i % kStages]);
+            umma_commit(&done);   // arrives once every MMA issued above has completed
         }
+        __syncwarp();
     }
-    // ---- wait for the last stage (its commit covers every earlier MMA)
-    if (nkb > 0) {
-        const int last = nkb - 1;
-        ok &= mbar_wait(&mbar[last % kStages], (uint32_t)((last / kStages) & 1));
-    }
+    // ---- all warps: the accumulator is complete (or the unit gave up)
+    pdl_wait();
+    const bool fin = mbar_wait(&done, 0u);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const bool ok = fin && !*abort;
     if (!ok) {
         if (tid == 0) atomicExch(a.error, 1);
     } else if (nkb > 0) {
