@@ -150,6 +150,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
     int *wxy = reinterpret_cast<int *>(wpair + NB * NB); // [Sw] site as x | y << 16 (bit 31: accepted)
     __shared__ int s_nmv[2];
     __shared__ double s_epart[32];
+    __shared__ double s_energy;   // the tracked energy after this window (measured windows)
     __shared__ float s_mred[kWThreads / 32][12];
 
     const RepParams P = buf.params[r];
@@ -629,12 +630,20 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
     if (tid == 0) {
         double et = 0.0;
         for (int i = 0; i < kWThreads / 32; ++i) et += s_epart[i];
-        buf.energy[r] += et;
+        // one adder per replica and launch: the reduction without a read-back is the
+        // same sum; a measured window needs the value
+        if (cfg.measure) {
+            s_energy = buf.energy[r] + et;
+            buf.energy[r] = s_energy;
+        } else {
+            atomicAdd(buf.energy + r, et);
+        }
     }
-    __syncthreads();
     if (cfg.measure) {
+        __syncthreads();
         float mv_[12] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         double *gt = buf.theta2 ? buf.theta2 + (size_t)r * N : nullptr;
+#pragma unroll 4
         for (int i = tid; i < N; i += kWThreads) {
             const float4 a = s4[i];
             const int iy = i / L, ix = i - iy * L;
@@ -672,7 +681,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
             x[MC_OBS_MZ] = Mz;
             x[MC_OBS_ABS_MZ] = fabs(Mz);
             x[MC_OBS_MPAR] = sqrt(Mx * Mx + My * My);
-            x[MC_OBS_E] = buf.energy[r] / N;
+            x[MC_OBS_E] = s_energy / N;
             x[MC_OBS_MST] = sqrt(Mh * Mh + Mv * Mv);
             stripe_obs(x, nh, nv, sm[11], N);
             obs_push_level(buf.obs[r], x, tid);
@@ -680,8 +689,8 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
         }
     }
     if (tid == 0 && buf.obs) {
-        buf.obs[r].accepted += n_acc;
-        buf.obs[r].attempted += (long long)Sw;
+        atomicAdd(reinterpret_cast<unsigned long long *>(&buf.obs[r].accepted), (unsigned long long)n_acc);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&buf.obs[r].attempted), (unsigned long long)Sw);
     }
 }
 
