@@ -198,6 +198,12 @@ int mc_sweep_trace(mc_lattice *lat, int nsweeps, float *trace, size_t trace_floa
 /* Statistics of one replica (synchronises the lattice's last stream). */
 int mc_observables(mc_lattice *lat, int replica, mc_obs *out);
 
+/* Statistics of replicas [first, first + count) into out[0 .. count-1]
+ * (caller-owned host array), exactly as mc_observables gives them one by one,
+ * with one synchronisation and one device-to-host copy for the whole range.
+ * MC_EINVAL for a range outside [0, R) or a null out. */
+int mc_observables_batch(mc_lattice *lat, int first, int count, mc_obs *out);
+
 /* Histogram of the energy per spin E/N over the measured sweeps (Appendix B,
  * energy distributions near the transition): nbins equal bins on [lo, hi) per
  * replica; samples outside are not counted.  Setting it clears the counts;

@@ -72,6 +72,7 @@ struct mc_lattice {
     double *etmp = nullptr;   // [R] scratch for mc_energy
     ObsAcc *obs = nullptr;    // [R]
     double *theta2 = nullptr; // [R][N]
+    double *eta_dev = nullptr; // [R] eta of the last read-back
     uint64_t t = 0;
     bool W_ready = false, energy_valid = false;
     int A = 0, tail = 0;
@@ -136,6 +137,7 @@ void free_all(mc_lattice *p) {
     cudaFree(p->etmp);
     cudaFree(p->obs);
     cudaFree(p->theta2);
+    cudaFree(p->eta_dev);
     cudaFree(p->spins_hi);
     cudaFree(p->spins_lo);
     cudaFree(p->wsh);
@@ -272,11 +274,34 @@ uint2 key_of(uint64_t seed) { return make_uint2((uint32_t)(seed & 0xFFFFFFFFu), 
 
 int full_field(mc_lattice *p, cudaStream_t st);
 
-int anchor_energy(mc_lattice *p, cudaStream_t st) {
-    int rc = full_field(p, st);
-    if (rc) return rc;
-    cudaError_t e = launch_energy(p->L, p->R, p->spins, p->field, p->dparams, p->energy, st);
+int ensure_fft(mc_lattice *p, cudaStream_t st);
+
+// Energy anchor of replicas [first, first + count): their full field by the
+// O(N log N) transform for power-of-two L >= 64 (a 256-replica L = 64 anchor:
+// tens of microseconds instead of milliseconds for the O(N^2) sum), else by the
+// direct sum; then the energy sums.  Both are per replica, so an anchor does not
+// depend on which other replicas share the handle.
+int anchor_replicas(mc_lattice *p, int first, int count, cudaStream_t st) {
+    const size_t off = (size_t)first * 3 * p->N();
+    cudaError_t e;
+    if (fft_supported(p->L) && p->L >= 64) {
+        int rc = ensure_fft(p, st);
+        if (rc) return rc;
+        TimedLaunch tl(p, MC_K_FULL_FIELD, st);
+        e = launch_fft_field(p->L, count, p->spins + off, p->What, p->fft_scratch, p->field + off, st);
+    } else {
+        TimedLaunch tl(p, MC_K_FULL_FIELD, st);
+        e = launch_full_field(p->L, count, p->W32, p->spins + off, p->field + off, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "full-field evaluation");
+    e = launch_energy(p->L, count, p->spins + off, p->field + off, p->dparams + first, p->energy + first, st);
     if (e != cudaSuccess) return cuda_fail(e, "energy kernel");
+    return MC_OK;
+}
+
+int anchor_energy(mc_lattice *p, cudaStream_t st) {
+    int rc = anchor_replicas(p, 0, p->R, st);
+    if (rc) return rc;
     p->energy_valid = true;
     return MC_OK;
 }
@@ -1000,54 +1025,72 @@ int mc_sweep_trace(mc_lattice *p, int nsweeps, float *trace, size_t trace_floats
     return run_sweeps(p, nsweeps, 0, trace, (cudaStream_t)stream);
 }
 
+// Statistics of replicas [first, first + count) into out[]: eta reduced on the
+// device, then one copy each of the accumulators, the energies and eta, on the
+// lattice's last stream.
+int obs_fill(mc_lattice *p, int first, int count, mc_obs *out) {
+    CK(cudaStreamSynchronize(p->last));
+    int rc = check_device_flag(p);
+    if (rc) return rc;
+    if (!p->eta_dev) CKA(cudaMalloc(&p->eta_dev, sizeof(double) * p->R));
+    const int N = p->N();
+    cudaError_t e = launch_eta(N, count, p->theta2 + (size_t)first * N, p->obs + first, p->eta_dev + first, p->last);
+    if (e != cudaSuccess) return cuda_fail(e, "eta reduction");
+    std::vector<ObsAcc> A((size_t)count);
+    std::vector<double> E((size_t)count), eta((size_t)count);
+    CK(cudaMemcpyAsync(A.data(), p->obs + first, sizeof(ObsAcc) * count, cudaMemcpyDeviceToHost, p->last));
+    CK(cudaMemcpyAsync(E.data(), p->energy + first, sizeof(double) * count, cudaMemcpyDeviceToHost, p->last));
+    CK(cudaMemcpyAsync(eta.data(), p->eta_dev + first, sizeof(double) * count, cudaMemcpyDeviceToHost, p->last));
+    CK(cudaStreamSynchronize(p->last));
+    for (int i = 0; i < count; ++i) {
+        const ObsAcc &a = A[i];
+        mc_obs *o = out + i;
+        std::memset(o, 0, sizeof(*o));
+        const long long n = a.bcnt[0];
+        o->samples = n;
+        o->accepted = a.accepted;
+        o->attempted = a.attempted;
+        o->energy = p->energy_valid ? E[i] / N : NAN;
+        for (int k = 0; k < MC_NOBS; ++k) {
+            if (n < 1) { o->mean[k] = NAN; continue; }
+            const double m = a.bsum[k][0] / n;
+            const double v = std::fmax(0.0, a.bsq[k][0] / n - m * m);
+            o->mean[k] = m;
+            o->var[k] = v;
+            o->err_naive[k] = n > 1 ? std::sqrt(v / (n - 1)) : NAN;
+            double best = o->err_naive[k];
+            for (int lv = 1; lv < kNB; ++lv) {
+                const long long nb = a.bcnt[lv];
+                if (nb < 32) break;
+                const double mk = a.bsum[k][lv] / nb;
+                const double vk = std::fmax(0.0, a.bsq[k][lv] / nb - mk * mk);
+                const double ek = std::sqrt(vk / (nb - 1));
+                if (ek > best) best = ek;
+            }
+            o->err[k] = best;
+            o->tau_int[k] = (o->err_naive[k] > 0) ? 0.5 * (best / o->err_naive[k]) * (best / o->err_naive[k]) : NAN;
+        }
+        o->eta = eta[i];
+    }
+    return MC_OK;
+}
+
 int mc_observables(mc_lattice *p, int replica, mc_obs *out) {
     int rc = check(p);
     if (rc) return rc;
     if (!out) return fail(MC_EINVAL, "out is null");
     if (replica < 0 || replica >= p->R) return fail(MC_EINVAL, "replica %d out of range", replica);
-    CK(cudaStreamSynchronize(p->last));
-    rc = check_device_flag(p);
+    return obs_fill(p, replica, 1, out);
+}
+
+int mc_observables_batch(mc_lattice *p, int first, int count, mc_obs *out) {
+    int rc = check(p);
     if (rc) return rc;
-    ObsAcc A;
-    CK(cudaMemcpy(&A, p->obs + replica, sizeof(ObsAcc), cudaMemcpyDeviceToHost));
-    std::vector<double> th((size_t)p->N());
-    CK(cudaMemcpy(th.data(), p->theta2 + (size_t)replica * p->N(), sizeof(double) * p->N(), cudaMemcpyDeviceToHost));
-    double E = 0;
-    CK(cudaMemcpy(&E, p->energy + replica, sizeof(double), cudaMemcpyDeviceToHost));
-    std::memset(out, 0, sizeof(*out));
-    const long long n = A.bcnt[0];
-    out->samples = n;
-    out->accepted = A.accepted;
-    out->attempted = A.attempted;
-    out->energy = p->energy_valid ? E / p->N() : NAN;
-    for (int o = 0; o < MC_NOBS; ++o) {
-        if (n < 1) { out->mean[o] = NAN; continue; }
-        const double m = A.bsum[o][0] / n;
-        const double v = std::fmax(0.0, A.bsq[o][0] / n - m * m);
-        out->mean[o] = m;
-        out->var[o] = v;
-        out->err_naive[o] = n > 1 ? std::sqrt(v / (n - 1)) : NAN;
-        double best = out->err_naive[o];
-        for (int k = 1; k < kNB; ++k) {
-            const long long nb = A.bcnt[k];
-            if (nb < 32) break;
-            const double mk = A.bsum[o][k] / nb;
-            const double vk = std::fmax(0.0, A.bsq[o][k] / nb - mk * mk);
-            const double ek = std::sqrt(vk / (nb - 1));
-            if (ek > best) best = ek;
-        }
-        out->err[o] = best;
-        out->tau_int[o] = (out->err_naive[o] > 0) ? 0.5 * (best / out->err_naive[o]) * (best / out->err_naive[o]) : NAN;
-    }
-    if (n > 0) {
-        double acc = 0;
-        const double c = (2.0 / M_PI) * (2.0 / M_PI) / (double)n;
-        for (double v : th) acc += std::sqrt(c * v);
-        out->eta = acc / p->N();
-    } else {
-        out->eta = NAN;
-    }
-    return MC_OK;
+    if (!out) return fail(MC_EINVAL, "out is null");
+    if (first < 0 || count < 0 || first + count > p->R)
+        return fail(MC_EINVAL, "replicas [%d, %d) outside [0, %d)", first, first + count, p->R);
+    if (count == 0) return MC_OK;
+    return obs_fill(p, first, count, out);
 }
 
 int mc_set_histogram(mc_lattice *p, double lo, double hi, int nbins) {
@@ -1351,7 +1394,7 @@ size_t lattice_footprint(int L, int l, int R) {
     size_t b = sizeof(RepParams) * R + sizeof(float) * 3 * N * R * 2 + sizeof(double) * 4 * N +
                sizeof(float) * 4 * N + sizeof(double) * 2 * R + sizeof(ObsAcc) * R + sizeof(double) * N * R +
                sizeof(float4) * hq * hq + sizeof(SlotState) * R;
-    if (fft_supported(L) && (!direct_supported(L, l) || L >= 128))
+    if (fft_supported(L) && (!direct_supported(L, l) || L >= 64))   // FFT path or FFT energy anchor
         b += sizeof(float) * 4 * N + fft_scratch_bytes(L, R) + sizeof(double2) * 4 * N;
     if ((!direct_supported(L, l) || L >= 128) && spectral_supported(L, l)) {
         const int es = spectral_esplit(L, l, R, 148);
@@ -1414,10 +1457,8 @@ int pack_fill(mc_lattice *p, int slot, int count, uint64_t seed, const RepParams
         CK(cudaMemsetAsync(p->energy + slot, 0xFF, sizeof(double) * count, st));
         return MC_OK;
     }
-    e = launch_full_field(p->L, count, p->W32, p->spins + off, p->field + off, st);
-    if (e != cudaSuccess) return cuda_fail(e, "full-field kernel");
-    e = launch_energy(p->L, count, p->spins + off, p->field + off, p->dparams + slot, p->energy + slot, st);
-    if (e != cudaSuccess) return cuda_fail(e, "energy kernel");
+    int rc = anchor_replicas(p, slot, count, st);
+    if (rc) return rc;
     p->last = st;
     return MC_OK;
 }
@@ -1492,12 +1533,9 @@ int pack_launch_direct(mc_lattice *p, int mx, int measure_every, cudaStream_t st
 // Results of replicas [first, first + count): observables and spins [count][3][N]
 // to host memory (spins may be null).  Synchronises st.
 int read_replicas(mc_lattice *p, int first, int count, cudaStream_t st, mc_obs *obs, float *spins) {
-    CK(cudaStreamSynchronize(st));
     p->last = st;
-    for (int i = 0; i < count; ++i) {
-        int rc = mc_observables(p, first + i, obs + i);
-        if (rc) return rc;
-    }
+    int rc = obs_fill(p, first, count, obs);
+    if (rc) return rc;
     if (spins)
         CK(cudaMemcpy(spins, p->spins + (size_t)first * 3 * p->N(), sizeof(float) * 3 * p->N() * count,
                       cudaMemcpyDeviceToHost));

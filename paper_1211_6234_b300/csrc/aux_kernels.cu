@@ -315,4 +315,32 @@ cudaError_t launch_energy(int L, int R, const float *spins, const float *h, cons
     return cudaGetLastError();
 }
 
+// Cone-angle order parameter of Sec. 4.1 per replica:
+//     eta = (1/N) sum_i sqrt((2/pi)^2 <(theta_i - pi/2)^2>),
+// the per-site mean over the n measured sweeps (theta2 holds the per-site sums).
+// One CTA per replica; a fixed-order reduction (deterministic).
+__global__ void k_eta(int N, const double *__restrict__ theta2, const ObsAcc *__restrict__ obs, double *eta) {
+    const int r = blockIdx.x;
+    const long long n = obs[r].bcnt[0];
+    const double pi = 3.14159265358979323846;
+    const double c = n > 0 ? (2.0 / pi) * (2.0 / pi) / (double)n : 0.0;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) acc += sqrt(c * theta2[(size_t)r * N + i]);
+    for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    __shared__ double red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        eta[r] = n > 0 ? s / N : (double)NAN;
+    }
+}
+
+cudaError_t launch_eta(int N, int count, const double *theta2, const ObsAcc *obs, double *eta, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    k_eta<<<count, 256, 0, st>>>(N, theta2, obs, eta);
+    return cudaGetLastError();
+}
+
 }  // namespace dipmc

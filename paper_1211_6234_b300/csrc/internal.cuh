@@ -197,6 +197,8 @@ cudaError_t launch_full_field(int L, int R, const float *W32, const float *spins
                               cudaStream_t st);
 cudaError_t launch_energy(int L, int R, const float *spins, const float *h, const RepParams *p,
                           double *E, cudaStream_t st);
+// eta (Sec. 4.1) of `count` replicas from their per-site sums of (theta - pi/2)^2.
+cudaError_t launch_eta(int N, int count, const double *theta2, const ObsAcc *obs, double *eta, cudaStream_t st);
 // Returns cudaErrorNotSupported when no direct-kernel instance fits (L, l).
 cudaError_t launch_sweep_direct(const SweepConfig &c, const SweepBuffers &b, int threads_hint,
                                 cudaStream_t st);

@@ -29,7 +29,8 @@ INIT_RANDOM, INIT_UP, INIT_USER, INIT_ISING = 0, 1, 2, 3
 ABI_SYMBOLS = (
     "mc_last_error", "mc_version", "mc_create_lattice", "mc_destroy", "mc_set_params",
     "mc_set_proposal", "mc_set_schedule", "mc_set_field_path", "mc_set_window", "mc_init_spins",
-    "mc_precompute_W", "mc_sweep", "mc_sweep_trace", "mc_observables", "mc_reset_observables",
+    "mc_precompute_W", "mc_sweep", "mc_sweep_trace", "mc_observables", "mc_observables_batch",
+    "mc_reset_observables",
     "mc_get_spins", "mc_get_field", "mc_get_W", "mc_energy", "mc_get_sweep_counter",
     "mc_checkpoint", "mc_restore", "mc_energy_noalloc", "mc_set_timing", "mc_get_timing",
     "mc_choose_spacing", "mc_autotune", "mc_set_histogram", "mc_get_histogram",
@@ -271,6 +272,14 @@ class Lattice:
         o = mc_obs()
         _ck(_lib.mc_observables(self.h, replica, C.byref(o)))
         return o.as_dict()
+
+    def observables_batch(self, first=0, count=None) -> list:
+        """observables() of replicas first .. first+count-1 with one read-back."""
+        if count is None:
+            count = self.R - first
+        arr = (mc_obs * max(count, 1))()
+        _ck(_lib.mc_observables_batch(self.h, first, count, arr))
+        return [arr[i].as_dict() for i in range(count)]
 
     def reset_observables(self):
         _ck(_lib.mc_reset_observables(self.h))

@@ -203,6 +203,33 @@ def test_determinism_checkpoint_and_batch_invariance(dipmc):
         assert o1["samples"] == o2["samples"] and o1["abs_m"]["mean"] == o2["abs_m"]["mean"]
 
 
+def test_observables_batch_equals_single_reads(dipmc):
+    """The batched read-back gives every replica's statistics exactly as the
+    one-replica call does; an out-of-range batch is MC_EINVAL."""
+    L, l, R = 16, 8, 5
+    with dipmc.Lattice(L, l, R, 9) as lat:
+        lat.precompute_W(16, True)
+        for r in range(R):
+            lat.set_params(F32(1.0), F32(0.1), F32(0.8), F32(0.0), F32(0.4 + 0.2 * r), replica=r)
+        lat.init_spins(0)
+        lat.sweep(40, 1)
+        one = [lat.observables(r) for r in range(R)]
+        many = lat.observables_batch()
+        part = lat.observables_batch(2, 2)
+        def same(x, y):
+            if isinstance(x, dict):
+                return x.keys() == y.keys() and all(same(x[k], y[k]) for k in x)
+            if isinstance(x, float) and np.isnan(x):
+                return isinstance(y, float) and np.isnan(y)
+            return x == y
+        for r in range(R):
+            assert same(one[r], many[r]), r
+        assert same(part[0], many[2]) and same(part[1], many[3])
+        with pytest.raises(dipmc.McError) as e:
+            lat.observables_batch(4, 2)
+        assert e.value.code == dipmc.MC_EINVAL
+
+
 def test_error_codes(dipmc):
     with dipmc.Lattice(16, 8, 1, 1) as lat:
         with pytest.raises(dipmc.McError) as e:
