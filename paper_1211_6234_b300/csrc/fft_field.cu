@@ -28,7 +28,9 @@ constexpr float kPiF = 3.14159265358979f;
 // Radix-2 Stockham auto-sort FFT of nrows rows of length L (in place in global
 // memory through shared memory).  Stage with half-span Ns: output
 // y[(t/Ns)*2Ns + t%Ns] = a + w b, y[... + Ns] = a - w b with a = x[t],
-// b = x[t + L/2], w = exp(-+ 2 pi i (t%Ns) / (2 Ns)).
+// b = x[t + L/2], w = exp(-+ 2 pi i (t%Ns) / (2 Ns)) = tw[(t%Ns) * L/(2Ns)],
+// tw[m] = exp(-+ 2 pi i m / L) tabulated once per CTA (the same sincospif values
+// as per-butterfly evaluation: the fractions k/Ns and 2m/L are equal and exact).
 template <bool INV>
 __global__ void k_fft_rows(float2 *data, int L, int logL, long long nrows) {
     extern __shared__ float2 fbuf[];
@@ -37,6 +39,12 @@ __global__ void k_fft_rows(float2 *data, int L, int logL, long long nrows) {
     const int rr = threadIdx.x / half, t = threadIdx.x % half;
     const long long row = (long long)blockIdx.x * rpc + rr;
     if (rpc == 0) return;
+    float2 *tw = fbuf + (size_t)rpc * 2 * L;             // [L/2]
+    for (int m = threadIdx.x; m < half; m += blockDim.x) {
+        float sw, cw;
+        sincospif((INV ? 1.0f : -1.0f) * (float)(2 * m) / (float)L, &sw, &cw);
+        tw[m] = make_float2(cw, sw);
+    }
     float2 *x = fbuf + (size_t)rr * 2 * L, *y = x + L;
     const bool valid = row < nrows;
     float2 *g = data + (valid ? row : 0) * L;
@@ -48,8 +56,8 @@ __global__ void k_fft_rows(float2 *data, int L, int logL, long long nrows) {
     for (int s = 0; s < logL; ++s) {
         const int Ns = 1 << s;
         const int k = t & (Ns - 1);
-        float sw, cw;
-        sincospif((INV ? 1.0f : -1.0f) * (float)k / (float)Ns, &sw, &cw);
+        const float2 wv = tw[k << (logL - 1 - s)];
+        const float sw = wv.y, cw = wv.x;
         const float2 a = x[t], b0 = x[t + half];
         const float2 b = make_float2(b0.x * cw - b0.y * sw, b0.x * sw + b0.y * cw);
         const int j = ((t >> s) << (s + 1)) + k;
@@ -408,7 +416,7 @@ cudaError_t rows(float2 *data, int L, long long nrows, bool inv, cudaStream_t st
     const int threads = half >= 256 ? half : 256;
     const int rpc = threads / half;
     const unsigned blocks = (unsigned)((nrows + rpc - 1) / rpc);
-    const size_t smem = sizeof(float2) * 2 * L * rpc;
+    const size_t smem = sizeof(float2) * (2 * L * rpc + half);
     if (inv) {
         cudaFuncSetAttribute(k_fft_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_fft_rows<true><<<blocks, threads, smem, st>>>(data, L, ilog2(L), nrows);
