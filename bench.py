@@ -39,6 +39,10 @@ L, l, R = 64, 32, 256
 J, CD, K2 = 1.0, 0.1, 0.8
 A_IMG = 64
 FP32_FMA_PER_CLK_PER_SM = 128  # B300 SM: 4 partitions x 32 FP32 lanes
+# device bytes the batched observables read-back copies per replica: the binning
+# accumulators (3 x 11 observables x 24 levels of FP64 sums, 2 x 24 counters, 4
+# counters) plus the energy and eta
+OBS_READBACK_BYTES = 3 * 11 * 24 * 8 + 2 * 24 * 8 + 4 * 8 + 2 * 8
 
 
 def f32(x):
@@ -558,13 +562,13 @@ def main():
     for i in range(e2e_steps):
         lat.init_spins(2, host_in.numpy())
         lat.sweep(S, 1, stream)
-        lat.get_spins(stream=stream)
+        lat.get_spins(out=host_out, stream=stream)
         lat.observables_batch()
     barrier()
     e_dt = time.perf_counter() - e0
     e2e = {"value": ws * R * L * L * S * e2e_steps / e_dt, "unit": "site-updates/s",
            "h2d_bytes_per_step": int(host_in.numel() * 4),
-           "d2h_bytes_per_step": int(host_in.numel() * 4 + R * (5 * 8 * 5 + 40))}
+           "d2h_bytes_per_step": int(host_in.numel() * 4 + R * OBS_READBACK_BYTES)}
 
     # the plain single-run FP32 path: one replica per launch, same L, l, sweeps
     plain = None

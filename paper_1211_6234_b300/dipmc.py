@@ -163,6 +163,11 @@ def _ck(rc: int):
     return rc
 
 
+def torch_float32():
+    import torch
+    return torch.float32
+
+
 def _stream_ptr(stream):
     if stream is None:
         import torch
@@ -295,8 +300,15 @@ class Lattice:
         return a
 
     def get_spins(self, out=None, stream=None) -> np.ndarray:
-        if out is not None:  # torch CUDA tensor
-            _ck(_lib.mc_get_spins(self.h, C.c_void_p(out.data_ptr()), 1, _stream_ptr(stream)))
+        """Spins [R][3][L][L]; into `out` if given: a torch tensor on the device or in
+        (pinned) host memory, or a float32 numpy array of that size."""
+        if isinstance(out, np.ndarray):
+            assert out.dtype == np.float32 and out.flags.c_contiguous and out.size == self.R * 3 * self.N
+            _ck(_lib.mc_get_spins(self.h, _np_ptr(out), 0, _stream_ptr(stream)))
+            return out
+        if out is not None:  # torch tensor
+            assert out.dtype == torch_float32() and out.is_contiguous() and out.numel() == self.R * 3 * self.N
+            _ck(_lib.mc_get_spins(self.h, C.c_void_p(out.data_ptr()), 1 if out.is_cuda else 0, _stream_ptr(stream)))
             return out
         a = np.empty((self.R, 3, self.L, self.L), np.float32)
         _ck(_lib.mc_get_spins(self.h, _np_ptr(a), 0, _stream_ptr(stream)))
