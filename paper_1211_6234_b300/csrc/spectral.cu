@@ -389,14 +389,22 @@ __global__ void __launch_bounds__(kUpdMaxThreads) k_spec_update(const SpecConfig
         thr = (uacc > 0.0f) ? -P.T * logf(uacc) : INFINITY;
     }
 
-    // ---- field spectra at the sites: sum of the partial chunks
+    // ---- field spectra at the sites: sum of the partial chunks, in chunk order,
+    // eight chunks' loads in flight at a time
     const int nchunks = cfg.esplit + (cfg.extra_in ? 1 : 0);
     for (int i = tid; i < 3 * n; i += blockDim.x) {
         float2 acc = b.Hpart[((size_t)r * 3) * n + i];
-        for (int z = 1; z < nchunks; ++z) {
-            const float2 v = b.Hpart[(((size_t)z * R + r) * 3) * n + i];
-            acc.x += v.x;
-            acc.y += v.y;
+        for (int z0 = 1; z0 < nchunks; z0 += 8) {
+            float2 v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                v[j] = z0 + j < nchunks ? b.Hpart[(((size_t)(z0 + j) * R + r) * 3) * n + i] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (z0 + j < nchunks) {
+                    acc.x += v[j].x;
+                    acc.y += v[j].y;
+                }
         }
         H[i] = acc;
     }
