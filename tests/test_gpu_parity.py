@@ -461,6 +461,63 @@ def test_fft_full_field_L256_sampled_sites(dipmc):
     assert max(errs) / hmax < 1e-5, (max(errs), hmax)
 
 
+def test_spectral_path_L256_sampled_attempts(dipmc):
+    """L = 256, l = 32 (the large-lattice configuration the spectral path serves):
+    one traced sweep of two replicas.  Every decision is consistent with its own dE
+    and u; the state is replayed attempt by attempt from the trace, and at sampled
+    sub-steps the recorded field and dE are compared with a direct sum over the
+    replayed state (W~ from the oracle)."""
+    L, l, R, A = 256, 32, 2, 8
+    n, ll = (L // l) ** 2, l * l
+    prm = [(F32(1.0), F32(0.1), F32(0.8), F32(0.0), F32(0.3)), (F32(1.0), F32(0.1), F32(0.8), F32(0.1), F32(0.9))]
+    s0 = inputs.random_spins(L, R, seed=913)
+    with dipmc.Lattice(L, l, R, 17) as lat:
+        lat.precompute_W(A, True)
+        lat.set_field_path(dipmc.MC_PATH_SPECTRAL)
+        for r in range(R):
+            lat.set_params(*prm[r], replica=r)
+        lat.init_spins(2, s0)
+        tr = lat.sweep_trace(1).astype(np.float64)
+        sg = lat.get_spins().astype(np.float64)
+    Wo = orc.wtilde(L, A, True)
+    W0 = Wo[:, 0, 0]
+    sample_k = {0, 1, 2, 37, 511, 1000, ll - 1}
+    for r in range(R):
+        J, CD, K2, K4, T = prm[r]
+        t_r = tr[r].reshape(ll, n, -1)
+        # decisions follow the recorded dE and u: accept iff dE < -T ln u
+        thr = np.where(t_r[:, :, 5] > 0, -T * np.log(np.maximum(t_r[:, :, 5], 1e-300)), np.inf)
+        assert np.array_equal(t_r[:, :, 6] > 0.5, t_r[:, :, 4] < thr)
+        s = np.array(s0[r], np.float64)
+        hmax, herr, derr = 0.0, 0.0, 0.0
+        for k in range(ll):
+            q = t_r[k, :, 0].astype(np.int64)
+            qy, qx = q // L, q % L
+            if k in sample_k:
+                for d in range(0, n, 7):
+                    y0, x0 = int(qy[d]), int(qx[d])
+                    dy = (y0 - np.arange(L)[:, None]) % L
+                    dx = (x0 - np.arange(L)[None, :]) % L
+                    xx, xy, yy, zz = Wo[0][dy, dx], Wo[1][dy, dx], Wo[2][dy, dx], Wo[3][dy, dx]
+                    h = np.array([(xx * s[0] + xy * s[1]).sum(), (xy * s[0] + yy * s[1]).sum(), (zz * s[2]).sum()])
+                    hmax = max(hmax, np.abs(h).max())
+                    herr = max(herr, np.abs(t_r[k, d, 1:4] - h).max())
+                    # dE of the proposal from the replayed state (exchange, anisotropy, dipole)
+                    sq = s[:, y0, x0]
+                    S = t_r[k, d, 7:10]
+                    dl = S - sq
+                    nb = (s[:, y0, (x0 + 1) % L] + s[:, y0, (x0 - 1) % L] + s[:, (y0 + 1) % L, x0] + s[:, (y0 - 1) % L, x0])
+                    ean = -K2 * S[2] ** 2 - K4 * S[2] ** 4 + K2 * sq[2] ** 2 + K4 * sq[2] ** 4
+                    self_ = W0[0] * dl[0] ** 2 + 2 * W0[1] * dl[0] * dl[1] + W0[2] * dl[1] ** 2 + W0[3] * dl[2] ** 2
+                    dE = -J * dl @ nb + ean + CD * (dl @ h + 0.5 * self_)
+                    derr = max(derr, abs(t_r[k, d, 4] - dE))
+            acc = t_r[k, :, 6] > 0.5
+            s[:, qy[acc], qx[acc]] = t_r[k, acc, 7:10].T
+        assert herr / hmax < 1e-5, (herr, hmax)
+        assert derr < 2e-5 * (1 + abs(J) + abs(K2) + abs(K4) + CD * hmax), derr
+        np.testing.assert_allclose(sg[r], s, rtol=0, atol=1e-6)   # the replay ends in the GPU's state
+
+
 FCASES = [
     # path, L, l, R, schedule, nsweeps
     (4, 16, 8, 2, 0, 2),
