@@ -89,6 +89,7 @@ struct mc_lattice {
     int mtiles = 0, ntiles = 0;
     int *err_flag = nullptr;
     bool wsh_ready = false;
+    bool wsh_spec2 = false;     // wsh holds the signed cell-grid spectra of W~
     float4 *wq = nullptr;     // quarter table of W~ for the windowed paths
     float *What = nullptr;    // [4][N] transform of W~ (FFT path), transposed layout
     float2 *fft_scratch = nullptr;
@@ -338,11 +339,15 @@ int ensure_tensor_buffers(mc_lattice *p, int Sw, cudaStream_t st) {
         CKA(cudaMalloc(&p->err_flag, sizeof(int)));
         CKA(cudaMemset(p->err_flag, 0, sizeof(int)));
     }
-    if (!p->wsh) CKA(cudaMalloc(&p->wsh, sizeof(__nv_bfloat16) * tc_wsh_elems(p->L)));
-    if (!p->wsh_ready) {
-        cudaError_t e = launch_build_wsh(p->L, p->W64, p->wsh, st);
+    // operand tables: the Toeplitz copies of W~, or for L = 2l with a 256-site window the
+    // signed spectra of W~ over the 2 x 2 cell grid (the lattice keeps one kind)
+    const bool spec2 = tc_spec2_supported(p->L, p->l, Sw);
+    if (!p->wsh) CKA(cudaMalloc(&p->wsh, sizeof(__nv_bfloat16) * std::max(tc_wsh_elems(p->L), tc_t2_elems(p->l))));
+    if (!p->wsh_ready || p->wsh_spec2 != spec2) {
+        cudaError_t e = spec2 ? launch_build_t2(p->L, p->W64, p->wsh, st) : launch_build_wsh(p->L, p->W64, p->wsh, st);
         if (e != cudaSuccess) return cuda_fail(e, "W~ bf16 tables");
         p->wsh_ready = true;
+        p->wsh_spec2 = spec2;
     }
     if (p->plan_Sw != Sw) {
         cudaFree(p->units);
@@ -355,7 +360,7 @@ int ensure_tensor_buffers(mc_lattice *p, int Sw, cudaStream_t st) {
         std::vector<TcUnit> u(65536);
         std::vector<int> tf(1 << 16);
         const int nu = tc_plan(p->L, Sw, p->R, nsm, u.data(), (int)u.size(), &p->NT, &p->tmem_cols, tf.data(),
-                               &p->mtiles, &p->ntiles);
+                               &p->mtiles, &p->ntiles, spec2);
         if (nu <= 0) return fail(MC_EINVAL, "tensor-core plan failed for Sw=%d R=%d", Sw, p->R);
         CKA(cudaMalloc(&p->units, sizeof(TcUnit) * nu));
         CKA(cudaMemcpy(p->units, u.data(), sizeof(TcUnit) * nu, cudaMemcpyHostToDevice));
@@ -377,11 +382,14 @@ int run_windows(mc_lattice *p, int path, int nsweeps, int measure_every, float *
     const bool tensor = path == MC_PATH_TENSOR;
     const int B = window_of(p, tensor);
     const int ll = p->l * p->l, n = p->n(), Sw = B * n, nwin = ll / B;
+    const bool spec2 = tensor && tc_spec2_supported(p->L, p->l, Sw);
     if (tensor) {
         int rc = ensure_tensor_buffers(p, Sw, st);
         if (rc) return rc;
-        cudaError_t e = launch_spins_to_bf16((size_t)p->R * 3 * p->N(), p->spins, p->spins_hi, p->spins_lo, st);
-        if (e != cudaSuccess) return cuda_fail(e, "bf16 split of the spins");
+        // the B operand: bf16 hi/lo of the spins, or of their cell-grid spectra
+        cudaError_t e = spec2 ? launch_spec2_init(p->L, p->R, p->spins, p->spins_hi, p->spins_lo, st)
+                              : launch_spins_to_bf16((size_t)p->R * 3 * p->N(), p->spins, p->spins_hi, p->spins_lo, st);
+        if (e != cudaSuccess) return cuda_fail(e, "bf16 operand of the spins");
     }
     WindowConfig c{};
     c.t_dev = p->t_dev;
@@ -392,7 +400,7 @@ int run_windows(mc_lattice *p, int path, int nsweeps, int measure_every, float *
     c.proposal = p->proposal;
     c.cap_c1 = (float)(1.0 - std::cos(p->cone));
     c.schedule = p->schedule;
-    c.stale_mode = tensor ? 2 : 0;   // tensor path: the sub-step kernel sums the split-K partial tiles
+    c.stale_mode = tensor ? (spec2 ? 3 : 2) : 0;   // tensor path: the sub-step kernel sums the split-K partial tiles
     c.NT = p->NT;
     c.mtiles = p->mtiles;
     WindowBuffers b{};
@@ -411,6 +419,7 @@ int run_windows(mc_lattice *p, int path, int nsweeps, int measure_every, float *
         ta.L = p->L; ta.Sw = Sw; ta.R = p->R; ta.NT = p->NT; ta.tmem_cols = p->tmem_cols;
         ta.units = p->units; ta.wsh = p->wsh;
         ta.l = p->l; ta.schedule = p->schedule; ta.key = c.key; ta.t_dev = p->t_dev;
+        ta.spec2 = spec2 ? 1 : 0;
         ta.spins_hi = p->spins_hi; ta.spins_lo = p->spins_lo; ta.error = p->err_flag;
         ta.part = p->tcpart; ta.tile_first = p->tile_first; ta.mtiles = p->mtiles; ta.ntiles = p->ntiles;
     }

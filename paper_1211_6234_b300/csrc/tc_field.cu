@@ -213,14 +213,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a,
     // producer thread: its tile row's window site and tensor components
     const bool producer = warp >= kProdWarp0;
     const int arow = tid - kProdWarp0 * 32;
-    int my_b = 0, my_qx = 0, my_qy = 0;
+    int my_b = 0, my_qx = 0, my_qy = 0, my_kap = 0;
     if (producer) {
         const int my_row = row0 + arow;
-        my_b = my_row / Sw;                          // output component 0 x, 1 y, 2 z
+        int slot;                                    // window site (Toeplitz) or first site of the offset (spectra)
+        if (a.spec2) {
+            // rows kappa*2B + b*B + j (in-plane) and 2 S_w + (kappa/2)*2B + (kappa%2)*B + j (zz), B = S_w/4
+            const int B4 = Sw >> 2;
+            if (my_row < 2 * Sw) {
+                my_kap = my_row / (2 * B4);
+                my_b = (my_row / B4) & 1;
+            } else {
+                const int rz = my_row - 2 * Sw;
+                my_kap = 2 * (rz / (2 * B4)) + ((rz / B4) & 1);
+                my_b = 2;
+            }
+            slot = 4 * (my_row % B4);
+        } else {
+            my_b = my_row / Sw;                      // output component 0 x, 1 y, 2 z
+            slot = my_row - my_b * Sw;
+        }
         const uint32_t t = a.t_dev ? *a.t_dev + (uint32_t)a.it : a.t_host;
         const uint4 rk = a.schedule == 0 ? philox(make_uint4(t, 0u, 0u, kTagPerm), a.key) : make_uint4(0, 0, 0, 0);
-        const int xy = window_site_xy(a.l, L / a.l, a.key, t, a.schedule, rk, a.k0, my_row - my_b * Sw);
-        my_qx = xy & 0xFFFF;
+        const int xy = window_site_xy(a.l, L / a.l, a.key, t, a.schedule, rk, a.k0, slot);
+        my_qx = xy & 0xFFFF;                         // spectra: the offset (ox, oy) of the row's sub-step
         my_qy = xy >> 16;
     }
     if (warp == 0) {
@@ -258,6 +274,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a,
             if (i >= kStages && !mbar_wait_abort(&empty[s], (uint32_t)(((i / kStages) - 1) & 1), abort)) break;
             const uint32_t sAhi = smem_u32(smem + s * kStage), sAlo = sAhi + kTileA;
             const int k0 = (u.kb_begin + i) * kKB;             // K offset within this tile's contraction
+            if (a.spec2) {
+                // signed spectrum of W~ at (o - e) mod l for the offsets e = e0 .. e0+31 (cell
+                // offsets in the order e' = ey*l + (l-1-ex), so each 8-run is ascending in i)
+                const int l = a.l, lsq = l * l, l2 = 2 * l;
+                const int part = k0 >= lsq;                    // in-plane: input component; zz: kappa of the pair
+                const int e0 = k0 - part * lsq;
+                const int comp = my_b == 2 ? 3 : (part == 0 ? comp_a0 : comp_a1);
+                const uint32_t bytes = (my_b == 2 && part != (my_kap & 1)) ? 0u : 16u;   // zz rows: own kappa only
+                const size_t cstride = (size_t)4 * 4 * 2 * 2 * l * l2;
+#pragma unroll
+                for (int kc = 0; kc < kKC; ++kc) {
+                    const int e = e0 + 8 * kc, ey = e / l, exq = e - ey * l;
+                    int dy = my_qy - ey;
+                    const int sy = dy < 0;
+                    dy += sy ? l : 0;
+                    const int i0 = my_qx + 1 + exq, c = i0 & 7;
+                    const size_t off = (size_t)c * cstride +
+                                       ((((size_t)my_kap * 4 + comp) * 2 + sy) * 2) * l * l2 + (size_t)dy * l2 + (i0 - c);
+                    cp_async16(sAhi + core_off(arow, kc), a.wsh + off, bytes);
+                    cp_async16(sAlo + core_off(arow, kc), a.wsh + off + (size_t)l * l2, bytes);
+                }
+                cp_async_arrive(&afull[s]);
+                continue;
+            }
             const int al = zz ? 2 : (k0 >= N ? 1 : 0);         // input component of this K block
             const int comp = zz ? 3 : (al == 0 ? comp_a0 : comp_a1);
             const int m0 = k0 - (zz ? 0 : al * N);             // first source site
@@ -287,7 +327,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a,
             for (int i = 0; i < nkb; ++i) {
                 const int s = i % kStages;
                 if (i >= kStages && !mbar_wait_abort(&empty[s], (uint32_t)(((i / kStages) - 1) & 1), abort)) break;
-                const int kofs = (zz ? 2 * N : 0) + (u.kb_begin + i) * kKB;
+                const int kk = (u.kb_begin + i) * kKB;
+                int kofs;
+                if (a.spec2) {
+                    // spectra [kappa][a][e']: in-plane tiles are kappa = mtile, zz tiles a kappa pair
+                    const int lsq = N >> 2;
+                    if (!zz) {
+                        kofs = u.mtile * 3 * lsq + kk;
+                    } else {
+                        const int part = kk >= lsq;
+                        kofs = (2 * (u.mtile - 2 * Sw / 128) + part) * 3 * lsq + 2 * lsq + (kk - part * lsq);
+                    }
+                } else {
+                    kofs = (zz ? 2 * N : 0) + kk;
+                }
                 const uint32_t sBhi = smem_u32(smem + s * kStage) + 2 * kTileA, sBlo = sBhi + kTileB;
                 mbar_expect_tx(&bfull[s], (uint32_t)(2 * kKC * nrows_b * 16));
 #pragma unroll
@@ -383,10 +436,93 @@ __global__ void k_build_wsh(int L, const double *__restrict__ W64, __nv_bfloat16
     wsh[base + (size_t)L * 2 * L + (size_t)y * 2 * L + i] = lo;
 }
 
-// Window sites of sweep t, window w (same schedule as the sweep kernels).
+// Spectral operand mode, L = 2l.  The 2 x 2 cell grid has the real DFT
+// F(kappa) = sum_D (-1)^(kappa.D) f(o + l D), kappa = Kx + 2 Ky, D = Dx + 2 Dy (Sec. 3.1
+// sub-lattices); the field at o + l D is h = (1/4) sum_kappa (-1)^(kappa.D) H_o(kappa) with
+//     H_o(kappa) = sum_e (-1)^(Kx sx + Ky sy) T_{(o - e) mod l}(kappa) S_e(kappa),
+// sx, sy = 1 where o - e wraps in x, y, and T, S the DFTs of W~ and of the spins.
+// The table holds, for each kappa, component and y-wrap sy, the row
+//     T2[dy][i] = (-1)^(Ky sy) (i >= l ? T_(dy, i-l) : (-1)^Kx T_(dy, i)),  i in [0, 2l),
+// so that the entries for e' = ey*l + (l-1-ex), ex descending, are T2[dy][ox + 1 + (l-1-ex)]:
+// an ascending run; copy c is shifted by c so that every 8-run is one aligned 16 bytes.
+__global__ void k_build_t2(int L, const double *__restrict__ W64, __nv_bfloat16 *t2) {
+    const int l = L / 2, l2 = 2 * l, N = L * L;
+    const size_t total = (size_t)8 * 4 * 4 * 2 * l * l2;
+    const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= total) return;
+    const int i = (int)(gid % l2);
+    size_t rest = gid / l2;
+    const int dy = (int)(rest % l);
+    rest /= l;
+    const int sy = (int)(rest % 2);
+    rest /= 2;
+    const int comp = (int)(rest % 4);
+    rest /= 4;
+    const int kap = (int)(rest % 4);
+    const int c = (int)(rest / 4);
+    const int Kx = kap & 1, Ky = kap >> 1;
+    const int x = i + c;
+    double v = 0.0;
+    if (x < l2) {
+        const int xx = x % l;
+        for (int F = 0; F < 4; ++F) {
+            const int Fx = F & 1, Fy = F >> 1;
+            const double w = W64[(size_t)comp * N + (size_t)(dy + l * Fy) * L + (xx + l * Fx)];
+            v += ((Kx * Fx + Ky * Fy) & 1) ? -w : w;
+        }
+        if (x < l && Kx) v = -v;
+        if (sy && Ky) v = -v;
+    }
+    const float f = (float)v;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(f);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(f - __bfloat162float(hi));
+    const size_t base = ((((size_t)c * 4 + kap) * 4 + comp) * 2 + sy) * 2 * l * l2 + (size_t)dy * l2 + i;
+    t2[base] = hi;
+    t2[base + (size_t)l * l2] = lo;
+}
+
+// Spin spectra S'[r][kappa][a][e'] (bf16 hi/lo), e' = ey*l + (l-1-ex), of every cell offset.
+__global__ void k_spec2_init(int L, int R, const float *__restrict__ spins, __nv_bfloat16 *hi,
+                             __nv_bfloat16 *lo) {
+    const int l = L / 2, lsq = l * l, N = L * L;
+    const size_t total = (size_t)R * 12 * lsq;
+    const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= total) return;
+    const int ep = (int)(gid % lsq);
+    const size_t ka = (gid / lsq) % 12, r = gid / ((size_t)12 * lsq);
+    const int kap = (int)(ka / 3), a = (int)(ka % 3), Kx = kap & 1, Ky = kap >> 1;
+    const int ey = ep / l, ex = l - 1 - (ep - ey * l);
+    const float *s = spins + (r * 3 + a) * N;
+    float v = 0.0f;
+    for (int D = 0; D < 4; ++D) {
+        const int Dx = D & 1, Dy = D >> 1;
+        const float x = s[(ey + l * Dy) * L + ex + l * Dx];
+        v += ((Kx * Dx + Ky * Dy) & 1) ? -x : x;
+    }
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[gid] = h;
+    lo[gid] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
 }  // namespace
 
 size_t tc_wsh_elems(int L) { return (size_t)8 * 4 * 2 * L * 2 * L; }
+
+size_t tc_t2_elems(int l) { return (size_t)8 * 4 * 4 * 2 * 2 * l * 2 * l; }
+
+bool tc_spec2_supported(int L, int l, int Sw) { return L == 2 * l && l % 8 == 0 && Sw == 256; }
+
+cudaError_t launch_build_t2(int L, const double *W64, __nv_bfloat16 *t2, cudaStream_t st) {
+    const int l = L / 2;
+    const size_t total = (size_t)8 * 4 * 4 * 2 * l * 2 * l;
+    k_build_t2<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(L, W64, t2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spec2_init(int L, int R, const float *spins, __nv_bfloat16 *hi, __nv_bfloat16 *lo, cudaStream_t st) {
+    const size_t total = (size_t)R * 12 * (L / 2) * (L / 2);
+    k_spec2_init<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(L, R, spins, hi, lo);
+    return cudaGetLastError();
+}
 
 bool tc_supported(int L, int l, int B) {
     if (L % 8 || L < 8 || l < 2 || L % l) return false;
@@ -404,12 +540,14 @@ cudaError_t launch_build_wsh(int L, const double *W64, __nv_bfloat16 *wsh, cudaS
 }
 
 int tc_plan(int L, int Sw, int R, int nsm, TcUnit *units, int max_units, int *NT_out, int *tmem_cols,
-            int *tile_first, int *mtiles_out, int *ntiles_out) {
+            int *tile_first, int *mtiles_out, int *ntiles_out, bool spec2) {
     const int N = L * L;
     const int NT = R >= 256 ? 256 : ((R + 15) / 16) * 16;
     const int ntiles = (R + NT - 1) / NT;
     const int mt_inplane = 2 * Sw / 128, mt_zz = Sw / 128;
-    const int kb_inplane = 2 * N / kKB, kb_zz = N / kKB;
+    // K per tile: Toeplitz rows contract (a, m) over 2N (in-plane) or N (zz); spectra
+    // contract (a, e') or (kappa pair, e') over 2 l^2 = N / 2
+    const int kb_inplane = spec2 ? N / 2 / kKB : 2 * N / kKB, kb_zz = spec2 ? N / 2 / kKB : N / kKB;
     const long long total = (long long)ntiles * (mt_inplane * kb_inplane + mt_zz * kb_zz);
     // smallest K-blocks per unit whose units (rounded up per tile) fit one wave
     int kbpu = (int)((total + nsm - 1) / nsm);

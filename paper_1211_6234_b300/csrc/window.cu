@@ -214,8 +214,36 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
         return make_float3((a.x + bb.x) + (c.x + dd.x), (a.y + bb.y) + (c.y + dd.y), (a.z + bb.z) + (c.z + dd.z));
     };
 
+    // sum of the split-K partial tiles of output row `row` of this replica's column,
+    // in unit order (the tensor-core field's reduction)
+    auto row_sum = [&](int row) -> float {
+        const int nt = r / cfg.NT, col = r - nt * cfg.NT, mt = row >> 7;
+        const int u0 = buf.tile_first[nt * cfg.mtiles + mt], u1 = buf.tile_first[nt * cfg.mtiles + mt + 1];
+        const float *pc = buf.part + ((size_t)u0 * cfg.NT + col) * 128 + (row & 127);
+        const size_t ustride = (size_t)cfg.NT * 128;
+        float h = 0.f;
+        for (int j0 = 0; j0 < u1 - u0; j0 += 8) {
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = (j0 + j < u1 - u0) ? __ldcg(pc + (size_t)(j0 + j) * ustride) : 0.f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (j0 + j < u1 - u0) h += v[j];
+        }
+        return h;
+    };
+    // stale_mode 3 (spectra of the window's offsets, L = 2l): the field of site
+    // 4j + d, d = Dx + 2 Dy, is (1/4) sum_kappa (-1)^(kappa.D) H_j(kappa); it is staged
+    // in shared memory (PRE: after dacc; otherwise in hcur) before the per-site set-up
+    float *hst = dacc + Sw;
+    auto staged = [&](int s) -> float3 {
+        if (PRE) return make_float3(hst[3 * s], hst[3 * s + 1], hst[3 * s + 2]);
+        const float4 h = hcur[s];
+        return make_float3(h.x, h.y, h.z);
+    };
     // the stale field at window site s (lattice site q)
     auto stale_at = [&](int s, int q) -> float3 {
+        if (cfg.stale_mode == 3) return staged(s);
         if (cfg.stale_mode == 0) {
             const float *f = buf.stale + (size_t)r * 3 * N;
             return make_float3(f[q], f[N + q], f[2 * N + q]);
@@ -259,6 +287,26 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
     for (int i = tid; i < hq * hq; i += kWThreads) wq[i] = buf.wq[i];
     for (int s = tid; s < Sw; s += kWThreads) wxy[s] = window_site_xy(l, C, key, t, cfg.schedule, rk, k0, s);
     pdl_wait();
+    if (cfg.stale_mode == 3) {
+        // rows kappa*2B + b*B + j (b = x, y) and 2 S_w + (kappa/2)*2B + (kappa%2)*B + j (z), B = S_w/4
+        const int B4 = Sw >> 2;
+        for (int task = tid; task < 3 * B4; task += kWThreads) {
+            const int j = task / 3, bb = task - 3 * j;
+            float H[4];
+#pragma unroll
+            for (int kap = 0; kap < 4; ++kap)
+                H[kap] = row_sum(bb < 2 ? kap * 2 * B4 + bb * B4 + j : 2 * Sw + (kap >> 1) * 2 * B4 + (kap & 1) * B4 + j);
+#pragma unroll
+            for (int d = 0; d < 4; ++d) {
+                float h = 0.f;
+#pragma unroll
+                for (int kap = 0; kap < 4; ++kap) h += (((kap & 1) * (d & 1) + (kap >> 1) * (d >> 1)) & 1) ? -H[kap] : H[kap];
+                h *= 0.25f;
+                if (PRE) hst[3 * (4 * j + d) + bb] = h;
+                else reinterpret_cast<float *>(hcur + 4 * j + d)[bb] = h;
+            }
+        }
+    }
     const float *gs = buf.spins + (size_t)r * 3 * N;
 #pragma unroll 4
     for (int q = tid; q < N; q += kWThreads) s4[q] = make_float4(gs[q], gs[N + q], gs[2 * N + q], 0.0f);
@@ -590,7 +638,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
         gd[q] = v.x;
         gd[N + q] = v.y;
         gd[2 * N + q] = v.z;
-        if (buf.spins_hi) {
+        if (buf.spins_hi && cfg.stale_mode != 3) {
             __nv_bfloat16 *hi = buf.spins_hi + (size_t)r * 3 * N;
             __nv_bfloat16 *lo = buf.spins_lo + (size_t)r * 3 * N;
             const float v3[3] = {v.x, v.y, v.z};
@@ -600,6 +648,26 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
                 hi[cc * N + q] = h16;
                 lo[cc * N + q] = __float2bfloat16_rn(v3[cc] - __bfloat162float(h16));
             }
+        }
+    }
+    if (cfg.stale_mode == 3) {
+        // ---- spectra of the window's offsets after its moves, S'[r][kappa][a][e'] (bf16 hi/lo)
+        const int lsq = l * l;
+        __nv_bfloat16 *hi = buf.spins_hi + (size_t)r * 12 * lsq, *lo = buf.spins_lo + (size_t)r * 12 * lsq;
+        for (int task = tid; task < 12 * (Sw >> 2); task += kWThreads) {
+            const int j = task / 12, ka = task - 12 * j, kap = ka / 3, aa = ka - 3 * kap;
+            const int o = wxy[4 * j], ox = o & 0xFFFF, oy = (o >> 16) & 0x7FFF;
+            float v = 0.0f;
+#pragma unroll
+            for (int D = 0; D < 4; ++D) {
+                const float4 sv = s4[(oy + l * (D >> 1)) * L + ox + l * (D & 1)];
+                const float x = aa == 0 ? sv.x : aa == 1 ? sv.y : sv.z;
+                v += (((kap & 1) * (D & 1) + (kap >> 1) * (D >> 1)) & 1) ? -x : x;
+            }
+            const size_t idx = (size_t)(kap * 3 + aa) * lsq + oy * l + (l - 1 - ox);
+            const __nv_bfloat16 h16 = __float2bfloat16_rn(v);
+            hi[idx] = h16;
+            lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h16));
         }
     }
     // ---- exact energy change of the window: accepted dE plus, per sub-step, the
