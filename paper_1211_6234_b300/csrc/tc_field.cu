@@ -551,7 +551,7 @@ int tc_plan(int L, int Sw, int R, int nsm, TcUnit *units, int max_units, int *NT
     const long long total = (long long)ntiles * (mt_inplane * kb_inplane + mt_zz * kb_zz);
     // smallest K-blocks per unit whose units (rounded up per tile) fit one wave
     int kbpu = (int)((total + nsm - 1) / nsm);
-    if (kbpu < 2) kbpu = 2;
+    if (kbpu < (spec2 ? 4 : 2)) kbpu = spec2 ? 4 : 2;   // spectra: at least 4 K-blocks a unit (measured)
     for (;; ++kbpu) {
         long long cnt = 0;
         for (int mt = 0; mt < mt_inplane + mt_zz; ++mt) {

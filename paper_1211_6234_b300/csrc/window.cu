@@ -214,23 +214,35 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
         return make_float3((a.x + bb.x) + (c.x + dd.x), (a.y + bb.y) + (c.y + dd.y), (a.z + bb.z) + (c.z + dd.z));
     };
 
-    // sum of the split-K partial tiles of output row `row` of this replica's column,
-    // in unit order (the tensor-core field's reduction)
-    auto row_sum = [&](int row) -> float {
-        const int nt = r / cfg.NT, col = r - nt * cfg.NT, mt = row >> 7;
-        const int u0 = buf.tile_first[nt * cfg.mtiles + mt], u1 = buf.tile_first[nt * cfg.mtiles + mt + 1];
-        const float *pc = buf.part + ((size_t)u0 * cfg.NT + col) * 128 + (row & 127);
+    // sums of the split-K partial tiles of four output rows of this replica's column,
+    // each in unit order (the tensor-core field's reduction), eight units of every row
+    // in flight at a time
+    auto row_sum4 = [&](const int (&row)[4], float (&h)[4]) {
+        const int nt = r / cfg.NT, col = r - nt * cfg.NT;
         const size_t ustride = (size_t)cfg.NT * 128;
-        float h = 0.f;
-        for (int j0 = 0; j0 < u1 - u0; j0 += 8) {
-            float v[8];
+        const float *pc[4];
+        int cnt[4], cmax = 0;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) v[j] = (j0 + j < u1 - u0) ? __ldcg(pc + (size_t)(j0 + j) * ustride) : 0.f;
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                if (j0 + j < u1 - u0) h += v[j];
+        for (int k = 0; k < 4; ++k) {
+            const int mt = row[k] >> 7;
+            const int u0 = buf.tile_first[nt * cfg.mtiles + mt], u1 = buf.tile_first[nt * cfg.mtiles + mt + 1];
+            pc[k] = buf.part + ((size_t)u0 * cfg.NT + col) * 128 + (row[k] & 127);
+            cnt[k] = u1 - u0;
+            cmax = max(cmax, cnt[k]);
+            h[k] = 0.f;
         }
-        return h;
+        for (int j0 = 0; j0 < cmax; j0 += 8) {
+            float v[4][8];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v[k][j] = (j0 + j < cnt[k]) ? __ldcg(pc[k] + (size_t)(j0 + j) * ustride) : 0.f;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (j0 + j < cnt[k]) h[k] += v[k][j];
+        }
     };
     // stale_mode 3 (spectra of the window's offsets, L = 2l): the field of site
     // 4j + d, d = Dx + 2 Dy, is (1/4) sum_kappa (-1)^(kappa.D) H_j(kappa); it is staged
@@ -292,10 +304,12 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
         const int B4 = Sw >> 2;
         for (int task = tid; task < 3 * B4; task += kWThreads) {
             const int j = task / 3, bb = task - 3 * j;
-            float H[4];
+            int rows[4];
 #pragma unroll
             for (int kap = 0; kap < 4; ++kap)
-                H[kap] = row_sum(bb < 2 ? kap * 2 * B4 + bb * B4 + j : 2 * Sw + (kap >> 1) * 2 * B4 + (kap & 1) * B4 + j);
+                rows[kap] = bb < 2 ? kap * 2 * B4 + bb * B4 + j : 2 * Sw + (kap >> 1) * 2 * B4 + (kap & 1) * B4 + j;
+            float H[4];
+            row_sum4(rows, H);
 #pragma unroll
             for (int d = 0; d < 4; ++d) {
                 float h = 0.f;
