@@ -326,11 +326,11 @@ def ising_leg(dipmc, stream, sweeps=50, neq=100, nms=200):
     s0 = np.zeros((Rb, 3, Lb, Lb), np.float32)
     s0[:, 2] = np.where(y % 2 == 0, 1.0, -1.0)
     out = {"workload": "256 x L=64 Ising, J_bond/C_D = 0.85, T/C_D in [0.3, 1.0], reversal moves",
-           "sweeps_timed": sweeps}
+           "sweeps_timed": sweeps, "field_path": "tensor"}
     for lb in (32, 64):
         lat = dipmc.Lattice(Lb, lb, Rb, seed=17)
         lat.precompute_W(A_IMG, True)
-        lat.set_field_path(dipmc.MC_PATH_DIRECT)
+        lat.set_field_path(dipmc.MC_PATH_TENSOR)
         lat.set_proposal(dipmc.PROPOSAL_FLIP, 0.5)
         for r in range(Rb):
             lat.set_params(1.0, cd, 0.0, 0.0, f32(tt[r] * cd), replica=r)
@@ -367,7 +367,7 @@ def srt_scan_leg(dipmc, stream, neq=500, nms=500):
     s0[:, 2] = np.where((y // 8) % 2 == 0, 1.0, -1.0)
     lat = dipmc.Lattice(Lb, lb, R, seed=29)
     lat.precompute_W(A_IMG, True)
-    lat.set_field_path(dipmc.MC_PATH_DIRECT)
+    lat.set_field_path(dipmc.MC_PATH_TENSOR)
     for i, a in enumerate(avals):
         for j, T in enumerate(Ts):
             lat.set_params(8.9, 1.0, 15.0 * (1.0 - a), 15.0 * a, f32(T), replica=i * len(Ts) + j)
@@ -378,7 +378,7 @@ def srt_scan_leg(dipmc, stream, neq=500, nms=500):
     lat.sweep(nms, 1, stream)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    out = {"workload": "L=64, l=32, J/C_D=8.9, K/C_D=15, a in {-1, 0, 2}, 16 T/C_D in [0.5, 10]",
+    out = {"workload": "L=64, l=32, J/C_D=8.9, K/C_D=15, a in {-1, 0, 2}, 16 T/C_D in [0.5, 10]", "field_path": "tensor",
            "sweeps": {"equilibration": neq, "measured": nms}, "T_over_CD": [round(float(v), 4) for v in Ts],
            "site_updates_per_s": R * Lb * Lb * nms / dt, "by_a": {}}
     for i, a in enumerate(avals):
@@ -581,6 +581,7 @@ def main():
     if not args.no_plain:
         p1 = dipmc.Lattice(L, l, 1, seed=5)
         p1.precompute_W(A_IMG, True)
+        p1.set_field_path(dipmc.MC_PATH_DIRECT)        # the FP32 CUDA-core path
         p1.set_params(*lad[0])
         p1.init_spins(2, s0[:1])
         p1.sweep(20, 1, stream)

@@ -149,9 +149,10 @@ int mc_set_schedule(mc_lattice *lat, int kind);
  * measured sweep.  MC_PATH_INCREMENTAL keeps the field at every site in shared
  * memory and adds W~ * delta of the accepted moves after each sub-step, so the
  * energy of a measured sweep is an O(L^2) sum over the kept field; the field is
- * re-evaluated from scratch every 8 sweeps.  MC_PATH_AUTO order: direct,
- * spectral, FFT, windowed (the incremental path is chosen explicitly or by
- * mc_autotune). */
+ * re-evaluated from scratch every 8 sweeps.  MC_PATH_AUTO order: tensor (where its
+ * window fits: L % 8 == 0, L/l in {1, 2, 4}, the spins of a replica in shared
+ * memory, i.e. L up to about 100), direct, spectral, FFT, windowed FP32 (the
+ * incremental path is chosen explicitly or by mc_autotune). */
 int mc_set_field_path(mc_lattice *lat, int path);
 
 /* Sub-steps per window of the windowed paths (must divide l^2; 0 = automatic). */

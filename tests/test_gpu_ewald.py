@@ -34,6 +34,7 @@ def test_ewald_in_a_handle_and_a_traced_sweep(dipmc):
     prm = (F32(1.0), F32(0.1), F32(0.8), F32(0.0), F32(0.6))
     with dipmc.Lattice(L, l, 1, seed) as lat:
         lat.precompute_W_ewald()
+        lat.set_field_path(dipmc.MC_PATH_DIRECT)   # the direct kernel
         Wg = lat.get_W()
         lat.set_params(*prm)
         lat.init_spins(2, s0)

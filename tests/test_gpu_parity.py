@@ -85,6 +85,7 @@ def _run_case(dipmc, L, l, R, proposal, schedule, nsw, A, params):
     s0 = inputs.random_spins(L, R, seed=L * 31 + l)
     with dipmc.Lattice(L, l, R, seed) as lat:
         lat.precompute_W(A, True)
+        lat.set_field_path(dipmc.MC_PATH_DIRECT)   # the direct kernel
         lat.set_proposal(proposal, 0.5)
         lat.set_schedule(schedule)
         for r, (J, CD, K2, K4, T) in enumerate(params):
@@ -133,6 +134,7 @@ def test_l_equals_L_gpu_matches_exact_sequential(dipmc):
     J, CD, K2, K4, T = F32(1.0), F32(0.5), F32(0.8), F32(0.2), F32(0.7)
     with dipmc.Lattice(L, L, 1, 5) as lat:
         lat.precompute_W(16, True)
+        lat.set_field_path(dipmc.MC_PATH_DIRECT)   # the direct kernel
         lat.set_params(J, CD, K2, K4, T)
         lat.init_spins(2, s0)
         tr = lat.sweep_trace(3)
@@ -156,6 +158,7 @@ def test_observables_statistically_match_oracle(dipmc, T):
     s0 = inputs.saturated_z(L, 1)
     with dipmc.Lattice(L, l, 1, 11) as lat:
         lat.precompute_W(64, True)
+        lat.set_field_path(dipmc.MC_PATH_DIRECT)   # the direct kernel
         lat.set_params(J, CD, K2, K4, T)
         lat.init_spins(2, s0)
         lat.sweep(warm_sw, 0)
@@ -184,6 +187,7 @@ def test_determinism_checkpoint_and_batch_invariance(dipmc):
     def make(R):
         lat = dipmc.Lattice(L, l, R, 42)
         lat.precompute_W(16, True)
+        lat.set_field_path(dipmc.MC_PATH_DIRECT)   # the direct kernel
         lat.init_spins(0)
         return lat
     with make(3) as a, make(3) as b, make(1) as c:
@@ -209,6 +213,7 @@ def test_observables_batch_equals_single_reads(dipmc):
     L, l, R = 16, 8, 5
     with dipmc.Lattice(L, l, R, 9) as lat:
         lat.precompute_W(16, True)
+        lat.set_field_path(dipmc.MC_PATH_DIRECT)   # the direct kernel
         for r in range(R):
             lat.set_params(F32(1.0), F32(0.1), F32(0.8), F32(0.0), F32(0.4 + 0.2 * r), replica=r)
         lat.init_spins(0)
@@ -269,6 +274,7 @@ def test_bench_configuration_sampled_replicas(dipmc):
     s0 = inputs.random_spins(L, R, seed=2024)
     with dipmc.Lattice(L, l, R, seed) as lat:
         lat.precompute_W(A, True)
+        lat.set_field_path(dipmc.MC_PATH_DIRECT)   # the direct kernel
         for r, prm in enumerate(lad):
             lat.set_params(*prm, replica=r)
         lat.init_spins(2, s0)
@@ -303,6 +309,7 @@ def test_many_replica_instance_small_lattice(dipmc):
     s0 = inputs.random_spins(L, R, seed=5)
     with dipmc.Lattice(L, l, R, 8) as lat:
         lat.precompute_W(64, True)
+        lat.set_field_path(dipmc.MC_PATH_DIRECT)   # the direct kernel
         lat.init_spins(2, s0)
         tr = lat.sweep_trace(2)
     W = oracle_W(L, 64)

@@ -100,7 +100,7 @@ def test_packed_requests_equal_their_lone_runs(dipmc):
             assert info["state"] == dipmc.MC_REQ_DONE, info
             assert info["packed"] and info["sweeps_done"] == s["sweeps"]
             assert info["path"] == (dipmc.MC_PATH_SPECTRAL if s["L"] == 128 else dipmc.MC_PATH_DIRECT)
-            spins_lone, obs_lone = lone_run(dipmc, **s)
+            spins_lone, obs_lone = lone_run(dipmc, path=info["path"], **s)   # alone, on the pack's path
             np.testing.assert_array_equal(srv.spins(rid), spins_lone)
             for r in range(s.get("replicas", 1)):
                 same_obs(srv.collect(rid, r), obs_lone[r])
@@ -112,7 +112,7 @@ def test_packed_requests_equal_their_lone_runs(dipmc):
 @gpu
 def test_lone_handle_requests_equal_their_lone_runs(dipmc):
     """Requests with more replicas than a pack holds run on pooled lone handles
-    (direct path at L = 64, spectral path at L = 256) beside a pack and match their
+    (tensor path at L = 64, spectral path at L = 256) beside a pack and match their
     lone runs; a later request of the same shape reuses a pooled handle.  A
     shape no path serves (L = 96, l = 2: L/l = 48) fails alone, with its reason,
     and stops nothing."""
@@ -132,7 +132,7 @@ def test_lone_handle_requests_equal_their_lone_runs(dipmc):
             info = srv.info(rid)
             assert info["state"] == dipmc.MC_REQ_DONE, info
             assert info["packed"] == (s["L"] == 32)
-            spins_lone, obs_lone = lone_run(dipmc, **s)
+            spins_lone, obs_lone = lone_run(dipmc, path=info["path"], **s)
             np.testing.assert_array_equal(srv.spins(rid), spins_lone)
             for r in (0, s.get("replicas", 1) - 1):
                 same_obs(srv.collect(rid, r), obs_lone[r])
@@ -192,7 +192,7 @@ def test_release_frees_slots_for_the_next_request(dipmc):
         assert srv.stats()["running"] == 0
         rid = srv.submit(L=32, l=8, T=0.5, sweeps=12, seed=42)
         srv.run_until_done([rid], timeout_s=120)
-        spins_lone, obs_lone = lone_run(dipmc, L=32, l=8, T=0.5, sweeps=12, seed=42)
+        spins_lone, obs_lone = lone_run(dipmc, L=32, l=8, T=0.5, sweeps=12, seed=42, path=srv.info(rid)["path"])
         np.testing.assert_array_equal(srv.spins(rid), spins_lone)
         same_obs(srv.collect(rid), obs_lone[0])
         srv.release(rid)
