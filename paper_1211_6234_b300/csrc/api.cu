@@ -323,6 +323,7 @@ int check_device_flag(mc_lattice *p) {
     CK(cudaMemcpy(&v, p->err_flag, sizeof v, cudaMemcpyDeviceToHost));
     if (v) {
         cudaMemset(p->err_flag, 0, sizeof v);
+        if (v == 2) return fail(MC_ECUDA, "tensor-core field: shared-memory stages not 1024-byte aligned; results invalid");
         return fail(MC_ETIMEOUT, "a tensor-core pipeline wait timed out; results of the last sweep are invalid");
     }
     return MC_OK;

@@ -70,7 +70,19 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo = 128u
 
 // B tile as the TMA boxes leave it: core-matrix column kc (8 K-elements of all
 // NT rows) at kc * NT * 16 bytes, 8-row groups 128 bytes apart.
-__device__ __forceinline__ uint32_t bcol_off(int NT, int kc) { return (uint32_t)(kc * NT * 16); }
+// B tiles (NT rows of kKB = 32 bf16 = 64 bytes, K-major) in the 64-byte swizzled layout
+// that the TMA writes with CU_TENSOR_MAP_SWIZZLE_64B: 8-row groups of 512 bytes, the
+// 16-byte chunk index of a row XORed with (row / 2) % 4.  The descriptor's start address
+// steps by 32 bytes per 16-element K slice; the tile base is 512-byte aligned.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);          // start address
+    d |= (uint64_t)1 << 16;                           // leading byte offset (unused when swizzled)
+    d |= (uint64_t)(512u >> 4) << 32;                 // stride byte offset: 8 rows x 64 bytes
+    d |= (uint64_t)1 << 46;                           // descriptor version for tcgen05
+    d |= (uint64_t)4 << 61;                           // layout: 64-byte swizzle
+    return d;
+}
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *m, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
@@ -199,6 +211,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a,
     volatile int *abort = &abort_s;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     pdl_trigger();
+    if (smem_u32(smem) & 1023u) {          // the swizzled B tiles need aligned stages
+        if (tid == 0) atomicExch(a.error, 2);
+        return;
+    }
 
     // ---- this CTA's unit: M-tile, N-tile, K-block range
     const TcUnit u = a.units[blockIdx.x];
@@ -342,12 +358,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a,
                     kofs = (zz ? 2 * N : 0) + kk;
                 }
                 const uint32_t sBhi = smem_u32(smem + s * kStage) + 2 * kTileA, sBlo = sBhi + kTileB;
-                mbar_expect_tx(&bfull[s], (uint32_t)(2 * kKC * nrows_b * 16));
-#pragma unroll
-                for (int kc = 0; kc < kKC; ++kc) {
-                    tma_load_2d(sBhi + bcol_off(nrows_b, kc), &tm_hi, kofs + kc * 8, n0, &bfull[s]);
-                    tma_load_2d(sBlo + bcol_off(nrows_b, kc), &tm_lo, kofs + kc * 8, n0, &bfull[s]);
-                }
+                mbar_expect_tx(&bfull[s], (uint32_t)(2 * nrows_b * kKB * 2));
+                tma_load_2d(sBhi, &tm_hi, kofs, n0, &bfull[s]);   // one 64-byte swizzled box row per replica
+                tma_load_2d(sBlo, &tm_lo, kofs, n0, &bfull[s]);
                 issued = i + 1;
             }
             // every issued copy lands before the CTA may leave (each slot's latest use)
@@ -358,7 +371,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a,
     } else if (warp == 0) {
         if (lane == 0) {
             // ---- MMAs: stage i once both operands landed; the commit frees the slot
-            const uint32_t blbo = (uint32_t)(nrows_b * 16);   // K-adjacent core matrices of B
             for (int i = 0; i < nkb; ++i) {
                 const int s = i % kStages;
                 const uint32_t par = (uint32_t)((i / kStages) & 1);
@@ -372,11 +384,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a,
 #pragma unroll
                 for (int ks = 0; ks < kKB / 16; ++ks) {
                     const uint32_t ko = ks * 256;        // A: 16 K elements = 2 core matrices = 256 B
-                    const uint32_t kb = ks * 2 * blbo;   // B: 2 core-matrix columns
+                    const uint32_t kb = ks * 32;         // B: 16 K elements of a 64-byte swizzled row
                     const uint32_t acc0 = (i > 0 || ks > 0) ? 1u : 0u;
-                    umma_bf16(tmem, smem_desc(ah + ko), smem_desc(bh + kb, blbo, 128u), idesc, acc0);
-                    umma_bf16(tmem, smem_desc(ah + ko), smem_desc(blo + kb, blbo, 128u), idesc, 1u);
-                    umma_bf16(tmem, smem_desc(alo + ko), smem_desc(bh + kb, blbo, 128u), idesc, 1u);
+                    umma_bf16(tmem, smem_desc(ah + ko), smem_desc_sw64(bh + kb), idesc, acc0);
+                    umma_bf16(tmem, smem_desc(ah + ko), smem_desc_sw64(blo + kb), idesc, 1u);
+                    umma_bf16(tmem, smem_desc(alo + ko), smem_desc_sw64(bh + kb), idesc, 1u);
                 }
                 umma_commit(&empty[s]);
             }
@@ -585,7 +597,8 @@ int tc_plan(int L, int Sw, int R, int nsm, TcUnit *units, int max_units, int *NT
     return nu;
 }
 
-// 2D tensor map of a [R][3N] bf16 spin array: boxes of 8 elements x NT rows.  The
+// 2D tensor map of a [R][3N] bf16 spin (or spectra) array: boxes of kKB = 32 elements
+// (64 bytes) x NT rows, written to shared memory in the 64-byte swizzled layout.  The
 // driver's encoder is reached through the runtime's entry-point query, so the
 // library does not link libcuda and loads on hosts without a driver.
 int tc_encode_map(void *map, const __nv_bfloat16 *spins, int L, int R, int NT) {
@@ -600,11 +613,11 @@ int tc_encode_map(void *map, const __nv_bfloat16 *spins, int L, int R, int NT) {
     }
     const cuuint64_t dims[2] = {(cuuint64_t)3 * L * L, (cuuint64_t)R};
     const cuuint64_t strides[1] = {(cuuint64_t)3 * L * L * sizeof(__nv_bfloat16)};
-    const cuuint32_t box[2] = {8u, (cuuint32_t)NT};
+    const cuuint32_t box[2] = {(cuuint32_t)kKB, (cuuint32_t)NT};
     const cuuint32_t estr[2] = {1u, 1u};
     const CUresult r = encode(static_cast<CUtensorMap *>(map), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
                                               const_cast<__nv_bfloat16 *>(spins), dims, strides, box, estr,
-                                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? 0 : -1;
 }

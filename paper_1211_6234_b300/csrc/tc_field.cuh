@@ -32,7 +32,7 @@ struct TcFieldArgs {
     const __nv_bfloat16 *wsh;            // tc_wsh_elems(L): shifted hi/lo copies of W~
     const __nv_bfloat16 *spins_hi;       // [R][3][N]
     const __nv_bfloat16 *spins_lo;       // [R][3][N]
-    int *error;                          // set to 1 if a bounded wait gave up
+    int *error;                          // set to 1 if a bounded wait gave up, 2 if the stages are misaligned
     float *part;                         // [nunits][NT][128]: each unit's partial tile, row fastest
     const int *tile_first;               // [ntiles * mtiles + 1]: first unit of tile (nt, mt)
     int mtiles, ntiles;

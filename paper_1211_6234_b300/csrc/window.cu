@@ -214,36 +214,6 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
         return make_float3((a.x + bb.x) + (c.x + dd.x), (a.y + bb.y) + (c.y + dd.y), (a.z + bb.z) + (c.z + dd.z));
     };
 
-    // sums of the split-K partial tiles of four output rows of this replica's column,
-    // each in unit order (the tensor-core field's reduction), eight units of every row
-    // in flight at a time
-    auto row_sum4 = [&](const int (&row)[4], float (&h)[4]) {
-        const int nt = r / cfg.NT, col = r - nt * cfg.NT;
-        const size_t ustride = (size_t)cfg.NT * 128;
-        const float *pc[4];
-        int cnt[4], cmax = 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int mt = row[k] >> 7;
-            const int u0 = buf.tile_first[nt * cfg.mtiles + mt], u1 = buf.tile_first[nt * cfg.mtiles + mt + 1];
-            pc[k] = buf.part + ((size_t)u0 * cfg.NT + col) * 128 + (row[k] & 127);
-            cnt[k] = u1 - u0;
-            cmax = max(cmax, cnt[k]);
-            h[k] = 0.f;
-        }
-        for (int j0 = 0; j0 < cmax; j0 += 8) {
-            float v[4][8];
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) v[k][j] = (j0 + j < cnt[k]) ? __ldcg(pc[k] + (size_t)(j0 + j) * ustride) : 0.f;
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    if (j0 + j < cnt[k]) h[k] += v[k][j];
-        }
-    };
     // stale_mode 3 (spectra of the window's offsets, L = 2l): the field of site
     // 4j + d, d = Dx + 2 Dy, is (1/4) sum_kappa (-1)^(kappa.D) H_j(kappa); it is staged
     // in shared memory (PRE: after dacc; otherwise in hcur) before the per-site set-up
@@ -298,18 +268,72 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
 #pragma unroll 4
     for (int i = tid; i < hq * hq; i += kWThreads) wq[i] = buf.wq[i];
     for (int s = tid; s < Sw; s += kWThreads) wxy[s] = window_site_xy(l, C, key, t, cfg.schedule, rk, k0, s);
+    // stale_mode 3: warp mt sums M-tile mt of this replica's column over the tile's units
+    // (six M-tiles of 128 rows); the work plan is fixed when the buffers are set up
+    const int st_mt = warp, st_f = lane;
+    int st_u0 = 0, st_cnt = 0;
+    if (cfg.stale_mode == 3 && st_mt < cfg.mtiles) {
+        const int nt = r / cfg.NT;
+        st_u0 = buf.tile_first[nt * cfg.mtiles + st_mt];
+        st_cnt = buf.tile_first[nt * cfg.mtiles + st_mt + 1] - st_u0;
+    }
     pdl_wait();
+    // the loads of the split-K partial tiles (stale_mode 3: lane f of warp mt takes rows
+    // 4f .. 4f+3 of M-tile mt, one 16-byte load of each unit's 512-byte column segment)
+    // and of the spins go out together
+    const bool st_on = cfg.stale_mode == 3 && st_mt < cfg.mtiles;
+    const size_t ustride = (size_t)cfg.NT * 32;   // float4 per unit
+    const float4 *pc = nullptr;
+    constexpr int kPV = 8;    // units whose loads go out at once
+    float4 pv[kPV];
+    if (st_on) {
+        const int col = r - (r / cfg.NT) * cfg.NT;
+        pc = reinterpret_cast<const float4 *>(buf.part + ((size_t)st_u0 * cfg.NT + col) * 128) + st_f;
+#pragma unroll
+        for (int j = 0; j < kPV; ++j) pv[j] = (j < st_cnt) ? __ldcg(pc + (size_t)j * ustride) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const float *gs = buf.spins + (size_t)r * 3 * N;
+#pragma unroll 8
+    for (int q = tid; q < N; q += kWThreads) s4[q] = make_float4(gs[q], gs[N + q], gs[2 * N + q], 0.0f);
     if (cfg.stale_mode == 3) {
+        // split-K sums in unit order (the tensor-core field's reduction) into rs[row]
+        // (scratch in the pair-table space, which is filled later)
+        float *rs = reinterpret_cast<float *>(etab);
+        if (st_on) {
+            float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < kPV; ++j)
+                if (j < st_cnt) {
+                    h.x += pv[j].x;
+                    h.y += pv[j].y;
+                    h.z += pv[j].z;
+                    h.w += pv[j].w;
+                }
+            for (int j0 = kPV; j0 < st_cnt; j0 += 8) {
+                float4 v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    v[j] = (j0 + j < st_cnt) ? __ldcg(pc + (size_t)(j0 + j) * ustride) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (j0 + j < st_cnt) {
+                        h.x += v[j].x;
+                        h.y += v[j].y;
+                        h.z += v[j].z;
+                        h.w += v[j].w;
+                    }
+            }
+            reinterpret_cast<float4 *>(rs)[st_mt * 32 + st_f] = h;
+        }
+        __syncthreads();
         // rows kappa*2B + b*B + j (b = x, y) and 2 S_w + (kappa/2)*2B + (kappa%2)*B + j (z), B = S_w/4
         const int B4 = Sw >> 2;
         for (int task = tid; task < 3 * B4; task += kWThreads) {
             const int j = task / 3, bb = task - 3 * j;
-            int rows[4];
+            float H[4];
 #pragma unroll
             for (int kap = 0; kap < 4; ++kap)
-                rows[kap] = bb < 2 ? kap * 2 * B4 + bb * B4 + j : 2 * Sw + (kap >> 1) * 2 * B4 + (kap & 1) * B4 + j;
-            float H[4];
-            row_sum4(rows, H);
+                H[kap] = rs[bb < 2 ? kap * 2 * B4 + bb * B4 + j : 2 * Sw + (kap >> 1) * 2 * B4 + (kap & 1) * B4 + j];
 #pragma unroll
             for (int d = 0; d < 4; ++d) {
                 float h = 0.f;
@@ -321,9 +345,6 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
             }
         }
     }
-    const float *gs = buf.spins + (size_t)r * 3 * N;
-#pragma unroll 4
-    for (int q = tid; q < N; q += kWThreads) s4[q] = make_float4(gs[q], gs[N + q], gs[2 * N + q], 0.0f);
     __syncthreads();
     for (int s = tid; s < Sw; s += kWThreads) {
         const int xy = wxy[s];
@@ -685,9 +706,27 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
         }
     }
     // ---- exact energy change of the window: accepted dE plus, per sub-step, the
-    // neglected cross terms C_D d_p.W~(q - p).d_q of its simultaneous moves (Sec. 3.2)
+    // neglected cross terms C_D d_p.W~(q - p).d_q of its simultaneous moves (Sec. 3.2).
+    // PRE: a thread per accepted site and per site pair of a sub-step; otherwise a thread
+    // per sub-step
     double e_loc = 0.0;
-    for (int j = tid; j < B; j += kWThreads) {
+    if (PRE) {
+        float e_f = 0.0f;   // a few terms per thread
+        for (int s = tid; s < Sw; s += kWThreads)
+            if (wxy[s] < 0) e_f += pS[s].w;
+        for (int task = tid; task < B * n * n; task += kWThreads) {
+            const int j = task / (n * n), rem = task - j * n * n, d = rem / n, dp = rem - d * n;
+            if (dp >= d) continue;
+            const int xy = wxy[j * n + d], pxy = wxy[j * n + dp];
+            if (xy >= 0 || pxy >= 0) continue;
+            const float4 m = pd[j * n + d], mp = pd[j * n + dp];
+            const float3 Wd = wq_apply(wq, L, (xy & 0xFFFF) - (pxy & 0xFFFF), ((xy >> 16) & 0x7FFF) - ((pxy >> 16) & 0x7FFF),
+                                       make_float3(m.x, m.y, m.z));
+            e_f += P.CD * (mp.x * Wd.x + mp.y * Wd.y + mp.z * Wd.z);
+        }
+        e_loc = (double)e_f;
+    }
+    for (int j = tid; !PRE && j < B; j += kWThreads) {
         float sub = 0.0f;
         for (int d = 0; d < n; ++d) {
             const int s = j * n + d;
