@@ -208,6 +208,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a,
     __shared__ uint64_t done;                // every MMA of the unit completed
     __shared__ uint32_t tmem_base_s;
     __shared__ int abort_s;
+    __shared__ int2 s_rinfo[kProducers];     // spectra: per tile row, offset x | y << 16 and kappa | b << 2
     volatile int *abort = &abort_s;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     pdl_trigger();
@@ -230,6 +231,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a,
     const bool producer = warp >= kProdWarp0;
     const int arow = tid - kProdWarp0 * 32;
     int my_b = 0, my_qx = 0, my_qy = 0, my_kap = 0;
+    int sp_xy[4] = {0, 0, 0, 0}, sp_kb[4] = {0, 0, 0, 0};   // spectra: rows arow / 4 + 32 m
     if (producer) {
         const int my_row = row0 + arow;
         int slot;                                    // window site (Toeplitz) or first site of the offset (spectra)
@@ -254,6 +256,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a,
         const int xy = window_site_xy(a.l, L / a.l, a.key, t, a.schedule, rk, a.k0, slot);
         my_qx = xy & 0xFFFF;                         // spectra: the offset (ox, oy) of the row's sub-step
         my_qy = xy >> 16;
+        if (a.spec2) {
+            // spectra rows are copied four lanes to a row (each lane one 16-byte chunk of the
+            // row's 64 bytes, so a warp's copies touch 8 rows instead of 32): lane arow takes
+            // rows arow / 4 + 32 m, m = 0..3, at chunk arow % 4
+            s_rinfo[arow] = make_int2(xy, my_kap | (my_b << 2));
+            asm volatile("bar.sync 1, %0;" ::"n"(kProducers) : "memory");
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int2 ri = s_rinfo[(arow >> 2) + 32 * m];
+                sp_xy[m] = ri.x;
+                sp_kb[m] = ri.y;
+            }
+        }
     }
     if (warp == 0) {
         // TMEM accumulator: 128 lanes x NT fp32 columns (allocation is a power of 2 >= 32)
@@ -295,21 +310,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a,
                 // offsets in the order e' = ey*l + (l-1-ex), so each 8-run is ascending in i)
                 const int l = a.l, lsq = l * l, l2 = 2 * l;
                 const int part = k0 >= lsq;                    // in-plane: input component; zz: kappa of the pair
-                const int e0 = k0 - part * lsq;
-                const int comp = my_b == 2 ? 3 : (part == 0 ? comp_a0 : comp_a1);
-                const uint32_t bytes = (my_b == 2 && part != (my_kap & 1)) ? 0u : 16u;   // zz rows: own kappa only
+                const int kc = arow & 3;
+                const int e = k0 - part * lsq + 8 * kc, ey = e / l, exq = e - ey * l;
                 const size_t cstride = (size_t)4 * 4 * 2 * 2 * l * l2;
 #pragma unroll
-                for (int kc = 0; kc < kKC; ++kc) {
-                    const int e = e0 + 8 * kc, ey = e / l, exq = e - ey * l;
-                    int dy = my_qy - ey;
+                for (int m = 0; m < 4; ++m) {
+                    const int kap = sp_kb[m] & 3, b = sp_kb[m] >> 2;
+                    const int comp = b == 2 ? 3 : b + part;   // (b, a): xx, xy | xy, yy; zz
+                    const uint32_t bytes = (b == 2 && part != (kap & 1)) ? 0u : 16u;   // zz rows: own kappa only
+                    int dy = (sp_xy[m] >> 16) - ey;
                     const int sy = dy < 0;
                     dy += sy ? l : 0;
-                    const int i0 = my_qx + 1 + exq, c = i0 & 7;
+                    const int i0 = (sp_xy[m] & 0xFFFF) + 1 + exq, c = i0 & 7;
                     const size_t off = (size_t)c * cstride +
-                                       ((((size_t)my_kap * 4 + comp) * 2 + sy) * 2) * l * l2 + (size_t)dy * l2 + (i0 - c);
-                    cp_async16(sAhi + core_off(arow, kc), a.wsh + off, bytes);
-                    cp_async16(sAlo + core_off(arow, kc), a.wsh + off + (size_t)l * l2, bytes);
+                                       ((((size_t)kap * 4 + comp) * 2 + sy) * 2) * l * l2 + (size_t)dy * l2 + (i0 - c);
+                    const int ar = (arow >> 2) + 32 * m;
+                    cp_async16(sAhi + core_off(ar, kc), a.wsh + off, bytes);
+                    cp_async16(sAlo + core_off(ar, kc), a.wsh + off + (size_t)l * l2, bytes);
                 }
                 cp_async_arrive(&afull[s]);
                 continue;
