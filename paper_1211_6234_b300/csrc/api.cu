@@ -97,8 +97,6 @@ struct mc_lattice {
     // sub-lattice spectral path
     float2 *specT = nullptr, *specS = nullptr, *specH = nullptr;
     int *specOff = nullptr;
-    cudaStream_t spec_aux = nullptr;      // the update lane of the pipelined sub-steps
-    cudaEvent_t spec_evF = nullptr, spec_evU[2] = {nullptr, nullptr};
     bool spec_ready = false;
     int spec_esplit = 0;
     // CUDA graphs of the multi-launch paths, keyed by (path, nsweeps, measure_every)
@@ -160,10 +158,6 @@ void free_all(mc_lattice *p) {
     cudaFree(p->specS);
     cudaFree(p->specH);
     cudaFree(p->specOff);
-    if (p->spec_aux) cudaStreamDestroy(p->spec_aux);
-    if (p->spec_evF) cudaEventDestroy(p->spec_evF);
-    for (cudaEvent_t ev : p->spec_evU)
-        if (ev) cudaEventDestroy(ev);
     cudaFree(p->slots_dev);
     if (p->slots_pin) cudaFreeHost(p->slots_pin);
     if (p->params_pin) cudaFreeHost(p->params_pin);
@@ -548,14 +542,9 @@ int ensure_spectral(mc_lattice *p, cudaStream_t st) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int es = spectral_esplit(p->L, p->l, p->R, nsm);
-    if (!p->specT) CKA(cudaMalloc(&p->specT, sizeof(float2) * 4 * (size_t)p->N()));
+    if (!p->specT) CKA(cudaMalloc(&p->specT, sizeof(float2) * 16 * (size_t)p->N()));
     if (!p->specS) CKA(cudaMalloc(&p->specS, sizeof(float2) * spectral_S_elems(p->L, p->R)));
     if (!p->specOff) CKA(cudaMalloc(&p->specOff, sizeof(int) * (size_t)p->R * p->l * p->l));
-    if (!p->spec_aux) {
-        CKA(cudaStreamCreateWithFlags(&p->spec_aux, cudaStreamNonBlocking));
-        CKA(cudaEventCreateWithFlags(&p->spec_evF, cudaEventDisableTiming));
-        for (cudaEvent_t &ev : p->spec_evU) CKA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    }
     if (p->spec_esplit != es) {
         cudaFree(p->specH);
         p->specH = nullptr;
@@ -571,7 +560,7 @@ int ensure_spectral(mc_lattice *p, cudaStream_t st) {
 }
 
 // Sub-lattice spectral path: spectra of every offset from the spins, then per
-// sub-step the field spectra at the sub-step's sites and the update; the energy
+// window of sub-steps the field spectra at its offsets and the update; the energy
 // and observables from a full field at measured sweeps (as the FFT path).
 int run_spectral(mc_lattice *p, int nsweeps, int measure_every, float *trace, cudaStream_t st) {
     int rc = ensure_spectral(p, st);
@@ -592,46 +581,33 @@ int run_spectral(mc_lattice *p, int nsweeps, int measure_every, float *trace, cu
     b.W32 = p->W32; b.spins = p->spins; b.params = p->dparams; b.obs = p->obs; b.trace = trace;
     b.slots = p->packed ? p->slots_dev : nullptr;
     b.T = p->specT; b.S = p->specS; b.off = p->specOff;
-    const size_t hbuf = spectral_part_elems(p->L, p->l, p->R, c.esplit) / 2;
+    c.wmax = spectral_window(p->L, p->l);
+    b.Hw = p->specH;
     cudaError_t e = launch_spec_init(p->L, p->l, p->R, p->spins, p->specS, st);
     if (e != cudaSuccess) return cuda_fail(e, "spectra of the spin sub-lattices");
-    // Two lanes: the contraction of sub-step k runs on st, the update on spec_aux.
-    // F_k waits for U_{k-2} (it reads the S that update wrote and refills the
-    // partial buffer that update read); U_k waits for F_k and, by lane order,
-    // for U_{k-1}.  F_k leaves out the offset U_{k-1} updated; U_{k-1} adds it.
-    cudaStream_t su = p->spec_aux;
+    // Per window of wmax sub-steps: the field spectra of its offsets from the spectra
+    // at its start, then the update, which adds the window's own changes sub-step by
+    // sub-step.
     bool measured_last = false;
     for (int it = 0; it < nsweeps; ++it) {
         c.t = (uint32_t)(p->t + (uint64_t)it);
         c.it = it;
         e = launch_spec_offsets(c, b, st);
         if (e != cudaSuccess) return cuda_fail(e, "sub-step offsets");
-        CKA(cudaEventRecord(p->spec_evU[0], st));   // the lanes start from the same point each sweep
-        CKA(cudaEventRecord(p->spec_evU[1], st));
-        CKA(cudaStreamWaitEvent(su, p->spec_evU[0], 0));
-        for (int k = 0; k < ll; ++k) {
-            c.k = k;
-            c.skip_prev = k > 0;
-            c.extra_in = k > 0;
-            c.extra_out = k + 1 < ll;
-            b.Hpart = p->specH + (size_t)(k & 1) * hbuf;
-            b.Hnext = p->specH + (size_t)((k + 1) & 1) * hbuf;
-            CKA(cudaStreamWaitEvent(st, p->spec_evU[k & 1], 0));     // U_{k-2}
+        for (int k0 = 0; k0 < ll; k0 += c.wmax) {
+            c.k = k0;
+            c.wlen = std::min(c.wmax, ll - k0);
             {
                 TimedLaunch tl(p, MC_K_SPEC_FIELD, st);
-                e = launch_spec_field(c, b, st);
+                e = launch_spec_wfield(c, b, st);
             }
             if (e != cudaSuccess) return cuda_fail(e, "spectral field");
-            CKA(cudaEventRecord(p->spec_evF, st));
-            CKA(cudaStreamWaitEvent(su, p->spec_evF, 0));
             {
-                TimedLaunch tl(p, MC_K_SPEC_UPDATE, su);
-                e = launch_spec_update(c, b, su);
+                TimedLaunch tl(p, MC_K_SPEC_UPDATE, st);
+                e = launch_spec_wupdate(c, b, st);
             }
             if (e != cudaSuccess) return cuda_fail(e, "spectral update");
-            CKA(cudaEventRecord(p->spec_evU[k & 1], su));
         }
-        CKA(cudaStreamWaitEvent(st, p->spec_evU[(ll - 1) & 1], 0));   // join: the sweep is done
         measured_last = measure_every > 0 && (b.slots || ((it + 1) % measure_every) == 0);
         if (measured_last) {
             rc = full_field(p, st);
@@ -1411,7 +1387,7 @@ size_t lattice_footprint(int L, int l, int R) {
         b += sizeof(float) * 4 * N + fft_scratch_bytes(L, R) + sizeof(double2) * 4 * N;
     if ((!direct_supported(L, l) || L >= 128) && spectral_supported(L, l)) {
         const int es = spectral_esplit(L, l, R, 148);
-        b += sizeof(float2) * (4 * N + spectral_S_elems(L, R) + spectral_part_elems(L, l, R, std::max(es, 16)));
+        b += sizeof(float2) * (16 * N + spectral_S_elems(L, R) + spectral_part_elems(L, l, R, std::max(es, 16)));
     }
     return b + 4096;
 }

@@ -15,17 +15,17 @@
 // spins.  A sub-step therefore costs O(N) -- the contraction over e -- instead
 // of the O(N n) of a direct sum or the O(N log N) of a full-lattice FFT.
 //
-// Kernels per sub-step: k_spec_field (contraction; grid over (replica, K)
-// pairs and chunks of e, partial spectra reduced in a fixed order) and
-// k_spec_update (one CTA per replica: inverse DFT, Metropolis decisions,
-// forward DFT of the updated sub-lattice).  DFTs are separable direct sums in
-// shared memory (C <= 32).  T is built once in FP64.
-//
-// Pipelining: the contraction of sub-step k+1 needs every S_e, but only S_o of
-// the offset o updated in sub-step k changes; so it leaves that e out and runs
-// concurrently with the update of sub-step k, which, once it has the new S_o,
-// adds that single term T_{(o' - o) mod l} S_o of the next offset o' as one
-// more partial chunk.  Partial spectra are double-buffered by sub-step parity.
+// Windows of wmax sub-steps: k_spec_wfield contracts, once per window, the spectra
+// at the window's start against T for all of the window's offsets (grid over
+// (replica, K, window slot) and chunks of e, partial spectra summed in a fixed
+// order), so that every S_e is read once per window instead of once per sub-step.
+// k_spec_wupdate (one CTA per replica) then runs the window's sub-steps in order:
+// since only S_o of the updated offset o changes in a sub-step, the spectra of a
+// later sub-step are its window-start spectra plus the terms
+// omega^(K.sigma) T_{(o' - o) mod l}(K) dS_o(K) of the window's earlier changes
+// dS_o; then the inverse DFT, Metropolis decisions and the forward DFT of the
+// updated sub-lattice.  DFTs are separable direct sums in shared memory (C <= 32).
+// T is built once in FP64.
 #include <algorithm>
 
 #include "spectral.cuh"
@@ -37,6 +37,7 @@ namespace {
 constexpr int kSpecThreads = 256;
 constexpr int kUpdMaxThreads = 1024;
 constexpr int kSpecMaxC = 32;
+constexpr int kSpecWinMax = 8;    // sub-steps of a window (k_spec_wfield: one warp each)
 
 // x / d by a multiply-high with m = ceil(2^32 / d): exact while x * d < 2^32
 // (here x < 3 n <= 3072, d <= 1024)
@@ -149,6 +150,8 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec_table(int L, int l, const
         U[i] = make_double2(re, im);
     }
     __syncthreads();
+    // four copies with the wrap phase omega^(K.sigma) applied, sigma = (sx, sy), copy sx + 2 sy
+    const size_t csz = (size_t)l * l * 4 * n;
     float2 *out = T + ((size_t)d * 4 + c) * n;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int Ky = i / C, Kx = i % C;
@@ -158,7 +161,11 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec_table(int L, int l, const
             re += u.x * o.x - u.y * o.y;
             im += u.x * o.y + u.y * o.x;
         }
-        out[i] = make_float2((float)re, (float)im);
+#pragma unroll
+        for (int sg = 0; sg < 4; ++sg) {
+            const double2 p = tw[((sg & 1) * Kx + (sg >> 1) * Ky) % C];
+            out[sg * csz + i] = make_float2((float)(re * p.x - im * p.y), (float)(re * p.y + im * p.x));
+        }
     }
 }
 
@@ -217,54 +224,41 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec_init(int L, int l, const 
 }
 
 // ---------------------------------------------------------------------------
-// Partial field spectra: thread = (replica r, wave vector K) x a slice of the
-// cell offsets e; the 8 warps of a CTA take interleaved e of the CTA's chunk and
-// are summed in a fixed order.
+// A window is wlen <= wmax consecutive sub-steps k .. k + wlen - 1.
+//
+// k_spec_wfield: the field spectra of the window's offsets o_w from the spectra at
+// the window's start, H_w(K) = sum_e omega^(K.sigma) T_{(o_w - e) mod l}(K) S_e(K).
+// Thread = (replica r, wave vector K, window slot w) over a chunk of the cell
+// offsets e (grid z); warp w of a CTA is slot w for 4 replicas x 8 wave vectors,
+// so the CTA's warps read the same S_e through L1.  Partial spectra per chunk,
+// Hw[z][r][w][3][n], are summed by the update in chunk order.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSpecThreads, 3) k_spec_field(const SpecConfig cfg, const SpecBuffers b) {
+__global__ void __launch_bounds__(kSpecThreads) k_spec_wfield(const SpecConfig cfg, const SpecBuffers b) {
     const int L = cfg.L, l = cfg.l, C = L / l, n = C * C, ll = l * l, R = cfg.R;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int j = blockIdx.x * 32 + lane;
-    const int rq = qdiv(j, cfg.mn);
-    const int r = j < R * n ? rq : 0, K = j < R * n ? j - rq * n : 0;
-    const int ov = j < R * n ? b.off[(size_t)r * ll + cfg.k] : -1;
-    const bool active = ov >= 0;
-    int eskip = -1;                                  // the previous sub-step's offset (added by its update)
-    if (active && cfg.skip_prev) {
-        const int pv = b.off[(size_t)r * ll + cfg.k - 1];
-        eskip = (pv >> 16) * l + (pv & 0xFFFF);
-    }
+    const int K = blockIdx.x * 8 + (lane & 7), r = blockIdx.y * 4 + (lane >> 3);
+    const bool mine = K < n && r < R && w < cfg.wlen;
+    const int ov = mine ? b.off[(size_t)r * ll + cfg.k + w] : -1;
     float2 hx = make_float2(0.f, 0.f), hy = hx, hz = hx;
-    if (active) {
+    if (ov >= 0) {
         const int ox = ov & 0xFFFF, oy = ov >> 16;
-        const int Ky = qdiv(K, cfg.mC), Kx = K - Ky * C;
-        const float2 ph1 = omega(Kx, C), ph2 = omega(Ky, C), ph3 = omega(Kx + Ky < C ? Kx + Ky : Kx + Ky - C, C);
-        const int ec = (ll + gridDim.y - 1) / gridDim.y;
-        const int e0 = blockIdx.y * ec, e1 = min(ll, e0 + ec);
+        const int ec = (ll + gridDim.z - 1) / gridDim.z;
+        const int e0 = blockIdx.z * ec, e1 = min(ll, e0 + ec);
         const float2 *Sr = b.S + (size_t)r * ll * 3 * n + K;
-        constexpr int kW = kSpecThreads / 32, kU = 2;  // warps; cell offsets in flight per warp
-        // cell offset (ex, ey) of e = eb + u * kW, stepped without divisions
-        int bx = (e0 + w) % l, by = (e0 + w) / l;
-        for (int eb = e0 + w; eb < e1; eb += kW * kU) {
+        int ex = e0 % l, ey = e0 / l;
+        constexpr int kU = 4;   // cell offsets in flight
+        for (int eb = e0; eb < e1; eb += kU) {
             float2 tv[kU][4], sv[kU][3];
-            int sg[kU];
-            int ex = bx, ey = by;
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
-                const int e = eb + u * kW;
-                sg[u] = 0;
-                if (u > 0) {
-                    ex += kW;
-                    while (ex >= l) { ex -= l; ++ey; }
-                }
-                if (e < e1 && e != eskip) {
+                if (eb + u < e1) {
                     int dx = ox - ex, dy = oy - ey;
                     const int sx = dx < 0, sy = dy < 0;
                     dx += sx ? l : 0;
                     dy += sy ? l : 0;
-                    sg[u] = sx + 2 * sy;
-                    const float2 *Tp = b.T + (size_t)(dy * l + dx) * 4 * n + K;
-                    const float2 *Sp = Sr + (size_t)e * 3 * n;
+                    // the table copy with the wrap phase omega^(K.sigma) applied
+                    const float2 *Tp = b.T + ((size_t)((sx + 2 * sy) * ll + dy * l + dx) * 4) * n + K;
+                    const float2 *Sp = Sr + (size_t)(eb + u) * 3 * n;
 #pragma unroll
                     for (int c = 0; c < 4; ++c) tv[u][c] = __ldg(Tp + c * n);
 #pragma unroll
@@ -275,257 +269,310 @@ __global__ void __launch_bounds__(kSpecThreads, 3) k_spec_field(const SpecConfig
 #pragma unroll
                     for (int c = 0; c < 3; ++c) sv[u][c] = make_float2(0.f, 0.f);
                 }
+                if (++ex == l) {
+                    ex = 0;
+                    ++ey;
+                }
             }
-            bx = ex + kW;
-            by = ey;
-            while (bx >= l) { bx -= l; ++by; }
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
-                const float2 p = sg[u] == 0 ? make_float2(1.f, 0.f) : sg[u] == 1 ? ph1 : sg[u] == 2 ? ph2 : ph3;
-                const float2 txx = cmul(tv[u][0], p), txy = cmul(tv[u][1], p);
-                const float2 tyy = cmul(tv[u][2], p), tzz = cmul(tv[u][3], p);
-                hx = cfma(txx, sv[u][0], cfma(txy, sv[u][1], hx));
-                hy = cfma(txy, sv[u][0], cfma(tyy, sv[u][1], hy));
-                hz = cfma(tzz, sv[u][2], hz);
+                hx = cfma(tv[u][0], sv[u][0], cfma(tv[u][1], sv[u][1], hx));
+                hy = cfma(tv[u][1], sv[u][0], cfma(tv[u][2], sv[u][1], hy));
+                hz = cfma(tv[u][3], sv[u][2], hz);
             }
         }
     }
-    __shared__ float2 red[kSpecThreads / 32][3][32];
-    red[w][0][lane] = hx;
-    red[w][1][lane] = hy;
-    red[w][2][lane] = hz;
-    __syncthreads();
-    if (active && w < 3) {
-        float2 acc = red[0][w][lane];
-        for (int v = 1; v < kSpecThreads / 32; ++v) {
-            acc.x += red[v][w][lane].x;
-            acc.y += red[v][w][lane].y;
-        }
-        b.Hpart[(((size_t)blockIdx.y * R + r) * 3 + w) * n + K] = acc;
+    if (mine) {
+        float2 *o = b.Hw + ((((size_t)blockIdx.z * R + r) * cfg.wmax + w) * 3) * n + K;
+        o[0] = hx;
+        o[n] = hy;
+        o[2 * n] = hz;
     }
 }
 
 // ---------------------------------------------------------------------------
-// Per replica: field at the n sites (inverse DFT of the summed partial spectra),
-// Metropolis decisions, new S of the updated offset.
+// k_spec_wupdate: one CTA per replica runs the window's sub-steps in order.  The
+// field spectra of sub-step w are its window-start spectra (the chunk sum of Hw)
+// plus, for every earlier sub-step v of the window, the term of the change of
+// S_{o_v}: omega^(K.sigma) T_{(o_w - o_v) mod l}(K) dS_v(K).  Then as a single
+// sub-step: inverse DFT to the n sites, Metropolis decisions, DFT of the updated
+// sub-lattice, whose change dS_w is kept for the later sub-steps.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kUpdMaxThreads) k_spec_update(const SpecConfig cfg, const SpecBuffers b) {
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT) k_spec_wupdate(const SpecConfig cfg, const SpecBuffers b) {
     const int L = cfg.L, l = cfg.l, C = L / l, n = C * C, ll = l * l, N = L * L, R = cfg.R;
     const int r = blockIdx.x, tid = threadIdx.x;
     uint2 key;
     uint32_t t, rid;
     if (!stream_state(cfg, b, r, key, t, rid)) return;  // whole block, before any barrier
-    const int ov = b.off[(size_t)r * ll + cfg.k];
-    const int ox = ov & 0xFFFF, oy = ov >> 16;
     extern __shared__ float2 sm_f2[];
     float2 *tw = sm_f2;                                          // [C]
-    float2 *H = tw + kSpecMaxC;                                  // [3][n] field spectra, later S_o
+    float2 *H = tw + kSpecMaxC;                                  // [3][n] field spectra
     float2 *U = H + 3 * n;                                       // [3][n]
-    float *hs = reinterpret_cast<float *>(U + 3 * n);            // [3][n] field at the sites
+    float2 *dS = U + 3 * n;                                      // [wmax][3][n] changes of S in the window
+    float *hs = reinterpret_cast<float *>(dS + (size_t)cfg.wmax * 3 * n);   // [3][n] field at the sites
     float *sn = hs + 3 * n;                                      // [3][n] spins after the update
-    __shared__ int s_acc;
+    __shared__ int s_acc, s_off[kSpecWinMax];
     if (tid == 0) s_acc = 0;
+    if (tid < cfg.wlen) s_off[tid] = b.off[(size_t)r * ll + cfg.k + tid];
     for (int m = tid; m < C; m += blockDim.x) tw[m] = omega(m, C);
-
-    // ---- everything that does not need the field, issued before the field arrives:
-    // thread d < n (blockDim >= n) owns site d: its spins, neighbours, proposal and
-    // the field-free part of dE
     float *s = b.spins + (size_t)r * 3 * N;
     const RepParams P = b.params[r];
-    const int d = tid;
-    const bool site = d < n;
-    int q = 0;
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, S0 = 0.f, S1 = 0.f, S2 = 0.f, pre = 0.f, thr = 0.f, uacc = 0.f;
-    if (site) {
-        const int dy_ = qdiv(d, cfg.mC);
-        const int qx = ox + l * (d - dy_ * C), qy = oy + l * dy_;
-        q = qy * L + qx;
-        const uint4 wds = philox(make_uint4((uint32_t)q, rid, t, ((uint32_t)cfg.k & 0x00FFFFFFu) | kTagAttempt), key);
-        const float u1 = u24f(wds.x);
-        uacc = u24f(wds.z);
-        float sps, cps;
-        sincospif(2.0f * u24f(wds.y), &sps, &cps);
-        s0 = s[q];
-        s1 = s[N + q];
-        s2 = s[2 * N + q];
-        const int xp = (qx + 1 == L) ? q - qx : q + 1;
-        const int xm = (qx == 0) ? q + L - 1 : q - 1;
-        const int yp = (qy + 1 == L) ? qx : q + L;
-        const int ym = (qy == 0) ? q + N - L : q - L;
-        const float n0 = (s[xp] + s[xm]) + (s[yp] + s[ym]);
-        const float n1 = (s[N + xp] + s[N + xm]) + (s[N + yp] + s[N + ym]);
-        const float n2 = (s[2 * N + xp] + s[2 * N + xm]) + (s[2 * N + yp] + s[2 * N + ym]);
-        if (cfg.proposal == kPropFlip) {            // Appendix B reversal
-            S0 = -s0;
-            S1 = -s1;
-            S2 = -s2;
-        } else if (cfg.proposal == kPropSphere) {
-            const float z = 2.0f * u1 - 1.0f;
-            const float rr = sqrtf(fmaxf(0.0f, (1.0f - z) * (1.0f + z)));
-            S0 = rr * cps;
-            S1 = rr * sps;
-            S2 = z;
-        } else {
-            const float omc = u1 * cfg.cap_c1;             // 1 - cos(alpha), no cancellation
-            const float ca = 1.0f - omc;
-            const float sa = sqrtf(fmaxf(0.0f, omc * (2.0f - omc)));
-            float3 b1, b2;
-            perp_basis_s(s0, s1, s2, b1, b2);
-            S0 = ca * s0 + sa * (cps * b1.x + sps * b2.x);
-            S1 = ca * s1 + sa * (cps * b1.y + sps * b2.y);
-            S2 = ca * s2 + sa * (cps * b1.z + sps * b2.z);
-            const float inv = 1.0f / sqrtf(S0 * S0 + S1 * S1 + S2 * S2);
-            S0 *= inv;
-            S1 *= inv;
-            S2 *= inv;
-        }
-        const float dX = S0 - s0, dY = S1 - s1, dZ = S2 - s2;
-        const float dex = -P.J * (dX * n0 + dY * n1 + dZ * n2);
-        const float z0 = s2 * s2, z1 = S2 * S2;
-        const float dan = (-P.K2 * z1 - P.K4 * z1 * z1) - (-P.K2 * z0 - P.K4 * z0 * z0);
-        const float W0xx = __ldg(b.W32), W0xy = __ldg(b.W32 + N), W0yy = __ldg(b.W32 + 2 * N), W0zz = __ldg(b.W32 + 3 * N);
-        const float self = W0xx * dX * dX + 2.0f * W0xy * dX * dY + W0yy * dY * dY + W0zz * dZ * dZ;
-        pre = dex + dan + P.CD * 0.5f * self;
-        thr = (uacc > 0.0f) ? -P.T * logf(uacc) : INFINITY;
-    }
-
-    // ---- field spectra at the sites: sum of the partial chunks, in chunk order,
-    // eight chunks' loads in flight at a time
-    const int nchunks = cfg.esplit + (cfg.extra_in ? 1 : 0);
-    for (int i = tid; i < 3 * n; i += blockDim.x) {
-        float2 acc = b.Hpart[((size_t)r * 3) * n + i];
-        for (int z0 = 1; z0 < nchunks; z0 += 8) {
-            float2 v[8];
+    const float W0xx = __ldg(b.W32), W0xy = __ldg(b.W32 + N), W0yy = __ldg(b.W32 + 2 * N), W0zz = __ldg(b.W32 + 3 * N);
+    const int nchunks = cfg.esplit;
+    const size_t zstride = (size_t)R * cfg.wmax * 3 * n;
+    __syncthreads();
+    for (int w = 0; w < cfg.wlen; ++w) {
+        const int k = cfg.k + w;
+        const int ov = s_off[w];
+        const int ox = ov & 0xFFFF, oy = ov >> 16;
+        float2 *So = b.S + ((size_t)r * ll + (oy * l + ox)) * 3 * n;
+        // ---- the loads of the thread's first spectral output i0 go out first: up to 16
+        // chunks of its window-start spectra, the table entries of the window's earlier
+        // offsets and S_o(before) for its change (MAXT = 256: registers for all of them)
+        constexpr int kHC = MAXT <= 256 ? 16 : 1;
+        constexpr int kHV = MAXT <= 256 ? kSpecWinMax : 1;
+        const int i0 = tid;
+        const bool first = MAXT <= 256 && i0 < 3 * n;
+        const int a0 = first ? qdiv(i0, cfg.mn) : 0, K0 = first ? i0 - a0 * n : 0;
+        const float2 *hp0 = b.Hw + (((size_t)r * cfg.wmax + w) * 3) * n + i0;
+        float2 hv[kHC], tv0[kHV], tv1[kHV], sold = make_float2(0.f, 0.f);
+        if (first) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                v[j] = z0 + j < nchunks ? b.Hpart[(((size_t)(z0 + j) * R + r) * 3) * n + i] : make_float2(0.f, 0.f);
+            for (int j = 0; j < kHC; ++j) hv[j] = j < nchunks ? hp0[(size_t)j * zstride] : make_float2(0.f, 0.f);
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                if (z0 + j < nchunks) {
-                    acc.x += v[j].x;
-                    acc.y += v[j].y;
+            for (int v = 0; v < kHV; ++v) {
+                tv0[v] = tv1[v] = make_float2(0.f, 0.f);
+                if (v < w) {
+                    const int pv = s_off[v];
+                    int dx = ox - (pv & 0xFFFF), dy = oy - (pv >> 16);
+                    const int sx = dx < 0, sy = dy < 0;
+                    dx += sx ? l : 0;
+                    dy += sy ? l : 0;
+                    const float2 *Tp = b.T + ((size_t)((sx + 2 * sy) * ll + dy * l + dx) * 4) * n + K0;
+                    tv0[v] = __ldg(Tp + (a0 == 2 ? 3 : a0) * n);
+                    if (a0 < 2) tv1[v] = __ldg(Tp + (a0 + 1) * n);
                 }
-        }
-        H[i] = acc;
-    }
-    __syncthreads();
-    // inverse DFT: over Kx, then over Ky (conjugate twiddles), real part / n
-    for (int i = tid; i < 3 * n; i += blockDim.x) {
-        const int a = qdiv(i, cfg.mn), jj = i - a * n, Ky = qdiv(jj, cfg.mC), Dx = jj - Ky * C;
-        const float2 *row = H + a * n + Ky * C;
-        float2 acc = make_float2(0.f, 0.f);
-        for (int Kx = 0, m = 0; Kx < C; ++Kx) {       // m = Kx * Dx mod C
-            const float2 o = tw[m];
-            acc = cfma(row[Kx], make_float2(o.x, -o.y), acc);
-            m += Dx;
-            if (m >= C) m -= C;
-        }
-        U[i] = acc;
-    }
-    __syncthreads();
-    const float inv_n = 1.0f / (float)n;
-    for (int i = tid; i < 3 * n; i += blockDim.x) {
-        const int a = qdiv(i, cfg.mn), jj = i - a * n, Dy = qdiv(jj, cfg.mC), Dx = jj - Dy * C;
-        const float2 *col = U + a * n + Dx;
-        float re = 0.f;
-        for (int Ky = 0, m = 0; Ky < C; ++Ky) {       // m = Ky * Dy mod C
-            const float2 u = col[Ky * C], o = tw[m];
-            re = fmaf(u.x, o.x, fmaf(u.y, o.y, re));   // Re(u * conj(o))
-            m += Dy;
-            if (m >= C) m -= C;
-        }
-        hs[i] = re * inv_n;
-    }
-    __syncthreads();
-    // ---- decisions (sites are numbered as in the other paths: d -> (d % C, d / C))
-    int accept = 0;
-    if (site) {
-        const float dX = S0 - s0, dY = S1 - s1, dZ = S2 - s2;
-        const float h0 = hs[d], h1 = hs[n + d], h2 = hs[2 * n + d];
-        const float dE = pre + P.CD * (dX * h0 + dY * h1 + dZ * h2);
-        accept = dE < thr;
-        if (b.trace) {
-            float *tr = b.trace + ((((size_t)r * cfg.nsweeps_call + cfg.it) * ll + cfg.k) * n + d) * MC_TRACE_W;
-            tr[0] = (float)q;
-            tr[1] = h0; tr[2] = h1; tr[3] = h2;
-            tr[4] = dE;
-            tr[5] = uacc;
-            tr[6] = (float)accept;
-            tr[7] = S0; tr[8] = S1; tr[9] = S2;
-        }
-        sn[d] = accept ? S0 : s0;
-        sn[n + d] = accept ? S1 : s1;
-        sn[2 * n + d] = accept ? S2 : s2;
-        if (accept) {
-            s[q] = S0;
-            s[N + q] = S1;
-            s[2 * N + q] = S2;
-        }
-    }
-    const unsigned ball = __ballot_sync(0xffffffffu, accept);
-    if ((tid & 31) == 0 && ball) atomicAdd(&s_acc, __popc(ball));
-    __syncthreads();
-    // ---- new S of the updated offset (global, and in H for the next sub-step's term)
-    float2 *So = b.S + ((size_t)r * ll + (oy * l + ox)) * 3 * n;
-    for (int i = tid; i < 3 * n; i += blockDim.x) {
-        const int bb = qdiv(i, cfg.mn), j = i - bb * n, Dy = qdiv(j, cfg.mC), Kx = j - Dy * C;
-        const float *row = sn + bb * n + Dy * C;
-        float2 acc = make_float2(0.f, 0.f);
-        for (int Dx = 0, m = 0; Dx < C; ++Dx) {       // m = Kx * Dx mod C
-            const float2 o = tw[m];
-            acc.x = fmaf(row[Dx], o.x, acc.x);
-            acc.y = fmaf(row[Dx], o.y, acc.y);
-            m += Kx;
-            if (m >= C) m -= C;
-        }
-        U[i] = acc;
-    }
-    __syncthreads();
-    for (int i = tid; i < 3 * n; i += blockDim.x) {
-        const int bb = qdiv(i, cfg.mn), j = i - bb * n, Ky = qdiv(j, cfg.mC), Kx = j - Ky * C;
-        const float2 *col = U + bb * n + Kx;
-        float2 acc = make_float2(0.f, 0.f);
-        for (int Dy = 0, m = 0; Dy < C; ++Dy) {       // m = Ky * Dy mod C
-            acc = cfma(col[Dy * C], tw[m], acc);
-            m += Ky;
-            if (m >= C) m -= C;
-        }
-        So[i] = acc;
-        H[i] = acc;
-    }
-    if (cfg.extra_out) {
-        __syncthreads();
-        // the next sub-step's term of this offset: omega^(K.sigma) T_{(o' - o) mod l}(K) S_o(K)
-        const int nv = b.off[(size_t)r * ll + cfg.k + 1];
-        const int nx = nv & 0xFFFF, ny = nv >> 16;
-        int dx = nx - ox, dy = ny - oy;
-        const int sx = dx < 0, sy = dy < 0;
-        dx += sx ? l : 0;
-        dy += sy ? l : 0;
-        const float2 *Tp = b.T + (size_t)(dy * l + dx) * 4 * n;
-        for (int i = tid; i < 3 * n; i += blockDim.x) {
-            const int a = qdiv(i, cfg.mn), K = i - a * n, Ky = qdiv(K, cfg.mC), Kx = K - Ky * C;
-            int m = (sx ? Kx : 0) + (sy ? Ky : 0);
-            if (m >= C) m -= C;
-            const float2 p = omega(m, C);
-            float2 h;
-            if (a == 2) {
-                h = cmul(cmul(__ldg(Tp + 3 * n + K), p), H[2 * n + K]);
-            } else {
-                const float2 t0 = cmul(__ldg(Tp + (a == 0 ? 0 : 1) * n + K), p);
-                const float2 t1 = cmul(__ldg(Tp + (a == 0 ? 1 : 2) * n + K), p);
-                h = cfma(t0, H[K], cmul(t1, H[n + K]));
             }
-            b.Hnext[(((size_t)cfg.esplit * R + r) * 3 + a) * n + K] = h;
+            sold = So[i0];
         }
+        // ---- everything that does not need the field, issued before the field sums:
+        // thread d < n (blockDim >= n) owns site d: its spins, neighbours, proposal and
+        // the field-free part of dE
+        const int d = tid;
+        const bool site = d < n;
+        int q = 0;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, S0 = 0.f, S1 = 0.f, S2 = 0.f, pre = 0.f, thr = 0.f, uacc = 0.f;
+        if (site) {
+            const int dy_ = qdiv(d, cfg.mC);
+            const int qx = ox + l * (d - dy_ * C), qy = oy + l * dy_;
+            q = qy * L + qx;
+            const uint4 wds = philox(make_uint4((uint32_t)q, rid, t, ((uint32_t)k & 0x00FFFFFFu) | kTagAttempt), key);
+            const float u1 = u24f(wds.x);
+            uacc = u24f(wds.z);
+            float sps, cps;
+            sincospif(2.0f * u24f(wds.y), &sps, &cps);
+            s0 = s[q];
+            s1 = s[N + q];
+            s2 = s[2 * N + q];
+            const int xp = (qx + 1 == L) ? q - qx : q + 1;
+            const int xm = (qx == 0) ? q + L - 1 : q - 1;
+            const int yp = (qy + 1 == L) ? qx : q + L;
+            const int ym = (qy == 0) ? q + N - L : q - L;
+            const float n0 = (s[xp] + s[xm]) + (s[yp] + s[ym]);
+            const float n1 = (s[N + xp] + s[N + xm]) + (s[N + yp] + s[N + ym]);
+            const float n2 = (s[2 * N + xp] + s[2 * N + xm]) + (s[2 * N + yp] + s[2 * N + ym]);
+            if (cfg.proposal == kPropFlip) {            // Appendix B reversal
+                S0 = -s0;
+                S1 = -s1;
+                S2 = -s2;
+            } else if (cfg.proposal == kPropSphere) {
+                const float z = 2.0f * u1 - 1.0f;
+                const float rr = sqrtf(fmaxf(0.0f, (1.0f - z) * (1.0f + z)));
+                S0 = rr * cps;
+                S1 = rr * sps;
+                S2 = z;
+            } else {
+                const float omc = u1 * cfg.cap_c1;             // 1 - cos(alpha), no cancellation
+                const float ca = 1.0f - omc;
+                const float sa = sqrtf(fmaxf(0.0f, omc * (2.0f - omc)));
+                float3 b1, b2;
+                perp_basis_s(s0, s1, s2, b1, b2);
+                S0 = ca * s0 + sa * (cps * b1.x + sps * b2.x);
+                S1 = ca * s1 + sa * (cps * b1.y + sps * b2.y);
+                S2 = ca * s2 + sa * (cps * b1.z + sps * b2.z);
+                const float inv = 1.0f / sqrtf(S0 * S0 + S1 * S1 + S2 * S2);
+                S0 *= inv;
+                S1 *= inv;
+                S2 *= inv;
+            }
+            const float dX = S0 - s0, dY = S1 - s1, dZ = S2 - s2;
+            const float dex = -P.J * (dX * n0 + dY * n1 + dZ * n2);
+            const float z0 = s2 * s2, z1 = S2 * S2;
+            const float dan = (-P.K2 * z1 - P.K4 * z1 * z1) - (-P.K2 * z0 - P.K4 * z0 * z0);
+            const float self = W0xx * dX * dX + 2.0f * W0xy * dX * dY + W0yy * dY * dY + W0zz * dZ * dZ;
+            pre = dex + dan + P.CD * 0.5f * self;
+            thr = (uacc > 0.0f) ? -P.T * logf(uacc) : INFINITY;
+        }
+
+        // ---- field spectra: the chunk sum in chunk order, then the window's earlier changes
+        if (first) {
+            float2 acc = hv[0];
+#pragma unroll
+            for (int j = 1; j < kHC; ++j)
+                if (j < nchunks) {
+                    acc.x += hv[j].x;
+                    acc.y += hv[j].y;
+                }
+            for (int z0 = kHC; z0 < nchunks; ++z0) {
+                const float2 v = hp0[(size_t)z0 * zstride];
+                acc.x += v.x;
+                acc.y += v.y;
+            }
+#pragma unroll
+            for (int v = 0; v < kHV; ++v)
+                if (v < w) {
+                    const float2 *dv = dS + (size_t)v * 3 * n + K0;
+                    if (a0 == 2) acc = cfma(tv0[v], dv[2 * n], acc);
+                    else acc = cfma(tv0[v], dv[0], cfma(tv1[v], dv[n], acc));
+                }
+            H[i0] = acc;
+        }
+        for (int i = tid + (first ? blockDim.x : 0); i < 3 * n; i += blockDim.x) {
+            const int a = qdiv(i, cfg.mn), K = i - a * n;
+            const float2 *hp = b.Hw + (((size_t)r * cfg.wmax + w) * 3) * n + i;
+            float2 acc = hp[0];
+            for (int z0 = 1; z0 < nchunks; z0 += 8) {
+                float2 v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v[j] = z0 + j < nchunks ? hp[(size_t)(z0 + j) * zstride] : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (z0 + j < nchunks) {
+                        acc.x += v[j].x;
+                        acc.y += v[j].y;
+                    }
+            }
+            if (w > 0) {
+                for (int v = 0; v < w; ++v) {
+                    const int pv = s_off[v];
+                    int dx = ox - (pv & 0xFFFF), dy = oy - (pv >> 16);
+                    const int sx = dx < 0, sy = dy < 0;
+                    dx += sx ? l : 0;
+                    dy += sy ? l : 0;
+                    const float2 *Tp = b.T + ((size_t)((sx + 2 * sy) * ll + dy * l + dx) * 4) * n + K;
+                    const float2 *dv = dS + (size_t)v * 3 * n + K;
+                    if (a == 2) {
+                        acc = cfma(__ldg(Tp + 3 * n), dv[2 * n], acc);
+                    } else {
+                        acc = cfma(__ldg(Tp + a * n), dv[0], cfma(__ldg(Tp + (a + 1) * n), dv[n], acc));
+                    }
+                }
+            }
+            H[i] = acc;
+        }
+        __syncthreads();
+        // inverse DFT: over Kx, then over Ky (conjugate twiddles), real part / n
+        for (int i = tid; i < 3 * n; i += blockDim.x) {
+            const int a = qdiv(i, cfg.mn), jj = i - a * n, Ky = qdiv(jj, cfg.mC), Dx = jj - Ky * C;
+            const float2 *row = H + a * n + Ky * C;
+            float2 acc = make_float2(0.f, 0.f);
+            for (int Kx = 0, m = 0; Kx < C; ++Kx) {       // m = Kx * Dx mod C
+                const float2 o = tw[m];
+                acc = cfma(row[Kx], make_float2(o.x, -o.y), acc);
+                m += Dx;
+                if (m >= C) m -= C;
+            }
+            U[i] = acc;
+        }
+        __syncthreads();
+        const float inv_n = 1.0f / (float)n;
+        for (int i = tid; i < 3 * n; i += blockDim.x) {
+            const int a = qdiv(i, cfg.mn), jj = i - a * n, Dy = qdiv(jj, cfg.mC), Dx = jj - Dy * C;
+            const float2 *col = U + a * n + Dx;
+            float re = 0.f;
+            for (int Ky = 0, m = 0; Ky < C; ++Ky) {       // m = Ky * Dy mod C
+                const float2 u = col[Ky * C], o = tw[m];
+                re = fmaf(u.x, o.x, fmaf(u.y, o.y, re));   // Re(u * conj(o))
+                m += Dy;
+                if (m >= C) m -= C;
+            }
+            hs[i] = re * inv_n;
+        }
+        __syncthreads();
+        // ---- decisions (sites are numbered as in the other paths: d -> (d % C, d / C))
+        int accept = 0;
+        if (site) {
+            const float dX = S0 - s0, dY = S1 - s1, dZ = S2 - s2;
+            const float h0 = hs[d], h1 = hs[n + d], h2 = hs[2 * n + d];
+            const float dE = pre + P.CD * (dX * h0 + dY * h1 + dZ * h2);
+            accept = dE < thr;
+            if (b.trace) {
+                float *tr = b.trace + ((((size_t)r * cfg.nsweeps_call + cfg.it) * ll + k) * n + d) * MC_TRACE_W;
+                tr[0] = (float)q;
+                tr[1] = h0; tr[2] = h1; tr[3] = h2;
+                tr[4] = dE;
+                tr[5] = uacc;
+                tr[6] = (float)accept;
+                tr[7] = S0; tr[8] = S1; tr[9] = S2;
+            }
+            sn[d] = accept ? S0 : s0;
+            sn[n + d] = accept ? S1 : s1;
+            sn[2 * n + d] = accept ? S2 : s2;
+            if (accept) {
+                s[q] = S0;
+                s[N + q] = S1;
+                s[2 * N + q] = S2;
+            }
+        }
+        const unsigned ball = __ballot_sync(0xffffffffu, accept);
+        if ((tid & 31) == 0 && ball) atomicAdd(&s_acc, __popc(ball));
+        __syncthreads();
+        // ---- new S of the updated offset and its change
+        for (int i = tid; i < 3 * n; i += blockDim.x) {
+            const int bb = qdiv(i, cfg.mn), j = i - bb * n, Dy = qdiv(j, cfg.mC), Kx = j - Dy * C;
+            const float *row = sn + bb * n + Dy * C;
+            float2 acc = make_float2(0.f, 0.f);
+            for (int Dx = 0, m = 0; Dx < C; ++Dx) {       // m = Kx * Dx mod C
+                const float2 o = tw[m];
+                acc.x = fmaf(row[Dx], o.x, acc.x);
+                acc.y = fmaf(row[Dx], o.y, acc.y);
+                m += Kx;
+                if (m >= C) m -= C;
+            }
+            U[i] = acc;
+        }
+        __syncthreads();
+        for (int i = tid; i < 3 * n; i += blockDim.x) {
+            const int bb = qdiv(i, cfg.mn), j = i - bb * n, Ky = qdiv(j, cfg.mC), Kx = j - Ky * C;
+            const float2 *col = U + bb * n + Kx;
+            float2 acc = make_float2(0.f, 0.f);
+            for (int Dy = 0, m = 0; Dy < C; ++Dy) {       // m = Ky * Dy mod C
+                acc = cfma(col[Dy * C], tw[m], acc);
+                m += Ky;
+                if (m >= C) m -= C;
+            }
+            const float2 old = (first && i == i0) ? sold : So[i];
+            So[i] = acc;
+            dS[(size_t)w * 3 * n + i] = make_float2(acc.x - old.x, acc.y - old.y);
+        }
+        __syncthreads();
     }
     if (tid == 0 && s_acc && b.obs)
         atomicAdd((unsigned long long *)&b.obs[r].accepted, (unsigned long long)s_acc);
 }
 
-size_t update_smem(int C) {
+template <int MAXT>
+cudaError_t launch_wupdate(const SpecConfig &c, const SpecBuffers &b, size_t smem, int th, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(k_spec_wupdate<MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_spec_wupdate<MAXT><<<c.R, th, smem, st>>>(c, b);
+    return cudaGetLastError();
+}
+
+size_t wupdate_smem(int C, int wmax) {
     const size_t n = (size_t)C * C;
-    return sizeof(float2) * (kSpecMaxC + 6 * n) + sizeof(float) * 6 * n;
+    return sizeof(float2) * (kSpecMaxC + (6 + 3 * (size_t)wmax) * n) + sizeof(float) * 6 * n;
 }
 
 size_t init_smem(int C) {
@@ -541,18 +588,27 @@ bool spectral_supported(int L, int l) {
     return C >= 2 && C <= kSpecMaxC && L <= 4096;
 }
 
+int spectral_window(int L, int l) {
+    // the window's changes dS ([wmax][3][n] complex) stay in shared memory
+    const long long n = (long long)(L / l) * (L / l);
+    int w = kSpecWinMax;
+    while (w > 1 && (long long)w * 24 * n > 96 * 1024) w >>= 1;
+    return w;
+}
+
 int spectral_esplit(int L, int l, int R, int nsm) {
+    // chunks of the cell offsets: about three CTAs of the window field per SM
     const long long n = (long long)(L / l) * (L / l), ll = (long long)l * l;
-    const long long tiles = (R * n + 31) / 32;
-    long long z = (4LL * nsm + tiles - 1) / tiles;
-    z = std::min(z, std::max(1LL, ll / 16));  // every warp keeps at least two cell offsets
+    const long long tiles = ((n + 7) / 8) * ((R + 3) / 4);
+    long long z = (3LL * nsm + tiles - 1) / tiles;
+    z = std::min(z, std::max(1LL, ll / 8));   // at least 8 cell offsets a chunk
     return (int)std::max(1LL, z);
 }
 
 size_t spectral_S_elems(int L, int R) { return (size_t)3 * L * L * R; }
 
 size_t spectral_part_elems(int L, int l, int R, int esplit) {
-    return (size_t)2 * (esplit + 1) * R * 3 * (L / l) * (L / l);
+    return (size_t)esplit * R * spectral_window(L, l) * 3 * (L / l) * (L / l);
 }
 
 cudaError_t launch_spec_table(int L, int l, const double *W64, float2 *T, cudaStream_t st) {
@@ -578,22 +634,18 @@ cudaError_t launch_spec_offsets(const SpecConfig &c, const SpecBuffers &b, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t launch_spec_field(const SpecConfig &c, const SpecBuffers &b, cudaStream_t st) {
+cudaError_t launch_spec_wfield(const SpecConfig &c, const SpecBuffers &b, cudaStream_t st) {
     const int C = c.L / c.l, n = C * C;
-    const unsigned tiles = (unsigned)((c.R * n + 31) / 32);
-    k_spec_field<<<dim3(tiles, c.esplit), kSpecThreads, 0, st>>>(c, b);
+    k_spec_wfield<<<dim3((n + 7) / 8, (c.R + 3) / 4, c.esplit), kSpecThreads, 0, st>>>(c, b);
     return cudaGetLastError();
 }
 
-cudaError_t launch_spec_update(const SpecConfig &c, const SpecBuffers &b, cudaStream_t st) {
-    const size_t smem = update_smem(c.L / c.l);
-    cudaError_t e = cudaFuncSetAttribute(k_spec_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+cudaError_t launch_spec_wupdate(const SpecConfig &c, const SpecBuffers &b, cudaStream_t st) {
+    const size_t smem = wupdate_smem(c.L / c.l, c.wmax);
     // one thread per output of a DFT stage (3 n), so that no warp idles at the
-    // stage barriers
-    const int C = c.L / c.l, th = std::min(kUpdMaxThreads, ((3 * C * C + 31) / 32) * 32);
-    k_spec_update<<<c.R, std::max(64, th), smem, st>>>(c, b);
-    return cudaGetLastError();
+    // stage barriers; up to 256 threads the kernel holds a sub-step's loads in registers
+    const int C = c.L / c.l, th = std::max(64, std::min(kUpdMaxThreads, ((3 * C * C + 31) / 32) * 32));
+    return th <= 256 ? launch_wupdate<256>(c, b, smem, th, st) : launch_wupdate<kUpdMaxThreads>(c, b, smem, th, st);
 }
 
 }  // namespace dipmc
