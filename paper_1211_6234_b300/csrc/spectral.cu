@@ -56,6 +56,29 @@ __device__ __forceinline__ float2 omega(int m, int C) {
     return make_float2(c, -s);
 }
 
+// Real spins and W~ make every spectrum Hermitian, X(-K) = conj X(K), so the window
+// field computes only an independent half of the C x C wave vectors: the row Ky = 0
+// with Kx <= C/2, the rows 0 < Ky < C/2 (all Kx) and, for even C, the row Ky = C/2
+// with Kx <= C/2.  half_count(C) of them; half_wave(t) is the t-th.
+__host__ __device__ __forceinline__ int half_count(int C) {
+    return C / 2 + 1 + ((C - 1) / 2) * C + (C % 2 == 0 ? C / 2 + 1 : 0);
+}
+__device__ __forceinline__ int half_wave(int t, int C) {   // K = Ky * C + Kx
+    const int h0 = C / 2 + 1, mid = (C - 1) / 2;
+    if (t < h0) return t;
+    t -= h0;
+    if (t < mid * C) return (1 + t / C) * C + t % C;
+    return (C / 2) * C + (t - mid * C);
+}
+// K itself if it is in the computed half, else its partner -K (conjugate on use)
+__device__ __forceinline__ int half_source(int K, int C, bool &conj) {
+    const int Ky = K / C, Kx = K - Ky * C;
+    const bool in = (Ky == 0 || 2 * Ky == C) ? 2 * Kx <= C : 2 * Ky < C;
+    conj = !in;
+    if (in) return K;
+    return ((C - Ky) % C) * C + (C - Kx) % C;
+}
+
 // Stream state of replica r: its key, its sweep counter at sweep `it` of the
 // call and the replica index its counters use; false for an idle slot.
 __device__ __forceinline__ bool stream_state(const SpecConfig &cfg, const SpecBuffers &b, int r, uint2 &key,
@@ -236,8 +259,9 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec_init(int L, int l, const 
 __global__ void __launch_bounds__(kSpecThreads) k_spec_wfield(const SpecConfig cfg, const SpecBuffers b) {
     const int L = cfg.L, l = cfg.l, C = L / l, n = C * C, ll = l * l, R = cfg.R;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int K = blockIdx.x * 8 + (lane & 7), r = blockIdx.y * 4 + (lane >> 3);
-    const bool mine = K < n && r < R && w < cfg.wlen;
+    const int th = blockIdx.x * 8 + (lane & 7), r = blockIdx.y * 4 + (lane >> 3);
+    const bool mine = th < half_count(C) && r < R && w < cfg.wlen;
+    const int K = mine ? half_wave(th, C) : 0;
     const int ov = mine ? b.off[(size_t)r * ll + cfg.k + w] : -1;
     float2 hx = make_float2(0.f, 0.f), hy = hx, hz = hx;
     if (ov >= 0) {
@@ -335,7 +359,9 @@ __global__ void __launch_bounds__(MAXT) k_spec_wupdate(const SpecConfig cfg, con
         const int i0 = tid;
         const bool first = MAXT <= 256 && i0 < 3 * n;
         const int a0 = first ? qdiv(i0, cfg.mn) : 0, K0 = first ? i0 - a0 * n : 0;
-        const float2 *hp0 = b.Hw + (((size_t)r * cfg.wmax + w) * 3) * n + i0;
+        bool cj0 = false;
+        const int src0 = first ? a0 * n + half_source(K0, C, cj0) : 0;
+        const float2 *hp0 = b.Hw + (((size_t)r * cfg.wmax + w) * 3) * n + src0;
         float2 hv[kHC], tv0[kHV], tv1[kHV], sold = make_float2(0.f, 0.f);
         if (first) {
 #pragma unroll
@@ -429,6 +455,7 @@ __global__ void __launch_bounds__(MAXT) k_spec_wupdate(const SpecConfig cfg, con
                 acc.x += v.x;
                 acc.y += v.y;
             }
+            if (cj0) acc.y = -acc.y;
 #pragma unroll
             for (int v = 0; v < kHV; ++v)
                 if (v < w) {
@@ -440,7 +467,8 @@ __global__ void __launch_bounds__(MAXT) k_spec_wupdate(const SpecConfig cfg, con
         }
         for (int i = tid + (first ? blockDim.x : 0); i < 3 * n; i += blockDim.x) {
             const int a = qdiv(i, cfg.mn), K = i - a * n;
-            const float2 *hp = b.Hw + (((size_t)r * cfg.wmax + w) * 3) * n + i;
+            bool cj = false;
+            const float2 *hp = b.Hw + (((size_t)r * cfg.wmax + w) * 3) * n + a * n + half_source(K, C, cj);
             float2 acc = hp[0];
             for (int z0 = 1; z0 < nchunks; z0 += 8) {
                 float2 v[8];
@@ -453,6 +481,7 @@ __global__ void __launch_bounds__(MAXT) k_spec_wupdate(const SpecConfig cfg, con
                         acc.y += v[j].y;
                     }
             }
+            if (cj) acc.y = -acc.y;
             if (w > 0) {
                 for (int v = 0; v < w; ++v) {
                     const int pv = s_off[v];
@@ -598,10 +627,11 @@ int spectral_window(int L, int l) {
 
 int spectral_esplit(int L, int l, int R, int nsm) {
     // chunks of the cell offsets: about three CTAs of the window field per SM
-    const long long n = (long long)(L / l) * (L / l), ll = (long long)l * l;
-    const long long tiles = ((n + 7) / 8) * ((R + 3) / 4);
+    const long long ll = (long long)l * l;
+    const long long tiles = ((half_count(L / l) + 7) / 8) * ((R + 3) / 4);
     long long z = (3LL * nsm + tiles - 1) / tiles;
     z = std::min(z, std::max(1LL, ll / 8));   // at least 8 cell offsets a chunk
+    z = std::min(z, 16LL);                    // the update loads all chunks of a spectrum at once
     return (int)std::max(1LL, z);
 }
 
@@ -635,8 +665,8 @@ cudaError_t launch_spec_offsets(const SpecConfig &c, const SpecBuffers &b, cudaS
 }
 
 cudaError_t launch_spec_wfield(const SpecConfig &c, const SpecBuffers &b, cudaStream_t st) {
-    const int C = c.L / c.l, n = C * C;
-    k_spec_wfield<<<dim3((n + 7) / 8, (c.R + 3) / 4, c.esplit), kSpecThreads, 0, st>>>(c, b);
+    const int C = c.L / c.l;
+    k_spec_wfield<<<dim3((half_count(C) + 7) / 8, (c.R + 3) / 4, c.esplit), kSpecThreads, 0, st>>>(c, b);
     return cudaGetLastError();
 }
 
