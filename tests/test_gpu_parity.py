@@ -536,6 +536,9 @@ FCASES = [
     (5, 48, 16, 2, 0, 1),     # L not a power of two, odd coarse grid (3 x 3)
     (5, 96, 12, 1, 0, 1),     # 8 x 8 coarse grid, L not a power of two
     (5, 128, 8, 1, 0, 1),     # 16 x 16 coarse grid, 256 simultaneous sites
+    (5, 60, 6, 2, 0, 1),      # 10 x 10 coarse grid: 36 sub-steps, the last window partial
+    (5, 50, 10, 1, 1, 1),     # odd 5 x 5 grid, with-replacement schedule (offsets repeat within windows)
+    (5, 64, 2, 1, 0, 2),      # 32 x 32 coarse grid: 1024 sites per sub-step, 4-sub-step windows
     (6, 16, 8, 2, 0, 2),      # incremental field: 4 sites per sub-step
     (6, 32, 4, 2, 1, 1),      # 64 sites per sub-step, with-replacement schedule
     (6, 48, 24, 1, 0, 1),     # L not a power of two
