@@ -249,8 +249,8 @@ int mc_energy(mc_lattice *lat, double *dst_host, void *stream);
 #define MC_K_TC_FIELD 1      /* tensor-core window field (one launch per window) */
 #define MC_K_WINDOW_STEPS 2  /* sequential sub-steps of a window */
 #define MC_K_FULL_FIELD 3    /* FP32 full field (energy anchor, windowed FP32 path) */
-#define MC_K_SPEC_FIELD 4    /* spectral path: field spectra at the sub-step's sites */
-#define MC_K_SPEC_UPDATE 5   /* spectral path: inverse DFT, update, DFT of the updated sub-lattice */
+#define MC_K_SPEC_FIELD 4    /* spectral path: field spectra of a window's offsets (one launch per window) */
+#define MC_K_SPEC_UPDATE 5   /* spectral path: a window's sub-steps (inverse DFT, update, DFT of the updated sub-lattice) */
 #define MC_K_TC_REDUCE 6     /* retired: the split-K sum now runs inside the sub-step kernel (no launches) */
 #define MC_NKCLASS 7
 typedef struct mc_timing {
