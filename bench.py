@@ -49,6 +49,9 @@ def f32(x):
     return float(np.float32(x))
 
 
+WORKLOAD = "batched replicas: 256 x L=64 (16 T x 16 K4/K2), l=32, 10^2 sweeps/step"
+
+
 def ladder():
     return [(f32(J), f32(CD), f32(k2), f32(k4), f32(T)) for (T, k2, k4) in inputs.ladder(16, 16)]
 
@@ -161,8 +164,10 @@ def run_reference(args):
         "impl": "reference", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "batched replicas L=64 l=32 (sampled)", "replicas": Rs, "L": L, "l": l,
-                   "sweeps_per_step": sw},
+        # the workload of the device arm; each step here is a bounded sample of it
+        "config": {"workload": WORKLOAD, "replicas_per_gpu": R, "L": L, "l": l, "sweeps_per_step": args.sweeps,
+                   "image_cutoff": A_IMG, "approx_error_at_Tmin": approx_error(0.2),
+                   "field_path": "FP64 oracle (direct sums)", "sampled_per_step": f"{Rs} replicas x {sw} sweep"},
         "cpu_baseline": {"value": val, "unit": "site-updates/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": val, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -623,7 +628,7 @@ def main():
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16x3+f32" if args.path == "tensor" else "f32", "data": "synthetic",
-            "config": {"workload": "batched replicas: 256 x L=64 (16 T x 16 K4/K2), l=32, 10^2 sweeps/step",
+            "config": {"workload": WORKLOAD,
                        "replicas_per_gpu": R, "L": L, "l": l, "sweeps_per_step": S,
                        "field_path": {"tensor": "tcgen05 split-BF16x3 window field + FP32 sub-steps",
                                       "direct": "FP32 direct", "window": "FP32 window"}[args.path],
