@@ -346,101 +346,127 @@ __global__ void __launch_bounds__(MAXT) k_spec_wupdate(const SpecConfig cfg, con
     const int nchunks = cfg.esplit;
     const size_t zstride = (size_t)R * cfg.wmax * 3 * n;
     __syncthreads();
+
+    // ---- a sub-step's loads and field-free work, issued one sub-step ahead (during the
+    // previous sub-step's forward DFT, after its spins are written).  First: the thread's
+    // first spectral output i0 -- up to 16 chunks of its window-start spectra, the table
+    // entries of the window's earlier offsets and S_o(before) for its change (MAXT = 256:
+    // registers for all of them).
+    constexpr int kHC = MAXT <= 256 ? 16 : 1;
+    constexpr int kHV = MAXT <= 256 ? kSpecWinMax : 1;
+    const int i0 = tid;
+    const bool first = MAXT <= 256 && i0 < 3 * n;
+    const int a0 = first ? qdiv(i0, cfg.mn) : 0, K0 = first ? i0 - a0 * n : 0;
+    bool cj0 = false;
+    const int src0 = first ? a0 * n + half_source(K0, C, cj0) : 0;
+    float2 hv[kHC], tv0[kHV], tv1[kHV], sold = make_float2(0.f, 0.f);
+    auto issue_loads = [&](int w) {
+        if (!first) return;
+        const int ov = s_off[w], ox = ov & 0xFFFF, oy = ov >> 16;
+        const float2 *hp0 = b.Hw + (((size_t)r * cfg.wmax + w) * 3) * n + src0;
+#pragma unroll
+        for (int j = 0; j < kHC; ++j) hv[j] = j < nchunks ? hp0[(size_t)j * zstride] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int v = 0; v < kHV; ++v) {
+            tv0[v] = tv1[v] = make_float2(0.f, 0.f);
+            if (v < w) {
+                const int pv = s_off[v];
+                int dx = ox - (pv & 0xFFFF), dy = oy - (pv >> 16);
+                const int sx = dx < 0, sy = dy < 0;
+                dx += sx ? l : 0;
+                dy += sy ? l : 0;
+                const float2 *Tp = b.T + ((size_t)((sx + 2 * sy) * ll + dy * l + dx) * 4) * n + K0;
+                tv0[v] = __ldg(Tp + (a0 == 2 ? 3 : a0) * n);
+                if (a0 < 2) tv1[v] = __ldg(Tp + (a0 + 1) * n);
+            }
+        }
+        // S_o(before); an offset drawn twice in a row is re-read after its first update
+        if (w == 0 || s_off[w - 1] != ov) sold = b.S[((size_t)r * ll + (oy * l + ox)) * 3 * n + i0];
+    };
+    // Thread d < n (blockDim >= n) owns site d: its spins, neighbours, proposal and the
+    // field-free part of dE.
+    const int d = tid;
+    const bool site = d < n;
+    int q = 0;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, S0 = 0.f, S1 = 0.f, S2 = 0.f, pre = 0.f, thr = 0.f, uacc = 0.f;
+    float nb[3][4];   // neighbour spins (+x, -x, +y, -y) per component
+    // the site's spin and neighbours: loads only, consumed by prep() a phase later
+    auto prep_load = [&](int w) {
+        if (!site) return;
+        const int ov = s_off[w], ox = ov & 0xFFFF, oy = ov >> 16;
+        const int dy_ = qdiv(d, cfg.mC);
+        const int qx = ox + l * (d - dy_ * C), qy = oy + l * dy_;
+        q = qy * L + qx;
+        s0 = s[q];
+        s1 = s[N + q];
+        s2 = s[2 * N + q];
+        const int xp = (qx + 1 == L) ? q - qx : q + 1;
+        const int xm = (qx == 0) ? q + L - 1 : q - 1;
+        const int yp = (qy + 1 == L) ? qx : q + L;
+        const int ym = (qy == 0) ? q + N - L : q - L;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            nb[c][0] = s[c * N + xp];
+            nb[c][1] = s[c * N + xm];
+            nb[c][2] = s[c * N + yp];
+            nb[c][3] = s[c * N + ym];
+        }
+    };
+    auto prep = [&](int w) {
+        if (!site) return;
+        const int k = cfg.k + w;
+        const uint4 wds = philox(make_uint4((uint32_t)q, rid, t, ((uint32_t)k & 0x00FFFFFFu) | kTagAttempt), key);
+        const float u1 = u24f(wds.x);
+        uacc = u24f(wds.z);
+        float sps, cps;
+        sincospif(2.0f * u24f(wds.y), &sps, &cps);
+        const float n0 = (nb[0][0] + nb[0][1]) + (nb[0][2] + nb[0][3]);
+        const float n1 = (nb[1][0] + nb[1][1]) + (nb[1][2] + nb[1][3]);
+        const float n2 = (nb[2][0] + nb[2][1]) + (nb[2][2] + nb[2][3]);
+        if (cfg.proposal == kPropFlip) {            // Appendix B reversal
+            S0 = -s0;
+            S1 = -s1;
+            S2 = -s2;
+        } else if (cfg.proposal == kPropSphere) {
+            const float z = 2.0f * u1 - 1.0f;
+            const float rr = sqrtf(fmaxf(0.0f, (1.0f - z) * (1.0f + z)));
+            S0 = rr * cps;
+            S1 = rr * sps;
+            S2 = z;
+        } else {
+            const float omc = u1 * cfg.cap_c1;             // 1 - cos(alpha), no cancellation
+            const float ca = 1.0f - omc;
+            const float sa = sqrtf(fmaxf(0.0f, omc * (2.0f - omc)));
+            float3 b1, b2;
+            perp_basis_s(s0, s1, s2, b1, b2);
+            S0 = ca * s0 + sa * (cps * b1.x + sps * b2.x);
+            S1 = ca * s1 + sa * (cps * b1.y + sps * b2.y);
+            S2 = ca * s2 + sa * (cps * b1.z + sps * b2.z);
+            const float inv = 1.0f / sqrtf(S0 * S0 + S1 * S1 + S2 * S2);
+            S0 *= inv;
+            S1 *= inv;
+            S2 *= inv;
+        }
+        const float dX = S0 - s0, dY = S1 - s1, dZ = S2 - s2;
+        const float dex = -P.J * (dX * n0 + dY * n1 + dZ * n2);
+        const float z0 = s2 * s2, z1 = S2 * S2;
+        const float dan = (-P.K2 * z1 - P.K4 * z1 * z1) - (-P.K2 * z0 - P.K4 * z0 * z0);
+        const float self = W0xx * dX * dX + 2.0f * W0xy * dX * dY + W0yy * dY * dY + W0zz * dZ * dZ;
+        pre = dex + dan + P.CD * 0.5f * self;
+        thr = (uacc > 0.0f) ? -P.T * logf(uacc) : INFINITY;
+    };
+    if (cfg.wlen > 0) {
+        issue_loads(0);
+        prep_load(0);
+    }
     for (int w = 0; w < cfg.wlen; ++w) {
         const int k = cfg.k + w;
+        prep(w);
         const int ov = s_off[w];
         const int ox = ov & 0xFFFF, oy = ov >> 16;
         float2 *So = b.S + ((size_t)r * ll + (oy * l + ox)) * 3 * n;
-        // ---- the loads of the thread's first spectral output i0 go out first: up to 16
-        // chunks of its window-start spectra, the table entries of the window's earlier
-        // offsets and S_o(before) for its change (MAXT = 256: registers for all of them)
-        constexpr int kHC = MAXT <= 256 ? 16 : 1;
-        constexpr int kHV = MAXT <= 256 ? kSpecWinMax : 1;
-        const int i0 = tid;
-        const bool first = MAXT <= 256 && i0 < 3 * n;
-        const int a0 = first ? qdiv(i0, cfg.mn) : 0, K0 = first ? i0 - a0 * n : 0;
-        bool cj0 = false;
-        const int src0 = first ? a0 * n + half_source(K0, C, cj0) : 0;
         const float2 *hp0 = b.Hw + (((size_t)r * cfg.wmax + w) * 3) * n + src0;
-        float2 hv[kHC], tv0[kHV], tv1[kHV], sold = make_float2(0.f, 0.f);
-        if (first) {
-#pragma unroll
-            for (int j = 0; j < kHC; ++j) hv[j] = j < nchunks ? hp0[(size_t)j * zstride] : make_float2(0.f, 0.f);
-#pragma unroll
-            for (int v = 0; v < kHV; ++v) {
-                tv0[v] = tv1[v] = make_float2(0.f, 0.f);
-                if (v < w) {
-                    const int pv = s_off[v];
-                    int dx = ox - (pv & 0xFFFF), dy = oy - (pv >> 16);
-                    const int sx = dx < 0, sy = dy < 0;
-                    dx += sx ? l : 0;
-                    dy += sy ? l : 0;
-                    const float2 *Tp = b.T + ((size_t)((sx + 2 * sy) * ll + dy * l + dx) * 4) * n + K0;
-                    tv0[v] = __ldg(Tp + (a0 == 2 ? 3 : a0) * n);
-                    if (a0 < 2) tv1[v] = __ldg(Tp + (a0 + 1) * n);
-                }
-            }
-            sold = So[i0];
-        }
-        // ---- everything that does not need the field, issued before the field sums:
-        // thread d < n (blockDim >= n) owns site d: its spins, neighbours, proposal and
-        // the field-free part of dE
-        const int d = tid;
-        const bool site = d < n;
-        int q = 0;
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f, S0 = 0.f, S1 = 0.f, S2 = 0.f, pre = 0.f, thr = 0.f, uacc = 0.f;
-        if (site) {
-            const int dy_ = qdiv(d, cfg.mC);
-            const int qx = ox + l * (d - dy_ * C), qy = oy + l * dy_;
-            q = qy * L + qx;
-            const uint4 wds = philox(make_uint4((uint32_t)q, rid, t, ((uint32_t)k & 0x00FFFFFFu) | kTagAttempt), key);
-            const float u1 = u24f(wds.x);
-            uacc = u24f(wds.z);
-            float sps, cps;
-            sincospif(2.0f * u24f(wds.y), &sps, &cps);
-            s0 = s[q];
-            s1 = s[N + q];
-            s2 = s[2 * N + q];
-            const int xp = (qx + 1 == L) ? q - qx : q + 1;
-            const int xm = (qx == 0) ? q + L - 1 : q - 1;
-            const int yp = (qy + 1 == L) ? qx : q + L;
-            const int ym = (qy == 0) ? q + N - L : q - L;
-            const float n0 = (s[xp] + s[xm]) + (s[yp] + s[ym]);
-            const float n1 = (s[N + xp] + s[N + xm]) + (s[N + yp] + s[N + ym]);
-            const float n2 = (s[2 * N + xp] + s[2 * N + xm]) + (s[2 * N + yp] + s[2 * N + ym]);
-            if (cfg.proposal == kPropFlip) {            // Appendix B reversal
-                S0 = -s0;
-                S1 = -s1;
-                S2 = -s2;
-            } else if (cfg.proposal == kPropSphere) {
-                const float z = 2.0f * u1 - 1.0f;
-                const float rr = sqrtf(fmaxf(0.0f, (1.0f - z) * (1.0f + z)));
-                S0 = rr * cps;
-                S1 = rr * sps;
-                S2 = z;
-            } else {
-                const float omc = u1 * cfg.cap_c1;             // 1 - cos(alpha), no cancellation
-                const float ca = 1.0f - omc;
-                const float sa = sqrtf(fmaxf(0.0f, omc * (2.0f - omc)));
-                float3 b1, b2;
-                perp_basis_s(s0, s1, s2, b1, b2);
-                S0 = ca * s0 + sa * (cps * b1.x + sps * b2.x);
-                S1 = ca * s1 + sa * (cps * b1.y + sps * b2.y);
-                S2 = ca * s2 + sa * (cps * b1.z + sps * b2.z);
-                const float inv = 1.0f / sqrtf(S0 * S0 + S1 * S1 + S2 * S2);
-                S0 *= inv;
-                S1 *= inv;
-                S2 *= inv;
-            }
-            const float dX = S0 - s0, dY = S1 - s1, dZ = S2 - s2;
-            const float dex = -P.J * (dX * n0 + dY * n1 + dZ * n2);
-            const float z0 = s2 * s2, z1 = S2 * S2;
-            const float dan = (-P.K2 * z1 - P.K4 * z1 * z1) - (-P.K2 * z0 - P.K4 * z0 * z0);
-            const float self = W0xx * dX * dX + 2.0f * W0xy * dX * dY + W0yy * dY * dY + W0zz * dZ * dZ;
-            pre = dex + dan + P.CD * 0.5f * self;
-            thr = (uacc > 0.0f) ? -P.T * logf(uacc) : INFINITY;
-        }
-
+        const bool sold_ok = w == 0 || s_off[w - 1] != ov;
         // ---- field spectra: the chunk sum in chunk order, then the window's earlier changes
         if (first) {
             float2 acc = hv[0];
@@ -557,6 +583,13 @@ __global__ void __launch_bounds__(MAXT) k_spec_wupdate(const SpecConfig cfg, con
         const unsigned ball = __ballot_sync(0xffffffffu, accept);
         if ((tid & 31) == 0 && ball) atomicAdd(&s_acc, __popc(ball));
         __syncthreads();
+        // ---- the next sub-step's loads and field-free work (its sites' spins and the
+        // neighbours this sub-step may have changed are in global memory by now)
+        const float2 sold_w = sold;
+        if (w + 1 < cfg.wlen) {
+            issue_loads(w + 1);
+            prep_load(w + 1);
+        }
         // ---- new S of the updated offset and its change
         for (int i = tid; i < 3 * n; i += blockDim.x) {
             const int bb = qdiv(i, cfg.mn), j = i - bb * n, Dy = qdiv(j, cfg.mC), Kx = j - Dy * C;
@@ -581,7 +614,7 @@ __global__ void __launch_bounds__(MAXT) k_spec_wupdate(const SpecConfig cfg, con
                 m += Ky;
                 if (m >= C) m -= C;
             }
-            const float2 old = (first && i == i0) ? sold : So[i];
+            const float2 old = (first && i == i0 && sold_ok) ? sold_w : So[i];
             So[i] = acc;
             dS[(size_t)w * 3 * n + i] = make_float2(acc.x - old.x, acc.y - old.y);
         }
