@@ -380,7 +380,9 @@ int mc_footprint(int L, int l, int replicas, size_t *bytes);
  * they need fit hbm_budget_bytes and fewer than max_active are running; a packed
  * request waits only for free slots.  Sweeps are issued in quanta of at most
  * quantum_sweeps; a request joins or leaves a pack between quanta.  max_error is
- * the flip-probability error bound (Sec. 3.2) used when a request leaves l = 0.
+ * the flip-probability error bound (Sec. 3.2) used when a request leaves l = 0: the
+ * smallest l within the bound that the direct pack serves, else the smallest that
+ * any pack serves (a larger l only lowers the error).
  * The server is single-threaded: call every function from one host thread.
  */
 int mc_server_create(size_t hbm_budget_bytes, int max_active, int quantum_sweeps, double max_error,

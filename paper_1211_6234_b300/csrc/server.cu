@@ -486,15 +486,17 @@ int mc_server_submit(mc_server *s, const mc_request *r, uint64_t *id) {
                                          "init_mode in {0, 1, 3} and proposal in {0, 1, 2}");
     if (q.l == 0) {
         // the smallest spacing within the error bound; a larger divisor of L only
-        // lowers the error, so move up to the first one a pack path serves
+        // lowers the error, so move up to the first one the direct pack serves (measured
+        // at L = 96: the direct kernel at l = 24 runs 64 packed requests several times
+        // faster than the spectral pack at l = 16), else to the first any pack serves
         int rc = mc_choose_spacing(q.L, q.C_D, q.T, s->max_error, &q.l);
         if (rc) return rc;
-        int cap = 0;
-        for (int d = q.l; d <= q.L; ++d)
-            if (q.L % d == 0 && pack_shape(q.L, d, &cap) >= 0) {
-                q.l = d;
-                break;
-            }
+        int cap = 0, best = -1;
+        for (int d = q.l; d <= q.L && best < 0; ++d)
+            if (q.L % d == 0 && pack_shape(q.L, d, &cap) == MC_PATH_DIRECT) best = d;
+        for (int d = q.l; d <= q.L && best < 0; ++d)
+            if (q.L % d == 0 && pack_shape(q.L, d, &cap) >= 0) best = d;
+        if (best > 0) q.l = best;
     }
     if (q.l < 2 || q.l > q.L || q.L % q.l) return set_last_error(MC_EINVAL, "request needs 2 <= l <= L and L % l == 0");
     if (lattice_footprint(q.L, q.l, q.replicas) > s->budget)

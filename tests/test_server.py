@@ -207,15 +207,23 @@ def test_release_frees_slots_for_the_next_request(dipmc):
 @gpu
 def test_spacing_chosen_at_the_error_bound(dipmc):
     """l = 0 in a request takes the spacing mc_choose_spacing gives at the
-    server's error bound."""
+    server's error bound, moved up to the first divisor the direct pack serves
+    where there is one."""
     with dipmc.Server(hbm_budget_bytes=1 << 30, quantum_sweeps=4, max_error=1e-3) as srv:
         rid = srv.submit(L=64, l=0, T=0.9, sweeps=3, seed=5)
         srv.run_until_done([rid], timeout_s=120)
         assert srv.info(rid)["l"] == dipmc.choose_spacing(64, 0.1, 0.9, 1e-3)
         # L = 96 at T = 0.9: the bound allows l = 16 (L/l = 6: no direct kernel
-        # instance); the request goes to a spectral pack at that spacing
+        # instance); the next divisor the direct pack serves, l = 24 (L/l = 4), only
+        # lowers the error, so the request goes to a direct pack at that spacing
         assert dipmc.choose_spacing(96, 0.1, 0.9, 1e-3) == 16
         rid = srv.submit(L=96, l=0, T=0.9, sweeps=2, seed=6)
         srv.run_until_done([rid], timeout_s=120)
         info = srv.info(rid)
-        assert info["l"] == 16 and info["packed"] and info["path"] == dipmc.MC_PATH_SPECTRAL
+        assert info["l"] == 24 and info["packed"] and info["path"] == dipmc.MC_PATH_DIRECT
+        # L = 256: no direct kernel; the bound's own spacing on a spectral pack
+        rid = srv.submit(L=256, l=0, T=0.9, sweeps=1, seed=7)
+        srv.run_until_done([rid], timeout_s=120)
+        info = srv.info(rid)
+        assert info["l"] == dipmc.choose_spacing(256, 0.1, 0.9, 1e-3)
+        assert info["packed"] and info["path"] == dipmc.MC_PATH_SPECTRAL
