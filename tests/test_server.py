@@ -221,6 +221,9 @@ def test_spacing_chosen_at_the_error_bound(dipmc):
         srv.run_until_done([rid], timeout_s=120)
         info = srv.info(rid)
         assert info["l"] == 24 and info["packed"] and info["path"] == dipmc.MC_PATH_DIRECT
+        spins_lone, obs_lone = lone_run(dipmc, L=96, l=24, T=0.9, sweeps=2, seed=6, path=dipmc.MC_PATH_DIRECT)
+        np.testing.assert_array_equal(srv.spins(rid), spins_lone)
+        same_obs(srv.collect(rid), obs_lone[0])
         # L = 256: no direct kernel; the bound's own spacing on a spectral pack
         rid = srv.submit(L=256, l=0, T=0.9, sweeps=1, seed=7)
         srv.run_until_done([rid], timeout_s=120)
