@@ -10,10 +10,16 @@
 // H_x + i H_y = (W^xx S_x + W^xy S_y) + i (W^xy S_x + W^yy S_y),  H_z = W^zz Z,
 // and two inverse transforms give h_x + i h_y and h_z.
 //
-// A 2D transform is a row pass (radix-2 Stockham in shared memory), a tiled
-// transpose and a second row pass; spectra stay in the transposed layout
-// [k_x][k_y] (W^ is stored the same way), so the inverse is row pass,
-// transpose, row pass back to [y][x].  L must be a power of two, 8 <= L <= 1024.
+// One full field is three kernels, with no transposes: k_fft_fwd_rows transforms
+// the rows of C and Z from the spins (over x, giving [y][kx]); k_fft_cols_conv takes
+// tiles of columns kx together with their mirrors -kx (the split of C into S_x and
+// S_y needs C(-k)), transforms them over y, multiplies by W^ and transforms back
+// over ky, in shared memory, writing H_x + i H_y and H_z in place; k_fft_inv_rows
+// transforms the rows back over kx and writes the field.  Radix-2 Stockham stages
+// in shared memory, all threads of a CTA taking (row, butterfly) tasks with one
+// barrier per stage.  L must be a power of two, 8 <= L <= 1024.
+#include <algorithm>
+
 #include <cuda_bf16.h>
 
 #include "fft_field.cuh"
@@ -25,112 +31,154 @@ namespace {
 
 constexpr float kPiF = 3.14159265358979f;
 
-// Radix-2 Stockham auto-sort FFT of nrows rows of length L (in place in global
-// memory through shared memory).  Stage with half-span Ns: output
+// Radix-2 Stockham auto-sort stages over nrow rows of length L in shared memory
+// (x, with y the ping-pong buffer).  Stage with half-span Ns: output
 // y[(t/Ns)*2Ns + t%Ns] = a + w b, y[... + Ns] = a - w b with a = x[t],
-// b = x[t + L/2], w = exp(-+ 2 pi i (t%Ns) / (2 Ns)) = tw[(t%Ns) * L/(2Ns)],
-// tw[m] = exp(-+ 2 pi i m / L) tabulated once per CTA (the same sincospif values
-// as per-butterfly evaluation: the fractions k/Ns and 2m/L are equal and exact).
+// b = x[t + L/2], w = exp(-+ 2 pi i (t%Ns) / (2 Ns)) = tw[(t%Ns) * L/(2Ns)] (conjugated
+// for the inverse), tw[m] = exp(-2 pi i m / L).  Returns the buffer with the result.
 template <bool INV>
-__global__ void k_fft_rows(float2 *data, int L, int logL, long long nrows) {
-    extern __shared__ float2 fbuf[];
-    const int half = L >> 1;
-    const int rpc = blockDim.x / half;                  // rows per CTA
-    const int rr = threadIdx.x / half, t = threadIdx.x % half;
-    const long long row = (long long)blockIdx.x * rpc + rr;
-    if (rpc == 0) return;
-    float2 *tw = fbuf + (size_t)rpc * 2 * L;             // [L/2]
-    for (int m = threadIdx.x; m < half; m += blockDim.x) {
-        float sw, cw;
-        sincospif((INV ? 1.0f : -1.0f) * (float)(2 * m) / (float)L, &sw, &cw);
-        tw[m] = make_float2(cw, sw);
-    }
-    float2 *x = fbuf + (size_t)rr * 2 * L, *y = x + L;
-    const bool valid = row < nrows;
-    float2 *g = data + (valid ? row : 0) * L;
-    if (valid) {
-        x[t] = g[t];
-        x[t + half] = g[t + half];
-    }
-    __syncthreads();
+__device__ float2 *stockham(float2 *x, float2 *y, const float2 *tw, int L, int logL, int nrow) {
+    const int half = L >> 1, ntask = nrow * half;
     for (int s = 0; s < logL; ++s) {
-        const int Ns = 1 << s;
-        const int k = t & (Ns - 1);
-        const float2 wv = tw[k << (logL - 1 - s)];
-        const float sw = wv.y, cw = wv.x;
-        const float2 a = x[t], b0 = x[t + half];
-        const float2 b = make_float2(b0.x * cw - b0.y * sw, b0.x * sw + b0.y * cw);
-        const int j = ((t >> s) << (s + 1)) + k;
-        y[j] = make_float2(a.x + b.x, a.y + b.y);
-        y[j + Ns] = make_float2(a.x - b.x, a.y - b.y);
+        const int Ns = 1 << s, tws = logL - 1 - s;
+        for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
+            const int tt = task & (half - 1), base = task - tt;   // base = row * L / 2
+            const float2 *xr = x + 2 * base;
+            float2 *yr = y + 2 * base;
+            const int k = tt & (Ns - 1);
+            const float2 wv = tw[k << tws];
+            const float ws = INV ? -wv.y : wv.y;
+            const float2 a = xr[tt], b0 = xr[tt + half];
+            const float2 b = make_float2(b0.x * wv.x - b0.y * ws, b0.x * ws + b0.y * wv.x);
+            const int jj = ((tt >> s) << (s + 1)) + k;
+            yr[jj] = make_float2(a.x + b.x, a.y + b.y);
+            yr[jj + Ns] = make_float2(a.x - b.x, a.y - b.y);
+        }
         __syncthreads();
         float2 *tmp = x;
         x = y;
         y = tmp;
     }
-    if (valid) {
-        g[t] = x[t];
-        g[t + half] = x[t + half];
+    return x;
+}
+
+__device__ __forceinline__ void fft_twiddles(float2 *tw, int L) {
+    for (int m = threadIdx.x; m < (L >> 1); m += blockDim.x) {
+        float sw, cw;
+        sincospif(-(float)(2 * m) / (float)L, &sw, &cw);
+        tw[m] = make_float2(cw, sw);
     }
 }
 
-// out[b][c][r] = in[b][r][c] for L x L matrices (32 x 32 tiles).
-__global__ void k_transpose(const float2 *__restrict__ in, float2 *__restrict__ out, int L) {
-    __shared__ float2 tile[32][33];
-    const size_t base = (size_t)blockIdx.z * L * L;
-    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
-    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-        const int r = by + i, c = bx + threadIdx.x;
-        if (r < L && c < L) tile[i][threadIdx.x] = in[base + (size_t)r * L + c];
+// Forward row transforms from the spins: C[r][y][kx] = FFT_x(s_x + i s_y),
+// Z[r][y][kx] = FFT_x(s_z); a CTA takes Y rows of one replica.
+__global__ void k_fft_fwd_rows(const float *__restrict__ spins, int L, int logL, int Y, float2 *C, float2 *Z) {
+    extern __shared__ float2 fbuf[];
+    const int N = L * L, r = blockIdx.y, y0 = blockIdx.x * Y;
+    float2 *tw = fbuf, *x = tw + (L >> 1), *yb = x + (size_t)2 * Y * L;   // x: [2Y][L] (C rows, then Z rows)
+    fft_twiddles(tw, L);
+    const float *s = spins + (size_t)r * 3 * N;
+    for (int i = threadIdx.x; i < Y * L; i += blockDim.x) {
+        const int q = (y0 + i / L) * L + i % L;
+        x[i] = make_float2(s[q], s[N + q]);
+        x[(size_t)Y * L + i] = make_float2(s[2 * N + q], 0.0f);
     }
     __syncthreads();
-    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-        const int r = bx + i, c = by + threadIdx.x;
-        if (r < L && c < L) out[base + (size_t)r * L + c] = tile[threadIdx.x][i];
+    const float2 *res = stockham<false>(x, yb, tw, L, logL, 2 * Y);
+    float2 *Cr = C + (size_t)r * N + (size_t)y0 * L, *Zr = Z + (size_t)r * N + (size_t)y0 * L;
+    for (int i = threadIdx.x; i < Y * L; i += blockDim.x) {
+        Cr[i] = res[i];
+        Zr[i] = res[(size_t)Y * L + i];
     }
 }
 
-__global__ void k_pack(const float *__restrict__ spins, int N, int R, float2 *C, float2 *Z) {
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (size_t)N * R) return;
-    const size_t r = i / N, p = i % N;
-    const float *s = spins + r * 3 * N;
-    C[i] = make_float2(s[p], s[N + p]);
-    Z[i] = make_float2(s[2 * N + p], 0.0f);
+// Columns kx in [tb*CT, tb*CT + CT) of [0, L/2] and their mirrors (L - kx) mod L, of C
+// and Z: transform over y, spectral product (S_x = (C + conj C(-k))/2,
+// S_y = (C - conj C(-k))/(2i), H_x + i H_y = (W^xx S_x + W^xy S_y) + i (W^xy S_x + W^yy S_y),
+// H_z = W^zz Z, W^ real and stored [kx][ky]), inverse transform over ky; the result
+// replaces the columns of C (H_x + i H_y) and Z (H_z).
+__global__ void k_fft_cols_conv(float2 *C, float2 *Z, const float *__restrict__ What, int L, int logL, int CT) {
+    extern __shared__ float2 fbuf[];
+    __shared__ int s_col[32], s_mir[32];
+    const int N = L * L, r = blockIdx.y, k0 = blockIdx.x * CT, hl = L >> 1;
+    // the tile's distinct columns: kx, then its mirror when different
+    if (threadIdx.x == 0) {
+        int nc = 0;
+        for (int kx = k0; kx < k0 + CT && kx <= hl; ++kx) {
+            s_col[nc++] = kx;
+            const int m = (L - kx) & (L - 1);
+            if (m != kx) s_col[nc++] = m;
+        }
+        for (int c = nc; c < 32; ++c) s_col[c] = -1;
+        for (int c = 0; c < nc; ++c) {
+            const int m = (L - s_col[c]) & (L - 1);
+            int cm = c;
+            for (int d = 0; d < nc; ++d)
+                if (s_col[d] == m) cm = d;
+            s_mir[c] = cm;
+        }
+    }
+    __syncthreads();
+    int nc = 0;
+    while (nc < 32 && s_col[nc] >= 0) ++nc;
+    float2 *tw = fbuf, *x = tw + hl, *yb = x + (size_t)2 * nc * L;   // x: [2nc][L] (C columns, then Z columns)
+    fft_twiddles(tw, L);
+    float2 *Cr = C + (size_t)r * N, *Zr = Z + (size_t)r * N;
+    for (int i = threadIdx.x; i < nc * L; i += blockDim.x) {
+        const int yy = i / nc, c = i % nc;                // consecutive threads: neighbouring columns of a row
+        const size_t g = (size_t)yy * L + s_col[c];
+        x[(size_t)c * L + yy] = Cr[g];
+        x[(size_t)(nc + c) * L + yy] = Zr[g];
+    }
+    __syncthreads();
+    float2 *X = stockham<false>(x, yb, tw, L, logL, 2 * nc);
+    float2 *Yv = X == x ? yb : x;
+    for (int i = threadIdx.x; i < nc * L; i += blockDim.x) {
+        const int c = i / L, ky = i % L, kx = s_col[c];
+        const int kym = (L - ky) & (L - 1);
+        const float2 cv = X[(size_t)c * L + ky], cm = X[(size_t)s_mir[c] * L + kym];
+        const float2 sx = make_float2(0.5f * (cv.x + cm.x), 0.5f * (cv.y - cm.y));
+        const float2 sy = make_float2(0.5f * (cv.y + cm.y), -0.5f * (cv.x - cm.x));
+        const size_t wi = (size_t)kx * L + ky;
+        const float wxx = What[wi], wxy = What[N + wi], wyy = What[2 * N + wi], wzz = What[3 * N + wi];
+        const float2 hx = make_float2(wxx * sx.x + wxy * sy.x, wxx * sx.y + wxy * sy.y);
+        const float2 hy = make_float2(wxy * sx.x + wyy * sy.x, wxy * sx.y + wyy * sy.y);
+        Yv[(size_t)c * L + ky] = make_float2(hx.x - hy.y, hx.y + hy.x);
+        const float2 z = X[(size_t)(nc + c) * L + ky];
+        Yv[(size_t)(nc + c) * L + ky] = make_float2(wzz * z.x, wzz * z.y);
+    }
+    __syncthreads();
+    const float2 *res = stockham<true>(Yv, X, tw, L, logL, 2 * nc);
+    for (int i = threadIdx.x; i < nc * L; i += blockDim.x) {
+        const int yy = i / nc, c = i % nc;
+        const size_t g = (size_t)yy * L + s_col[c];
+        Cr[g] = res[(size_t)c * L + yy];
+        Zr[g] = res[(size_t)(nc + c) * L + yy];
+    }
 }
 
-// Spectral product in the transposed layout i = kx*L + ky.
-__global__ void k_spectral(const float2 *__restrict__ C, float2 *__restrict__ Hxy, float2 *Z,
-                           const float *__restrict__ What, int L, int R) {
-    const int N = L * L;
-    const size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= (size_t)N * R) return;
-    const size_t r = g / N;
-    const int i = (int)(g % N);
-    const int kx = i / L, ky = i % L;
-    const int ni = ((L - kx) & (L - 1)) * L + ((L - ky) & (L - 1));
-    const float2 c = C[r * N + i], cm = C[r * N + ni];
-    // S_x = (c + conj cm)/2, S_y = (c - conj cm)/(2i)
-    const float2 sx = make_float2(0.5f * (c.x + cm.x), 0.5f * (c.y - cm.y));
-    const float2 sy = make_float2(0.5f * (c.y + cm.y), -0.5f * (c.x - cm.x));
-    const float wxx = What[i], wxy = What[N + i], wyy = What[2 * N + i], wzz = What[3 * N + i];
-    const float2 hx = make_float2(wxx * sx.x + wxy * sy.x, wxx * sx.y + wxy * sy.y);
-    const float2 hy = make_float2(wxy * sx.x + wyy * sy.x, wxy * sx.y + wyy * sy.y);
-    Hxy[r * N + i] = make_float2(hx.x - hy.y, hx.y + hy.x);      // H_x + i H_y
-    const float2 z = Z[r * N + i];
-    Z[r * N + i] = make_float2(wzz * z.x, wzz * z.y);
-}
-
-__global__ void k_unpack(const float2 *__restrict__ Hxy, const float2 *__restrict__ Hz, int N, int R, float scale,
-                         float *field) {
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (size_t)N * R) return;
-    const size_t r = i / N, p = i % N;
-    float *f = field + r * 3 * N;
-    const float2 a = Hxy[i];
-    f[p] = a.x * scale;
-    f[N + p] = a.y * scale;
-    f[2 * N + p] = Hz[i].x * scale;
+// Inverse row transforms over kx and the field: h_x + i h_y = IFFT(H_x + i H_y),
+// h_z = Re IFFT(H_z), scaled by 1/N.
+__global__ void k_fft_inv_rows(const float2 *__restrict__ C, const float2 *__restrict__ Z, int L, int logL, int Y,
+                               float scale, float *field) {
+    extern __shared__ float2 fbuf[];
+    const int N = L * L, r = blockIdx.y, y0 = blockIdx.x * Y;
+    float2 *tw = fbuf, *x = tw + (L >> 1), *yb = x + (size_t)2 * Y * L;
+    fft_twiddles(tw, L);
+    const float2 *Cr = C + (size_t)r * N + (size_t)y0 * L, *Zr = Z + (size_t)r * N + (size_t)y0 * L;
+    for (int i = threadIdx.x; i < Y * L; i += blockDim.x) {
+        x[i] = Cr[i];
+        x[(size_t)Y * L + i] = Zr[i];
+    }
+    __syncthreads();
+    const float2 *res = stockham<true>(x, yb, tw, L, logL, 2 * Y);
+    float *f = field + (size_t)r * 3 * N + (size_t)y0 * L;
+    for (int i = threadIdx.x; i < Y * L; i += blockDim.x) {
+        const float2 a = res[i];
+        f[i] = a.x * scale;
+        f[N + i] = a.y * scale;
+        f[2 * N + i] = res[(size_t)Y * L + i].x * scale;
+    }
 }
 
 // W^(kx, ky) = sum_{x,y} W~(x, y) exp(-2 pi i (kx x + ky y)/L), real for the even
@@ -411,26 +459,11 @@ int ilog2(int v) {
     return b;
 }
 
-cudaError_t rows(float2 *data, int L, long long nrows, bool inv, cudaStream_t st) {
-    const int half = L / 2;
-    const int threads = half >= 256 ? half : 256;
-    const int rpc = threads / half;
-    const unsigned blocks = (unsigned)((nrows + rpc - 1) / rpc);
-    const size_t smem = sizeof(float2) * (2 * L * rpc + half);
-    if (inv) {
-        cudaFuncSetAttribute(k_fft_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_fft_rows<true><<<blocks, threads, smem, st>>>(data, L, ilog2(L), nrows);
-    } else {
-        cudaFuncSetAttribute(k_fft_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_fft_rows<false><<<blocks, threads, smem, st>>>(data, L, ilog2(L), nrows);
-    }
-    return cudaGetLastError();
-}
+int fft_rows_per_cta(int L) { return L >= 256 ? 1 : std::min(L, 256 / L); }   // rows Y of a row-pass CTA
 
-cudaError_t transpose(const float2 *in, float2 *out, int L, int R, cudaStream_t st) {
-    dim3 grid((L + 31) / 32, (L + 31) / 32, R), block(32, 8);
-    k_transpose<<<grid, block, 0, st>>>(in, out, L);
-    return cudaGetLastError();
+int fft_cols_per_tile(int L) {      // columns kx (plus mirrors) of a column-pass CTA
+    const int ct = 1024 / L;
+    return ct < 1 ? 1 : (ct > 8 ? 8 : ct);
 }
 
 }  // namespace
@@ -455,29 +488,20 @@ cudaError_t launch_build_what(int L, const double *W64, float *What, cudaStream_
 
 cudaError_t launch_fft_field(int L, int R, const float *spins, const float *What, float2 *scratch, float *field,
                              cudaStream_t st) {
-    const int N = L * L;
+    const int N = L * L, logL = ilog2(L);
     const size_t tot = (size_t)N * R;
-    float2 *C = scratch, *Z = scratch + tot, *T = scratch + 2 * tot;
-    const unsigned nb = (unsigned)((tot + 255) / 256);
+    float2 *C = scratch, *Z = scratch + tot;
+    const int Y = fft_rows_per_cta(L), CT = fft_cols_per_tile(L);
+    const int rthreads = std::min(1024, std::max(64, Y * L)), cthreads = 1024;
+    const size_t rsmem = sizeof(float2) * ((size_t)(L / 2) + (size_t)4 * Y * L);
+    const size_t csmem = sizeof(float2) * ((size_t)(L / 2) + (size_t)4 * 2 * CT * L);
     cudaError_t e;
-    k_pack<<<nb, 256, 0, st>>>(spins, N, R, C, Z);
-    // forward: rows over x, transpose to [x][y], rows over y -> spectra [kx][ky]
-    if ((e = rows(C, L, (long long)L * R, false, st)) != cudaSuccess) return e;
-    if ((e = rows(Z, L, (long long)L * R, false, st)) != cudaSuccess) return e;
-    if ((e = transpose(C, T, L, R, st)) != cudaSuccess) return e;
-    if ((e = rows(T, L, (long long)L * R, false, st)) != cudaSuccess) return e;
-    if ((e = transpose(Z, C, L, R, st)) != cudaSuccess) return e;
-    if ((e = rows(C, L, (long long)L * R, false, st)) != cudaSuccess) return e;
-    // now T = C^ and C = Z^ (both [kx][ky]); spectral product: T -> Z (H_xy), C (H_z) in place
-    k_spectral<<<nb, 256, 0, st>>>(T, Z, C, What, L, R);
-    // inverse: rows over ky, transpose back to [y][kx], rows over kx
-    if ((e = rows(Z, L, (long long)L * R, true, st)) != cudaSuccess) return e;
-    if ((e = rows(C, L, (long long)L * R, true, st)) != cudaSuccess) return e;
-    if ((e = transpose(Z, T, L, R, st)) != cudaSuccess) return e;
-    if ((e = rows(T, L, (long long)L * R, true, st)) != cudaSuccess) return e;
-    if ((e = transpose(C, Z, L, R, st)) != cudaSuccess) return e;
-    if ((e = rows(Z, L, (long long)L * R, true, st)) != cudaSuccess) return e;
-    k_unpack<<<nb, 256, 0, st>>>(T, Z, N, R, 1.0f / (float)N, field);
+    if ((e = cudaFuncSetAttribute(k_fft_fwd_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_fft_inv_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_fft_cols_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem)) != cudaSuccess) return e;
+    k_fft_fwd_rows<<<dim3(L / Y, R), rthreads, rsmem, st>>>(spins, L, logL, Y, C, Z);
+    k_fft_cols_conv<<<dim3((L / 2 + 1 + CT - 1) / CT, R), cthreads, csmem, st>>>(C, Z, What, L, logL, CT);
+    k_fft_inv_rows<<<dim3(L / Y, R), rthreads, rsmem, st>>>(C, Z, L, logL, Y, 1.0f / (float)N, field);
     return cudaGetLastError();
 }
 
