@@ -252,14 +252,15 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec_init(int L, int l, const 
 // k_spec_wfield: the field spectra of the window's offsets o_w from the spectra at
 // the window's start, H_w(K) = sum_e omega^(K.sigma) T_{(o_w - e) mod l}(K) S_e(K).
 // Thread = (replica r, wave vector K, window slot w) over a chunk of the cell
-// offsets e (grid z); warp w of a CTA is slot w for 4 replicas x 8 wave vectors,
-// so the CTA's warps read the same S_e through L1.  Partial spectra per chunk,
+// offsets e (grid z); warp w of a CTA is slot w for 2 replicas x 16 wave vectors
+// (a warp's table and spectra loads are 128-byte runs), so the CTA's warps read the
+// same S_e through L1.  Partial spectra per chunk,
 // Hw[z][r][w][3][n], are summed by the update in chunk order.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kSpecThreads) k_spec_wfield(const SpecConfig cfg, const SpecBuffers b) {
     const int L = cfg.L, l = cfg.l, C = L / l, n = C * C, ll = l * l, R = cfg.R;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int th = blockIdx.x * 8 + (lane & 7), r = blockIdx.y * 4 + (lane >> 3);
+    const int th = blockIdx.x * 16 + (lane & 15), r = blockIdx.y * 2 + (lane >> 4);
     const bool mine = th < half_count(C) && r < R && w < cfg.wlen;
     const int K = mine ? half_wave(th, C) : 0;
     const int ov = mine ? b.off[(size_t)r * ll + cfg.k + w] : -1;
@@ -661,7 +662,7 @@ int spectral_window(int L, int l) {
 int spectral_esplit(int L, int l, int R, int nsm) {
     // chunks of the cell offsets: about three CTAs of the window field per SM
     const long long ll = (long long)l * l;
-    const long long tiles = ((half_count(L / l) + 7) / 8) * ((R + 3) / 4);
+    const long long tiles = ((half_count(L / l) + 15) / 16) * ((R + 1) / 2);
     long long z = (3LL * nsm + tiles - 1) / tiles;
     z = std::min(z, std::max(1LL, ll / 8));   // at least 8 cell offsets a chunk
     z = std::min(z, 16LL);                    // the update loads all chunks of a spectrum at once
@@ -699,7 +700,7 @@ cudaError_t launch_spec_offsets(const SpecConfig &c, const SpecBuffers &b, cudaS
 
 cudaError_t launch_spec_wfield(const SpecConfig &c, const SpecBuffers &b, cudaStream_t st) {
     const int C = c.L / c.l;
-    k_spec_wfield<<<dim3((half_count(C) + 7) / 8, (c.R + 3) / 4, c.esplit), kSpecThreads, 0, st>>>(c, b);
+    k_spec_wfield<<<dim3((half_count(C) + 15) / 16, (c.R + 1) / 2, c.esplit), kSpecThreads, 0, st>>>(c, b);
     return cudaGetLastError();
 }
 
