@@ -574,7 +574,7 @@ def main():
         lat.init_spins(2, host_in.numpy())
         lat.sweep(S, 1, stream)
         lat.get_spins(out=host_out, stream=stream)
-        lat.observables_batch()
+        lat.observables_arrays()
     barrier()
     e_dt = time.perf_counter() - e0
     e2e = {"value": ws * R * L * L * S * e2e_steps / e_dt, "unit": "site-updates/s",

@@ -71,6 +71,13 @@ class mc_obs(C.Structure):
         return d
 
 
+# the same record as a numpy structured type (all fields 8 bytes: no padding)
+OBS_DTYPE = np.dtype([("samples", "<i8"), ("mean", "<f8", (MC_NOBS,)), ("var", "<f8", (MC_NOBS,)),
+                      ("err_naive", "<f8", (MC_NOBS,)), ("err", "<f8", (MC_NOBS,)), ("tau_int", "<f8", (MC_NOBS,)),
+                      ("eta", "<f8"), ("energy", "<f8"), ("accepted", "<i8"), ("attempted", "<i8")])
+assert OBS_DTYPE.itemsize == C.sizeof(mc_obs)
+
+
 class mc_request(C.Structure):
     _fields_ = [("L", C.c_int), ("l", C.c_int), ("replicas", C.c_int),
                 ("J", C.c_double), ("C_D", C.c_double), ("K2", C.c_double), ("K4", C.c_double), ("T", C.c_double),
@@ -278,13 +285,29 @@ class Lattice:
         _ck(_lib.mc_observables(self.h, replica, C.byref(o)))
         return o.as_dict()
 
-    def observables_batch(self, first=0, count=None) -> list:
-        """observables() of replicas first .. first+count-1 with one read-back."""
+    def observables_arrays(self, first=0, count=None) -> np.ndarray:
+        """Observables of replicas first .. first+count-1 with one read-back, as a numpy
+        record array of OBS_DTYPE (fields samples, mean/var/err_naive/err/tau_int
+        [count][MC_NOBS] in OBS_NAMES order, eta, energy, accepted, attempted)."""
         if count is None:
             count = self.R - first
-        arr = (mc_obs * max(count, 1))()
-        _ck(_lib.mc_observables_batch(self.h, first, count, arr))
-        return [arr[i].as_dict() for i in range(count)]
+        out = np.zeros(max(count, 1), OBS_DTYPE)
+        _ck(_lib.mc_observables_batch(self.h, first, count, out.ctypes.data_as(C.POINTER(mc_obs))))
+        return out[:count]
+
+    def observables_batch(self, first=0, count=None) -> list:
+        """observables() of replicas first .. first+count-1 with one read-back."""
+        a = self.observables_arrays(first, count)
+        cols = {f: a[f].tolist() for f in OBS_DTYPE.names}
+        res = []
+        for i in range(len(a)):
+            d = {"samples": cols["samples"][i], "eta": cols["eta"][i], "energy": cols["energy"][i],
+                 "accepted": cols["accepted"][i], "attempted": cols["attempted"][i]}
+            for k, nm in enumerate(OBS_NAMES):
+                d[nm] = {"mean": cols["mean"][i][k], "var": cols["var"][i][k], "err_naive": cols["err_naive"][i][k],
+                         "err": cols["err"][i][k], "tau_int": cols["tau_int"][i][k]}
+            res.append(d)
+        return res
 
     def reset_observables(self):
         _ck(_lib.mc_reset_observables(self.h))

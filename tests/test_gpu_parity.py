@@ -230,6 +230,12 @@ def test_observables_batch_equals_single_reads(dipmc):
         for r in range(R):
             assert same(one[r], many[r]), r
         assert same(part[0], many[2]) and same(part[1], many[3])
+        arr = lat.observables_arrays()
+        assert arr["samples"].tolist() == [m["samples"] for m in many]
+        for k, nm in enumerate(dipmc.OBS_NAMES):
+            np.testing.assert_array_equal(arr["mean"][:, k], [m[nm]["mean"] for m in many])
+            np.testing.assert_array_equal(arr["err"][:, k], [m[nm]["err"] for m in many])
+        np.testing.assert_array_equal(arr["energy"], [m["energy"] for m in many])
         with pytest.raises(dipmc.McError) as e:
             lat.observables_batch(4, 2)
         assert e.value.code == dipmc.MC_EINVAL
