@@ -375,11 +375,14 @@ def test_window_paths_match_oracle(dipmc, path, case):
         assert abs(Eg_tracked[r] - Eg_full[r]) < 1e-5 * (L * L) * (1 + abs(J) + abs(K2) + abs(K4) + CD * 10)
 
 
-def test_tensor_path_bench_configuration(dipmc):
-    """256 replicas x L = 64 on the tensor path (the benchmark's configuration): one
-    traced sweep, sampled replicas compared attempt by attempt with the oracle."""
-    L, l, R, A = 64, 32, 256, 64
+@pytest.mark.parametrize("R,sample", [(256, (0, 1, 100, 200, 255)), (300, (0, 255, 256, 299))])
+def test_tensor_path_bench_configuration(dipmc, R, sample):
+    """256 replicas x L = 64 on the tensor path (the benchmark's configuration), and 300
+    (a second, ragged N-tile of 44 replicas): one traced sweep, sampled replicas
+    compared attempt by attempt with the oracle."""
+    L, l, A = 64, 32, 64
     lad = [(F32(1.0), F32(0.1), F32(k2), F32(k4), F32(T)) for (T, k2, k4) in inputs.ladder(16, 16)]
+    lad = [lad[r % len(lad)] for r in range(R)]
     s0 = inputs.random_spins(L, R, seed=2024)
     with dipmc.Lattice(L, l, R, 1) as lat:
         lat.precompute_W(A, True)
@@ -391,7 +394,7 @@ def test_tensor_path_bench_configuration(dipmc):
         sg = lat.get_spins().astype(np.float64)
     W = oracle_W(L, A)
     worst = 0.0
-    for r in (0, 1, 100, 200, 255):
+    for r in sample:
         J, CD, K2, K4, T = lad[r]
         p = orc.params(L, l, J, CD, K2, K4, T, proposal=0, cone=0.5, schedule=0, seed=1, replica=r)
         o = orc.sweeps(p, W, s0[r], 0, 1)
