@@ -31,28 +31,56 @@ namespace {
 
 constexpr float kPiF = 3.14159265358979f;
 
-// Radix-2 Stockham auto-sort stages over nrow rows of length L in shared memory
-// (x, with y the ping-pong buffer).  Stage with half-span Ns: output
-// y[(t/Ns)*2Ns + t%Ns] = a + w b, y[... + Ns] = a - w b with a = x[t],
-// b = x[t + L/2], w = exp(-+ 2 pi i (t%Ns) / (2 Ns)) = tw[(t%Ns) * L/(2Ns)] (conjugated
-// for the inverse), tw[m] = exp(-2 pi i m / L).  Returns the buffer with the result.
+// Stockham auto-sort stages over nrow rows of length L in shared memory (x, with y
+// the ping-pong buffer): one radix-2 stage when log2 L is odd, then radix-4 stages.
+// A radix-R stage with span Ns takes, for t in [0, L/R) and k = t % Ns, the inputs
+// v_r = x[t + r L/R] w^(r k), w = exp(-+ 2 pi i / (R Ns)) = tw[L/(R Ns)] (tw[m] =
+// exp(-2 pi i m / L), conjugated for the inverse), their R-point DFT b_m, and writes
+// y[(t - k) R + k + m Ns] = b_m; the span grows by R per stage.  All threads of the
+// CTA take (row, butterfly) tasks, one barrier per stage.  Returns the result buffer.
+__device__ __forceinline__ float2 cmulw(float2 a, float2 w, bool inv) {   // a * w (or * conj w)
+    const float ws = inv ? -w.y : w.y;
+    return make_float2(a.x * w.x - a.y * ws, a.x * ws + a.y * w.x);
+}
+
 template <bool INV>
 __device__ float2 *stockham(float2 *x, float2 *y, const float2 *tw, int L, int logL, int nrow) {
-    const int half = L >> 1, ntask = nrow * half;
-    for (int s = 0; s < logL; ++s) {
-        const int Ns = 1 << s, tws = logL - 1 - s;
+    int lgNs = 0;
+    if (logL & 1) {                                        // radix 2, Ns = 1: no twiddles
+        const int half = L >> 1, ntask = nrow * half;
         for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
-            const int tt = task & (half - 1), base = task - tt;   // base = row * L / 2
-            const float2 *xr = x + 2 * base;
-            float2 *yr = y + 2 * base;
-            const int k = tt & (Ns - 1);
-            const float2 wv = tw[k << tws];
-            const float ws = INV ? -wv.y : wv.y;
-            const float2 a = xr[tt], b0 = xr[tt + half];
-            const float2 b = make_float2(b0.x * wv.x - b0.y * ws, b0.x * ws + b0.y * wv.x);
-            const int jj = ((tt >> s) << (s + 1)) + k;
-            yr[jj] = make_float2(a.x + b.x, a.y + b.y);
-            yr[jj + Ns] = make_float2(a.x - b.x, a.y - b.y);
+            const int tt = task & (half - 1), base = 2 * (task - tt);
+            const float2 a = x[base + tt], b = x[base + tt + half];
+            y[base + 2 * tt] = make_float2(a.x + b.x, a.y + b.y);
+            y[base + 2 * tt + 1] = make_float2(a.x - b.x, a.y - b.y);
+        }
+        __syncthreads();
+        float2 *tmp = x;
+        x = y;
+        y = tmp;
+        lgNs = 1;
+    }
+    const int q = L >> 2, ntask = nrow * q;
+    for (; lgNs < logL; lgNs += 2) {
+        const int Ns = 1 << lgNs, sh = logL - 2 - lgNs;
+        for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
+            const int tt = task & (q - 1), base = (task >> (logL - 2)) * L;
+            const int k = tt & (Ns - 1), m1 = k << sh;
+            const float2 *xr = x + base;
+            const float2 v0 = xr[tt];
+            const float2 v1 = cmulw(xr[tt + q], tw[m1], INV);
+            const float2 v2 = cmulw(xr[tt + 2 * q], tw[2 * m1], INV);
+            const float2 v3 = cmulw(xr[tt + 3 * q], tw[3 * m1], INV);
+            // 4-point DFT, omega_4 = -i (forward) or +i (inverse)
+            const float2 s02 = make_float2(v0.x + v2.x, v0.y + v2.y), d02 = make_float2(v0.x - v2.x, v0.y - v2.y);
+            const float2 s13 = make_float2(v1.x + v3.x, v1.y + v3.y), d13 = make_float2(v1.x - v3.x, v1.y - v3.y);
+            // -i d13 (forward) or +i d13 (inverse)
+            const float2 r13 = INV ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);
+            float2 *yr = y + base + (tt - k) * 4 + k;
+            yr[0] = make_float2(s02.x + s13.x, s02.y + s13.y);
+            yr[Ns] = make_float2(d02.x + r13.x, d02.y + r13.y);
+            yr[2 * Ns] = make_float2(s02.x - s13.x, s02.y - s13.y);
+            yr[3 * Ns] = make_float2(d02.x - r13.x, d02.y - r13.y);
         }
         __syncthreads();
         float2 *tmp = x;
@@ -62,8 +90,8 @@ __device__ float2 *stockham(float2 *x, float2 *y, const float2 *tw, int L, int l
     return x;
 }
 
-__device__ __forceinline__ void fft_twiddles(float2 *tw, int L) {
-    for (int m = threadIdx.x; m < (L >> 1); m += blockDim.x) {
+__device__ __forceinline__ void fft_twiddles(float2 *tw, int L) {   // tw[m] = exp(-2 pi i m / L), m < L
+    for (int m = threadIdx.x; m < L; m += blockDim.x) {
         float sw, cw;
         sincospif(-(float)(2 * m) / (float)L, &sw, &cw);
         tw[m] = make_float2(cw, sw);
@@ -75,7 +103,7 @@ __device__ __forceinline__ void fft_twiddles(float2 *tw, int L) {
 __global__ void k_fft_fwd_rows(const float *__restrict__ spins, int L, int logL, int Y, float2 *C, float2 *Z) {
     extern __shared__ float2 fbuf[];
     const int N = L * L, r = blockIdx.y, y0 = blockIdx.x * Y;
-    float2 *tw = fbuf, *x = tw + (L >> 1), *yb = x + (size_t)2 * Y * L;   // x: [2Y][L] (C rows, then Z rows)
+    float2 *tw = fbuf, *x = tw + L, *yb = x + (size_t)2 * Y * L;   // x: [2Y][L] (C rows, then Z rows)
     fft_twiddles(tw, L);
     const float *s = spins + (size_t)r * 3 * N;
     for (int i = threadIdx.x; i < Y * L; i += blockDim.x) {
@@ -121,7 +149,7 @@ __global__ void k_fft_cols_conv(float2 *C, float2 *Z, const float *__restrict__ 
     __syncthreads();
     int nc = 0;
     while (nc < 32 && s_col[nc] >= 0) ++nc;
-    float2 *tw = fbuf, *x = tw + hl, *yb = x + (size_t)2 * nc * L;   // x: [2nc][L] (C columns, then Z columns)
+    float2 *tw = fbuf, *x = tw + L, *yb = x + (size_t)2 * nc * L;   // x: [2nc][L] (C columns, then Z columns)
     fft_twiddles(tw, L);
     float2 *Cr = C + (size_t)r * N, *Zr = Z + (size_t)r * N;
     for (int i = threadIdx.x; i < nc * L; i += blockDim.x) {
@@ -163,7 +191,7 @@ __global__ void k_fft_inv_rows(const float2 *__restrict__ C, const float2 *__res
                                float scale, float *field) {
     extern __shared__ float2 fbuf[];
     const int N = L * L, r = blockIdx.y, y0 = blockIdx.x * Y;
-    float2 *tw = fbuf, *x = tw + (L >> 1), *yb = x + (size_t)2 * Y * L;
+    float2 *tw = fbuf, *x = tw + L, *yb = x + (size_t)2 * Y * L;
     fft_twiddles(tw, L);
     const float2 *Cr = C + (size_t)r * N + (size_t)y0 * L, *Zr = Z + (size_t)r * N + (size_t)y0 * L;
     for (int i = threadIdx.x; i < Y * L; i += blockDim.x) {
@@ -493,8 +521,8 @@ cudaError_t launch_fft_field(int L, int R, const float *spins, const float *What
     float2 *C = scratch, *Z = scratch + tot;
     const int Y = fft_rows_per_cta(L), CT = fft_cols_per_tile(L);
     const int rthreads = std::min(1024, std::max(64, Y * L)), cthreads = 1024;
-    const size_t rsmem = sizeof(float2) * ((size_t)(L / 2) + (size_t)4 * Y * L);
-    const size_t csmem = sizeof(float2) * ((size_t)(L / 2) + (size_t)4 * 2 * CT * L);
+    const size_t rsmem = sizeof(float2) * ((size_t)L + (size_t)4 * Y * L);
+    const size_t csmem = sizeof(float2) * ((size_t)L + (size_t)4 * 2 * CT * L);
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_fft_fwd_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_fft_inv_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem)) != cudaSuccess) return e;
