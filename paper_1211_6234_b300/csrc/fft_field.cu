@@ -44,12 +44,12 @@ __device__ __forceinline__ float2 cmulw(float2 a, float2 w, bool inv) {   // a *
 }
 
 template <bool INV>
-__device__ float2 *stockham(float2 *x, float2 *y, const float2 *tw, int L, int logL, int nrow) {
+__device__ float2 *stockham(float2 *x, float2 *y, const float2 *tw, int L, int logL, int nrow, int ld) {   // row stride ld
     int lgNs = 0;
     if (logL & 1) {                                        // radix 2, Ns = 1: no twiddles
         const int half = L >> 1, ntask = nrow * half;
         for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
-            const int tt = task & (half - 1), base = 2 * (task - tt);
+            const int tt = task & (half - 1), base = (task >> (logL - 1)) * ld;
             const float2 a = x[base + tt], b = x[base + tt + half];
             y[base + 2 * tt] = make_float2(a.x + b.x, a.y + b.y);
             y[base + 2 * tt + 1] = make_float2(a.x - b.x, a.y - b.y);
@@ -64,7 +64,7 @@ __device__ float2 *stockham(float2 *x, float2 *y, const float2 *tw, int L, int l
     for (; lgNs < logL; lgNs += 2) {
         const int Ns = 1 << lgNs, sh = logL - 2 - lgNs;
         for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
-            const int tt = task & (q - 1), base = (task >> (logL - 2)) * L;
+            const int tt = task & (q - 1), base = (task >> (logL - 2)) * ld;
             const int k = tt & (Ns - 1), m1 = k << sh;
             const float2 *xr = x + base;
             const float2 v0 = xr[tt];
@@ -112,7 +112,7 @@ __global__ void k_fft_fwd_rows(const float *__restrict__ spins, int L, int logL,
         x[(size_t)Y * L + i] = make_float2(s[2 * N + q], 0.0f);
     }
     __syncthreads();
-    const float2 *res = stockham<false>(x, yb, tw, L, logL, 2 * Y);
+    const float2 *res = stockham<false>(x, yb, tw, L, logL, 2 * Y, L);
     float2 *Cr = C + (size_t)r * N + (size_t)y0 * L, *Zr = Z + (size_t)r * N + (size_t)y0 * L;
     for (int i = threadIdx.x; i < Y * L; i += blockDim.x) {
         Cr[i] = res[i];
@@ -149,39 +149,40 @@ __global__ void k_fft_cols_conv(float2 *C, float2 *Z, const float *__restrict__ 
     __syncthreads();
     int nc = 0;
     while (nc < 32 && s_col[nc] >= 0) ++nc;
-    float2 *tw = fbuf, *x = tw + L, *yb = x + (size_t)2 * nc * L;   // x: [2nc][L] (C columns, then Z columns)
+    const int ld = L + 1;   // padded rows: a row of the tile's columns lands in distinct banks
+    float2 *tw = fbuf, *x = tw + L, *yb = x + (size_t)2 * nc * ld;   // x: [2nc][ld] (C columns, then Z columns)
     fft_twiddles(tw, L);
     float2 *Cr = C + (size_t)r * N, *Zr = Z + (size_t)r * N;
     for (int i = threadIdx.x; i < nc * L; i += blockDim.x) {
         const int yy = i / nc, c = i % nc;                // consecutive threads: neighbouring columns of a row
         const size_t g = (size_t)yy * L + s_col[c];
-        x[(size_t)c * L + yy] = Cr[g];
-        x[(size_t)(nc + c) * L + yy] = Zr[g];
+        x[(size_t)c * ld + yy] = Cr[g];
+        x[(size_t)(nc + c) * ld + yy] = Zr[g];
     }
     __syncthreads();
-    float2 *X = stockham<false>(x, yb, tw, L, logL, 2 * nc);
+    float2 *X = stockham<false>(x, yb, tw, L, logL, 2 * nc, ld);
     float2 *Yv = X == x ? yb : x;
     for (int i = threadIdx.x; i < nc * L; i += blockDim.x) {
         const int c = i / L, ky = i % L, kx = s_col[c];
         const int kym = (L - ky) & (L - 1);
-        const float2 cv = X[(size_t)c * L + ky], cm = X[(size_t)s_mir[c] * L + kym];
+        const float2 cv = X[(size_t)c * ld + ky], cm = X[(size_t)s_mir[c] * ld + kym];
         const float2 sx = make_float2(0.5f * (cv.x + cm.x), 0.5f * (cv.y - cm.y));
         const float2 sy = make_float2(0.5f * (cv.y + cm.y), -0.5f * (cv.x - cm.x));
         const size_t wi = (size_t)kx * L + ky;
         const float wxx = What[wi], wxy = What[N + wi], wyy = What[2 * N + wi], wzz = What[3 * N + wi];
         const float2 hx = make_float2(wxx * sx.x + wxy * sy.x, wxx * sx.y + wxy * sy.y);
         const float2 hy = make_float2(wxy * sx.x + wyy * sy.x, wxy * sx.y + wyy * sy.y);
-        Yv[(size_t)c * L + ky] = make_float2(hx.x - hy.y, hx.y + hy.x);
-        const float2 z = X[(size_t)(nc + c) * L + ky];
-        Yv[(size_t)(nc + c) * L + ky] = make_float2(wzz * z.x, wzz * z.y);
+        Yv[(size_t)c * ld + ky] = make_float2(hx.x - hy.y, hx.y + hy.x);
+        const float2 z = X[(size_t)(nc + c) * ld + ky];
+        Yv[(size_t)(nc + c) * ld + ky] = make_float2(wzz * z.x, wzz * z.y);
     }
     __syncthreads();
-    const float2 *res = stockham<true>(Yv, X, tw, L, logL, 2 * nc);
+    const float2 *res = stockham<true>(Yv, X, tw, L, logL, 2 * nc, ld);
     for (int i = threadIdx.x; i < nc * L; i += blockDim.x) {
         const int yy = i / nc, c = i % nc;
         const size_t g = (size_t)yy * L + s_col[c];
-        Cr[g] = res[(size_t)c * L + yy];
-        Zr[g] = res[(size_t)(nc + c) * L + yy];
+        Cr[g] = res[(size_t)c * ld + yy];
+        Zr[g] = res[(size_t)(nc + c) * ld + yy];
     }
 }
 
@@ -199,7 +200,7 @@ __global__ void k_fft_inv_rows(const float2 *__restrict__ C, const float2 *__res
         x[(size_t)Y * L + i] = Zr[i];
     }
     __syncthreads();
-    const float2 *res = stockham<true>(x, yb, tw, L, logL, 2 * Y);
+    const float2 *res = stockham<true>(x, yb, tw, L, logL, 2 * Y, L);
     float *f = field + (size_t)r * 3 * N + (size_t)y0 * L;
     for (int i = threadIdx.x; i < Y * L; i += blockDim.x) {
         const float2 a = res[i];
@@ -522,7 +523,7 @@ cudaError_t launch_fft_field(int L, int R, const float *spins, const float *What
     const int Y = fft_rows_per_cta(L), CT = fft_cols_per_tile(L);
     const int rthreads = std::min(1024, std::max(64, Y * L)), cthreads = 1024;
     const size_t rsmem = sizeof(float2) * ((size_t)L + (size_t)4 * Y * L);
-    const size_t csmem = sizeof(float2) * ((size_t)L + (size_t)4 * 2 * CT * L);
+    const size_t csmem = sizeof(float2) * ((size_t)L + (size_t)4 * 2 * CT * (L + 1));
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_fft_fwd_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_fft_inv_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem)) != cudaSuccess) return e;
