@@ -488,7 +488,8 @@ int ilog2(int v) {
     return b;
 }
 
-int fft_rows_per_cta(int L) { return L >= 256 ? 1 : std::min(L, 256 / L); }   // rows Y of a row-pass CTA
+// rows Y of a row-pass CTA: 2Y rows of L/4 radix-4 butterflies, at least 256 a stage
+int fft_rows_per_cta(int L) { return L >= 512 ? 1 : std::min(L, 512 / L); }
 
 int fft_cols_per_tile(int L) {      // columns kx (plus mirrors) of a column-pass CTA
     const int ct = 1024 / L;
@@ -521,7 +522,7 @@ cudaError_t launch_fft_field(int L, int R, const float *spins, const float *What
     const size_t tot = (size_t)N * R;
     float2 *C = scratch, *Z = scratch + tot;
     const int Y = fft_rows_per_cta(L), CT = fft_cols_per_tile(L);
-    const int rthreads = std::min(1024, std::max(64, Y * L)), cthreads = 1024;
+    const int rthreads = std::min(1024, std::max(64, Y * L / 2)), cthreads = 1024;
     const size_t rsmem = sizeof(float2) * ((size_t)L + (size_t)4 * Y * L);
     const size_t csmem = sizeof(float2) * ((size_t)L + (size_t)4 * 2 * CT * (L + 1));
     cudaError_t e;
