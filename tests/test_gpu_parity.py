@@ -336,6 +336,8 @@ WCASES = [
     (32, 16, 2, 0, 1, 1),      # the paper's with-replacement schedule
     (64, 32, 2, 0, 0, 1),      # L = 64, S_w = 512 (F32) / 256 (tensor)
     (64, 32, 2, 128, 0, 1),    # L = 64, S_w = 512 on both paths
+    (80, 40, 2, 0, 0, 1),      # non-power-of-two L = 80: spectral operands (L = 2l, l % 8 == 0)
+    (80, 20, 1, 0, 0, 1),      # L = 80, 16 sites per sub-step: Toeplitz operands at a large lattice
 ]
 
 
