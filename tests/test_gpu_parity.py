@@ -432,7 +432,7 @@ def test_tensor_path_observables_match_direct(dipmc):
 
 
 # ---------------------------------------------------------------- FFT path
-@pytest.mark.parametrize("L,R", [(8, 1), (16, 3), (64, 2), (128, 1)])
+@pytest.mark.parametrize("L,R", [(8, 1), (16, 3), (32, 2), (64, 2), (128, 1)])
 def test_fft_full_field_matches_oracle(dipmc, L, R):
     s0 = inputs.random_spins(L, R, seed=40 + L)
     A = 16
@@ -448,11 +448,12 @@ def test_fft_full_field_matches_oracle(dipmc, L, R):
         assert err < 1e-5, err
 
 
-def test_fft_full_field_L256_sampled_sites(dipmc):
-    """L = 256 (N = 65536): the FFT field of two replicas at sampled sites against
-    the oracle's direct sum at those sites (energy of the same state as a check of
-    all sites)."""
-    L, R, A = 256, 2, 8
+@pytest.mark.parametrize("L", [256, 512, 1024])
+def test_fft_full_field_L256_sampled_sites(dipmc, L):
+    """L = 256, 512 (odd log2 L: a radix-2 stage) and 1024 (one column pair a tile): the
+    FFT field of two replicas at sampled sites against the oracle's direct sum at
+    those sites."""
+    R, A = 2, 8
     s0 = inputs.random_spins(L, R, seed=256)
     with dipmc.Lattice(L, 32, R, 3) as lat:
         lat.precompute_W(A, True)
