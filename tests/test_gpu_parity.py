@@ -237,6 +237,22 @@ def test_windowed_paths_checkpoint_and_batch_invariance(dipmc, path):
         assert o1["samples"] == o2["samples"] and o1["energy"] == o2["energy"]
 
 
+@pytest.mark.parametrize("path", [1, 2, 3, 4, 5, 6], ids=["direct", "window_f32", "tensor", "fft", "spectral", "incr"])
+def test_zero_sweeps_change_nothing(dipmc, path):
+    """mc_sweep with nsweeps = 0 on every path: the spins, the sweep counter and the
+    observables stay as they were."""
+    L, l = 32, 16
+    with dipmc.Lattice(L, l, 2, 3) as lat:
+        lat.precompute_W(16, True)
+        lat.set_field_path(path)
+        lat.init_spins(0)
+        lat.sweep(2, 1)
+        s0, c0, o0 = lat.get_spins(), lat.sweep_counter(), lat.observables(1)
+        lat.sweep(0, 1)
+        assert np.array_equal(lat.get_spins(), s0) and lat.sweep_counter() == c0
+        assert lat.observables(1)["samples"] == o0["samples"]
+
+
 def test_observables_batch_equals_single_reads(dipmc):
     """The batched read-back gives every replica's statistics exactly as the
     one-replica call does; an out-of-range batch is MC_EINVAL."""
