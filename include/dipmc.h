@@ -48,7 +48,7 @@ extern "C" {
 #define MC_ENOTREADY (-3) /* a prerequisite step was not done (e.g. W~ not computed) */
 #define MC_ETIMEOUT (-4)  /* a bounded device wait gave up */
 #define MC_ECUDA (-5)     /* a CUDA call failed; the message names it */
-#define MC_ENOSYS (-6)    /* no field path supports this (L, l) on this build */
+#define MC_ENOSYS (-6)    /* no field path supports this (L, l) in this library */
 
 /* Observable indices (per sample, once per measured sweep). */
 #define MC_OBS_ABS_M 0  /* |m| = |sum s| / N                        */

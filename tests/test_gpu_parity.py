@@ -67,7 +67,7 @@ def test_full_field_matches_oracle(dipmc, L, R):
 # ---------------------------------------------------------------- a1-a3: sweeps
 CASES = [
     # L, l, R, proposal, schedule, nsweeps, A
-    (16, 8, 2, 0, 0, 4, 64),    # BASELINE small config shape: L=16, l=L/2, cap 0.5 rad
+    (16, 8, 2, 0, 0, 4, 64),    # the small L = 16 workload: l = L/2, cap 0.5 rad
     (16, 16, 1, 0, 0, 2, 64),   # l = L: exact sequential (n = 1)
     (16, 4, 2, 0, 0, 3, 64),    # C = 4: 16 simultaneous sites
     (12, 6, 2, 1, 0, 4, 16),    # non-power-of-two L, ragged thread tail, sphere proposals
