@@ -15,9 +15,10 @@
 // tiles of columns kx together with their mirrors -kx (the split of C into S_x and
 // S_y needs C(-k)), transforms them over y, multiplies by W^ and transforms back
 // over ky, in shared memory, writing H_x + i H_y and H_z in place; k_fft_inv_rows
-// transforms the rows back over kx and writes the field.  Radix-2 Stockham stages
-// in shared memory, all threads of a CTA taking (row, butterfly) tasks with one
-// barrier per stage.  L must be a power of two, 8 <= L <= 1024.
+// transforms the rows back over kx and writes the field.  The transforms are
+// Stockham passes in shared memory (radix 16, after one pass of radix 2, 4 or 8
+// when log2 L is not a multiple of 4), each thread taking one DFT of the pass in
+// registers, one barrier per pass.  L must be a power of two, 8 <= L <= 1024.
 #include <algorithm>
 
 #include <cuda_bf16.h>
@@ -31,57 +32,143 @@ namespace {
 
 constexpr float kPiF = 3.14159265358979f;
 
-// Stockham auto-sort stages over nrow rows of length L in shared memory (x, with y
-// the ping-pong buffer): one radix-2 stage when log2 L is odd, then radix-4 stages.
-// A radix-R stage with span Ns takes, for t in [0, L/R) and k = t % Ns, the inputs
-// v_r = x[t + r L/R] w^(r k), w = exp(-+ 2 pi i / (R Ns)) = tw[L/(R Ns)] (tw[m] =
-// exp(-2 pi i m / L), conjugated for the inverse), their R-point DFT b_m, and writes
-// y[(t - k) R + k + m Ns] = b_m; the span grows by R per stage.  All threads of the
-// CTA take (row, butterfly) tasks, one barrier per stage.  Returns the result buffer.
+// Transforms of length L = 2^logL along rows of shared memory, by Stockham
+// auto-sort passes: a first pass of radix 2^(logL mod 4) when logL is not a
+// multiple of 4, then radix-16 passes.  A radix-R pass of span Ns takes, for t in
+// [0, L/R) and k = t mod Ns, the inputs v_r = x[t + r L/R] w^(r k),
+// w = exp(-+ 2 pi i / (R Ns)), their R-point DFT b_m (in registers), and writes
+// y[(t - k) R + k + m Ns] = b_m; the span grows by R per pass.
+//
+// Element i of a row sits at pad16(i) = i + i/16: with one slot of padding after
+// every 16 elements, the stride-R stores of a pass with a small span and the
+// strided loads land in distinct banks.  The twiddles w^(r k) of each pass with
+// Ns > 1 are a table [r - 1][k] in shared memory, read with consecutive k by
+// consecutive threads.  All threads of a CTA take (row, t) tasks, one barrier per
+// pass.
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+
+// Row pitch in float2 of a padded row (odd, so that the same element of
+// neighbouring rows falls in different banks).
+__host__ __device__ constexpr int fft_pitch(int L) { return L + L / 16 + 1; }
+
+// Asynchronous global -> shared copies of 4 and 8 bytes (all of a thread's copies
+// in flight at once), completed by cp_async_wait_all and a barrier.
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ float2 cmulw(float2 a, float2 w, bool inv) {   // a * w (or * conj w)
     const float ws = inv ? -w.y : w.y;
     return make_float2(a.x * w.x - a.y * ws, a.x * ws + a.y * w.x);
 }
 
-template <bool INV>
-__device__ float2 *stockham(float2 *x, float2 *y, const float2 *tw, int L, int logL, int nrow, int ld) {   // row stride ld
-    int lgNs = 0;
-    if (logL & 1) {                                        // radix 2, Ns = 1: no twiddles
-        const int half = L >> 1, ntask = nrow * half;
-        for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
-            const int tt = task & (half - 1), base = (task >> (logL - 1)) * ld;
-            const float2 a = x[base + tt], b = x[base + tt + half];
-            y[base + 2 * tt] = make_float2(a.x + b.x, a.y + b.y);
-            y[base + 2 * tt + 1] = make_float2(a.x - b.x, a.y - b.y);
+// cos and sin of pi E / 8, E in [0, 8)
+__device__ __forceinline__ float cos_pi8(int E) {
+    constexpr float c1 = 0.92387953251128674f, h = 0.70710678118654752f, s1 = 0.38268343236508977f;
+    return E == 0 ? 1.0f : E == 1 ? c1 : E == 2 ? h : E == 3 ? s1 : E == 4 ? 0.0f : E == 5 ? -s1 : E == 6 ? -h : -c1;
+}
+__device__ __forceinline__ float sin_pi8(int E) {
+    constexpr float c1 = 0.92387953251128674f, h = 0.70710678118654752f, s1 = 0.38268343236508977f;
+    return E == 0 ? 0.0f : E == 1 ? s1 : E == 2 ? h : E == 3 ? c1 : E == 4 ? 1.0f : E == 5 ? c1 : E == 6 ? h : s1;
+}
+
+// a * exp(-+ 2 pi i E / 16) (forward: minus), E in [0, 8); E = 0 and 4 exact
+__device__ __forceinline__ float2 rot16(float2 a, int E, bool inv) {
+    if (E == 0) return a;
+    if (E == 4) return inv ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+    const float c = cos_pi8(E), s = inv ? sin_pi8(E) : -sin_pi8(E);
+    return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
+}
+
+__device__ __forceinline__ int bitrev_bits(int m, int bits) {
+    int r = 0;
+    for (int b = 0; b < bits; ++b) r |= ((m >> b) & 1) << (bits - 1 - b);
+    return r;
+}
+
+// R-point DFT in registers (R = 2, 4, 8, 16): radix-2 decimation in frequency,
+// natural input order, output in bit-reversed order (v[j] = X[bitrev(j)]).  The
+// butterfly of span h multiplies the difference by w_(2h)^k = w_16^(8k/h).
+template <int R, bool INV>
+__device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
+#pragma unroll
+    for (int h = R / 2; h >= 1; h >>= 1) {
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            if (j & h) continue;
+            const int k = j & (h - 1);
+            const float2 a = v[j], b = v[j + h];
+            v[j] = make_float2(a.x + b.x, a.y + b.y);
+            v[j + h] = rot16(make_float2(a.x - b.x, a.y - b.y), (8 * k) / h, INV);
         }
+    }
+}
+
+template <int R, int LGR, bool INV>
+__device__ __forceinline__ void fft_pass(const float2 *x, float2 *y, const float2 *tw, int logL, int lgNs, int nrow,
+                                         int ld) {
+    const int lgq = logL - LGR, q = 1 << lgq, Ns = 1 << lgNs, ntask = nrow << lgq;
+    for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
+        const int tt = task & (q - 1), base = (task >> lgq) * ld;
+        const int k = tt & (Ns - 1);
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = x[base + pad16(tt + r * q)];
+        if (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmulw(v[r], tw[(r - 1) * Ns + k], INV);
+        }
+        dft_reg<R, INV>(v);
+        const int o = (tt - k) * R + k;
+#pragma unroll
+        for (int m = 0; m < R; ++m) y[base + pad16(o + m * Ns)] = v[bitrev_bits(m, LGR)];
+    }
+}
+
+// The twiddle tables of the radix-16 passes with span Ns > 1, one after another:
+// tw[(r - 1) Ns + k] = exp(-2 pi i r k / (16 Ns)) (the argument r k / (8 Ns) of
+// sincospif is exact: 8 Ns is a power of two).  At most L - 1 entries.
+__device__ __forceinline__ void fft_twiddles(float2 *tw, int logL) {
+    int off = 0;
+    for (int lg = logL & 3; lg < logL; lg += 4) {
+        if (lg == 0) continue;
+        const int Ns = 1 << lg, cnt = 15 * Ns;
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            const int r = (i >> lg) + 1, k = i & (Ns - 1);
+            float sw, cw;
+            sincospif(-(float)(r * k) / (float)(8 * Ns), &sw, &cw);
+            tw[off + i] = make_float2(cw, sw);
+        }
+        off += cnt;
+    }
+}
+
+// Transform of nrow padded rows of pitch ld in x (y: the ping-pong buffer).
+// Returns the buffer holding the result.  Ends with a barrier.
+template <bool INV>
+__device__ float2 *fft_rows_smem(float2 *x, float2 *y, const float2 *tw, int logL, int nrow, int ld) {
+    const int r0 = logL & 3;
+    int lg = 0;
+    if (r0) {
+        if (r0 == 1) fft_pass<2, 1, INV>(x, y, tw, logL, 0, nrow, ld);
+        else if (r0 == 2) fft_pass<4, 2, INV>(x, y, tw, logL, 0, nrow, ld);
+        else fft_pass<8, 3, INV>(x, y, tw, logL, 0, nrow, ld);
         __syncthreads();
         float2 *tmp = x;
         x = y;
         y = tmp;
-        lgNs = 1;
+        lg = r0;
     }
-    const int q = L >> 2, ntask = nrow * q;
-    for (; lgNs < logL; lgNs += 2) {
-        const int Ns = 1 << lgNs, sh = logL - 2 - lgNs;
-        for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
-            const int tt = task & (q - 1), base = (task >> (logL - 2)) * ld;
-            const int k = tt & (Ns - 1), m1 = k << sh;
-            const float2 *xr = x + base;
-            const float2 v0 = xr[tt];
-            const float2 v1 = cmulw(xr[tt + q], tw[m1], INV);
-            const float2 v2 = cmulw(xr[tt + 2 * q], tw[2 * m1], INV);
-            const float2 v3 = cmulw(xr[tt + 3 * q], tw[3 * m1], INV);
-            // 4-point DFT, omega_4 = -i (forward) or +i (inverse)
-            const float2 s02 = make_float2(v0.x + v2.x, v0.y + v2.y), d02 = make_float2(v0.x - v2.x, v0.y - v2.y);
-            const float2 s13 = make_float2(v1.x + v3.x, v1.y + v3.y), d13 = make_float2(v1.x - v3.x, v1.y - v3.y);
-            // -i d13 (forward) or +i d13 (inverse)
-            const float2 r13 = INV ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);
-            float2 *yr = y + base + (tt - k) * 4 + k;
-            yr[0] = make_float2(s02.x + s13.x, s02.y + s13.y);
-            yr[Ns] = make_float2(d02.x + r13.x, d02.y + r13.y);
-            yr[2 * Ns] = make_float2(s02.x - s13.x, s02.y - s13.y);
-            yr[3 * Ns] = make_float2(d02.x - r13.x, d02.y - r13.y);
-        }
+    int off = 0;
+    for (; lg < logL; lg += 4) {
+        fft_pass<16, 4, INV>(x, y, tw + off, logL, lg, nrow, ld);
+        if (lg) off += 15 << lg;
         __syncthreads();
         float2 *tmp = x;
         x = y;
@@ -90,33 +177,30 @@ __device__ float2 *stockham(float2 *x, float2 *y, const float2 *tw, int L, int l
     return x;
 }
 
-__device__ __forceinline__ void fft_twiddles(float2 *tw, int L) {   // tw[m] = exp(-2 pi i m / L), m < L
-    for (int m = threadIdx.x; m < L; m += blockDim.x) {
-        float sw, cw;
-        sincospif(-(float)(2 * m) / (float)L, &sw, &cw);
-        tw[m] = make_float2(cw, sw);
-    }
-}
-
 // Forward row transforms from the spins: C[r][y][kx] = FFT_x(s_x + i s_y),
 // Z[r][y][kx] = FFT_x(s_z); a CTA takes Y rows of one replica.
-__global__ void k_fft_fwd_rows(const float *__restrict__ spins, int L, int logL, int Y, float2 *C, float2 *Z) {
+__global__ void __launch_bounds__(1024) k_fft_fwd_rows(const float *__restrict__ spins, int L, int logL, int Y, float2 *C, float2 *Z) {
     extern __shared__ float2 fbuf[];
-    const int N = L * L, r = blockIdx.y, y0 = blockIdx.x * Y;
-    float2 *tw = fbuf, *x = tw + L, *yb = x + (size_t)2 * Y * L;   // x: [2Y][L] (C rows, then Z rows)
-    fft_twiddles(tw, L);
+    const int N = L * L, r = blockIdx.y, y0 = blockIdx.x * Y, ld = fft_pitch(L);
+    float2 *tw = fbuf, *x = tw + L, *yb = x + (size_t)2 * Y * ld;   // x: [2Y][ld] (C rows, then Z rows)
+    fft_twiddles(tw, logL);
     const float *s = spins + (size_t)r * 3 * N;
     for (int i = threadIdx.x; i < Y * L; i += blockDim.x) {
-        const int q = (y0 + i / L) * L + i % L;
-        x[i] = make_float2(s[q], s[N + q]);
-        x[(size_t)Y * L + i] = make_float2(s[2 * N + q], 0.0f);
+        const int row = i >> logL, col = i & (L - 1), q = (y0 + row) * L + col;
+        float2 *cx = x + row * ld + pad16(col), *zx = x + (Y + row) * ld + pad16(col);
+        cp_async4(&cx->x, s + q);
+        cp_async4(&cx->y, s + N + q);
+        cp_async4(&zx->x, s + 2 * N + q);
+        zx->y = 0.0f;
     }
+    cp_async_wait_all();
     __syncthreads();
-    const float2 *res = stockham<false>(x, yb, tw, L, logL, 2 * Y, L);
+    const float2 *res = fft_rows_smem<false>(x, yb, tw, logL, 2 * Y, ld);
     float2 *Cr = C + (size_t)r * N + (size_t)y0 * L, *Zr = Z + (size_t)r * N + (size_t)y0 * L;
     for (int i = threadIdx.x; i < Y * L; i += blockDim.x) {
-        Cr[i] = res[i];
-        Zr[i] = res[(size_t)Y * L + i];
+        const int row = i >> logL, col = pad16(i & (L - 1));
+        Cr[i] = res[row * ld + col];
+        Zr[i] = res[(Y + row) * ld + col];
     }
 }
 
@@ -125,7 +209,7 @@ __global__ void k_fft_fwd_rows(const float *__restrict__ spins, int L, int logL,
 // S_y = (C - conj C(-k))/(2i), H_x + i H_y = (W^xx S_x + W^xy S_y) + i (W^xy S_x + W^yy S_y),
 // H_z = W^zz Z, W^ real and stored [kx][ky]), inverse transform over ky; the result
 // replaces the columns of C (H_x + i H_y) and Z (H_z).
-__global__ void k_fft_cols_conv(float2 *C, float2 *Z, const float *__restrict__ What, int L, int logL, int CT) {
+__global__ void __launch_bounds__(1024) k_fft_cols_conv(float2 *C, float2 *Z, const float *__restrict__ What, int L, int logL, int CT) {
     extern __shared__ float2 fbuf[];
     __shared__ int s_col[32], s_mir[32];
     const int N = L * L, r = blockIdx.y, k0 = blockIdx.x * CT, hl = L >> 1;
@@ -149,64 +233,69 @@ __global__ void k_fft_cols_conv(float2 *C, float2 *Z, const float *__restrict__ 
     __syncthreads();
     int nc = 0;
     while (nc < 32 && s_col[nc] >= 0) ++nc;
-    const int ld = L + 1;   // padded rows: a row of the tile's columns lands in distinct banks
+    const int ld = fft_pitch(L);   // odd pitch: a row of the tile's columns lands in distinct banks
     float2 *tw = fbuf, *x = tw + L, *yb = x + (size_t)2 * nc * ld;   // x: [2nc][ld] (C columns, then Z columns)
-    fft_twiddles(tw, L);
+    fft_twiddles(tw, logL);
     float2 *Cr = C + (size_t)r * N, *Zr = Z + (size_t)r * N;
     for (int i = threadIdx.x; i < nc * L; i += blockDim.x) {
         const int yy = i / nc, c = i % nc;                // consecutive threads: neighbouring columns of a row
         const size_t g = (size_t)yy * L + s_col[c];
-        x[(size_t)c * ld + yy] = Cr[g];
-        x[(size_t)(nc + c) * ld + yy] = Zr[g];
+        cp_async8(x + c * ld + pad16(yy), Cr + g);
+        cp_async8(x + (nc + c) * ld + pad16(yy), Zr + g);
     }
+    cp_async_wait_all();
     __syncthreads();
-    float2 *X = stockham<false>(x, yb, tw, L, logL, 2 * nc, ld);
+    float2 *X = fft_rows_smem<false>(x, yb, tw, logL, 2 * nc, ld);
     float2 *Yv = X == x ? yb : x;
+#pragma unroll 4
     for (int i = threadIdx.x; i < nc * L; i += blockDim.x) {
-        const int c = i / L, ky = i % L, kx = s_col[c];
-        const int kym = (L - ky) & (L - 1);
-        const float2 cv = X[(size_t)c * ld + ky], cm = X[(size_t)s_mir[c] * ld + kym];
+        const int c = i >> logL, ky = i & (L - 1), kx = s_col[c];
+        const int kym = (L - ky) & (L - 1), p = pad16(ky);
+        const float2 cv = X[c * ld + p], cm = X[s_mir[c] * ld + pad16(kym)];
         const float2 sx = make_float2(0.5f * (cv.x + cm.x), 0.5f * (cv.y - cm.y));
         const float2 sy = make_float2(0.5f * (cv.y + cm.y), -0.5f * (cv.x - cm.x));
         const size_t wi = (size_t)kx * L + ky;
         const float wxx = What[wi], wxy = What[N + wi], wyy = What[2 * N + wi], wzz = What[3 * N + wi];
         const float2 hx = make_float2(wxx * sx.x + wxy * sy.x, wxx * sx.y + wxy * sy.y);
         const float2 hy = make_float2(wxy * sx.x + wyy * sy.x, wxy * sx.y + wyy * sy.y);
-        Yv[(size_t)c * ld + ky] = make_float2(hx.x - hy.y, hx.y + hy.x);
-        const float2 z = X[(size_t)(nc + c) * ld + ky];
-        Yv[(size_t)(nc + c) * ld + ky] = make_float2(wzz * z.x, wzz * z.y);
+        Yv[c * ld + p] = make_float2(hx.x - hy.y, hx.y + hy.x);
+        const float2 z = X[(nc + c) * ld + p];
+        Yv[(nc + c) * ld + p] = make_float2(wzz * z.x, wzz * z.y);
     }
     __syncthreads();
-    const float2 *res = stockham<true>(Yv, X, tw, L, logL, 2 * nc, ld);
+    const float2 *res = fft_rows_smem<true>(Yv, X, tw, logL, 2 * nc, ld);
     for (int i = threadIdx.x; i < nc * L; i += blockDim.x) {
         const int yy = i / nc, c = i % nc;
         const size_t g = (size_t)yy * L + s_col[c];
-        Cr[g] = res[(size_t)c * ld + yy];
-        Zr[g] = res[(size_t)(nc + c) * ld + yy];
+        Cr[g] = res[c * ld + pad16(yy)];
+        Zr[g] = res[(nc + c) * ld + pad16(yy)];
     }
 }
 
 // Inverse row transforms over kx and the field: h_x + i h_y = IFFT(H_x + i H_y),
 // h_z = Re IFFT(H_z), scaled by 1/N.
-__global__ void k_fft_inv_rows(const float2 *__restrict__ C, const float2 *__restrict__ Z, int L, int logL, int Y,
+__global__ void __launch_bounds__(1024) k_fft_inv_rows(const float2 *__restrict__ C, const float2 *__restrict__ Z, int L, int logL, int Y,
                                float scale, float *field) {
     extern __shared__ float2 fbuf[];
-    const int N = L * L, r = blockIdx.y, y0 = blockIdx.x * Y;
-    float2 *tw = fbuf, *x = tw + L, *yb = x + (size_t)2 * Y * L;
-    fft_twiddles(tw, L);
+    const int N = L * L, r = blockIdx.y, y0 = blockIdx.x * Y, ld = fft_pitch(L);
+    float2 *tw = fbuf, *x = tw + L, *yb = x + (size_t)2 * Y * ld;
+    fft_twiddles(tw, logL);
     const float2 *Cr = C + (size_t)r * N + (size_t)y0 * L, *Zr = Z + (size_t)r * N + (size_t)y0 * L;
     for (int i = threadIdx.x; i < Y * L; i += blockDim.x) {
-        x[i] = Cr[i];
-        x[(size_t)Y * L + i] = Zr[i];
+        const int row = i >> logL, col = pad16(i & (L - 1));
+        cp_async8(x + row * ld + col, Cr + i);
+        cp_async8(x + (Y + row) * ld + col, Zr + i);
     }
+    cp_async_wait_all();
     __syncthreads();
-    const float2 *res = stockham<true>(x, yb, tw, L, logL, 2 * Y, L);
+    const float2 *res = fft_rows_smem<true>(x, yb, tw, logL, 2 * Y, ld);
     float *f = field + (size_t)r * 3 * N + (size_t)y0 * L;
     for (int i = threadIdx.x; i < Y * L; i += blockDim.x) {
-        const float2 a = res[i];
+        const int row = i >> logL, col = pad16(i & (L - 1));
+        const float2 a = res[row * ld + col];
         f[i] = a.x * scale;
         f[N + i] = a.y * scale;
-        f[2 * N + i] = res[(size_t)Y * L + i].x * scale;
+        f[2 * N + i] = res[(Y + row) * ld + col].x * scale;
     }
 }
 
@@ -489,12 +578,20 @@ int ilog2(int v) {
 }
 
 // rows Y of a row-pass CTA: 2Y rows of L/4 radix-4 butterflies, at least 256 a stage
-int fft_rows_per_cta(int L) { return L >= 512 ? 1 : std::min(L, 512 / L); }
+// Rows of a row-pass CTA: at least 64 tasks in a radix-16 pass (2Y rows x L/16),
+// then doubled while the grid keeps four CTAs per SM and a CTA at most 256 tasks.
+int fft_rows_per_cta(int L, int R, int nsm) {
+    int Y = std::min(L, std::max(1, 512 / L));
+    while (2 * Y <= L && 4 * Y * L / 16 <= 256 && (long long)(L / (2 * Y)) * R >= 4LL * nsm) Y *= 2;
+    return Y;
+}
 
 int fft_cols_per_tile(int L) {      // columns kx (plus mirrors) of a column-pass CTA
     const int ct = 1024 / L;
     return ct < 1 ? 1 : (ct > 8 ? 8 : ct);
 }
+
+int fft_threads(int tasks) { return std::min(1024, std::max(64, (tasks + 31) / 32 * 32)); }
 
 }  // namespace
 
@@ -521,10 +618,18 @@ cudaError_t launch_fft_field(int L, int R, const float *spins, const float *What
     const int N = L * L, logL = ilog2(L);
     const size_t tot = (size_t)N * R;
     float2 *C = scratch, *Z = scratch + tot;
-    const int Y = fft_rows_per_cta(L), CT = fft_cols_per_tile(L);
-    const int rthreads = std::min(1024, std::max(64, Y * L / 2)), cthreads = 1024;
-    const size_t rsmem = sizeof(float2) * ((size_t)L + (size_t)4 * Y * L);
-    const size_t csmem = sizeof(float2) * ((size_t)L + (size_t)4 * 2 * CT * (L + 1));
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int Y = fft_rows_per_cta(L, R, nsm), CT = fft_cols_per_tile(L), ld = fft_pitch(L);
+    // threads: the tasks of a radix-16 pass (16 points a task); a grid smaller than
+    // the SM count gets wider CTAs, for more loads in flight in the gather, the
+    // spectral product and the scatter
+    const int rblocks = L / Y * R, cblocks = (L / 2 + 1 + CT - 1) / CT * R;
+    const int rthreads = rblocks < nsm ? fft_threads(std::max(2 * Y * L / 16, Y * L / 2)) : fft_threads(2 * Y * L / 16);
+    const int cthreads = cblocks < nsm ? 1024 : fft_threads(2 * 2 * CT * L / 16);
+    const size_t rsmem = sizeof(float2) * ((size_t)L + (size_t)2 * 2 * Y * ld);
+    const size_t csmem = sizeof(float2) * ((size_t)L + (size_t)2 * 2 * 2 * CT * ld);
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_fft_fwd_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_fft_inv_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem)) != cudaSuccess) return e;
