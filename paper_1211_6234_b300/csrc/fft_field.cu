@@ -110,25 +110,39 @@ __device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
     }
 }
 
+// One pass in place: thread u < nu = nrow L / 16 takes the 16 / R tasks u + j nu,
+// loads their inputs, applies the twiddles and the DFTs in registers, waits at a
+// barrier (every load of the pass done) and stores.  Needs blockDim.x >= nu.
 template <int R, int LGR, bool INV>
-__device__ __forceinline__ void fft_pass(const float2 *x, float2 *y, const float2 *tw, int logL, int lgNs, int nrow,
-                                         int ld) {
-    const int lgq = logL - LGR, q = 1 << lgq, Ns = 1 << lgNs, ntask = nrow << lgq;
-    for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
-        const int tt = task & (q - 1), base = (task >> lgq) * ld;
-        const int k = tt & (Ns - 1);
-        float2 v[R];
+__device__ __forceinline__ void fft_pass(float2 *x, const float2 *tw, int logL, int lgNs, int nrow, int ld) {
+    constexpr int TPT = 16 / R;
+    const int lgq = logL - LGR, q = 1 << lgq, Ns = 1 << lgNs, nu = (nrow << logL) >> 4;
+    const int u = threadIdx.x;
+    float2 v[TPT][R];
+    if (u < nu) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = x[base + pad16(tt + r * q)];
-        if (Ns > 1) {
+        for (int j = 0; j < TPT; ++j) {
+            const int task = u + j * nu, tt = task & (q - 1), base = (task >> lgq) * ld, k = tt & (Ns - 1);
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = cmulw(v[r], tw[(r - 1) * Ns + k], INV);
+            for (int r = 0; r < R; ++r) v[j][r] = x[base + pad16(tt + r * q)];
+            if (Ns > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[j][r] = cmulw(v[j][r], tw[(r - 1) * Ns + k], INV);
+            }
+            dft_reg<R, INV>(v[j]);
         }
-        dft_reg<R, INV>(v);
-        const int o = (tt - k) * R + k;
-#pragma unroll
-        for (int m = 0; m < R; ++m) y[base + pad16(o + m * Ns)] = v[bitrev_bits(m, LGR)];
     }
+    __syncthreads();
+    if (u < nu) {
+#pragma unroll
+        for (int j = 0; j < TPT; ++j) {
+            const int task = u + j * nu, tt = task & (q - 1), base = (task >> lgq) * ld, k = tt & (Ns - 1);
+            const int o = (tt - k) * R + k;
+#pragma unroll
+            for (int m = 0; m < R; ++m) x[base + pad16(o + m * Ns)] = v[j][bitrev_bits(m, LGR)];
+        }
+    }
+    __syncthreads();
 }
 
 // The twiddle tables of the radix-16 passes with span Ns > 1, one after another:
@@ -149,32 +163,23 @@ __device__ __forceinline__ void fft_twiddles(float2 *tw, int logL) {
     }
 }
 
-// Transform of nrow padded rows of pitch ld in x (y: the ping-pong buffer).
-// Returns the buffer holding the result.  Ends with a barrier.
+// Transform of nrow padded rows of pitch ld in x, in place (nrow L / 16 <= blockDim.x).
+// Starts and ends with a barrier inside each pass.
 template <bool INV>
-__device__ float2 *fft_rows_smem(float2 *x, float2 *y, const float2 *tw, int logL, int nrow, int ld) {
+__device__ void fft_rows_smem(float2 *x, const float2 *tw, int logL, int nrow, int ld) {
     const int r0 = logL & 3;
     int lg = 0;
     if (r0) {
-        if (r0 == 1) fft_pass<2, 1, INV>(x, y, tw, logL, 0, nrow, ld);
-        else if (r0 == 2) fft_pass<4, 2, INV>(x, y, tw, logL, 0, nrow, ld);
-        else fft_pass<8, 3, INV>(x, y, tw, logL, 0, nrow, ld);
-        __syncthreads();
-        float2 *tmp = x;
-        x = y;
-        y = tmp;
+        if (r0 == 1) fft_pass<2, 1, INV>(x, tw, logL, 0, nrow, ld);
+        else if (r0 == 2) fft_pass<4, 2, INV>(x, tw, logL, 0, nrow, ld);
+        else fft_pass<8, 3, INV>(x, tw, logL, 0, nrow, ld);
         lg = r0;
     }
     int off = 0;
     for (; lg < logL; lg += 4) {
-        fft_pass<16, 4, INV>(x, y, tw + off, logL, lg, nrow, ld);
+        fft_pass<16, 4, INV>(x, tw + off, logL, lg, nrow, ld);
         if (lg) off += 15 << lg;
-        __syncthreads();
-        float2 *tmp = x;
-        x = y;
-        y = tmp;
     }
-    return x;
 }
 
 // Forward row transforms from the spins: C[r][y][kx] = FFT_x(s_x + i s_y),
@@ -182,7 +187,7 @@ __device__ float2 *fft_rows_smem(float2 *x, float2 *y, const float2 *tw, int log
 __global__ void __launch_bounds__(1024) k_fft_fwd_rows(const float *__restrict__ spins, int L, int logL, int Y, float2 *C, float2 *Z) {
     extern __shared__ float2 fbuf[];
     const int N = L * L, r = blockIdx.y, y0 = blockIdx.x * Y, ld = fft_pitch(L);
-    float2 *tw = fbuf, *x = tw + L, *yb = x + (size_t)2 * Y * ld;   // x: [2Y][ld] (C rows, then Z rows)
+    float2 *tw = fbuf, *x = tw + L;   // x: [2Y][ld] (C rows, then Z rows)
     fft_twiddles(tw, logL);
     const float *s = spins + (size_t)r * 3 * N;
     for (int i = threadIdx.x; i < Y * L; i += blockDim.x) {
@@ -195,12 +200,12 @@ __global__ void __launch_bounds__(1024) k_fft_fwd_rows(const float *__restrict__
     }
     cp_async_wait_all();
     __syncthreads();
-    const float2 *res = fft_rows_smem<false>(x, yb, tw, logL, 2 * Y, ld);
+    fft_rows_smem<false>(x, tw, logL, 2 * Y, ld);
     float2 *Cr = C + (size_t)r * N + (size_t)y0 * L, *Zr = Z + (size_t)r * N + (size_t)y0 * L;
     for (int i = threadIdx.x; i < Y * L; i += blockDim.x) {
         const int row = i >> logL, col = pad16(i & (L - 1));
-        Cr[i] = res[row * ld + col];
-        Zr[i] = res[(Y + row) * ld + col];
+        Cr[i] = x[row * ld + col];
+        Zr[i] = x[(Y + row) * ld + col];
     }
 }
 
@@ -234,7 +239,7 @@ __global__ void __launch_bounds__(1024) k_fft_cols_conv(float2 *C, float2 *Z, co
     int nc = 0;
     while (nc < 32 && s_col[nc] >= 0) ++nc;
     const int ld = fft_pitch(L);   // odd pitch: a row of the tile's columns lands in distinct banks
-    float2 *tw = fbuf, *x = tw + L, *yb = x + (size_t)2 * nc * ld;   // x: [2nc][ld] (C columns, then Z columns)
+    float2 *tw = fbuf, *x = tw + L;   // x: [2nc][ld] (C columns, then Z columns)
     fft_twiddles(tw, logL);
     float2 *Cr = C + (size_t)r * N, *Zr = Z + (size_t)r * N;
     for (int i = threadIdx.x; i < nc * L; i += blockDim.x) {
@@ -245,30 +250,38 @@ __global__ void __launch_bounds__(1024) k_fft_cols_conv(float2 *C, float2 *Z, co
     }
     cp_async_wait_all();
     __syncthreads();
-    float2 *X = fft_rows_smem<false>(x, yb, tw, logL, 2 * nc, ld);
-    float2 *Yv = X == x ? yb : x;
-#pragma unroll 4
+    fft_rows_smem<false>(x, tw, logL, 2 * nc, ld);
+    // In place: the item (c, ky) and its partner (mirror of c, -ky) read the same two
+    // values of C, so one thread takes both (the one with c < mirror, or c = mirror
+    // and ky <= -ky mod L).
     for (int i = threadIdx.x; i < nc * L; i += blockDim.x) {
-        const int c = i >> logL, ky = i & (L - 1), kx = s_col[c];
-        const int kym = (L - ky) & (L - 1), p = pad16(ky);
-        const float2 cv = X[c * ld + p], cm = X[s_mir[c] * ld + pad16(kym)];
-        const float2 sx = make_float2(0.5f * (cv.x + cm.x), 0.5f * (cv.y - cm.y));
-        const float2 sy = make_float2(0.5f * (cv.y + cm.y), -0.5f * (cv.x - cm.x));
-        const size_t wi = (size_t)kx * L + ky;
-        const float wxx = What[wi], wxy = What[N + wi], wyy = What[2 * N + wi], wzz = What[3 * N + wi];
-        const float2 hx = make_float2(wxx * sx.x + wxy * sy.x, wxx * sx.y + wxy * sy.y);
-        const float2 hy = make_float2(wxy * sx.x + wyy * sy.x, wxy * sx.y + wyy * sy.y);
-        Yv[c * ld + p] = make_float2(hx.x - hy.y, hx.y + hy.x);
-        const float2 z = X[(nc + c) * ld + p];
-        Yv[(nc + c) * ld + p] = make_float2(wzz * z.x, wzz * z.y);
+        const int c = i >> logL, ky = i & (L - 1), cmi = s_mir[c];
+        const int kym = (L - ky) & (L - 1), p = pad16(ky), pm = pad16(kym);
+        const float2 z = x[(nc + c) * ld + p];
+        const float wzz = What[3 * N + (size_t)s_col[c] * L + ky];
+        x[(nc + c) * ld + p] = make_float2(wzz * z.x, wzz * z.y);
+        if (c > cmi || (c == cmi && ky > kym)) continue;
+        const float2 cv = x[c * ld + p], cm = x[cmi * ld + pm];
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {    // the item (c, ky), then its partner
+            const float2 a = side ? cm : cv, b = side ? cv : cm;
+            const size_t wi = (size_t)s_col[side ? cmi : c] * L + (side ? kym : ky);
+            const float2 sx = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+            const float2 sy = make_float2(0.5f * (a.y + b.y), -0.5f * (a.x - b.x));
+            const float wxx = What[wi], wxy = What[N + wi], wyy = What[2 * N + wi];
+            const float2 hx = make_float2(wxx * sx.x + wxy * sy.x, wxx * sx.y + wxy * sy.y);
+            const float2 hy = make_float2(wxy * sx.x + wyy * sy.x, wxy * sx.y + wyy * sy.y);
+            x[(side ? cmi : c) * ld + (side ? pm : p)] = make_float2(hx.x - hy.y, hx.y + hy.x);
+            if (cmi == c && kym == ky) break;    // its own partner
+        }
     }
     __syncthreads();
-    const float2 *res = fft_rows_smem<true>(Yv, X, tw, logL, 2 * nc, ld);
+    fft_rows_smem<true>(x, tw, logL, 2 * nc, ld);
     for (int i = threadIdx.x; i < nc * L; i += blockDim.x) {
         const int yy = i / nc, c = i % nc;
         const size_t g = (size_t)yy * L + s_col[c];
-        Cr[g] = res[c * ld + pad16(yy)];
-        Zr[g] = res[(nc + c) * ld + pad16(yy)];
+        Cr[g] = x[c * ld + pad16(yy)];
+        Zr[g] = x[(nc + c) * ld + pad16(yy)];
     }
 }
 
@@ -278,7 +291,7 @@ __global__ void __launch_bounds__(1024) k_fft_inv_rows(const float2 *__restrict_
                                float scale, float *field) {
     extern __shared__ float2 fbuf[];
     const int N = L * L, r = blockIdx.y, y0 = blockIdx.x * Y, ld = fft_pitch(L);
-    float2 *tw = fbuf, *x = tw + L, *yb = x + (size_t)2 * Y * ld;
+    float2 *tw = fbuf, *x = tw + L;
     fft_twiddles(tw, logL);
     const float2 *Cr = C + (size_t)r * N + (size_t)y0 * L, *Zr = Z + (size_t)r * N + (size_t)y0 * L;
     for (int i = threadIdx.x; i < Y * L; i += blockDim.x) {
@@ -288,14 +301,14 @@ __global__ void __launch_bounds__(1024) k_fft_inv_rows(const float2 *__restrict_
     }
     cp_async_wait_all();
     __syncthreads();
-    const float2 *res = fft_rows_smem<true>(x, yb, tw, logL, 2 * Y, ld);
+    fft_rows_smem<true>(x, tw, logL, 2 * Y, ld);
     float *f = field + (size_t)r * 3 * N + (size_t)y0 * L;
     for (int i = threadIdx.x; i < Y * L; i += blockDim.x) {
         const int row = i >> logL, col = pad16(i & (L - 1));
-        const float2 a = res[row * ld + col];
+        const float2 a = x[row * ld + col];
         f[i] = a.x * scale;
         f[N + i] = a.y * scale;
-        f[2 * N + i] = res[(Y + row) * ld + col].x * scale;
+        f[2 * N + i] = x[(Y + row) * ld + col].x * scale;
     }
 }
 
@@ -628,8 +641,8 @@ cudaError_t launch_fft_field(int L, int R, const float *spins, const float *What
     const int rblocks = L / Y * R, cblocks = (L / 2 + 1 + CT - 1) / CT * R;
     const int rthreads = rblocks < nsm ? fft_threads(std::max(2 * Y * L / 16, Y * L / 2)) : fft_threads(2 * Y * L / 16);
     const int cthreads = cblocks < nsm ? 1024 : fft_threads(2 * 2 * CT * L / 16);
-    const size_t rsmem = sizeof(float2) * ((size_t)L + (size_t)2 * 2 * Y * ld);
-    const size_t csmem = sizeof(float2) * ((size_t)L + (size_t)2 * 2 * 2 * CT * ld);
+    const size_t rsmem = sizeof(float2) * ((size_t)L + (size_t)2 * Y * ld);
+    const size_t csmem = sizeof(float2) * ((size_t)L + (size_t)2 * 2 * CT * ld);
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_fft_fwd_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_fft_inv_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem)) != cudaSuccess) return e;
