@@ -188,7 +188,9 @@ __global__ void __launch_bounds__(1024) k_fft_fwd_rows(const float *__restrict__
     extern __shared__ float2 fbuf[];
     const int N = L * L, r = blockIdx.y, y0 = blockIdx.x * Y, ld = fft_pitch(L);
     float2 *tw = fbuf, *x = tw + L;   // x: [2Y][ld] (C rows, then Z rows)
+    pdl_trigger();
     fft_twiddles(tw, logL);
+    pdl_wait();   // the spins of the previous update, and no reader of C, Z left
     const float *s = spins + (size_t)r * 3 * N;
     for (int i = threadIdx.x; i < Y * L; i += blockDim.x) {
         const int row = i >> logL, col = i & (L - 1), q = (y0 + row) * L + col;
@@ -240,7 +242,9 @@ __global__ void __launch_bounds__(1024) k_fft_cols_conv(float2 *C, float2 *Z, co
     while (nc < 32 && s_col[nc] >= 0) ++nc;
     const int ld = fft_pitch(L);   // odd pitch: a row of the tile's columns lands in distinct banks
     float2 *tw = fbuf, *x = tw + L;   // x: [2nc][ld] (C columns, then Z columns)
+    pdl_trigger();
     fft_twiddles(tw, logL);
+    pdl_wait();   // the row transforms
     float2 *Cr = C + (size_t)r * N, *Zr = Z + (size_t)r * N;
     for (int i = threadIdx.x; i < nc * L; i += blockDim.x) {
         const int yy = i / nc, c = i % nc;                // consecutive threads: neighbouring columns of a row
@@ -292,7 +296,9 @@ __global__ void __launch_bounds__(1024) k_fft_inv_rows(const float2 *__restrict_
     extern __shared__ float2 fbuf[];
     const int N = L * L, r = blockIdx.y, y0 = blockIdx.x * Y, ld = fft_pitch(L);
     float2 *tw = fbuf, *x = tw + L;
+    pdl_trigger();
     fft_twiddles(tw, logL);
+    pdl_wait();   // the column pass
     const float2 *Cr = C + (size_t)r * N + (size_t)y0 * L, *Zr = Z + (size_t)r * N + (size_t)y0 * L;
     for (int i = threadIdx.x; i < Y * L; i += blockDim.x) {
         const int row = i >> logL, col = pad16(i & (L - 1));
@@ -379,6 +385,8 @@ __device__ __forceinline__ void perp_basis_f(float nx, float ny, float nz, float
 }
 
 __global__ void k_fft_update(const FftStepConfig cfg, const FftStepBuffers buf) {
+    pdl_trigger();
+    pdl_wait();   // the field of the state before the sub-step
     const int L = cfg.L, l = cfg.l, N = L * L, C = L / l, n = C * C, ll = l * l;
     const int r = blockIdx.y;
     const int d = blockIdx.x * blockDim.x + threadIdx.x;
@@ -606,6 +614,24 @@ int fft_cols_per_tile(int L) {      // columns kx (plus mirrors) of a column-pas
 
 int fft_threads(int tasks) { return std::min(1024, std::max(64, (tasks + 31) / 32 * 32)); }
 
+// Launch with programmatic stream serialization: the kernel may start while the
+// previous kernel of the stream drains; it builds its twiddle table, then waits
+// (griddepcontrol.wait) before its first global access.
+template <typename... Exp, typename... Act>
+cudaError_t launch_pdl(void (*k)(Exp...), dim3 grid, int threads, size_t smem, cudaStream_t st, Act... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 }  // namespace
 
 bool fft_supported(int L) { return L >= 8 && L <= 1024 && (L & (L - 1)) == 0; }
@@ -647,18 +673,20 @@ cudaError_t launch_fft_field(int L, int R, const float *spins, const float *What
     if ((e = cudaFuncSetAttribute(k_fft_fwd_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_fft_inv_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_fft_cols_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem)) != cudaSuccess) return e;
-    k_fft_fwd_rows<<<dim3(L / Y, R), rthreads, rsmem, st>>>(spins, L, logL, Y, C, Z);
-    k_fft_cols_conv<<<dim3((L / 2 + 1 + CT - 1) / CT, R), cthreads, csmem, st>>>(C, Z, What, L, logL, CT);
-    k_fft_inv_rows<<<dim3(L / Y, R), rthreads, rsmem, st>>>(C, Z, L, logL, Y, 1.0f / (float)N, field);
-    return cudaGetLastError();
+    if ((e = launch_pdl(k_fft_fwd_rows, dim3(L / Y, R), rthreads, rsmem, st, spins, L, logL, Y, C, Z)) != cudaSuccess)
+        return e;
+    if ((e = launch_pdl(k_fft_cols_conv, dim3((L / 2 + 1 + CT - 1) / CT, R), cthreads, csmem, st, C, Z, What, L, logL,
+                        CT)) != cudaSuccess)
+        return e;
+    return launch_pdl(k_fft_inv_rows, dim3(L / Y, R), rthreads, rsmem, st, (const float2 *)C, (const float2 *)Z, L, logL,
+                      Y, 1.0f / (float)N, field);
 }
 
 cudaError_t launch_fft_update(const FftStepConfig &c, const FftStepBuffers &b, cudaStream_t st) {
     const int n = (c.L / c.l) * (c.L / c.l);
     const int threads = n >= 256 ? 256 : ((n + 31) / 32) * 32;
     dim3 grid((n + threads - 1) / threads, c.R);
-    k_fft_update<<<grid, threads, 0, st>>>(c, b);
-    return cudaGetLastError();
+    return launch_pdl(k_fft_update, grid, threads, 0, st, c, b);
 }
 
 cudaError_t launch_fft_observe(int L, int R, const float *spins, const float *field, const RepParams *P,
