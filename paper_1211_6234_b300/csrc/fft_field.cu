@@ -614,23 +614,6 @@ int fft_cols_per_tile(int L) {      // columns kx (plus mirrors) of a column-pas
 
 int fft_threads(int tasks) { return std::min(1024, std::max(64, (tasks + 31) / 32 * 32)); }
 
-// Launch with programmatic stream serialization: the kernel may start while the
-// previous kernel of the stream drains; it builds its twiddle table, then waits
-// (griddepcontrol.wait) before its first global access.
-template <typename... Exp, typename... Act>
-cudaError_t launch_pdl(void (*k)(Exp...), dim3 grid, int threads, size_t smem, cudaStream_t st, Act... args) {
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = grid;
-    cfg.blockDim = dim3(threads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k, args...);
-}
 
 }  // namespace
 

@@ -99,6 +99,23 @@ __device__ __forceinline__ int window_site_xy(int l, int C, uint2 key, uint32_t 
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// Launch with programmatic stream serialization (the kernel must call pdl_wait
+// before its first access to memory that earlier work of the stream writes).
+template <typename... Exp, typename... Act>
+cudaError_t launch_pdl(void (*k)(Exp...), dim3 grid, int threads, size_t smem, cudaStream_t st, Act... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // Per-replica couplings as the kernels read them.
 struct RepParams {
     float J, CD, K2, K4, T;

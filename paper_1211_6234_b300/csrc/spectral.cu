@@ -258,6 +258,8 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec_init(int L, int l, const 
 // Hw[z][r][w][3][n], are summed by the update in chunk order.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kSpecThreads) k_spec_wfield(const SpecConfig cfg, const SpecBuffers b) {
+    pdl_trigger();
+    pdl_wait();   // the spectra and offsets written by the previous kernels
     const int L = cfg.L, l = cfg.l, C = L / l, n = C * C, ll = l * l, R = cfg.R;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int th = blockIdx.x * 16 + (lane & 15), r = blockIdx.y * 2 + (lane >> 4);
@@ -325,6 +327,8 @@ __global__ void __launch_bounds__(kSpecThreads) k_spec_wfield(const SpecConfig c
 // ---------------------------------------------------------------------------
 template <int MAXT>
 __global__ void __launch_bounds__(MAXT) k_spec_wupdate(const SpecConfig cfg, const SpecBuffers b) {
+    pdl_trigger();
+    pdl_wait();   // the window's partial field spectra
     const int L = cfg.L, l = cfg.l, C = L / l, n = C * C, ll = l * l, N = L * L, R = cfg.R;
     const int r = blockIdx.x, tid = threadIdx.x;
     uint2 key;
@@ -629,8 +633,7 @@ template <int MAXT>
 cudaError_t launch_wupdate(const SpecConfig &c, const SpecBuffers &b, size_t smem, int th, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(k_spec_wupdate<MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_spec_wupdate<MAXT><<<c.R, th, smem, st>>>(c, b);
-    return cudaGetLastError();
+    return launch_pdl(k_spec_wupdate<MAXT>, dim3(c.R), th, smem, st, c, b);
 }
 
 size_t wupdate_smem(int C, int wmax) {
@@ -700,8 +703,8 @@ cudaError_t launch_spec_offsets(const SpecConfig &c, const SpecBuffers &b, cudaS
 
 cudaError_t launch_spec_wfield(const SpecConfig &c, const SpecBuffers &b, cudaStream_t st) {
     const int C = c.L / c.l;
-    k_spec_wfield<<<dim3((half_count(C) + 15) / 16, (c.R + 1) / 2, c.esplit), kSpecThreads, 0, st>>>(c, b);
-    return cudaGetLastError();
+    return launch_pdl(k_spec_wfield, dim3((half_count(C) + 15) / 16, (c.R + 1) / 2, c.esplit), kSpecThreads, 0, st, c,
+                      b);
 }
 
 cudaError_t launch_spec_wupdate(const SpecConfig &c, const SpecBuffers &b, cudaStream_t st) {
