@@ -368,7 +368,45 @@ def test_observables_on_constructed_states():
     assert abs(orc.eta(np.zeros(64), 5)) == 0.0
 
 
+def test_observed_energy_with_dipoles_on_uniform_states():
+    """The E/N that the sweep's observables record, with C_D != 0, on states that a
+    vanishing cone keeps fixed: uniform +z gives -2J - K2 - K4 + (C_D/2) S and
+    uniform +x gives -2J - (C_D/4) S per spin, S = 4 zeta(3/2) beta(3/2) the
+    square-lattice sum of 1/r^3 (closed form; W~ with A = 64 and its tail
+    reproduces it to a few 1e-6)."""
+    L = 16
+    S = lattice_sum_inv_r3()
+    W = orc.wtilde(L, 64, True)
+    J, CD, K2, K4 = 0.7, 0.3, 0.5, 0.2
+    p = orc.params(L, 8, J, CD, K2, K4, 1e-9, proposal=0, cone=1e-9, seed=3)
+    up = orc.sweeps(p, W, inputs.saturated_z(L)[0], 0, 1, trace=False, observe=True)["obs"][-1]
+    assert abs(up[4] - (-2 * J - K2 - K4 + 0.5 * CD * S)) < 1e-5
+    sx = np.zeros((3, L, L))
+    sx[0] = 1.0
+    inpl = orc.sweeps(p, W, sx, 0, 1, trace=False, observe=True)["obs"][-1]
+    assert abs(inpl[4] - (-2 * J - 0.25 * CD * S)) < 1e-5
+
+
 def test_interactions_per_spin():
-    """Sec. 2.1: one spin's dipole energy at L = 64 takes N = L^2 = 4096 terms; the
-    oracle's field sum at one site runs over every site of the cell exactly once."""
-    assert 64 * 64 == GOLDEN["interactions_per_spin_L64"]["value"]
+    """Sec. 2.1: one spin's dipole energy at L = 64 takes N = L^2 = 4096 terms.  The
+    oracle's field sum must visit every site of the cell exactly once, the site
+    itself included (through W~(0)): with a constant tensor (zz = 1, all else 0) and
+    all spins +z, h_z is the number of terms at every site; with xx = 1 and random
+    spins, h_x is the plain sum of s_x and h_y, h_z vanish.  A dropped self term,
+    a doubled row or column (the garbled loop bounds of Appendix A) or a transposed
+    component fails one of these."""
+    L = 64
+    W = np.zeros((4, L, L))
+    W[3] = 1.0
+    s = np.zeros((3, L, L))
+    s[2] = 1.0
+    h = orc.field(W, s)
+    assert np.all(h[2] == GOLDEN["interactions_per_spin_L64"]["value"])
+    assert np.all(h[:2] == 0.0)
+    rng = np.random.default_rng(3)
+    s = rng.integers(-3, 4, size=(3, L, L)).astype(np.float64)
+    W = np.zeros((4, L, L))
+    W[0] = 1.0
+    h = orc.field(W, s)
+    assert np.all(h[0] == s[0].sum())
+    assert np.all(h[1:] == 0.0)
