@@ -304,9 +304,10 @@ int mc_restore(mc_lattice *lat, const void *buf, size_t len);
  * needs no lattice handle and allocates nothing: the field it needs between its
  * two kernels lives in a fixed 4 MiB array in device memory that every GPU which
  * loads the library holds until the process exits.
- *   L, R       lattice size and number of states (L >= 2, R >= 1), with
- *              R * 3 * L * L <= 1048576 (e.g. R <= 85 at L = 64, R <= 5 at L = 256);
- *              larger requests fail with MC_EINVAL and name the largest R.
+ *   L, R       lattice size and number of states, 2 <= L <= 4096, 1 <= R <= 65535,
+ *              with R * 3 * L * L <= 1048576 (e.g. R <= 85 at L = 64, R <= 5 at
+ *              L = 256); larger requests fail with MC_EINVAL, whose message names
+ *              the bound that was exceeded (and the largest R for this L).
  *   W32        device, [4][L][L] FP32 replica-summed tensor (as from mc_get_W, cast).
  *   spins      device, [R][3][L][L] FP32.
  *   couplings  device, [R][4] FP32: J, C_D, K2, K4 of each state.

@@ -282,31 +282,9 @@ __global__ void __launch_bounds__(256) k_energy(int L, const float *__restrict__
                                                 const float *__restrict__ h,
                                                 const RepParams *__restrict__ P, double *E) {
     const int N = L * L, r = blockIdx.x;
-    const float *s = spins + (size_t)r * 3 * N;
-    const float *f = h + (size_t)r * 3 * N;
     const RepParams p = P[r];
-    double ex = 0, an = 0, dp = 0;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        const int x = i % L, y = i / L;
-        const int ixp = y * L + (x + 1 == L ? 0 : x + 1);
-        const int iyp = (y + 1 == L ? 0 : y + 1) * L + x;
-        const double a = s[i], b = s[N + i], c = s[2 * N + i];
-        ex += a * ((double)s[ixp] + (double)s[iyp]) + b * ((double)s[N + ixp] + (double)s[N + iyp]) +
-              c * ((double)s[2 * N + ixp] + (double)s[2 * N + iyp]);
-        const double z2 = c * c;
-        an += -(double)p.K2 * z2 - (double)p.K4 * z2 * z2;
-        dp += a * (double)f[i] + b * (double)f[N + i] + c * (double)f[2 * N + i];
-    }
-    double tot = -(double)p.J * ex + an + 0.5 * (double)p.CD * dp;
-    for (int off = 16; off; off >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, off);
-    __shared__ double red[32];
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tot;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s2 = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s2 += red[w];
-        E[r] = s2;
-    }
+    const double e = cta_replica_energy(L, spins + (size_t)r * 3 * N, h + (size_t)r * 3 * N, p.J, p.CD, p.K2, p.K4);
+    if (threadIdx.x == 0) E[r] = e;
 }
 
 cudaError_t launch_energy(int L, int R, const float *spins, const float *h, const RepParams *p,

@@ -22,6 +22,8 @@ namespace {
 
 // Capacity of the field scratch: R * 3 * L * L FP32 values (4 MiB).
 constexpr size_t kScratchFloats = size_t(1) << 20;
+// The field kernel runs one grid row per state (gridDim.y), at most 65535 rows.
+constexpr int kMaxStates = 65535;
 
 static __device__ __align__(256) float g_field_scratch[kScratchFloats];
 
@@ -29,40 +31,16 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 float *g_scratch_addr[kMaxDevices] = {};  // device address of g_field_scratch, per device
 
-// Same sums as the energy kernel of the lattice handles (Sec. 4 energy with the
-// ferromagnetic-exchange and E_A = -K2 z^2 - K4 z^4 readings), reading the
-// couplings as [R][4] = (J, C_D, K2, K4).
+// The energy sums of the lattice handles' energy kernel (cta_replica_energy),
+// reading the couplings as [R][4] = (J, C_D, K2, K4).
 __global__ void __launch_bounds__(256) k_energy_couplings(int L, const float *__restrict__ spins,
                                                           const float *__restrict__ h,
                                                           const float *__restrict__ couplings,
                                                           double *E) {
     const int N = L * L, r = blockIdx.x;
-    const float *s = spins + (size_t)r * 3 * N;
-    const float *f = h + (size_t)r * 3 * N;
-    const double J = couplings[4 * r + 0], CD = couplings[4 * r + 1];
-    const double K2 = couplings[4 * r + 2], K4 = couplings[4 * r + 3];
-    double ex = 0, an = 0, dp = 0;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        const int x = i % L, y = i / L;
-        const int ixp = y * L + (x + 1 == L ? 0 : x + 1);
-        const int iyp = (y + 1 == L ? 0 : y + 1) * L + x;
-        const double a = s[i], b = s[N + i], c = s[2 * N + i];
-        ex += a * ((double)s[ixp] + (double)s[iyp]) + b * ((double)s[N + ixp] + (double)s[N + iyp]) +
-              c * ((double)s[2 * N + ixp] + (double)s[2 * N + iyp]);
-        const double z2 = c * c;
-        an += -K2 * z2 - K4 * z2 * z2;
-        dp += a * (double)f[i] + b * (double)f[N + i] + c * (double)f[2 * N + i];
-    }
-    double tot = -J * ex + an + 0.5 * CD * dp;
-    for (int off = 16; off; off >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, off);
-    __shared__ double red[32];
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tot;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s2 = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s2 += red[w];
-        E[r] = s2;
-    }
+    const float *c = couplings + 4 * (size_t)r;
+    const double e = cta_replica_energy(L, spins + (size_t)r * 3 * N, h + (size_t)r * 3 * N, c[0], c[1], c[2], c[3]);
+    if (threadIdx.x == 0) E[r] = e;
 }
 
 }  // namespace
@@ -72,7 +50,10 @@ using namespace dipmc;
 
 extern "C" int mc_energy_noalloc(int L, int R, const float *W32, const float *spins,
                                  const float *couplings, double *energy, void *stream) {
-    if (L < 2 || L > 4096 || R < 1) return set_last_error(MC_EINVAL, "mc_energy_noalloc: need L >= 2 and R >= 1");
+    if (L < 2 || L > 4096)
+        return set_last_error(MC_EINVAL, "mc_energy_noalloc: need 2 <= L <= 4096");
+    if (R < 1 || R > kMaxStates)
+        return set_last_error(MC_EINVAL, "mc_energy_noalloc: need 1 <= R <= 65535 (one grid row per state)");
     if (!W32 || !spins || !couplings || !energy)
         return set_last_error(MC_EINVAL, "mc_energy_noalloc: null buffer");
     const size_t need = (size_t)R * 3 * (size_t)L * (size_t)L;

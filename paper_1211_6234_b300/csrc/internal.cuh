@@ -203,6 +203,39 @@ struct SweepBuffers {
     EnergyHist hist;                    // optional energy histogram
 };
 
+// Total energy of one replica (Sec. 4 energy with the ferromagnetic-exchange and
+// E_A = -K2 z^2 - K4 z^4 readings) from its spins s [3][L][L] and field f = W~ * s
+// [3][L][L]:  -J sum_bonds s_i.s_j + sum_i E_A(s_i) + (C_D / 2) sum_i s_i.h_i, each bond
+// (i, i + x), (i, i + y) once, FP64 sums.  Called by every thread of one CTA (a
+// multiple of 32 threads, at most 1024); the result is valid in thread 0.  The
+// handle energy kernel and the allocation-free energy kernel both call it.
+__device__ __forceinline__ double cta_replica_energy(int L, const float *__restrict__ s,
+                                                     const float *__restrict__ f, double J, double CD,
+                                                     double K2, double K4) {
+    const int N = L * L;
+    double ex = 0, an = 0, dp = 0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const int x = i % L, y = i / L;
+        const int ixp = y * L + (x + 1 == L ? 0 : x + 1);
+        const int iyp = (y + 1 == L ? 0 : y + 1) * L + x;
+        const double a = s[i], b = s[N + i], c = s[2 * N + i];
+        ex += a * ((double)s[ixp] + (double)s[iyp]) + b * ((double)s[N + ixp] + (double)s[N + iyp]) +
+              c * ((double)s[2 * N + ixp] + (double)s[2 * N + iyp]);
+        const double z2 = c * c;
+        an += -K2 * z2 - K4 * z2 * z2;
+        dp += a * (double)f[i] + b * (double)f[N + i] + c * (double)f[2 * N + i];
+    }
+    double tot = -J * ex + an + 0.5 * CD * dp;
+    for (int off = 16; off; off >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, off);
+    __shared__ double red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tot;
+    __syncthreads();
+    double sum = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w];
+    return sum;
+}
+
 // Launchers (implemented in their .cu files).  Return a cudaError_t.
 cudaError_t launch_wtilde(int L, int A, int tail, double *W64, float *W32, cudaStream_t st);
 cudaError_t launch_cast_W(int L, const double *W64, float *W32, cudaStream_t st);
