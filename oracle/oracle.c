@@ -539,12 +539,60 @@ static void observe(const orc_params *p, const double *W, const double *s, doubl
 }
 
 /*
+ * Decisions of one sub-step (Sec. 3.1 algorithm, Sec. 3.2 approximation): sub-step
+ * k of sweep t uses offset o = schedule(t, k); each of the n = (L/l)^2 update sites
+ * q = o + l(a, b), in the order d = b*C + a (C = L/l), gets its field, a proposal,
+ * dE and the Metropolis decision, all from the state s as given (s is not
+ * changed).  Per site d: q[d], h[3d..3d+2], dE[d], u[d], acc[d], S[3d..3d+2].
+ */
+void orc_substep(const orc_params *p, const double *W, const double *s, uint32_t t, uint32_t k,
+                 int32_t *q, double *h, double *dE, double *u, int32_t *acc, double *S)
+{
+    const int L = p->L, l = p->l;
+    const int N = L * L, C = L / l, n = C * C;
+    uint32_t key[2];
+    keyof(p->seed, key);
+    uint32_t v = orc_offset(p->seed, l, p->schedule, t, k);
+    int ox = (int)(v % (uint32_t)l), oy = (int)(v / (uint32_t)l);
+    for (int d = 0; d < n; ++d) {
+        int qx = ox + l * (d % C), qy = oy + l * (d / C);
+        int qq = qy * L + qx;
+        q[d] = qq;
+        field_at(W, L, s, qx, qy, h + 3 * d);
+        uint32_t c[4] = {(uint32_t)qq, p->replica, t, (k & 0x00FFFFFFu) | (TAG_ATTEMPT << 24)};
+        uint32_t w[4];
+        orc_philox4x32_10(c, key, w);
+        double sq[3] = {s[qq], s[N + qq], s[2 * N + qq]};
+        propose(p->proposal, p->cone, sq, u24(w[0]), u24(w[1]), S + 3 * d);
+        dE[d] = delta_e(p, W, s, qx, qy, h + 3 * d, S + 3 * d);
+        u[d] = u24(w[2]);
+        acc[d] = (u[d] < exp(-dE[d] / p->T)) ? 1 : 0;
+    }
+}
+
+/* Per-sweep observables and cone-angle sums of the state after sweep `it`. */
+static void observe_sweep(const orc_params *p, const double *W, const double *s, int it, double *obs,
+                          double *theta2)
+{
+    const int N = p->L * p->L;
+    if (obs) observe(p, W, s, obs + ORC_NOBS * it);
+    if (theta2)
+        for (int i = 0; i < N; ++i) {
+            double zc = fmax(-1.0, fmin(1.0, s[2 * N + i]));
+            double dt = acos(zc) - 0.5 * ORC_PI;
+            theta2[i] += dt * dt;
+        }
+}
+
+/*
  * Approximated parallel sweeps (Sec. 3.1 algorithm, Sec. 3.2 approximation).
  * s is [3][L][L], updated in place.  Sweeps t0 .. t0+nsweeps-1; each has l^2
- * sub-steps.  Trace arrays (may be NULL) hold one record per attempt, in order
- * (sweep, sub-step, site d = Dy*C + Dx with C = L/l):  q (site index), h[3],
- * dE, u, accept, S[3].  obs (may be NULL) gets ORC_NOBS values per sweep;
- * theta2 (may be NULL) accumulates (acos s_z - pi/2)^2 per site per sweep.
+ * sub-steps, decided by orc_substep from the state before the step, after which
+ * all accepted moves are applied together.  Trace arrays (may be NULL) hold one
+ * record per attempt, in order (sweep, sub-step, site d = Dy*C + Dx with
+ * C = L/l):  q (site index), h[3], dE, u, accept, S[3].  obs (may be NULL) gets
+ * ORC_NOBS values per sweep; theta2 (may be NULL) accumulates
+ * (acos s_z - pi/2)^2 per site per sweep.
  */
 int orc_sweeps(const orc_params *p, const double *W, double *s, uint32_t t0, int nsweeps,
                int32_t *tr_q, double *tr_h, double *tr_dE, double *tr_u, int32_t *tr_acc,
@@ -553,64 +601,87 @@ int orc_sweeps(const orc_params *p, const double *W, double *s, uint32_t t0, int
     const int L = p->L, l = p->l;
     if (l < 1 || L % l != 0) return -1;
     const int N = L * L, C = L / l, n = C * C;
-    uint32_t key[2];
-    keyof(p->seed, key);
     double *hq = (double *)malloc(sizeof(double) * 3 * n);
     double *Sq = (double *)malloc(sizeof(double) * 3 * n);
-    int *acc = (int *)malloc(sizeof(int) * n);
-    int *qs = (int *)malloc(sizeof(int) * n);
+    double *dE = (double *)malloc(sizeof(double) * n);
+    double *u = (double *)malloc(sizeof(double) * n);
+    int32_t *acc = (int32_t *)malloc(sizeof(int32_t) * n);
+    int32_t *qs = (int32_t *)malloc(sizeof(int32_t) * n);
     size_t rec = 0;
     for (int it = 0; it < nsweeps; ++it) {
         uint32_t t = t0 + (uint32_t)it;
         for (uint32_t k = 0; k < (uint32_t)(l * l); ++k) {
-            uint32_t v = orc_offset(p->seed, l, p->schedule, t, k);
-            int ox = (int)(v % (uint32_t)l), oy = (int)(v / (uint32_t)l);
             /* decide every site from the state before the step */
-            for (int d = 0; d < n; ++d) {
-                int qx = ox + l * (d % C), qy = oy + l * (d / C);
-                int q = qy * L + qx;
-                qs[d] = q;
-                double h[3];
-                field_at(W, L, s, qx, qy, h);
-                uint32_t c[4] = {(uint32_t)q, p->replica, t, (k & 0x00FFFFFFu) | (TAG_ATTEMPT << 24)};
-                uint32_t w[4];
-                orc_philox4x32_10(c, key, w);
-                double sq[3] = {s[q], s[N + q], s[2 * N + q]};
-                double S[3];
-                propose(p->proposal, p->cone, sq, u24(w[0]), u24(w[1]), S);
-                double dE = delta_e(p, W, s, qx, qy, h, S);
-                double u = u24(w[2]);
-                acc[d] = (u < exp(-dE / p->T)) ? 1 : 0;
-                for (int c3 = 0; c3 < 3; ++c3) {
-                    hq[3 * d + c3] = h[c3];
-                    Sq[3 * d + c3] = S[c3];
-                }
-                if (tr_q) tr_q[rec] = q;
-                if (tr_h) for (int c3 = 0; c3 < 3; ++c3) tr_h[3 * rec + c3] = h[c3];
-                if (tr_dE) tr_dE[rec] = dE;
-                if (tr_u) tr_u[rec] = u;
+            orc_substep(p, W, s, t, k, qs, hq, dE, u, acc, Sq);
+            for (int d = 0; d < n; ++d, ++rec) {
+                if (tr_q) tr_q[rec] = qs[d];
+                if (tr_h) for (int c3 = 0; c3 < 3; ++c3) tr_h[3 * rec + c3] = hq[3 * d + c3];
+                if (tr_dE) tr_dE[rec] = dE[d];
+                if (tr_u) tr_u[rec] = u[d];
                 if (tr_acc) tr_acc[rec] = acc[d];
-                if (tr_S) for (int c3 = 0; c3 < 3; ++c3) tr_S[3 * rec + c3] = S[c3];
-                ++rec;
+                if (tr_S) for (int c3 = 0; c3 < 3; ++c3) tr_S[3 * rec + c3] = Sq[3 * d + c3];
             }
             /* then apply all accepted moves together */
             for (int d = 0; d < n; ++d)
                 if (acc[d])
                     for (int c3 = 0; c3 < 3; ++c3) s[c3 * N + qs[d]] = Sq[3 * d + c3];
         }
-        if (obs) observe(p, W, s, obs + ORC_NOBS * it);
-        if (theta2)
-            for (int i = 0; i < N; ++i) {
-                double zc = fmax(-1.0, fmin(1.0, s[2 * N + i]));
-                double dt = acos(zc) - 0.5 * ORC_PI;
-                theta2[i] += dt * dt;
-            }
+        observe_sweep(p, W, s, it, obs, theta2);
     }
     free(hq);
     free(Sq);
+    free(dE);
+    free(u);
     free(acc);
     free(qs);
     return 0;
+}
+
+/*
+ * Decisions re-synchronised to another trajectory (the decision parity of the
+ * simultaneous update, Sec. 3.1, judged per sub-step): the sub-steps of sweeps
+ * t0 .. t0+nsweeps-1 are decided in order by orc_substep from the state s, and
+ * s then takes the moves that the other trajectory made at that sub-step's sites
+ * (ext_acc[rec] = 1: the site becomes ext_S[3 rec .. 3 rec + 2]), whatever the
+ * oracle decided.  So every sub-step is decided from the other trajectory's
+ * pre-step state (up to the FP32 rounding of ext_S), and one differing decision
+ * does not separate the two for the rest of the run.  Records as orc_sweeps.
+ */
+int orc_replay(const orc_params *p, const double *W, double *s, uint32_t t0, int nsweeps,
+               const int32_t *ext_acc, const double *ext_S, int32_t *tr_q, double *tr_h, double *tr_dE,
+               double *tr_u, int32_t *tr_acc, double *tr_S)
+{
+    const int L = p->L, l = p->l;
+    if (l < 1 || L % l != 0) return -1;
+    const int N = L * L, C = L / l, n = C * C;
+    size_t rec = 0;
+    for (int it = 0; it < nsweeps; ++it) {
+        uint32_t t = t0 + (uint32_t)it;
+        for (uint32_t k = 0; k < (uint32_t)(l * l); ++k, rec += (size_t)n) {
+            orc_substep(p, W, s, t, k, tr_q + rec, tr_h + 3 * rec, tr_dE + rec, tr_u + rec, tr_acc + rec,
+                        tr_S + 3 * rec);
+            for (int d = 0; d < n; ++d)
+                if (ext_acc[rec + d])
+                    for (int c3 = 0; c3 < 3; ++c3) s[c3 * N + tr_q[rec + d]] = ext_S[3 * (rec + d) + c3];
+        }
+    }
+    return 0;
+}
+
+/* orc_replay for R independent replicas over all host threads: s is [R][3][L][L],
+ * ext and trace arrays are replica-major with nsweeps * L^2 records each. */
+int orc_replay_batch(int R, const orc_params *ps, const double *W, double *s, uint32_t t0, int nsweeps,
+                     const int32_t *ext_acc, const double *ext_S, int32_t *tr_q, double *tr_h,
+                     double *tr_dE, double *tr_u, int32_t *tr_acc, double *tr_S)
+{
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+    for (int r = 0; r < R; ++r) {
+        const size_t N = (size_t)ps[r].L * ps[r].L, m = (size_t)nsweeps * N, o = (size_t)r * m;
+        bad |= orc_replay(&ps[r], W, s + (size_t)r * 3 * N, t0, nsweeps, ext_acc + o, ext_S + 3 * o, tr_q + o,
+                          tr_h + 3 * o, tr_dE + o, tr_u + o, tr_acc + o, tr_S + 3 * o) != 0;
+    }
+    return bad ? -1 : 0;
 }
 
 /* Several independent replicas (one params struct and one [3][L][L] state

@@ -81,6 +81,11 @@ def lib():
         _lib.orc_sweeps_batch.argtypes = [C.c_int, C.POINTER(Params), d, d, C.c_uint32, C.c_int,
                                           d, d]
         _lib.orc_sweeps_batch.restype = C.c_int
+        _lib.orc_substep.argtypes = [C.POINTER(Params), d, d, C.c_uint32, C.c_uint32, i32, d, d, d, i32, d]
+        _lib.orc_substep.restype = None
+        _lib.orc_replay_batch.argtypes = [C.c_int, C.POINTER(Params), d, d, C.c_uint32, C.c_int, i32, d,
+                                          i32, d, d, d, i32, d]
+        _lib.orc_replay_batch.restype = C.c_int
         _lib.orc_sweeps_exact.argtypes = [C.POINTER(Params), d, d, C.c_uint32, C.c_int, d, i32]
         _lib.orc_sweeps_exact.restype = C.c_int
         _lib.orc_init_random.argtypes = [C.c_int, C.c_uint64, C.c_uint32, d]
@@ -185,6 +190,43 @@ def sweeps(p: Params, W, s, t0: int, nsweeps: int, trace: bool = True, observe: 
         _dp(out["dE"]) if trace else null, _dp(out["u"]) if trace else null,
         _ip(out["acc"]) if trace else null, _dp(out["S"]) if trace else null,
         _dp(out["obs"]) if observe else null, _dp(out["theta2"]) if observe else null)
+    if rc != 0:
+        raise ValueError("bad arguments")
+    out["s"] = s
+    return out
+
+
+def substep(p: Params, W, s, t: int, k: int):
+    """Decisions of sub-step k of sweep t from state s (unchanged): per update
+    site d, q, h[3], dE, u, accept, S[3]."""
+    n = (p.L // p.l) ** 2
+    W = np.ascontiguousarray(W, np.float64)
+    s = np.ascontiguousarray(s, np.float64)
+    out = {"q": np.zeros(n, np.int32), "h": np.zeros((n, 3)), "dE": np.zeros(n), "u": np.zeros(n),
+           "acc": np.zeros(n, np.int32), "S": np.zeros((n, 3))}
+    lib().orc_substep(C.byref(p), _dp(W), _dp(s), t, k, _ip(out["q"]), _dp(out["h"]), _dp(out["dE"]),
+                      _dp(out["u"]), _ip(out["acc"]), _dp(out["S"]))
+    return out
+
+
+def replay_batch(ps, W, s, t0: int, nsweeps: int, ext_acc, ext_S):
+    """Decisions of every sub-step, each from the pre-step state of another
+    trajectory (orc_replay): s is [R, 3, L, L] (copied); ext_acc [R, n_att] and
+    ext_S [R, n_att, 3] are that trajectory's decisions and proposals in trace
+    order (n_att = nsweeps * L^2).  Returns the oracle's q, h, dE, u, acc, S per
+    attempt, [R, n_att, ...], and the final state (the other trajectory's)."""
+    R = len(ps)
+    arr = (Params * R)(*ps)
+    L = ps[0].L
+    m = nsweeps * L * L
+    W = np.ascontiguousarray(W, np.float64)
+    s = np.array(s, np.float64, copy=True, order="C")
+    ea = np.ascontiguousarray(ext_acc, np.int32).reshape(R, m)
+    eS = np.ascontiguousarray(ext_S, np.float64).reshape(R, m, 3)
+    out = {"q": np.zeros((R, m), np.int32), "h": np.zeros((R, m, 3)), "dE": np.zeros((R, m)),
+           "u": np.zeros((R, m)), "acc": np.zeros((R, m), np.int32), "S": np.zeros((R, m, 3))}
+    rc = lib().orc_replay_batch(R, arr, _dp(W), _dp(s), t0, nsweeps, _ip(ea), _dp(eS), _ip(out["q"]),
+                                _dp(out["h"]), _dp(out["dE"]), _dp(out["u"]), _ip(out["acc"]), _dp(out["S"]))
     if rc != 0:
         raise ValueError("bad arguments")
     out["s"] = s
