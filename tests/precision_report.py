@@ -3,7 +3,8 @@
     python -m tests.precision_report        # on a GPU host; prints a markdown table
 
 For each path: one traced sweep of two replicas at L = 64, l = 32 (the paper's
-lattice and spacing), compared attempt by attempt with the oracle (field error
+lattice and spacing), compared attempt by attempt with the oracle decided from the GPU's pre-step
+state (field error
 normwise, dE error, straddled decisions); then a 12-sweep run at L = 16, l = 8
 whose trajectory equals the oracle's, with the largest deviation of the per-sweep
 observable means from the oracle's.
@@ -20,7 +21,7 @@ sys.path.insert(0, ROOT)
 
 from oracle import oracle as orc  # noqa: E402
 from paper_1211_6234_b300 import dipmc, inputs  # noqa: E402
-from tests.parity_util import F32, compare_trace  # noqa: E402
+from tests.parity_util import F32, compare_trace, resync  # noqa: E402
 
 PATHS = [("direct", dipmc.MC_PATH_DIRECT), ("window_f32", dipmc.MC_PATH_WINDOW_F32),
          ("tensor_bf16x3", dipmc.MC_PATH_TENSOR), ("fft", dipmc.MC_PATH_FFT),
@@ -41,7 +42,7 @@ def traced(path, L=64, l=32, R=2, A=64):
     out = {"h": 0.0, "dE": 0.0, "straddles": 0, "attempts": 0}
     for r in range(R):
         J, CD, K2, K4, T = prm[r]
-        o = orc.sweeps(orc.params(L, l, J, CD, K2, K4, T, seed=5, replica=r), W, s0[r], 0, 1)
+        o = resync(orc.params(L, l, J, CD, K2, K4, T, seed=5, replica=r), W, s0[r], 0, 1, tr[r])
         hmax = float(np.abs(o["h"]).max())
         rep = compare_trace(tr[r], o, T, scale=1 + abs(J) + abs(K2) + abs(K4) + CD * hmax)
         out["h"] = max(out["h"], rep.h_err_norm)

@@ -10,7 +10,7 @@ pytestmark = pytest.mark.gpu
 
 from oracle import oracle as orc  # noqa: E402
 from paper_1211_6234_b300 import inputs  # noqa: E402
-from tests.parity_util import F32, compare_trace  # noqa: E402
+from tests.parity_util import F32, compare_trace, resync  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -43,5 +43,5 @@ def test_ewald_in_a_handle_and_a_traced_sweep(dipmc):
     assert np.abs(Wg - We).max() <= 1e-12 * np.abs(We).max()
     assert np.abs(Wg - orc.wtilde(L, 64, True)).max() <= 1e-7 * np.abs(We).max()
     p = orc.params(L, l, *prm, proposal=0, cone=0.5, schedule=0, seed=seed, replica=0)
-    o = orc.sweeps(p, We, s0[0], 0, 2)
+    o = resync(p, We, s0[0], 0, 2, tr[0])
     compare_trace(tr[0], o, prm[4], scale=2 + 0.1 * float(np.abs(o["h"]).max()))

@@ -12,7 +12,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from oracle import oracle as orc  # noqa: E402
-from tests.parity_util import F32, compare_trace  # noqa: E402
+from tests.parity_util import F32, compare_trace, resync  # noqa: E402
 
 # Appendix B's J/C_D = 1.7 with its energy (J/2) sum_<ij> counting each bond
 # once: a coupling of 0.85 C_D per bond, where stripes of width 1 have the
@@ -57,7 +57,7 @@ def test_ising_trace_matches_oracle(dipmc, path):
     for r in range(R):
         s0 = orc.init_ising(L, seed, r)
         p = orc.params(L, l, J, CD, 0.0, 0.0, Ts[r], proposal=2, schedule=0, seed=seed, replica=r)
-        o = orc.sweeps(p, W, s0, 0, nsw)
+        o = resync(p, W, s0, 0, nsw, tr[r])
         hmax = float(np.abs(o["h"]).max())
         rep = compare_trace(tr[r], o, Ts[r], scale=1 + abs(J) + abs(CD) * hmax)
         if rep.straddles == 0:
@@ -125,4 +125,4 @@ def test_simultaneous_update_against_exact_sequential(dipmc):
             eb = math.sqrt(np.mean([res[32][r][nm]["err"] ** 2 for r in rs]) / len(rs))
             diff = abs(a.mean() - b.mean())
             print(f"{phase} {nm}: l=16 {a.mean():.5f} +- {ea:.5f}, l=32 {b.mean():.5f} +- {eb:.5f}")
-            assert diff < 4 * math.hypot(ea, eb) + 0.01 * abs(b.mean()), (phase, nm, a.mean(), b.mean(), ea, eb)
+            assert diff < 3 * math.hypot(ea, eb) + 0.01 * abs(b.mean()), (phase, nm, a.mean(), b.mean(), ea, eb)

@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 from oracle import oracle as orc  # noqa: E402
 from paper_1211_6234_b300 import inputs  # noqa: E402
-from tests.parity_util import F32, binned_error, compare_trace  # noqa: E402
+from tests.parity_util import F32, binned_error, compare_trace, resync  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -110,7 +110,7 @@ def test_sweep_trace_matches_oracle(dipmc, case):
         J, CD, K2, K4, T = params[r]
         p = orc.params(L, l, J, CD, K2, K4, T, proposal=proposal, cone=0.5, schedule=schedule,
                        seed=seed, replica=r)
-        o = orc.sweeps(p, W, s0[r], 0, nsw)
+        o = resync(p, W, s0[r], 0, nsw, tr[r])
         hmax = float(np.abs(o["h"]).max())
         rep = compare_trace(tr[r], o, T, scale=1 + abs(J) + abs(K2) + abs(K4) + abs(CD) * hmax)
         straddles += rep.straddles
@@ -123,7 +123,7 @@ def test_sweep_trace_matches_oracle(dipmc, case):
             assert abs(Eg_tracked[r] - Eo) < 1e-5 * (L * L) * (1 + abs(J) + abs(K2) + abs(K4) + CD * 10)
         assert abs(Eg_tracked[r] - Eg_full[r]) < 1e-5 * (L * L) * (1 + abs(J) + abs(K2) + abs(K4) + CD * 10)
     total = sum(nsw * L * L for _ in range(R))
-    assert straddles / total <= 1e-3, straddles
+    assert straddles / total <= 1e-6, straddles
 
 
 def test_l_equals_L_gpu_matches_exact_sequential(dipmc):
@@ -152,7 +152,7 @@ def test_l_equals_L_gpu_matches_exact_sequential(dipmc):
 def test_observables_statistically_match_oracle(dipmc, T):
     """L = 16, 2000 sweeps measured every sweep, away from the ordering temperature
     (ordered at T = 0.5, paramagnetic at T = 2.5): GPU means against the oracle's
-    run (independent trajectories, same law) within 4 combined binned errors."""
+    run (independent trajectories, same law) within 3 combined binned errors."""
     L, l, nsw, warm_sw = 16, 8, 2000, 300
     J, CD, K2, K4, T = F32(1.0), F32(0.1), F32(0.8), F32(0.0), F32(T)
     s0 = inputs.saturated_z(L, 1)
@@ -175,7 +175,7 @@ def test_observables_statistically_match_oracle(dipmc, T):
         eo = binned_error(x)
         eg = og[nm]["err"]
         diff = abs(og[nm]["mean"] - x.mean())
-        assert diff <= 4 * math.hypot(eo, eg) + 1e-9, (nm, og[nm]["mean"], x.mean(), eo, eg)
+        assert diff <= 3 * math.hypot(eo, eg) + 1e-9, (nm, og[nm]["mean"], x.mean(), eo, eg)
     eta_o = orc.eta(o["theta2"], nsw)
     assert abs(og["eta"] - eta_o) < 0.03, (og["eta"], eta_o)
     assert 0 < og["accepted"] <= og["attempted"] == nsw * L * L
@@ -348,7 +348,7 @@ def test_bench_configuration_sampled_replicas(dipmc):
     for r in (0, 37, 148, 255):
         J, CD, K2, K4, T = lad[r]
         p = orc.params(L, l, J, CD, K2, K4, T, proposal=0, cone=0.5, schedule=0, seed=seed, replica=r)
-        o = orc.sweeps(p, W, s0[r], 0, 1)
+        o = resync(p, W, s0[r], 0, 1, tr[r])
         hmax = float(np.abs(o["h"]).max())
         rep = compare_trace(tr[r], o, T, scale=1 + abs(J) + abs(K2) + abs(K4) + abs(CD) * hmax)
         if rep.straddles == 0:
@@ -367,7 +367,7 @@ def test_many_replica_instance_small_lattice(dipmc):
     W = oracle_W(L, 64)
     for r in (0, 159):
         p = orc.params(L, l, 1.0, F32(0.1), F32(0.8), 0.0, F32(0.6), seed=8, replica=r)
-        o = orc.sweeps(p, W, s0[r], 0, 2)
+        o = resync(p, W, s0[r], 0, 2, tr[r])
         compare_trace(tr[r], o, F32(0.6), scale=2 + 0.1 * float(np.abs(o["h"]).max()))
 
 
@@ -415,7 +415,7 @@ def test_window_paths_match_oracle(dipmc, path, case):
     for r in range(R):
         J, CD, K2, K4, T = params[r]
         p = orc.params(L, l, J, CD, K2, K4, T, proposal=0, cone=0.5, schedule=schedule, seed=seed, replica=r)
-        o = orc.sweeps(p, W, s0[r], 0, nsw)
+        o = resync(p, W, s0[r], 0, nsw, tr[r])
         hmax = float(np.abs(o["h"]).max())
         rep = compare_trace(tr[r], o, T, scale=1 + abs(J) + abs(K2) + abs(K4) + abs(CD) * hmax)
         if rep.straddles == 0:
@@ -423,12 +423,75 @@ def test_window_paths_match_oracle(dipmc, path, case):
         assert abs(Eg_tracked[r] - Eg_full[r]) < 1e-5 * (L * L) * (1 + abs(J) + abs(K2) + abs(K4) + CD * 10)
 
 
-@pytest.mark.parametrize("R,sample", [(256, (0, 1, 100, 200, 255)), (300, (0, 255, 256, 299))])
-def test_tensor_path_bench_configuration(dipmc, R, sample):
-    """256 replicas x L = 64 on the tensor path (the benchmark's configuration), and 300
-    (a second, ragged N-tile of 44 replicas): one traced sweep, sampled replicas
-    compared attempt by attempt with the oracle."""
-    L, l, A = 64, 32, 64
+def _resync_all(lad, L, l, seed, W, s0, tr, nsw, chunk=32):
+    """Every replica's trace against the oracle re-synchronised per sub-step
+    (orc_replay over all host threads, `chunk` replicas at a time); returns the
+    straddle count, the attempts compared and the worst field / dE errors."""
+    R = tr.shape[0]
+    tot = {"straddles": 0, "compared": 0, "h_err": 0.0, "dE_err": 0.0}
+    for c0 in range(0, R, chunk):
+        rr = range(c0, min(R, c0 + chunk))
+        ps = [orc.params(L, l, *lad[r], proposal=0, cone=0.5, schedule=0, seed=seed, replica=r) for r in rr]
+        out = orc.replay_batch(ps, W, s0[c0:c0 + len(rr)], 0, nsw, tr[c0:c0 + len(rr), :, 6].astype(np.int32),
+                               tr[c0:c0 + len(rr), :, 7:10].astype(np.float64))
+        for i, r in enumerate(rr):
+            J, CD, K2, K4, T = lad[r]
+            o = {k: v[i] for k, v in out.items()}
+            hmax = float(np.abs(o["h"]).max())
+            rep = compare_trace(tr[r], o, T, scale=1 + abs(J) + abs(K2) + abs(K4) + abs(CD) * hmax)
+            tot["straddles"] += rep.straddles
+            tot["compared"] += rep.compared
+            tot["h_err"] = max(tot["h_err"], rep.h_err_norm)
+            tot["dE_err"] = max(tot["dE_err"], rep.dE_err)
+    return tot
+
+
+@pytest.mark.parametrize("path", ["tensor", "direct"])
+def test_bench_shape_every_attempt_resynced(dipmc, path):
+    """The benchmark's launch configuration -- 256 replicas x L = 64, l = 32, the
+    16 T x 16 K4/K2 ladder -- traced over 4 sweeps on the tensor path (4.2e6
+    attempts; 1 sweep on the direct path), and every attempt of every replica
+    compared with the oracle decided from the GPU's pre-step state: fields within
+    1e-5 normwise at every attempt, dE within the FP32 tolerance, and differing
+    decisions only where the threshold straddles the two dE, at a fraction of at
+    most 1e-6 of the attempts."""
+    L, l, R, A = 64, 32, 256, 64
+    nsw = 4 if path == "tensor" else 1
+    lad = [(F32(1.0), F32(0.1), F32(k2), F32(k4), F32(T)) for (T, k2, k4) in inputs.ladder(16, 16)]
+    s0 = inputs.random_spins(L, R, seed=2024)
+    with dipmc.Lattice(L, l, R, 1) as lat:
+        lat.precompute_W(A, True)
+        lat.set_field_path(dipmc.MC_PATH_TENSOR if path == "tensor" else dipmc.MC_PATH_DIRECT)
+        for r, prm in enumerate(lad):
+            lat.set_params(*prm, replica=r)
+        lat.init_spins(2, s0)
+        tr = lat.sweep_trace(nsw)
+        sg = lat.get_spins()
+    assert tr.shape == (R, nsw * L * L, 10)
+    tot = _resync_all(lad, L, l, 1, oracle_W(L, A), s0, tr, nsw)
+    print(f"\n[{path} path, 256 x L=64, l=32, {nsw} sweep(s)] attempts compared: {tot['compared']}, "
+          f"straddles: {tot['straddles']}, max field error (normwise): {tot['h_err']:.2e}, "
+          f"max dE error: {tot['dE_err']:.2e}")
+    assert tot["compared"] == R * nsw * L * L
+    assert tot["straddles"] / tot["compared"] <= 1e-6, tot
+    assert tot["h_err"] <= 1e-5
+    # the final spins are the trace's last accepted proposals: replay the trace
+    st = s0.astype(np.float32).copy()
+    for r in range(R):
+        acc = np.nonzero(tr[r, :, 6] > 0.5)[0]
+        q = tr[r, acc, 0].astype(np.int64)
+        _, last = np.unique(q[::-1], return_index=True)    # each site's last accepted move
+        pick = acc[len(acc) - 1 - last]
+        st[r].reshape(3, -1)[:, tr[r, pick, 0].astype(np.int64)] = tr[r, pick, 7:10].T
+    np.testing.assert_allclose(sg, st, rtol=0, atol=1e-6)
+
+
+def test_tensor_path_ragged_second_tile(dipmc):
+    """300 replicas x L = 64 on the tensor path: a second, ragged N-tile of 44
+    replicas; one traced sweep, sampled replicas of both tiles compared attempt by
+    attempt with the re-synchronised oracle."""
+    L, l, A, R = 64, 32, 64, 300
+    sample = (0, 255, 256, 299)
     lad = [(F32(1.0), F32(0.1), F32(k2), F32(k4), F32(T)) for (T, k2, k4) in inputs.ladder(16, 16)]
     lad = [lad[r % len(lad)] for r in range(R)]
     s0 = inputs.random_spins(L, R, seed=2024)
@@ -445,18 +508,18 @@ def test_tensor_path_bench_configuration(dipmc, R, sample):
     for r in sample:
         J, CD, K2, K4, T = lad[r]
         p = orc.params(L, l, J, CD, K2, K4, T, proposal=0, cone=0.5, schedule=0, seed=1, replica=r)
-        o = orc.sweeps(p, W, s0[r], 0, 1)
+        o = resync(p, W, s0[r], 0, 1, tr[r])
         hmax = float(np.abs(o["h"]).max())
         rep = compare_trace(tr[r], o, T, scale=1 + abs(J) + abs(K2) + abs(K4) + abs(CD) * hmax)
         worst = max(worst, rep.h_err_norm)
-        if rep.straddles == 0:
-            np.testing.assert_allclose(sg[r], o["s"], rtol=0, atol=1e-5)
+        assert rep.straddles == 0
+        np.testing.assert_allclose(sg[r], o["s"], rtol=0, atol=1e-6)
     assert worst < 1e-5
 
 
 def test_tensor_path_observables_match_direct(dipmc):
     """Long runs of the tensor and direct paths sample the same law: means within
-    4 combined binned errors (L = 16, 64 replicas pooled by temperature)."""
+    3 combined binned errors (L = 16, 64 replicas pooled by temperature)."""
     L, l, R, nsw = 16, 8, 64, 600
     res = {}
     for path in (dipmc.MC_PATH_DIRECT, dipmc.MC_PATH_TENSOR):
@@ -474,7 +537,44 @@ def test_tensor_path_observables_match_direct(dipmc):
         b = np.array([o[nm]["mean"] for o in res[3]])
         ea = np.sqrt(np.mean([o[nm]["err"] ** 2 for o in res[1]]) / R)
         eb = np.sqrt(np.mean([o[nm]["err"] ** 2 for o in res[3]]) / R)
-        assert abs(a.mean() - b.mean()) < 4 * math.hypot(ea, eb) + 1e-9, (nm, a.mean(), b.mean(), ea, eb)
+        assert abs(a.mean() - b.mean()) < 3 * math.hypot(ea, eb) + 1e-9, (nm, a.mean(), b.mean(), ea, eb)
+
+
+def test_tensor_path_ordered_phase_matches_oracle(dipmc):
+    """A long run of the tensor path in the perpendicular ordered phase (T = 0.4,
+    L = 32, l = 16: the spectral tensor operands of the benchmark's L = 2l) against
+    the oracle's own runs: |m|, M_par, E/N and the cone angle eta, each averaged
+    over independent replicas (64 on the GPU, 16 in the oracle, both from +z),
+    agree within 3 combined standard errors of the replica means."""
+    L, l, R_gpu, R_orc, neq, nms = 32, 16, 64, 16, 150, 600
+    prm = (F32(1.0), F32(0.1), F32(0.8), F32(0.0), F32(0.4))
+    with dipmc.Lattice(L, l, R_gpu, 71) as lat:
+        lat.precompute_W(64, True)
+        lat.set_field_path(dipmc.MC_PATH_TENSOR)
+        lat.set_params(*prm)
+        lat.init_spins(1)
+        lat.sweep(neq, 0)
+        lat.reset_observables()
+        lat.sweep(nms, 1)
+        og = lat.observables_batch()
+    W = oracle_W(L, 64)
+    ps = [orc.params(L, l, *prm, proposal=0, cone=0.5, schedule=0, seed=72, replica=r) for r in range(R_orc)]
+    s0 = inputs.saturated_z(L, R_orc)
+    warm = orc.sweeps_batch(ps, W, s0, 0, neq, observe=False)["s"]
+    o = orc.sweeps_batch(ps, W, warm, neq, nms, observe=True)
+    names = {"abs_m": 0, "m_par": 3, "e": 4}
+    for nm, k in names.items():
+        a = np.array([g[nm]["mean"] for g in og])
+        b = o["obs"][:, :, k].mean(axis=1)
+        ea, eb = a.std(ddof=1) / math.sqrt(len(a)), b.std(ddof=1) / math.sqrt(len(b))
+        print(f"T=0.4 {nm}: tensor {a.mean():.6f} +- {ea:.6f}, oracle {b.mean():.6f} +- {eb:.6f}")
+        assert abs(a.mean() - b.mean()) <= 3 * math.hypot(ea, eb), (nm, a.mean(), b.mean(), ea, eb)
+    a = np.array([g["eta"] for g in og])
+    b = np.array([orc.eta(o["theta2"][r], nms) for r in range(R_orc)])
+    ea, eb = a.std(ddof=1) / math.sqrt(len(a)), b.std(ddof=1) / math.sqrt(len(b))
+    print(f"T=0.4 eta: tensor {a.mean():.6f} +- {ea:.6f}, oracle {b.mean():.6f} +- {eb:.6f}")
+    assert abs(a.mean() - b.mean()) <= 3 * math.hypot(ea, eb), ("eta", a.mean(), b.mean(), ea, eb)
+    assert a.mean() > 0.6     # ordered perpendicular (the disordered limit is 0.4352)
 
 
 # ---------------------------------------------------------------- FFT path
@@ -629,7 +729,7 @@ def test_fft_path_trace_matches_oracle(dipmc, case):
     for r in range(R):
         J, CD, K2, K4, T = params[r]
         p = orc.params(L, l, J, CD, K2, K4, T, proposal=0, cone=0.5, schedule=schedule, seed=seed, replica=r)
-        o = orc.sweeps(p, W, s0[r], 0, nsw)
+        o = resync(p, W, s0[r], 0, nsw, tr[r])
         hmax = float(np.abs(o["h"]).max())
         rep = compare_trace(tr[r], o, T, scale=1 + abs(J) + abs(K2) + abs(K4) + abs(CD) * hmax)
         if rep.straddles == 0:
@@ -659,7 +759,7 @@ def test_fft_path_observables_match_direct(dipmc, other):
         b = np.array([o[nm]["mean"] for o in res[other]])
         ea = np.sqrt(np.mean([o[nm]["err"] ** 2 for o in res[1]]) / R)
         eb = np.sqrt(np.mean([o[nm]["err"] ** 2 for o in res[other]]) / R)
-        assert abs(a.mean() - b.mean()) < 4 * math.hypot(ea, eb) + 1e-9, (nm, a.mean(), b.mean(), ea, eb)
+        assert abs(a.mean() - b.mean()) < 3 * math.hypot(ea, eb) + 1e-9, (nm, a.mean(), b.mean(), ea, eb)
 
 
 # ---------------------------------------------------------------- graphs and autotuning
