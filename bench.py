@@ -11,6 +11,13 @@ W~ summed over 64 image cells with the continuum tail, seeded random initial
 spins.  Metric: site-updates/s including the dipole field (replicas x L^2 x
 sweeps / time).  The L2 cache is flushed (256 MiB write) before every timed step.
 
+Further legs on rank 0 (each labelled in the JSON line): the plain single-replica
+FP32 path; L = 256 with 16 replicas (FFT vs spectral vs direct, autotuned); the
+dipolar Ising variant; a reduced-length Sec. 4 scan; the L = 64 cooling scan
+(nine (K2, K4) pairs, T = 1.2 -> 0.2, 1e4 sweeps per temperature); the serving
+stream at its stated sweep counts for a bounded window, and the same stream with
+scaled-down sweep counts run to completion.
+
 Under torchrun each rank runs its own 256-replica batch (independent chains,
 no data exchange: weak scaling); the time is the max over ranks.
 
@@ -198,12 +205,19 @@ def cpu_baseline_sample(seconds_target=12.0):
                       f"{dt:.1f} s"}
 
 
-def serving_leg(dipmc, n_req, scale, quantum, budget_gb, rate_hz, timeout_s=240.0):
+def serving_leg(dipmc, n_req, scale, quantum, budget_gb, rate_hz, timeout_s=240.0, window_s=None):
     """Continuous batching of a Poisson stream of simulation requests (L uniform
     over {32, 48, 64, 96, 128, 256}, T ~ U[0.2, 1.2], K2 ~ U[0.5, 1], K4 ~
-    U[-0.3, 0.3], C_D = 0.1, log-uniform sweeps scaled by `scale`, l chosen at
-    flip-probability error 1e-3).  Requests are submitted at their arrival times;
-    latency = completion (results on the host) - arrival."""
+    U[-0.3, 0.3], C_D = 0.1, log-uniform sweeps 1e3 .. 1e5 times `scale`, l chosen
+    at flip-probability error 1e-3).  Requests are submitted at their arrival
+    times; latency = completion (results on the host) - arrival.
+
+    window_s = None: the whole stream runs to completion (bounded by timeout_s).
+    window_s = W: the stream runs for W seconds of wall time and stops there; the
+    throughput counts every sweep the server has credited to any request by then
+    (finished or not), and the latency percentiles cover the requests that
+    finished inside the window (the rest are reported as still running or queued,
+    i.e. censored)."""
     reqs = inputs.request_stream(n_req, seed=7, rate_hz=rate_hz, sweeps_scale=scale)
     srv = dipmc.Server(hbm_budget_bytes=int(budget_gb * (1 << 30)), quantum_sweeps=quantum, max_error=1e-3)
     # untimed warm-up: W~ of every L and one handle per L, one sweep each
@@ -215,10 +229,11 @@ def serving_leg(dipmc, n_req, scale, quantum, budget_gb, rate_hz, timeout_s=240.
     reasons = {}
     pending = {}
     i = 0
+    limit = window_s if window_s else timeout_s
     t0 = time.perf_counter()
     while i < len(reqs) or pending:
         now = time.perf_counter() - t0
-        if now > timeout_s:
+        if now > limit:
             break
         while i < len(reqs) and reqs[i]["arrival"] <= now:
             r = reqs[i]
@@ -241,15 +256,99 @@ def serving_leg(dipmc, n_req, scale, quantum, budget_gb, rate_hz, timeout_s=240.
                     reasons[why] = reasons.get(why, 0) + 1
                 srv.release(rid)
     span = time.perf_counter() - t0
+    # work credited to the requests still in the system (sweeps of finished quanta)
+    partial = 0
+    running = 0
+    for rid, r in pending.items():
+        st, done = srv.poll(rid)
+        partial += r["L"] * r["L"] * done
+        running += st == dipmc.MC_REQ_RUNNING
     st = srv.stats()
     srv.close()
     lat.sort()
     q = (lambda f: lat[min(len(lat) - 1, int(f * len(lat)))] if lat else None)  # noqa: E731
-    return {"requests": len(reqs), "completed": len(lat), "failed": failed, "unfinished": len(pending) + len(reqs) - i,
-            "site_updates_per_s": upd / span, "makespan_s": span, "p50_latency_s": q(0.50), "p99_latency_s": q(0.99),
-            "arrival_rate_hz": rate_hz, "sweeps": f"log-uniform [1e3, 1e5] x {scale}", "quantum_sweeps": quantum,
-            "hbm_budget_gb": budget_gb, "packs": st["packs"], "lone_handles": st["lone"],
-            "site_updates": upd, "failure_reasons": reasons}
+    total_work = sum(r["L"] * r["L"] * r["sweeps"] for r in reqs)
+    return {"requests": len(reqs), "submitted": i, "completed": len(lat), "failed": failed,
+            "running_at_end": running, "queued_at_end": len(pending) - running, "not_yet_arrived": len(reqs) - i,
+            "site_updates_per_s": (upd + partial) / span, "makespan_s": span,
+            "p50_latency_s": q(0.50), "p99_latency_s": q(0.99),
+            "latency_over": "requests finished inside the window" if window_s else "all requests",
+            "window_s": window_s, "arrival_rate_hz": rate_hz, "sweeps": f"log-uniform [1e3, 1e5] x {scale}",
+            "quantum_sweeps": quantum, "hbm_budget_gb": budget_gb, "packs": st["packs"], "lone_handles": st["lone"],
+            "site_updates": upd + partial, "stream_site_updates": total_work, "failure_reasons": reasons}
+
+
+def cooling_scan_leg(dipmc, stream, sweeps_per_T=10000, chunk=100):
+    """L = 64 cooling scan: J = 1, C_D = 0.1, the nine (K2, K4) pairs K2 in {0.6, 0.8,
+    1.0} x K4 in {-0.2, 0, 0.2} as nine replicas of one handle, l = 32, from
+    saturated +z at T = 1.2 down to 0.2 in steps of 0.05 (21 temperatures, each
+    continuing from the previous one's final state), `sweeps_per_T` sweeps per
+    temperature with observables every sweep.  The field path is the one the
+    library's autotuner picks for this handle.  Reports site-updates/s over the
+    whole scan and, per (K2, K4) and T, |m|, m_z, M_par (planar |m_xy|), the cone
+    angle eta and E/N with their binned errors."""
+    import torch
+    Lc, lc = 64, 32
+    pairs = [(k2, k4) for k2 in (0.6, 0.8, 1.0) for k4 in (-0.2, 0.0, 0.2)]
+    Ts = inputs.cooling_schedule()
+    names = {dipmc.MC_PATH_DIRECT: "direct", dipmc.MC_PATH_TENSOR: "tensor", dipmc.MC_PATH_FFT: "fft",
+             dipmc.MC_PATH_SPECTRAL: "spectral", dipmc.MC_PATH_INCREMENTAL: "incremental",
+             dipmc.MC_PATH_WINDOW_F32: "window_f32"}
+    lat = dipmc.Lattice(Lc, lc, len(pairs), seed=31)
+    lat.precompute_W(A_IMG, True)
+    for r, (k2, k4) in enumerate(pairs):
+        lat.set_params(J, CD, f32(k2), f32(k4), f32(Ts[0]), replica=r)
+    lat.init_spins(1)
+    path, _ = lat.autotune(2, stream)
+    lat.init_spins(1)
+    lat.sweep(2, 1, stream)               # warm-up: graphs of the chunk shape
+    lat.init_spins(1)
+    torch.cuda.synchronize()
+    rows = {f"K2={k2},K4={k4}": {nm: [] for nm in ("abs_m", "m_z", "m_par", "eta", "e")} for (k2, k4) in pairs}
+    errs = {k: {nm: [] for nm in ("abs_m", "m_z", "m_par", "e")} for k in rows}
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_dev = 0.0
+    w0 = time.perf_counter()
+    for T in Ts:
+        for r, (k2, k4) in enumerate(pairs):
+            lat.set_params(J, CD, f32(k2), f32(k4), f32(T), replica=r)
+        lat.reset_observables()
+        a.record(stream)
+        done = 0
+        while done < sweeps_per_T:
+            c = min(chunk, sweeps_per_T - done)
+            lat.sweep(c, 1, stream)
+            done += c
+        b.record(stream)
+        torch.cuda.synchronize()
+        t_dev += a.elapsed_time(b) / 1e3
+        obs = lat.observables_batch()
+        for r, (k2, k4) in enumerate(pairs):
+            key = f"K2={k2},K4={k4}"
+            o = obs[r]
+            for nm, src in (("abs_m", "abs_m"), ("m_z", "m_z"), ("m_par", "m_par"), ("e", "e")):
+                rows[key][nm].append(round(float(o[src]["mean"]), 5))
+                errs[key][nm].append(float(f"{o[src]['err']:.2g}"))
+            rows[key]["eta"].append(round(float(o["eta"]), 5))
+    wall = time.perf_counter() - w0
+    ups = len(pairs) * Lc * Lc * sweeps_per_T * len(Ts)
+    lat.close()
+    return {"workload": "L=64 cooling scan: 9 (K2, K4) pairs, T = 1.2 -> 0.2 step 0.05 from +z, l=32",
+            "sweeps_per_T": sweeps_per_T, "temperatures": Ts, "field_path": names.get(path, str(path)),
+            "site_updates_per_s": ups / t_dev, "device_s": t_dev, "wall_s": wall,
+            "by_pair": {k: {"mean": rows[k], "err": errs[k]} for k in rows}}
+
+
+def serving_legs(dipmc, args):
+    """The 2000-request stream at its stated sweep counts (1e3 .. 1e5) for a
+    bounded window, and the same stream with every sweep count scaled down so
+    that it runs to completion (complete latency distribution, labelled)."""
+    out = {"serving": serving_leg(dipmc, args.serve_requests, 1.0, args.serve_quantum, 64.0, args.serve_rate,
+                                  window_s=args.serve_window if args.serve_window > 0 else None,
+                                  timeout_s=1e9)}
+    if args.serve_scaled > 0:
+        out["serving_scaled"] = serving_leg(dipmc, args.serve_requests, args.serve_scaled, 8, 64.0, 2000.0)
+    return out
 
 
 def large_lattice_leg(dipmc, stream, sweeps=8):
@@ -412,11 +511,17 @@ def main():
     ap.add_argument("--large-only", action="store_true", help="run only the L=256 leg")
     ap.add_argument("--no-ising", action="store_true", help="skip the dipolar Ising leg")
     ap.add_argument("--no-scan", action="store_true", help="skip the Sec. 4 scan leg")
-    ap.add_argument("--serve-only", action="store_true", help="run only the serving leg")
+    ap.add_argument("--serve-only", action="store_true", help="run only the serving legs")
     ap.add_argument("--serve-requests", type=int, default=2000)
-    ap.add_argument("--serve-scale", type=float, default=0.002, help="factor on the requests' sweep counts")
-    ap.add_argument("--serve-quantum", type=int, default=8)
-    ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate, requests/s")
+    ap.add_argument("--serve-window", type=float, default=60.0,
+                    help="seconds of the full-sweep-count serving stream (0 = run it to completion)")
+    ap.add_argument("--serve-quantum", type=int, default=32)
+    ap.add_argument("--serve-rate", type=float, default=50.0, help="Poisson arrival rate, requests/s")
+    ap.add_argument("--serve-scaled", type=float, default=0.002,
+                    help="sweep factor of the second, complete serving stream (0 = skip it)")
+    ap.add_argument("--no-cooling", action="store_true", help="skip the L=64 cooling scan")
+    ap.add_argument("--cooling-only", action="store_true", help="run only the L=64 cooling scan")
+    ap.add_argument("--cooling-sweeps", type=int, default=10000, help="sweeps per temperature of the cooling scan")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -440,8 +545,12 @@ def main():
         return
     if args.serve_only:
         if rank == 0:
-            print(json.dumps({"serving": serving_leg(dipmc, args.serve_requests, args.serve_scale,
-                                                     args.serve_quantum, 64.0, args.serve_rate)}), flush=True)
+            print(json.dumps(serving_legs(dipmc, args)), flush=True)
+        return
+    if args.cooling_only:
+        if rank == 0:
+            print(json.dumps({"cooling_scan": cooling_scan_leg(dipmc, torch.cuda.current_stream(),
+                                                               args.cooling_sweeps)}), flush=True)
         return
 
     lad = ladder()
@@ -613,10 +722,13 @@ def main():
     if rank == 0 and not args.no_scan:
         scan = srt_scan_leg(dipmc, stream)
 
-    serving = None
+    cooling = None
+    if rank == 0 and not args.no_cooling:
+        cooling = cooling_scan_leg(dipmc, stream, args.cooling_sweeps)
+
+    serving = {}
     if rank == 0 and not args.no_serve:
-        serving = serving_leg(dipmc, args.serve_requests, args.serve_scale, args.serve_quantum, 64.0,
-                              args.serve_rate)
+        serving = serving_legs(dipmc, args)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -643,7 +755,9 @@ def main():
             "large_lattice": large,
             "ising": ising,
             "srt_scan": scan,
-            "serving": serving,
+            "cooling_scan": cooling,
+            "serving": serving.get("serving"),
+            "serving_scaled": serving.get("serving_scaled"),
             "gpu_launches": gpu_launches,
             "clocks": clk,
             "wall_s_timed": wall,
