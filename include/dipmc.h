@@ -277,10 +277,39 @@ int mc_choose_spacing(int L, double C_D, double T_min, double max_error, int *l_
  * Autotuner: times every supported field path (and, for the tensor path, window
  * sizes of 32, 64 and 128 sub-steps) for nsweeps_trial sweeps on this handle,
  * restoring the state after each trial (checkpoint/restore), and keeps the
- * fastest.  The chosen path and window are returned (either pointer may be NULL).
- * Synchronises the device.
+ * fastest.  When the tensor path wins, its launch shapes (mc_tuning: split-K
+ * K-blocks per unit, N-tile, sub-step warp layout) are then tuned one at a time
+ * the same way.  The chosen path and window are returned (either pointer may be
+ * NULL); mc_get_tuning gives the rest.  Synchronises the device.
  */
 int mc_autotune(mc_lattice *lat, int nsweeps_trial, void *stream, int *path_out, int *window_out);
+
+/*
+ * Launch shapes of the windowed tensor path (none changes what is computed; the
+ * split-K shape changes the FP32 summation order, so trajectories under
+ * different shapes agree to rounding, not bit for bit):
+ *   window        sub-steps per window (as mc_set_window; 0 = automatic)
+ *   tc_kblocks    K-blocks of 32 per split-K unit of the tensor-core contraction
+ *                 (0 = automatic: the fewest whose units fit one wave of SMs)
+ *   tc_ntile      replicas per N-tile of the contraction, a multiple of 16 in
+ *                 [16, 256] (0 = automatic: 256, or all replicas when fewer)
+ *   steps_layout  warp roles of the sub-step kernel under the permutation
+ *                 schedule: 0 = one decider warp and seven helper warps; 1 = the
+ *                 helper that shares the decider's SM sub-partition stays idle
+ *                 during the blocks (six helpers); 2 = as 1, and the CTAs of every
+ *                 second wave of SMs decide on another sub-partition, so that two
+ *                 CTAs sharing an SM do not decide on the same one
+ * mc_set_tuning checks the fields and keeps them; mc_get_tuning returns them.
+ * mc_autotune searches them for the tensor path and leaves the fastest set.
+ */
+typedef struct mc_tuning {
+    int window;
+    int tc_kblocks;
+    int tc_ntile;
+    int steps_layout;
+} mc_tuning;
+int mc_set_tuning(mc_lattice *lat, const mc_tuning *t);
+int mc_get_tuning(mc_lattice *lat, mc_tuning *out);
 
 /* Sweep counter (index of the next sweep; the RNG counters depend on it). */
 int mc_get_sweep_counter(mc_lattice *lat, uint64_t *out);

@@ -79,6 +79,8 @@ struct mc_lattice {
     cudaStream_t last = nullptr;
     // windowed / tensor-core paths
     int window_B = 0;
+    int tc_kblocks = 0, tc_ntile = 0, steps_layout = 0;   // launch shapes (mc_tuning)
+    int plan_kb = 0, plan_nt = 0;                         // shapes the current tensor plan was made with
     __nv_bfloat16 *spins_hi = nullptr, *spins_lo = nullptr, *wsh = nullptr;
     TcUnit *units = nullptr;
     int nunits = 0, NT = 0, tmem_cols = 0, plan_Sw = 0;
@@ -347,7 +349,7 @@ int ensure_tensor_buffers(mc_lattice *p, int Sw, cudaStream_t st) {
         p->wsh_ready = true;
         p->wsh_spec2 = spec2;
     }
-    if (p->plan_Sw != Sw) {
+    if (p->plan_Sw != Sw || p->plan_kb != p->tc_kblocks || p->plan_nt != p->tc_ntile) {
         cudaFree(p->units);
         cudaFree(p->tcpart);
         cudaFree(p->tile_first);
@@ -358,7 +360,7 @@ int ensure_tensor_buffers(mc_lattice *p, int Sw, cudaStream_t st) {
         std::vector<TcUnit> u(65536);
         std::vector<int> tf(1 << 16);
         const int nu = tc_plan(p->L, Sw, p->R, nsm, u.data(), (int)u.size(), &p->NT, &p->tmem_cols, tf.data(),
-                               &p->mtiles, &p->ntiles, spec2);
+                               &p->mtiles, &p->ntiles, spec2, p->tc_kblocks, p->tc_ntile);
         if (nu <= 0) return fail(MC_EINVAL, "tensor-core plan failed for Sw=%d R=%d", Sw, p->R);
         CKA(cudaMalloc(&p->units, sizeof(TcUnit) * nu));
         CKA(cudaMemcpy(p->units, u.data(), sizeof(TcUnit) * nu, cudaMemcpyHostToDevice));
@@ -368,6 +370,8 @@ int ensure_tensor_buffers(mc_lattice *p, int Sw, cudaStream_t st) {
         CKA(cudaMalloc(&p->tcpart, sizeof(float) * (size_t)nu * p->NT * 128));
         p->nunits = nu;
         p->plan_Sw = Sw;
+        p->plan_kb = p->tc_kblocks;
+        p->plan_nt = p->tc_ntile;
         if (tc_map_bytes() > sizeof(p->tm_hi) || tc_encode_map(p->tm_hi, p->spins_hi, p->L, p->R, p->NT) ||
             tc_encode_map(p->tm_lo, p->spins_lo, p->L, p->R, p->NT))
             return fail(MC_ECUDA, "TMA map of the bf16 spins could not be encoded");
@@ -401,6 +405,13 @@ int run_windows(mc_lattice *p, int path, int nsweeps, int measure_every, float *
     c.stale_mode = tensor ? (spec2 ? 3 : 2) : 0;   // tensor path: the sub-step kernel sums the split-K partial tiles
     c.NT = p->NT;
     c.mtiles = p->mtiles;
+    c.layout = p->steps_layout;
+    {
+        int dev = 0, nsm = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        c.nsm = nsm;
+    }
     WindowBuffers b{};
     b.W32 = p->W32; b.spins = p->spins;
     b.spins_hi = tensor ? p->spins_hi : nullptr;
@@ -916,6 +927,32 @@ int mc_set_window(mc_lattice *p, int B) {
     return MC_OK;
 }
 
+int mc_set_tuning(mc_lattice *p, const mc_tuning *t) {
+    int rc = check(p);
+    if (rc) return rc;
+    if (!t) return fail(MC_EINVAL, "null tuning");
+    if (t->tc_kblocks < 0 || t->tc_kblocks > 4096) return fail(MC_EINVAL, "tc_kblocks must be in [0, 4096]");
+    if (t->tc_ntile != 0 && (t->tc_ntile < 16 || t->tc_ntile > 256 || t->tc_ntile % 16))
+        return fail(MC_EINVAL, "tc_ntile must be 0 or a multiple of 16 in [16, 256]");
+    if (t->steps_layout < 0 || t->steps_layout > 2) return fail(MC_EINVAL, "steps_layout must be 0, 1 or 2");
+    rc = mc_set_window(p, t->window);
+    if (rc) return rc;
+    drop_graphs(p);
+    p->tc_kblocks = t->tc_kblocks;
+    p->tc_ntile = t->tc_ntile;
+    p->steps_layout = t->steps_layout;
+    return MC_OK;
+}
+
+int mc_get_tuning(mc_lattice *p, mc_tuning *out) {
+    if (!p || !out) return fail(MC_EINVAL, "null argument");
+    out->window = p->window_B;
+    out->tc_kblocks = p->tc_kblocks;
+    out->tc_ntile = p->tc_ntile;
+    out->steps_layout = p->steps_layout;
+    return MC_OK;
+}
+
 int mc_init_spins(mc_lattice *p, int mode, const float *user) {
     int rc = check(p);
     if (rc) return rc;
@@ -1263,12 +1300,52 @@ int mc_autotune(mc_lattice *p, int nsweeps_trial, void *stream, int *path_out, i
         int r2 = mc_restore(p, saved.data(), len);
         if (r2) return r2;
     }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
     drop_graphs(p);
     (void)old_path;
     p->path = win.path;
     p->window_B = win.B;
+    if (win.path == MC_PATH_TENSOR) {
+        // launch shapes of the tensor path, one field at a time (coordinate search),
+        // each candidate timed as above; a candidate that fails is skipped
+        auto trial = [&](float *ms) -> int {
+            drop_graphs(p);
+            int r = run_sweeps(p, 1, 0, nullptr, st);
+            if (!r) {
+                CK(cudaEventRecord(a, st));
+                r = run_sweeps(p, nsweeps_trial, 0, nullptr, st);
+                CK(cudaEventRecord(b, st));
+            }
+            CK(cudaStreamSynchronize(st));
+            if (!r) CK(cudaEventElapsedTime(ms, a, b));
+            int r2 = mc_restore(p, saved.data(), len);
+            if (r2) return r2;
+            return r;
+        };
+        int *fields[3] = {&p->tc_kblocks, &p->tc_ntile, &p->steps_layout};
+        const std::vector<int> choices[3] = {{0, 2, 4, 6, 8, 12}, {0, 128}, {0, 1, 2}};
+        for (int f = 0; f < 3; ++f) {
+            int keep = *fields[f];
+            float bf = 1e30f;
+            for (int v : choices[f]) {
+                *fields[f] = v;
+                float ms = 0.f;
+                const int r = trial(&ms);
+                if (r == MC_ETIMEOUT || r == MC_ECUDA) {
+                    cudaEventDestroy(a);
+                    cudaEventDestroy(b);
+                    return r;
+                }
+                if (!r && ms < bf) {
+                    bf = ms;
+                    keep = v;
+                }
+            }
+            *fields[f] = keep;
+        }
+        drop_graphs(p);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
     if (path_out) *path_out = win.path;
     if (window_out) *window_out = win.B;
     return MC_OK;

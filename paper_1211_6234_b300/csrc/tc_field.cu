@@ -28,6 +28,8 @@
 // unit's partial tile (split-K); the sub-step kernel sums the partial tiles of
 // each output tile in a fixed order as it loads the window (deterministic, no
 // atomics).
+#include <algorithm>
+
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -569,9 +571,10 @@ cudaError_t launch_build_wsh(int L, const double *W64, __nv_bfloat16 *wsh, cudaS
 }
 
 int tc_plan(int L, int Sw, int R, int nsm, TcUnit *units, int max_units, int *NT_out, int *tmem_cols,
-            int *tile_first, int *mtiles_out, int *ntiles_out, bool spec2) {
+            int *tile_first, int *mtiles_out, int *ntiles_out, bool spec2, int kblocks, int ntile) {
     const int N = L * L;
-    const int NT = R >= 256 ? 256 : ((R + 15) / 16) * 16;
+    const int cap = (ntile >= 16 && ntile <= 256) ? (ntile / 16) * 16 : 256;
+    const int NT = R >= cap ? cap : ((R + 15) / 16) * 16;
     const int ntiles = (R + NT - 1) / NT;
     const int mt_inplane = 2 * Sw / 128, mt_zz = Sw / 128;
     // K per tile: Toeplitz rows contract (a, m) over 2N (in-plane) or N (zz); spectra
@@ -581,7 +584,8 @@ int tc_plan(int L, int Sw, int R, int nsm, TcUnit *units, int max_units, int *NT
     // smallest K-blocks per unit whose units (rounded up per tile) fit one wave
     int kbpu = (int)((total + nsm - 1) / nsm);
     if (kbpu < (spec2 ? 4 : 2)) kbpu = spec2 ? 4 : 2;   // spectra: at least 4 K-blocks a unit (measured)
-    for (;; ++kbpu) {
+    if (kblocks > 0) kbpu = std::min(kblocks, kb_inplane);
+    for (; kblocks <= 0; ++kbpu) {
         long long cnt = 0;
         for (int mt = 0; mt < mt_inplane + mt_zz; ++mt) {
             const int nkb = mt < mt_inplane ? kb_inplane : kb_zz;

@@ -54,8 +54,10 @@ cudaError_t launch_build_wsh(int L, const double *W64, __nv_bfloat16 *wsh, cudaS
 // units (CTAs) or -1 if max_units is too small.
 // Work plan: units ordered by (N-tile, M-tile, K range); tile_first (host,
 // ntiles * mtiles + 1 entries) gets the first unit of each tile.
+// kblocks > 0 fixes the K-blocks per unit (else the fewest whose units fit one wave);
+// ntile > 0 caps the replicas per N-tile (a multiple of 16, at most 256).
 int tc_plan(int L, int Sw, int R, int nsm, TcUnit *units, int max_units, int *NT, int *tmem_cols,
-            int *tile_first, int *mtiles, int *ntiles, bool spec2 = false);
+            int *tile_first, int *mtiles, int *ntiles, bool spec2 = false, int kblocks = 0, int ntile = 0);
 // TMA maps of the bf16 spin arrays (opaque 64-byte-aligned buffers of tc_map_bytes()).
 size_t tc_map_bytes();
 int tc_encode_map(void *map, const __nv_bfloat16 *spins, int L, int R, int NT);

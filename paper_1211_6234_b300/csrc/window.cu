@@ -375,6 +375,14 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
 
     long long n_acc = 0;
     const int nblk = B / G;
+    // warp roles during the blocks (layout): the decider warp dw, an idle warp or none,
+    // and the helpers, numbered hw = 0 .. nh-1
+    const int dw = (PRE && cfg.layout == 2 && ((r / cfg.nsm) & 1)) ? 2 : 0;
+    const bool spare = PRE && cfg.layout >= 1;
+    const bool idle = spare && warp == dw + 4;
+    const int hw = warp - (warp > dw ? 1 : 0) - (spare && warp > dw + 4 ? 1 : 0);
+    const int kH = (spare ? kWThreads / 32 - 2 : kWThreads / 32 - 1) * 32;   // helper threads
+    const int ht = hw * 32 + lane;                                           // helper thread index
     if constexpr (PRE) {
         // pair energies of block nb into etab[nb & 1]: row i is site nb*NB + i; columns
         // 0..NB-1 the sites of block nb-1 (dipolar part: their exchange acts through the
@@ -411,7 +419,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
         unsigned pm = 0;   // accepted sites of the previous block (decider)
         for (int bk = 0; bk < nblk; ++bk) {
             const int cur = bk & 1, prv = cur ^ 1, base = bk * NB;
-            if (warp == 0) {
+            if (warp == dw) {
                 const int i = lane & (NB - 1);
                 const int s = base + i;
                 const float4 *er = etab + cur * (2 * NB / 4) * NB + i;
@@ -483,9 +491,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
                     s_nmv[cur] = __popc(am);
                     n_acc += __popc(am);
                 }
-            } else {
-                constexpr int kH = kWThreads - 32;
-                const int ht = tid - 32;
+            } else if (!idle) {
                 const int nprev = bk > 0 ? s_nmv[prv] : 0;
                 // push the moves of block b-1 into the dE of the sites of blocks >= b+1
                 if (nprev > 0) {
@@ -809,10 +815,10 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
             if (tid == 0) hist_push(buf.hist, r, x[MC_OBS_E]);
         }
     }
-    if (tid == 0 && buf.obs) {
+    if (warp == dw && lane == 0 && buf.obs)
         atomicAdd(reinterpret_cast<unsigned long long *>(&buf.obs[r].accepted), (unsigned long long)n_acc);
+    if (tid == 0 && buf.obs)
         atomicAdd(reinterpret_cast<unsigned long long *>(&buf.obs[r].attempted), (unsigned long long)Sw);
-    }
 }
 
 __global__ void k_build_wq(int L, const float *__restrict__ W32, float4 *wq) {

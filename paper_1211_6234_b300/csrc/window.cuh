@@ -23,6 +23,13 @@ struct WindowConfig {
     int stale_mode;      // 0: stale = full field [R][3][N]; 2: the split-K partial tiles of the
                          // tensor-core field (part, tile_first), rows b*Sw + s
     int NT, mtiles;      // stale_mode 2: replicas per N-tile, M-tiles of 128 rows
+    int layout;          // warp roles of the permutation-schedule sub-steps (mc_tuning.steps_layout):
+                         // 0 decider warp 0, helpers 1..7; 1 decider warp 0, warp 4 (the
+                         // decider's sub-partition partner) idle during the blocks, helpers the
+                         // other six; 2 as 1, but CTAs r with (r / nsm) odd decide on warp 2
+                         // (partner warp 6 idle), so that two CTAs sharing an SM decide on
+                         // different sub-partitions
+    int nsm;             // SMs of the device (layout 2)
 };
 
 struct WindowBuffers {

@@ -34,7 +34,7 @@ ABI_SYMBOLS = (
     "mc_get_spins", "mc_get_field", "mc_get_W", "mc_energy", "mc_get_sweep_counter",
     "mc_checkpoint", "mc_restore", "mc_energy_noalloc", "mc_set_timing", "mc_get_timing",
     "mc_choose_spacing", "mc_autotune", "mc_set_histogram", "mc_get_histogram",
-    "mc_precompute_W_ewald", "mc_wtilde_ewald",
+    "mc_precompute_W_ewald", "mc_wtilde_ewald", "mc_set_tuning", "mc_get_tuning",
     "mc_footprint", "mc_server_create", "mc_server_submit", "mc_server_step", "mc_server_poll", "mc_server_request_info",
     "mc_server_collect", "mc_server_get_spins", "mc_server_release", "mc_server_get_stats", "mc_server_destroy",
 )
@@ -97,6 +97,10 @@ class mc_server_stats(C.Structure):
                 ("bytes_in_use", C.c_size_t), ("budget", C.c_size_t)]
 
 
+class mc_tuning(C.Structure):
+    _fields_ = [("window", C.c_int), ("tc_kblocks", C.c_int), ("tc_ntile", C.c_int), ("steps_layout", C.c_int)]
+
+
 class mc_timing(C.Structure):
     _fields_ = [("launches", C.c_int64 * 7), ("ms", C.c_double * 7)]
 
@@ -149,6 +153,8 @@ def _load():
         "mc_server_get_stats": ([vp, C.POINTER(mc_server_stats)], i32),
         "mc_server_destroy": ([vp], i32),
         "mc_get_timing": ([vp, C.POINTER(mc_timing)], i32),
+        "mc_set_tuning": ([vp, C.POINTER(mc_tuning)], i32),
+        "mc_get_tuning": ([vp, C.POINTER(mc_tuning)], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -250,6 +256,16 @@ class Lattice:
 
     def set_window(self, B=0):
         _ck(_lib.mc_set_window(self.h, B))
+
+    def set_tuning(self, window=0, tc_kblocks=0, tc_ntile=0, steps_layout=0):
+        """Launch shapes of the windowed tensor path (mc_set_tuning)."""
+        t = mc_tuning(window, tc_kblocks, tc_ntile, steps_layout)
+        _ck(_lib.mc_set_tuning(self.h, C.byref(t)))
+
+    def tuning(self) -> dict:
+        t = mc_tuning()
+        _ck(_lib.mc_get_tuning(self.h, C.byref(t)))
+        return {k: getattr(t, k) for k, _ in mc_tuning._fields_}
 
     def init_spins(self, mode=0, user=None):
         if mode == 2:

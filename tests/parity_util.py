@@ -86,6 +86,14 @@ def compare_trace(gpu_tr: np.ndarray, orc_out: dict, T: float, scale: float,
     return rep
 
 
+def pooled(means) -> tuple:
+    """Mean over independent replicas of their time averages, and its standard
+    error from the replicas' spread (autocorrelation-corrected by construction:
+    each replica's average carries its own autocorrelation)."""
+    x = np.asarray(means, np.float64)
+    return float(x.mean()), float(x.std(ddof=1) / math.sqrt(len(x)))
+
+
 def binned_error(x: np.ndarray, min_blocks: int = 32) -> float:
     """Autocorrelation-corrected standard error by blocking: the largest error over
     block sizes 2^k that leave at least min_blocks blocks."""
