@@ -185,6 +185,21 @@ int mc_precompute_W(mc_lattice *lat, int image_cutoff, int tail_correction);
 int mc_sweep(mc_lattice *lat, int nsweeps, int measure_every, void *stream);
 
 /*
+ * Uneven lattices in one launch: run nsweeps sweeps of every replica of `count`
+ * handles of possibly different L as ONE persistent launch of the direct kernel
+ * (one CTA per replica for the whole call), e.g. requests or parameter ladders of
+ * L = 32, 48, 64, 96 together.  The handles must all resolve to the direct path
+ * (MC_PATH_DIRECT), share C = L / l (the number of simultaneous sites per
+ * sub-step, Sec. 3.1), the proposal, cone and schedule, have W~ computed, keep no
+ * energy histogram and appear once each.  Every replica gets exactly the
+ * arithmetic of mc_sweep on its own handle (the same cell offsets per thread and
+ * reduction orders), so its spins, observables and tracked energy are those of
+ * that call, bit for bit; each handle's sweep counter advances by nsweeps.
+ * Asynchronous on `stream`.  MC_EINVAL for a handle that breaks a rule above.
+ */
+int mc_sweep_group(mc_lattice *const *lats, int count, int nsweeps, int measure_every, void *stream);
+
+/*
  * As mc_sweep (no measurement), and also record every attempt into `trace`
  * (device pointer, caller-owned, FP32).  Record layout, MC_TRACE_W floats per
  * attempt, ordered [replica][sweep][sub-step][site d] with d = Dy*(L/l) + Dx:
@@ -390,6 +405,7 @@ typedef struct mc_server_stats {
     int packs, lone;                    /* device handles held: packs and lone handles */
     int64_t completed;
     size_t bytes_in_use, budget;
+    int64_t grouped_launches;           /* launches that ran direct packs of different L together */
 } mc_server_stats;
 
 typedef struct mc_server mc_server;
@@ -403,8 +419,11 @@ int mc_footprint(int L, int l, int replicas, size_t *bytes);
  * whose replica slots belong to different requests, each slot with its own seed,
  * sweep counter and sweep budget, so that a request's result is bit-identical to
  * the same request run alone on a lone handle (mc_create_lattice with its seed,
- * mc_set_params, mc_precompute_W(A, 1), mc_init_spins, mc_sweep).  Other requests
- * get a lone handle of their own.  Handles run on separate streams and overlap.
+ * mc_set_params, mc_precompute_W(A, 1), mc_init_spins, mc_sweep).  Direct packs of
+ * different L with the same L / l, proposal and measurement interval whose busy
+ * slots fit one resident wave together run as one launch (as mc_sweep_group),
+ * still bit-identical to each request's lone run.  Other requests get a lone
+ * handle of their own.  Handles run on separate streams and overlap.
  *
  * Requests are admitted in arrival order while the device bytes of the handles
  * they need fit hbm_budget_bytes and fewer than max_active are running; a packed

@@ -114,6 +114,11 @@ struct mc_lattice {
     unsigned long long *hist = nullptr;
     double hist_lo = 0.0, hist_scale = 0.0;
     int hist_bins = 0;
+    // grouped direct launches (mc_sweep_group, server): descriptors staged through
+    // pinned memory, one copy in flight at a time
+    SlotGeom *geom_dev = nullptr, *geom_pin = nullptr;
+    int geom_cap = 0;
+    cudaEvent_t geom_copied = nullptr;
     // packed launches (serving): per-slot stream state, host shadow and pinned staging
     bool packed = false;
     SlotState *slots_dev = nullptr, *slots_pin = nullptr;
@@ -129,6 +134,9 @@ struct mc_lattice {
 namespace {
 
 void free_all(mc_lattice *p) {
+    cudaFree(p->geom_dev);
+    cudaFreeHost(p->geom_pin);
+    if (p->geom_copied) cudaEventDestroy(p->geom_copied);
     cudaFree(p->dparams);
     cudaFree(p->spins);
     cudaFree(p->field);
@@ -789,6 +797,114 @@ int run_sweeps(mc_lattice *p, int nsweeps, int measure_every, float *trace, cuda
     return MC_OK;
 }
 
+// One grouped launch of the direct kernel over every replica (or, for a pack,
+// every slot with sweeps to run) of several handles whose L / l agree: the
+// descriptors go to the device through the first handle's pinned staging, and
+// each CTA runs the arithmetic of its own handle's lone launch (mc_sweep, or a
+// packed launch), so every replica's result is the one it has there.  For packs,
+// nsweeps is each slot's own count (slots_host); `launched` = the largest.
+// Launch shape of a group: the largest lone thread count and EPT of its handles and
+// the shared memory of its largest lattice at that thread count.
+bool group_shape(mc_lattice *const *lats, int count, int *max_nt, int *max_ept, size_t *smem) {
+    *max_nt = 0;
+    *max_ept = 0;
+    *smem = 0;
+    for (int i = 0; i < count; ++i) {
+        int th = 0, ept = 0;
+        if (!direct_lone_shape(lats[i]->L, lats[i]->l, lats[i]->packed ? 1 : lats[i]->R, &th, &ept)) return false;
+        *max_nt = std::max(*max_nt, th);
+        *max_ept = std::max(*max_ept, ept);
+    }
+    for (int i = 0; i < count; ++i) *smem = std::max(*smem, direct_smem_bytes(lats[i]->L, lats[i]->l, *max_nt));
+    return true;
+}
+
+int run_group(mc_lattice *const *lats, int count, int nsweeps, int measure_every, cudaStream_t st, int *launched) {
+    mc_lattice *h0 = lats[0];
+    const int C = h0->L / h0->l;
+    std::vector<SlotGeom> g;
+    int max_nt = 0, max_ept = 0, mx = 0;
+    size_t smem = 0;
+    for (int i = 0; i < count; ++i) {
+        mc_lattice *p = lats[i];
+        int th = 0, ept = 0;
+        if (!direct_lone_shape(p->L, p->l, p->packed ? 1 : p->R, &th, &ept))
+            return fail(MC_ENOSYS, "the direct kernel does not serve L=%d l=%d", p->L, p->l);
+        max_nt = std::max(max_nt, th);
+        max_ept = std::max(max_ept, ept);
+        const uint2 key = key_of(p->seed);
+        for (int r = 0; r < p->R; ++r) {
+            SlotGeom d{};
+            d.L = p->L;
+            d.l = p->l;
+            d.nft = th - 32;
+            d.nt = th;
+            if (p->packed) {
+                const SlotState &sl = p->slots_host[r];
+                if (sl.nsweeps <= 0) continue;
+                d.key_lo = sl.key_lo;
+                d.key_hi = sl.key_hi;
+                d.t0 = sl.t0;
+                d.rid = sl.rid;
+                d.nsweeps = sl.nsweeps;
+                d.mphase = sl.t0;
+            } else {
+                d.key_lo = key.x;
+                d.key_hi = key.y;
+                d.t0 = (uint32_t)p->t;
+                d.rid = (uint32_t)r;
+                d.nsweeps = nsweeps;
+                d.mphase = 0;
+            }
+            const size_t N = p->N();
+            d.W32 = p->W32;
+            d.spins = p->spins + (size_t)r * 3 * N;
+            d.params = p->dparams + r;
+            d.energy = p->energy + r;
+            d.obs = p->obs + r;
+            d.theta2 = p->theta2 + (size_t)r * N;
+            mx = std::max(mx, d.nsweeps);
+            g.push_back(d);
+        }
+    }
+    *launched = mx;
+    if (g.empty() || mx == 0) return MC_OK;
+    group_shape(lats, count, &max_nt, &max_ept, &smem);
+    const int n = (int)g.size();
+    if (h0->geom_cap < n) {
+        if (h0->geom_copied) CK(cudaEventSynchronize(h0->geom_copied));
+        cudaFree(h0->geom_dev);
+        cudaFreeHost(h0->geom_pin);
+        h0->geom_dev = nullptr;
+        h0->geom_pin = nullptr;
+        h0->geom_cap = 0;
+        CK(cudaMalloc(&h0->geom_dev, sizeof(SlotGeom) * n));
+        CK(cudaMallocHost(&h0->geom_pin, sizeof(SlotGeom) * n));
+        h0->geom_cap = n;
+    }
+    if (!h0->geom_copied) CK(cudaEventCreateWithFlags(&h0->geom_copied, cudaEventDisableTiming));
+    CK(cudaEventSynchronize(h0->geom_copied));   // the previous call's staging copy is done
+    std::memcpy(h0->geom_pin, g.data(), sizeof(SlotGeom) * n);
+    CK(cudaMemcpyAsync(h0->geom_dev, h0->geom_pin, sizeof(SlotGeom) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(h0->geom_copied, st));
+    SweepConfig c{};
+    c.L = h0->L;
+    c.l = h0->l;
+    c.nsweeps = mx;
+    c.measure_every = measure_every;
+    c.proposal = h0->proposal;
+    c.cap_c1 = (float)(1.0 - std::cos(h0->cone));
+    c.schedule = h0->schedule;
+    cudaError_t e;
+    {
+        TimedLaunch tl(h0, MC_K_SWEEP_DIRECT, st);
+        e = launch_sweep_direct_grouped(C, max_ept, max_nt, smem, c, h0->geom_dev, n, st);
+    }
+    if (e == cudaErrorNotSupported) return fail(MC_ENOSYS, "no direct-kernel instance covers this group");
+    if (e != cudaSuccess) return cuda_fail(e, "grouped sweep launch");
+    return MC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1040,6 +1156,45 @@ int mc_sweep(mc_lattice *p, int nsweeps, int measure_every, void *stream) {
     int rc = check(p);
     if (rc) return rc;
     return run_sweeps(p, nsweeps, measure_every, nullptr, (cudaStream_t)stream);
+}
+
+int mc_sweep_group(mc_lattice *const *lats, int count, int nsweeps, int measure_every, void *stream) {
+    if (!lats || count < 1) return fail(MC_EINVAL, "mc_sweep_group needs at least one handle");
+    if (nsweeps < 0 || measure_every < 0) return fail(MC_EINVAL, "nsweeps and measure_every must be >= 0");
+    mc_lattice *h0 = lats[0];
+    int rc = check(h0);
+    if (rc) return rc;
+    for (int i = 0; i < count; ++i) {
+        mc_lattice *p = lats[i];
+        if (!p) return fail(MC_EINVAL, "handle %d is null", i);
+        for (int j = 0; j < i; ++j)
+            if (lats[j] == p) return fail(MC_EINVAL, "handle %d appears twice", i);
+        if (p->device != h0->device) return fail(MC_EINVAL, "handles of one group must be on one device");
+        if (p->packed) return fail(MC_EINVAL, "handle %d is a serving pack", i);
+        if (!p->W_ready) return fail(MC_ENOTREADY, "handle %d: mc_precompute_W has not been called", i);
+        if (resolve_path(p) != MC_PATH_DIRECT)
+            return fail(MC_EINVAL, "handle %d does not run the direct path (set MC_PATH_DIRECT)", i);
+        if (p->L / p->l != h0->L / h0->l)
+            return fail(MC_EINVAL, "handles of one group need the same L / l (%d vs %d)", p->L / p->l, h0->L / h0->l);
+        if (p->proposal != h0->proposal || p->cone != h0->cone || p->schedule != h0->schedule)
+            return fail(MC_EINVAL, "handles of one group need the same proposal, cone and schedule");
+        if (p->hist) return fail(MC_EINVAL, "handle %d keeps an energy histogram (not kept in grouped launches)", i);
+    }
+    if (nsweeps == 0) return MC_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int i = 0; i < count; ++i)
+        if (!lats[i]->energy_valid) {
+            rc = anchor_energy(lats[i], st);
+            if (rc) return rc;
+        }
+    int launched = 0;
+    rc = run_group(lats, count, nsweeps, measure_every, st, &launched);
+    if (rc) return rc;
+    for (int i = 0; i < count; ++i) {
+        lats[i]->t += (uint64_t)nsweeps;
+        lats[i]->last = st;
+    }
+    return MC_OK;
 }
 
 int mc_sweep_trace(mc_lattice *p, int nsweeps, float *trace, size_t trace_floats, void *stream) {
@@ -1534,6 +1689,30 @@ void pack_set_sweeps(mc_lattice *p, int slot, int count, int nsweeps) {
 }
 
 int pack_launch_direct(mc_lattice *p, int mx, int measure_every, cudaStream_t st);
+
+// Direct packs of one C, proposal, cone and measurement interval in one grouped
+// launch (their slots' own counts, as set by pack_set_sweeps); slot counters
+// advance as after pack_launch.  *launched = the longest slot's sweeps.
+int pack_group_launch(mc_lattice *const *packs, int count, int measure_every, cudaStream_t st, int *launched) {
+    int rc = run_group(packs, count, 0, measure_every, st, launched);
+    if (rc) return rc;
+    for (int i = 0; i < count; ++i) {
+        for (SlotState &s : packs[i]->slots_host) {
+            s.t0 += (uint32_t)std::max(0, (int)s.nsweeps);
+            s.nsweeps = 0;
+        }
+        packs[i]->last = st;
+    }
+    return MC_OK;
+}
+
+// CTAs a grouped launch of these packs keeps resident at once (0: not groupable).
+int pack_group_capacity(mc_lattice *const *packs, int count) {
+    int nt = 0, ept = 0;
+    size_t smem = 0;
+    if (!group_shape(packs, count, &nt, &ept, &smem)) return 0;
+    return direct_grouped_resident(packs[0]->L / packs[0]->l, ept, nt, smem);
+}
 
 // One packed launch: every slot with nsweeps > 0 advances that many sweeps of its
 // own chain; idle slots are untouched.  *launched = the longest slot's sweeps.

@@ -191,6 +191,28 @@ struct SlotState {
     uint32_t pad[3];
 };
 
+// One CTA of a grouped direct launch: lattices of different L (with the same
+// C = L / l) share one launch, each CTA carrying its own geometry, stream state
+// and buffers.  nft and nt are the field threads and the threads of the launch
+// the replica would have on its own handle, so that the CTA's arithmetic (which
+// cell offsets each thread sums, the order of every reduction) is the lone one.
+struct SlotGeom {
+    int L, l;
+    int nft;                    // field threads of the lone launch: cell offset e = ftid + j * nft
+    int nt;                     // threads of the lone launch: stride of the observable sums
+    uint32_t key_lo, key_hi;    // Philox key
+    uint32_t t0;                // sweep counter at the start of the launch
+    uint32_t rid;               // replica index of the counters
+    int nsweeps;                // sweeps of this CTA (<= the launch's)
+    uint32_t mphase;            // observables after sweep it of the launch when (mphase + it + 1) % measure_every == 0
+    const float *W32;           // [4][L*L]
+    float *spins;               // [3][L*L] of this replica
+    const RepParams *params;    // this replica's couplings
+    double *energy;             // its tracked energy
+    ObsAcc *obs;                // its accumulators (may be null)
+    double *theta2;             // [L*L] (may be null)
+};
+
 struct SweepBuffers {
     const float *W32 = nullptr;         // [4][N]
     float *spins = nullptr;             // [R][3][N]
@@ -201,6 +223,7 @@ struct SweepBuffers {
     float *trace = nullptr;             // optional [R][nsweeps][l^2][n][MC_TRACE_W]
     const SlotState *slots = nullptr;   // optional [R]: packed launch
     EnergyHist hist;                    // optional energy histogram
+    const SlotGeom *geom = nullptr;     // optional [grid]: grouped direct launch (the fields above unused)
 };
 
 // Total energy of one replica (Sec. 4 energy with the ferromagnetic-exchange and
@@ -253,6 +276,19 @@ cudaError_t launch_eta(int N, int count, const double *theta2, const ObsAcc *obs
 cudaError_t launch_sweep_direct(const SweepConfig &c, const SweepBuffers &b, int threads_hint,
                                 cudaStream_t st);
 bool direct_supported(int L, int l);
+// Threads and cell offsets per field thread (EPT) of the direct launch a handle
+// of R replicas of (L, l) gets; false if the direct kernel does not serve (L, l).
+bool direct_lone_shape(int L, int l, int R, int *threads, int *ept);
+// Dynamic shared memory of a direct CTA of (L, l) with `threads` threads.
+size_t direct_smem_bytes(int L, int l, int threads);
+// One launch over `count` CTAs of possibly different L (all with L / l == C), each
+// described by geom_dev[i] (device memory); c.nsweeps is the largest per-CTA count
+// and c.R is ignored.  threads = the largest lone thread count, max_ept the largest
+// lone EPT, smem the largest direct_smem_bytes at `threads`.
+cudaError_t launch_sweep_direct_grouped(int C, int max_ept, int threads, size_t smem, const SweepConfig &c,
+                                        const SlotGeom *geom_dev, int count, cudaStream_t st);
+// CTAs of such a grouped launch resident on the whole GPU at once (0: no instance).
+int direct_grouped_resident(int C, int max_ept, int threads, size_t smem);
 // CTAs of the direct kernel resident on the whole GPU for a packed launch of (L, l).
 int direct_resident_ctas(int L, int l);
 

@@ -48,6 +48,8 @@ int pack_fill(mc_lattice *p, int slot, int count, uint64_t seed, const RepParams
               cudaStream_t st);
 void pack_set_sweeps(mc_lattice *p, int slot, int count, int nsweeps);
 int pack_launch(mc_lattice *p, int measure_every, cudaStream_t st, int *launched);
+int pack_group_launch(mc_lattice *const *packs, int count, int measure_every, cudaStream_t st, int *launched);
+int pack_group_capacity(mc_lattice *const *packs, int count);
 int read_replicas(mc_lattice *p, int first, int count, cudaStream_t st, mc_obs *obs, float *spins);
 int lattice_refill(mc_lattice *p, uint64_t seed, const RepParams &rp, int init_mode, cudaStream_t st);
 }  // namespace dipmc
@@ -102,6 +104,7 @@ struct Runner {                 // a handle with its stream and completion event
 
 struct Pack : Runner {
     PackKey key;
+    int path = 0;                 // MC_PATH_DIRECT, _SPECTRAL or _FFT
     std::vector<uint64_t> owner;  // per slot: request id, 0 = free
     int measure_every = 0;
 };
@@ -137,6 +140,7 @@ struct mc_server {
     double max_error = 1e-3;
     uint64_t next_id = 1;
     int64_t completed = 0;
+    int64_t grouped_launches = 0;   // launches that carried direct packs of more than one L
     std::deque<uint64_t> queue;
     std::map<uint64_t, std::unique_ptr<Req>> reqs;
     std::map<std::pair<int, int>, double *> wcache;  // (L, A) -> W~ FP64 on the device
@@ -265,6 +269,7 @@ int try_admit(mc_server *s, Req &q) {
             const size_t bytes = lattice_footprint(r.L, r.l, cap);
             auto np = std::make_unique<Pack>();
             np->key = key;
+            np->path = ppath;
             np->measure_every = r.measure_every;
             np->owner.assign(cap, 0);
             const double *W = nullptr;
@@ -400,9 +405,11 @@ void retire(mc_server *s, Runner &u, bool is_pack) {
     }
 }
 
-void launch_pack(mc_server *s, Pack &p) {
-    if (p.inflight) return;
-    bool any = false;
+// The next quantum of every occupied slot of an idle pack (pack_set_sweeps);
+// returns the number of slots with sweeps to run.
+int plan_pack(mc_server *s, Pack &p) {
+    if (p.inflight) return 0;
+    int active = 0;
     for (int i = 0; i < (int)p.owner.size();) {
         Req *q = p.owner[i] ? find(s, p.owner[i]) : nullptr;
         if (!q) {
@@ -412,22 +419,85 @@ void launch_pack(mc_server *s, Pack &p) {
         const int n = (int)std::min<int64_t>(s->quantum, q->r.sweeps - q->done);
         pack_set_sweeps(p.lat, i, q->r.replicas, n);
         q->quantum_sweeps = n;
-        any = any || n > 0;
+        if (n > 0) active += q->r.replicas;
         i += q->r.replicas;
     }
-    if (!any) return;
+    return active;
+}
+
+void fail_pack(mc_server *s, Pack &p, const std::string &why) {
+    for (uint64_t o : p.owner) {
+        Req *q = o ? find(s, o) : nullptr;
+        if (q && q->state == MC_REQ_RUNNING) fail_req(s, *q, why);
+    }
+}
+
+void launch_pack(mc_server *s, Pack &p) {
+    if (p.inflight || plan_pack(s, p) == 0) return;
     int launched = 0;
     int rc = pack_launch(p.lat, p.measure_every, p.st, &launched);
     if (!rc && cudaEventRecord(p.ev, p.st) != cudaSuccess) rc = MC_ECUDA;
     if (rc) {
-        const std::string why = mc_last_error();
-        for (uint64_t o : p.owner) {
-            Req *q = o ? find(s, o) : nullptr;
-            if (q && q->state == MC_REQ_RUNNING) fail_req(s, *q, why);
-        }
+        fail_pack(s, p, mc_last_error());
         return;
     }
     p.inflight = launched > 0;
+}
+
+// Idle direct packs of one (C, proposal, cone, measurement interval) whose slots
+// with work all fit one resident wave of a grouped launch run as ONE launch on
+// the first pack's stream (lattices of different L side by side); the other packs'
+// streams are joined to it by events before and after, so their fills and
+// read-backs stay ordered.  Larger groups run pack by pack, at each pack's own
+// launch shape (a grouped launch takes the largest lattice's shape for every CTA).
+void launch_groups(mc_server *s) {
+    std::map<std::tuple<int, int, double, int>, std::vector<Pack *>> groups;
+    for (auto &p : s->packs) {
+        if (p->inflight || p->path != MC_PATH_DIRECT) continue;
+        const int L = std::get<0>(p->key), l = std::get<1>(p->key);
+        groups[std::make_tuple(L / l, std::get<3>(p->key), std::get<4>(p->key), p->measure_every)].push_back(p.get());
+    }
+    for (auto &kv : groups) {
+        std::vector<Pack *> &ps = kv.second;
+        if (ps.size() < 2) continue;
+        std::vector<Pack *> live;
+        int active = 0;
+        for (Pack *p : ps) {
+            const int a = plan_pack(s, *p);
+            if (a > 0) {
+                live.push_back(p);
+                active += a;
+            }
+        }
+        bool mixed = false;
+        for (Pack *p : live) mixed = mixed || std::get<0>(p->key) != std::get<0>(live[0]->key);
+        if (live.size() < 2 || !mixed) continue;   // launched one by one below
+        std::vector<mc_lattice *> lats;
+        for (Pack *p : live) lats.push_back(p->lat);
+        if (active > pack_group_capacity(lats.data(), (int)lats.size())) continue;
+        Pack &h = *live[0];
+        int rc = MC_OK;
+        for (size_t i = 1; i < live.size() && !rc; ++i) {
+            if (cudaEventRecord(live[i]->ev, live[i]->st) != cudaSuccess ||
+                cudaStreamWaitEvent(h.st, live[i]->ev, 0) != cudaSuccess)
+                rc = MC_ECUDA;
+        }
+        int launched = 0;
+        if (!rc) rc = pack_group_launch(lats.data(), (int)lats.size(), h.measure_every, h.st, &launched);
+        if (!rc && cudaEventRecord(h.ev, h.st) != cudaSuccess) rc = MC_ECUDA;
+        for (size_t i = 1; i < live.size() && !rc; ++i) {
+            if (cudaStreamWaitEvent(live[i]->st, h.ev, 0) != cudaSuccess ||
+                cudaEventRecord(live[i]->ev, live[i]->st) != cudaSuccess)
+                rc = MC_ECUDA;
+        }
+        if (rc) {
+            const std::string why = mc_last_error();
+            for (Pack *p : live) fail_pack(s, *p, why);
+            continue;
+        }
+        for (Pack *p : live) p->inflight = launched > 0;
+        ++s->grouped_launches;
+    }
 }
 
 void launch_solo(mc_server *s, Solo &u) {
@@ -534,6 +604,7 @@ int mc_server_step(mc_server *s) {
             else if (q.solo) finish(s, q, q.solo->lat, 0, q.solo->st);
         }
     }
+    launch_groups(s);
     for (auto &p : s->packs) launch_pack(s, *p);
     for (auto &u : s->solos) launch_solo(s, *u);
     return MC_OK;
@@ -618,6 +689,7 @@ int mc_server_get_stats(mc_server *s, mc_server_stats *out) {
         else if (st == MC_REQ_FAILED) ++out->failed;
     }
     out->completed = s->completed;
+    out->grouped_launches = s->grouped_launches;
     out->bytes_in_use = s->in_use;
     out->budget = s->budget;
     out->packs = (int)s->packs.size();

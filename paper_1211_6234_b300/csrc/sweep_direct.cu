@@ -126,16 +126,33 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
     constexpr int V = 3 * n;                    // partial-field values per thread
     constexpr int G = (V + 31) / 32;            // groups of <= 32 values
     constexpr int PV = pow2_at_least(V < 32 ? V : 32);
-    const int L = cfg.L, l = cfg.l, N = L * L, ll = l * l;
     const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5, NW = NT >> 5;
     const int NWF = NW - 1;                     // field warps; warp 0 is the control warp
-    const int ftid = tid - 32, NTF = NT - 32;
+    const int ftid = tid - 32;
     const int r = blockIdx.x;
-    // stream state of this replica: the lattice's own, or its slot's in a packed launch
+    // geometry, buffers and stream state of this replica: the lattice's own, its
+    // slot's in a packed launch, or its descriptor's in a grouped launch
+    const SlotGeom *G0 = buf.geom ? buf.geom + r : nullptr;
+    const int L = G0 ? G0->L : cfg.L, l = G0 ? G0->l : cfg.l, N = L * L, ll = l * l;
+    const int NTF = G0 ? G0->nft : NT - 32;     // field threads whose cell offsets this CTA sums
+    const int NTO = G0 ? G0->nt : NT;           // threads of the observable sums
+    const float *__restrict__ W32 = G0 ? G0->W32 : buf.W32;
+    float *spins_r = G0 ? G0->spins : buf.spins + (size_t)r * 3 * N;
+    const RepParams *par_r = G0 ? G0->params : buf.params + r;
+    double *energy_r = G0 ? G0->energy : (buf.energy ? buf.energy + r : nullptr);
+    ObsAcc *obs_r = G0 ? G0->obs : (buf.obs ? buf.obs + r : nullptr);
+    double *theta2_r = G0 ? G0->theta2 : (buf.theta2 ? buf.theta2 + (size_t)r * N : nullptr);
     uint2 key = cfg.key;
     uint32_t t0 = cfg.t0, rid = (uint32_t)r, mphase = 0;
     int nsw = cfg.nsweeps;
-    if (buf.slots) {
+    if (G0) {
+        key = make_uint2(G0->key_lo, G0->key_hi);
+        t0 = G0->t0;
+        mphase = G0->mphase;
+        rid = G0->rid;
+        nsw = min(nsw, G0->nsweeps);
+        if (nsw <= 0) return;
+    } else if (buf.slots) {
         const SlotState sl = buf.slots[r];
         key = make_uint2(sl.key_lo, sl.key_hi);
         t0 = sl.t0;
@@ -163,22 +180,22 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
     __shared__ float c_W0[4];
 
     // ---- load state: global SoA -> shared AoS
-    const float *gs = buf.spins + (size_t)r * 3 * N;
+    const float *gs = spins_r;
     for (int i = tid; i < N; i += NT) s4[i] = make_float4(gs[i], gs[N + i], gs[2 * N + i], 0.0f);
     const bool measuring = cfg.measure_every > 0;
     // per-site sum of (theta - pi/2)^2, added in FP64 at every measured sweep so
     // that the result does not depend on how the sweeps are split into launches
-    double *gt = buf.theta2 ? buf.theta2 + (size_t)r * N : nullptr;
+    double *gt = theta2_r;
     if (tid < 4 * n) {
         const int D = tid >> 2, c = tid & 3;
-        wl[tid] = buf.W32[c * N + (l * (D / C)) * L + l * (D % C)];
+        wl[tid] = W32[c * N + (l * (D / C)) * L + l * (D % C)];
     }
     if (tid == 0) {
-        if (buf.obs) acc_s = buf.obs[r];
-        e_track_s = buf.energy ? buf.energy[r] : 0.0;
-        c_P = buf.params[r];
+        if (obs_r) acc_s = *obs_r;
+        e_track_s = energy_r ? *energy_r : 0.0;
+        c_P = *par_r;
     }
-    if (tid < 4) c_W0[tid] = buf.W32[tid * N];
+    if (tid < 4) c_W0[tid] = W32[tid * N];
     if (tid < 32) {
         c_epart[tid] = 0.0;
         b_d[0][tid] = b_d[1][tid] = b_d[2][tid] = b_E[tid] = 0.0f;
@@ -190,7 +207,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
 #pragma unroll
     for (int j = 0; j < EPT; ++j) {
         const int e = ftid + j * NTF;
-        const bool valid = warp > 0 && e < ll;
+        const bool valid = warp > 0 && ftid < NTF && e < ll;
         ex[j] = valid ? e % l : 0;
         ey[j] = valid ? e / l : 0;
 #pragma unroll
@@ -201,7 +218,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
             if (ry < 0) ry += L;
             const int idx = ry * L + rx;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) w[j][D][c] = valid ? buf.W32[c * N + idx] : 0.0f;
+            for (int c = 0; c < 4; ++c) w[j][D][c] = valid ? W32[c * N + idx] : 0.0f;
         }
     }
 
@@ -425,7 +442,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
         // ---- observables of this sweep
         if (measuring && ((mphase + (uint32_t)it + 1u) % (uint32_t)cfg.measure_every) == 0) {
             float mv_[12] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            for (int i = tid; i < N; i += NT) {
+            for (int i = tid; tid < NTO && i < N; i += NTO) {
                 const float4 a = s4[i];
                 const int iy = i / L, ix = i - iy * L;
                 const float4 ax = s4[iy * L + (ix + 1 == L ? 0 : ix + 1)], ay = s4[(iy + 1 == L ? 0 : iy + 1) * L + ix];
@@ -466,8 +483,8 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
                     x[MC_OBS_E] = e_track_s / N;
                     x[MC_OBS_MST] = sqrt(Mh * Mh + Mv * Mv);
                     stripe_obs(x, nh, nv, sm[11], N);
-                    if (buf.obs) obs_push(acc_s, x);
-                    hist_push(buf.hist, r, x[MC_OBS_E]);
+                    if (obs_r) obs_push(acc_s, x);
+                    if (!G0) hist_push(buf.hist, r, x[MC_OBS_E]);
                 }
             }
             __syncthreads();
@@ -475,7 +492,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
     }
 
     // ---- write back
-    float *gd = buf.spins + (size_t)r * 3 * N;
+    float *gd = spins_r;
     for (int i = tid; i < N; i += NT) {
         const float4 a = s4[i];
         gd[i] = a.x;
@@ -484,11 +501,11 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
     }
     if (warp == 0) {
         if (lane == 0) {
-            if (buf.energy) buf.energy[r] = e_track_s;
-            if (buf.obs) {
+            if (energy_r) *energy_r = e_track_s;
+            if (obs_r) {
                 acc_s.accepted += n_acc;
                 acc_s.attempted += (long long)nsw * N;
-                buf.obs[r] = acc_s;
+                *obs_r = acc_s;
             }
         }
     }
@@ -571,6 +588,48 @@ const Inst *pick(int L, int l, int R, int nsm, int *threads) {
 }
 
 }  // namespace
+
+bool direct_lone_shape(int L, int l, int R, int *threads, int *ept) {
+    int dev = 0, nsm = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const Inst *in = pick(L, l, R, nsm, threads);
+    if (!in) return false;
+    *ept = in->EPT;
+    return true;
+}
+
+size_t direct_smem_bytes(int L, int l, int threads) { return smem_bytes(L, l, threads); }
+
+// The instance of a grouped launch: the fewest cell offsets per thread that cover
+// every slot's lone EPT and thread count (the extra offsets of a thread are empty).
+const Inst *pick_grouped(int C, int max_ept, int threads) {
+    const Inst *best = nullptr;
+    for (const Inst &in : kInst) {
+        if (in.C != C || in.EPT < max_ept || in.MAXT < threads) continue;
+        if (!best || in.EPT < best->EPT || (in.EPT == best->EPT && in.MAXT > best->MAXT)) best = &in;
+    }
+    return best;
+}
+
+int direct_grouped_resident(int C, int max_ept, int threads, size_t smem) {
+    const Inst *in = pick_grouped(C, max_ept, threads);
+    if (!in || smem > 227 * 1024) return 0;
+    int dev = 0, nsm = 148, per_sm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (in->occupancy(threads, smem, &per_sm) != cudaSuccess) return 0;
+    return per_sm * nsm;
+}
+
+cudaError_t launch_sweep_direct_grouped(int C, int max_ept, int threads, size_t smem, const SweepConfig &c,
+                                        const SlotGeom *geom_dev, int count, cudaStream_t st) {
+    const Inst *best = pick_grouped(C, max_ept, threads);
+    if (!best || smem > 227 * 1024) return cudaErrorNotSupported;
+    SweepConfig g = c;
+    g.R = count;
+    SweepBuffers b;
+    b.geom = geom_dev;
+    return best->launch(g, b, threads, smem, st);
+}
 
 bool direct_supported(int L, int l) {
     int th = 0;

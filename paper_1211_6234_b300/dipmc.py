@@ -34,7 +34,7 @@ ABI_SYMBOLS = (
     "mc_get_spins", "mc_get_field", "mc_get_W", "mc_energy", "mc_get_sweep_counter",
     "mc_checkpoint", "mc_restore", "mc_energy_noalloc", "mc_set_timing", "mc_get_timing",
     "mc_choose_spacing", "mc_autotune", "mc_set_histogram", "mc_get_histogram",
-    "mc_precompute_W_ewald", "mc_wtilde_ewald", "mc_set_tuning", "mc_get_tuning",
+    "mc_precompute_W_ewald", "mc_wtilde_ewald", "mc_set_tuning", "mc_get_tuning", "mc_sweep_group",
     "mc_footprint", "mc_server_create", "mc_server_submit", "mc_server_step", "mc_server_poll", "mc_server_request_info",
     "mc_server_collect", "mc_server_get_spins", "mc_server_release", "mc_server_get_stats", "mc_server_destroy",
 )
@@ -94,7 +94,7 @@ class mc_request_info(C.Structure):
 class mc_server_stats(C.Structure):
     _fields_ = [("queued", C.c_int), ("running", C.c_int), ("done", C.c_int), ("failed", C.c_int),
                 ("packs", C.c_int), ("lone", C.c_int), ("completed", C.c_int64),
-                ("bytes_in_use", C.c_size_t), ("budget", C.c_size_t)]
+                ("bytes_in_use", C.c_size_t), ("budget", C.c_size_t), ("grouped_launches", C.c_int64)]
 
 
 class mc_tuning(C.Structure):
@@ -154,6 +154,7 @@ def _load():
         "mc_server_destroy": ([vp], i32),
         "mc_get_timing": ([vp, C.POINTER(mc_timing)], i32),
         "mc_set_tuning": ([vp, C.POINTER(mc_tuning)], i32),
+        "mc_sweep_group": ([C.POINTER(vp), i32, i32, i32, vp], i32),
         "mc_get_tuning": ([vp, C.POINTER(mc_tuning)], i32),
     }
     for name, (args, res) in sig.items():
@@ -197,6 +198,13 @@ def energy_noalloc(L: int, R: int, W32, spins, couplings, energy, stream=None):
     _ck(_lib.mc_energy_noalloc(L, R, C.c_void_p(W32.data_ptr()), C.c_void_p(spins.data_ptr()),
                                C.c_void_p(couplings.data_ptr()), C.c_void_p(energy.data_ptr()),
                                _stream_ptr(stream)))
+
+
+def sweep_group(lattices, nsweeps: int, measure_every: int = 0, stream=None):
+    """mc_sweep_group: sweeps of handles of different L (same L / l, direct path)
+    in one persistent launch; each replica's result equals its own mc_sweep."""
+    arr = (C.c_void_p * len(lattices))(*[lat.h.value for lat in lattices])
+    _ck(_lib.mc_sweep_group(arr, len(lattices), nsweeps, measure_every, _stream_ptr(stream)))
 
 
 def choose_spacing(L: int, C_D: float, T_min: float, max_error: float) -> int:

@@ -110,6 +110,29 @@ def test_packed_requests_equal_their_lone_runs(dipmc):
 
 
 @gpu
+def test_mixed_lattice_sizes_share_one_launch(dipmc):
+    """Requests of L = 32, 48, 64 and 96 at l = L / 2 run in the same grouped
+    launches of the direct kernel (uneven L in one persistent launch), and each
+    result still equals its lone run bit for bit."""
+    specs = [dict(L=32, l=16, T=0.7, sweeps=21, seed=31), dict(L=48, l=24, T=0.4, sweeps=13, seed=32, K4=0.1),
+             dict(L=64, l=32, T=0.9, sweeps=17, seed=33, replicas=2), dict(L=96, l=48, T=0.5, sweeps=9, seed=34),
+             dict(L=48, l=24, T=1.1, sweeps=25, seed=35, init_mode=1)]
+    with dipmc.Server(hbm_budget_bytes=4 << 30, quantum_sweeps=4) as srv:
+        ids = [srv.submit(**s) for s in specs]
+        srv.run_until_done(ids, timeout_s=300)
+        st = srv.stats()
+        assert st["grouped_launches"] > 0
+        for rid, s in zip(ids, specs):
+            info = srv.info(rid)
+            assert info["state"] == dipmc.MC_REQ_DONE and info["packed"], info
+            assert info["path"] == dipmc.MC_PATH_DIRECT
+            spins_lone, obs_lone = lone_run(dipmc, path=dipmc.MC_PATH_DIRECT, **s)
+            np.testing.assert_array_equal(srv.spins(rid), spins_lone)
+            for r in range(s.get("replicas", 1)):
+                same_obs(srv.collect(rid, r), obs_lone[r])
+
+
+@gpu
 def test_lone_handle_requests_equal_their_lone_runs(dipmc):
     """Requests with more replicas than a pack holds run on pooled lone handles
     (tensor path at L = 64, spectral path at L = 256) beside a pack and match their
