@@ -77,6 +77,8 @@ extern "C" {
 #define MC_PATH_FFT 4         /* full field per sub-step by 2D FFT convolution (L a power of two) */
 #define MC_PATH_SPECTRAL 5    /* field at the sub-step's sites from sub-lattice spectra (L/l <= 32) */
 #define MC_PATH_INCREMENTAL 6 /* field kept at every site, rank-n update per sub-step (L <= 64, (L/l)^2 <= 64) */
+#define MC_PATH_FFT_CLUSTER 7 /* 2D transform of each replica held in a 16-CTA cluster's shared memory (L a power
+                                 of two, 16 <= L <= 256, L/l a power of two <= 16) */
 
 typedef struct mc_lattice mc_lattice;
 
@@ -149,10 +151,17 @@ int mc_set_schedule(mc_lattice *lat, int kind);
  * measured sweep.  MC_PATH_INCREMENTAL keeps the field at every site in shared
  * memory and adds W~ * delta of the accepted moves after each sub-step, so the
  * energy of a measured sweep is an O(L^2) sum over the kept field; the field is
- * re-evaluated from scratch every 8 sweeps.  MC_PATH_AUTO order: tensor (where its
+ * re-evaluated from scratch every 8 sweeps.  MC_PATH_FFT_CLUSTER runs each
+ * replica in a cluster of 16 CTAs that keeps the replica's 2D Fourier transform
+ * (S^, and W^, the transform of W~) in shared memory, each CTA a sixteenth of the
+ * wave vectors and of the rows: the field at a sub-step's n sites is a partial
+ * inverse transform (h = W~ * s is a convolution, Sec. 2.1, Eq. 2), the accepted
+ * moves update S^ exactly, and S^ is taken afresh by a 2D DFT before every sweep;
+ * the energy is measured afresh at measured sweeps.  It is meant for one or a
+ * few large lattices.  MC_PATH_AUTO order: tensor (where its
  * window fits: L % 8 == 0, L/l in {1, 2, 4}, the spins of a replica in shared
  * memory, i.e. L up to about 100), direct, spectral, FFT, windowed FP32 (the
- * incremental path is chosen explicitly or by mc_autotune). */
+ * incremental and cluster paths are chosen explicitly or by mc_autotune). */
 int mc_set_field_path(mc_lattice *lat, int path);
 
 /* Sub-steps per window of the windowed paths (must divide l^2; 0 = automatic). */

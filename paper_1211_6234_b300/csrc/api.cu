@@ -10,6 +10,7 @@
 #include <tuple>
 #include <vector>
 
+#include "fft_cluster.cuh"
 #include "fft_field.cuh"
 #include "incremental.cuh"
 #include "internal.cuh"
@@ -96,6 +97,10 @@ struct mc_lattice {
     float *What = nullptr;    // [4][N] transform of W~ (FFT path), transposed layout
     float2 *fft_scratch = nullptr;
     bool what_ready = false;
+    // cluster-resident transform path: W^ on the half plane, the spins' transform and row scratch
+    float *cl_What = nullptr;
+    float2 *cl_S = nullptr, *cl_rows = nullptr;
+    bool cl_ready = false;
     // sub-lattice spectral path
     float2 *specT = nullptr, *specS = nullptr, *specH = nullptr;
     int *specOff = nullptr;
@@ -157,6 +162,9 @@ void free_all(mc_lattice *p) {
     cudaFree(p->wq);
     cudaFree(p->What);
     cudaFree(p->fft_scratch);
+    cudaFree(p->cl_What);
+    cudaFree(p->cl_S);
+    cudaFree(p->cl_rows);
     cudaFree(p->t_dev);
     for (auto &g : p->graphs) cudaGraphExecDestroy(g.second);
     p->graphs.clear();
@@ -239,6 +247,7 @@ bool path_supported(const mc_lattice *p, int path) {
         case MC_PATH_FFT: return fft_supported(p->L);
         case MC_PATH_SPECTRAL: return spectral_supported(p->L, p->l);
         case MC_PATH_INCREMENTAL: return incremental_supported(p->L, p->l);
+        case MC_PATH_FFT_CLUSTER: return cluster_supported(p->L, p->l);
         default: return false;
     }
 }
@@ -553,6 +562,67 @@ int run_fft(mc_lattice *p, int nsweeps, int measure_every, float *trace, cudaStr
     return MC_OK;
 }
 
+int ensure_cluster(mc_lattice *p, cudaStream_t st) {
+    const size_t K2 = (size_t)p->L / 2 + 1;
+    if (!p->cl_What) CKA(cudaMalloc(&p->cl_What, sizeof(float) * 4 * K2 * p->L));
+    if (!p->cl_S) {
+        CKA(cudaMalloc(&p->cl_S, sizeof(float2) * (size_t)p->R * 3 * K2 * p->L));
+        CKA(cudaMalloc(&p->cl_rows, sizeof(float2) * (size_t)p->R * 3 * K2 * p->L));
+    }
+    if (!p->cl_ready) {
+        cudaError_t e = launch_cluster_what(p->L, p->W64, p->cl_What, st);
+        if (e != cudaSuccess) return cuda_fail(e, "half-plane transform of W~");
+        p->cl_ready = true;
+    }
+    return MC_OK;
+}
+
+// Cluster-resident transform path: per sweep, the 2D DFT of the spins, then one
+// cluster launch for the sweep's l^2 sub-steps; the energy and observables of a
+// measured sweep from a full field, as on the FFT path.
+int run_cluster(mc_lattice *p, int nsweeps, int measure_every, float *trace, cudaStream_t st) {
+    int rc = ensure_cluster(p, st);
+    if (rc) return rc;
+    ClusterSweepArgs a{};
+    a.L = p->L; a.l = p->l; a.R = p->R;
+    a.key = key_of(p->seed);
+    a.t_dev = p->t_dev;
+    a.nsweeps_call = nsweeps;
+    a.proposal = p->proposal;
+    a.cap_c1 = (float)(1.0 - std::cos(p->cone));
+    a.schedule = p->schedule;
+    a.What = p->cl_What; a.Shat = p->cl_S; a.spins = p->spins; a.W32 = p->W32;
+    a.params = p->dparams; a.obs = p->obs; a.trace = trace;
+    bool measured_last = false;
+    for (int it = 0; it < nsweeps; ++it) {
+        a.t = (uint32_t)(p->t + (uint64_t)it);
+        a.it = it;
+        cudaError_t e;
+        {
+            TimedLaunch tl(p, MC_K_FULL_FIELD, st);
+            e = launch_cluster_transform(p->L, p->R, p->spins, p->cl_rows, p->cl_S, st);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "transform of the spins");
+        {
+            TimedLaunch tl(p, MC_K_SPEC_UPDATE, st);
+            e = launch_cluster_sweep(a, st);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cluster sweep launch");
+        measured_last = measure_every > 0 && ((it + 1) % measure_every) == 0;
+        if (measured_last) {
+            rc = full_field(p, st);
+            if (rc) return rc;
+            e = launch_fft_observe(p->L, p->R, p->spins, p->field, p->dparams, p->energy, p->obs, p->theta2, nullptr,
+                                   it, measure_every, hist_of(p), st);
+            if (e != cudaSuccess) return cuda_fail(e, "observables");
+        }
+    }
+    cudaError_t e = launch_add_attempted(p->obs, p->R, (long long)nsweeps * p->N(), nullptr, nsweeps, p->N(), st);
+    if (e != cudaSuccess) return cuda_fail(e, "acceptance counters");
+    p->energy_valid = measured_last;
+    return MC_OK;
+}
+
 int ensure_spectral(mc_lattice *p, cudaStream_t st) {
     // the kernels divide (replica, K) indices below R n by n with a multiply-high
     if ((unsigned long long)p->R * p->n() * p->n() >= (1ull << 32))
@@ -683,6 +753,7 @@ int run_incremental(mc_lattice *p, int nsweeps, int measure_every, float *trace,
 
 int run_path(mc_lattice *p, int path, int nsweeps, int measure_every, float *trace, cudaStream_t st) {
     if (path == MC_PATH_FFT) return run_fft(p, nsweeps, measure_every, trace, st);
+    if (path == MC_PATH_FFT_CLUSTER) return run_cluster(p, nsweeps, measure_every, trace, st);
     if (path == MC_PATH_SPECTRAL) return run_spectral(p, nsweeps, measure_every, trace, st);
     return run_windows(p, path, nsweeps, measure_every, trace, st);
 }
@@ -709,8 +780,12 @@ int run_multi(mc_lattice *p, int path, int nsweeps, int measure_every, float *tr
     auto it = p->graphs.find(key);
     if (it == p->graphs.end()) {
         // buffers and tables are made outside the capture
-        if (path == MC_PATH_FFT || (path == MC_PATH_SPECTRAL && use_fft_full_field(p))) {
+        if (path == MC_PATH_FFT || ((path == MC_PATH_SPECTRAL || path == MC_PATH_FFT_CLUSTER) && use_fft_full_field(p))) {
             int rc = ensure_fft(p, st);
+            if (rc) return rc;
+        }
+        if (path == MC_PATH_FFT_CLUSTER) {
+            int rc = ensure_cluster(p, st);
             if (rc) return rc;
         }
         if (path == MC_PATH_SPECTRAL) {
@@ -738,7 +813,7 @@ int run_multi(mc_lattice *p, int path, int nsweeps, int measure_every, float *tr
     CKA(cudaGraphLaunch(it->second, p->own));
     CKA(cudaEventRecord(p->ev_out, p->own));
     CKA(cudaStreamWaitEvent(st, p->ev_out, 0));
-    if (path == MC_PATH_FFT || path == MC_PATH_SPECTRAL)
+    if (path == MC_PATH_FFT || path == MC_PATH_SPECTRAL || path == MC_PATH_FFT_CLUSTER)
         p->energy_valid = p->packed || (measure_every > 0 && nsweeps % measure_every == 0);
     return MC_OK;
 }
@@ -749,7 +824,8 @@ int run_sweeps(mc_lattice *p, int nsweeps, int measure_every, float *trace, cuda
     if (measure_every < 0) return fail(MC_EINVAL, "measure_every must be >= 0");
     if (nsweeps == 0) return MC_OK;
     const int path0 = resolve_path(p);
-    if (!p->energy_valid && path0 != MC_PATH_FFT && path0 != MC_PATH_SPECTRAL && path0 != MC_PATH_INCREMENTAL) {
+    if (!p->energy_valid && path0 != MC_PATH_FFT && path0 != MC_PATH_SPECTRAL && path0 != MC_PATH_INCREMENTAL &&
+        path0 != MC_PATH_FFT_CLUSTER) {
         int rc = anchor_energy(p, st);
         if (rc) return rc;
     }
@@ -1026,7 +1102,7 @@ int mc_set_field_path(mc_lattice *p, int path) {
     if (p) drop_graphs(p);
     int rc = check(p);
     if (rc) return rc;
-    if (path < MC_PATH_AUTO || path > MC_PATH_INCREMENTAL) return fail(MC_EINVAL, "unknown field path %d", path);
+    if (path < MC_PATH_AUTO || path > MC_PATH_FFT_CLUSTER) return fail(MC_EINVAL, "unknown field path %d", path);
     if (path != MC_PATH_AUTO && !path_supported(p, path))
         return fail(MC_ENOSYS, "field path %d does not support L=%d l=%d", path, p->L, p->l);
     p->path = path;
@@ -1105,6 +1181,7 @@ int mc_precompute_W(mc_lattice *p, int A, int tail) {
     p->W_ready = true;
     p->wsh_ready = false;
     p->what_ready = false;
+    p->cl_ready = false;
     p->spec_ready = false;
     p->energy_valid = false;
     return MC_OK;
@@ -1131,6 +1208,7 @@ int mc_precompute_W_ewald(mc_lattice *p, double eta) {
     p->W_ready = true;
     p->wsh_ready = false;
     p->what_ready = false;
+    p->cl_ready = false;
     p->spec_ready = false;
     p->energy_valid = false;
     return MC_OK;
@@ -1429,6 +1507,7 @@ int mc_autotune(mc_lattice *p, int nsweeps_trial, void *stream, int *path_out, i
     if (path_supported(p, MC_PATH_FFT)) cands.push_back({MC_PATH_FFT, 0});
     if (path_supported(p, MC_PATH_SPECTRAL)) cands.push_back({MC_PATH_SPECTRAL, 0});
     if (path_supported(p, MC_PATH_INCREMENTAL)) cands.push_back({MC_PATH_INCREMENTAL, 0});
+    if (path_supported(p, MC_PATH_FFT_CLUSTER)) cands.push_back({MC_PATH_FFT_CLUSTER, 0});
     if (cands.empty()) return fail(MC_ENOSYS, "no field path supports L=%d l=%d", p->L, p->l);
     cudaEvent_t a, b;
     CK(cudaEventCreate(&a));
@@ -1604,6 +1683,7 @@ int lattice_copy_W(mc_lattice *p, const double *W64_dev, int A, int tail) {
     p->W_ready = true;
     p->wsh_ready = false;
     p->what_ready = false;
+    p->cl_ready = false;
     p->spec_ready = false;
     p->energy_valid = false;
     return MC_OK;

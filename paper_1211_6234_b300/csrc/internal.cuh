@@ -116,6 +116,42 @@ cudaError_t launch_pdl(void (*k)(Exp...), dim3 grid, int threads, size_t smem, c
     return cudaLaunchKernelEx(&cfg, k, args...);
 }
 
+// Orthonormal pair perpendicular to a unit vector n (Duff, Burgess, Christensen,
+// Hery, Kensler, Liani, Villemin, "Building an orthonormal basis, revisited",
+// JCGT 2017), continuous except across n_z = 0.
+__device__ __forceinline__ void perp_basis_unit(float nx, float ny, float nz, float3 &b1, float3 &b2) {
+    const float sign = copysignf(1.0f, nz);
+    const float a = -1.0f / (sign + nz);
+    const float b = nx * ny * a;
+    b1 = make_float3(1.0f + sign * nx * nx * a, sign * b, -sign * nx);
+    b2 = make_float3(b, sign + ny * ny * a, -ny);
+}
+
+// Proposal S for the current spin s (Sec. 3.1 proposal): kind 2 the complete
+// reversal of Appendix B, kind 1 uniform on S^2 (z = 2 u1 - 1, azimuth from
+// cps, sps), otherwise uniform on the cap of half-angle cone around s with
+// 1 - cos(alpha) = u1 (1 - cos cone) = u1 cap_c1 (formed without cancellation),
+// renormalised.
+__device__ __forceinline__ float3 propose_spin(int kind, float cap_c1, float s0, float s1, float s2, float u1,
+                                               float cps, float sps) {
+    if (kind == kPropFlip) return make_float3(-s0, -s1, -s2);
+    if (kind == kPropSphere) {
+        const float z = 2.0f * u1 - 1.0f;
+        const float rr = sqrtf(fmaxf(0.0f, (1.0f - z) * (1.0f + z)));
+        return make_float3(rr * cps, rr * sps, z);
+    }
+    const float omc = u1 * cap_c1;
+    const float ca = 1.0f - omc;
+    const float sa = sqrtf(fmaxf(0.0f, omc * (2.0f - omc)));
+    float3 b1, b2;
+    perp_basis_unit(s0, s1, s2, b1, b2);
+    float S0 = ca * s0 + sa * (cps * b1.x + sps * b2.x);
+    float S1 = ca * s1 + sa * (cps * b1.y + sps * b2.y);
+    float S2 = ca * s2 + sa * (cps * b1.z + sps * b2.z);
+    const float inv = 1.0f / sqrtf(S0 * S0 + S1 * S1 + S2 * S2);
+    return make_float3(S0 * inv, S1 * inv, S2 * inv);
+}
+
 // Per-replica couplings as the kernels read them.
 struct RepParams {
     float J, CD, K2, K4, T;

@@ -20,7 +20,7 @@ MC_OK, MC_EINVAL, MC_ENOMEM, MC_ENOTREADY, MC_ETIMEOUT, MC_ECUDA, MC_ENOSYS = 0,
 MC_NOBS = 11
 OBS_NAMES = ("abs_m", "m_z", "abs_m_z", "m_par", "e", "m_st", "wall", "o_x", "o_y", "o_z", "cone")
 (MC_PATH_AUTO, MC_PATH_DIRECT, MC_PATH_WINDOW_F32, MC_PATH_TENSOR, MC_PATH_FFT, MC_PATH_SPECTRAL,
- MC_PATH_INCREMENTAL) = 0, 1, 2, 3, 4, 5, 6
+ MC_PATH_INCREMENTAL, MC_PATH_FFT_CLUSTER) = 0, 1, 2, 3, 4, 5, 6, 7
 MC_TRACE_W = 10
 PROPOSAL_CAP, PROPOSAL_SPHERE, PROPOSAL_FLIP = 0, 1, 2
 INIT_RANDOM, INIT_UP, INIT_USER, INIT_ISING = 0, 1, 2, 3

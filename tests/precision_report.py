@@ -25,7 +25,8 @@ from tests.parity_util import F32, compare_trace, resync  # noqa: E402
 
 PATHS = [("direct", dipmc.MC_PATH_DIRECT), ("window_f32", dipmc.MC_PATH_WINDOW_F32),
          ("tensor_bf16x3", dipmc.MC_PATH_TENSOR), ("fft", dipmc.MC_PATH_FFT),
-         ("spectral", dipmc.MC_PATH_SPECTRAL), ("incremental", dipmc.MC_PATH_INCREMENTAL)]
+         ("spectral", dipmc.MC_PATH_SPECTRAL), ("incremental", dipmc.MC_PATH_INCREMENTAL),
+         ("fft_cluster", dipmc.MC_PATH_FFT_CLUSTER)]
 
 
 def traced(path, L=64, l=32, R=2, A=64):

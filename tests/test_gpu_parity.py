@@ -239,7 +239,8 @@ def test_windowed_paths_checkpoint_and_batch_invariance(dipmc, path):
         assert o1["samples"] == o2["samples"] and o1["energy"] == o2["energy"]
 
 
-@pytest.mark.parametrize("path", [1, 2, 3, 4, 5, 6], ids=["direct", "window_f32", "tensor", "fft", "spectral", "incr"])
+@pytest.mark.parametrize("path", [1, 2, 3, 4, 5, 6, 7],
+                         ids=["direct", "window_f32", "tensor", "fft", "spectral", "incr", "cluster"])
 def test_zero_sweeps_change_nothing(dipmc, path):
     """mc_sweep with nsweeps = 0 on every path: the spins, the sweep counter and the
     observables stay as they were."""
@@ -624,8 +625,9 @@ def test_fft_full_field_L256_sampled_sites(dipmc, L):
     assert max(errs) / hmax < 1e-5, (max(errs), hmax)
 
 
-def test_spectral_path_L256_sampled_attempts(dipmc):
-    """L = 256, l = 32 (the large-lattice configuration the spectral path serves):
+@pytest.mark.parametrize("path", [5, 7], ids=["spectral", "cluster"])
+def test_spectral_path_L256_sampled_attempts(dipmc, path):
+    """L = 256, l = 32 (the large-lattice configuration the spectral and cluster paths serve):
     one traced sweep of two replicas.  Every decision is consistent with its own dE
     and u; the state is replayed attempt by attempt from the trace, and at sampled
     sub-steps the recorded field and dE are compared with a direct sum over the
@@ -636,7 +638,7 @@ def test_spectral_path_L256_sampled_attempts(dipmc):
     s0 = inputs.random_spins(L, R, seed=913)
     with dipmc.Lattice(L, l, R, 17) as lat:
         lat.precompute_W(A, True)
-        lat.set_field_path(dipmc.MC_PATH_SPECTRAL)
+        lat.set_field_path(path)
         for r in range(R):
             lat.set_params(*prm[r], replica=r)
         lat.init_spins(2, s0)
@@ -699,10 +701,16 @@ FCASES = [
     (6, 32, 4, 2, 1, 1),      # 64 sites per sub-step, with-replacement schedule
     (6, 48, 24, 1, 0, 1),     # L not a power of two
     (6, 64, 32, 1, 0, 1),     # the paper's L and l
+    (7, 16, 8, 2, 0, 2),      # cluster transform: 2 x 2 sites, two replicas (two clusters)
+    (7, 16, 16, 1, 0, 1),     # l = L: one site per sub-step (exact sequential)
+    (7, 16, 2, 1, 0, 1),      # 8 x 8 sites, one row per CTA
+    (7, 32, 8, 2, 1, 1),      # 4 x 4 sites, with-replacement schedule
+    (7, 64, 32, 1, 0, 1),     # the paper's L and l
+    (7, 128, 16, 1, 0, 1),    # 8 x 8 sites of a large lattice
 ]
 
 
-@pytest.mark.parametrize("case", FCASES, ids=[f"{ {4: 'fft', 5: 'spec', 6: 'incr'}[c[0]]}_L{c[1]}_l{c[2]}_R{c[3]}_s{c[4]}"
+@pytest.mark.parametrize("case", FCASES, ids=[f"{ {4: 'fft', 5: 'spec', 6: 'incr', 7: 'clus'}[c[0]]}_L{c[1]}_l{c[2]}_R{c[3]}_s{c[4]}"
                                               for c in FCASES])
 def test_fft_path_trace_matches_oracle(dipmc, case):
     """FFT (full-lattice transform per sub-step) and spectral (sub-lattice
@@ -734,7 +742,7 @@ def test_fft_path_trace_matches_oracle(dipmc, case):
             np.testing.assert_allclose(sg[r], o["s"], rtol=0, atol=1e-5)
 
 
-@pytest.mark.parametrize("other", [4, 5, 6], ids=["fft", "spectral", "incremental"])
+@pytest.mark.parametrize("other", [4, 5, 6, 7], ids=["fft", "spectral", "incremental", "cluster"])
 def test_fft_path_observables_match_direct(dipmc, other):
     """The FFT and spectral paths sample the same law as the direct path (L = 16,
     pooled replicas)."""
@@ -759,7 +767,7 @@ def test_fft_path_observables_match_direct(dipmc, other):
 
 
 # ---------------------------------------------------------------- graphs and autotuning
-@pytest.mark.parametrize("path", [3, 4, 5], ids=["tensor", "fft", "spectral"])
+@pytest.mark.parametrize("path", [3, 4, 5, 7], ids=["tensor", "fft", "spectral", "cluster"])
 def test_graph_replay_is_bit_identical(dipmc, path):
     """Repeated calls of the windowed / FFT paths replay a captured CUDA graph; three
     calls of 2 sweeps must equal one direct call of 6 sweeps bit for bit."""
@@ -814,8 +822,8 @@ def test_incremental_path_energy_from_the_kept_field(dipmc):
     np.testing.assert_allclose(e_kept, e_full, rtol=0, atol=2e-4 * L * L * 1e-2 + 1e-3)
 
 
-@pytest.mark.parametrize("path", [1, 2, 3, 4, 5, 6],
-                         ids=["direct", "window_f32", "tensor", "fft", "spectral", "incremental"])
+@pytest.mark.parametrize("path", [1, 2, 3, 4, 5, 6, 7],
+                         ids=["direct", "window_f32", "tensor", "fft", "spectral", "incremental", "cluster"])
 def test_observables_on_identical_trajectories(dipmc, path):
     """Every path measures the observables in its own kernel: on a seeded run whose
     final state equals the oracle's (no straddled decision), the per-sweep means of
