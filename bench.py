@@ -355,11 +355,14 @@ def large_lattice_leg(dipmc, stream, sweeps=8):
     """L = 256, 16 replicas at T in [0.3, 0.9], C_D in {0.05, 0.1, 0.2}: the
     spacing l that the Sec. 3.2 error bound 1e-3 allows at T = 0.3, then each
     field path that serves (L, l) timed on `sweeps` sweeps (observables every
-    sweep), and the path the autotuner picks."""
+    sweep), and the path the autotuner picks.  Then one replica: the full-plane
+    FFT convolution per sub-step, the sub-lattice spectral path and the
+    cluster-resident transform path."""
     import torch
     Lb, Rb = 256, 16
     Ts = np.linspace(0.3, 0.9, Rb)
-    names = {dipmc.MC_PATH_FFT: "fft", dipmc.MC_PATH_SPECTRAL: "spectral", dipmc.MC_PATH_DIRECT: "direct"}
+    names = {dipmc.MC_PATH_FFT: "fft", dipmc.MC_PATH_SPECTRAL: "spectral", dipmc.MC_PATH_DIRECT: "direct",
+             dipmc.MC_PATH_FFT_CLUSTER: "fft_cluster"}
     out = []
     for cd in (0.05, 0.1, 0.2):
         lb = dipmc.choose_spacing(Lb, cd, 0.3, 1e-3)
@@ -397,7 +400,8 @@ def large_lattice_leg(dipmc, stream, sweeps=8):
     lat.precompute_W(A_IMG, True)
     lat.set_params(J, 0.1, K2, 0.0, f32(0.3))
     lat.init_spins(0)
-    for path, nm in ((dipmc.MC_PATH_FFT, "fft"), (dipmc.MC_PATH_SPECTRAL, "spectral")):
+    for path, nm in ((dipmc.MC_PATH_FFT, "fft"), (dipmc.MC_PATH_SPECTRAL, "spectral"),
+                     (dipmc.MC_PATH_FFT_CLUSTER, "fft_cluster")):
         try:
             lat.set_field_path(path)
             lat.sweep(1, 1, stream)
@@ -608,6 +612,7 @@ def main():
         flush.fill_(float(i))
         lat.sweep(S, 1, stream)
     kt = lat.timing()
+    wcyc = lat.window_cycles() if args.path != "direct" else None
     lat.set_timing(False)
     kernels = {k: {"launches": v["launches"], "ms_total": v["ms"],
                    "ms_per_launch": v["ms"] / v["launches"] if v["launches"] else None}
@@ -651,6 +656,15 @@ def main():
             rl[k] = {"bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk,
                      "note": "sequential sub-steps: latency-bound, not bandwidth-bound",
                      "peak_basis": "measured copy bandwidth (of measured)"}
+            if wcyc and wcyc["per_block"] > 0:
+                # the bound that governs it: SM cycles per 16-site decision block (live, on the
+                # kernel's own clock counters) against the block of the decider warp alone,
+                # ~1,000 cycles, measured once with the helper warps' work removed
+                floor = 1000.0
+                rl[k]["latency"] = {"cycles_per_block": wcyc["per_block"], "decider_alone_cycles": floor,
+                                    "ratio": wcyc["per_block"] / floor, "setup_cycles": wcyc["setup"],
+                                    "tail_cycles": wcyc["tail"], "blocks_per_launch": wcyc["blocks_per_launch"],
+                                    "sites_per_block": 16}
         elif k == "full_field":
             fl = flops_per_update * R * L * L
             ach = fl / sec / 1e12

@@ -288,6 +288,13 @@ int mc_set_timing(mc_lattice *lat, int enable);
 /* Accumulated kernel times since the last mc_set_timing (synchronises the device). */
 int mc_get_timing(mc_lattice *lat, mc_timing *out);
 
+/* SM clock cycles of the windowed paths' sub-step kernel while timing was enabled,
+ * averaged over its CTAs and launches: out[0] per decision block of 16 sites (the
+ * sequential part), out[1] the set-up before the first block, out[2] the tail
+ * after the last block (write-back, spectra, energy, observables), out[3] blocks
+ * per launch.  Zeros when nothing was timed.  Synchronises the device. */
+int mc_get_window_cycles(mc_lattice *lat, double *out);
+
 /*
  * Update spacing for a stated error (Sec. 3.2).  The flip probability of the
  * simultaneous update errs by about eps/T with eps = 2 C_D sum_{v != 0} |l v|^-3

@@ -114,6 +114,7 @@ struct mc_lattice {
     std::map<std::tuple<int, int, int>, int> seen;
     // kernel timing (events recorded around launches while enabled)
     bool timing = false;
+    unsigned long long *wcyc = nullptr;   // [4] sub-step kernel cycle counters while timing
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> tev[MC_NKCLASS];
     // energy histogram of the measured sweeps, [R][hist_bins]
     unsigned long long *hist = nullptr;
@@ -166,6 +167,7 @@ void free_all(mc_lattice *p) {
     cudaFree(p->cl_S);
     cudaFree(p->cl_rows);
     cudaFree(p->t_dev);
+    cudaFree(p->wcyc);
     for (auto &g : p->graphs) cudaGraphExecDestroy(g.second);
     p->graphs.clear();
     if (p->own) cudaStreamDestroy(p->own);
@@ -440,6 +442,7 @@ int run_windows(mc_lattice *p, int path, int nsweeps, int measure_every, float *
     b.tile_first = tensor ? p->tile_first : nullptr;
     b.wq = p->wq;
     b.hist = hist_of(p);
+    b.cycles = p->timing ? p->wcyc : nullptr;
     TcFieldArgs ta{};
     if (tensor) {
         ta.L = p->L; ta.Sw = Sw; ta.R = p->R; ta.NT = p->NT; ta.tmem_cols = p->tmem_cols;
@@ -1448,6 +1451,30 @@ int mc_set_timing(mc_lattice *p, int enable) {
     CK(cudaDeviceSynchronize());
     clear_timing(p);
     p->timing = enable != 0;
+    if (p->timing) {
+        if (!p->wcyc) CK(cudaMalloc(&p->wcyc, 4 * sizeof(unsigned long long)));
+        CK(cudaMemset(p->wcyc, 0, 4 * sizeof(unsigned long long)));
+    }
+    return MC_OK;
+}
+
+int mc_get_window_cycles(mc_lattice *p, double *out) {
+    int rc = check(p);
+    if (rc) return rc;
+    if (!out) return fail(MC_EINVAL, "out is null");
+    unsigned long long c[4] = {0, 0, 0, 0};
+    if (p->wcyc) {
+        CK(cudaDeviceSynchronize());
+        CK(cudaMemcpy(c, p->wcyc, sizeof c, cudaMemcpyDeviceToHost));
+    }
+    // c[3] counts blocks over CTAs and launches; CTA-launches = blocks / blocks per launch
+    const int B = window_of(p, resolve_path(p) == MC_PATH_TENSOR);
+    const double nblk = (p->n() <= 16 && B > 0) ? (double)B / (16.0 / p->n()) : 0.0;   // blocks per launch
+    const double ctal = (c[3] && nblk > 0) ? (double)c[3] / nblk : 0.0;                  // CTA-launches
+    out[0] = c[3] ? (double)c[0] / (double)c[3] : 0.0;
+    out[1] = ctal > 0 ? (double)c[1] / ctal : 0.0;
+    out[2] = ctal > 0 ? (double)c[2] / ctal : 0.0;
+    out[3] = nblk;
     return MC_OK;
 }
 

@@ -261,6 +261,8 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
         return make_float3(h[0], h[1], h[2]);
     };
 
+    const long long cyc0 = clock64();   // the kernel's start on this SM (for buf.cycles)
+    long long cyc1 = 0, cyc2 = 0;
     // ---- window set-up.  Before the previous kernel of the stream has finished:
     // the tensor table and the window's sites (they depend on the sweep counter
     // only); then the state, stale field and proposals.
@@ -375,6 +377,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
 
     long long n_acc = 0;
     const int nblk = B / G;
+    if (tid == 0) cyc1 = clock64();
     // warp roles during the blocks (layout): the decider warp dw, an idle warp or none,
     // and the helpers, numbered hw = 0 .. nh-1
     const int dw = (PRE && cfg.layout == 2 && ((r / cfg.nsm) & 1)) ? 2 : 0;
@@ -669,6 +672,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
         }
     }
 
+    if (tid == 0) cyc2 = clock64();
     // ---- write the accepted moves back to global memory (FP32 and the bf16 split)
     float *gd = buf.spins + (size_t)r * 3 * N;
     for (int s = tid; s < Sw; s += kWThreads) {
@@ -817,6 +821,12 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
     }
     if (warp == dw && lane == 0 && buf.obs)
         atomicAdd(reinterpret_cast<unsigned long long *>(&buf.obs[r].accepted), (unsigned long long)n_acc);
+    if (tid == 0 && buf.cycles) {
+        atomicAdd(buf.cycles + 0, (unsigned long long)(cyc2 - cyc1));
+        atomicAdd(buf.cycles + 1, (unsigned long long)(cyc1 - cyc0));
+        atomicAdd(buf.cycles + 2, (unsigned long long)(clock64() - cyc2));
+        atomicAdd(buf.cycles + 3, (unsigned long long)nblk);
+    }
     if (tid == 0 && buf.obs)
         atomicAdd(reinterpret_cast<unsigned long long *>(&buf.obs[r].attempted), (unsigned long long)Sw);
 }

@@ -47,6 +47,8 @@ struct WindowBuffers {
     const int *tile_first;        // stale_mode 2: [ntiles * mtiles + 1] first unit of tile (nt, mt)
     const float4 *wq;             // [(L/2+1)^2] W~ on the minimum-image quarter, (xx, xy, yy, zz)
     EnergyHist hist;              // optional energy histogram
+    unsigned long long *cycles;   // optional [4]: SM clock cycles summed over CTAs of the blocks, the
+                                  // set-up before them and the tail after them, and the blocks run
 };
 
 size_t window_smem_bytes(int L, int Sw, int n);

@@ -35,6 +35,7 @@ ABI_SYMBOLS = (
     "mc_checkpoint", "mc_restore", "mc_energy_noalloc", "mc_set_timing", "mc_get_timing",
     "mc_choose_spacing", "mc_autotune", "mc_set_histogram", "mc_get_histogram",
     "mc_precompute_W_ewald", "mc_wtilde_ewald", "mc_set_tuning", "mc_get_tuning", "mc_sweep_group",
+    "mc_get_window_cycles",
     "mc_footprint", "mc_server_create", "mc_server_submit", "mc_server_step", "mc_server_poll", "mc_server_request_info",
     "mc_server_collect", "mc_server_get_spins", "mc_server_release", "mc_server_get_stats", "mc_server_destroy",
 )
@@ -155,6 +156,7 @@ def _load():
         "mc_get_timing": ([vp, C.POINTER(mc_timing)], i32),
         "mc_set_tuning": ([vp, C.POINTER(mc_tuning)], i32),
         "mc_sweep_group": ([C.POINTER(vp), i32, i32, i32, vp], i32),
+        "mc_get_window_cycles": ([vp, C.POINTER(f64)], i32),
         "mc_get_tuning": ([vp, C.POINTER(mc_tuning)], i32),
     }
     for name, (args, res) in sig.items():
@@ -385,6 +387,12 @@ class Lattice:
         _ck(_lib.mc_get_timing(self.h, C.byref(t)))
         return {nm: {"launches": t.launches[i], "ms": t.ms[i]} for i, nm in enumerate(KERNEL_CLASSES)}
 
+    def window_cycles(self) -> dict:
+        """mc_get_window_cycles: SM cycles per 16-site decision block, set-up and tail
+        of the sub-step kernel, averaged over its CTAs and launches while timing."""
+        out = (C.c_double * 4)()
+        _ck(_lib.mc_get_window_cycles(self.h, out))
+        return {"per_block": out[0], "setup": out[1], "tail": out[2], "blocks_per_launch": out[3]}
     def autotune(self, nsweeps_trial=2, stream=None):
         """Time the supported paths on a copy of the state; keep the fastest.
         Returns (path, window)."""
