@@ -724,9 +724,14 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
         float e_f = 0.0f;   // a few terms per thread
         for (int s = tid; s < Sw; s += kWThreads)
             if (wxy[s] < 0) e_f += pS[s].w;
-        for (int task = tid; task < B * n * n; task += kWThreads) {
-            const int j = task / (n * n), rem = task - j * n * n, d = rem / n, dp = rem - d * n;
-            if (dp >= d) continue;
+        constexpr int npair = n * (n - 1) / 2;   // site pairs d > dp of a sub-step
+        for (int task = tid; task < B * npair; task += kWThreads) {
+            const int j = task / npair;
+            int d = 1, dp = task - j * npair;
+            while (dp >= d) {
+                dp -= d;
+                ++d;
+            }
             const int xy = wxy[j * n + d], pxy = wxy[j * n + dp];
             if (xy >= 0 || pxy >= 0) continue;
             const float4 m = pd[j * n + d], mp = pd[j * n + dp];
