@@ -69,6 +69,22 @@ def approx_error(T):
     return 2 * CD * 9.033621683 / (l**3 * T)
 
 
+def max_over_ranks(t: float, ws: int, device: str) -> float:
+    """The job's time: the largest of the ranks' times (every rank calls this)."""
+    if ws <= 1:
+        return t
+    import torch
+    tt = torch.tensor([t], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_throughput(ws: int, updates_per_rank: int, t_job: float) -> float:
+    """Whole-job site-updates/s: every rank's independent batch (weak scaling), over
+    the slowest rank's time."""
+    return ws * updates_per_rank / t_job
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -598,12 +614,8 @@ def main():
     clk = clocks.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     t_dev = sum(step_ms) / 1e3
-    if ws > 1:
-        tt = torch.tensor([t_dev], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_dev = float(tt.item())
-    updates = ws * R * L * L * S * args.steps
-    value = updates / t_dev
+    t_dev = max_over_ranks(t_dev, ws, "cuda")
+    value = job_throughput(ws, R * L * L * S * args.steps, t_dev)
 
     # per-kernel device times (CUDA events recorded by the library around each
     # launch on this stream), from a separate pass of 2 steps after the timed ones
