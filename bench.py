@@ -536,7 +536,9 @@ def main():
     ap.add_argument("--serve-window", type=float, default=60.0,
                     help="seconds of the full-sweep-count serving stream (0 = run it to completion)")
     ap.add_argument("--serve-quantum", type=int, default=32)
-    ap.add_argument("--serve-rate", type=float, default=50.0, help="Poisson arrival rate, requests/s")
+    ap.add_argument("--serve-rate", type=float, default=500.0,
+                    help="Poisson arrival rate, requests/s (the whole stream arrives in about 4 s, so the "
+                         "window measures a saturated server)")
     ap.add_argument("--serve-scaled", type=float, default=0.002,
                     help="sweep factor of the second, complete serving stream (0 = skip it)")
     ap.add_argument("--no-cooling", action="store_true", help="skip the L=64 cooling scan")

@@ -42,8 +42,10 @@ def _state(lat):
 
 
 @pytest.mark.parametrize("shapes", [((32, 16, 3), (48, 24, 2), (64, 32, 5), (96, 48, 1)),
-                                    ((64, 16, 2), (96, 24, 3), (32, 8, 1))],
-                         ids=["C2_L32_48_64_96", "C4_L64_96_32"])
+                                    ((64, 16, 2), (96, 24, 3), (32, 8, 1)),
+                                    ((16, 16, 2), (32, 32, 1)),
+                                    ((48, 24, 4),)],
+                         ids=["C2_L32_48_64_96", "C4_L64_96_32", "C1_exact_L16_32", "one_handle"])
 def test_group_launch_equals_separate_sweeps(dipmc, shapes):
     grp = [_make(dipmc, L, l, R, 100 + L) for (L, l, R) in shapes]
     sep = [_make(dipmc, L, l, R, 100 + L) for (L, l, R) in shapes]

@@ -520,6 +520,33 @@ def test_tensor_path_ragged_second_tile(dipmc):
     assert worst < 1e-5
 
 
+@pytest.mark.parametrize("R,sample", [(1, (0,)), (520, (0, 255, 256, 511, 512, 519))], ids=["R1", "R520"])
+def test_tensor_path_replica_count_edges(dipmc, R, sample):
+    """The tensor path at its replica-count edges: one replica (an N-tile of 16 with 15
+    empty rows) and 520 replicas (two full N-tiles and a ragged third of 8): sampled
+    replicas of every tile, one traced sweep, against the re-synchronised oracle."""
+    L, l, A = 64, 32, 16
+    lad = [(F32(1.0), F32(0.1), F32(k2), F32(k4), F32(T)) for (T, k2, k4) in inputs.ladder(16, 16)]
+    lad = [lad[(7 * r) % len(lad)] for r in range(R)]
+    s0 = inputs.random_spins(L, R, seed=3 * R)
+    with dipmc.Lattice(L, l, R, 11) as lat:
+        lat.precompute_W(A, True)
+        lat.set_field_path(dipmc.MC_PATH_TENSOR)
+        for r, prm in enumerate(lad):
+            lat.set_params(*prm, replica=r)
+        lat.init_spins(2, s0)
+        tr = lat.sweep_trace(1)
+        sg = lat.get_spins().astype(np.float64)
+    W = oracle_W(L, A)
+    for r in sample:
+        J, CD, K2, K4, T = lad[r]
+        p = orc.params(L, l, J, CD, K2, K4, T, proposal=0, cone=0.5, schedule=0, seed=11, replica=r)
+        o = resync(p, W, s0[r], 0, 1, tr[r])
+        rep = compare_trace(tr[r], o, T, scale=1 + abs(J) + abs(K2) + abs(K4) + abs(CD) * float(np.abs(o["h"]).max()))
+        assert rep.straddles == 0
+        np.testing.assert_allclose(sg[r], o["s"], rtol=0, atol=1e-6)
+
+
 def test_tensor_path_observables_match_direct(dipmc):
     """Long runs of the tensor and direct paths sample the same law: means within
     3 combined standard errors of the replica means (L = 16, 64 independent replicas)."""
