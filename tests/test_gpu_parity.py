@@ -603,6 +603,38 @@ def test_tensor_path_ordered_phase_matches_oracle(dipmc):
     assert a > 0.6     # ordered perpendicular (the disordered limit is 0.4352)
 
 
+def test_tensor_path_bench_lattice_low_T_matches_oracle(dipmc):
+    """The benchmark's lattice on the tensor path in the ordered phase: L = 64, l = 32,
+    T = 0.3 (the low end of the benchmark's temperature ladder), K2 = 0.8, K4 = 0.2 K2,
+    from +z, 100 sweeps then 200 measured, 64 GPU replicas against 16 oracle replicas
+    under the same protocol (so the same law at every sweep, equilibrated or not):
+    |m|, M_par, E/N and eta within 3 combined standard errors of the replica means."""
+    L, l, R_gpu, R_orc, neq, nms = 64, 32, 64, 16, 100, 200
+    prm = (F32(1.0), F32(0.1), F32(0.8), F32(0.16), F32(0.3))
+    with dipmc.Lattice(L, l, R_gpu, 81) as lat:
+        lat.precompute_W(64, True)
+        lat.set_field_path(dipmc.MC_PATH_TENSOR)
+        lat.set_params(*prm)
+        lat.init_spins(1)
+        lat.sweep(neq, 0)
+        lat.reset_observables()
+        lat.sweep(nms, 1)
+        og = lat.observables_batch()
+    W = oracle_W(L, 64)
+    ps = [orc.params(L, l, *prm, proposal=0, cone=0.5, schedule=0, seed=82, replica=r) for r in range(R_orc)]
+    warm = orc.sweeps_batch(ps, W, inputs.saturated_z(L, R_orc), 0, neq, observe=False)["s"]
+    o = orc.sweeps_batch(ps, W, warm, neq, nms, observe=True)
+    for nm, k in {"abs_m": 0, "m_par": 3, "e": 4}.items():
+        a, ea = pooled([g[nm]["mean"] for g in og])
+        b, eb = pooled(o["obs"][:, :, k].mean(axis=1))
+        print(f"L=64 T=0.3 {nm}: tensor {a:.6f} +- {ea:.6f}, oracle {b:.6f} +- {eb:.6f}")
+        assert abs(a - b) <= 3 * math.hypot(ea, eb), (nm, a, b, ea, eb)
+    a, ea = pooled([g["eta"] for g in og])
+    b, eb = pooled([orc.eta(o["theta2"][r], nms) for r in range(R_orc)])
+    print(f"L=64 T=0.3 eta: tensor {a:.6f} +- {ea:.6f}, oracle {b:.6f} +- {eb:.6f}")
+    assert abs(a - b) <= 3 * math.hypot(ea, eb), ("eta", a, b, ea, eb)
+
+
 # ---------------------------------------------------------------- FFT path
 @pytest.mark.parametrize("L,R", [(8, 1), (16, 3), (32, 2), (64, 2), (128, 1)])
 def test_fft_full_field_matches_oracle(dipmc, L, R):
