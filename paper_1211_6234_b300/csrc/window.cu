@@ -394,6 +394,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
         // column e / NB of row e % NB, so a warp's lanes take one column pair.
         auto etab_fill = [&](int nb, int t0, int stride) {
             float *et = reinterpret_cast<float *>(etab + (nb & 1) * (2 * NB / 4) * NB);
+#pragma unroll 2
             for (int e = t0; e < NB * 2 * NB; e += stride) {
                 const int c = e / NB, i = e % NB;
                 const int si = nb * NB + i;
@@ -503,7 +504,24 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
                         const int qx = xy & 0xFFFF, qy = (xy >> 16) & 0x7FFF;
                         const float4 D = pd[s];
                         float e = 0.0f;
-                        for (int m = 0; m < nprev; ++m) {
+                        // four moves at a time: their loads go out together (the sum keeps
+                        // the order m = 0, 1, 2, ...)
+                        int m = 0;
+                        for (; m + 4 <= nprev; m += 4) {
+                            float4 mv[4];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) mv[u] = s_mvb[prv * NB + m + u];
+                            float3 w[4];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const int pxy = __float_as_int(mv[u].w);
+                                w[u] = wq_apply(wq, L, qx - (pxy & 0xFFFF), qy - ((pxy >> 16) & 0x7FFF),
+                                                make_float3(mv[u].x, mv[u].y, mv[u].z));
+                            }
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) e += D.x * w[u].x + D.y * w[u].y + D.z * w[u].z;
+                        }
+                        for (; m < nprev; ++m) {
                             const float4 mv = s_mvb[prv * NB + m];
                             const int pxy = __float_as_int(mv.w);
                             const float3 w = wq_apply(wq, L, qx - (pxy & 0xFFFF), qy - ((pxy >> 16) & 0x7FFF),
