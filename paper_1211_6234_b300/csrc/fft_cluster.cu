@@ -36,6 +36,10 @@
 // of the updates accumulates over one sweep at most.
 #include <cooperative_groups.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "fft_cluster.cuh"
 
 namespace cg = cooperative_groups;
@@ -501,12 +505,7 @@ cudaError_t set_attrs(size_t bytes) {
     return cudaFuncSetAttribute(k_cluster_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-}  // namespace
-
-bool cluster_supported(int L, int l) {
-    if (!cluster_shape_ok(L, l)) return false;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+bool cluster_runs(int L, int l) {
     const CLayout g = clayout(L, l);
     if (set_attrs(g.bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -521,6 +520,29 @@ bool cluster_supported(int L, int l) {
     }
     return nc >= 1;
 }
+
+}  // namespace
+
+bool cluster_supported(int L, int l) {
+    if (!cluster_shape_ok(L, l)) return false;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    // the answer depends on the device and the layout only: cached per (device, L, l)
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int>, bool> known;
+    const auto key = std::make_tuple(dev, L, l);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = known.find(key);
+        if (it != known.end()) return it->second;
+    }
+    const bool ok = cluster_runs(L, l);
+    std::lock_guard<std::mutex> lk(mu);
+    known[key] = ok;
+    return ok;
+}
+
+
 
 size_t cluster_scratch_bytes(int L, int R) {
     const size_t K2 = (size_t)L / 2 + 1;

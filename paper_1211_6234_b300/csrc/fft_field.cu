@@ -371,19 +371,6 @@ __global__ void k_what_pass2(const double2 *__restrict__ T, int L, float *What) 
     What[(size_t)c * N + i] = (float)re;
 }
 
-// ---------------------------------------------------------------------------
-// FFT sweep: the update of one sub-step at all n sites of all replicas, from the
-// full field of the state before the sub-step (in place: update sites are never
-// nearest neighbours for l >= 2).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void perp_basis_f(float nx, float ny, float nz, float3 &b1, float3 &b2) {
-    const float sign = copysignf(1.0f, nz);
-    const float a = -1.0f / (sign + nz);
-    const float b = nx * ny * a;
-    b1 = make_float3(1.0f + sign * nx * nx * a, sign * b, -sign * nx);
-    b2 = make_float3(b, sign + ny * ny * a, -ny);
-}
-
 __global__ void k_fft_update(const FftStepConfig cfg, const FftStepBuffers buf) {
     pdl_trigger();
     pdl_wait();   // the field of the state before the sub-step
@@ -424,29 +411,11 @@ __global__ void k_fft_update(const FftStepConfig cfg, const FftStepBuffers buf) 
         sincospif(2.0f * u24f(wds.y), &sps, &cps);
         const float s0 = s[q], s1 = s[N + q], s2 = s[2 * N + q];
         float S0, S1, S2;
-        if (cfg.proposal == kPropFlip) {            // Appendix B reversal
-            S0 = -s0;
-            S1 = -s1;
-            S2 = -s2;
-        } else if (cfg.proposal == kPropSphere) {
-            const float z = 2.0f * u1 - 1.0f;
-            const float rr = sqrtf(fmaxf(0.0f, (1.0f - z) * (1.0f + z)));
-            S0 = rr * cps;
-            S1 = rr * sps;
-            S2 = z;
-        } else {
-            const float omc = u1 * cfg.cap_c1;             // 1 - cos(alpha), no cancellation
-            const float ca = 1.0f - omc;
-            const float sa = sqrtf(fmaxf(0.0f, omc * (2.0f - omc)));
-            float3 b1, b2;
-            perp_basis_f(s0, s1, s2, b1, b2);
-            S0 = ca * s0 + sa * (cps * b1.x + sps * b2.x);
-            S1 = ca * s1 + sa * (cps * b1.y + sps * b2.y);
-            S2 = ca * s2 + sa * (cps * b1.z + sps * b2.z);
-            const float inv = 1.0f / sqrtf(S0 * S0 + S1 * S1 + S2 * S2);
-            S0 *= inv;
-            S1 *= inv;
-            S2 *= inv;
+        {
+            const float3 Sv = propose_spin(cfg.proposal, cfg.cap_c1, s0, s1, s2, u1, cps, sps);   // Sec. 3.1 proposal
+            S0 = Sv.x;
+            S1 = Sv.y;
+            S2 = Sv.z;
         }
         const float dX = S0 - s0, dY = S1 - s1, dZ = S2 - s2;
         const int xp = (qx + 1 == L) ? q - qx : q + 1;

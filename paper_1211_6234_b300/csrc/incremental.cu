@@ -20,14 +20,6 @@ namespace {
 constexpr int kIThreads = 512;
 constexpr float kPiF = 3.14159265358979f;
 
-__device__ __forceinline__ void basis_duff(float nx, float ny, float nz, float3 &b1, float3 &b2) {
-    const float sign = copysignf(1.0f, nz);
-    const float a = -1.0f / (sign + nz);
-    const float b = nx * ny * a;
-    b1 = make_float3(1.0f + sign * nx * nx * a, sign * b, -sign * nx);
-    b2 = make_float3(b, sign + ny * ny * a, -ny);
-}
-
 // One measurement sample into the binning accumulators (FP64, one thread).
 __device__ void push_sample(ObsAcc &A, const double x[MC_NOBS]) {
     A.nsamples += 1;
@@ -107,29 +99,11 @@ __global__ void __launch_bounds__(kIThreads, 1) k_sweep_incremental(const IncrCo
                 sincospif(2.0f * u24f(wds.y), &sps, &cps);
                 const float4 sq = s4[q];
                 float S0, S1, S2;
-                if (cfg.proposal == kPropFlip) {
-                    S0 = -sq.x;
-                    S1 = -sq.y;
-                    S2 = -sq.z;
-                } else if (cfg.proposal == kPropSphere) {
-                    const float zz = 2.0f * u1 - 1.0f;
-                    const float rr = sqrtf(fmaxf(0.0f, (1.0f - zz) * (1.0f + zz)));
-                    S0 = rr * cps;
-                    S1 = rr * sps;
-                    S2 = zz;
-                } else {
-                    const float omc = u1 * cfg.cap_c1;   // 1 - cos(alpha), no cancellation
-                    const float ca = 1.0f - omc;
-                    const float sa = sqrtf(fmaxf(0.0f, omc * (2.0f - omc)));
-                    float3 b1, b2;
-                    basis_duff(sq.x, sq.y, sq.z, b1, b2);
-                    S0 = ca * sq.x + sa * (cps * b1.x + sps * b2.x);
-                    S1 = ca * sq.y + sa * (cps * b1.y + sps * b2.y);
-                    S2 = ca * sq.z + sa * (cps * b1.z + sps * b2.z);
-                    const float inv = 1.0f / sqrtf(S0 * S0 + S1 * S1 + S2 * S2);
-                    S0 *= inv;
-                    S1 *= inv;
-                    S2 *= inv;
+                {
+                    const float3 Sv = propose_spin(cfg.proposal, cfg.cap_c1, sq.x, sq.y, sq.z, u1, cps, sps);   // Sec. 3.1 proposal
+                    S0 = Sv.x;
+                    S1 = Sv.y;
+                    S2 = Sv.z;
                 }
                 const float dX = S0 - sq.x, dY = S1 - sq.y, dZ = S2 - sq.z;
                 const int xp = (qx + 1 == L) ? q - qx : q + 1;

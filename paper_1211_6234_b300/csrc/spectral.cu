@@ -43,9 +43,6 @@ constexpr int kSpecWinMax = 8;    // sub-steps of a window (k_spec_wfield: one w
 // (here x < 3 n <= 3072, d <= 1024)
 __device__ __forceinline__ int qdiv(int x, uint32_t m) { return (int)__umulhi((uint32_t)x, m); }
 
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
 __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {  // a*b + c
     return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
 }
@@ -110,14 +107,6 @@ __device__ __forceinline__ void sub_offset(const SpecConfig &cfg, uint2 key, uin
     }
     ox = (int)(v % l);
     oy = (int)(v / l);
-}
-
-__device__ __forceinline__ void perp_basis_s(float nx, float ny, float nz, float3 &b1, float3 &b2) {
-    const float sign = copysignf(1.0f, nz);
-    const float a = -1.0f / (sign + nz);
-    const float bb = nx * ny * a;
-    b1 = make_float3(1.0f + sign * nx * nx * a, sign * bb, -sign * nx);
-    b2 = make_float3(bb, sign + ny * ny * a, -ny);
 }
 
 // ---------------------------------------------------------------------------
@@ -428,29 +417,11 @@ __global__ void __launch_bounds__(MAXT) k_spec_wupdate(const SpecConfig cfg, con
         const float n0 = (nb[0][0] + nb[0][1]) + (nb[0][2] + nb[0][3]);
         const float n1 = (nb[1][0] + nb[1][1]) + (nb[1][2] + nb[1][3]);
         const float n2 = (nb[2][0] + nb[2][1]) + (nb[2][2] + nb[2][3]);
-        if (cfg.proposal == kPropFlip) {            // Appendix B reversal
-            S0 = -s0;
-            S1 = -s1;
-            S2 = -s2;
-        } else if (cfg.proposal == kPropSphere) {
-            const float z = 2.0f * u1 - 1.0f;
-            const float rr = sqrtf(fmaxf(0.0f, (1.0f - z) * (1.0f + z)));
-            S0 = rr * cps;
-            S1 = rr * sps;
-            S2 = z;
-        } else {
-            const float omc = u1 * cfg.cap_c1;             // 1 - cos(alpha), no cancellation
-            const float ca = 1.0f - omc;
-            const float sa = sqrtf(fmaxf(0.0f, omc * (2.0f - omc)));
-            float3 b1, b2;
-            perp_basis_s(s0, s1, s2, b1, b2);
-            S0 = ca * s0 + sa * (cps * b1.x + sps * b2.x);
-            S1 = ca * s1 + sa * (cps * b1.y + sps * b2.y);
-            S2 = ca * s2 + sa * (cps * b1.z + sps * b2.z);
-            const float inv = 1.0f / sqrtf(S0 * S0 + S1 * S1 + S2 * S2);
-            S0 *= inv;
-            S1 *= inv;
-            S2 *= inv;
+        {
+            const float3 Sv = propose_spin(cfg.proposal, cfg.cap_c1, s0, s1, s2, u1, cps, sps);   // Sec. 3.1 proposal
+            S0 = Sv.x;
+            S1 = Sv.y;
+            S2 = Sv.z;
         }
         const float dX = S0 - s0, dY = S1 - s1, dZ = S2 - s2;
         const float dex = -P.J * (dX * n0 + dY * n1 + dZ * n2);

@@ -86,16 +86,6 @@ __device__ __forceinline__ int reduce_scatter_writer(int lane) {
 
 __host__ __device__ constexpr int pow2_at_least(int v) { return v <= 1 ? 1 : 2 * pow2_at_least((v + 1) / 2); }
 
-// Orthonormal pair perpendicular to a unit vector n (Duff et al., "Building an
-// orthonormal basis, revisited", JCGT 2017).
-__device__ __forceinline__ void perp_basis(float nx, float ny, float nz, float3 &b1, float3 &b2) {
-    const float sign = copysignf(1.0f, nz);
-    const float a = -1.0f / (sign + nz);
-    const float b = nx * ny * a;
-    b1 = make_float3(1.0f + sign * nx * nx * a, sign * b, -sign * nx);
-    b2 = make_float3(b, sign + ny * ny * a, -ny);
-}
-
 // One measurement sample into the binning accumulators (FP64, one thread).
 __device__ void obs_push(ObsAcc &A, const double x[MC_NOBS]) {
     A.nsamples += 1;
@@ -284,30 +274,11 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
                     const float uacc = u24f(wds.z);
                     const float4 sq = s4[q];
                     float S0, S1, S2;
-                    if (cfg.proposal == kPropFlip) {            // Appendix B reversal
-                        S0 = -sq.x;
-                        S1 = -sq.y;
-                        S2 = -sq.z;
-                    } else if (cfg.proposal == kPropSphere) {
-                        const float z = 2.0f * u1 - 1.0f;
-                        const float rr = sqrtf(fmaxf(0.0f, (1.0f - z) * (1.0f + z)));
-                        S0 = rr * cps;
-                        S1 = rr * sps;
-                        S2 = z;
-                    } else {
-                        // 1 - cos(alpha) = u1 (1 - cos cone), formed without cancellation
-                        const float omc = u1 * cfg.cap_c1;
-                        const float ca = 1.0f - omc;
-                        const float sa = sqrtf(fmaxf(0.0f, omc * (2.0f - omc)));
-                        float3 b1, b2;
-                        perp_basis(sq.x, sq.y, sq.z, b1, b2);
-                        S0 = ca * sq.x + sa * (cps * b1.x + sps * b2.x);
-                        S1 = ca * sq.y + sa * (cps * b1.y + sps * b2.y);
-                        S2 = ca * sq.z + sa * (cps * b1.z + sps * b2.z);
-                        const float inv = 1.0f / sqrtf(S0 * S0 + S1 * S1 + S2 * S2);
-                        S0 *= inv;
-                        S1 *= inv;
-                        S2 *= inv;
+                    {
+                        const float3 Sv = propose_spin(cfg.proposal, cfg.cap_c1, sq.x, sq.y, sq.z, u1, cps, sps);   // Sec. 3.1 proposal
+                        S0 = Sv.x;
+                        S1 = Sv.y;
+                        S2 = Sv.z;
                     }
                     const float dX = S0 - sq.x, dY = S1 - sq.y, dZ = S2 - sq.z;
                     const int xp = (qx + 1 == L) ? q - qx : q + 1;

@@ -28,14 +28,6 @@ constexpr int kWThreads = 256;
 constexpr int kBlockSites = 16; // sites per decider block (G = 16 / n sub-steps; at least one sub-step)
 constexpr float kPiF = 3.14159265358979f;
 
-__device__ __forceinline__ void perp_basis_w(float nx, float ny, float nz, float3 &b1, float3 &b2) {
-    const float sign = copysignf(1.0f, nz);
-    const float a = -1.0f / (sign + nz);
-    const float b = nx * ny * a;
-    b1 = make_float3(1.0f + sign * nx * nx * a, sign * b, -sign * nx);
-    b2 = make_float3(b, sign + ny * ny * a, -ny);
-}
-
 // One measurement sample into the log-binning accumulators (FP64, global memory):
 // thread k < kNB updates binning level k (blocks of 2^k samples); the levels are
 // independent, so their memory round trips overlap.
@@ -163,30 +155,11 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
     auto propose = [&](int q, float u1, float cps, float sps, float4 &S, float4 &D) {
         const float4 sq = s4[q];
         float S0, S1, S2;
-        if (cfg.proposal == kPropFlip) {            // Appendix B reversal
-            S0 = -sq.x;
-            S1 = -sq.y;
-            S2 = -sq.z;
-        } else if (cfg.proposal == kPropSphere) {
-            const float z = 2.0f * u1 - 1.0f;
-            const float rr = sqrtf(fmaxf(0.0f, (1.0f - z) * (1.0f + z)));
-            S0 = rr * cps;
-            S1 = rr * sps;
-            S2 = z;
-        } else {
-            // 1 - cos(alpha) = u1 (1 - cos cone), formed without cancellation
-            const float omc = u1 * cfg.cap_c1;
-            const float ca = 1.0f - omc;
-            const float sa = sqrtf(fmaxf(0.0f, omc * (2.0f - omc)));
-            float3 b1, b2;
-            perp_basis_w(sq.x, sq.y, sq.z, b1, b2);
-            S0 = ca * sq.x + sa * (cps * b1.x + sps * b2.x);
-            S1 = ca * sq.y + sa * (cps * b1.y + sps * b2.y);
-            S2 = ca * sq.z + sa * (cps * b1.z + sps * b2.z);
-            const float inv = 1.0f / sqrtf(S0 * S0 + S1 * S1 + S2 * S2);
-            S0 *= inv;
-            S1 *= inv;
-            S2 *= inv;
+        {
+            const float3 Sv = propose_spin(cfg.proposal, cfg.cap_c1, sq.x, sq.y, sq.z, u1, cps, sps);   // Sec. 3.1 proposal
+            S0 = Sv.x;
+            S1 = Sv.y;
+            S2 = Sv.z;
         }
         const float dX = S0 - sq.x, dY = S1 - sq.y, dZ = S2 - sq.z;
         const float z0 = sq.z * sq.z, z1 = S2 * S2;
