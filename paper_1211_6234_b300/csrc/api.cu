@@ -93,7 +93,7 @@ struct mc_lattice {
     int *err_flag = nullptr;
     bool wsh_ready = false;
     bool wsh_spec2 = false;     // wsh holds the signed cell-grid spectra of W~
-    float4 *wq = nullptr;     // quarter table of W~ for the windowed paths
+    float4 *wq = nullptr;     // W~ tables of the windowed paths (wq_table_elems)
     float *What = nullptr;    // [4][N] transform of W~ (FFT path), transposed layout
     float2 *fft_scratch = nullptr;
     bool what_ready = false;
@@ -1175,7 +1175,7 @@ int mc_precompute_W(mc_lattice *p, int A, int tail) {
     if (A < 0 || A > 4096) return fail(MC_EINVAL, "image_cutoff %d outside [0, 4096]", A);
     cudaError_t e = launch_wtilde(p->L, A, tail ? 1 : 0, p->W64, p->W32, nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "W~ kernel");
-    if (!p->wq) CK(cudaMalloc(&p->wq, sizeof(float4) * (size_t)(p->L / 2 + 1) * (p->L / 2 + 1)));
+    if (!p->wq) CK(cudaMalloc(&p->wq, sizeof(float4) * wq_table_elems(p->L)));
     e = launch_build_wq(p->L, p->W32, p->wq, nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "W~ quarter table");
     CK(cudaDeviceSynchronize());
@@ -1202,7 +1202,7 @@ int mc_precompute_W_ewald(mc_lattice *p, double eta) {
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     cudaFree(W6);
     if (e != cudaSuccess) return cuda_fail(e, "Ewald W~ kernel");
-    if (!p->wq) CK(cudaMalloc(&p->wq, sizeof(float4) * (size_t)(p->L / 2 + 1) * (p->L / 2 + 1)));
+    if (!p->wq) CK(cudaMalloc(&p->wq, sizeof(float4) * wq_table_elems(p->L)));
     e = launch_build_wq(p->L, p->W32, p->wq, nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "W~ quarter table");
     CK(cudaDeviceSynchronize());
@@ -1701,7 +1701,7 @@ int lattice_copy_W(mc_lattice *p, const double *W64_dev, int A, int tail) {
     CK(cudaMemcpy(p->W64, W64_dev, sizeof(double) * 4 * (size_t)p->N(), cudaMemcpyDeviceToDevice));
     cudaError_t e = launch_cast_W(p->L, p->W64, p->W32, nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "W~ cast");
-    if (!p->wq) CK(cudaMalloc(&p->wq, sizeof(float4) * (size_t)(p->L / 2 + 1) * (p->L / 2 + 1)));
+    if (!p->wq) CK(cudaMalloc(&p->wq, sizeof(float4) * wq_table_elems(p->L)));
     e = launch_build_wq(p->L, p->W32, p->wq, nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "W~ quarter table");
     CK(cudaDeviceSynchronize());

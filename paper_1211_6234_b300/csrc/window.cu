@@ -28,6 +28,14 @@ constexpr int kWThreads = 256;
 constexpr int kBlockSites = 16; // sites per decider block (G = 16 / n sub-steps; at least one sub-step)
 constexpr float kPiF = 3.14159265358979f;
 
+// float4 entries of the W~ table in shared memory: the minimum-image quarter, or at
+// n = 4 (L = 2l) the larger of it and the sub-lattice spectra U (the permutation
+// schedule reads U, the other schedule the quarter; one layout serves both)
+__host__ __device__ __forceinline__ int wtab_smem_elems(int L, int n) {
+    const int hq = L / 2 + 1, hu = L / 4 + 1;
+    return (n == 4 && 4 * hu * hu > hq * hq) ? 4 * hu * hu : hq * hq;
+}
+
 // One measurement sample into the log-binning accumulators (FP64, global memory):
 // thread k < kNB updates binning level k (blocks of 2^k samples); the levels are
 // independent, so their memory round trips overlap.
@@ -110,6 +118,51 @@ __device__ __forceinline__ float pair_energy(const float4 *__restrict__ wq, int 
     return e;
 }
 
+// The 2 x 2 sub-lattice spectra of W~ at L = 2l (table U, k_build_uq).  For a signed
+// offset difference d (|dx|, |dy| < l) of two l x l cells, U_d(kappa) = sum_P
+// (-1)^(kappa.P) W~(d + l P) is read at (|dx|, |dy|) folded into [0, l/2]: a negative
+// component reflects W~ in that axis (xy changes sign; l P is its own negative modulo
+// L), and a component a > l/2 is read at l - a, which reflects and shifts P by one in
+// that axis (xy changes sign, and U(kappa) by (-1)^kappa_axis).
+struct UFold {
+    int base;        // float4 index of kappa = 0
+    float sxy;       // sign of the xy component
+    unsigned kneg;   // bit kappa set: U(kappa) changes sign
+};
+__device__ __forceinline__ UFold u_fold(int l, int dx, int dy) {
+    const int hl = l >> 1;
+    int ax = abs(dx), ay = abs(dy);
+    int par = (dx < 0) ^ (dy < 0);
+    unsigned kneg = 0u;
+    if (ax > hl) { ax = l - ax; par ^= 1; kneg ^= 0xAu; }   // kappa with kx = 1: 1, 3
+    if (ay > hl) { ay = l - ay; par ^= 1; kneg ^= 0xCu; }   // kappa with ky = 1: 2, 3
+    return {(ay * (hl + 1) + ax) * 4, par ? -1.0f : 1.0f, kneg};
+}
+__device__ __forceinline__ float4 u_get(const float4 *__restrict__ uq, const UFold &f, int kap) {
+    const float4 u = uq[f.base + kap];
+    const float sg = ((f.kneg >> kap) & 1u) ? -1.0f : 1.0f;
+    return make_float4(sg * u.x, sg * f.sxy * u.y, sg * u.z, sg * u.w);
+}
+// W~ between lattice sites (xi, yi) and (xp, yp) of an L = 2l lattice from U: with
+// d = o_i - o_p (offsets in the l x l cell) and P = D_i xor D_p (cells),
+// W~(d + l P) = (1/4) sum_kappa (-1)^(kappa.P) U_d(kappa).
+__device__ __forceinline__ float4 w_from_u(const float4 *__restrict__ uq, int l, int xi, int yi, int xp, int yp) {
+    const int Dxi = xi >= l, Dyi = yi >= l, Dxp = xp >= l, Dyp = yp >= l;
+    const UFold f = u_fold(l, (xi - l * Dxi) - (xp - l * Dxp), (yi - l * Dyi) - (yp - l * Dyp));
+    const int P = (Dxi ^ Dxp) | ((Dyi ^ Dyp) << 1);
+    float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int kap = 0; kap < 4; ++kap) {
+        const float4 u = u_get(uq, f, kap);
+        const float sg = (__popc(kap & P) & 1) ? -0.25f : 0.25f;
+        w.x += sg * u.x;
+        w.y += sg * u.y;
+        w.z += sg * u.z;
+        w.w += sg * u.w;
+    }
+    return w;
+}
+
 // PRE: the permutation schedule, where every site is visited once per sweep, so the
 // proposal, its threshold and the field-free part of dE of every window site are fixed
 // at the window's start.  The window's sub-steps then only add, to each site's dE, the
@@ -122,6 +175,9 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
     constexpr int n = C * C;
     constexpr int NB = kBlockSites;   // sites per decider block
     constexpr int G = NB / n;         // sub-steps per block
+    // permutation schedule at L = 2l: moves pushed, and pair energies tabulated, through
+    // the 2 x 2 sub-lattice spectra (table U in place of the quarter of W~)
+    constexpr bool SPX = PRE && C == 2;
     const int L = cfg.L, l = cfg.l, N = L * L, ll = l * l, B = cfg.B, Sw = B * n;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int r = blockIdx.x;
@@ -133,9 +189,12 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
     float *dacc = reinterpret_cast<float *>(hcur);       // PRE: [Sw] dE so far, without exchange and block pairs
     float4 *pS = hcur + Sw;                              // [Sw] proposal S, threshold -T ln u; after the decision w = dE
     float4 *pd = pS + Sw;                                // [Sw] delta = S - s, field-free part of dE
-    float4 *wq = pd + Sw;                                // [(L/2+1)^2] minimum-image quarter of W~
-    float4 *s_mvb = wq + hq * hq;                        // [2][NB] accepted moves of a block:
+    float4 *wq = pd + Sw;                                // [wtab_smem_elems] minimum-image quarter of W~
+                                                         // (SPX: the sub-lattice spectra U)
+    float4 *s_mvb = wq + wtab_smem_elems(L, n);          // [2][NB] accepted moves of a block:
                                                          // (delta, x | y << 16), double-buffered by parity
+                                                         // (SPX: lane 4u + kappa holds the 2 x 2 spectrum
+                                                         // at kappa of sub-step u's moves)
     float4 *wpair = s_mvb + 2 * NB;                      // !PRE: [NB][NB] W~ between the sites of a block
     float4 *etab = wpair;                                // PRE: [2][2 NB / 4][NB] pair energies by block parity,
                                                          // four columns of a row per float4
@@ -240,8 +299,24 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
     // the tensor table and the window's sites (they depend on the sweep counter
     // only); then the state, stale field and proposals.
     pdl_trigger();
+    if constexpr (SPX) {
+        const int hu = (l >> 1) + 1;
+        const float4 *gu = buf.wq + hq * hq;
 #pragma unroll 4
-    for (int i = tid; i < hq * hq; i += kWThreads) wq[i] = buf.wq[i];
+        for (int i = tid; i < 4 * hu * hu; i += kWThreads) wq[i] = gu[i];
+    } else {
+#pragma unroll 4
+        for (int i = tid; i < hq * hq; i += kWThreads) wq[i] = buf.wq[i];
+    }
+    // W~(q_i - q_p) v for lattice sites i = (xi, yi), p = (xp, yp)
+    auto w_apply_sites = [&](int xi, int yi, int xp, int yp, float3 v) -> float3 {
+        if constexpr (SPX) {
+            const float4 w = w_from_u(wq, l, xi, yi, xp, yp);
+            return make_float3(w.x * v.x + w.y * v.y, w.y * v.x + w.z * v.y, w.w * v.z);
+        } else {
+            return wq_apply(wq, L, xi - xp, yi - yp, v);
+        }
+    };
     for (int s = tid; s < Sw; s += kWThreads) wxy[s] = window_site_xy(l, C, key, t, cfg.schedule, rk, k0, s);
     // stale_mode 3: warp mt sums M-tile mt of this replica's column over the tile's units
     // (six M-tiles of 128 rows); the work plan is fixed when the buffers are set up
@@ -384,7 +459,56 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
                 et[((c >> 2) * NB + i) * 4 + (c & 3)] = v;
             }
         };
-        etab_fill(0, tid, kWThreads);
+        // SPX: item it = g * NB + i of block nb's table, the four entries of row i and
+        // column group g (the four cells D_p of one sub-step) as one float4: W~ between the
+        // cells of the two sub-steps' offsets from U (four loads and one inverse 2 x 2
+        // transform), the exchange as in pair_energy
+        auto etab_item = [&](int nb, int it) {
+            float *etf = reinterpret_cast<float *>(etab + (nb & 1) * (2 * NB / 4) * NB);
+            const int g = it / NB, i = it - g * NB, ui = i / n, Di = i - ui * n;
+            const bool prevb = g < G;
+            if (prevb ? nb == 0 : (g - G) >= ui) {
+                reinterpret_cast<float4 *>(etf)[it] = make_float4(0.f, 0.f, 0.f, 0.f);
+                return;
+            }
+            const int jr = nb * G + ui, jc = prevb ? (nb - 1) * G + g : nb * G + (g - G);
+            const int orr = wxy[n * jr], oc = wxy[n * jc];
+            const UFold f = u_fold(l, (orr & 0xFFFF) - (oc & 0xFFFF), ((orr >> 16) & 0x7FFF) - ((oc >> 16) & 0x7FFF));
+            const float4 U0 = u_get(wq, f, 0), U1 = u_get(wq, f, 1), U2 = u_get(wq, f, 2), U3 = u_get(wq, f, 3);
+            // 4 W~(d + l P), P = Px + 2 Py: sum_kappa (-1)^(kappa.P) U(kappa)
+            const float4 a = make_float4(U0.x + U1.x, U0.y + U1.y, U0.z + U1.z, U0.w + U1.w);
+            const float4 b = make_float4(U0.x - U1.x, U0.y - U1.y, U0.z - U1.z, U0.w - U1.w);
+            const float4 c = make_float4(U2.x + U3.x, U2.y + U3.y, U2.z + U3.z, U2.w + U3.w);
+            const float4 e = make_float4(U2.x - U3.x, U2.y - U3.y, U2.z - U3.z, U2.w - U3.w);
+            const float4 Wp[4] = {make_float4(a.x + c.x, a.y + c.y, a.z + c.z, a.w + c.w),
+                                  make_float4(b.x + e.x, b.y + e.y, b.z + e.z, b.w + e.w),
+                                  make_float4(a.x - c.x, a.y - c.y, a.z - c.z, a.w - c.w),
+                                  make_float4(b.x - e.x, b.y - e.y, b.z - e.z, b.w - e.w)};
+            const float4 di = pd[n * jr + Di];
+            const int ai = wxy[n * jr + Di];
+            const float cd4 = 0.25f * P.CD;
+#pragma unroll
+            for (int Pp = 0; Pp < 4; ++Pp) {
+                const int Dp = Di ^ Pp;
+                const float4 W = Wp[Pp], dp = pd[n * jc + Dp];
+                float v = cd4 * (di.x * (W.x * dp.x + W.y * dp.y) + di.y * (W.y * dp.x + W.z * dp.y) + di.z * (W.w * dp.z));
+                if (!prevb) {
+                    const int ap = wxy[n * jc + Dp];
+                    const int dx = (ai & 0xFFFF) - (ap & 0xFFFF), dy = ((ai >> 16) & 0x7FFF) - ((ap >> 16) & 0x7FFF);
+                    const int ax = dx < 0 ? dx + L : dx, ay = dy < 0 ? dy + L : dy;
+                    int m = 0;
+                    if (ay == 0) m += (ax == 1) + (ax == L - 1);
+                    if (ax == 0) m += (ay == 1) + (ay == L - 1);
+                    if (m) v -= P.J * (float)m * (di.x * dp.x + di.y * dp.y + di.z * dp.z);
+                }
+                etf[it * 4 + Dp] = v;
+            }
+        };
+        if constexpr (SPX) {
+            for (int it = tid; it < 2 * NB / 4 * NB; it += kWThreads) etab_item(0, it);
+        } else {
+            etab_fill(0, tid, kWThreads);
+        }
         __syncthreads();
         // Blocks of G sub-steps (16 sites), one CTA barrier per block.  Warp 0 (the
         // decider) takes block b's decisions: a site's dE is its window-start value, plus
@@ -439,8 +563,8 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
                         const bool moved = p < base ? pxy < 0 : ((p - base) / n < i / n && ((am >> (p - base)) & 1u));
                         if (!moved) continue;
                         const float4 dp = pd[p];
-                        const float3 w = wq_apply(wq, L, qx - (pxy & 0xFFFF), qy - ((pxy >> 16) & 0x7FFF),
-                                                  make_float3(dp.x, dp.y, dp.z));
+                        const float3 w = w_apply_sites(qx, qy, pxy & 0xFFFF, (pxy >> 16) & 0x7FFF,
+                                                       make_float3(dp.x, dp.y, dp.z));
                         hx += w.x;
                         hy += w.y;
                         hz += w.z;
@@ -460,8 +584,26 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
                     if (acc) {
                         s4[q] = make_float4(S.x, S.y, S.z, 0.0f);
                         wxy[s] = xy | (int)0x80000000;
-                        s_mvb[cur * NB + __popc(am & ((1u << lane) - 1u))] = make_float4(D.x, D.y, D.z, __int_as_float(xy));
+                        if constexpr (!SPX)
+                            s_mvb[cur * NB + __popc(am & ((1u << lane) - 1u))] = make_float4(D.x, D.y, D.z, __int_as_float(xy));
                     }
+                }
+                if constexpr (SPX) {
+                    // the block's moves as 2 x 2 spectra: lane 4u + kappa takes sum_D
+                    // (-1)^(kappa.D) (accepted move of site 4u + D), a Walsh-Hadamard
+                    // butterfly over the four lanes of sub-step u
+                    float x = acc ? D.x : 0.f, y = acc ? D.y : 0.f, z = acc ? D.z : 0.f;
+#pragma unroll
+                    for (int bb = 1; bb <= 2; bb <<= 1) {
+                        const float px = __shfl_xor_sync(0xffffffffu, x, bb);
+                        const float py = __shfl_xor_sync(0xffffffffu, y, bb);
+                        const float pz = __shfl_xor_sync(0xffffffffu, z, bb);
+                        const bool up = lane & bb;
+                        x = up ? px - x : x + px;
+                        y = up ? py - y : y + py;
+                        z = up ? pz - z : z + pz;
+                    }
+                    if (act) s_mvb[cur * NB + lane] = make_float4(x, y, z, 0.0f);
                 }
                 pm = am;
                 if (lane == 0) {
@@ -470,6 +612,54 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
                 }
             } else if (!idle) {
                 const int nprev = bk > 0 ? s_nmv[prv] : 0;
+                if constexpr (SPX) {
+                    // push the moves of block b-1 into the dE of the sites of blocks >= b+1
+                    // through their spectra: item 4 j + kappa of target sub-step j (offset o)
+                    // sums dH(kappa) = sum_u U_{o - e_u}(kappa) S_u(kappa) over the block's
+                    // four sub-steps u (offsets e_u); the four kappa lanes of a target then
+                    // exchange their parts of (C_D / 4) sum_kappa (-1)^(kappa.D) d_D . dH(kappa)
+                    // so that lane kappa adds the one of cell D = kappa
+                    if (nprev > 0) {
+                        const int j0 = (bk + 1) * G, nitem = n * (B - j0), kap = lane & 3;
+                        const bool b0 = lane & 1, b1 = lane & 2;
+                        for (int ib = hw * 32; ib < nitem; ib += kH) {   // warp-uniform
+                            const int item = ib + lane;
+                            const bool on = item < nitem;
+                            const int jt = on ? j0 + (item >> 2) : j0;
+                            const int ot = wxy[n * jt], otx = ot & 0xFFFF, oty = (ot >> 16) & 0x7FFF;
+                            float Hx = 0.f, Hy = 0.f, Hz = 0.f;
+#pragma unroll
+                            for (int u = 0; u < G; ++u) {
+                                const int os = wxy[n * ((bk - 1) * G + u)];
+                                const float4 Sk = s_mvb[prv * NB + n * u + kap];
+                                const UFold f = u_fold(l, otx - (os & 0xFFFF), oty - ((os >> 16) & 0x7FFF));
+                                const float4 Uv = u_get(wq, f, kap);
+                                Hx += Uv.x * Sk.x + Uv.y * Sk.y;
+                                Hy += Uv.y * Sk.x + Uv.z * Sk.y;
+                                Hz += Uv.w * Sk.z;
+                            }
+                            float c[4];
+#pragma unroll
+                            for (int Dp = 0; Dp < 4; ++Dp) {
+                                const float4 Dv = pd[n * jt + Dp];
+                                const float v = Dv.x * Hx + Dv.y * Hy + Dv.z * Hz;
+                                c[Dp] = (__popc(kap & Dp) & 1) ? -v : v;
+                            }
+                            // reduce-scatter over the four kappa lanes
+                            const float s0 = __shfl_xor_sync(0xffffffffu, b0 ? c[0] : c[1], 1);
+                            const float s1 = __shfl_xor_sync(0xffffffffu, b0 ? c[2] : c[3], 1);
+                            const float k0 = (b0 ? c[1] : c[0]) + s0;   // cell b0
+                            const float k1 = (b0 ? c[3] : c[2]) + s1;   // cell b0 + 2
+                            const float s2 = __shfl_xor_sync(0xffffffffu, b1 ? k0 : k1, 2);
+                            const float fin = (b1 ? k1 : k0) + s2;      // cell kappa
+                            if (on) dacc[n * jt + kap] += 0.25f * P.CD * fin;
+                        }
+                    }
+                    // block b+1's pair energies on the helper threads from the last down
+                    // (their pushes are the fewest)
+                    const int it = ht - (kH - 2 * NB / 4 * NB);
+                    if (bk + 1 < nblk && it >= 0) etab_item(bk + 1, it);
+                } else {
                 // push the moves of block b-1 into the dE of the sites of blocks >= b+1
                 if (nprev > 0) {
                     for (int s = base + NB + ht; s < Sw; s += kH) {
@@ -505,6 +695,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
                     }
                 }
                 if (bk + 1 < nblk) etab_fill(bk + 1, ht, kH);
+                }
             }
             __syncthreads();
         }
@@ -726,8 +917,8 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
             const int xy = wxy[j * n + d], pxy = wxy[j * n + dp];
             if (xy >= 0 || pxy >= 0) continue;
             const float4 m = pd[j * n + d], mp = pd[j * n + dp];
-            const float3 Wd = wq_apply(wq, L, (xy & 0xFFFF) - (pxy & 0xFFFF), ((xy >> 16) & 0x7FFF) - ((pxy >> 16) & 0x7FFF),
-                                       make_float3(m.x, m.y, m.z));
+            const float3 Wd = w_apply_sites(xy & 0xFFFF, (xy >> 16) & 0x7FFF, pxy & 0xFFFF, (pxy >> 16) & 0x7FFF,
+                                            make_float3(m.x, m.y, m.z));
             e_f += P.CD * (mp.x * Wd.x + mp.y * Wd.y + mp.z * Wd.z);
         }
         e_loc = (double)e_f;
@@ -835,6 +1026,23 @@ __global__ void k_build_wq(int L, const float *__restrict__ W32, float4 *wq) {
     wq[i] = make_float4(W32[g], W32[N + g], W32[2 * N + g], W32[3 * N + g]);
 }
 
+// The sub-lattice spectra of W~ for l = L/2 (the table U of the permutation-schedule
+// sub-steps at L = 2l): U_d(kappa) = sum_P (-1)^(kappa.P) W~(d + l P), P in {0,1}^2,
+// for 0 <= dx, dy <= l/2; one thread per entry, the four terms summed in FP64.
+__global__ void k_build_uq(int L, const float *__restrict__ W32, float4 *uq) {
+    const int l = L / 2, hu = l / 2 + 1, N = L * L;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 4 * hu * hu) return;
+    const int kap = i & 3, cell = i >> 2, dx = cell % hu, dy = cell / hu;
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int P = 0; P < 4; ++P) {
+        const double sg = (__popc(kap & P) & 1) ? -1.0 : 1.0;
+        const int g = (dy + l * (P >> 1)) * L + dx + l * (P & 1);
+        for (int c = 0; c < 4; ++c) a[c] += sg * (double)W32[c * N + g];
+    }
+    uq[i] = make_float4((float)a[0], (float)a[1], (float)a[2], (float)a[3]);
+}
+
 __global__ void k_spins_to_bf16(size_t count, const float *__restrict__ s, __nv_bfloat16 *hi, __nv_bfloat16 *lo) {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
@@ -846,10 +1054,16 @@ __global__ void k_spins_to_bf16(size_t count, const float *__restrict__ s, __nv_
 
 }  // namespace
 
+size_t wq_table_elems(int L) {
+    const size_t hq = (size_t)(L / 2 + 1), hu = (size_t)(L / 4 + 1);
+    return hq * hq + (L % 2 == 0 ? 4 * hu * hu : 0);
+}
+
 size_t window_smem_bytes(int L, int Sw, int n) {
-    const size_t N = (size_t)L * L, hq = (size_t)(L / 2 + 1);
-    (void)n;   // blocks of kBlockSites sites (n <= kBlockSites)
-    return sizeof(float4) * (N + 3 * (size_t)Sw + hq * hq + 2 * kBlockSites + kBlockSites * kBlockSites) +
+    const size_t N = (size_t)L * L;
+    // blocks of kBlockSites sites (n <= kBlockSites)
+    return sizeof(float4) * (N + 3 * (size_t)Sw + (size_t)wtab_smem_elems(L, n) + 2 * kBlockSites +
+                             kBlockSites * kBlockSites) +
            sizeof(int) * (size_t)Sw;
 }
 
@@ -906,6 +1120,10 @@ cudaError_t launch_set_u32(uint32_t *dst, uint32_t v, cudaStream_t st) {
 cudaError_t launch_build_wq(int L, const float *W32, float4 *wq, cudaStream_t st) {
     const int hq = L / 2 + 1;
     k_build_wq<<<(hq * hq + 127) / 128, 128, 0, st>>>(L, W32, wq);
+    if (L % 2 == 0) {
+        const int hu = L / 4 + 1;
+        k_build_uq<<<(4 * hu * hu + 127) / 128, 128, 0, st>>>(L, W32, wq + (size_t)hq * hq);
+    }
     return cudaGetLastError();
 }
 

@@ -45,13 +45,21 @@ struct WindowBuffers {
     const float *stale;           // see stale_mode
     const float *part;            // stale_mode 2: [units][NT][128] partial tiles, row fastest
     const int *tile_first;        // stale_mode 2: [ntiles * mtiles + 1] first unit of tile (nt, mt)
-    const float4 *wq;             // [(L/2+1)^2] W~ on the minimum-image quarter, (xx, xy, yy, zz)
+    const float4 *wq;             // [wq_table_elems(L)]: W~ on the minimum-image quarter, (xx, xy, yy, zz),
+                                  // [(L/2+1)^2]; for even L then the sub-lattice spectra of W~ for
+                                  // l = L/2, [L/4+1][L/4+1][4] (wq_table_elems)
     EnergyHist hist;              // optional energy histogram
     unsigned long long *cycles;   // optional [4]: SM clock cycles summed over CTAs of the blocks, the
                                   // set-up before them and the tail after them, and the blocks run
 };
 
 size_t window_smem_bytes(int L, int Sw, int n);
+// float4 entries of the W~ tables of the windowed path: the minimum-image quarter
+// [(L/2+1)^2] and, for even L, after it the table U of the 2 x 2 sub-lattice spectra
+// at l = L/2: U_d(kappa) = sum_P (-1)^(kappa.P) W~(d + l P) for 0 <= dx, dy <= l/2 and
+// kappa = kx + 2 ky, entry (dy (l/2+1) + dx) * 4 + kappa.
+size_t wq_table_elems(int L);
+// Fills both tables from the FP32 W~ (wq holds wq_table_elems(L) entries).
 cudaError_t launch_build_wq(int L, const float *W32, float4 *wq, cudaStream_t st);
 cudaError_t launch_set_u32(uint32_t *dst, uint32_t v, cudaStream_t st);
 bool window_supported(int L, int l, int B);
