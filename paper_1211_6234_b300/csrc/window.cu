@@ -143,6 +143,19 @@ __device__ __forceinline__ float4 u_get(const float4 *__restrict__ uq, const UFo
     const float sg = ((f.kneg >> kap) & 1u) ? -1.0f : 1.0f;
     return make_float4(sg * u.x, sg * f.sxy * u.y, sg * u.z, sg * u.w);
 }
+// The fold of u_fold packed in one word: cell index << 4 | kneg | (xy sign bit), so
+// that the lanes of a warp can share it (kneg uses bits 1..3: kappa = 0 never changes sign).
+__device__ __forceinline__ int u_fold_word(int l, int dx, int dy) {
+    const UFold f = u_fold(l, dx, dy);
+    return ((f.base >> 2) << 4) | (int)f.kneg | (f.sxy < 0.0f ? 1 : 0);
+}
+__device__ __forceinline__ float4 u_get_word(const float4 *__restrict__ uq, int w, int kap) {
+    const float4 u = uq[((w >> 4) << 2) + kap];
+    const unsigned neg = ((unsigned)((w & 0xE) >> kap) & 1u) << 31;
+    const unsigned negxy = neg ^ ((unsigned)(w & 1) << 31);
+    return make_float4(__uint_as_float(__float_as_uint(u.x) ^ neg), __uint_as_float(__float_as_uint(u.y) ^ negxy),
+                       __uint_as_float(__float_as_uint(u.z) ^ neg), __uint_as_float(__float_as_uint(u.w) ^ neg));
+}
 // W~ between lattice sites (xi, yi) and (xp, yp) of an L = 2l lattice from U: with
 // d = o_i - o_p (offsets in the l x l cell) and P = D_i xor D_p (cells),
 // W~(d + l P) = (1/4) sum_kappa (-1)^(kappa.P) U_d(kappa).
@@ -487,11 +500,12 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
             const float4 di = pd[n * jr + Di];
             const int ai = wxy[n * jr + Di];
             const float cd4 = 0.25f * P.CD;
+            float v[4];   // v[Pp]: the entry of cell D_p = D_i xor Pp
 #pragma unroll
             for (int Pp = 0; Pp < 4; ++Pp) {
                 const int Dp = Di ^ Pp;
                 const float4 W = Wp[Pp], dp = pd[n * jc + Dp];
-                float v = cd4 * (di.x * (W.x * dp.x + W.y * dp.y) + di.y * (W.y * dp.x + W.z * dp.y) + di.z * (W.w * dp.z));
+                v[Pp] = cd4 * (di.x * (W.x * dp.x + W.y * dp.y) + di.y * (W.y * dp.x + W.z * dp.y) + di.z * (W.w * dp.z));
                 if (!prevb) {
                     const int ap = wxy[n * jc + Dp];
                     const int dx = (ai & 0xFFFF) - (ap & 0xFFFF), dy = ((ai >> 16) & 0x7FFF) - ((ap >> 16) & 0x7FFF);
@@ -499,10 +513,19 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
                     int m = 0;
                     if (ay == 0) m += (ax == 1) + (ax == L - 1);
                     if (ax == 0) m += (ay == 1) + (ay == L - 1);
-                    if (m) v -= P.J * (float)m * (di.x * dp.x + di.y * dp.y + di.z * dp.z);
+                    if (m) v[Pp] -= P.J * (float)m * (di.x * dp.x + di.y * dp.y + di.z * dp.z);
                 }
-                etf[it * 4 + Dp] = v;
             }
+            // into cell order: entry D_p is v[D_i xor D_p]
+            if (Di & 1) {
+                float t = v[0]; v[0] = v[1]; v[1] = t;
+                t = v[2]; v[2] = v[3]; v[3] = t;
+            }
+            if (Di & 2) {
+                float t = v[0]; v[0] = v[2]; v[2] = t;
+                t = v[1]; v[1] = v[3]; v[3] = t;
+            }
+            reinterpret_cast<float4 *>(etf)[it] = make_float4(v[0], v[1], v[2], v[3]);
         };
         if constexpr (SPX) {
             for (int it = tid; it < 2 * NB / 4 * NB; it += kWThreads) etab_item(0, it);
@@ -518,6 +541,20 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
         // meanwhile push the moves of block b-1 into the sites of blocks >= b+1 and
         // tabulate block b+1's pair energies.
         unsigned pm = 0;   // accepted sites of the previous block (decider)
+        // decider: the site data of its next block (fixed since the window's start) and
+        // their neighbour sums (the decider alone writes spins during the blocks), taken
+        // before the block barrier
+        int nx_xy = 0;
+        float4 nx_D = make_float4(0.f, 0.f, 0.f, 0.f), nx_S = nx_D;
+        float3 nx_nb = make_float3(0.f, 0.f, 0.f);
+        auto dec_prefetch = [&](int nb) {
+            const int s = nb * NB + (lane & (NB - 1));
+            nx_xy = wxy[s];
+            nx_D = pd[s];
+            nx_S = pS[s];
+            nx_nb = nbr_sum(nx_xy & 0xFFFF, (nx_xy >> 16) & 0x7FFF);
+        };
+        if (warp == dw) dec_prefetch(0);
         for (int bk = 0; bk < nblk; ++bk) {
             const int cur = bk & 1, prv = cur ^ 1, base = bk * NB;
             if (warp == dw) {
@@ -533,10 +570,10 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
                     E[c + 2] = v.z;
                     E[c + 3] = v.w;
                 }
-                const int xy = wxy[s];
+                const int xy = nx_xy;
                 const int qx = xy & 0xFFFF, qy = (xy >> 16) & 0x7FFF, q = qy * L + qx;
-                const float4 D = pd[s], S = pS[s];
-                const float3 nb3 = nbr_sum(qx, qy);
+                const float4 D = nx_D, S = nx_S;
+                const float3 nb3 = nx_nb;
                 float dE = dacc[s] - P.J * (D.x * nb3.x + D.y * nb3.y + D.z * nb3.z);
 #pragma unroll
                 for (int p = 0; p < NB; ++p)
@@ -610,49 +647,56 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
                     s_nmv[cur] = __popc(am);
                     n_acc += __popc(am);
                 }
+                if (bk + 1 < nblk) {
+                    __syncwarp();   // this block's spins before the next block's neighbour sums
+                    dec_prefetch(bk + 1);
+                }
             } else if (!idle) {
                 const int nprev = bk > 0 ? s_nmv[prv] : 0;
                 if constexpr (SPX) {
                     // push the moves of block b-1 into the dE of the sites of blocks >= b+1
                     // through their spectra: item 4 j + kappa of target sub-step j (offset o)
                     // sums dH(kappa) = sum_u U_{o - e_u}(kappa) S_u(kappa) over the block's
-                    // four sub-steps u (offsets e_u); the four kappa lanes of a target then
-                    // exchange their parts of (C_D / 4) sum_kappa (-1)^(kappa.D) d_D . dH(kappa)
-                    // so that lane kappa adds the one of cell D = kappa
+                    // four sub-steps u (offsets e_u; lane kappa folds o - e_kappa and the four
+                    // lanes of the target share the folds); an inverse 2 x 2 transform over the
+                    // four lanes then leaves lane D with the field change of cell D,
+                    // (1/4) sum_kappa (-1)^(kappa.D) dH(kappa), and lane D adds C_D d_D . dh
                     if (nprev > 0) {
                         const int j0 = (bk + 1) * G, nitem = n * (B - j0), kap = lane & 3;
-                        const bool b0 = lane & 1, b1 = lane & 2;
+                        const int os = wxy[n * ((bk - 1) * G + kap)];
+                        const int osx = os & 0xFFFF, osy = (os >> 16) & 0x7FFF;
+                        float4 Sk[G];
+#pragma unroll
+                        for (int u = 0; u < G; ++u) Sk[u] = s_mvb[prv * NB + n * u + kap];
                         for (int ib = hw * 32; ib < nitem; ib += kH) {   // warp-uniform
                             const int item = ib + lane;
                             const bool on = item < nitem;
                             const int jt = on ? j0 + (item >> 2) : j0;
-                            const int ot = wxy[n * jt], otx = ot & 0xFFFF, oty = (ot >> 16) & 0x7FFF;
+                            const int ot = wxy[n * jt];
+                            const int fw = u_fold_word(l, (ot & 0xFFFF) - osx, ((ot >> 16) & 0x7FFF) - osy);
                             float Hx = 0.f, Hy = 0.f, Hz = 0.f;
 #pragma unroll
                             for (int u = 0; u < G; ++u) {
-                                const int os = wxy[n * ((bk - 1) * G + u)];
-                                const float4 Sk = s_mvb[prv * NB + n * u + kap];
-                                const UFold f = u_fold(l, otx - (os & 0xFFFF), oty - ((os >> 16) & 0x7FFF));
-                                const float4 Uv = u_get(wq, f, kap);
-                                Hx += Uv.x * Sk.x + Uv.y * Sk.y;
-                                Hy += Uv.y * Sk.x + Uv.z * Sk.y;
-                                Hz += Uv.w * Sk.z;
+                                const int w = __shfl_sync(0xffffffffu, fw, (lane & ~3) | u);
+                                const float4 Uv = u_get_word(wq, w, kap);
+                                Hx += Uv.x * Sk[u].x + Uv.y * Sk[u].y;
+                                Hy += Uv.y * Sk[u].x + Uv.z * Sk[u].y;
+                                Hz += Uv.w * Sk[u].z;
                             }
-                            float c[4];
 #pragma unroll
-                            for (int Dp = 0; Dp < 4; ++Dp) {
-                                const float4 Dv = pd[n * jt + Dp];
-                                const float v = Dv.x * Hx + Dv.y * Hy + Dv.z * Hz;
-                                c[Dp] = (__popc(kap & Dp) & 1) ? -v : v;
+                            for (int bb = 1; bb <= 2; bb <<= 1) {
+                                const float px = __shfl_xor_sync(0xffffffffu, Hx, bb);
+                                const float py = __shfl_xor_sync(0xffffffffu, Hy, bb);
+                                const float pz = __shfl_xor_sync(0xffffffffu, Hz, bb);
+                                const bool up = lane & bb;
+                                Hx = up ? px - Hx : Hx + px;
+                                Hy = up ? py - Hy : Hy + py;
+                                Hz = up ? pz - Hz : Hz + pz;
                             }
-                            // reduce-scatter over the four kappa lanes
-                            const float s0 = __shfl_xor_sync(0xffffffffu, b0 ? c[0] : c[1], 1);
-                            const float s1 = __shfl_xor_sync(0xffffffffu, b0 ? c[2] : c[3], 1);
-                            const float k0 = (b0 ? c[1] : c[0]) + s0;   // cell b0
-                            const float k1 = (b0 ? c[3] : c[2]) + s1;   // cell b0 + 2
-                            const float s2 = __shfl_xor_sync(0xffffffffu, b1 ? k0 : k1, 2);
-                            const float fin = (b1 ? k1 : k0) + s2;      // cell kappa
-                            if (on) dacc[n * jt + kap] += 0.25f * P.CD * fin;
+                            if (on) {
+                                const float4 Dv = pd[n * jt + kap];
+                                dacc[n * jt + kap] += 0.25f * P.CD * (Dv.x * Hx + Dv.y * Hy + Dv.z * Hz);
+                            }
                         }
                     }
                     // block b+1's pair energies on the helper threads from the last down
@@ -907,20 +951,33 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
         for (int s = tid; s < Sw; s += kWThreads)
             if (wxy[s] < 0) e_f += pS[s].w;
         constexpr int npair = n * (n - 1) / 2;   // site pairs d > dp of a sub-step
-        for (int task = tid; task < B * npair; task += kWThreads) {
-            const int j = task / npair;
-            int d = 1, dp = task - j * npair;
-            while (dp >= d) {
-                dp -= d;
-                ++d;
+        if constexpr (npair > 0) {
+            for (int task = tid; task < B * npair; task += kWThreads) {
+                const int j = task / npair;
+                int d = 1, dp = task - j * npair;
+                while (dp >= d) {
+                    dp -= d;
+                    ++d;
+                }
+                const int xy = wxy[j * n + d], pxy = wxy[j * n + dp];
+                if (xy >= 0 || pxy >= 0) continue;
+                const float4 m = pd[j * n + d], mp = pd[j * n + dp];
+                float3 Wd;
+                if constexpr (SPX) {
+                    // cells d and dp of one offset: W~(l P), P = d xor dp, from W~ itself
+                    const int Pp = d ^ dp, g = l * (Pp >> 1) * L + l * (Pp & 1);
+                    const float wa = __ldg(buf.W32 + g), wb = __ldg(buf.W32 + N + g);
+                    const float wc = __ldg(buf.W32 + 2 * N + g), wd = __ldg(buf.W32 + 3 * N + g);
+                    Wd = make_float3(wa * m.x + wb * m.y, wb * m.x + wc * m.y, wd * m.z);
+                } else {
+                    Wd = w_apply_sites(xy & 0xFFFF, (xy >> 16) & 0x7FFF, pxy & 0xFFFF, (pxy >> 16) & 0x7FFF,
+                                       make_float3(m.x, m.y, m.z));
+                }
+                e_f += P.CD * (mp.x * Wd.x + mp.y * Wd.y + mp.z * Wd.z);
             }
-            const int xy = wxy[j * n + d], pxy = wxy[j * n + dp];
-            if (xy >= 0 || pxy >= 0) continue;
-            const float4 m = pd[j * n + d], mp = pd[j * n + dp];
-            const float3 Wd = w_apply_sites(xy & 0xFFFF, (xy >> 16) & 0x7FFF, pxy & 0xFFFF, (pxy >> 16) & 0x7FFF,
-                                            make_float3(m.x, m.y, m.z));
-            e_f += P.CD * (mp.x * Wd.x + mp.y * Wd.y + mp.z * Wd.z);
         }
+        // a few terms per thread, then 32 per warp in FP32; the warps' sums in FP64
+        for (int off = 16; off; off >>= 1) e_f += __shfl_xor_sync(0xffffffffu, e_f, off);
         e_loc = (double)e_f;
     }
     for (int j = tid; !PRE && j < B; j += kWThreads) {
@@ -942,7 +999,8 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
         }
         e_loc += (double)sub;
     }
-    for (int off = 16; off; off >>= 1) e_loc += __shfl_xor_sync(0xffffffffu, e_loc, off);
+    if (!PRE)
+        for (int off = 16; off; off >>= 1) e_loc += __shfl_xor_sync(0xffffffffu, e_loc, off);
     if (lane == 0) s_epart[warp] = e_loc;
     __syncthreads();
     if (tid == 0) {
