@@ -42,7 +42,7 @@ __host__ __device__ __forceinline__ int wtab_smem_elems(int L, int n) {
 __device__ void obs_push_level(ObsAcc &A, const double x[MC_NOBS], int k) {
     const long long pc = A.pcnt[k] + 1;
     const bool done = pc == (1LL << k);
-    const double inv = 1.0 / (double)(1LL << k);
+    const double inv = __longlong_as_double((long long)(1023 - k) << 52);   // 2^-k
     double ps[MC_NOBS], bs[MC_NOBS], bq[MC_NOBS];
 #pragma unroll
     for (int o = 0; o < MC_NOBS; ++o) {
@@ -312,6 +312,12 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
     // the tensor table and the window's sites (they depend on the sweep counter
     // only); then the state, stale field and proposals.
     pdl_trigger();
+    __shared__ float4 s_wl[4];   // SPX: W~(l P), P = Px + 2 Py (the cells of one offset)
+    if (SPX && tid < 4) {
+        const int g = l * (tid >> 1) * L + l * (tid & 1);
+        s_wl[tid] = make_float4(__ldg(buf.W32 + g), __ldg(buf.W32 + N + g), __ldg(buf.W32 + 2 * N + g),
+                                __ldg(buf.W32 + 3 * N + g));
+    }
     if constexpr (SPX) {
         const int hu = (l >> 1) + 1;
         const float4 *gu = buf.wq + hq * hq;
@@ -964,11 +970,9 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
                 const float4 m = pd[j * n + d], mp = pd[j * n + dp];
                 float3 Wd;
                 if constexpr (SPX) {
-                    // cells d and dp of one offset: W~(l P), P = d xor dp, from W~ itself
-                    const int Pp = d ^ dp, g = l * (Pp >> 1) * L + l * (Pp & 1);
-                    const float wa = __ldg(buf.W32 + g), wb = __ldg(buf.W32 + N + g);
-                    const float wc = __ldg(buf.W32 + 2 * N + g), wd = __ldg(buf.W32 + 3 * N + g);
-                    Wd = make_float3(wa * m.x + wb * m.y, wb * m.x + wc * m.y, wd * m.z);
+                    // cells d and dp of one offset: W~(l P), P = d xor dp
+                    const float4 w = s_wl[d ^ dp];
+                    Wd = make_float3(w.x * m.x + w.y * m.y, w.y * m.x + w.z * m.y, w.w * m.z);
                 } else {
                     Wd = w_apply_sites(xy & 0xFFFF, (xy >> 16) & 0x7FFF, pxy & 0xFFFF, (pxy >> 16) & 0x7FFF,
                                        make_float3(m.x, m.y, m.z));
@@ -1046,22 +1050,39 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
 #pragma unroll
             for (int c = 0; c < 12; ++c) s_mred[warp][c] = mv_[c];
         __syncthreads();
-        if (tid < kNB && buf.obs) {
-            double sm[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-            for (int ww = 0; ww < kWThreads / 32; ++ww)
-                for (int c = 0; c < 12; ++c) sm[c] += s_mred[ww][c];
-            const double Mx = sm[0] / N, My = sm[1] / N, Mz = sm[2] / N, Mh = sm[3] / N, Mv = sm[4] / N;
-            const double nh[3] = {sm[5], sm[7], sm[9]}, nv[3] = {sm[6], sm[8], sm[10]};
-            double x[MC_NOBS];
-            x[MC_OBS_ABS_M] = sqrt(Mx * Mx + My * My + Mz * Mz);
-            x[MC_OBS_MZ] = Mz;
-            x[MC_OBS_ABS_MZ] = fabs(Mz);
-            x[MC_OBS_MPAR] = sqrt(Mx * Mx + My * My);
-            x[MC_OBS_E] = s_energy / N;
-            x[MC_OBS_MST] = sqrt(Mh * Mh + Mv * Mv);
-            stripe_obs(x, nh, nv, sm[11], N);
-            obs_push_level(buf.obs[r], x, tid);
-            if (tid == 0) hist_push(buf.hist, r, x[MC_OBS_E]);
+        // the sample once (FP64 is slow here: lane c sums component c over the warps, lane
+        // 0 forms the observables), then lane k < kNB pushes it into binning level k
+        if (warp == 0 && buf.obs) {
+            __shared__ double s_sm[12], s_x[MC_NOBS];
+            if (lane < 12) {
+                double v = 0.0;
+                for (int ww = 0; ww < kWThreads / 32; ++ww) v += s_mred[ww][lane];
+                s_sm[lane] = v;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                const double *sm = s_sm;
+                const double Mx = sm[0] / N, My = sm[1] / N, Mz = sm[2] / N, Mh = sm[3] / N, Mv = sm[4] / N;
+                const double nh[3] = {sm[5], sm[7], sm[9]}, nv[3] = {sm[6], sm[8], sm[10]};
+                double x[MC_NOBS];
+                x[MC_OBS_ABS_M] = sqrt(Mx * Mx + My * My + Mz * Mz);
+                x[MC_OBS_MZ] = Mz;
+                x[MC_OBS_ABS_MZ] = fabs(Mz);
+                x[MC_OBS_MPAR] = sqrt(Mx * Mx + My * My);
+                x[MC_OBS_E] = s_energy / N;
+                x[MC_OBS_MST] = sqrt(Mh * Mh + Mv * Mv);
+                stripe_obs(x, nh, nv, sm[11], N);
+#pragma unroll
+                for (int o = 0; o < MC_NOBS; ++o) s_x[o] = x[o];
+                hist_push(buf.hist, r, x[MC_OBS_E]);
+            }
+            __syncwarp();
+            if (lane < kNB) {
+                double x[MC_NOBS];
+#pragma unroll
+                for (int o = 0; o < MC_NOBS; ++o) x[o] = s_x[o];
+                obs_push_level(buf.obs[r], x, lane);
+            }
         }
     }
     if (warp == dw && lane == 0 && buf.obs)
