@@ -191,6 +191,8 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
     // permutation schedule at L = 2l: moves pushed, and pair energies tabulated, through
     // the 2 x 2 sub-lattice spectra (table U in place of the quarter of W~)
     constexpr bool SPX = PRE && C == 2;
+    constexpr int kTab = 2 * NB / 4 * NB;   // float4 entries of one block's pair table
+    constexpr int kDecItems = 64;           // of them taken by the decider warp after its decisions
     const int L = cfg.L, l = cfg.l, N = L * L, ll = l * l, B = cfg.B, Sw = B * n;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int r = blockIdx.x;
@@ -482,14 +484,10 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
         // column group g (the four cells D_p of one sub-step) as one float4: W~ between the
         // cells of the two sub-steps' offsets from U (four loads and one inverse 2 x 2
         // transform), the exchange as in pair_energy
-        auto etab_item = [&](int nb, int it) {
-            float *etf = reinterpret_cast<float *>(etab + (nb & 1) * (2 * NB / 4) * NB);
+        auto etab_item = [&](int nb, int it) -> float4 {
             const int g = it / NB, i = it - g * NB, ui = i / n, Di = i - ui * n;
             const bool prevb = g < G;
-            if (prevb ? nb == 0 : (g - G) >= ui) {
-                reinterpret_cast<float4 *>(etf)[it] = make_float4(0.f, 0.f, 0.f, 0.f);
-                return;
-            }
+            if (prevb ? nb == 0 : (g - G) >= ui) return make_float4(0.f, 0.f, 0.f, 0.f);
             const int jr = nb * G + ui, jc = prevb ? (nb - 1) * G + g : nb * G + (g - G);
             const int orr = wxy[n * jr], oc = wxy[n * jc];
             const UFold f = u_fold(l, (orr & 0xFFFF) - (oc & 0xFFFF), ((orr >> 16) & 0x7FFF) - ((oc >> 16) & 0x7FFF));
@@ -531,10 +529,10 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
                 float t = v[0]; v[0] = v[2]; v[2] = t;
                 t = v[1]; v[1] = v[3]; v[3] = t;
             }
-            reinterpret_cast<float4 *>(etf)[it] = make_float4(v[0], v[1], v[2], v[3]);
+            return make_float4(v[0], v[1], v[2], v[3]);
         };
         if constexpr (SPX) {
-            for (int it = tid; it < 2 * NB / 4 * NB; it += kWThreads) etab_item(0, it);
+            for (int it = tid; it < kTab; it += kWThreads) etab[it] = etab_item(0, it);
         } else {
             etab_fill(0, tid, kWThreads);
         }
@@ -656,6 +654,10 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
                 if (bk + 1 < nblk) {
                     __syncwarp();   // this block's spins before the next block's neighbour sums
                     dec_prefetch(bk + 1);
+                    // SPX: items 0..kDecItems-1 of block b+1's pair table (the helpers take the rest)
+                    if constexpr (SPX)
+#pragma unroll
+                        for (int it = lane; it < kDecItems; it += 32) etab[((bk + 1) & 1) * kTab + it] = etab_item(bk + 1, it);
                 }
             } else if (!idle) {
                 const int nprev = bk > 0 ? s_nmv[prv] : 0;
@@ -705,10 +707,10 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
                             }
                         }
                     }
-                    // block b+1's pair energies on the helper threads from the last down
+                    // block b+1's pair energies 32.. on the helper threads from the last down
                     // (their pushes are the fewest)
-                    const int it = ht - (kH - 2 * NB / 4 * NB);
-                    if (bk + 1 < nblk && it >= 0) etab_item(bk + 1, it);
+                    const int it = ht - (kH - kTab);
+                    if (bk + 1 < nblk && it >= kDecItems) etab[((bk + 1) & 1) * kTab + it] = etab_item(bk + 1, it);
                 } else {
                 // push the moves of block b-1 into the dE of the sites of blocks >= b+1
                 if (nprev > 0) {
