@@ -933,20 +933,27 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
         // ---- spectra of the window's offsets after its moves, S'[r][kappa][a][e'] (bf16 hi/lo)
         const int lsq = l * l;
         __nv_bfloat16 *hi = buf.spins_hi + (size_t)r * 12 * lsq, *lo = buf.spins_lo + (size_t)r * 12 * lsq;
-        for (int task = tid; task < 12 * (Sw >> 2); task += kWThreads) {
-            const int j = task / 12, ka = task - 12 * j, kap = ka / 3, aa = ka - 3 * kap;
+        // a thread per offset j and frequency kappa: its three components
+        for (int task = tid; task < 4 * (Sw >> 2); task += kWThreads) {
+            const int j = task >> 2, kap = task & 3;
             const int o = wxy[4 * j], ox = o & 0xFFFF, oy = (o >> 16) & 0x7FFF;
-            float v = 0.0f;
+            float v[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
             for (int D = 0; D < 4; ++D) {
                 const float4 sv = s4[(oy + l * (D >> 1)) * L + ox + l * (D & 1)];
-                const float x = aa == 0 ? sv.x : aa == 1 ? sv.y : sv.z;
-                v += (((kap & 1) * (D & 1) + (kap >> 1) * (D >> 1)) & 1) ? -x : x;
+                const bool neg = ((kap & 1) * (D & 1) + (kap >> 1) * (D >> 1)) & 1;
+                v[0] += neg ? -sv.x : sv.x;
+                v[1] += neg ? -sv.y : sv.y;
+                v[2] += neg ? -sv.z : sv.z;
             }
-            const size_t idx = (size_t)(kap * 3 + aa) * lsq + oy * l + (l - 1 - ox);
-            const __nv_bfloat16 h16 = __float2bfloat16_rn(v);
-            hi[idx] = h16;
-            lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h16));
+            const size_t e = (size_t)oy * l + (l - 1 - ox);
+#pragma unroll
+            for (int aa = 0; aa < 3; ++aa) {
+                const size_t idx = (size_t)(kap * 3 + aa) * lsq + e;
+                const __nv_bfloat16 h16 = __float2bfloat16_rn(v[aa]);
+                hi[idx] = h16;
+                lo[idx] = __float2bfloat16_rn(v[aa] - __bfloat162float(h16));
+            }
         }
     }
     // ---- exact energy change of the window: accepted dE plus, per sub-step, the
