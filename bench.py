@@ -136,15 +136,15 @@ class ClockSampler:
 
 def window_sites(B_set=0):
     """Sites per window: B_set sub-steps if given, else the library's default for
-    the tensor path at L = 64, l = 32 (n = 4): the largest power of two B dividing
-    l^2 with 4B <= 256 and 4B a multiple of 128."""
+    the tensor path at L = 64, l = 32 (n = 4, cell-grid spectra up to 512 sites):
+    the largest power of two B dividing l^2 with 4B <= 512 and 4B a multiple of 128."""
     n = (L // l) ** 2
     if B_set:
         return B_set * n
     best = 0
     B = 1
     while B <= l * l:
-        if (l * l) % B == 0 and B * n <= 256 and (B * n) % 128 == 0:
+        if (l * l) % B == 0 and B * n <= 512 and (B * n) % 128 == 0:
             best = B
         B *= 2
     return best * n
@@ -665,10 +665,10 @@ def main():
             fl = flops_per_update * Sw * R            # one launch: stale field of Sw sites x R replicas
             ach = fl / sec / 1e12
             pk = peaks.get("bf16_tflops_sustained", 1351.5)
-            # MMA work the kernel issues: for L = 2l and 256-site windows the library
+            # MMA work the kernel issues: for L = 2l and 256- or 512-site windows the library
             # contracts cell-grid spectra (rows 3 Sw, K = L^2 / 2); otherwise Toeplitz
             # rows (5 Sw L^2 multiply-adds per replica); three BF16 products each
-            spectral = L == 2 * l and Sw == 256
+            spectral = L == 2 * l and Sw in (256, 512)
             issued = (3 * Sw * (L * L // 2) if spectral else 5 * Sw * L * L) * R * 2 * 3
             rl[k] = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
                      "operands": "cell-grid spectra" if spectral else "Toeplitz rows",

@@ -219,16 +219,20 @@ void clear_timing(mc_lattice *p) {
 }
 
 // Sub-steps per window: the given B, else the largest power of two dividing l^2
-// with B*n <= 512 (tensor path: <= 256, and a multiple of 128).  The in-window
-// pushes grow with B*n per site while the per-window costs shrink; at L = 64,
-// l = 32 the tensor path is fastest with 256-site windows.
+// with B*n <= 512 (tensor path: a multiple of 128, and <= 256 unless the cell-grid
+// spectra serve 512 sites with two sub-step CTAs per SM).  The in-window pushes grow
+// with B*n per site while the per-window costs shrink; at L = 64, l = 32 the tensor
+// path is fastest with 512-site windows (50.7 against 53.5 ms per 100 sweeps of
+// 256 replicas).
 int window_of(const mc_lattice *p, bool tensor) {
     const int ll = p->l * p->l, n = p->n();
     if (p->window_B > 0) return p->window_B;
+    const int cap = (!tensor || (tc_spec2_supported(p->L, p->l, 512) &&
+                                 window_smem_bytes(p->L, 512, n) <= kWindowSmemTwoCtas)) ? 512 : 256;
     int best = 0;
     for (int B = 1; B <= ll; B <<= 1) {
         if (ll % B) continue;
-        if (B * n > (tensor ? 256 : 512)) break;
+        if (B * n > cap) break;
         if (tensor && (B * n) % 128) continue;
         best = B;
     }
@@ -358,7 +362,7 @@ int ensure_tensor_buffers(mc_lattice *p, int Sw, cudaStream_t st) {
         CKA(cudaMalloc(&p->err_flag, sizeof(int)));
         CKA(cudaMemset(p->err_flag, 0, sizeof(int)));
     }
-    // operand tables: the Toeplitz copies of W~, or for L = 2l with a 256-site window the
+    // operand tables: the Toeplitz copies of W~, or for L = 2l with a 256- or 512-site window the
     // signed spectra of W~ over the 2 x 2 cell grid (the lattice keeps one kind)
     const bool spec2 = tc_spec2_supported(p->L, p->l, Sw);
     if (!p->wsh) CKA(cudaMalloc(&p->wsh, sizeof(__nv_bfloat16) * std::max(tc_wsh_elems(p->L), tc_t2_elems(p->l))));

@@ -365,13 +365,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a,
                 const int kk = (u.kb_begin + i) * kKB;
                 int kofs;
                 if (a.spec2) {
-                    // spectra [kappa][a][e']: in-plane tiles are kappa = mtile, zz tiles a kappa pair
-                    const int lsq = N >> 2;
+                    // spectra [kappa][a][e']: in-plane rows kappa*2B + b*B + j and zz rows
+                    // (kappa/2)*2B + (kappa%2)*B + j, B = S_w/4, so a 128-row tile holds one
+                    // kappa (in-plane; 2B/128 tiles a kappa) or lies in one kappa pair (zz)
+                    const int lsq = N >> 2, B4 = Sw >> 2;
                     if (!zz) {
-                        kofs = u.mtile * 3 * lsq + kk;
+                        kofs = (u.mtile * 128 / (2 * B4)) * 3 * lsq + kk;
                     } else {
-                        const int part = kk >= lsq;
-                        kofs = (2 * (u.mtile - 2 * Sw / 128) + part) * 3 * lsq + 2 * lsq + (kk - part * lsq);
+                        const int part = kk >= lsq, pair = (u.mtile - 2 * Sw / 128) * 128 / (2 * B4);
+                        kofs = (2 * pair + part) * 3 * lsq + 2 * lsq + (kk - part * lsq);
                     }
                 } else {
                     kofs = (zz ? 2 * N : 0) + kk;
@@ -540,7 +542,7 @@ size_t tc_wsh_elems(int L) { return (size_t)8 * 4 * 2 * L * 2 * L; }
 
 size_t tc_t2_elems(int l) { return (size_t)8 * 4 * 4 * 2 * 2 * l * 2 * l; }
 
-bool tc_spec2_supported(int L, int l, int Sw) { return L == 2 * l && l % 8 == 0 && Sw == 256; }
+bool tc_spec2_supported(int L, int l, int Sw) { return L == 2 * l && l % 8 == 0 && (Sw == 256 || Sw == 512); }
 
 cudaError_t launch_build_t2(int L, const double *W64, __nv_bfloat16 *t2, cudaStream_t st) {
     const int l = L / 2;
@@ -579,7 +581,10 @@ int tc_plan(int L, int Sw, int R, int nsm, TcUnit *units, int max_units, int *NT
     const int mt_inplane = 2 * Sw / 128, mt_zz = Sw / 128;
     // K per tile: Toeplitz rows contract (a, m) over 2N (in-plane) or N (zz); spectra
     // contract (a, e') or (kappa pair, e') over 2 l^2 = N / 2
-    const int kb_inplane = spec2 ? N / 2 / kKB : 2 * N / kKB, kb_zz = spec2 ? N / 2 / kKB : N / kKB;
+    // (a spectra zz tile of a 512-site window holds one kappa, B = S_w/4 >= 128 rows: only its
+    // half of the pair's K range, kappa % 2, is nonzero)
+    const bool zz_one = spec2 && Sw / 4 >= 128;
+    const int kb_inplane = spec2 ? N / 2 / kKB : 2 * N / kKB, kb_zz = spec2 ? (zz_one ? N / 4 : N / 2) / kKB : N / kKB;
     const long long total = (long long)ntiles * (mt_inplane * kb_inplane + mt_zz * kb_zz);
     // smallest K-blocks per unit whose units (rounded up per tile) fit one wave
     int kbpu = (int)((total + nsm - 1) / nsm);
@@ -599,12 +604,13 @@ int tc_plan(int L, int Sw, int R, int nsm, TcUnit *units, int max_units, int *NT
         for (int mt = 0; mt < mtiles; ++mt) {
             tile_first[nt * mtiles + mt] = nu;
             const int nkb = mt < mt_inplane ? kb_inplane : kb_zz;
+            const int kb0 = (mt >= mt_inplane && zz_one) ? ((mt - mt_inplane) & 1) * kb_zz : 0;
             for (int kb = 0; kb < nkb; kb += kbpu) {
                 if (nu >= max_units) return -1;
                 units[nu].mtile = mt;
                 units[nu].ntile = nt;
-                units[nu].kb_begin = kb;
-                units[nu].kb_end = kb + kbpu < nkb ? kb + kbpu : nkb;
+                units[nu].kb_begin = kb0 + kb;
+                units[nu].kb_end = kb0 + (kb + kbpu < nkb ? kb + kbpu : nkb);
                 ++nu;
             }
         }

@@ -39,7 +39,7 @@ struct TcFieldArgs {
 };
 
 size_t tc_wsh_elems(int L);
-// Spectral operand mode (L = 2l, l % 8 == 0, a 256-site window).
+// Spectral operand mode (L = 2l, l % 8 == 0, a 256- or 512-site window).
 bool tc_spec2_supported(int L, int l, int Sw);
 size_t tc_t2_elems(int l);
 // t2[c][kappa][comp][sy][hl][dy][i]: bf16 hi/lo of the signed, doubled spectrum of W~

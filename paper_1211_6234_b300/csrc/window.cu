@@ -199,8 +199,9 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
 
     extern __shared__ float4 smem_w[];
     const int hq = (L >> 1) + 1;
-    float4 *s4 = smem_w;                                 // [N] spins
-    float4 *hcur = s4 + N;                               // [Sw] !PRE: field of the window sites (stale + pushed moves)
+    float *sxyz = reinterpret_cast<float *>(smem_w);     // [3][N] spins (x, y, z planes)
+    float4 *hcur = reinterpret_cast<float4 *>(sxyz + 3 * N);   // [Sw] !PRE: field of the window sites
+                                                         // (stale + pushed moves); 3N floats keep it 16-byte aligned (N % 4 == 0)
     float *dacc = reinterpret_cast<float *>(hcur);       // PRE: [Sw] dE so far, without exchange and block pairs
     float4 *pS = hcur + Sw;                              // [Sw] proposal S, threshold -T ln u; after the decision w = dE
     float4 *pd = pS + Sw;                                // [Sw] delta = S - s, field-free part of dE
@@ -223,11 +224,17 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
     const uint2 key = cfg.key;
     const uint32_t t = cfg.t_dev ? *cfg.t_dev + (uint32_t)cfg.it : cfg.t;
     const int k0 = cfg.w * B;
+    auto spin = [&](int q) -> float3 { return make_float3(sxyz[q], sxyz[N + q], sxyz[2 * N + q]); };
+    auto set_spin = [&](int q, float a, float b, float c) {
+        sxyz[q] = a;
+        sxyz[N + q] = b;
+        sxyz[2 * N + q] = c;
+    };
     const float W0xx = __ldg(buf.W32), W0xy = __ldg(buf.W32 + N), W0yy = __ldg(buf.W32 + 2 * N), W0zz = __ldg(buf.W32 + 3 * N);
 
     // proposal, delta and the field-free part of dE (anisotropy + self-image) of site q
     auto propose = [&](int q, float u1, float cps, float sps, float4 &S, float4 &D) {
-        const float4 sq = s4[q];
+        const float3 sq = spin(q);
         float S0, S1, S2;
         {
             const float3 Sv = propose_spin(cfg.proposal, cfg.cap_c1, sq.x, sq.y, sq.z, u1, cps, sps);   // Sec. 3.1 proposal
@@ -257,7 +264,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
         const int xm = (qx == 0) ? q + L - 1 : q - 1;
         const int yp = (qy + 1 == L) ? qx : q + L;
         const int ym = (qy == 0) ? q + N - L : q - L;
-        const float4 a = s4[xp], bb = s4[xm], c = s4[yp], dd = s4[ym];
+        const float3 a = spin(xp), bb = spin(xm), c = spin(yp), dd = spin(ym);
         return make_float3((a.x + bb.x) + (c.x + dd.x), (a.y + bb.y) + (c.y + dd.y), (a.z + bb.z) + (c.z + dd.z));
     };
 
@@ -340,7 +347,8 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
     };
     for (int s = tid; s < Sw; s += kWThreads) wxy[s] = window_site_xy(l, C, key, t, cfg.schedule, rk, k0, s);
     // stale_mode 3: warp mt sums M-tile mt of this replica's column over the tile's units
-    // (six M-tiles of 128 rows); the work plan is fixed when the buffers are set up
+    // (3 S_w / 128 M-tiles of 128 rows: six, or twelve at 512 sites); the work plan is
+    // fixed when the buffers are set up
     const int st_mt = warp, st_f = lane;
     int st_u0 = 0, st_cnt = 0;
     if (cfg.stale_mode == 3 && st_mt < cfg.mtiles) {
@@ -365,11 +373,11 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
     }
     const float *gs = buf.spins + (size_t)r * 3 * N;
 #pragma unroll 8
-    for (int q = tid; q < N; q += kWThreads) s4[q] = make_float4(gs[q], gs[N + q], gs[2 * N + q], 0.0f);
+    for (int i = tid; i < 3 * N / 4; i += kWThreads) smem_w[i] = reinterpret_cast<const float4 *>(gs)[i];
     if (cfg.stale_mode == 3) {
         // split-K sums in unit order (the tensor-core field's reduction) into rs[row]
-        // (scratch in the pair-table space, which is filled later)
-        float *rs = reinterpret_cast<float *>(etab);
+        // (scratch in the proposals' space, which is filled later: 3 S_w rows <= 4 S_w floats)
+        float *rs = reinterpret_cast<float *>(pS);
         if (st_on) {
             float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
@@ -395,6 +403,28 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
                     }
             }
             reinterpret_cast<float4 *>(rs)[st_mt * 32 + st_f] = h;
+        }
+        // M-tiles beyond the eight warps (512-site windows: twelve): warp mt takes mt + 8, ...
+        for (int mt = st_mt + kWThreads / 32; mt < cfg.mtiles; mt += kWThreads / 32) {
+            const int nt = r / cfg.NT, col = r - nt * cfg.NT;
+            const int u0 = buf.tile_first[nt * cfg.mtiles + mt], cnt = buf.tile_first[nt * cfg.mtiles + mt + 1] - u0;
+            const float4 *pm = reinterpret_cast<const float4 *>(buf.part + ((size_t)u0 * cfg.NT + col) * 128) + st_f;
+            float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int j0 = 0; j0 < cnt; j0 += 8) {
+                float4 v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    v[j] = (j0 + j < cnt) ? __ldcg(pm + (size_t)(j0 + j) * ustride) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (j0 + j < cnt) {
+                        h.x += v[j].x;
+                        h.y += v[j].y;
+                        h.z += v[j].z;
+                        h.w += v[j].w;
+                    }
+            }
+            reinterpret_cast<float4 *>(rs)[mt * 32 + st_f] = h;
         }
         __syncthreads();
         // rows kappa*2B + b*B + j (b = x, y) and 2 S_w + (kappa/2)*2B + (kappa%2)*B + j (z), B = S_w/4
@@ -623,7 +653,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
                 if (act) {
                     reinterpret_cast<float *>(pS + s)[3] = dE;
                     if (acc) {
-                        s4[q] = make_float4(S.x, S.y, S.z, 0.0f);
+                        set_spin(q, S.x, S.y, S.z);
                         wxy[s] = xy | (int)0x80000000;
                         if constexpr (!SPX)
                             s_mvb[cur * NB + __popc(am & ((1u << lane) - 1u))] = make_float4(D.x, D.y, D.z, __int_as_float(xy));
@@ -863,7 +893,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
                             tr[7] = S.x; tr[8] = S.y; tr[9] = S.z;
                         }
                         if (accept) {
-                            s4[q] = make_float4(S.x, S.y, S.z, 0.0f);
+                            set_spin(q, S.x, S.y, S.z);
                             wxy[s] = xy | (int)0x80000000;             // accepted
                         }
                         // the move (for the block's later sub-steps and the window-end bookkeeping)
@@ -913,7 +943,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
         const int xy = wxy[s];
         if (xy >= 0) continue;
         const int q = ((xy >> 16) & 0x7FFF) * L + (xy & 0xFFFF);
-        const float4 v = s4[q];
+        const float3 v = spin(q);
         gd[q] = v.x;
         gd[N + q] = v.y;
         gd[2 * N + q] = v.z;
@@ -940,7 +970,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
             float v[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
             for (int D = 0; D < 4; ++D) {
-                const float4 sv = s4[(oy + l * (D >> 1)) * L + ox + l * (D & 1)];
+                const float3 sv = spin((oy + l * (D >> 1)) * L + ox + l * (D & 1));
                 const bool neg = ((kap & 1) * (D & 1) + (kap >> 1) * (D >> 1)) & 1;
                 v[0] += neg ? -sv.x : sv.x;
                 v[1] += neg ? -sv.y : sv.y;
@@ -1034,9 +1064,9 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
         double *gt = buf.theta2 ? buf.theta2 + (size_t)r * N : nullptr;
 #pragma unroll 4
         for (int i = tid; i < N; i += kWThreads) {
-            const float4 a = s4[i];
+            const float3 a = spin(i);
             const int iy = i / L, ix = i - iy * L;
-            const float4 ax = s4[iy * L + (ix + 1 == L ? 0 : ix + 1)], ay = s4[(iy + 1 == L ? 0 : iy + 1) * L + ix];
+            const float3 ax = spin(iy * L + (ix + 1 == L ? 0 : ix + 1)), ay = spin((iy + 1 == L ? 0 : iy + 1) * L + ix);
             mv_[0] += a.x;
             mv_[1] += a.y;
             mv_[2] += a.z;
@@ -1150,8 +1180,8 @@ size_t wq_table_elems(int L) {
 size_t window_smem_bytes(int L, int Sw, int n) {
     const size_t N = (size_t)L * L;
     // blocks of kBlockSites sites (n <= kBlockSites)
-    return sizeof(float4) * (N + 3 * (size_t)Sw + (size_t)wtab_smem_elems(L, n) + 2 * kBlockSites +
-                             kBlockSites * kBlockSites) +
+    return sizeof(float) * 3 * N +
+           sizeof(float4) * (3 * (size_t)Sw + (size_t)wtab_smem_elems(L, n) + 2 * kBlockSites + kBlockSites * kBlockSites) +
            sizeof(int) * (size_t)Sw;
 }
 

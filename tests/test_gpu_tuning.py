@@ -63,11 +63,14 @@ def test_warp_layouts_give_identical_trajectories(dipmc):
 
 
 @pytest.mark.parametrize("tuning", [{"tc_kblocks": 2}, {"tc_kblocks": 8, "tc_ntile": 128},
-                                    {"tc_ntile": 64, "steps_layout": 2}, {"tc_kblocks": 12, "steps_layout": 1}],
-                         ids=["kb2", "kb8_nt128", "nt64_layout2", "kb12_layout1"])
+                                    {"tc_ntile": 64, "steps_layout": 2}, {"tc_kblocks": 12, "steps_layout": 1},
+                                    {"window": 128}, {"window": 128, "tc_ntile": 128, "steps_layout": 1}],
+                         ids=["kb2", "kb8_nt128", "nt64_layout2", "kb12_layout1", "win512", "win512_nt128_layout1"])
 def test_tile_shapes_match_oracle(dipmc, tuning):
     """One traced sweep of 256 replicas of L = 64, l = 32 under a given split-K
-    shape / N-tile / layout: sampled replicas of every N-tile against the oracle."""
+    shape / N-tile / layout / window (128 sub-steps: 512-site windows, twelve
+    M-tiles of cell-grid spectra): sampled replicas of every N-tile against the
+    oracle."""
     L, l, R = 64, 32, 256
     lad, s0, tr, sg, _ = _run(dipmc, L, l, R, tuning, 1, trace=True, seed=1)
     W = orc.wtilde(L, 16, True)
