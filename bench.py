@@ -668,8 +668,10 @@ def main():
             # MMA work the kernel issues: for L = 2l and 256- or 512-site windows the library
             # contracts cell-grid spectra (rows 3 Sw, K = L^2 / 2); otherwise Toeplitz
             # rows (5 Sw L^2 multiply-adds per replica); three BF16 products each
+            # (512-site windows: a zz tile holds one kappa and contracts only its half, L^2 / 4)
             spectral = L == 2 * l and Sw in (256, 512)
-            issued = (3 * Sw * (L * L // 2) if spectral else 5 * Sw * L * L) * R * 2 * 3
+            k_zz = L * L // 4 if Sw >= 512 else L * L // 2
+            issued = ((2 * Sw * (L * L // 2) + Sw * k_zz) if spectral else 5 * Sw * L * L) * R * 2 * 3
             rl[k] = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
                      "operands": "cell-grid spectra" if spectral else "Toeplitz rows",
                      "issued_tflops": issued / sec / 1e12, "issued_frac": issued / sec / 1e12 / pk,
