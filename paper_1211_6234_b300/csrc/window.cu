@@ -11,10 +11,12 @@
 // This is the same field the direct path computes, up to rounding.
 //
 // k_window_steps: one CTA (8 warps) per replica.  Spins live in shared memory
-// for the window; warp 0 takes the decisions of blocks of 16 sites on its own;
-// warps 1..7 push older moves into the window's later sites.  Under the
-// permutation schedule a site's proposal is fixed at the window's start, so what
-// the decider adds per sub-step is a sum of precomputed scalar pair energies.
+// for the window (three planes); warp 0 takes the decisions of blocks of 16 sites
+// on its own; warps 1..7 push older moves into the window's later sites.  Under
+// the permutation schedule a site's proposal is fixed at the window's start, so
+// what the decider adds per sub-step is a sum of precomputed scalar pair energies;
+// at L = 2l the pushes and the pair energies go through the 2 x 2 sub-lattice
+// spectra of the moves and of W~ (the four cells o + l D of a sub-step's offset o).
 #include <cuda_bf16.h>
 
 #include "internal.cuh"
