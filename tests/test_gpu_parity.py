@@ -387,6 +387,8 @@ WCASES = [
     (64, 32, 2, 128, 0, 1),    # L = 64, S_w = 512 on both paths
     (80, 40, 2, 0, 0, 1),      # non-power-of-two L = 80: spectral operands (L = 2l, l % 8 == 0)
     (80, 20, 1, 0, 0, 1),      # L = 80, 16 sites per sub-step: Toeplitz operands at a large lattice
+    (12, 6, 2, 12, 0, 2),      # l = 6: the 2 x 2 spectra's folds at odd l/2 = 3 (F32 only)
+    (20, 10, 2, 20, 0, 2),     # l = 10: odd l/2 = 5 (F32 only)
 ]
 
 
@@ -394,7 +396,7 @@ WCASES = [
 @pytest.mark.parametrize("case", WCASES, ids=[f"L{c[0]}_l{c[1]}_R{c[2]}_B{c[3]}_s{c[4]}" for c in WCASES])
 def test_window_paths_match_oracle(dipmc, path, case):
     L, l, R, B, schedule, nsw = case
-    if path == 3 and B == 16:
+    if path == 3 and B in (12, 16, 20):
         pytest.skip("the tensor path needs windows of a multiple of 128 sites")
     params = [(F32(1.0), F32(0.1), F32(0.8), F32(0.0), F32(0.6)),
               (F32(0.7), F32(0.3), F32(0.5), F32(-0.2), F32(1.1)),
