@@ -210,6 +210,20 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
 #pragma unroll
             for (int c = 0; c < 4; ++c) w[j][D][c] = valid ? W32[c * N + idx] : 0.0f;
         }
+        if constexpr (C == 2) {
+            // at C = 2 the field of cell d from the four cells m of offset o + e is the XOR
+            // convolution sum_m W~(l (d xor m) - e) s_m, which the 2 x 2 Walsh-Hadamard
+            // transform diagonalises: keep the slices' transform T(kappa) = sum_D (-1)^(kappa.D) W(D)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float a = w[j][0][c] + w[j][1][c], b = w[j][0][c] - w[j][1][c];
+                const float cc = w[j][2][c] + w[j][3][c], dd = w[j][2][c] - w[j][3][c];
+                w[j][0][c] = a + cc;
+                w[j][1][c] = b + dd;
+                w[j][2][c] = a - cc;
+                w[j][3][c] = b - dd;
+            }
+        }
     }
 
     const int hbits = ceil_log2_u((uint32_t)l);
@@ -302,10 +316,41 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
                     c_q[lane] = q;
                 }
             } else {
-                // ---- field warps: partial fields at the n update sites
+                // ---- field warps: partial fields at the n update sites (C = 2: their
+                // 2 x 2 transform H(kappa) = sum_e T_e(kappa) S_e(kappa), inverted by the
+                // control warp)
                 float acc[n][3];
 #pragma unroll
                 for (int d = 0; d < n; ++d) acc[d][0] = acc[d][1] = acc[d][2] = 0.0f;
+                if constexpr (C == 2) {
+#pragma unroll
+                    for (int j = 0; j < EPT; ++j) {
+                        const int bx = ox + ex[j], by = oy + ey[j];
+                        float3 sm[4];
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) {
+                            int xx = bx + l * (m & 1), yy = by + l * (m >> 1);
+                            if (xx >= L) xx -= L;
+                            if (yy >= L) yy -= L;
+                            const float4 v = s4[yy * L + xx];
+                            sm[m] = make_float3(v.x, v.y, v.z);
+                        }
+                        const float3 a = make_float3(sm[0].x + sm[1].x, sm[0].y + sm[1].y, sm[0].z + sm[1].z);
+                        const float3 b = make_float3(sm[0].x - sm[1].x, sm[0].y - sm[1].y, sm[0].z - sm[1].z);
+                        const float3 cc = make_float3(sm[2].x + sm[3].x, sm[2].y + sm[3].y, sm[2].z + sm[3].z);
+                        const float3 dd = make_float3(sm[2].x - sm[3].x, sm[2].y - sm[3].y, sm[2].z - sm[3].z);
+                        const float3 S[4] = {make_float3(a.x + cc.x, a.y + cc.y, a.z + cc.z),
+                                             make_float3(b.x + dd.x, b.y + dd.y, b.z + dd.z),
+                                             make_float3(a.x - cc.x, a.y - cc.y, a.z - cc.z),
+                                             make_float3(b.x - dd.x, b.y - dd.y, b.z - dd.z)};
+#pragma unroll
+                        for (int kap = 0; kap < 4; ++kap) {
+                            acc[kap][0] = fmaf(w[j][kap][0], S[kap].x, fmaf(w[j][kap][1], S[kap].y, acc[kap][0]));
+                            acc[kap][1] = fmaf(w[j][kap][1], S[kap].x, fmaf(w[j][kap][2], S[kap].y, acc[kap][1]));
+                            acc[kap][2] = fmaf(w[j][kap][3], S[kap].z, acc[kap][2]);
+                        }
+                    }
+                } else {
 #pragma unroll
                 for (int j = 0; j < EPT; ++j) {
                     const int bx = ox + ex[j], by = oy + ey[j];
@@ -330,6 +375,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
                                 }
                         }
                     }
+                }
                 }
 #pragma unroll
                 for (int g = 0; g < G; ++g) {
@@ -358,6 +404,20 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
                     hsum[g] = s;
                 }
                 float h[3];
+                if constexpr (C == 2) {
+                    // cell d = lane: h = (1/4) sum_kappa (-1)^(kappa.d) H(kappa); H(kappa) sits at 3 kappa + c
+                    const int d = lane & 3;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        float val = 0.0f;
+#pragma unroll
+                        for (int kap = 0; kap < 4; ++kap) {
+                            const float Hk = __shfl_sync(0xffffffffu, hsum[0], 3 * kap + c);
+                            val += (__popc(kap & d) & 1) ? -Hk : Hk;
+                        }
+                        h[c] = 0.25f * val;
+                    }
+                } else {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     const int vi = 3 * (lane < n ? lane : 0) + c;
@@ -368,6 +428,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
                         if ((vi >> 5) == g) val = t2;
                     }
                     h[c] = val;
+                }
                 }
                 int accept = 0;
                 if (lane < n) {
