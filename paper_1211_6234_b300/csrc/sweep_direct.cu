@@ -110,6 +110,11 @@ __device__ void obs_push(ObsAcc &A, const double x[MC_NOBS]) {
     }
 }
 
+// Sites whose proposals the permutation schedule draws together (all threads, at the start
+// of every batch of sub-steps): a site is visited once per sweep, so its proposal depends
+// only on its spin at the sweep's start.
+constexpr int kPropBatch = 128;
+
 template <int C, int EPT, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig cfg, const SweepBuffers buf) {
     constexpr int n = C * C;
@@ -158,6 +163,13 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
     float *mred = red + NWF * V;                                  // [NW][12] magnetisation, staggered and wall sums
     float *wl = mred + NW * 12;                                   // [n][4] W~(l*D), D in [0,C)^2
     uint16_t *sched = reinterpret_cast<uint16_t *>(wl + n * 4);   // [ll] offsets of the sweep
+    // [kPropBatch] proposals of a batch (schedule 0): (S, threshold), (delta, anisotropy +
+    // self-image part of dE), the acceptance uniform; 16-byte aligned after the schedule
+    const size_t pb_off = ((size_t)(reinterpret_cast<char *>(sched + ll) - reinterpret_cast<char *>(smem_f4)) + 15) & ~(size_t)15;
+    float4 *pbS = reinterpret_cast<float4 *>(reinterpret_cast<char *>(smem_f4) + pb_off);
+    float4 *pbX = pbS + kPropBatch;
+    float *pbU = reinterpret_cast<float *>(pbX + kPropBatch);
+    constexpr int KB = kPropBatch / n;                             // sub-steps per batch
     __shared__ ObsAcc acc_s;
     __shared__ double e_track_s;
     // control-warp state kept in shared memory so that it does not occupy
@@ -249,6 +261,27 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
         __syncwarp();
     };
 
+    // Sec. 3.1 proposal of site q at sub-step kk of sweep t: the new spin and its delta,
+    // the threshold -T ln u, the uniform u, and the field- and exchange-free part of dE
+    // (anisotropy and the self-image term)
+    auto proposal = [&](int q, int kk, uint32_t t, float3 &Sn, float3 &dS, float &thr, float &uacc, float &part) {
+        const RepParams &P = c_P;
+        const uint4 wds = philox(make_uint4((uint32_t)q, rid, t, ((uint32_t)kk & 0x00FFFFFFu) | kTagAttempt), key);
+        const float u1 = u24f(wds.x);
+        float sps, cps;
+        sincospif(2.0f * u24f(wds.y), &sps, &cps);
+        uacc = u24f(wds.z);
+        const float4 sq = s4[q];
+        Sn = propose_spin(cfg.proposal, cfg.cap_c1, sq.x, sq.y, sq.z, u1, cps, sps);
+        dS = make_float3(Sn.x - sq.x, Sn.y - sq.y, Sn.z - sq.z);
+        const float z0 = sq.z * sq.z, z1 = Sn.z * Sn.z;
+        const float dan = (-P.K2 * z1 - P.K4 * z1 * z1) - (-P.K2 * z0 - P.K4 * z0 * z0);
+        const float self = c_W0[0] * dS.x * dS.x + 2.0f * c_W0[1] * dS.x * dS.y + c_W0[2] * dS.y * dS.y + c_W0[3] * dS.z * dS.z;
+        part = dan + 0.5f * P.CD * self;
+        // accept iff u < exp(-dE/T)  <=>  dE < -T ln u   (u = 0: always)
+        thr = (uacc > 0.0f) ? -P.T * logf(uacc) : INFINITY;
+    };
+
     for (int it = 0; it < nsw; ++it) {
         const uint32_t t = t0 + (uint32_t)it;
         // ---- the sweep's schedule
@@ -268,6 +301,22 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
         __syncthreads();
 
         for (int k = 0; k < ll; ++k) {
+            if (cfg.schedule == 0 && k % KB == 0) {
+                // ---- the proposals of sub-steps k .. k+KB-1, all threads
+                for (int i = tid; i < KB * n; i += NT) {
+                    const int kk = k + i / n, d = i % n;
+                    if (kk >= ll) break;
+                    const int vv = sched[kk];
+                    const int q = ((vv >> 8) + l * (d / C)) * L + (vv & 0xFF) + l * (d % C);
+                    float3 Sn, dS;
+                    float thr, uacc, part;
+                    proposal(q, kk, t, Sn, dS, thr, uacc, part);
+                    pbS[i] = make_float4(Sn.x, Sn.y, Sn.z, thr);
+                    pbX[i] = make_float4(dS.x, dS.y, dS.z, part);
+                    pbU[i] = uacc;
+                }
+                __syncthreads();
+            }
             const int v = sched[k];
             const int ox = v & 0xFF, oy = v >> 8;
             if (warp == 0) {
@@ -281,20 +330,20 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
                     const RepParams &P = c_P;
                     const int qx = ox + l * (lane % C), qy = oy + l * (lane / C);
                     const int q = qy * L + qx;
-                    const uint4 wds = philox(make_uint4((uint32_t)q, rid, t, ((uint32_t)k & 0x00FFFFFFu) | kTagAttempt), key);
-                    const float u1 = u24f(wds.x);
-                    float sps, cps;
-                    sincospif(2.0f * u24f(wds.y), &sps, &cps);
-                    const float uacc = u24f(wds.z);
-                    const float4 sq = s4[q];
-                    float S0, S1, S2;
-                    {
-                        const float3 Sv = propose_spin(cfg.proposal, cfg.cap_c1, sq.x, sq.y, sq.z, u1, cps, sps);   // Sec. 3.1 proposal
-                        S0 = Sv.x;
-                        S1 = Sv.y;
-                        S2 = Sv.z;
+                    float3 Sn, dS;
+                    float thr, uacc, part;
+                    if (cfg.schedule == 0) {
+                        const int i = (k % KB) * n + lane;
+                        const float4 a4 = pbS[i], b4 = pbX[i];
+                        Sn = make_float3(a4.x, a4.y, a4.z);
+                        thr = a4.w;
+                        dS = make_float3(b4.x, b4.y, b4.z);
+                        part = b4.w;
+                        uacc = pbU[i];
+                    } else {
+                        proposal(q, k, t, Sn, dS, thr, uacc, part);
                     }
-                    const float dX = S0 - sq.x, dY = S1 - sq.y, dZ = S2 - sq.z;
+                    // exchange with the current neighbour spins
                     const int xp = (qx + 1 == L) ? q - qx : q + 1;
                     const int xm = (qx == 0) ? q + L - 1 : q - 1;
                     const int yp = (qy + 1 == L) ? qx : q + L;
@@ -303,15 +352,11 @@ __global__ void __launch_bounds__(MAXT, MINB) k_sweep_direct(const SweepConfig c
                     const float n0 = (a.x + b.x) + (c.x + d.x);
                     const float n1 = (a.y + b.y) + (c.y + d.y);
                     const float n2 = (a.z + b.z) + (c.z + d.z);
-                    const float dex = -P.J * (dX * n0 + dY * n1 + dZ * n2);
-                    const float z0 = sq.z * sq.z, z1 = S2 * S2;
-                    const float dan = (-P.K2 * z1 - P.K4 * z1 * z1) - (-P.K2 * z0 - P.K4 * z0 * z0);
-                    const float self = c_W0[0] * dX * dX + 2.0f * c_W0[1] * dX * dY + c_W0[2] * dY * dY + c_W0[3] * dZ * dZ;
-                    c_S[0][lane] = S0; c_S[1][lane] = S1; c_S[2][lane] = S2;
-                    c_d[0][lane] = dX; c_d[1][lane] = dY; c_d[2][lane] = dZ;
-                    c_pre[lane] = dex + dan + 0.5f * P.CD * self;
-                    // accept iff u < exp(-dE/T)  <=>  dE < -T ln u   (u = 0: always)
-                    c_thr[lane] = (uacc > 0.0f) ? -P.T * logf(uacc) : INFINITY;
+                    const float dex = -P.J * (dS.x * n0 + dS.y * n1 + dS.z * n2);
+                    c_S[0][lane] = Sn.x; c_S[1][lane] = Sn.y; c_S[2][lane] = Sn.z;
+                    c_d[0][lane] = dS.x; c_d[1][lane] = dS.y; c_d[2][lane] = dS.z;
+                    c_pre[lane] = dex + part;
+                    c_thr[lane] = thr;
                     c_u[lane] = uacc;
                     c_q[lane] = q;
                 }
@@ -588,7 +633,8 @@ size_t smem_bytes(int L, int l, int threads) {
     const int N = L * L, C = L / l, n = C * C, NW = threads / 32;
     size_t b = sizeof(float4) * (size_t)N + sizeof(float) * (size_t)((NW - 1) * 3 * n + NW * 12 + 4 * n);
     b += sizeof(uint16_t) * (size_t)l * l;
-    return (b + 15) & ~(size_t)15;
+    b = (b + 15) & ~(size_t)15;
+    return b + (size_t)kPropBatch * (2 * sizeof(float4) + sizeof(float));
 }
 
 // Choose the instance.  Many replicas (more than one wave of SMs): prefer two
