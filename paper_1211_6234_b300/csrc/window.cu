@@ -186,7 +186,7 @@ __device__ __forceinline__ float4 w_from_u(const float4 *__restrict__ uq, int l,
 // with-replacement schedule, where a site may recur within a window) each decision
 // proposes from the current spin and pulls the field vector of the block's moves.
 template <int C, bool PRE>
-__global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfig cfg, const WindowBuffers buf) {
+__global__ void __launch_bounds__(2 * kWThreads, 1) k_window_steps(const WindowConfig cfg, const WindowBuffers buf) {
     constexpr int n = C * C;
     constexpr int NB = kBlockSites;   // sites per decider block
     constexpr int G = NB / n;         // sub-steps per block
@@ -196,10 +196,22 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
     constexpr int kTab = 2 * NB / 4 * NB;   // float4 entries of one block's pair table
     constexpr int kDecItems = 64;           // of them taken by the decider warp after its decisions
     const int L = cfg.L, l = cfg.l, N = L * L, ll = l * l, B = cfg.B, Sw = B * n;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int r = blockIdx.x;
+    // two replicas a CTA where shared memory allows (cfg.gpc == 2): replica group g takes the
+    // even or the odd warps, so that each has two SM sub-partitions to itself and its decider
+    // (the group's lowest warp) the first claim on them; below, tid and warp count within the
+    // group (0..255, 0..7), and every barrier is the group's own
+    const int g = cfg.gpc == 2 ? (int)((threadIdx.x >> 5) & 1) : 0;
+    const int tid = cfg.gpc == 2 ? (int)(((threadIdx.x >> 6) << 5) | (threadIdx.x & 31)) : (int)threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int r = cfg.gpc * blockIdx.x + g;
+    if (r >= cfg.R) return;   // the odd group of the last CTA when R is odd (it shares no barrier)
+    auto gsync = [&]() {
+        if (g) asm volatile("bar.sync 2, %0;" ::"n"(kWThreads) : "memory");
+        else asm volatile("bar.sync 1, %0;" ::"n"(kWThreads) : "memory");
+    };
 
-    extern __shared__ float4 smem_w[];
+    extern __shared__ float4 smem_all[];
+    float4 *smem_w = smem_all + (size_t)g * (cfg.smem_group / sizeof(float4));
     const int hq = (L >> 1) + 1;
     float *sxyz = reinterpret_cast<float *>(smem_w);     // [3][N] spins (x, y, z planes)
     float4 *hcur = reinterpret_cast<float4 *>(sxyz + 3 * N);   // [Sw] !PRE: field of the window sites
@@ -217,10 +229,14 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
     float4 *etab = wpair;                                // PRE: [2][2 NB / 4][NB] pair energies by block parity,
                                                          // four columns of a row per float4
     int *wxy = reinterpret_cast<int *>(wpair + NB * NB); // [Sw] site as x | y << 16 (bit 31: accepted)
-    __shared__ int s_nmv[2];
-    __shared__ double s_epart[32];
-    __shared__ double s_energy;   // the tracked energy after this window (measured windows)
-    __shared__ float s_mred[kWThreads / 32][12];
+    __shared__ int s_nmv_g[2][2];
+    __shared__ double s_epart_g[2][32];
+    __shared__ double s_energy_g[2];   // the tracked energy after this window (measured windows)
+    __shared__ float s_mred_g[2][kWThreads / 32][12];
+    int *s_nmv = s_nmv_g[g];
+    double *s_epart = s_epart_g[g];
+    double &s_energy = s_energy_g[g];
+    float(*s_mred)[12] = s_mred_g[g];
 
     const RepParams P = buf.params[r];
     const uint2 key = cfg.key;
@@ -323,7 +339,8 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
     // the tensor table and the window's sites (they depend on the sweep counter
     // only); then the state, stale field and proposals.
     pdl_trigger();
-    __shared__ float4 s_wl[4];   // SPX: W~(l P), P = Px + 2 Py (the cells of one offset)
+    __shared__ float4 s_wl_g[2][4];   // SPX: W~(l P), P = Px + 2 Py (the cells of one offset)
+    float4 *s_wl = s_wl_g[g];
     if (SPX && tid < 4) {
         const int g = l * (tid >> 1) * L + l * (tid & 1);
         s_wl[tid] = make_float4(__ldg(buf.W32 + g), __ldg(buf.W32 + N + g), __ldg(buf.W32 + 2 * N + g),
@@ -428,7 +445,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
             }
             reinterpret_cast<float4 *>(rs)[mt * 32 + st_f] = h;
         }
-        __syncthreads();
+        gsync();
         // rows kappa*2B + b*B + j (b = x, y) and 2 S_w + (kappa/2)*2B + (kappa%2)*B + j (z), B = S_w/4
         const int B4 = Sw >> 2;
         for (int task = tid; task < 3 * B4; task += kWThreads) {
@@ -448,7 +465,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
             }
         }
     }
-    __syncthreads();
+    gsync();
     for (int s = tid; s < Sw; s += kWThreads) {
         const int xy = wxy[s];
         const int q = (xy >> 16) * L + (xy & 0xFFFF);
@@ -474,7 +491,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
         s_nmv[0] = 0;
         s_nmv[1] = 0;
     }
-    __syncthreads();
+    gsync();
 
     long long n_acc = 0;
     const int nblk = B / G;
@@ -568,7 +585,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
         } else {
             etab_fill(0, tid, kWThreads);
         }
-        __syncthreads();
+        gsync();
         // Blocks of G sub-steps (16 sites), one CTA barrier per block.  Warp 0 (the
         // decider) takes block b's decisions: a site's dE is its window-start value, plus
         // the pushed pair energies of the moves of blocks <= b-2, plus those of block b-1
@@ -781,7 +798,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
                 if (bk + 1 < nblk) etab_fill(bk + 1, ht, kH);
                 }
             }
-            __syncthreads();
+            gsync();
         }
     } else {
         // Blocks of G sub-steps (16 sites), two CTA barriers per block.  At the start
@@ -839,7 +856,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
                     hcur[s] = h;
                 }
             }
-            if (G > 1 || nprev > 0) __syncthreads();
+            if (G > 1 || nprev > 0) gsync();
             if (warp == 0) {
                 int ncur = 0;                                    // moves of this block so far (warp-uniform)
                 for (int u = 0; u < G; ++u) {
@@ -934,7 +951,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
                     hcur[s] = h;
                 }
             }
-            __syncthreads();
+            gsync();
         }
     }
 
@@ -1047,7 +1064,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
     if (!PRE)
         for (int off = 16; off; off >>= 1) e_loc += __shfl_xor_sync(0xffffffffu, e_loc, off);
     if (lane == 0) s_epart[warp] = e_loc;
-    __syncthreads();
+    gsync();
     if (tid == 0) {
         double et = 0.0;
         for (int i = 0; i < kWThreads / 32; ++i) et += s_epart[i];
@@ -1061,7 +1078,7 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
         }
     }
     if (cfg.measure) {
-        __syncthreads();
+        gsync();
         float mv_[12] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         double *gt = buf.theta2 ? buf.theta2 + (size_t)r * N : nullptr;
 #pragma unroll 4
@@ -1090,11 +1107,12 @@ __global__ void __launch_bounds__(kWThreads, 2) k_window_steps(const WindowConfi
         if (lane == 0)
 #pragma unroll
             for (int c = 0; c < 12; ++c) s_mred[warp][c] = mv_[c];
-        __syncthreads();
+        gsync();
         // the sample once (FP64 is slow here: lane c sums component c over the warps, lane
         // 0 forms the observables), then lane k < kNB pushes it into binning level k
         if (warp == 0 && buf.obs) {
-            __shared__ double s_sm[12], s_x[MC_NOBS];
+            __shared__ double s_sm_g[2][12], s_x_g[2][MC_NOBS];
+            double *s_sm = s_sm_g[g], *s_x = s_x_g[g];
             if (lane < 12) {
                 double v = 0.0;
                 for (int ww = 0; ww < kWThreads / 32; ++ww) v += s_mred[ww][lane];
@@ -1198,17 +1216,23 @@ bool window_supported(int L, int l, int B) {
     return window_smem_bytes(L, B * C * C, C * C) <= 200 * 1024;
 }
 
-cudaError_t launch_window_steps(const WindowConfig &c, const WindowBuffers &b, cudaStream_t st) {
-    const int C = c.L / c.l;
-    const size_t smem = window_smem_bytes(c.L, c.B * C * C, C * C);
+cudaError_t launch_window_steps(const WindowConfig &c0, const WindowBuffers &b, cudaStream_t st) {
+    const int C = c0.L / c0.l;
+    // two replicas a CTA (one on the even, one on the odd warps) when both fit an SM's shared
+    // memory, else one
+    const size_t group = (window_smem_bytes(c0.L, c0.B * C * C, C * C) + 127) & ~(size_t)127;
+    WindowConfig c = c0;
+    c.gpc = 2 * group <= kWindowSmemTwoGroups ? 2 : 1;
+    c.smem_group = (unsigned)group;
+    const size_t smem = c.gpc * group;
     cudaError_t e;
 #define LAUNCH1(CC, PRE)                                                                             \
     e = cudaFuncSetAttribute(k_window_steps<CC, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
     if (e != cudaSuccess) return e;                                                                  \
     {                                                                                                \
         cudaLaunchConfig_t lc{};                                                                     \
-        lc.gridDim = dim3(c.R);                                                                      \
-        lc.blockDim = dim3(kWThreads);                                                               \
+        lc.gridDim = dim3((c.R + c.gpc - 1) / c.gpc);                                                \
+        lc.blockDim = dim3(kWThreads * c.gpc);                                                       \
         lc.dynamicSmemBytes = smem;                                                                  \
         lc.stream = st;                                                                              \
         cudaLaunchAttribute at[1];                                                                   \

@@ -30,6 +30,8 @@ struct WindowConfig {
                          // (partner warp 6 idle), so that two CTAs sharing an SM decide on
                          // different sub-partitions
     int nsm;             // SMs of the device (layout 2)
+    int gpc;             // replicas a CTA (1 or 2; set by launch_window_steps)
+    unsigned smem_group; // shared-memory bytes of one replica (set by launch_window_steps)
 };
 
 struct WindowBuffers {
@@ -56,6 +58,8 @@ struct WindowBuffers {
 size_t window_smem_bytes(int L, int Sw, int n);
 // Dynamic shared memory of a sub-step CTA that still leaves room for two per SM.
 constexpr size_t kWindowSmemTwoCtas = 112 * 1024;
+// Dynamic shared memory of a CTA that carries two replicas' sub-steps.
+constexpr size_t kWindowSmemTwoGroups = 224 * 1024;
 // float4 entries of the W~ tables of the windowed path: the minimum-image quarter
 // [(L/2+1)^2] and, for even L, after it the table U of the 2 x 2 sub-lattice spectra
 // at l = L/2: U_d(kappa) = sum_P (-1)^(kappa.P) W~(d + l P) for 0 <= dx, dy <= l/2 and
