@@ -691,9 +691,10 @@ def main():
             if wcyc and wcyc["per_block"] > 0:
                 # the bound that governs it: SM cycles per 16-site decision block (live, on the
                 # kernel's own clock counters) against the block of the decider warp's own
-                # decisions alone, 1,163 cycles, measured once on a copy of the kernel with the
-                # helper warps' pushes and every pair-table item removed
-                floor = 1163.0
+                # decisions alone, 1,167 cycles at this workload's 512-site windows and two
+                # replicas a CTA, measured once on a copy of the kernel with the helper warps'
+                # pushes and every pair-table item removed
+                floor = 1167.0
                 rl[k]["latency"] = {"cycles_per_block": wcyc["per_block"], "decider_alone_cycles": floor,
                                     "ratio": wcyc["per_block"] / floor, "setup_cycles": wcyc["setup"],
                                     "tail_cycles": wcyc["tail"], "blocks_per_launch": wcyc["blocks_per_launch"],

@@ -233,6 +233,12 @@ __global__ void __launch_bounds__(2 * kWThreads, 1) k_window_steps(const WindowC
     __shared__ double s_epart_g[2][32];
     __shared__ double s_energy_g[2];   // the tracked energy after this window (measured windows)
     __shared__ float s_mred_g[2][kWThreads / 32][12];
+    // stale_mode 3: one bit per group of 16 cell offsets (one 32-byte sector of a spectra
+    // plane) holding a move accepted in this window; 256 groups cover l <= 64
+    constexpr int kSpecWords = 8;
+    __shared__ uint32_t s_ck_g[2][kSpecWords];
+    uint32_t *s_ck = s_ck_g[g];
+    if (tid < kSpecWords) s_ck[tid] = 0u;
     int *s_nmv = s_nmv_g[g];
     double *s_epart = s_epart_g[g];
     double &s_energy = s_energy_g[g];
@@ -956,10 +962,25 @@ __global__ void __launch_bounds__(2 * kWThreads, 1) k_window_steps(const WindowC
     }
 
     if (tid == 0) cyc2 = clock64();
-    // ---- write the accepted moves back to global memory (FP32 and the bf16 split)
+    // ---- write the accepted moves back to global memory (FP32 and the bf16 split);
+    // stale_mode 3 also marks the offset groups whose spectra change (S_w is a multiple of
+    // 256 there, so every warp runs the loop whole)
     float *gd = buf.spins + (size_t)r * 3 * N;
+    const int nck = (l * l) >> 4;   // stale_mode 3 (l % 8 == 0): groups of 16 offsets
     for (int s = tid; s < Sw; s += kWThreads) {
         const int xy = wxy[s];
+        if (cfg.stale_mode == 3) {
+            int c = -1;
+            if (xy < 0) {
+                const int x = xy & 0xFFFF, y = (xy >> 16) & 0x7FFF;
+                const int ox = x >= l ? x - l : x, oy = y >= l ? y - l : y;
+                c = (oy * l + (l - 1 - ox)) >> 4;
+            }
+            for (int w = 0; w < kSpecWords && 32 * w < nck; ++w) {
+                const uint32_t m = __reduce_or_sync(0xffffffffu, (c >> 5) == w ? 1u << (c & 31) : 0u);
+                if (lane == 0 && m) atomicOr(&s_ck[w], m);
+            }
+        }
         if (xy >= 0) continue;
         const int q = ((xy >> 16) & 0x7FFF) * L + (xy & 0xFFFF);
         const float3 v = spin(q);
@@ -975,33 +996,6 @@ __global__ void __launch_bounds__(2 * kWThreads, 1) k_window_steps(const WindowC
                 const __nv_bfloat16 h16 = __float2bfloat16_rn(v3[cc]);
                 hi[cc * N + q] = h16;
                 lo[cc * N + q] = __float2bfloat16_rn(v3[cc] - __bfloat162float(h16));
-            }
-        }
-    }
-    if (cfg.stale_mode == 3) {
-        // ---- spectra of the window's offsets after its moves, S'[r][kappa][a][e'] (bf16 hi/lo)
-        const int lsq = l * l;
-        __nv_bfloat16 *hi = buf.spins_hi + (size_t)r * 12 * lsq, *lo = buf.spins_lo + (size_t)r * 12 * lsq;
-        // a thread per offset j and frequency kappa: its three components
-        for (int task = tid; task < 4 * (Sw >> 2); task += kWThreads) {
-            const int j = task >> 2, kap = task & 3;
-            const int o = wxy[4 * j], ox = o & 0xFFFF, oy = (o >> 16) & 0x7FFF;
-            float v[3] = {0.0f, 0.0f, 0.0f};
-#pragma unroll
-            for (int D = 0; D < 4; ++D) {
-                const float3 sv = spin((oy + l * (D >> 1)) * L + ox + l * (D & 1));
-                const bool neg = ((kap & 1) * (D & 1) + (kap >> 1) * (D >> 1)) & 1;
-                v[0] += neg ? -sv.x : sv.x;
-                v[1] += neg ? -sv.y : sv.y;
-                v[2] += neg ? -sv.z : sv.z;
-            }
-            const size_t e = (size_t)oy * l + (l - 1 - ox);
-#pragma unroll
-            for (int aa = 0; aa < 3; ++aa) {
-                const size_t idx = (size_t)(kap * 3 + aa) * lsq + e;
-                const __nv_bfloat16 h16 = __float2bfloat16_rn(v[aa]);
-                hi[idx] = h16;
-                lo[idx] = __float2bfloat16_rn(v[aa] - __bfloat162float(h16));
             }
         }
     }
@@ -1075,6 +1069,44 @@ __global__ void __launch_bounds__(2 * kWThreads, 1) k_window_steps(const WindowC
             buf.energy[r] = s_energy;
         } else {
             atomicAdd(buf.energy + r, et);
+        }
+    }
+    if (cfg.stale_mode == 3) {
+        // ---- spectra S'[r][kappa][a][e'] (bf16 hi/lo) of every marked offset group after the
+        // window's moves, F(kappa) = sum_D (-1)^(kappa.D) s(o + l D).  A thread takes two
+        // adjacent offsets e', e' + 1 (columns ex, ex - 1 of one row) through all twelve
+        // (kappa, a) planes, so eight threads fill one 32-byte sector of a plane; an unchanged
+        // offset of a marked group is rewritten with the bits it already holds (same sum order)
+        const int lsq = l * l;
+        __nv_bfloat16 *hi = buf.spins_hi + (size_t)r * 12 * lsq, *lo = buf.spins_lo + (size_t)r * 12 * lsq;
+        for (int task = tid; task < nck * 8; task += kWThreads) {
+            const int c = task >> 3;
+            if (c < 32 * kSpecWords && !((s_ck[c >> 5] >> (c & 31)) & 1u)) continue;
+            const int ep = (c << 4) + ((task & 7) << 1);
+            const int ey = ep / l, ex = l - 1 - (ep - ey * l);   // ex odd: e' + 1 sits at ex - 1
+            float2 sv[3][4];
+#pragma unroll
+            for (int aa = 0; aa < 3; ++aa)
+#pragma unroll
+                for (int D = 0; D < 4; ++D)
+                    sv[aa][D] = *reinterpret_cast<const float2 *>(sxyz + aa * N + (ey + l * (D >> 1)) * L + ex - 1 + l * (D & 1));
+#pragma unroll
+            for (int kap = 0; kap < 4; ++kap)
+#pragma unroll
+                for (int aa = 0; aa < 3; ++aa) {
+                    float v0 = 0.0f, v1 = 0.0f;   // offsets e' (.y) and e' + 1 (.x)
+#pragma unroll
+                    for (int D = 0; D < 4; ++D) {
+                        const bool neg = ((kap & 1) * (D & 1) + (kap >> 1) * (D >> 1)) & 1;
+                        v0 += neg ? -sv[aa][D].y : sv[aa][D].y;
+                        v1 += neg ? -sv[aa][D].x : sv[aa][D].x;
+                    }
+                    const __nv_bfloat16 h0 = __float2bfloat16_rn(v0), h1 = __float2bfloat16_rn(v1);
+                    const size_t idx = (size_t)(kap * 3 + aa) * lsq + ep;
+                    *reinterpret_cast<__nv_bfloat162 *>(hi + idx) = __halves2bfloat162(h0, h1);
+                    *reinterpret_cast<__nv_bfloat162 *>(lo + idx) = __halves2bfloat162(
+                        __float2bfloat16_rn(v0 - __bfloat162float(h0)), __float2bfloat16_rn(v1 - __bfloat162float(h1)));
+                }
         }
     }
     if (cfg.measure) {
@@ -1218,11 +1250,15 @@ bool window_supported(int L, int l, int B) {
 
 cudaError_t launch_window_steps(const WindowConfig &c0, const WindowBuffers &b, cudaStream_t st) {
     const int C = c0.L / c0.l;
-    // two replicas a CTA (one on the even, one on the odd warps) when both fit an SM's shared
-    // memory, else one
+    // two replicas a CTA (one on the even, one on the odd warps) when the replicas outnumber the
+    // SMs, so that two would share an SM anyway, and both fit its shared memory; else one replica
+    // a CTA, each alone on its SM while R <= SM count
     const size_t group = (window_smem_bytes(c0.L, c0.B * C * C, C * C) + 127) & ~(size_t)127;
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     WindowConfig c = c0;
-    c.gpc = 2 * group <= kWindowSmemTwoGroups ? 2 : 1;
+    c.gpc = (c0.R > nsm && 2 * group <= kWindowSmemTwoGroups) ? 2 : 1;
     c.smem_group = (unsigned)group;
     const size_t smem = c.gpc * group;
     cudaError_t e;

@@ -428,6 +428,40 @@ def test_window_paths_match_oracle(dipmc, path, case):
         assert abs(Eg_tracked[r] - Eg_full[r]) < 1e-5 * (L * L) * (1 + abs(J) + abs(K2) + abs(K4) + CD * 10)
 
 
+@pytest.mark.parametrize("path", [2, 3], ids=["window_f32", "tensor_bf16x3"])
+def test_window_paths_paired_replicas_odd_count(dipmc, path):
+    """One replica more than the device has SMs: the sub-step kernel runs two replicas
+    a CTA (even and odd warps), and the last CTA holds one.  Replicas of the first,
+    a middle and the last CTA against the re-synchronised oracle."""
+    import torch
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    L, l, A, R = 16, 8, 16, nsm + 1
+    sample = (0, 1, R // 2, R - 2, R - 1)
+    lad = [(F32(1.0), F32(0.1), F32(k2), F32(k4), F32(T)) for (T, k2, k4) in inputs.ladder(16, 16)]
+    lad = [lad[r % len(lad)] for r in range(R)]
+    s0 = inputs.random_spins(L, R, seed=77)
+    with dipmc.Lattice(L, l, R, 12) as lat:
+        lat.precompute_W(A, True)
+        lat.set_field_path(path)
+        for r, prm in enumerate(lad):
+            lat.set_params(*prm, replica=r)
+        lat.init_spins(2, s0)
+        tr = lat.sweep_trace(2)
+        sg = lat.get_spins().astype(np.float64)
+        Eg_full = lat.energy()
+        Eg_tracked = np.array([lat.observables(r)["energy"] * L * L for r in range(R)])
+    W = oracle_W(L, A)
+    for r in sample:
+        J, CD, K2, K4, T = lad[r]
+        p = orc.params(L, l, J, CD, K2, K4, T, proposal=0, cone=0.5, schedule=0, seed=12, replica=r)
+        o = resync(p, W, s0[r], 0, 2, tr[r])
+        hmax = float(np.abs(o["h"]).max())
+        rep = compare_trace(tr[r], o, T, scale=1 + abs(J) + abs(K2) + abs(K4) + abs(CD) * hmax)
+        if rep.straddles == 0:
+            np.testing.assert_allclose(sg[r], o["s"], rtol=0, atol=1e-5)
+    np.testing.assert_allclose(Eg_tracked, Eg_full, rtol=0, atol=1e-5 * L * L * 3)
+
+
 def _resync_all(lad, L, l, seed, W, s0, tr, nsw, chunk=32):
     """Every replica's trace against the oracle re-synchronised per sub-step
     (orc_replay over all host threads, `chunk` replicas at a time); returns the
