@@ -343,6 +343,7 @@ int check_device_flag(mc_lattice *p) {
     if (v) {
         cudaMemset(p->err_flag, 0, sizeof v);
         if (v == 2) return fail(MC_ECUDA, "tensor-core field: shared-memory stages not 1024-byte aligned; results invalid");
+        if (v == 3) return fail(MC_ETIMEOUT, "sub-step kernel: the bulk copy of the spins did not complete; results of the last sweep are invalid");
         return fail(MC_ETIMEOUT, "a tensor-core pipeline wait timed out; results of the last sweep are invalid");
     }
     return MC_OK;
@@ -447,6 +448,7 @@ int run_windows(mc_lattice *p, int path, int nsweeps, int measure_every, float *
     b.wq = p->wq;
     b.hist = hist_of(p);
     b.cycles = p->timing ? p->wcyc : nullptr;
+    b.error = tensor ? p->err_flag : nullptr;
     TcFieldArgs ta{};
     if (tensor) {
         ta.L = p->L; ta.Sw = Sw; ta.R = p->R; ta.NT = p->NT; ta.tmem_cols = p->tmem_cols;

@@ -213,7 +213,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a,
     __shared__ int2 s_rinfo[kProducers];     // spectra: per tile row, offset x | y << 16 and kappa | b << 2
     volatile int *abort = &abort_s;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    pdl_trigger();
     if (smem_u32(smem) & 1023u) {          // the swizzled B tiles need aligned stages
         if (tid == 0) atomicExch(a.error, 2);
         return;
@@ -356,6 +355,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_field(const TcFieldArgs a,
     } else if (warp == 1) {
         if (lane == 0) {
             pdl_wait();
+            // the next kernel (the sub-step kernel) may launch once every CTA is past this
+            // wait: every kernel before this one has then completed, so that kernel may read
+            // the spins before its own wait
+            pdl_trigger();
             // ---- B: spins of NT replicas x kKB by TMA (x = K offset, a multiple of 8
             // elements = 16 bytes; rows past R read as zeros)
             int issued = 0;

@@ -10,8 +10,9 @@
 //     h_q = h_q(stale) + sum_{p accepted since the window start} W~(q - p) (S_p - s_p).
 // This is the same field the direct path computes, up to rounding.
 //
-// k_window_steps: one CTA (8 warps) per replica.  Spins live in shared memory
-// for the window (three planes); warp 0 takes the decisions of blocks of 16 sites
+// k_window_steps: eight warps per replica (one CTA, or one half of a CTA that
+// carries two).  Spins live in shared memory for the window (three planes); the
+// replica's first warp takes the decisions of blocks of 16 sites
 // on its own; warps 1..7 push older moves into the window's later sites.  Under
 // the permutation schedule a site's proposal is fixed at the window's start, so
 // what the decider adds per sub-step is a sum of precomputed scalar pair energies;
@@ -36,6 +37,46 @@ constexpr float kPiF = 3.14159265358979f;
 __host__ __device__ __forceinline__ int wtab_smem_elems(int L, int n) {
     const int hq = L / 2 + 1, hu = L / 4 + 1;
     return (n == 4 && 4 * hu * hu > hq * hq) ? 4 * hu * hu : hq * hq;
+}
+
+// Bulk global -> shared copies on an mbarrier (the set-up's tables and spins).  Waits are
+// bounded: a copy that has not landed after kCopyWaitCycles is reported, not waited on forever.
+constexpr long long kCopyWaitCycles = 1LL << 31;   // about one second at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bar_init_tx(uint64_t *m) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(m)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void bar_expect_tx(uint64_t *m, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(m)), "r"(bytes) : "memory");
+}
+
+// bytes: a multiple of 16; both addresses 16-byte aligned
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *m) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(m))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool bar_wait_bounded(uint64_t *m, uint32_t parity) {
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_addr(m)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > kCopyWaitCycles) return false;
+    }
 }
 
 // One measurement sample into the log-binning accumulators (FP64, global memory):
@@ -228,7 +269,8 @@ __global__ void __launch_bounds__(2 * kWThreads, 1) k_window_steps(const WindowC
     float4 *wpair = s_mvb + 2 * NB;                      // !PRE: [NB][NB] W~ between the sites of a block
     float4 *etab = wpair;                                // PRE: [2][2 NB / 4][NB] pair energies by block parity,
                                                          // four columns of a row per float4
-    int *wxy = reinterpret_cast<int *>(wpair + NB * NB); // [Sw] site as x | y << 16 (bit 31: accepted)
+    int *wxy = reinterpret_cast<int *>(wpair + NB * NB); // [Sw] site as x | y << 16 (bit 31: accepted);
+                                                         // then stale_mode 3: [3 Sw] floats of split-K sums
     __shared__ int s_nmv_g[2][2];
     __shared__ double s_epart_g[2][32];
     __shared__ double s_energy_g[2];   // the tracked energy after this window (measured windows)
@@ -345,6 +387,26 @@ __global__ void __launch_bounds__(2 * kWThreads, 1) k_window_steps(const WindowC
     // the tensor table and the window's sites (they depend on the sweep counter
     // only); then the state, stale field and proposals.
     pdl_trigger();
+    // the spins, and under PRE the proposals (they depend on the spins at the window's start
+    // and the counter-based draws only), before the wait when the previous kernel is the
+    // tensor-core field kernel (stale_mode 2, 3): it lets this kernel launch only once it is
+    // past its own wait on the sub-step kernel before it, so every writer of the spins has
+    // completed.  The W~ table and the spins then come by two bulk copies (async proxy, read
+    // through L2) that thread 0 issues first and waits for.
+    const bool early = cfg.stale_mode >= 2;
+    const float *gs = buf.spins + (size_t)r * 3 * N;
+    const float4 *gwq = SPX ? buf.wq + hq * hq : buf.wq;
+    const int nwq = SPX ? 4 * ((l >> 1) + 1) * ((l >> 1) + 1) : hq * hq;   // float4 of the table
+    __shared__ uint64_t s_cbar_g[2][2];   // per group: the spins, the table
+    __shared__ int s_cok_g[2];
+    if (early && tid == 0) {
+        bar_init_tx(&s_cbar_g[g][0]);
+        bar_init_tx(&s_cbar_g[g][1]);
+        bar_expect_tx(&s_cbar_g[g][0], (uint32_t)(12 * N));
+        bulk_g2s(sxyz, gs, (uint32_t)(12 * N), &s_cbar_g[g][0]);
+        bar_expect_tx(&s_cbar_g[g][1], (uint32_t)(16 * nwq));
+        bulk_g2s(wq, gwq, (uint32_t)(16 * nwq), &s_cbar_g[g][1]);
+    }
     __shared__ float4 s_wl_g[2][4];   // SPX: W~(l P), P = Px + 2 Py (the cells of one offset)
     float4 *s_wl = s_wl_g[g];
     if (SPX && tid < 4) {
@@ -352,14 +414,9 @@ __global__ void __launch_bounds__(2 * kWThreads, 1) k_window_steps(const WindowC
         s_wl[tid] = make_float4(__ldg(buf.W32 + g), __ldg(buf.W32 + N + g), __ldg(buf.W32 + 2 * N + g),
                                 __ldg(buf.W32 + 3 * N + g));
     }
-    if constexpr (SPX) {
-        const int hu = (l >> 1) + 1;
-        const float4 *gu = buf.wq + hq * hq;
+    if (!early) {
 #pragma unroll 4
-        for (int i = tid; i < 4 * hu * hu; i += kWThreads) wq[i] = gu[i];
-    } else {
-#pragma unroll 4
-        for (int i = tid; i < hq * hq; i += kWThreads) wq[i] = buf.wq[i];
+        for (int i = tid; i < nwq; i += kWThreads) wq[i] = gwq[i];
     }
     // W~(q_i - q_p) v for lattice sites i = (xi, yi), p = (xp, yp)
     auto w_apply_sites = [&](int xi, int yi, int xp, int yp, float3 v) -> float3 {
@@ -381,10 +438,70 @@ __global__ void __launch_bounds__(2 * kWThreads, 1) k_window_steps(const WindowC
         st_u0 = buf.tile_first[nt * cfg.mtiles + st_mt];
         st_cnt = buf.tile_first[nt * cfg.mtiles + st_mt + 1] - st_u0;
     }
+    auto load_spins = [&]() {
+#pragma unroll 8
+        for (int i = tid; i < 3 * N / 4; i += kWThreads) smem_w[i] = reinterpret_cast<const float4 *>(gs)[i];
+    };
+    // proposal of window site s (lattice site q): pS = (S, -T ln u), pd = (delta, field-free dE)
+    auto propose_site = [&](int s, int q) {
+        const uint4 wds = attempt_rng(s, q);
+        float sps, cps;
+        sincospif(2.0f * u24f(wds.y), &sps, &cps);
+        const float u = u24f(wds.z);
+        float4 S, D;
+        propose(q, u24f(wds.x), cps, sps, S, D);
+        // accept iff u < exp(-dE/T)  <=>  dE < -T ln u   (u = 0: always)
+        S.w = (u > 0.0f) ? -P.T * logf(u) : INFINITY;
+        pS[s] = S;
+        pd[s] = D;
+    };
+    if (early) {
+        if (PRE) {
+            // the draws first, while the copies land: pd[s] = (u1, cos, sin) of the proposal,
+            // pS[s].w = -T ln u (same thread and site as below)
+            for (int s = tid; s < Sw; s += kWThreads) {
+                const int xy = wxy[s];
+                const uint4 wds = attempt_rng(s, (xy >> 16) * L + (xy & 0xFFFF));
+                float sps, cps;
+                sincospif(2.0f * u24f(wds.y), &sps, &cps);
+                const float u = u24f(wds.z);
+                pS[s].w = (u > 0.0f) ? -P.T * logf(u) : INFINITY;
+                pd[s] = make_float4(u24f(wds.x), cps, sps, 0.0f);
+            }
+        }
+        if (tid == 0) {
+            const bool ok = bar_wait_bounded(&s_cbar_g[g][0], 0u);
+            if (!ok) {
+                if (buf.error) atomicExch(buf.error, 3);
+                bar_wait_bounded(&s_cbar_g[g][0], 0u);   // once more for the copies in flight
+                bar_wait_bounded(&s_cbar_g[g][1], 0u);
+            }
+            s_cok_g[g] = ok ? 1 : 0;
+        }
+        gsync();
+        if (!s_cok_g[g]) return;   // the whole group: results of this call are invalid (reported)
+        if (PRE) {
+            for (int s = tid; s < Sw; s += kWThreads) {
+                const int xy = wxy[s];
+                const float4 dr = pd[s];
+                float4 S, D;
+                propose((xy >> 16) * L + (xy & 0xFFFF), dr.x, dr.y, dr.z, S, D);
+                S.w = pS[s].w;
+                pS[s] = S;
+                pd[s] = D;
+            }
+        }
+    }
     pdl_wait();
+    if (early && tid == 0 && !bar_wait_bounded(&s_cbar_g[g][1], 0u)) {
+        // the table (needed from the first pair table on, after the barrier below): reported;
+        // once more for the copy in flight
+        if (buf.error) atomicExch(buf.error, 3);
+        bar_wait_bounded(&s_cbar_g[g][1], 0u);
+    }
     // the loads of the split-K partial tiles (stale_mode 3: lane f of warp mt takes rows
     // 4f .. 4f+3 of M-tile mt, one 16-byte load of each unit's 512-byte column segment)
-    // and of the spins go out together
+    // and (late) of the spins go out together
     const bool st_on = cfg.stale_mode == 3 && st_mt < cfg.mtiles;
     const size_t ustride = (size_t)cfg.NT * 32;   // float4 per unit
     const float4 *pc = nullptr;
@@ -396,13 +513,11 @@ __global__ void __launch_bounds__(2 * kWThreads, 1) k_window_steps(const WindowC
 #pragma unroll
         for (int j = 0; j < kPV; ++j) pv[j] = (j < st_cnt) ? __ldcg(pc + (size_t)j * ustride) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    const float *gs = buf.spins + (size_t)r * 3 * N;
-#pragma unroll 8
-    for (int i = tid; i < 3 * N / 4; i += kWThreads) smem_w[i] = reinterpret_cast<const float4 *>(gs)[i];
+    if (!early) load_spins();
     if (cfg.stale_mode == 3) {
         // split-K sums in unit order (the tensor-core field's reduction) into rs[row]
-        // (scratch in the proposals' space, which is filled later: 3 S_w rows <= 4 S_w floats)
-        float *rs = reinterpret_cast<float *>(pS);
+        // (3 S_w rows of scratch after the window's site list)
+        float *rs = reinterpret_cast<float *>(wxy + Sw);
         if (st_on) {
             float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
@@ -478,16 +593,8 @@ __global__ void __launch_bounds__(2 * kWThreads, 1) k_window_steps(const WindowC
         const float3 hs = stale_at(s, q);
         const float h0 = hs.x, h1 = hs.y, h2 = hs.z;
         if (PRE) {
-            const uint4 wds = attempt_rng(s, q);
-            float sps, cps;
-            sincospif(2.0f * u24f(wds.y), &sps, &cps);
-            const float u = u24f(wds.z);
-            float4 S, D;
-            propose(q, u24f(wds.x), cps, sps, S, D);
-            // accept iff u < exp(-dE/T)  <=>  dE < -T ln u   (u = 0: always)
-            S.w = (u > 0.0f) ? -P.T * logf(u) : INFINITY;
-            pS[s] = S;
-            pd[s] = D;
+            if (!early) propose_site(s, q);
+            const float4 D = pd[s];
             dacc[s] = D.w + P.CD * (D.x * h0 + D.y * h1 + D.z * h2);
         } else {
             hcur[s] = make_float4(h0, h1, h2, 0.0f);
@@ -1234,7 +1341,7 @@ size_t window_smem_bytes(int L, int Sw, int n) {
     // blocks of kBlockSites sites (n <= kBlockSites)
     return sizeof(float) * 3 * N +
            sizeof(float4) * (3 * (size_t)Sw + (size_t)wtab_smem_elems(L, n) + 2 * kBlockSites + kBlockSites * kBlockSites) +
-           sizeof(int) * (size_t)Sw;
+           sizeof(int) * (size_t)Sw + sizeof(float) * 3 * (size_t)Sw;   // sites, split-K sums
 }
 
 bool window_supported(int L, int l, int B) {

@@ -53,6 +53,8 @@ struct WindowBuffers {
     EnergyHist hist;              // optional energy histogram
     unsigned long long *cycles;   // optional [4]: SM clock cycles summed over CTAs of the blocks, the
                                   // set-up before them and the tail after them, and the blocks run
+    int *error;                   // stale_mode 2, 3: set to 3 when the set-up's bulk copy of the spins
+                                  // did not complete within its bound (the replica's window is skipped)
 };
 
 size_t window_smem_bytes(int L, int Sw, int n);
