@@ -1220,25 +1220,42 @@ __global__ void __launch_bounds__(2 * kWThreads, 1) k_window_steps(const WindowC
         gsync();
         float mv_[12] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         double *gt = buf.theta2 ? buf.theta2 + (size_t)r * N : nullptr;
-#pragma unroll 4
-        for (int i = tid; i < N; i += kWThreads) {
-            const float3 a = spin(i);
+        // two sites of a row a thread (L even): i and i + 1, their right neighbours i + 1 and
+        // (ix + 2) mod L, and the sites below them, with the shared loads as pairs
+#pragma unroll 2
+        for (int i = 2 * tid; i < N; i += 2 * kWThreads) {
             const int iy = i / L, ix = i - iy * L;
-            const float3 ax = spin(iy * L + (ix + 1 == L ? 0 : ix + 1)), ay = spin((iy + 1 == L ? 0 : iy + 1) * L + ix);
-            mv_[0] += a.x;
-            mv_[1] += a.y;
-            mv_[2] += a.z;
-            mv_[3] += (iy & 1) ? -a.z : a.z;     // m1 + m2 - m3 - m4 (rows)
-            mv_[4] += (ix & 1) ? -a.z : a.z;     // m1 + m4 - m3 - m2 (columns)
-            mv_[5] += wall_term(a.x, ax.x);
-            mv_[6] += wall_term(a.x, ay.x);
-            mv_[7] += wall_term(a.y, ax.y);
-            mv_[8] += wall_term(a.y, ay.y);
-            mv_[9] += wall_term(a.z, ax.z);
-            mv_[10] += wall_term(a.z, ay.z);
-            const float th = acosf(fminf(1.0f, fmaxf(-1.0f, a.z))) - 0.5f * kPiF;
-            mv_[11] += fabsf(th);
-            if (gt) gt[i] += (double)(th * th);
+            const int ir = iy * L + (ix + 2 == L ? 0 : ix + 2), id = (iy + 1 == L ? 0 : iy + 1) * L + ix;
+            float2 va[3], vd[3];
+            float vr[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                va[c] = *reinterpret_cast<const float2 *>(sxyz + c * N + i);
+                vd[c] = *reinterpret_cast<const float2 *>(sxyz + c * N + id);
+                vr[c] = sxyz[c * N + ir];
+            }
+            const float zr = (iy & 1) ? -1.0f : 1.0f;   // m1 + m2 - m3 - m4 (rows); columns: ix even
+            mv_[0] += va[0].x + va[0].y;
+            mv_[1] += va[1].x + va[1].y;
+            mv_[2] += va[2].x + va[2].y;
+            mv_[3] += zr * (va[2].x + va[2].y);
+            mv_[4] += va[2].x - va[2].y;                 // m1 + m4 - m3 - m2 (columns)
+            mv_[5] += wall_term(va[0].x, va[0].y) + wall_term(va[0].y, vr[0]);
+            mv_[6] += wall_term(va[0].x, vd[0].x) + wall_term(va[0].y, vd[0].y);
+            mv_[7] += wall_term(va[1].x, va[1].y) + wall_term(va[1].y, vr[1]);
+            mv_[8] += wall_term(va[1].x, vd[1].x) + wall_term(va[1].y, vd[1].y);
+            mv_[9] += wall_term(va[2].x, va[2].y) + wall_term(va[2].y, vr[2]);
+            mv_[10] += wall_term(va[2].x, vd[2].x) + wall_term(va[2].y, vd[2].y);
+            const float th0 = acosf(fminf(1.0f, fmaxf(-1.0f, va[2].x))) - 0.5f * kPiF;
+            const float th1 = acosf(fminf(1.0f, fmaxf(-1.0f, va[2].y))) - 0.5f * kPiF;
+            mv_[11] += fabsf(th0) + fabsf(th1);
+            if (gt) {
+                double2 *g2 = reinterpret_cast<double2 *>(gt + i);
+                double2 v = *g2;
+                v.x += (double)(th0 * th0);
+                v.y += (double)(th1 * th1);
+                *g2 = v;
+            }
         }
 #pragma unroll
         for (int c = 0; c < 12; ++c)
@@ -1247,40 +1264,52 @@ __global__ void __launch_bounds__(2 * kWThreads, 1) k_window_steps(const WindowC
 #pragma unroll
             for (int c = 0; c < 12; ++c) s_mred[warp][c] = mv_[c];
         gsync();
-        // the sample once (FP64 is slow here: lane c sums component c over the warps, lane
-        // 0 forms the observables), then lane k < kNB pushes it into binning level k
+        // the sample once, in FP64 across the lanes of one warp: lane c sums component c over
+        // the warps; every quotient of the observables is one lane's share of a single
+        // division, the three norms of a single square root; then lane k < kNB pushes the
+        // sample into binning level k
         if (warp == 0 && buf.obs) {
-            __shared__ double s_sm_g[2][12], s_x_g[2][MC_NOBS];
-            double *s_sm = s_sm_g[g], *s_x = s_x_g[g];
-            if (lane < 12) {
-                double v = 0.0;
-                for (int ww = 0; ww < kWThreads / 32; ++ww) v += s_mred[ww][lane];
-                s_sm[lane] = v;
-            }
-            __syncwarp();
-            if (lane == 0) {
-                const double *sm = s_sm;
-                const double Mx = sm[0] / N, My = sm[1] / N, Mz = sm[2] / N, Mh = sm[3] / N, Mv = sm[4] / N;
-                const double nh[3] = {sm[5], sm[7], sm[9]}, nv[3] = {sm[6], sm[8], sm[10]};
-                double x[MC_NOBS];
-                x[MC_OBS_ABS_M] = sqrt(Mx * Mx + My * My + Mz * Mz);
-                x[MC_OBS_MZ] = Mz;
-                x[MC_OBS_ABS_MZ] = fabs(Mz);
-                x[MC_OBS_MPAR] = sqrt(Mx * Mx + My * My);
-                x[MC_OBS_E] = s_energy / N;
-                x[MC_OBS_MST] = sqrt(Mh * Mh + Mv * Mv);
-                stripe_obs(x, nh, nv, sm[11], N);
+            double smv = 0.0;
+            if (lane < 12)
+                for (int ww = 0; ww < kWThreads / 32; ++ww) smv += s_mred[ww][lane];
+            double sm[12];
 #pragma unroll
-                for (int o = 0; o < MC_NOBS; ++o) s_x[o] = x[o];
-                hist_push(buf.hist, r, x[MC_OBS_E]);
-            }
-            __syncwarp();
-            if (lane < kNB) {
-                double x[MC_NOBS];
-#pragma unroll
-                for (int o = 0; o < MC_NOBS; ++o) x[o] = s_x[o];
-                obs_push_level(buf.obs[r], x, lane);
-            }
+            for (int c = 0; c < 12; ++c) sm[c] = __shfl_sync(0xffffffffu, smv, c);
+            const double Nd = (double)N;
+            // lanes 0-4: M_x, M_y, M_z, M_h, M_v; 5: E/N; 6: wall density; 7-9: O_x, O_y, O_z
+            // (n_h^a = sm[5 + 2a], n_v^a = sm[6 + 2a]); 10: cone angle
+            const double nh = lane == 7 ? sm[5] : (lane == 8 ? sm[7] : sm[9]);
+            const double nv = lane == 7 ? sm[6] : (lane == 8 ? sm[8] : sm[10]);
+            const double osum = nh + nv;
+            const bool ol = lane >= 7 && lane <= 9;
+            double num = 0.0, den = 1.0;
+            if (lane < 5) { num = smv; den = Nd; }
+            else if (lane == 5) { num = s_energy; den = Nd; }
+            else if (lane == 6) { num = sm[10] + sm[9]; den = 4.0 * Nd; }
+            else if (ol) { num = fabs(nh - nv); den = osum > 0.0 ? osum : 1.0; }
+            else if (lane == 10) { num = 0.63661977236758134 * sm[11]; den = Nd; }   // 2/pi
+            double q = num / den;
+            if (ol && !(osum > 0.0)) q = 0.0;
+            const double Mx = __shfl_sync(0xffffffffu, q, 0), My = __shfl_sync(0xffffffffu, q, 1),
+                         Mz = __shfl_sync(0xffffffffu, q, 2), Mh = __shfl_sync(0xffffffffu, q, 3),
+                         Mv = __shfl_sync(0xffffffffu, q, 4);
+            const double rad = lane == 0 ? Mx * Mx + My * My + Mz * Mz
+                                         : (lane == 1 ? Mx * Mx + My * My : (lane == 2 ? Mh * Mh + Mv * Mv : 0.0));
+            const double rt = sqrt(rad);
+            double x[MC_NOBS];
+            x[MC_OBS_ABS_M] = __shfl_sync(0xffffffffu, rt, 0);
+            x[MC_OBS_MZ] = Mz;
+            x[MC_OBS_ABS_MZ] = fabs(Mz);
+            x[MC_OBS_MPAR] = __shfl_sync(0xffffffffu, rt, 1);
+            x[MC_OBS_E] = __shfl_sync(0xffffffffu, q, 5);
+            x[MC_OBS_MST] = __shfl_sync(0xffffffffu, rt, 2);
+            x[MC_OBS_WALL] = __shfl_sync(0xffffffffu, q, 6);
+            x[MC_OBS_OX] = __shfl_sync(0xffffffffu, q, 7);
+            x[MC_OBS_OY] = __shfl_sync(0xffffffffu, q, 8);
+            x[MC_OBS_OZ] = __shfl_sync(0xffffffffu, q, 9);
+            x[MC_OBS_CONE] = __shfl_sync(0xffffffffu, q, 10);
+            if (lane == 0) hist_push(buf.hist, r, x[MC_OBS_E]);
+            if (lane < kNB) obs_push_level(buf.obs[r], x, lane);
         }
     }
     if (warp == dw && lane == 0 && buf.obs)
