@@ -350,6 +350,11 @@ int mc_get_sweep_counter(mc_lattice *lat, uint64_t *out);
  * parameters, spins, tracked energy, observable accumulators) into buf.  Call
  * with buf = NULL to get the size in *len.  Resuming with mc_restore on a handle
  * of the same L, l, R continues the run bit-exactly (the RNG is counter-based).
+ * mc_restore replaces the handle's seed, sweep counter, parameters, proposal kind,
+ * cone and site schedule with the checkpoint's, whatever the handle ran before;
+ * the handle's W~ must already match the checkpoint's (mc_precompute_W with the
+ * same cutoff and tail, else MC_ENOTREADY).  A buffer that is too short or not a
+ * checkpoint of this library gives MC_EINVAL and leaves the handle unchanged.
  */
 int mc_checkpoint(mc_lattice *lat, void *buf, size_t *len);
 int mc_restore(mc_lattice *lat, const void *buf, size_t len);

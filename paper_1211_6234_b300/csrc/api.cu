@@ -1671,9 +1671,14 @@ int mc_restore(mc_lattice *p, const void *buf, size_t len) {
     const size_t need = sizeof(CkptHeader) + sizeof(RepParams) * R + sizeof(float) * 3 * N * R +
                         sizeof(double) * R + sizeof(ObsAcc) * R + sizeof(double) * N * R;
     if (len < need) return fail(MC_EINVAL, "checkpoint truncated (%zu < %zu)", len, need);
+    if (h.proposal < 0 || h.proposal > 2 || (h.schedule != 0 && h.schedule != 1) || !(h.cone > 0.0 && h.cone <= M_PI))
+        return fail(MC_EINVAL, "checkpoint holds an invalid proposal kind, schedule or cone");
     if (h.W_ready && (!p->W_ready || h.A != p->A || h.tail != p->tail))
         return fail(MC_ENOTREADY, "call mc_precompute_W(%d, %d) on this handle before mc_restore", h.A, h.tail);
     CK(cudaDeviceSynchronize());
+    // the captured launch graphs hold the seed's key, the proposal kind, the cone and the
+    // schedule as kernel arguments; the checkpoint may carry other ones
+    drop_graphs(p);
     const char *o = (const char *)buf + sizeof h;
     std::memcpy(p->hp.data(), o, sizeof(RepParams) * R); o += sizeof(RepParams) * R;
     rc = upload_params(p);
