@@ -725,6 +725,12 @@ def main():
     host_in = torch.from_numpy(s0).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
     e2e_steps = max(2, min(args.steps, 5))
+    # one untimed step first: the first copies into freshly pinned buffers and the first
+    # read-back pay one-time costs (page mapping, staging set-up) that later steps do not
+    lat.init_spins(2, host_in.numpy())
+    lat.sweep(S, 1, stream)
+    lat.get_spins(out=host_out, stream=stream)
+    lat.observables_arrays()
     barrier()
     e0 = time.perf_counter()
     for i in range(e2e_steps):

@@ -74,6 +74,10 @@ struct mc_lattice {
     ObsAcc *obs = nullptr;    // [R]
     double *theta2 = nullptr; // [R][N]
     double *eta_dev = nullptr; // [R] eta of the last read-back
+    // pinned staging of the observables read-back: [cap] accumulators, then [cap]
+    // energies and [cap] eta values (grown on demand, kept for the handle's life)
+    unsigned char *obs_pin = nullptr;
+    int obs_pin_cap = 0;
     uint64_t t = 0;
     bool W_ready = false, energy_valid = false;
     int A = 0, tail = 0;
@@ -153,6 +157,7 @@ void free_all(mc_lattice *p) {
     cudaFree(p->obs);
     cudaFree(p->theta2);
     cudaFree(p->eta_dev);
+    if (p->obs_pin) cudaFreeHost(p->obs_pin);
     cudaFree(p->spins_hi);
     cudaFree(p->spins_lo);
     cudaFree(p->wsh);
@@ -1304,11 +1309,34 @@ int obs_fill(mc_lattice *p, int first, int count, mc_obs *out) {
     const int N = p->N();
     cudaError_t e = launch_eta(N, count, p->theta2 + (size_t)first * N, p->obs + first, p->eta_dev + first, p->last);
     if (e != cudaSuccess) return cuda_fail(e, "eta reduction");
-    std::vector<ObsAcc> A((size_t)count);
-    std::vector<double> E((size_t)count), eta((size_t)count);
-    CK(cudaMemcpyAsync(A.data(), p->obs + first, sizeof(ObsAcc) * count, cudaMemcpyDeviceToHost, p->last));
-    CK(cudaMemcpyAsync(E.data(), p->energy + first, sizeof(double) * count, cudaMemcpyDeviceToHost, p->last));
-    CK(cudaMemcpyAsync(eta.data(), p->eta_dev + first, sizeof(double) * count, cudaMemcpyDeviceToHost, p->last));
+    // the copies land in pinned staging (direct DMA, no per-call allocation); if pinned
+    // memory cannot be had, in pageable vectors
+    if (count > p->obs_pin_cap) {
+        if (p->obs_pin) cudaFreeHost(p->obs_pin);
+        p->obs_pin = nullptr;
+        p->obs_pin_cap = 0;
+        if (cudaMallocHost((void **)&p->obs_pin, (sizeof(ObsAcc) + 2 * sizeof(double)) * (size_t)count) == cudaSuccess)
+            p->obs_pin_cap = count;
+        else
+            cudaGetLastError();
+    }
+    std::vector<ObsAcc> Av;
+    std::vector<double> Ev, etav;
+    const ObsAcc *A;
+    const double *E, *eta;
+    if (p->obs_pin) {
+        A = reinterpret_cast<const ObsAcc *>(p->obs_pin);
+        E = reinterpret_cast<const double *>(p->obs_pin + sizeof(ObsAcc) * (size_t)p->obs_pin_cap);
+        eta = E + p->obs_pin_cap;
+    } else {
+        Av.resize((size_t)count);
+        Ev.resize((size_t)count);
+        etav.resize((size_t)count);
+        A = Av.data(); E = Ev.data(); eta = etav.data();
+    }
+    CK(cudaMemcpyAsync((void *)A, p->obs + first, sizeof(ObsAcc) * count, cudaMemcpyDeviceToHost, p->last));
+    CK(cudaMemcpyAsync((void *)E, p->energy + first, sizeof(double) * count, cudaMemcpyDeviceToHost, p->last));
+    CK(cudaMemcpyAsync((void *)eta, p->eta_dev + first, sizeof(double) * count, cudaMemcpyDeviceToHost, p->last));
     CK(cudaStreamSynchronize(p->last));
     for (int i = 0; i < count; ++i) {
         const ObsAcc &a = A[i];
