@@ -183,6 +183,94 @@ def test_observables_statistically_match_oracle(dipmc, T):
     assert abs(a - b) <= 3 * math.hypot(ea, eb), ("eta", a, b, ea, eb)
 
 
+def binning_reference(x, min_blocks=32):
+    """Textbook binning analysis of one time series x (Flyvbjerg and Petersen): the
+    population variance, the naive error of the mean, and the autocorrelation-corrected
+    error as the largest error of the means of blocks of 2^k samples over the levels that
+    still hold min_blocks blocks (never below the naive one), with tau_int = (err/naive)^2 / 2."""
+    n = len(x)
+    var = max(0.0, float(np.mean(x * x) - np.mean(x) ** 2))
+    naive = math.sqrt(var / (n - 1))
+    err, k = naive, 1
+    while n >> k >= min_blocks:
+        nb = n >> k
+        b = x[: nb << k].reshape(nb, 1 << k).mean(axis=1)
+        vk = max(0.0, float(np.mean(b * b) - np.mean(b) ** 2))
+        err = max(err, math.sqrt(vk / (nb - 1)))
+        k += 1
+    tau = 0.5 * (err / naive) ** 2 if naive > 0 else float("nan")
+    return var, naive, err, tau
+
+
+@pytest.mark.parametrize("path", [1, 2, 3, 4, 5, 6, 7],
+                         ids=["direct", "window_f32", "tensor", "fft", "spectral", "incremental", "cluster"])
+def test_error_bars_equal_a_binning_analysis_of_the_samples(dipmc, path):
+    """Each path's kernel keeps its own binning accumulators.  Run 128 one-sweep calls,
+    measured every sweep, recover every per-sweep sample from the running means, and
+    compare the library's variance, naive error, autocorrelation-corrected error and
+    tau_int of every observable with a binning analysis of those samples in numpy."""
+    L, l, R, n = 16, 8, 2, 128
+    with dipmc.Lattice(L, l, R, 5) as lat:
+        lat.precompute_W(16, True)
+        lat.set_field_path(path)
+        lat.set_params(F32(1.0), F32(0.15), F32(0.8), F32(-0.1), F32(0.9))
+        lat.init_spins(0)
+        means = np.zeros((n, R, len(dipmc.OBS_NAMES)))
+        for t in range(n):
+            lat.sweep(1, 1)
+            a = lat.observables_arrays()
+            means[t] = a["mean"]
+        last = lat.observables_batch()
+    cnt = np.arange(1, n + 1, dtype=np.float64)[:, None, None]
+    sums = means * cnt
+    x = np.diff(np.concatenate([np.zeros((1, R, means.shape[2])), sums]), axis=0)
+    for r in range(R):
+        assert last[r]["samples"] == n
+        for i, nm in enumerate(dipmc.OBS_NAMES):
+            var, naive, err, tau = binning_reference(x[:, r, i])
+            got = last[r][nm]
+            scale = abs(float(np.mean(x[:, r, i]))) + 1.0
+            # the samples come back from FP64 running means (a few ulp of the sums each), and
+            # a constant observable leaves the library rounding residue in its variance
+            assert got["var"] == pytest.approx(var, rel=1e-4, abs=1e-11 * scale * scale), (nm, r)
+            assert got["err_naive"] == pytest.approx(naive, rel=1e-4, abs=1e-7 * scale), (nm, r)
+            assert got["err"] == pytest.approx(err, rel=1e-4, abs=1e-7 * scale), (nm, r)
+            if naive > 1e-5 * scale:
+                assert got["tau_int"] == pytest.approx(tau, rel=1e-3), (nm, r)
+
+
+def test_error_bars_match_the_spread_of_replica_means(dipmc):
+    """What the autocorrelation-corrected error estimates: over 64 independent replicas
+    of one law (L = 16, T = 1.5 from +z, 3000 sweeps dropped, 16000 measured, so that the
+    binning levels with at least 32 blocks reach blocks of 256 sweeps, well beyond
+    tau_int of about 25), the RMS of the replicas' own binning errors of |m|, |m_z|,
+    M_par and E/N equals the standard deviation of their means within the sampling
+    scatter of both, where the naive errors fall short by more than half; every error is
+    at least the naive one and tau_int >= 1/2."""
+    L, l, R, warm, nsw = 16, 8, 64, 3000, 16000
+    with dipmc.Lattice(L, l, R, 23) as lat:
+        lat.precompute_W(64, True)
+        lat.set_field_path(dipmc.MC_PATH_DIRECT)
+        lat.set_params(F32(1.0), F32(0.1), F32(0.8), F32(0.0), F32(1.5))
+        lat.init_spins(1)
+        lat.sweep(warm, 0)
+        lat.reset_observables()
+        lat.sweep(nsw, 1)
+        og = lat.observables_batch()
+    for nm in ("abs_m", "abs_m_z", "m_par", "e"):
+        means = np.array([g[nm]["mean"] for g in og])
+        errs = np.array([g[nm]["err"] for g in og])
+        naive = np.array([g[nm]["err_naive"] for g in og])
+        assert np.all(errs >= naive) and np.all(naive > 0), nm
+        assert all(g[nm]["tau_int"] >= 0.5 for g in og), nm
+        sd = float(means.std(ddof=1))
+        ratio = math.sqrt(float(np.mean(errs ** 2))) / sd
+        print(f"{nm}: binning error / spread of means = {ratio:.3f}, "
+              f"naive / spread = {math.sqrt(float(np.mean(naive ** 2))) / sd:.3f}")
+        assert 0.7 <= ratio <= 1.35, (nm, ratio)
+        assert math.sqrt(float(np.mean(naive ** 2))) / sd < 0.5, nm
+
+
 # ---------------------------------------------------------------- state handling
 def test_determinism_checkpoint_and_batch_invariance(dipmc):
     L, l = 16, 8
