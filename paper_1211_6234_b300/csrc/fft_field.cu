@@ -526,31 +526,7 @@ __global__ void __launch_bounds__(256) k_fft_observe(int L, const float *__restr
         hist_push(hist, r, E / N);
     }
     __syncthreads();
-    if (obs && tid < kNB) {
-        ObsAcc &A = obs[r];
-        const int k = tid;
-        const long long pc = A.pcnt[k] + 1;
-        const bool done = pc == (1LL << k);
-        const double inv = 1.0 / (double)(1LL << k);
-        for (int o = 0; o < MC_NOBS; ++o) {
-            const double pv = A.psum[o][k] + x_s[o];
-            if (done) {
-                const double mean = pv * inv;
-                A.bsum[o][k] += mean;
-                A.bsq[o][k] += mean * mean;
-                A.psum[o][k] = 0.0;
-            } else {
-                A.psum[o][k] = pv;
-            }
-        }
-        if (done) {
-            A.bcnt[k] += 1;
-            A.pcnt[k] = 0;
-        } else {
-            A.pcnt[k] = pc;
-        }
-        if (k == 0) A.nsamples += 1;
-    }
+    if (obs && tid < kNB) obs_push_level(obs[r], x_s, tid);
 }
 
 __global__ void k_add_attempted(ObsAcc *obs, int R, long long add, const SlotState *slots, int nsweeps_call,

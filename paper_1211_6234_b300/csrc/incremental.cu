@@ -20,29 +20,6 @@ namespace {
 constexpr int kIThreads = 512;
 constexpr float kPiF = 3.14159265358979f;
 
-// One measurement sample into the binning accumulators (FP64, one thread).
-__device__ void push_sample(ObsAcc &A, const double x[MC_NOBS]) {
-    A.nsamples += 1;
-#pragma unroll 1
-    for (int k = 0; k < kNB; ++k) {
-        A.pcnt[k] += 1;
-        const bool done = A.pcnt[k] == (1LL << k);
-        const double inv = 1.0 / (double)(1LL << k);
-        for (int o = 0; o < MC_NOBS; ++o) {
-            A.psum[o][k] += x[o];
-            if (done) {
-                const double mean = A.psum[o][k] * inv;
-                A.bsum[o][k] += mean;
-                A.bsq[o][k] += mean * mean;
-                A.psum[o][k] = 0.0;
-            }
-        }
-        if (done) {
-            A.bcnt[k] += 1;
-            A.pcnt[k] = 0;
-        }
-    }
-}
 
 __global__ void __launch_bounds__(kIThreads, 1) k_sweep_incremental(const IncrConfig cfg, const IncrBuffers b) {
     const int L = cfg.L, l = cfg.l, N = L * L, C = L / l, n = C * C, ll = l * l;
@@ -209,7 +186,7 @@ __global__ void __launch_bounds__(kIThreads, 1) k_sweep_incremental(const IncrCo
                 x[MC_OBS_MST] = sqrt(s[3] * s[3] + s[4] * s[4]) / N;
                 const double nh[3] = {s[8], s[10], s[12]}, nv[3] = {s[9], s[11], s[13]};
                 stripe_obs(x, nh, nv, s[14], N);
-                if (b.obs) push_sample(b.obs[r], x);
+                if (b.obs) obs_push(b.obs[r], x);
                 hist_push(b.hist, r, E / N);
                 if (b.energy) b.energy[r] = E;
             }

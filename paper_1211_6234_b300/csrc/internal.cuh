@@ -173,6 +173,67 @@ struct ObsAcc {
     long long pad;
 };
 
+// One measurement sample x into binning level k (blocks of 2^k samples): the level's
+// running block sum takes x, and when the block is complete its mean (the sum times the
+// exact 2^-k) joins the sums of block means and of their squares.  Levels are
+// independent, so kNB threads may push one level each; k == 0 also counts the sample.
+__device__ __forceinline__ void obs_push_level(ObsAcc &A, const double x[MC_NOBS], int k) {
+    const long long pc = A.pcnt[k] + 1;
+    const bool done = pc == (1LL << k);
+    const double inv = __longlong_as_double((long long)(1023 - k) << 52);   // 2^-k
+    double ps[MC_NOBS], bs[MC_NOBS], bq[MC_NOBS];
+#pragma unroll
+    for (int o = 0; o < MC_NOBS; ++o) {   // the loads of the level first, so they overlap
+        ps[o] = A.psum[o][k];
+        bs[o] = A.bsum[o][k];
+        bq[o] = A.bsq[o][k];
+    }
+#pragma unroll
+    for (int o = 0; o < MC_NOBS; ++o) {
+        const double p = ps[o] + x[o];
+        if (done) {
+            const double mean = p * inv;
+            A.bsum[o][k] = bs[o] + mean;
+            A.bsq[o][k] = bq[o] + mean * mean;
+            A.psum[o][k] = 0.0;
+        } else {
+            A.psum[o][k] = p;
+        }
+    }
+    if (done) {
+        A.bcnt[k] += 1;
+        A.pcnt[k] = 0;
+    } else {
+        A.pcnt[k] = pc;
+    }
+    if (k == 0) A.nsamples += 1;
+}
+
+// The same sample into every level, by one thread: the arithmetic of obs_push_level
+// element by element (no staged loads, so the one thread holds few registers).
+__device__ __forceinline__ void obs_push(ObsAcc &A, const double x[MC_NOBS]) {
+    A.nsamples += 1;
+#pragma unroll 1
+    for (int k = 0; k < kNB; ++k) {
+        A.pcnt[k] += 1;
+        const bool done = A.pcnt[k] == (1LL << k);
+        const double inv = 1.0 / (double)(1LL << k);
+        for (int o = 0; o < MC_NOBS; ++o) {
+            A.psum[o][k] += x[o];
+            if (done) {
+                const double mean = A.psum[o][k] * inv;
+                A.bsum[o][k] += mean;
+                A.bsq[o][k] += mean * mean;
+                A.psum[o][k] = 0.0;
+            }
+        }
+        if (done) {
+            A.bcnt[k] += 1;
+            A.pcnt[k] = 0;
+        }
+    }
+}
+
 struct SweepConfig {
     int L, l, R;
     uint2 key;

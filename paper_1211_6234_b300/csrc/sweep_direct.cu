@@ -86,29 +86,6 @@ __device__ __forceinline__ int reduce_scatter_writer(int lane) {
 
 __host__ __device__ constexpr int pow2_at_least(int v) { return v <= 1 ? 1 : 2 * pow2_at_least((v + 1) / 2); }
 
-// One measurement sample into the binning accumulators (FP64, one thread).
-__device__ void obs_push(ObsAcc &A, const double x[MC_NOBS]) {
-    A.nsamples += 1;
-#pragma unroll 1
-    for (int k = 0; k < kNB; ++k) {
-        A.pcnt[k] += 1;
-        const bool done = A.pcnt[k] == (1LL << k);
-        const double inv = 1.0 / (double)(1LL << k);
-        for (int o = 0; o < MC_NOBS; ++o) {
-            A.psum[o][k] += x[o];
-            if (done) {
-                const double mean = A.psum[o][k] * inv;
-                A.bsum[o][k] += mean;
-                A.bsq[o][k] += mean * mean;
-                A.psum[o][k] = 0.0;
-            }
-        }
-        if (done) {
-            A.bcnt[k] += 1;
-            A.pcnt[k] = 0;
-        }
-    }
-}
 
 // Sites whose proposals the permutation schedule draws together (all threads, at the start
 // of every batch of sub-steps): a site is visited once per sweep, so its proposal depends

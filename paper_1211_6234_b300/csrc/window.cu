@@ -79,40 +79,6 @@ __device__ __forceinline__ bool bar_wait_bounded(uint64_t *m, uint32_t parity) {
     }
 }
 
-// One measurement sample into the log-binning accumulators (FP64, global memory):
-// thread k < kNB updates binning level k (blocks of 2^k samples); the levels are
-// independent, so their memory round trips overlap.
-__device__ void obs_push_level(ObsAcc &A, const double x[MC_NOBS], int k) {
-    const long long pc = A.pcnt[k] + 1;
-    const bool done = pc == (1LL << k);
-    const double inv = __longlong_as_double((long long)(1023 - k) << 52);   // 2^-k
-    double ps[MC_NOBS], bs[MC_NOBS], bq[MC_NOBS];
-#pragma unroll
-    for (int o = 0; o < MC_NOBS; ++o) {
-        ps[o] = A.psum[o][k];
-        bs[o] = A.bsum[o][k];
-        bq[o] = A.bsq[o][k];
-    }
-#pragma unroll
-    for (int o = 0; o < MC_NOBS; ++o) {
-        const double p = ps[o] + x[o];
-        if (done) {
-            const double mean = p * inv;
-            A.bsum[o][k] = bs[o] + mean;
-            A.bsq[o][k] = bq[o] + mean * mean;
-            A.psum[o][k] = 0.0;
-        } else {
-            A.psum[o][k] = p;
-        }
-    }
-    if (done) {
-        A.bcnt[k] += 1;
-        A.pcnt[k] = 0;
-    } else {
-        A.pcnt[k] = pc;
-    }
-    if (k == 0) A.nsamples += 1;
-}
 
 // W~ restricted to the minimum-image quarter 0 <= x, y <= L/2, as (xx, xy, yy, zz).
 // The tensor is even in x and in y except xy, which is odd in each: a
