@@ -88,8 +88,13 @@ typedef struct mc_obs {
     double mean[MC_NOBS];       /* sample means */
     double var[MC_NOBS];        /* sample variances (1/n) */
     double err_naive[MC_NOBS];  /* sqrt(var / (n - 1)) */
-    double err[MC_NOBS];        /* autocorrelation-corrected error (binning plateau) */
-    double tau_int[MC_NOBS];    /* 0.5 (err / err_naive)^2 */
+    double err[MC_NOBS];        /* autocorrelation-corrected error of the mean: the largest error of
+                                   the means of blocks of 2^k sweeps over the levels k >= 1 that
+                                   still hold >= 32 blocks, and never below err_naive.  It reaches
+                                   the true error only when a block of 2^k sweeps is long against
+                                   tau_int (a run of about 320 tau_int sweeps or more); shorter runs
+                                   underestimate it */
+    double tau_int[MC_NOBS];    /* 0.5 (err / err_naive)^2, in sweeps between samples */
     double eta;                 /* cone angle (Sec. 4.1): (1/N) sum_i sqrt((2/pi)^2 <(theta_i - pi/2)^2>) */
     double energy;              /* current energy per spin (tracked exactly, FP64) */
     int64_t accepted;           /* accepted single-site moves */
