@@ -16,7 +16,9 @@
  *     throws across the ABI.  mc_last_error() gives a one-line reason (per thread).
  *   - Handles are opaque and owned by the library (create/destroy).  Buffers
  *     passed in are owned by the caller; the library never keeps a pointer to
- *     them past the call.
+ *     them past the call.  A handle is not safe for concurrent calls: call the
+ *     functions of one handle from one host thread at a time (different handles
+ *     may be driven from different threads).
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *     Device work of a call is enqueued on that stream; calls that return host
  *     data synchronise it.
