@@ -632,15 +632,19 @@ int tc_plan(int L, int Sw, int R, int nsm, TcUnit *units, int max_units, int *NT
 // driver's encoder is reached through the runtime's entry-point query, so the
 // library does not link libcuda and loads on hosts without a driver.
 int tc_encode_map(void *map, const __nv_bfloat16 *spins, int L, int R, int NT) {
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    if (!encode) {
+    // looked up once per process (a function-local static: initialised once, even when
+    // several host threads drive handles of their own)
+    static const PFN_cuTensorMapEncodeTiled_v12000 encode = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
         void *fn = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-            q != cudaDriverEntryPointSuccess || !fn)
-            return -1;
-        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    }
+            q != cudaDriverEntryPointSuccess || !fn) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }();
+    if (!encode) return -1;
     const cuuint64_t dims[2] = {(cuuint64_t)3 * L * L, (cuuint64_t)R};
     const cuuint64_t strides[1] = {(cuuint64_t)3 * L * L * sizeof(__nv_bfloat16)};
     const cuuint32_t box[2] = {(cuuint32_t)kKB, (cuuint32_t)NT};
