@@ -478,7 +478,9 @@ int mc_server_collect(mc_server *srv, uint64_t id, int replica, mc_obs *out);
 /* Final spins of a DONE request, [replicas][3][L][L] FP32, to a host pointer. */
 int mc_server_get_spins(mc_server *srv, uint64_t id, float *dst_host);
 /* Drop a request in any state: a queued or running one stops (its slots are
- * refilled only behind the launch that still carries it); stored results are freed. */
+ * refilled only behind the launch that still carries it); its results and its record
+ * are freed.  Its id then polls as MC_REQ_RELEASED with 0 sweeps done, collecting from
+ * it gives MC_ENOTREADY, and releasing it again is a no-op. */
 int mc_server_release(mc_server *srv, uint64_t id);
 int mc_server_get_stats(mc_server *srv, mc_server_stats *out);
 int mc_server_destroy(mc_server *srv);

@@ -379,6 +379,10 @@ Req *find(mc_server *s, uint64_t id) {
     return it == s->reqs.end() ? nullptr : it->second.get();
 }
 
+// Ids are handed out in sequence and only mc_server_release drops a record, so an id
+// below next_id without a record was released.
+bool was_released(const mc_server *s, uint64_t id) { return id >= 1 && id < s->next_id && !s->reqs.count(id); }
+
 // Credit a finished launch to the requests it carried.
 void retire(mc_server *s, Runner &u, bool is_pack) {
     if (!u.inflight) return;
@@ -613,6 +617,11 @@ int mc_server_step(mc_server *s) {
 int mc_server_poll(mc_server *s, uint64_t id, int *state, int64_t *sweeps_done) {
     if (!s) return set_last_error(MC_EINVAL, "null server");
     Req *q = find(s, id);
+    if (!q && was_released(s, id)) {
+        if (state) *state = MC_REQ_RELEASED;
+        if (sweeps_done) *sweeps_done = 0;
+        return MC_OK;
+    }
     if (!q) return set_last_error(MC_EINVAL, "unknown request id");
     if (state) *state = q->state;
     if (sweeps_done) *sweeps_done = q->done;
@@ -622,6 +631,11 @@ int mc_server_poll(mc_server *s, uint64_t id, int *state, int64_t *sweeps_done) 
 int mc_server_request_info(mc_server *s, uint64_t id, mc_request_info *out) {
     if (!s || !out) return set_last_error(MC_EINVAL, "null argument");
     Req *q = find(s, id);
+    if (!q && was_released(s, id)) {
+        std::memset(out, 0, sizeof *out);
+        out->state = MC_REQ_RELEASED;
+        return MC_OK;
+    }
     if (!q) return set_last_error(MC_EINVAL, "unknown request id");
     std::memset(out, 0, sizeof *out);
     out->state = q->state;
@@ -640,6 +654,7 @@ int mc_server_request_info(mc_server *s, uint64_t id, mc_request_info *out) {
 int mc_server_collect(mc_server *s, uint64_t id, int replica, mc_obs *out) {
     if (!s || !out) return set_last_error(MC_EINVAL, "null argument");
     Req *q = find(s, id);
+    if (!q && was_released(s, id)) return set_last_error(MC_ENOTREADY, "request was released");
     if (!q) return set_last_error(MC_EINVAL, "unknown request id");
     if (q->state != MC_REQ_DONE) return set_last_error(MC_ENOTREADY, "request is not done");
     if (replica < 0 || replica >= q->r.replicas) return set_last_error(MC_EINVAL, "replica out of range");
@@ -650,6 +665,7 @@ int mc_server_collect(mc_server *s, uint64_t id, int replica, mc_obs *out) {
 int mc_server_get_spins(mc_server *s, uint64_t id, float *dst_host) {
     if (!s || !dst_host) return set_last_error(MC_EINVAL, "null argument");
     Req *q = find(s, id);
+    if (!q && was_released(s, id)) return set_last_error(MC_ENOTREADY, "request was released");
     if (!q) return set_last_error(MC_EINVAL, "unknown request id");
     if (q->state != MC_REQ_DONE) return set_last_error(MC_ENOTREADY, "request is not done");
     std::memcpy(dst_host, q->spins.data(), sizeof(float) * q->spins.size());
@@ -659,6 +675,7 @@ int mc_server_get_spins(mc_server *s, uint64_t id, float *dst_host) {
 int mc_server_release(mc_server *s, uint64_t id) {
     if (!s) return set_last_error(MC_EINVAL, "null server");
     Req *q = find(s, id);
+    if (!q && was_released(s, id)) return MC_OK;
     if (!q) return set_last_error(MC_EINVAL, "unknown request id");
     if (q->state == MC_REQ_RUNNING) {
         // A pack's launch that still carries the request runs on untouched; the
@@ -670,11 +687,9 @@ int mc_server_release(mc_server *s, uint64_t id) {
         }
         detach(s, *q);
     }
-    q->obs.clear();
-    q->obs.shrink_to_fit();
-    q->spins.clear();
-    q->spins.shrink_to_fit();
-    q->state = MC_REQ_RELEASED;
+    // the record goes too, so a long-lived server does not grow with the requests it
+    // has served; the id still polls as released (a queued id is skipped at admission)
+    s->reqs.erase(id);
     return MC_OK;
 }
 

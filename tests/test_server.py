@@ -202,17 +202,23 @@ def test_admission_waits_for_budget_in_arrival_order(dipmc):
 
 @gpu
 def test_release_frees_slots_for_the_next_request(dipmc):
-    """Releasing a running packed request frees its slot at once; a request that
-    takes the slot (filled behind the launch still in flight) matches its lone
-    run, and finished requests drop their results on release."""
+    """Releasing a running packed request frees its slot at once and drops its record
+    (the id still polls as released); a request that takes the slot (filled behind the
+    launch still in flight) matches its lone run, and finished requests drop their
+    results on release."""
     with dipmc.Server(hbm_budget_bytes=4 << 30, quantum_sweeps=5) as srv:
         long_id = srv.submit(L=32, l=8, T=0.7, sweeps=10**6, seed=41)
         srv.step()
         srv.step()
         assert srv.poll(long_id)[0] == dipmc.MC_REQ_RUNNING
         srv.release(long_id)
-        assert srv.poll(long_id)[0] == dipmc.MC_REQ_RELEASED
+        assert srv.poll(long_id) == (dipmc.MC_REQ_RELEASED, 0)   # the record is gone, the id is known
+        assert srv.info(long_id)["state"] == dipmc.MC_REQ_RELEASED
+        srv.release(long_id)                                      # a second release is a no-op
         assert srv.stats()["running"] == 0
+        with pytest.raises(dipmc.McError) as e:
+            srv.poll(long_id + 10**6)                             # never handed out
+        assert e.value.code == dipmc.MC_EINVAL
         rid = srv.submit(L=32, l=8, T=0.5, sweeps=12, seed=42)
         srv.run_until_done([rid], timeout_s=120)
         spins_lone, obs_lone = lone_run(dipmc, L=32, l=8, T=0.5, sweeps=12, seed=42, path=srv.info(rid)["path"])
