@@ -69,3 +69,19 @@ def test_binding_constants_match_the_header():
     for k in consts:
         if re.match(r"MC_(OK|E[A-Z]+|PATH_\w+|REQ_\w+|NOBS)$", k):
             assert k in shared, k
+
+
+def test_observable_and_kernel_class_orders_match_the_header():
+    """OBS_NAMES and KERNEL_CLASSES index the header's MC_OBS_* and MC_K_* arrays."""
+    from paper_1211_6234_b300 import dipmc
+    consts = header_constants()
+    obs = {k[len("MC_OBS_"):]: v for k, v in consts.items() if k.startswith("MC_OBS_")}
+    names = {"ABS_M": "abs_m", "MZ": "m_z", "ABS_MZ": "abs_m_z", "MPAR": "m_par", "E": "e", "MST": "m_st",
+             "WALL": "wall", "OX": "o_x", "OY": "o_y", "OZ": "o_z", "CONE": "cone"}
+    assert len(obs) == consts["MC_NOBS"] == len(dipmc.OBS_NAMES)
+    for k, v in obs.items():
+        assert dipmc.OBS_NAMES[v] == names[k], k
+    kc = {k[len("MC_K_"):].lower(): v for k, v in consts.items() if k.startswith("MC_K_")}
+    assert len(kc) == consts["MC_NKCLASS"] == len(dipmc.KERNEL_CLASSES)
+    for k, v in kc.items():
+        assert dipmc.KERNEL_CLASSES[v] == k, k
