@@ -1570,9 +1570,17 @@ int mc_autotune(mc_lattice *p, int nsweeps_trial, void *stream, int *path_out, i
     if (path_supported(p, MC_PATH_INCREMENTAL)) cands.push_back({MC_PATH_INCREMENTAL, 0});
     if (path_supported(p, MC_PATH_FFT_CLUSTER)) cands.push_back({MC_PATH_FFT_CLUSTER, 0});
     if (cands.empty()) return fail(MC_ENOSYS, "no field path supports L=%d l=%d", p->L, p->l);
-    cudaEvent_t a, b;
-    CK(cudaEventCreate(&a));
-    CK(cudaEventCreate(&b));
+    // the timing events are destroyed on every return below, early ones included
+    struct EventPair {
+        cudaEvent_t a = nullptr, b = nullptr;
+        ~EventPair() {
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+        }
+    } events;
+    CK(cudaEventCreate(&events.a));
+    CK(cudaEventCreate(&events.b));
+    cudaEvent_t a = events.a, b = events.b;
     float best = 1e30f;
     Cand win = cands[0];
     for (const Cand &c : cands) {
@@ -1625,11 +1633,7 @@ int mc_autotune(mc_lattice *p, int nsweeps_trial, void *stream, int *path_out, i
                 *fields[f] = v;
                 float ms = 0.f;
                 const int r = trial(&ms);
-                if (r == MC_ETIMEOUT || r == MC_ECUDA) {
-                    cudaEventDestroy(a);
-                    cudaEventDestroy(b);
-                    return r;
-                }
+                if (r == MC_ETIMEOUT || r == MC_ECUDA) return r;
                 if (!r && ms < bf) {
                     bf = ms;
                     keep = v;
@@ -1639,8 +1643,6 @@ int mc_autotune(mc_lattice *p, int nsweeps_trial, void *stream, int *path_out, i
         }
         drop_graphs(p);
     }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
     if (path_out) *path_out = win.path;
     if (window_out) *window_out = win.B;
     return MC_OK;
