@@ -209,6 +209,8 @@ struct TimedLaunch {
         if (a && b) {
             cudaEventRecord(b, st);
             p->tev[cls].push_back({a, b});
+        } else if (a) {
+            cudaEventDestroy(a);   // the second event could not be created
         }
     }
 };

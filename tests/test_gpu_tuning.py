@@ -109,3 +109,29 @@ def test_autotune_tunes_tensor_shapes_and_keeps_state(dipmc):
         print(f"\nautotune 256 x L=64: path {path}, window {win}, tuning {tun}")
         lat.sweep(2, 1)
         assert lat.observables(0)["samples"] == 2
+
+
+def test_kernel_timing_records_every_launch_of_a_call(dipmc):
+    """With timing on, every launch of a call is bracketed by CUDA events (and the call
+    is not replayed from a graph): two sweeps of the tensor path at 4 x L = 64, l = 32
+    with 512-site windows (eight windows a sweep) record 16 tensor-core field and 16
+    sub-step launches with positive times, and the sub-step kernel's clock counters
+    report 32 blocks of 16 sites a launch; turning timing off clears the record."""
+    with dipmc.Lattice(64, 32, 4, 3) as lat:
+        lat.precompute_W(16, True)
+        lat.set_field_path(dipmc.MC_PATH_TENSOR)
+        lat.set_window(128)
+        lat.init_spins(0)
+        lat.sweep(1, 1)                  # buffers, tables and the energy anchor outside the record
+        lat.set_timing(True)
+        lat.sweep(2, 1)
+        t = lat.timing()
+        cyc = lat.window_cycles()
+        lat.set_timing(False)
+        t_off = lat.timing()
+    assert t["tc_field"]["launches"] == 16 and t["window_steps"]["launches"] == 16
+    assert t["tc_field"]["ms"] > 0 and t["window_steps"]["ms"] > 0
+    assert t["sweep_direct"]["launches"] == 0
+    assert cyc["blocks_per_launch"] == 32
+    assert cyc["per_block"] > 0 and cyc["setup"] > 0 and cyc["tail"] > 0
+    assert all(v["launches"] == 0 for v in t_off.values())
