@@ -94,15 +94,21 @@ def pooled(means) -> tuple:
     return float(x.mean()), float(x.std(ddof=1) / math.sqrt(len(x)))
 
 
-def binned_error(x: np.ndarray, min_blocks: int = 32) -> float:
-    """Autocorrelation-corrected standard error by blocking: the largest error over
-    block sizes 2^k that leave at least min_blocks blocks."""
+def binning_reference(x, min_blocks=32):
+    """Textbook binning analysis of one time series x (Flyvbjerg and Petersen): the
+    population variance, the naive error of the mean, and the autocorrelation-corrected
+    error as the largest error of the means of blocks of 2^k samples over the levels that
+    still hold min_blocks blocks (never below the naive one), with tau_int = (err/naive)^2 / 2."""
     x = np.asarray(x, np.float64)
     n = len(x)
-    best = x.std() / math.sqrt(max(n - 1, 1))
-    b = 2
-    while n // b >= min_blocks:
-        m = x[: (n // b) * b].reshape(-1, b).mean(1)
-        best = max(best, m.std() / math.sqrt(len(m) - 1))
-        b *= 2
-    return best
+    var = max(0.0, float(np.mean(x * x) - np.mean(x) ** 2))
+    naive = math.sqrt(var / (n - 1))
+    err, k = naive, 1
+    while n >> k >= min_blocks:
+        nb = n >> k
+        b = x[: nb << k].reshape(nb, 1 << k).mean(axis=1)
+        vk = max(0.0, float(np.mean(b * b) - np.mean(b) ** 2))
+        err = max(err, math.sqrt(vk / (nb - 1)))
+        k += 1
+    tau = 0.5 * (err / naive) ** 2 if naive > 0 else float("nan")
+    return var, naive, err, tau

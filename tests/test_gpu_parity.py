@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 from oracle import oracle as orc  # noqa: E402
 from paper_1211_6234_b300 import inputs  # noqa: E402
-from tests.parity_util import F32, compare_trace, pooled, resync  # noqa: E402
+from tests.parity_util import F32, binning_reference, compare_trace, pooled, resync  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -181,25 +181,6 @@ def test_observables_statistically_match_oracle(dipmc, T):
     a, ea = pooled([g["eta"] for g in og])
     b, eb = pooled([orc.eta(o["theta2"][r], nsw) for r in range(R_orc)])
     assert abs(a - b) <= 3 * math.hypot(ea, eb), ("eta", a, b, ea, eb)
-
-
-def binning_reference(x, min_blocks=32):
-    """Textbook binning analysis of one time series x (Flyvbjerg and Petersen): the
-    population variance, the naive error of the mean, and the autocorrelation-corrected
-    error as the largest error of the means of blocks of 2^k samples over the levels that
-    still hold min_blocks blocks (never below the naive one), with tau_int = (err/naive)^2 / 2."""
-    n = len(x)
-    var = max(0.0, float(np.mean(x * x) - np.mean(x) ** 2))
-    naive = math.sqrt(var / (n - 1))
-    err, k = naive, 1
-    while n >> k >= min_blocks:
-        nb = n >> k
-        b = x[: nb << k].reshape(nb, 1 << k).mean(axis=1)
-        vk = max(0.0, float(np.mean(b * b) - np.mean(b) ** 2))
-        err = max(err, math.sqrt(vk / (nb - 1)))
-        k += 1
-    tau = 0.5 * (err / naive) ** 2 if naive > 0 else float("nan")
-    return var, naive, err, tau
 
 
 @pytest.mark.parametrize("path", [1, 2, 3, 4, 5, 6, 7],

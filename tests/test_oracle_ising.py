@@ -12,7 +12,12 @@ import pytest
 from scipy.special import ellipk
 
 from oracle import oracle as orc
-from tests.parity_util import binned_error
+from tests.parity_util import binning_reference
+
+
+def _err(x):
+    """Autocorrelation-corrected standard error of the mean of a series (binning)."""
+    return binning_reference(x)[2]
 
 
 def ising_state(L, pattern):
@@ -94,8 +99,8 @@ def test_onsager_energy_and_magnetisation():
     s = orc.sweeps(p, W, s, 0, 500, trace=False)["s"]            # equilibrate
     o = orc.sweeps(p, W, s, 500, 12000, trace=False, observe=True)
     e, m = o["obs"][:, 4], o["obs"][:, 2]
-    assert abs(e.mean() - u_exact) < 4 * binned_error(e) + 2e-4, (e.mean(), u_exact, binned_error(e))
-    assert abs(m.mean() - m_exact) < 4 * binned_error(m) + 2e-4, (m.mean(), m_exact, binned_error(m))
+    assert abs(e.mean() - u_exact) < 4 * _err(e) + 2e-4, (e.mean(), u_exact, _err(e))
+    assert abs(m.mean() - m_exact) < 4 * _err(m) + 2e-4, (m.mean(), m_exact, _err(m))
 
 
 def test_exact_enumeration_4x4_with_dipoles():
@@ -127,8 +132,8 @@ def test_exact_enumeration_4x4_with_dipoles():
     s = orc.sweeps(p, W, s, 0, 2000, trace=False)["s"]
     o = orc.sweeps(p, W, s, 2000, 150000, trace=False, observe=True)
     e, m = o["obs"][:, 4], o["obs"][:, 5]
-    assert abs(e.mean() - e_exact) < 4 * binned_error(e) + 1e-4, (e.mean(), e_exact, binned_error(e))
-    assert abs(m.mean() - m_exact) < 4 * binned_error(m) + 1e-4, (m.mean(), m_exact, binned_error(m))
+    assert abs(e.mean() - e_exact) < 4 * _err(e) + 1e-4, (e.mean(), e_exact, _err(e))
+    assert abs(m.mean() - m_exact) < 4 * _err(m) + 1e-4, (m.mean(), m_exact, _err(m))
 
 
 @pytest.mark.parametrize("pattern,wall,oz", [("ferro", 0.0, 0.0), ("checker", 1.0, 0.0), ("hstripes", 0.5, 1.0),
@@ -162,5 +167,5 @@ def test_walls_and_cone_of_random_states():
     W = orc.wtilde(L, 4, True)
     p = orc.params(L, 2, 0.0, 0.0, 0.0, 0.0, 1.0, proposal=1, seed=3)
     o = orc.sweeps(p, W, orc.init_random(L, 7), 0, 200, trace=False, observe=True)["obs"]
-    assert o[:, 6].mean() == pytest.approx(0.5, abs=4 * binned_error(o[:, 6]) + 1e-4)
-    assert o[:, 10].mean() == pytest.approx(1 - 2 / math.pi, abs=4 * binned_error(o[:, 10]) + 1e-4)
+    assert o[:, 6].mean() == pytest.approx(0.5, abs=4 * _err(o[:, 6]) + 1e-4)
+    assert o[:, 10].mean() == pytest.approx(1 - 2 / math.pi, abs=4 * _err(o[:, 10]) + 1e-4)

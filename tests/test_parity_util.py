@@ -91,3 +91,27 @@ def test_compare_trace_counts_straddles_and_rejects_real_mismatches():
     tr, o = _toy(T, [0.2], [0.2 + 1e-3], [0.25], [1], [1])
     with pytest.raises(AssertionError):
         compare_trace(tr, o, T, scale=1.0)
+
+
+def test_binning_reference_on_series_of_known_autocorrelation():
+    """The numpy binning analysis that the GPU error-bar tests compare every path's
+    accumulators with: on independent samples its corrected error stays near the naive
+    one (tau_int near 1/2); on AR(1) series x_t = rho x_(t-1) + sqrt(1 - rho^2) e_t it
+    reaches the closed form tau_int = (1 + rho) / (2 (1 - rho)) of the integrated
+    autocorrelation time (2^17 samples; rho = 0.5, 0.8, 0.95)."""
+    from scipy.signal import lfilter
+
+    from tests.parity_util import binning_reference
+    rng = np.random.default_rng(5)
+    x = rng.normal(size=1 << 16)
+    var, naive, err, tau = binning_reference(x)
+    assert abs(var - 1.0) < 0.03
+    assert naive == pytest.approx(math.sqrt(var / (len(x) - 1)), rel=1e-12)
+    assert err >= naive and 0.5 <= tau < 0.9
+    for rho in (0.5, 0.8, 0.95):
+        e = rng.normal(size=1 << 17)
+        y = lfilter([math.sqrt(1.0 - rho * rho)], [1.0, -rho], e)
+        _, _, _, tau = binning_reference(y)
+        expect = (1.0 + rho) / (2.0 * (1.0 - rho))
+        # the largest error over the levels leans high by the scatter of the deep levels
+        assert 0.9 < tau / expect < 1.25, (rho, tau, expect)
