@@ -14,7 +14,9 @@ the derivations the kernels rest on, written out with numpy from their definitio
     U_d(k) = sum_P (-1)^(k.P) W~(d + l P), and W~(d + l P) is the inverse 2 x 2 transform
     of U_d (its pair-energy table);
   * W~ is even, so its 2D transform is real (the FFT path), and the field at the rows
-    y_i = o_y + l i needs only the transform's rows summed by k_y mod C (the cluster path).
+    y_i = o_y + l i needs only the transform's rows summed by k_y mod C (the cluster path);
+  * a window's field is the stale field at its start plus the change from the moves it
+    accepted in earlier sub-steps (every windowed path).
 """
 import numpy as np
 import pytest
@@ -116,3 +118,38 @@ def test_real_transform_of_w_and_rows_grouped_by_ky_mod_C(L, l):
         xs = ox + l * np.arange(C)
         hq = np.einsum("jx,cix->cij", np.exp(2j * np.pi * np.outer(xs, kx) / L), G).real / (L * L)
         np.testing.assert_allclose(hq, h[:, oy::l, ox::l], rtol=0, atol=1e-11 * np.abs(h).max())
+
+
+@pytest.mark.parametrize("L,l,B,schedule", [(16, 8, 16, 0), (16, 4, 8, 0), (12, 6, 12, 0), (16, 8, 16, 1)])
+def test_window_field_is_the_stale_field_plus_the_windows_earlier_moves(L, l, B, schedule):
+    """The windowed paths evaluate the field at all of a window's sites once, on the state
+    at the window's start, and add per sub-step the change from the moves the window
+    accepted in earlier sub-steps (linearity of Eq. 2; a sub-step's own sites are decided
+    together from the pre-step state, Sec. 3.1).  Along the oracle's own sweep, whose every
+    sub-step takes the full field of the current state, that decomposition reproduces the
+    field of every attempt, also under the with-replacement schedule where a site may recur."""
+    n = (L // l) ** 2
+    p = orc.params(L, l, 1.0, 0.1, 0.8, 0.0, 0.6, proposal=0, cone=0.5, schedule=schedule, seed=9)
+    W = orc.wtilde(L, 8, True)
+    s0 = inputs.random_spins(L, 1, seed=4)[0]
+    o = orc.sweeps(p, W, s0, 0, 1, trace=True)
+    cur = s0.reshape(3, -1).copy()
+    scale = np.abs(o["h"]).max()
+    for w0 in range(0, l * l, B):
+        h0 = orc.field(W, cur.reshape(3, L, L)).reshape(3, -1)
+        moves = []                                                # (x, y, change) accepted in the window
+        for k in range(w0, w0 + B):
+            rows = range(k * n, (k + 1) * n)
+            for a in rows:
+                q = int(o["q"][a])
+                qx, qy = q % L, q // L
+                pred = h0[:, q].copy()
+                for px, py, dv in moves:
+                    pred += apply_w(wt(W, qx - px, qy - py), dv)
+                np.testing.assert_allclose(pred, o["h"][a], rtol=0, atol=1e-12 * scale)
+            for a in rows:                                        # then the sub-step's accepted moves
+                if o["acc"][a]:
+                    q = int(o["q"][a])
+                    moves.append((q % L, q // L, o["S"][a] - cur[:, q]))
+                    cur[:, q] = o["S"][a]
+    np.testing.assert_array_equal(cur.reshape(3, L, L), o["s"])
