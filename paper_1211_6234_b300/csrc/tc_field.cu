@@ -13,7 +13,7 @@
 //               chunk is an aligned vector load),
 //     B       = the spins of the replicas, bf16 hi/lo, row r = [x-plane | y-plane | z-plane].
 // Each value v is split v = hi + lo (hi = bf16(v), lo = bf16(v - hi)) and the
-// product is hi_A hi_B + hi_A lo_B + lo_A hi_B (error ~2^-18 relative).
+// product is hi_A hi_B + hi_A lo_B + lo_A hi_B (off by at most ~3 x 2^-16 relative).
 //
 // One CTA = one (M-tile of 128 rows, N-tile of up to 256 replicas, range of
 // K-blocks of 32).  Operands sit in the canonical K-major, no-swizzle
