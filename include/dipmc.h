@@ -443,15 +443,18 @@ typedef struct mc_server mc_server;
 int mc_footprint(int L, int l, int replicas, size_t *bytes);
 
 /*
- * Requests whose (L, l) the direct path serves share packed launches: one handle
+ * Requests whose (L, l) the direct path serves, with L < 128, share packed launches: one handle
  * whose replica slots belong to different requests, each slot with its own seed,
  * sweep counter and sweep budget, so that a request's result is bit-identical to
  * the same request run alone on a lone handle (mc_create_lattice with its seed,
  * mc_set_params, mc_precompute_W(A, 1), mc_init_spins, mc_sweep).  Direct packs of
  * different L with the same L / l, proposal and measurement interval whose busy
  * slots fit one resident wave together run as one launch (as mc_sweep_group),
- * still bit-identical to each request's lone run.  Other requests get a lone
- * handle of their own.  Handles run on separate streams and overlap.
+ * still bit-identical to each request's lone run.  Larger lattices (L >= 128, or
+ * (L, l) outside the direct path) share spectral packs, else FFT packs, whose
+ * launches run all slots' sub-steps together, again bit-identical to each request's
+ * lone run on that path.  A request that fits no pack gets a lone handle of its own.
+ * Packs and lone handles run on separate streams and overlap.
  *
  * Requests are admitted in arrival order while the device bytes of the handles
  * they need fit hbm_budget_bytes and fewer than max_active are running; a packed
@@ -471,7 +474,11 @@ int mc_server_submit(mc_server *srv, const mc_request *req, uint64_t *id);
  * the next quantum everywhere idle.  Does not wait for the GPU except to read the
  * results of a request that just finished; call it repeatedly. */
 int mc_server_step(mc_server *srv);
+/* State (MC_REQ_*) and sweeps completed of a request; either pointer may be NULL.
+ * MC_EINVAL for an id the server never handed out. */
 int mc_server_poll(mc_server *srv, uint64_t id, int *state, int64_t *sweeps_done);
+/* State, chosen spacing and path, packing, submit/admit/done times (steady clock, s),
+ * device bytes and the failure reason of a request. */
 int mc_server_request_info(mc_server *srv, uint64_t id, mc_request_info *out);
 /* Observables of one replica of a DONE request (as mc_observables).  MC_ENOTREADY otherwise. */
 int mc_server_collect(mc_server *srv, uint64_t id, int replica, mc_obs *out);
@@ -482,7 +489,9 @@ int mc_server_get_spins(mc_server *srv, uint64_t id, float *dst_host);
  * are freed.  Its id then polls as MC_REQ_RELEASED with 0 sweeps done, collecting from
  * it gives MC_ENOTREADY, and releasing it again is a no-op. */
 int mc_server_release(mc_server *srv, uint64_t id);
+/* Counts of requests by state, packs and lone handles held, device bytes in use. */
 int mc_server_get_stats(mc_server *srv, mc_server_stats *out);
+/* Wait for the server's launches, free its handles and memory.  NULL is a no-op. */
 int mc_server_destroy(mc_server *srv);
 
 #ifdef __cplusplus
