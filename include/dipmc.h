@@ -450,7 +450,7 @@ int mc_footprint(int L, int l, int replicas, size_t *bytes);
  * mc_set_params, mc_precompute_W(A, 1), mc_init_spins, mc_sweep).  Direct packs of
  * different L with the same L / l, proposal and measurement interval whose busy
  * slots fit one resident wave together run as one launch (as mc_sweep_group),
- * still bit-identical to each request's lone run.  Larger lattices (L >= 128, or
+ * still bit-identical to each request's lone run.  Other lattices (L >= 128, or
  * (L, l) outside the direct path) share spectral packs, else FFT packs, whose
  * launches run all slots' sub-steps together, again bit-identical to each request's
  * lone run on that path.  A request that fits no pack gets a lone handle of its own.
