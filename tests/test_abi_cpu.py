@@ -76,3 +76,20 @@ def test_choose_spacing_against_oracle_error_estimate(L, CD, T, err):
     for m in range(2, l):
         if L % m == 0:
             assert orc.eps_total(L, m, CD, T, 1, 64) + tail(m) > err
+
+
+def test_binding_without_the_library_fails_to_import(tmp_path):
+    """A copy of the package without libdipmc.so: importing the binding raises
+    ImportError naming the missing library, so no call can run anywhere but in it."""
+    import shutil
+    import sys
+    pkg = tmp_path / "paper_1211_6234_b300"
+    pkg.mkdir()
+    for f in ("__init__.py", "dipmc.py", "inputs.py"):
+        shutil.copy(os.path.join(ROOT, "paper_1211_6234_b300", f), pkg / f)
+    code = ("import sys; sys.path.insert(0, sys.argv[1])\n"
+            "try:\n    import paper_1211_6234_b300.dipmc\nexcept ImportError as e:\n"
+            "    print('IMPORT-ERROR', e); sys.exit(0)\nsys.exit(3)\n")
+    r = subprocess.run([sys.executable, "-c", code, str(tmp_path)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, (r.stdout, r.stderr)
+    assert "IMPORT-ERROR" in r.stdout and "libdipmc.so" in r.stdout and "not built" in r.stdout
